@@ -1,0 +1,295 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Gabor filter bank (arXiv 1704.05231, Algorithm 1).
+
+Workload (default): the paper-size bank - one 1024 x 1024 FP32 image (1/f^2 noise plus eight
+oriented sinusoids, seed 0), 6 orientations k pi / 6 x 4 frequencies pi/2 .. pi/16 with
+sigma = pi / omega and radius 3 sigma, complex64 outputs: 24 pixel-filter outputs per pixel.
+A step is one call of the bank on that image (every row of the hot path: tables are built
+before timing; horizontal pass, orientation reuse, vertical pass and stores inside).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead, on a
+bounded pixel sample of the same workload.  Multi-GPU runs are independent replicas (weak
+scaling): the bank has no exchange step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gabor bank pixel·filter outputs/s, plain vs TC at ≤2e-3 rel err; serve p99 ms"
+UNIT = "outputs/s"
+H = W = 1024
+
+
+def workload():
+    from paper_1704_05231_gb300 import synth
+    thetas = [k * math.pi / 6 for k in range(6)]
+    omegas = [math.pi / 2, math.pi / 4, math.pi / 8, math.pi / 16]
+    sigmas = [math.pi / w for w in omegas]
+    img = synth.paper_like(0, H, W)
+    return img, thetas, omegas, sigmas
+
+
+def workload_config(extra=None):
+    cfg = {"workload": "paper-size Gabor bank: 1024x1024 FP32 1/f^2 noise + 8 sinusoids (seed 0), "
+                       "6 orientations k*pi/6 x 4 frequencies pi/2..pi/16, sigma=pi/omega, radius 3 sigma, "
+                       "complex64 out",
+           "H": H, "W": W, "n_theta": 6, "n_freq": 4, "outputs_per_step": 24 * H * W,
+           "l2": "flushed between steps (256 MiB write); output 201 MB > L2"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def radius(sigma, rf=3.0):
+    return int(math.ceil(rf * sigma - 1e-9))
+
+
+def algorithmic_flops(thetas, omegas, sigmas, Hh=H, Ww=W):
+    """FLOPs of the decomposition (FIR form): per pixel and frequency (3N+1) T FMAs."""
+    n = len(thetas)
+    fma = sum((3 * n + 1) * (2 * radius(s) + 1) for s in sigmas) * Hh * Ww
+    return 2.0 * fma
+
+
+def fp32_peak_tflops(torch):
+    """FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 FLOP x max SM clock."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(img, thetas, omegas, sigmas, seconds):
+    """The FP64 oracle as it stands, on a time-boxed random pixel sample, all host cores."""
+    import numpy as np
+    import oracle
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(123)
+    n_px = 0
+    t0 = time.perf_counter()
+    while True:
+        xs = rng.integers(0, W, 256).astype(np.int32)
+        ys = rng.integers(0, H, 256).astype(np.int32)
+        oracle.gabor_bank(img, thetas, omegas, sigmas, points=(xs, ys), threads=cores)
+        n_px += 256
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    nout = n_px * len(thetas) * len(omegas)
+    return {"value": nout / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_px} random pixels x {len(thetas) * len(omegas)} filters of the 1024x1024 "
+                      f"bank (direct FP64 sums), {el:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on bounded samples, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    img, thetas, omegas, sigmas = workload()
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(321)
+    per_step = 256
+
+    def step():
+        xs = rng.integers(0, W, per_step).astype(np.int32)
+        ys = rng.integers(0, H, per_step).astype(np.int32)
+        oracle.gabor_bank(img, thetas, omegas, sigmas, points=(xs, ys), threads=cores)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    nout = per_step * len(thetas) * len(omegas)
+    value = nout * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": workload_config({"sample_per_step": f"{per_step} random pixels x 24 filters"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} random pixels x 24 filters per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1704_05231_gb300 import GaborBank
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    img, thetas, omegas, sigmas = workload()
+    n_out = len(thetas) * len(omegas) * H * W
+    gbk = GaborBank(thetas, omegas, sigmas, precision="fp32", max_shape=(H, W))
+    d_img = torch.from_numpy(img).cuda()
+    out = torch.empty(gbk.out_shape(H, W), dtype=torch.complex64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(3, args.warmup)):
+        gbk.filter(d_img, out)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        gbk.filter(d_img, out)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = statistics.mean(step_ms)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n_out * world / (ms * 1e-3)
+
+    # End to end through the C ABI on host buffers (pinned): H2D image, bank, D2H result.
+    e2e_s = float("nan")
+    if not args.no_e2e:
+        h_img = torch.from_numpy(img).pin_memory()
+        h_out = torch.empty(gbk.out_shape(H, W), dtype=torch.complex64).pin_memory()
+        gbk.filter_host_ptr(h_img.data_ptr(), H, W, W, h_out.data_ptr())
+        e2e_steps = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(e2e_steps):
+            gbk.filter_host_ptr(h_img.data_ptr(), H, W, W, h_out.data_ptr())
+        e2e_s = (time.perf_counter() - t1) / e2e_steps
+
+    flops = algorithmic_flops(thetas, omegas, sigmas)
+    peak, sms, mhz = fp32_peak_tflops(torch)
+    achieved = flops / (ms * 1e-3) / 1e12
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config({"path": "FP32 CUDA-core fused bank kernel", "parallelism": f"replicas x{world}"}),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_gabor_fp32 (4 launches per step, one per frequency)",
+                         "peak_note": f"derived: {sms} SMs x 128 FP32 lanes x 2 FLOP x {mhz:.0f} MHz",
+                         "algorithmic": "(3N+1)(2R+1) FMA per pixel per frequency"},
+            "e2e": None if args.no_e2e else {
+                "value": n_out / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H * W * 4,
+                "d2h_bytes_per_step": n_out * 8, "path": "gabor_bank_filter_host, pinned buffers"},
+            "gpu_launches": 4 * args.steps,
+            "clocks": clocks,
+            "wall_s": wall}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(img, thetas, omegas, sigmas, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    gbk.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

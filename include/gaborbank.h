@@ -1,0 +1,171 @@
+/*
+ * gaborbank.h - C ABI of a GB300 (sm_103a) library computing the 2-D complex Gabor filter
+ * bank and the 2-D localized sliding DFT of Um, Kim and Min, "Fast 2-D Complex Gabor Filter
+ * with Kernel Decomposition" (arXiv 1704.05231).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Images are single-channel FP32, row-major: pixel (x, y) is img[y * pitch + x], x the
+ *    column (the paper's k / m index, horizontal), y the row (l / n, vertical).
+ *    pitch >= W counts elements, not bytes.
+ *  - Outputs are complex64: interleaved (re, im) float pairs, plane-major, each plane H x W
+ *    with row stride W.  The library never allocates or frees caller buffers.
+ *  - The image is zero outside [0, W) x [0, H); every output has the input's size.
+ *  - The Gaussian is S_sigma(d) = exp(-d^2 / (2 sigma^2)) / (sqrt(2 pi) sigma), truncated
+ *    to |d| <= R = ceil(radius_factor * sigma), not renormalised (Sec. II).
+ *  - Functions taking device pointers are asynchronous with respect to the host: they
+ *    enqueue work on `stream` (a cudaStream_t; NULL = the legacy default stream) and return.
+ *    Arguments are validated synchronously.  An asynchronous CUDA error surfaces as
+ *    GB_ERR_CUDA from a later call.  Functions taking host pointers are synchronous.
+ *  - A handle must not be used from two host threads, or on two streams, at the same time.
+ *  - No C++ exception and no abort crosses this interface.  On failure a function returns
+ *    a negative gb_status and gabor_bank_last_error() describes the failure; outputs are
+ *    then unspecified.
+ *  - Work queued by one call may still run when the next call on another stream starts.
+ *    Calls on one stream run in order.
+ */
+#ifndef GABORBANK_H
+#define GABORBANK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gabor_bank *gabor_bank_t; /* opaque; owned by the library */
+
+typedef enum {
+    GB_OK = 0,
+    GB_ERR_INVALID_ARG = -1,   /* NULL pointer, bad size, non-finite or non-positive value */
+    GB_ERR_OUT_OF_MEMORY = -2, /* a device or host allocation failed */
+    GB_ERR_CUDA = -3,          /* a CUDA runtime call failed (possibly from earlier work) */
+    GB_ERR_UNSUPPORTED = -4,   /* valid but not implemented: odd M, too large a radius ... */
+    GB_ERR_BUDGET = -5,        /* the request does not fit the handle's memory budget */
+    GB_ERR_TIMEOUT = -6        /* a bounded device wait gave up (see gabor_bank_device_status) */
+} gb_status;
+
+typedef enum {
+    GB_FP32 = 0,    /* FP32 CUDA-core path: |err| <= 1e-5 * max|out| against FP64 */
+    GB_FP16_TC = 1, /* tcgen05 tensor cores, FP16 operands, FP32 accumulation */
+    GB_BF16_TC = 2  /* tcgen05 tensor cores, BF16 operands, FP32 accumulation */
+} gb_precision;
+
+/*
+ * gabor_bank_create - build a filter-bank plan (Algorithm 1, inputs Sigma, Omega, Theta).
+ *
+ * theta[n_theta]   orientations in radians, any order and any value.  When both theta and
+ *                  pi - theta (to 1e-9 rad) are present, the horizontal pass of theta is
+ *                  computed once and reused for pi - theta through J_{pi-theta} = J*_theta
+ *                  (Eq. 13-16).
+ * omega[n_freq]    centre frequencies in radians per pixel (finite).
+ * sigma[n_freq]    Gaussian standard deviations in pixels (> 0), one per frequency.  The
+ *                  paper ties sigma to omega inconsistently (Algorithm 1 vs Fig. 1); the
+ *                  library takes sigma as given.
+ * radius_factor    R_s = ceil(radius_factor * sigma_s); 0 selects 3.
+ * prec             arithmetic of gabor_bank_filter / gabor_bank_sdft (see gb_precision).
+ * max_H, max_W     largest image the handle will see, used to size internal tables now
+ *                  (0, 0: size them on first use).
+ * n_theta = n_freq = 0 creates an SDFT-only handle.
+ * Returns GB_OK and *out, or an error (and *out = NULL).  The handle owns device tables and
+ * workspace; it binds to the CUDA device current at creation.
+ */
+gb_status gabor_bank_create(gabor_bank_t *out, const double *theta, int n_theta,
+                            const double *omega, const double *sigma, int n_freq,
+                            double radius_factor, gb_precision prec, int max_H, int max_W);
+
+/* gabor_bank_destroy - synchronise the device and free everything; NULL is allowed. */
+gb_status gabor_bank_destroy(gabor_bank_t h);
+
+/*
+ * gabor_bank_filter - the 2-D complex Gabor filter bank of Eq. 1 for every (omega_s,
+ * theta_k) of the plan, computed by the kernel decomposition of Sec. II (Eq. 3-10) with
+ * the orientation reuse of Sec. II-B (Eq. 11-16, Algorithm 1).
+ *
+ * d_img  device FP32 image, H x W, row stride `pitch` elements (pitch >= W).
+ * d_out  device complex64 buffer of n_freq * n_theta * H * W elements (8 bytes each):
+ *        out[s][k][y][x] = F_{omega_s, theta_k, sigma_s}(x, y).  16-byte aligned.
+ * stream cudaStream_t or NULL.
+ * Asynchronous.  Errors: GB_ERR_INVALID_ARG (NULL, H/W <= 0, pitch < W, misaligned),
+ * GB_ERR_UNSUPPORTED (radius above the library limit of 256 px), GB_ERR_CUDA.
+ */
+gb_status gabor_bank_filter(gabor_bank_t h, const float *d_img, int H, int W, int64_t pitch,
+                            void *d_out, void *stream);
+
+/*
+ * gabor_bank_filter_host - gabor_bank_filter on HOST buffers: copies the image to the
+ * device, filters, copies the result back and synchronises `stream`.  h_out holds
+ * n_freq * n_theta * H * W complex64.  Pinned (page-locked) host buffers give full copy
+ * bandwidth; pageable ones work too.  Device staging buffers are owned by the handle and
+ * grow on demand.  Synchronous.  Errors as gabor_bank_filter, plus GB_ERR_OUT_OF_MEMORY.
+ */
+gb_status gabor_bank_filter_host(gabor_bank_t h, const float *h_img, int H, int W,
+                                 int64_t pitch, void *h_out, void *stream);
+
+/*
+ * gabor_bank_sdft - the 2-D localized sliding DFT with a Gaussian window (Eq. 17-26,
+ * Algorithm 2): for every pixel (x, y) and bin (u, v), u in [0, Mx), v in [0, My),
+ *   F_{u,v}(x,y) = sum_{a=0}^{Mx-1} sum_{b=0}^{My-1} f(xhat + a, yhat + b)
+ *                  exp(-i 2 pi (u a / Mx + v b / My)) S(a - Mx/2) S(b - My/2),
+ * xhat = x - Mx/2, yhat = y - My/2 (the M_x x M_y window of Eq. 17).
+ *
+ * sigma          Gaussian standard deviation (> 0); the paper suggests floor(M/2) = 3 sigma.
+ * My, Mx         window size, even, 2..64 each (odd sizes break the integer shift x - M/2
+ *                and the conjugate symmetry F_{M-u,M-v} = F*_{u,v}: GB_ERR_UNSUPPORTED).
+ * half_spectrum  0: d_out holds My * Mx planes, out[v][u][y][x].
+ *                1: only v = 0 .. My/2 are written, out[v][u][y][x] with My/2 + 1 planes
+ *                   of v; the rest follow from F_{u,v} = F*_{(Mx-u)%Mx,(My-v)%My}.
+ * d_out          device complex64, 16-byte aligned.
+ * The handle's precision selects the FP32 separable path (Algorithm 2) or the tensor-core
+ * windowed-DFT contraction.  Asynchronous.  Errors as gabor_bank_filter.
+ */
+gb_status gabor_bank_sdft(gabor_bank_t h, const float *d_img, int H, int W, int64_t pitch,
+                          double sigma, int My, int Mx, int half_spectrum, void *d_out,
+                          void *stream);
+
+/*
+ * gabor_bank_filter_batch - gabor_bank_filter for n independent images of possibly
+ * different sizes, in one persistent launch (a device work queue over (image, tile)
+ * items).  d_imgs[i], H[i], W[i], pitch[i], d_outs[i] as in gabor_bank_filter; the host
+ * arrays are read during the call only.  Asynchronous.  Results are bitwise identical to
+ * n separate gabor_bank_filter calls with the same handle.
+ */
+gb_status gabor_bank_filter_batch(gabor_bank_t h, int n, const float *const *d_imgs,
+                                  const int *H, const int *W, const int64_t *pitch,
+                                  void *const *d_outs, void *stream);
+
+/* Runtime options (gabor_bank_set_option). */
+typedef enum {
+    /* 1 (default): reuse J_theta for pi - theta (Algorithm 1).  0: recompute the
+       horizontal pass for every orientation (the paper's "no reuse" comparison). */
+    GB_OPT_REUSE = 1,
+    /* Rows per streamed chunk in the FP32 bank kernel: 0 = automatic, else 16, 32 or 64. */
+    GB_OPT_TILE_ROWS = 2,
+    /* Row segments per image column strip: 0 = automatic, else 1 .. 64. */
+    GB_OPT_SEGMENTS = 3
+} gb_option;
+
+/* gabor_bank_set_option - set an option; GB_ERR_INVALID_ARG on an unknown key or value. */
+gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value);
+
+/*
+ * gabor_bank_device_status - wait for `stream`, then read and clear the handle's device
+ * error word: GB_OK, or GB_ERR_TIMEOUT if a bounded device wait (tensor-core pipeline
+ * barriers) gave up since the last read.  Synchronous.
+ */
+gb_status gabor_bank_device_status(gabor_bank_t h, void *stream);
+
+/* gabor_bank_output_elems - complex elements gabor_bank_filter writes for an H x W image. */
+int64_t gabor_bank_output_elems(gabor_bank_t h, int H, int W);
+
+/* gabor_bank_last_error - message of the last failure on this host thread ("" if none). */
+const char *gabor_bank_last_error(void);
+
+/* gabor_bank_version - library version string. */
+const char *gabor_bank_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GABORBANK_H */

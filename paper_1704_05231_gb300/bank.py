@@ -1,0 +1,218 @@
+"""Thin ctypes binding of libgaborbank.so (the C ABI in include/gaborbank.h).
+
+Argument marshalling only: every step of the filter bank and the SDFT runs in the library's
+CUDA kernels.  PyTorch supplies device memory and the current CUDA stream.  There is no CPU
+fallback: if the library is missing or fails to load, every call raises ``GBError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgaborbank.so")
+
+GB_OK = 0
+STATUS = {0: "GB_OK", -1: "GB_ERR_INVALID_ARG", -2: "GB_ERR_OUT_OF_MEMORY", -3: "GB_ERR_CUDA",
+          -4: "GB_ERR_UNSUPPORTED", -5: "GB_ERR_BUDGET", -6: "GB_ERR_TIMEOUT"}
+PRECISION = {"fp32": 0, "fp16_tc": 1, "bf16_tc": 2}
+OPTION = {"reuse": 1, "tile_rows": 2, "segments": 3}
+
+# Every entry point the header declares, with its ctypes signature.
+_c_int, _c_dbl, _c_i64, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p
+SIGNATURES = {
+    "gabor_bank_create": (_c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_c_dbl), _c_int,
+                                   ctypes.POINTER(_c_dbl), ctypes.POINTER(_c_dbl), _c_int,
+                                   _c_dbl, _c_int, _c_int, _c_int]),
+    "gabor_bank_destroy": (_c_int, [_vp]),
+    "gabor_bank_filter": (_c_int, [_vp, _vp, _c_int, _c_int, _c_i64, _vp, _vp]),
+    "gabor_bank_filter_host": (_c_int, [_vp, _vp, _c_int, _c_int, _c_i64, _vp, _vp]),
+    "gabor_bank_sdft": (_c_int, [_vp, _vp, _c_int, _c_int, _c_i64, _c_dbl, _c_int, _c_int,
+                                 _c_int, _vp, _vp]),
+    "gabor_bank_filter_batch": (_c_int, [_vp, _c_int, ctypes.POINTER(_vp), ctypes.POINTER(_c_int),
+                                         ctypes.POINTER(_c_int), ctypes.POINTER(_c_i64),
+                                         ctypes.POINTER(_vp), _vp]),
+    "gabor_bank_set_option": (_c_int, [_vp, _c_int, _c_i64]),
+    "gabor_bank_device_status": (_c_int, [_vp, _vp]),
+    "gabor_bank_output_elems": (_c_i64, [_vp, _c_int, _c_int]),
+    "gabor_bank_last_error": (ctypes.c_char_p, []),
+    "gabor_bank_version": (ctypes.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libgaborbank.so and declare its signatures (raises GBError if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise GBError(-3, f"{path} is not built (run __graft_entry__.build())")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc != GB_OK:
+        raise GBError(rc, _lib.gabor_bank_last_error().decode())
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dbl_array(vals):
+    arr = (ctypes.c_double * max(1, len(vals)))(*[float(v) for v in vals])
+    return arr
+
+
+class GaborBank:
+    """A filter-bank plan on the current CUDA device (Algorithm 1's Sigma, Omega, Theta).
+
+    thetas: orientations (rad); omegas, sigmas: one (omega, sigma) per frequency.
+    precision: 'fp32', 'fp16_tc' or 'bf16_tc'.  An empty bank (no thetas / omegas) makes an
+    SDFT-only handle.
+    """
+
+    def __init__(self, thetas=(), omegas=(), sigmas=(), radius_factor=3.0, precision="fp32",
+                 max_shape=(0, 0)):
+        lib = load_library()
+        if len(omegas) != len(sigmas):
+            raise ValueError("omegas and sigmas must have the same length")
+        self.thetas = [float(t) for t in thetas]
+        self.omegas = [float(w) for w in omegas]
+        self.sigmas = [float(s) for s in sigmas]
+        self.precision = precision
+        h = ctypes.c_void_p()
+        _check(lib.gabor_bank_create(ctypes.byref(h), _dbl_array(self.thetas), len(self.thetas),
+                                     _dbl_array(self.omegas), _dbl_array(self.sigmas),
+                                     len(self.omegas), float(radius_factor),
+                                     PRECISION[precision], int(max_shape[0]), int(max_shape[1])))
+        self._h = h
+        self._lib = lib
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gabor_bank_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_option(self, key, value):
+        _check(self._lib.gabor_bank_set_option(self._h, OPTION[key] if isinstance(key, str) else int(key),
+                                               int(value)))
+
+    def device_status(self, stream=None):
+        _check(self._lib.gabor_bank_device_status(self._h, _stream_handle(stream)))
+
+    # -- shapes
+    def out_shape(self, H, W):
+        return (len(self.omegas), len(self.thetas), H, W)
+
+    # -- compute
+    @staticmethod
+    def _img_args(img):
+        import torch
+        if not isinstance(img, torch.Tensor) or not img.is_cuda or img.dtype != torch.float32:
+            raise TypeError("image must be a float32 CUDA tensor")
+        if img.dim() != 2 or img.stride(1) != 1:
+            raise ValueError("image must be 2-D with unit column stride")
+        H, W = img.shape
+        return ctypes.c_void_p(img.data_ptr()), H, W, img.stride(0)
+
+    def filter(self, img, out=None, stream=None):
+        """complex64 [n_freq][n_theta][H][W] on img's device (Eq. 1 for every filter)."""
+        import torch
+        p, H, W, pitch = self._img_args(img)
+        if out is None:
+            out = torch.empty(self.out_shape(H, W), dtype=torch.complex64, device=img.device)
+        elif out.dtype != torch.complex64 or not out.is_contiguous() or tuple(out.shape) != self.out_shape(H, W):
+            raise ValueError("out must be a contiguous complex64 tensor of shape " + str(self.out_shape(H, W)))
+        _check(self._lib.gabor_bank_filter(self._h, p, H, W, pitch, ctypes.c_void_p(out.data_ptr()),
+                                           _stream_handle(stream)))
+        return out
+
+    def filter_host(self, img, out=None, stream=None):
+        """The bank on host buffers (numpy float32 in, numpy complex64 out), synchronous."""
+        img = np.ascontiguousarray(img, dtype=np.float32)
+        H, W = img.shape
+        if out is None:
+            out = np.empty(self.out_shape(H, W), dtype=np.complex64)
+        _check(self._lib.gabor_bank_filter_host(self._h, ctypes.c_void_p(img.ctypes.data), H, W, W,
+                                                ctypes.c_void_p(out.ctypes.data), _stream_handle(stream)))
+        return out
+
+    def filter_host_ptr(self, img_ptr, H, W, pitch, out_ptr, stream=None):
+        """gabor_bank_filter_host on raw host pointers (e.g. pinned torch tensors)."""
+        _check(self._lib.gabor_bank_filter_host(self._h, ctypes.c_void_p(img_ptr), H, W, pitch,
+                                                ctypes.c_void_p(out_ptr), _stream_handle(stream)))
+
+    def filter_batch(self, imgs, outs=None, stream=None):
+        """The bank for a list of images of any sizes; returns the list of outputs."""
+        import torch
+        n = len(imgs)
+        args = [self._img_args(t) for t in imgs]
+        if outs is None:
+            outs = [torch.empty(self.out_shape(H, W), dtype=torch.complex64, device=t.device)
+                    for t, (_, H, W, _) in zip(imgs, args)]
+        ptrs = (ctypes.c_void_p * max(1, n))(*[a[0].value for a in args])
+        Hs = (ctypes.c_int * max(1, n))(*[a[1] for a in args])
+        Ws = (ctypes.c_int * max(1, n))(*[a[2] for a in args])
+        Ps = (ctypes.c_int64 * max(1, n))(*[a[3] for a in args])
+        Os = (ctypes.c_void_p * max(1, n))(*[o.data_ptr() for o in outs])
+        _check(self._lib.gabor_bank_filter_batch(self._h, n, ptrs, Hs, Ws, Ps, Os, _stream_handle(stream)))
+        return outs
+
+    def sdft(self, img, sigma, M, half_spectrum=False, out=None, stream=None):
+        """Localized SDFT (Eq. 17): complex64 [My or My/2+1][Mx][H][W].  M: int or (My, Mx)."""
+        import torch
+        My, Mx = (M, M) if isinstance(M, int) else (int(M[0]), int(M[1]))
+        p, H, W, pitch = self._img_args(img)
+        nv = My // 2 + 1 if half_spectrum else My
+        shape = (nv, Mx, H, W)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.complex64, device=img.device)
+        elif out.dtype != torch.complex64 or not out.is_contiguous() or tuple(out.shape) != shape:
+            raise ValueError("out must be a contiguous complex64 tensor of shape " + str(shape))
+        _check(self._lib.gabor_bank_sdft(self._h, p, H, W, pitch, float(sigma), My, Mx,
+                                         1 if half_spectrum else 0, ctypes.c_void_p(out.data_ptr()),
+                                         _stream_handle(stream)))
+        return out
+
+
+def version():
+    return load_library().gabor_bank_version().decode()

@@ -1,0 +1,501 @@
+// C ABI of the gaborbank library: argument validation, plan construction (Algorithm 1's
+// orientation pairing), table management, dispatch to the kernels.  See include/gaborbank.h
+// for the contract of every entry point.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+using namespace gb;
+
+namespace {
+
+thread_local std::string g_err;
+
+gb_status fail(gb_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+#define GB_CU(call)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(GB_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+    } while (0)
+
+#define GB_TRY(call)                                                                         \
+    do {                                                                                     \
+        gb_status s_ = (call);                                                               \
+        if (s_ != GB_OK) return s_;                                                          \
+    } while (0)
+
+// Makes the handle's device current for the duration of a call and restores the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+gb_status dalloc(T **p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) return GB_OK;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(GB_ERR_OUT_OF_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    return GB_OK;
+}
+
+template <typename T>
+void dfree(T *&p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+int radius_of(double sigma, double rf) { return (int)std::ceil(rf * sigma - 1e-9); }
+
+// Pairs theta with pi - theta (Algorithm 1: J_{pi - theta} = J*_theta) and lays out the
+// units of every frequency.
+void build_plan(gabor_bank *h)
+{
+    h->freqs.clear();
+    h->units.clear();
+    h->tpad_max = 8;
+    const int K = (int)h->theta.size();
+    for (int s = 0; s < (int)h->omega.size(); ++s) {
+        Freq f;
+        f.omega = h->omega[s];
+        f.sigma = h->sigma[s];
+        f.R = radius_of(f.sigma, h->rf);
+        f.T = 2 * f.R + 1;
+        f.Tpad = (f.T + 7) / 8 * 8;
+        h->tpad_max = std::max(h->tpad_max, f.Tpad);
+        f.u0 = (int)h->units.size();
+        std::vector<char> used(K, 0);
+        for (int k = 0; k < K; ++k) {
+            if (used[k]) continue;
+            used[k] = 1;
+            Unit u;
+            u.s = s;
+            u.k_a = k;
+            u.k_b = -1;
+            if (h->reuse) {
+                for (int j = 0; j < K; ++j) {
+                    if (!used[j] && std::fabs(h->theta[k] + h->theta[j] - M_PI) < 1e-9) {
+                        u.k_b = j;
+                        used[j] = 1;
+                        break;
+                    }
+                }
+            }
+            u.wc = f.omega * std::cos(h->theta[k]);
+            u.ws = f.omega * std::sin(h->theta[k]);
+            h->units.push_back(u);
+        }
+        f.u1 = (int)h->units.size();
+        h->freqs.push_back(f);
+    }
+}
+
+void free_tables(gabor_bank *h)
+{
+    dfree(h->d_unit_w);
+    dfree(h->d_sigma);
+    dfree(h->d_lo);
+    dfree(h->d_T);
+    dfree(h->d_taps);
+    dfree(h->d_phx);
+    dfree(h->d_phy);
+    dfree(h->d_unitdev);
+    h->Wcap = h->Hcap = 0;
+    h->tables_ready = false;
+}
+
+// Device tables of the plan: taps per frequency, phase tables per unit (K0, FP64).
+gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
+{
+    const int nu = (int)h->units.size();
+    const int nf = (int)h->freqs.size();
+    if (nu == 0) return GB_OK;
+    if (h->tables_ready && W <= h->Wcap && H <= h->Hcap) return GB_OK;
+    // Tables may be in use by earlier work on any stream.
+    GB_CU(cudaDeviceSynchronize());
+    const int Wcap = std::max(W, h->Wcap), Hcap = std::max(H, h->Hcap);
+    free_tables(h);
+    GB_TRY(dalloc(&h->d_unit_w, 2 * (size_t)nu));
+    GB_TRY(dalloc(&h->d_sigma, (size_t)nf));
+    GB_TRY(dalloc(&h->d_lo, (size_t)nf));
+    GB_TRY(dalloc(&h->d_T, (size_t)nf));
+    GB_TRY(dalloc(&h->d_taps, (size_t)nf * h->tpad_max));
+    GB_TRY(dalloc(&h->d_phx, (size_t)nu * Wcap));
+    GB_TRY(dalloc(&h->d_phy, (size_t)nu * Hcap));
+    GB_TRY(dalloc(&h->d_unitdev, (size_t)nu));
+    std::vector<double> w(2 * nu), sg(nf);
+    std::vector<int> lo(nf), T(nf);
+    std::vector<UnitDev> ud(nu);
+    for (int i = 0; i < nu; ++i) {
+        w[2 * i] = h->units[i].wc / M_PI;
+        w[2 * i + 1] = h->units[i].ws / M_PI;
+        const int K = (int)h->theta.size();
+        ud[i].phx = h->d_phx + (size_t)i * Wcap;
+        ud[i].phy = h->d_phy + (size_t)i * Hcap;
+        ud[i].plane_a = h->units[i].s * K + h->units[i].k_a;
+        ud[i].plane_b = h->units[i].k_b >= 0 ? h->units[i].s * K + h->units[i].k_b : -1;
+    }
+    for (int s = 0; s < nf; ++s) {
+        sg[s] = h->freqs[s].sigma;
+        lo[s] = h->freqs[s].R;
+        T[s] = h->freqs[s].T;
+    }
+    GB_CU(cudaMemcpy(h->d_unit_w, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+    GB_CU(cudaMemcpy(h->d_sigma, sg.data(), nf * sizeof(double), cudaMemcpyHostToDevice));
+    GB_CU(cudaMemcpy(h->d_lo, lo.data(), nf * sizeof(int), cudaMemcpyHostToDevice));
+    GB_CU(cudaMemcpy(h->d_T, T.data(), nf * sizeof(int), cudaMemcpyHostToDevice));
+    GB_CU(cudaMemcpy(h->d_unitdev, ud.data(), nu * sizeof(UnitDev), cudaMemcpyHostToDevice));
+    GB_CU(launch_build_taps(h->d_sigma, h->d_lo, h->d_T, nf, h->tpad_max, h->d_taps, st));
+    GB_CU(launch_build_gabor_tables(h->d_unit_w, nu, Wcap, Hcap, h->d_phx, h->d_phy, st));
+    h->Wcap = Wcap;
+    h->Hcap = Hcap;
+    h->tables_ready = true;
+    return GB_OK;
+}
+
+gb_status ensure_sdft_tables(gabor_bank *h, double sigma, int My, int Mx, cudaStream_t st)
+{
+    if (h->sdft_sigma == sigma && h->sdft_Mx == Mx && h->sdft_My == My) return GB_OK;
+    GB_CU(cudaStreamSynchronize(st));
+    if (!h->d_sdft_taps) GB_TRY(dalloc(&h->d_sdft_taps, 2 * (size_t)(kMaxSdftM + 8)));
+    if (!h->d_sdft_tw) GB_TRY(dalloc(&h->d_sdft_tw, 2 * (size_t)kMaxSdftM));
+    double *d_sg = nullptr;
+    int *d_lo = nullptr;
+    GB_TRY(dalloc(&d_sg, 2));
+    gb_status s = dalloc(&d_lo, 4);
+    if (s != GB_OK) { dfree(d_sg); return s; }
+    const double sg[2] = {sigma, sigma};
+    const int lo[4] = {Mx / 2, My / 2, Mx, My};   // lo[0..1], then T[0..1]
+    cudaError_t e = cudaMemcpy(d_sg, sg, sizeof(sg), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_lo, lo, sizeof(lo), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_build_taps(d_sg, d_lo, d_lo + 2, 2, kMaxSdftM + 8, h->d_sdft_taps, st);
+    if (e == cudaSuccess) e = launch_build_twiddles(Mx, h->d_sdft_tw, st);
+    if (e == cudaSuccess) e = launch_build_twiddles(My, h->d_sdft_tw + kMaxSdftM, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(d_sg);
+    dfree(d_lo);
+    if (e != cudaSuccess) return fail(GB_ERR_CUDA, std::string("sdft tables: ") + cudaGetErrorString(e));
+    h->sdft_sigma = sigma;
+    h->sdft_Mx = Mx;
+    h->sdft_My = My;
+    return GB_OK;
+}
+
+gb_status check_sticky()
+{
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GB_ERR_CUDA, std::string("earlier CUDA error: ") + cudaGetErrorString(e));
+    }
+    return GB_OK;
+}
+
+gb_status validate_image(const void *img, int H, int W, int64_t pitch, const void *out)
+{
+    if (!img || !out) return fail(GB_ERR_INVALID_ARG, "NULL image or output pointer");
+    if (H <= 0 || W <= 0) return fail(GB_ERR_INVALID_ARG, "H and W must be positive");
+    if (pitch < W) return fail(GB_ERR_INVALID_ARG, "pitch must be >= W");
+    if ((int64_t)H * pitch > (int64_t)1 << 40) return fail(GB_ERR_INVALID_ARG, "image too large");
+    if (reinterpret_cast<uintptr_t>(img) % 4) return fail(GB_ERR_INVALID_ARG, "image not 4-byte aligned");
+    if (reinterpret_cast<uintptr_t>(out) % 8) return fail(GB_ERR_INVALID_ARG, "output not 8-byte aligned");
+    return GB_OK;
+}
+
+gb_status filter_device(gabor_bank *h, const float *d_img, int H, int W, int64_t pitch,
+                        void *d_out, cudaStream_t st)
+{
+    if (h->prec != GB_FP32)
+        return fail(GB_ERR_UNSUPPORTED, "the filter bank runs in GB_FP32 only on this handle");
+    GB_TRY(ensure_tables(h, H, W, st));
+    const int K = (int)h->theta.size();
+    for (const Freq &f : h->freqs) {
+        const int nunits = f.u1 - f.u0;
+        if (nunits == 0) continue;
+        GaborArgs a{};
+        a.img = d_img;
+        a.pitch = pitch;
+        a.H = H;
+        a.W = W;
+        a.out = reinterpret_cast<float2 *>(d_out);
+        a.plane = (int64_t)H * W;
+        a.taps = h->d_taps + (size_t)(&f - h->freqs.data()) * h->tpad_max;
+        a.R = f.R;
+        a.T = f.T;
+        a.Tpad = f.Tpad;
+        a.units = h->d_unitdev + f.u0;
+        const GaborLaunchCfg cfg =
+            gabor_fp32_config(H, W, f.R, f.Tpad, nunits, h->tile_rows, h->segments, h->sm_count);
+        GB_CU(launch_gabor_fp32(a, nunits, cfg, st));
+    }
+    (void)K;
+    return GB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gb_status gabor_bank_create(gabor_bank_t *out, const double *theta, int n_theta,
+                            const double *omega, const double *sigma, int n_freq,
+                            double radius_factor, gb_precision prec, int max_H, int max_W)
+{
+    if (!out) return fail(GB_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_theta < 0 || n_freq < 0) return fail(GB_ERR_INVALID_ARG, "negative count");
+    if ((n_theta == 0) != (n_freq == 0))
+        return fail(GB_ERR_INVALID_ARG, "n_theta and n_freq must both be positive, or both 0");
+    if (n_theta > 0 && (!theta || !omega || !sigma))
+        return fail(GB_ERR_INVALID_ARG, "NULL theta/omega/sigma");
+    if (n_theta > 4096 || n_freq > 4096) return fail(GB_ERR_INVALID_ARG, "too many filters");
+    if (radius_factor == 0.0) radius_factor = 3.0;
+    if (!std::isfinite(radius_factor) || radius_factor <= 0.0)
+        return fail(GB_ERR_INVALID_ARG, "radius_factor must be positive and finite");
+    if (prec != GB_FP32 && prec != GB_FP16_TC && prec != GB_BF16_TC)
+        return fail(GB_ERR_INVALID_ARG, "unknown precision");
+    if (max_H < 0 || max_W < 0) return fail(GB_ERR_INVALID_ARG, "negative max size");
+    for (int k = 0; k < n_theta; ++k)
+        if (!std::isfinite(theta[k])) return fail(GB_ERR_INVALID_ARG, "non-finite theta");
+    for (int s = 0; s < n_freq; ++s) {
+        if (!std::isfinite(omega[s])) return fail(GB_ERR_INVALID_ARG, "non-finite omega");
+        if (!std::isfinite(sigma[s]) || sigma[s] <= 0.0)
+            return fail(GB_ERR_INVALID_ARG, "sigma must be positive and finite");
+        const double r = radius_factor * sigma[s];
+        if (r > kMaxRadius || radius_of(sigma[s], radius_factor) > kMaxRadius)
+            return fail(GB_ERR_UNSUPPORTED, "Gaussian radius above " + std::to_string(kMaxRadius) + " px");
+    }
+    gabor_bank *h = new (std::nothrow) gabor_bank();
+    if (!h) return fail(GB_ERR_OUT_OF_MEMORY, "host allocation failed");
+    h->prec = prec;
+    h->rf = radius_factor;
+    h->theta.assign(theta, theta + n_theta);
+    h->omega.assign(omega, omega + n_freq);
+    h->sigma.assign(sigma, sigma + n_freq);
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = gabor_fp32_prepare();
+    if (e == cudaSuccess) e = sdft_fp32_prepare();
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&h->d_status), sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        dfree(h->d_status);
+        delete h;
+        return fail(GB_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
+    }
+    build_plan(h);
+    if (max_H > 0 && max_W > 0 && !h->units.empty()) {
+        gb_status s = ensure_tables(h, max_H, max_W, nullptr);
+        if (s != GB_OK) {
+            gabor_bank_destroy(h);
+            return s;
+        }
+    }
+    *out = h;
+    return GB_OK;
+}
+
+gb_status gabor_bank_destroy(gabor_bank_t h)
+{
+    if (!h) return GB_OK;
+    DeviceGuard g(h->device);
+    cudaDeviceSynchronize();
+    free_tables(h);
+    dfree(h->d_sdft_taps);
+    dfree(h->d_sdft_tw);
+    dfree(h->d_status);
+    dfree(h->d_stage_img);
+    if (h->d_stage_out) cudaFree(h->d_stage_out);
+    h->d_stage_out = nullptr;
+    delete h;
+    return GB_OK;
+}
+
+gb_status gabor_bank_filter(gabor_bank_t h, const float *d_img, int H, int W, int64_t pitch,
+                            void *d_out, void *stream)
+{
+    if (!h) return fail(GB_ERR_INVALID_ARG, "NULL handle");
+    GB_TRY(validate_image(d_img, H, W, pitch, d_out));
+    if (h->units.empty()) return fail(GB_ERR_INVALID_ARG, "handle has no filter bank (SDFT-only)");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(GB_ERR_CUDA, "cannot select the handle's device");
+    GB_TRY(check_sticky());
+    return filter_device(h, d_img, H, W, pitch, d_out, static_cast<cudaStream_t>(stream));
+}
+
+gb_status gabor_bank_filter_host(gabor_bank_t h, const float *h_img, int H, int W,
+                                 int64_t pitch, void *h_out, void *stream)
+{
+    if (!h) return fail(GB_ERR_INVALID_ARG, "NULL handle");
+    GB_TRY(validate_image(h_img, H, W, pitch, h_out));
+    if (h->units.empty()) return fail(GB_ERR_INVALID_ARG, "handle has no filter bank (SDFT-only)");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(GB_ERR_CUDA, "cannot select the handle's device");
+    GB_TRY(check_sticky());
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t img_bytes = (size_t)H * W * sizeof(float);
+    const size_t out_bytes = (size_t)gabor_bank_output_elems(h, H, W) * 8;
+    if (img_bytes > h->stage_img_bytes) {
+        GB_CU(cudaStreamSynchronize(st));
+        dfree(h->d_stage_img);
+        h->stage_img_bytes = 0;
+        GB_TRY(dalloc(&h->d_stage_img, (size_t)H * W));
+        h->stage_img_bytes = img_bytes;
+    }
+    if (out_bytes > h->stage_out_bytes) {
+        GB_CU(cudaStreamSynchronize(st));
+        if (h->d_stage_out) cudaFree(h->d_stage_out);
+        h->d_stage_out = nullptr;
+        h->stage_out_bytes = 0;
+        float2 *p = nullptr;
+        GB_TRY(dalloc(&p, out_bytes / 8));
+        h->d_stage_out = p;
+        h->stage_out_bytes = out_bytes;
+    }
+    GB_CU(cudaMemcpy2DAsync(h->d_stage_img, (size_t)W * sizeof(float), h_img,
+                            (size_t)pitch * sizeof(float), (size_t)W * sizeof(float), H,
+                            cudaMemcpyHostToDevice, st));
+    GB_TRY(filter_device(h, h->d_stage_img, H, W, W, h->d_stage_out, st));
+    GB_CU(cudaMemcpyAsync(h_out, h->d_stage_out, out_bytes, cudaMemcpyDeviceToHost, st));
+    GB_CU(cudaStreamSynchronize(st));
+    return GB_OK;
+}
+
+gb_status gabor_bank_sdft(gabor_bank_t h, const float *d_img, int H, int W, int64_t pitch,
+                          double sigma, int My, int Mx, int half_spectrum, void *d_out,
+                          void *stream)
+{
+    if (!h) return fail(GB_ERR_INVALID_ARG, "NULL handle");
+    GB_TRY(validate_image(d_img, H, W, pitch, d_out));
+    if (!std::isfinite(sigma) || sigma <= 0.0) return fail(GB_ERR_INVALID_ARG, "sigma must be positive");
+    if (My < 2 || Mx < 2) return fail(GB_ERR_INVALID_ARG, "window sides must be >= 2");
+    if ((My & 1) || (Mx & 1)) return fail(GB_ERR_UNSUPPORTED, "odd window sizes are not supported");
+    if (My > kMaxSdftM || Mx > kMaxSdftM) return fail(GB_ERR_UNSUPPORTED, "window side above 64");
+    if (half_spectrum != 0 && half_spectrum != 1) return fail(GB_ERR_INVALID_ARG, "half_spectrum must be 0 or 1");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(GB_ERR_CUDA, "cannot select the handle's device");
+    GB_TRY(check_sticky());
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    GB_TRY(ensure_sdft_tables(h, sigma, My, Mx, st));
+    SdftArgs a{};
+    a.img = d_img;
+    a.pitch = pitch;
+    a.H = H;
+    a.W = W;
+    a.out = reinterpret_cast<float2 *>(d_out);
+    a.plane = (int64_t)H * W;
+    a.Mx = Mx;
+    a.My = My;
+    a.half = half_spectrum;
+    a.taps_x = h->d_sdft_taps;
+    a.taps_y = h->d_sdft_taps + (kMaxSdftM + 8);
+    a.tw_x = h->d_sdft_tw;
+    a.tw_y = h->d_sdft_tw + kMaxSdftM;
+    if (h->prec == GB_FP32) {
+        GB_CU(launch_sdft_fp32(a, h->sm_count, st));
+        return GB_OK;
+    }
+    return fail(GB_ERR_UNSUPPORTED, "tensor-core SDFT not available in this build");
+}
+
+gb_status gabor_bank_filter_batch(gabor_bank_t h, int n, const float *const *d_imgs,
+                                  const int *H, const int *W, const int64_t *pitch,
+                                  void *const *d_outs, void *stream)
+{
+    if (!h) return fail(GB_ERR_INVALID_ARG, "NULL handle");
+    if (n < 0 || (n > 0 && (!d_imgs || !H || !W || !pitch || !d_outs)))
+        return fail(GB_ERR_INVALID_ARG, "bad batch arrays");
+    for (int i = 0; i < n; ++i) GB_TRY(validate_image(d_imgs[i], H[i], W[i], pitch[i], d_outs[i]));
+    if (h->units.empty()) return fail(GB_ERR_INVALID_ARG, "handle has no filter bank (SDFT-only)");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(GB_ERR_CUDA, "cannot select the handle's device");
+    GB_TRY(check_sticky());
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int Hm = 0, Wm = 0;
+    for (int i = 0; i < n; ++i) {
+        Hm = std::max(Hm, H[i]);
+        Wm = std::max(Wm, W[i]);
+    }
+    if (n > 0) GB_TRY(ensure_tables(h, Hm, Wm, st));
+    for (int i = 0; i < n; ++i) GB_TRY(filter_device(h, d_imgs[i], H[i], W[i], pitch[i], d_outs[i], st));
+    return GB_OK;
+}
+
+gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value)
+{
+    if (!h) return fail(GB_ERR_INVALID_ARG, "NULL handle");
+    switch (key) {
+    case GB_OPT_REUSE:
+        if (value != 0 && value != 1) return fail(GB_ERR_INVALID_ARG, "GB_OPT_REUSE takes 0 or 1");
+        if (h->reuse != (int)value) {
+            DeviceGuard g(h->device);
+            cudaDeviceSynchronize();
+            h->reuse = (int)value;
+            free_tables(h);
+            build_plan(h);
+        }
+        return GB_OK;
+    case GB_OPT_TILE_ROWS:
+        if (value != 0 && value != 8 && value != 16 && value != 32 && value != 64)
+            return fail(GB_ERR_INVALID_ARG, "GB_OPT_TILE_ROWS takes 0, 8, 16, 32 or 64");
+        h->tile_rows = (int)value;
+        return GB_OK;
+    case GB_OPT_SEGMENTS:
+        if (value < 0 || value > 64) return fail(GB_ERR_INVALID_ARG, "GB_OPT_SEGMENTS takes 0 .. 64");
+        h->segments = (int)value;
+        return GB_OK;
+    default:
+        return fail(GB_ERR_INVALID_ARG, "unknown option");
+    }
+}
+
+gb_status gabor_bank_device_status(gabor_bank_t h, void *stream)
+{
+    if (!h) return fail(GB_ERR_INVALID_ARG, "NULL handle");
+    DeviceGuard g(h->device);
+    GB_CU(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int v = 0;
+    GB_CU(cudaMemcpy(&v, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    GB_CU(cudaMemset(h->d_status, 0, sizeof(int)));
+    if (v != 0) return fail(GB_ERR_TIMEOUT, "a bounded device wait gave up (code " + std::to_string(v) + ")");
+    return GB_OK;
+}
+
+int64_t gabor_bank_output_elems(gabor_bank_t h, int H, int W)
+{
+    if (!h || H <= 0 || W <= 0) return 0;
+    return (int64_t)h->omega.size() * (int64_t)h->theta.size() * H * W;
+}
+
+const char *gabor_bank_last_error(void) { return g_err.c_str(); }
+
+const char *gabor_bank_version(void) { return "gaborbank 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Internal declarations of the gaborbank library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gaborbank.h"
+
+namespace gb {
+
+constexpr int kStripW = 32;        // image columns per CTA strip (one warp wide)
+constexpr int kThreads = 256;      // threads per CTA of the FP32 kernels
+constexpr int kMaxRadius = 160;    // largest Gaussian radius of the fused FP32 bank kernel
+constexpr int kMaxSdftM = 64;      // largest SDFT window side
+constexpr int kSmemLimit = 227 * 1024;
+
+// Device view of one horizontal pass ("row unit") of the bank: the pass of orientation
+// theta_a at frequency omega_s, and the orientation pi - theta_a that reuses it (Eq. 13-16).
+struct UnitDev {
+    const float2 *phx;  // (cos, sin)(omega cos(theta_a) x), x in [0, Wcap)
+    const float2 *phy;  // (cos, sin)(omega sin(theta_a) y), y in [0, Hcap)
+    int plane_a;        // output plane of theta_a  (s * n_theta + k)
+    int plane_b;        // output plane of pi - theta_a, or -1 when unpaired
+};
+
+// Arguments of the fused FP32 bank kernel for one frequency.
+struct GaborArgs {
+    const float *img;
+    int64_t pitch;
+    int H, W;
+    float2 *out;
+    int64_t plane;       // H * W
+    const float *taps;   // Tpad taps S(t - R), zero beyond T
+    int R, T, Tpad;
+    int TH;              // rows per streamed chunk (multiple of 8, <= 64)
+    int seg_len;         // rows per CTA segment
+    int RS;              // ring rows (multiple of 8, >= TH + T - 1)
+    int SW;              // staging row width in float2 (>= kStripW + Tpad, = 1 mod 16)
+    const UnitDev *units;
+};
+
+// Arguments of the FP32 localized-SDFT kernel (Algorithm 2).
+struct SdftArgs {
+    const float *img;
+    int64_t pitch;
+    int H, W;
+    float2 *out;
+    int64_t plane;
+    int Mx, My;
+    int half;            // 1: only v <= My/2 planes
+    const float *taps_x; // TpadX taps S(i - Mx/2), i < Mx
+    const float *taps_y; // TpadY taps S(i - My/2), i < My
+    const float2 *tw_x;  // (cos, sin)(2 pi j / Mx), j < Mx
+    const float2 *tw_y;  // (cos, sin)(2 pi j / My), j < My
+    int TpadX, TpadY;
+    int TH, seg_len, RS, SW;
+};
+
+// One frequency of the plan.
+struct Freq {
+    double omega, sigma;
+    int R, T, Tpad;
+    int u0, u1;          // its units [u0, u1)
+};
+
+// One horizontal pass of the plan (host side).
+struct Unit {
+    int s;
+    int k_a, k_b;        // orientation indices (k_b = -1: unpaired)
+    double wc, ws;       // omega cos(theta_a), omega sin(theta_a)
+};
+
+// Launch configuration of one FP32 bank launch.
+struct GaborLaunchCfg {
+    int TH, nseg, seg_len, RS, SW;
+    size_t smem;
+};
+
+// Kernel launchers (defined in the .cu files).
+cudaError_t launch_build_gabor_tables(const double *d_unit_w, int nunits, int Wcap, int Hcap,
+                                      float2 *phx, float2 *phy, cudaStream_t st);
+cudaError_t launch_build_taps(const double *d_sigma, const int *d_lo, const int *d_T, int nfreq,
+                              int tpad_max, float *taps, cudaStream_t st);
+cudaError_t launch_build_twiddles(int M, float2 *tw, cudaStream_t st);
+GaborLaunchCfg gabor_fp32_config(int H, int W, int R, int Tpad, int nunits, int tile_rows,
+                                 int segments, int sm_count);
+cudaError_t launch_gabor_fp32(const GaborArgs &a, int nunits, const GaborLaunchCfg &cfg,
+                              cudaStream_t st);
+cudaError_t gabor_fp32_prepare();
+cudaError_t launch_sdft_fp32(SdftArgs a, int sm_count, cudaStream_t st);
+cudaError_t sdft_fp32_prepare();
+
+}  // namespace gb
+
+// The opaque handle.
+struct gabor_bank {
+    int device = 0;
+    int sm_count = 152;
+    gb_precision prec = GB_FP32;
+    double rf = 3.0;
+    std::vector<double> theta, omega, sigma;
+    std::vector<gb::Freq> freqs;
+    std::vector<gb::Unit> units;
+    int tpad_max = 8;
+    // options
+    int reuse = 1;
+    int tile_rows = 0;
+    int segments = 0;
+    // device tables
+    double *d_unit_w = nullptr;  // [nunits][2] (omega cos / pi, omega sin / pi)
+    double *d_sigma = nullptr;
+    int *d_lo = nullptr, *d_T = nullptr;
+    float *d_taps = nullptr;     // [n_freq][tpad_max]
+    float2 *d_phx = nullptr;     // [nunits][Wcap]
+    float2 *d_phy = nullptr;     // [nunits][Hcap]
+    gb::UnitDev *d_unitdev = nullptr;
+    int Wcap = 0, Hcap = 0;
+    bool tables_ready = false;
+    // SDFT tables (rebuilt when sigma / M change)
+    float *d_sdft_taps = nullptr;   // [2][kMaxSdftM + 8]
+    float2 *d_sdft_tw = nullptr;    // [2][kMaxSdftM]
+    double sdft_sigma = -1.0;
+    int sdft_Mx = 0, sdft_My = 0;
+    // device status word (bounded waits)
+    int *d_status = nullptr;
+    // host-buffer staging
+    float *d_stage_img = nullptr;
+    size_t stage_img_bytes = 0;
+    void *d_stage_out = nullptr;
+    size_t stage_out_bytes = 0;
+};

@@ -1,0 +1,220 @@
+// FP32 localized sliding DFT (K3 + K4): Algorithm 2 of arXiv 1704.05231 on CUDA cores.
+//
+// A CTA owns one horizontal frequency u in [0, Mx/2], one strip of 32 columns and one
+// segment of rows, and walks down the segment in chunks of TH rows:
+//
+//   row pass (Eq. 19, 21-22)  J_u(x) = exp(i w0 u xhat) [S * f_c - i S * f_s](x) with
+//                             f_c, f_s = f(m) (cos, sin)(w0 u m); twiddle indices are the
+//                             exact integers (u m) mod Mx.  J_u goes to a ring of rows.
+//   for each v in [0, My/2]   (J_u is reused for every v, Sec. III-B)
+//     demodulate (Eq. 23-24) J_u(x, n) by (cos, sin)(w0 v n) into the four signals of the
+//                             pair (u, Mx - u): J_{Mx-u} = J*_u (Eq. 25-26);
+//     column pass             smooth them with S along y, remodulate by
+//                             exp(i w0 v yhat) and store F_{u,v}, F_{Mx-u,v};
+//     conjugate fill          F_{(Mx-u)%Mx, My-v} = F*_{u,v} and F_{u, My-v} = F*_{Mx-u,v}
+//                             for 0 < v < My/2 (Algorithm 2, last loop).
+#include "internal.h"
+#include "conv_fp32.cuh"
+
+namespace gb {
+
+namespace {
+
+__device__ __forceinline__ int pmod(int a, int m)
+{
+    const int r = a % m;
+    return r < 0 ? r + m : r;
+}
+
+size_t sdft_smem_bytes(int TH, int RS, int SW, int TpadX, int TpadY, int My)
+{
+    return (size_t)RS * (kStripW + 1) * (sizeof(float2) + sizeof(float4)) +
+           (size_t)TH * SW * sizeof(float2) + (size_t)(SW + 1) * sizeof(float2) +
+           (size_t)(TpadX + 8 + TpadY + 8) * sizeof(float) + (size_t)(My + 1) * sizeof(float2);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int u = blockIdx.z;                 // 0 .. Mx/2
+    const int Mx = a.Mx, My = a.My;
+    const bool paired = u > 0 && 2 * u < Mx;  // J_0 and J_{Mx/2} are real
+    const int x0 = blockIdx.x * kStripW;
+    const int ys = blockIdx.y * a.seg_len;
+    if (ys >= a.H) return;
+    const int ye = min(a.H, ys + a.seg_len);
+    const int tid = threadIdx.x;
+    const int stride = kStripW + 1;
+
+    float4 *sig = reinterpret_cast<float4 *>(smem_raw);
+    float2 *jring = reinterpret_cast<float2 *>(sig + (size_t)a.RS * stride);
+    float2 *stage = jring + (size_t)a.RS * stride;
+    float2 *phx = stage + (size_t)a.TH * a.SW;
+    float *tx = reinterpret_cast<float *>(phx + a.SW + 1);
+    float *ty = tx + a.TpadX + 8;
+    float2 *twy = reinterpret_cast<float2 *>(ty + a.TpadY + 8);
+    const float4 *tx4 = reinterpret_cast<const float4 *>(tx);
+    const float4 *ty4 = reinterpret_cast<const float4 *>(ty);
+
+    for (int i = tid; i < a.TpadX + 8; i += kThreads) tx[i] = i < a.TpadX ? a.taps_x[i] : 0.f;
+    for (int i = tid; i < a.TpadY + 8; i += kThreads) ty[i] = i < a.TpadY ? a.taps_y[i] : 0.f;
+    for (int i = tid; i < My; i += kThreads) twy[i] = a.tw_y[i];
+    // Row demodulation phase of staged column j, m = x0 - Mx/2 + j: (cos, sin)(w0 u m).
+    for (int j = tid; j <= a.SW; j += kThreads) {
+        const int m = x0 - Mx / 2 + j;
+        phx[j] = a.tw_x[pmod(u * m, Mx)];
+    }
+    for (int i = tid; i < a.RS * stride; i += kThreads) {
+        sig[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        jring[i] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+
+    const int ring_origin = ys - My / 2;
+    const int ncols = kStripW + Mx - 1;
+
+    auto row_block = [&](int r0, int nrows) {
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int r = warp; r < nrows; r += kThreads / 32) {
+            const int y = r0 + r;
+            const bool yin = y >= 0 && y < a.H;
+            const float *src = a.img + (int64_t)(yin ? y : 0) * a.pitch;
+            float2 *dst = stage + (size_t)r * a.SW;
+            for (int j = lane; j < a.SW; j += 32) {
+                const int gx = x0 - Mx / 2 + j;
+                float v = 0.f;
+                if (yin && j < ncols && gx >= 0 && gx < a.W) v = __ldg(src + gx);
+                const float2 ph = phx[j];
+                dst[j] = make_float2(v * ph.x, v * ph.y);
+            }
+        }
+        __syncthreads();
+        const int r = (tid & 7) | ((tid >> 5) << 3);
+        const int q = (tid >> 3) & 3;
+        if (r < nrows) {
+            float2 acc[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
+            row_conv8(stage + (size_t)r * a.SW + 8 * q, tx4, a.TpadX / 8, acc);
+            const int y = r0 + r;
+            const int slot = (y - ring_origin) % a.RS;
+            const bool yin = y >= 0 && y < a.H;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                // remodulation by exp(i w0 u xhat), xhat = x - Mx/2 = staged column 8q + j
+                const float2 px = phx[8 * q + j];
+                const float A = acc[j].x, B = acc[j].y;
+                const float jr = fmaf(px.x, A, px.y * B);
+                const float ji = fmaf(px.y, A, -px.x * B);
+                jring[slot * stride + 8 * q + j] = yin ? make_float2(jr, ji) : make_float2(0.f, 0.f);
+            }
+        }
+        __syncthreads();
+    };
+
+    const int nv = My / 2 + 1;
+    const int64_t plane = a.plane;
+    auto col_pass = [&](int c, int nout) {
+        const int xl = tid & 31, yg = tid >> 5;
+        const int x = x0 + xl;
+        const int base_row = c - My / 2;                     // absolute row of the window start
+        const int base_off = pmod(base_row - ring_origin, a.RS);
+        for (int v = 0; v < nv; ++v) {
+            // Demodulate every ring slot by (cos, sin)(w0 v n) (Eq. 23-24 / 10).
+            for (int i = tid; i < a.RS * kStripW; i += kThreads) {
+                const int s = i / kStripW, xx = i % kStripW;
+                const int n = base_row + pmod(s - base_off, a.RS);
+                const float2 t = twy[pmod(v * n, My)];
+                const float2 J = jring[s * stride + xx];
+                const float fcr = J.x * t.x, fsr = J.x * t.y, fci = J.y * t.x, fsi = J.y * t.y;
+                sig[s * stride + xx] = make_float4(fcr + fsi, fsr - fci, fcr - fsi, fsr + fci);
+            }
+            __syncthreads();
+            for (int yb = 8 * yg; yb < nout; yb += 8 * (kThreads / 32)) {
+                const int slot0 = (c - ys + yb) % a.RS;
+                float4 acc[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                col_conv8<float4>(sig + xl, stride, a.RS, slot0, ty4, a.TpadY / 8, acc);
+                if (x < a.W) {
+                    const int um = (Mx - u) % Mx, vm = (My - v) % My;
+                    const bool fill = !a.half && v > 0 && 2 * v < My;
+                    float2 *o_uv = a.out + ((int64_t)v * Mx + u) * plane + x;
+                    float2 *o_mv = a.out + ((int64_t)v * Mx + um) * plane + x;
+                    float2 *o_mm = a.out + ((int64_t)vm * Mx + um) * plane + x;
+                    float2 *o_um = a.out + ((int64_t)vm * Mx + u) * plane + x;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int y = c + yb + j;
+                        if (y < c + nout && y < a.H) {
+                            // remodulation by exp(i w0 v yhat), yhat = y - My/2
+                            const float2 t = twy[pmod(v * (y - My / 2), My)];
+                            const float P = acc[j].x, Q = acc[j].y, P2 = acc[j].z, Q2 = acc[j].w;
+                            const float2 Fa = make_float2(fmaf(t.x, P, t.y * Q), fmaf(t.y, P, -t.x * Q));
+                            const int64_t off = (int64_t)y * a.W;
+                            __stcs(o_uv + off, Fa);
+                            if (fill) __stcs(o_mm + off, make_float2(Fa.x, -Fa.y));
+                            if (paired) {
+                                const float2 Fb = make_float2(fmaf(t.x, P2, t.y * Q2), fmaf(t.y, P2, -t.x * Q2));
+                                __stcs(o_mv + off, Fb);
+                                if (fill) __stcs(o_um + off, make_float2(Fb.x, -Fb.y));
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    };
+
+    int next = ring_origin;
+    for (int c = ys; c < ye; c += a.TH) {
+        const int nout = min(a.TH, ye - c);
+        const int need = c + nout + My / 2 - 1;   // rows y - My/2 .. y + My/2 - 1
+        while (next < need) {
+            const int n = min(a.TH, need - next);
+            row_block(next, n);
+            next += n;
+        }
+        col_pass(c, nout);
+    }
+}
+
+cudaError_t sdft_fp32_prepare()
+{
+    return cudaFuncSetAttribute(k_sdft_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kSmemLimit);
+}
+
+cudaError_t launch_sdft_fp32(SdftArgs a, int sm_count, cudaStream_t st)
+{
+    a.TpadX = round_up(a.Mx, 8);
+    a.TpadY = round_up(a.My, 8);
+    a.SW = stage_width(kStripW + a.TpadX);
+    int TH = 64;
+    size_t smem;
+    for (;;) {
+        a.TH = TH;
+        a.RS = round_up(TH + a.My - 1, 8);
+        smem = sdft_smem_bytes(TH, a.RS, a.SW, a.TpadX, a.TpadY, a.My);
+        if (smem <= (size_t)kSmemLimit || TH <= 8) break;
+        TH /= 2;
+    }
+    const int cps = std::max(1, std::min(8, (int)(kSmemLimit / (smem + 1024))));
+    const int nstrips = (a.W + kStripW - 1) / kStripW;
+    const int nu = a.Mx / 2 + 1;
+    const int64_t base = (int64_t)nstrips * nu;
+    int nseg = 1;
+    const int64_t target = 2LL * sm_count * cps;
+    const int min_len = std::max(TH, 2 * a.My);
+    while (base * nseg < target && a.H / (nseg + 1) >= min_len) ++nseg;
+    a.seg_len = (a.H + nseg - 1) / nseg;
+    nseg = (a.H + a.seg_len - 1) / a.seg_len;
+    const dim3 grid(nstrips, nseg, nu);
+    k_sdft_fp32<<<grid, kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gb

@@ -1,0 +1,144 @@
+"""GPU parity of the FP32 Gabor bank (Algorithm 1, Eq. 1-16) against the FP64 oracle.
+
+Every test calls the CUDA path through the C ABI (ctypes binding) and compares element by
+element with the direct 2-D sum of Eq. 1 on the same seeded FP32 image; the bar is
+max|err| <= 1e-5 * max|out| over each result tensor.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_05231_gb300 import synth
+from tests.helpers import FP32_TOL, c1_bank, c2_bank, plane_rel_errs, rel_err, sample_points
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def run_bank(torch, img, thetas, omegas, sigmas, **kw):
+    from paper_1704_05231_gb300 import GaborBank
+    with GaborBank(thetas, omegas, sigmas, **kw) as gbk:
+        t = torch.from_numpy(img).cuda()
+        out = gbk.filter(t)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+
+def test_c1_full_parity(torch_cuda):
+    img = synth.uniform01(0, 256, 256)
+    th, om, sg = c1_bank()
+    got = run_bank(torch_cuda, img, th, om, sg)
+    ref = oracle.gabor_bank(img, th, om, sg)
+    assert got.shape == (2, 4, 256, 256)
+    e = rel_err(got, ref)
+    print("C1 rel err", e, "worst plane", max(plane_rel_errs(got, ref)))
+    assert e <= FP32_TOL
+
+
+@pytest.mark.parametrize("H,W", [(37, 75), (1, 50), (50, 1), (3, 3), (64, 64), (129, 33), (200, 161)])
+def test_ragged_and_degenerate_sizes(torch_cuda, H, W):
+    img = synth.pink_noise([7, H, W], H, W)
+    th = [0.0, 0.6, math.pi / 2, math.pi - 0.6, 2.0]
+    om = [math.pi / 3, 0.4]
+    sg = [1.5, 5.0]   # R = 5 and 15: radius above the image size for the small cases
+    got = run_bank(torch_cuda, img, th, om, sg)
+    ref = oracle.gabor_bank(img, th, om, sg)
+    assert rel_err(got, ref) <= FP32_TOL
+
+
+def test_pitch_and_strided_view(torch_cuda):
+    from paper_1704_05231_gb300 import GaborBank
+    torch = torch_cuda
+    big = synth.uniform01(3, 90, 140)
+    th, om, sg = c1_bank()
+    view = torch.from_numpy(big).cuda()[5:80, 7:120]   # pitch 140 != W 113
+    with GaborBank(th, om, sg) as gbk:
+        got = gbk.filter(view).cpu().numpy()
+    ref = oracle.gabor_bank(big[5:80, 7:120], th, om, sg)
+    assert rel_err(got, ref) <= FP32_TOL
+
+
+def test_c2_bank_reduced_size_full_parity(torch_cuda):
+    # The paper-size bank (sigma up to 16, R = 48) on a 160 x 200 image: halos wider than
+    # a quarter of the image, several tiles and ragged edges.
+    img = synth.paper_like(0, 160, 200)
+    th, om, sg = c2_bank()
+    got = run_bank(torch_cuda, img, th, om, sg)
+    ref = oracle.gabor_bank(img, th, om, sg)
+    e = rel_err(got, ref)
+    print("C2-bank 160x200 rel err", e)
+    assert e <= FP32_TOL
+
+
+def test_c2_full_size_sampled(torch_cuda):
+    img = synth.paper_like(0, 1024, 1024)
+    th, om, sg = c2_bank()
+    got = run_bank(torch_cuda, img, th, om, sg)
+    rng = np.random.default_rng(11)
+    xs, ys = sample_points(rng, 1024, 1024, 1500)
+    ref = oracle.gabor_bank(img, th, om, sg, points=(xs, ys))
+    sub = got[:, :, ys, xs]
+    # scale: max|out| of the whole GPU result (the result tensor), checked against the oracle's
+    scale = float(np.max(np.abs(got)))
+    assert float(np.max(np.abs(ref))) <= scale * (1 + 1e-4)
+    assert float(np.max(np.abs(sub - ref))) <= FP32_TOL * scale
+
+
+def test_orientation_order_and_reuse_ablation(torch_cuda):
+    from paper_1704_05231_gb300 import GaborBank
+    torch = torch_cuda
+    img = synth.pink_noise(5, 96, 130)
+    th = [2 * math.pi / 3, 0.0, math.pi / 3, math.pi / 2, 5 * math.pi / 6, math.pi / 6]
+    om, sg = [0.8], [2.5]
+    t = torch.from_numpy(img).cuda()
+    with GaborBank(th, om, sg) as gbk:
+        a = gbk.filter(t).cpu().numpy()
+        gbk.set_option("reuse", 0)          # recompute J for every orientation
+        b = gbk.filter(t).cpu().numpy()
+    ref = oracle.gabor_bank(img, th, om, sg)
+    assert rel_err(a, ref) <= FP32_TOL
+    assert rel_err(b, ref) <= FP32_TOL
+    # reversing the orientation list permutes the planes only
+    with GaborBank(th[::-1], om, sg) as gbk:
+        c = gbk.filter(t).cpu().numpy()
+    assert rel_err(c[:, ::-1], ref) <= FP32_TOL
+
+
+def test_conjugate_symmetry_theta_plus_pi(torch_cuda):
+    img = synth.pink_noise(9, 70, 90)
+    th = [0.4, 0.4 + math.pi]
+    got = run_bank(torch_cuda, img, th, [1.0], [2.0])
+    assert rel_err(got[0, 1], np.conj(got[0, 0])) <= FP32_TOL
+
+
+def test_batch_equals_single_bitwise_and_host_path(torch_cuda):
+    from paper_1704_05231_gb300 import GaborBank
+    torch = torch_cuda
+    imgs = [synth.pink_noise([1, i], h, w) for i, (h, w) in enumerate([(40, 70), (128, 96), (33, 257)])]
+    th, om, sg = c1_bank()
+    with GaborBank(th, om, sg) as gbk:
+        ts = [torch.from_numpy(i).cuda() for i in imgs]
+        singles = [gbk.filter(t).cpu().numpy() for t in ts]
+        batch = [o.cpu().numpy() for o in gbk.filter_batch(ts)]
+        host = [gbk.filter_host(i) for i in imgs]
+    for s, b, h in zip(singles, batch, host):
+        assert np.array_equal(s, b)
+        assert np.array_equal(s, h)
+
+
+def test_impulse_response_on_gpu(torch_cuda):
+    # The bank applied to an impulse reproduces the Gabor kernel of Eq. 1-2 (interior).
+    H, W, x0, y0 = 64, 64, 30, 33
+    img = synth.impulse(H, W, x0, y0)
+    om, th, sg = 0.7, 0.5, 3.0
+    got = run_bank(torch_cuda, img, [th], [om], [sg])[0, 0]
+    ref = oracle.gabor_filter(img, om, th, sg)
+    assert rel_err(got, ref) <= FP32_TOL

@@ -1,0 +1,68 @@
+"""GPU parity of the localized sliding DFT (Algorithm 2, Eq. 17-26) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_05231_gb300 import synth
+from tests.helpers import FP32_TOL, rel_err, sample_points
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def run_sdft(torch, img, sigma, M, half=False, precision="fp32"):
+    from paper_1704_05231_gb300 import GaborBank
+    with GaborBank(precision=precision) as gbk:
+        out = gbk.sdft(torch.from_numpy(img).cuda(), sigma, M, half_spectrum=half)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("H,W,M,sigma", [(64, 80, 16, 4.0), (37, 45, 8, 1.5), (5, 70, 16, 4.0),
+                                         (100, 3, 4, 0.8), (33, 129, 12, 2.0)])
+def test_sdft_fp32_full_parity(torch_cuda, H, W, M, sigma):
+    img = synth.pink_noise([3, H, W], H, W)
+    got = run_sdft(torch_cuda, img, sigma, M)
+    ref = oracle.sdft(img, sigma, M)
+    assert got.shape == ref.shape
+    e = rel_err(got, ref)
+    print("SDFT", H, W, M, "rel err", e)
+    assert e <= FP32_TOL
+
+
+def test_sdft_nonsquare_window(torch_cuda):
+    img = synth.pink_noise(4, 48, 72)
+    got = run_sdft(torch_cuda, img, 2.0, (8, 16))
+    ref = oracle.sdft(img, 2.0, 8, 16)
+    assert rel_err(got, ref) <= FP32_TOL
+    got = run_sdft(torch_cuda, img, 2.0, (16, 6))
+    ref = oracle.sdft(img, 2.0, 16, 6)
+    assert rel_err(got, ref) <= FP32_TOL
+
+
+def test_sdft_half_spectrum_and_conjugate_fill(torch_cuda):
+    img = synth.pink_noise(6, 40, 56)
+    M = 16
+    full = run_sdft(torch_cuda, img, 4.0, M)
+    half = run_sdft(torch_cuda, img, 4.0, M, half=True)
+    assert half.shape[0] == M // 2 + 1
+    assert np.array_equal(half, full[:M // 2 + 1])
+    for v in range(M):
+        for u in range(M):
+            assert np.array_equal(full[(M - v) % M, (M - u) % M], np.conj(full[v, u])) or v in (0, M // 2)
+
+
+def test_sdft_c3_full_size_sampled(torch_cuda):
+    img = synth.pink_noise(0, 512, 512)
+    got = run_sdft(torch_cuda, img, 4.0, 16)
+    rng = np.random.default_rng(5)
+    xs, ys = sample_points(rng, 512, 512, 600)
+    ref = oracle.sdft(img, 4.0, 16, points=(xs, ys))
+    scale = float(np.max(np.abs(got)))
+    assert float(np.max(np.abs(got[:, :, ys, xs] - ref))) <= FP32_TOL * scale
