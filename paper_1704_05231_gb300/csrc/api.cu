@@ -1,6 +1,7 @@
 // C ABI of the gaborbank library: argument validation, plan construction (Algorithm 1's
 // orientation pairing), table management, dispatch to the kernels.  See include/gaborbank.h
 // for the contract of every entry point.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -126,6 +127,10 @@ void free_tables(gabor_bank *h)
     dfree(h->d_phx);
     dfree(h->d_phy);
     dfree(h->d_unitdev);
+    dfree(h->d_freqdev);
+    for (auto &kv : h->worklists) cudaFree(kv.second.first);
+    h->worklists.clear();
+    h->freqdev.clear();
     h->Wcap = h->Hcap = 0;
     h->tables_ready = false;
 }
@@ -149,6 +154,7 @@ gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
     GB_TRY(dalloc(&h->d_phx, (size_t)nu * Wcap));
     GB_TRY(dalloc(&h->d_phy, (size_t)nu * Hcap));
     GB_TRY(dalloc(&h->d_unitdev, (size_t)nu));
+    GB_TRY(dalloc(&h->d_freqdev, (size_t)nf));
     std::vector<double> w(2 * nu), sg(nf);
     std::vector<int> lo(nf), T(nf);
     std::vector<UnitDev> ud(nu);
@@ -158,6 +164,8 @@ gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
         const int K = (int)h->theta.size();
         ud[i].phx = h->d_phx + (size_t)i * Wcap;
         ud[i].phy = h->d_phy + (size_t)i * Hcap;
+        ud[i].s = h->units[i].s;
+        ud[i].pad_ = 0;
         ud[i].plane_a = h->units[i].s * K + h->units[i].k_a;
         ud[i].plane_b = h->units[i].k_b >= 0 ? h->units[i].s * K + h->units[i].k_b : -1;
     }
@@ -171,6 +179,15 @@ gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
     GB_CU(cudaMemcpy(h->d_lo, lo.data(), nf * sizeof(int), cudaMemcpyHostToDevice));
     GB_CU(cudaMemcpy(h->d_T, T.data(), nf * sizeof(int), cudaMemcpyHostToDevice));
     GB_CU(cudaMemcpy(h->d_unitdev, ud.data(), nu * sizeof(UnitDev), cudaMemcpyHostToDevice));
+    h->freqdev.resize(nf);
+    h->max_smem = 0;
+    for (int s = 0; s < nf; ++s) {
+        FreqDev fd = gabor_fp32_geometry(h->freqs[s].R, h->tile_rows);
+        fd.taps = h->d_taps + (size_t)s * h->tpad_max;
+        h->freqdev[s] = fd;
+        h->max_smem = std::max(h->max_smem, gabor_fp32_smem_bytes(fd));
+    }
+    GB_CU(cudaMemcpy(h->d_freqdev, h->freqdev.data(), nf * sizeof(FreqDev), cudaMemcpyHostToDevice));
     GB_CU(launch_build_taps(h->d_sigma, h->d_lo, h->d_T, nf, h->tpad_max, h->d_taps, st));
     GB_CU(launch_build_gabor_tables(h->d_unit_w, nu, Wcap, Hcap, h->d_phx, h->d_phy, st));
     h->Wcap = Wcap;
@@ -229,33 +246,85 @@ gb_status validate_image(const void *img, int H, int W, int64_t pitch, const voi
     return GB_OK;
 }
 
+// Work list of one launch over `shapes` (H, W pairs): every (image, unit, strip, segment),
+// most expensive first.  Segments are cut so that no item exceeds ~1/3 of an SM's share.
+gb_status get_worklist(gabor_bank *h, const std::vector<int64_t> &shapes, WorkItem **items, int *n)
+{
+    auto itr = h->worklists.find(shapes);
+    if (itr != h->worklists.end()) {
+        *items = itr->second.first;
+        *n = itr->second.second;
+        return GB_OK;
+    }
+    const int nimg = (int)shapes.size() / 2;
+    struct Cand { double cost; WorkItem w; };
+    std::vector<Cand> cands;
+    // cost of one full-height column strip of a unit, in FMA lanes
+    auto strip_cost = [&](int s, bool paired, int Hh, int nseg) {
+        const FreqDev &f = h->freqdev[s];
+        const double seg = (double)Hh / nseg;
+        return 32.0 * f.Tpad * (seg * (paired ? 4 : 2) + (seg + 2 * f.R) * 2);
+    };
+    double total = 0;
+    for (int i = 0; i < nimg; ++i) {
+        const int Hh = (int)shapes[2 * i], Ww = (int)shapes[2 * i + 1];
+        const int nstrips = (Ww + kStripW - 1) / kStripW;
+        for (const Unit &u : h->units) total += nstrips * strip_cost(u.s, u.k_b >= 0, Hh, 1);
+    }
+    const double cap = total / std::max(1, h->sm_count) / 3.0;
+    for (int i = 0; i < nimg; ++i) {
+        const int Hh = (int)shapes[2 * i], Ww = (int)shapes[2 * i + 1];
+        const int nstrips = (Ww + kStripW - 1) / kStripW;
+        for (int s = 0; s < (int)h->freqs.size(); ++s) {
+            const FreqDev &f = h->freqdev[s];
+            int nseg = h->segments > 0 ? h->segments : 1;
+            if (h->segments <= 0) {
+                const int min_len = std::max(f.TH, 2 * f.R);
+                while (strip_cost(s, true, Hh, nseg) > cap && Hh / (nseg + 1) >= min_len) ++nseg;
+            }
+            nseg = std::max(1, std::min(nseg, Hh));
+            const int seg_len = (Hh + nseg - 1) / nseg;
+            for (int ui = h->freqs[s].u0; ui < h->freqs[s].u1; ++ui) {
+                const bool paired = h->units[ui].k_b >= 0;
+                for (int st = 0; st < nstrips; ++st)
+                    for (int y0 = 0; y0 < Hh; y0 += seg_len) {
+                        Cand c;
+                        c.w = WorkItem{i, ui, st, y0, std::min(Hh, y0 + seg_len)};
+                        const double rows = c.w.y1 - c.w.y0;
+                        c.cost = 32.0 * f.Tpad * (rows * (paired ? 4 : 2) + (rows + 2 * f.R) * 2);
+                        cands.push_back(c);
+                    }
+            }
+        }
+    }
+    std::stable_sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b) { return a.cost > b.cost; });
+    std::vector<WorkItem> w(cands.size());
+    for (size_t k = 0; k < cands.size(); ++k) w[k] = cands[k].w;
+    WorkItem *d = nullptr;
+    GB_TRY(dalloc(&d, w.size()));
+    GB_CU(cudaMemcpy(d, w.data(), w.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+    h->worklists[shapes] = {d, (int)w.size()};
+    *items = d;
+    *n = (int)w.size();
+    return GB_OK;
+}
+
 gb_status filter_device(gabor_bank *h, const float *d_img, int H, int W, int64_t pitch,
                         void *d_out, cudaStream_t st)
 {
     if (h->prec != GB_FP32)
         return fail(GB_ERR_UNSUPPORTED, "the filter bank runs in GB_FP32 only on this handle");
     GB_TRY(ensure_tables(h, H, W, st));
-    const int K = (int)h->theta.size();
-    for (const Freq &f : h->freqs) {
-        const int nunits = f.u1 - f.u0;
-        if (nunits == 0) continue;
-        GaborArgs a{};
-        a.img = d_img;
-        a.pitch = pitch;
-        a.H = H;
-        a.W = W;
-        a.out = reinterpret_cast<float2 *>(d_out);
-        a.plane = (int64_t)H * W;
-        a.taps = h->d_taps + (size_t)(&f - h->freqs.data()) * h->tpad_max;
-        a.R = f.R;
-        a.T = f.T;
-        a.Tpad = f.Tpad;
-        a.units = h->d_unitdev + f.u0;
-        const GaborLaunchCfg cfg =
-            gabor_fp32_config(H, W, f.R, f.Tpad, nunits, h->tile_rows, h->segments, h->sm_count);
-        GB_CU(launch_gabor_fp32(a, nunits, cfg, st));
-    }
-    (void)K;
+    WorkItem *items = nullptr;
+    int n = 0;
+    GB_TRY(get_worklist(h, {H, W}, &items, &n));
+    BankArgs a{};
+    a.img0 = ImageDev{d_img, pitch, reinterpret_cast<float2 *>(d_out), H, W};
+    a.imgs = nullptr;
+    a.freqs = h->d_freqdev;
+    a.units = h->d_unitdev;
+    a.items = items;
+    GB_CU(launch_gabor_fp32(a, n, h->max_smem, st));
     return GB_OK;
 }
 
@@ -332,6 +401,7 @@ gb_status gabor_bank_destroy(gabor_bank_t h)
     dfree(h->d_sdft_tw);
     dfree(h->d_status);
     dfree(h->d_stage_img);
+    dfree(h->d_imgs);
     if (h->d_stage_out) cudaFree(h->d_stage_out);
     h->d_stage_out = nullptr;
     delete h;
@@ -438,13 +508,41 @@ gb_status gabor_bank_filter_batch(gabor_bank_t h, int n, const float *const *d_i
     if (!g.ok) return fail(GB_ERR_CUDA, "cannot select the handle's device");
     GB_TRY(check_sticky());
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n == 0) return GB_OK;
+    if (h->prec != GB_FP32)
+        return fail(GB_ERR_UNSUPPORTED, "the filter bank runs in GB_FP32 only on this handle");
     int Hm = 0, Wm = 0;
     for (int i = 0; i < n; ++i) {
         Hm = std::max(Hm, H[i]);
         Wm = std::max(Wm, W[i]);
     }
-    if (n > 0) GB_TRY(ensure_tables(h, Hm, Wm, st));
-    for (int i = 0; i < n; ++i) GB_TRY(filter_device(h, d_imgs[i], H[i], W[i], pitch[i], d_outs[i], st));
+    GB_TRY(ensure_tables(h, Hm, Wm, st));
+    // One launch over every image: upload the image descriptors, then the shared work list.
+    if (n > h->imgs_cap) {
+        GB_CU(cudaStreamSynchronize(st));
+        dfree(h->d_imgs);
+        h->imgs_cap = 0;
+        GB_TRY(dalloc(&h->d_imgs, (size_t)n));
+        h->imgs_cap = n;
+    }
+    std::vector<ImageDev> imgs(n);
+    std::vector<int64_t> shapes(2 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        imgs[i] = ImageDev{d_imgs[i], pitch[i], reinterpret_cast<float2 *>(d_outs[i]), H[i], W[i]};
+        shapes[2 * i] = H[i];
+        shapes[2 * i + 1] = W[i];
+    }
+    // Pageable source: the copy is complete (staged) when the call returns.
+    GB_CU(cudaMemcpyAsync(h->d_imgs, imgs.data(), n * sizeof(ImageDev), cudaMemcpyHostToDevice, st));
+    WorkItem *items = nullptr;
+    int nitems = 0;
+    GB_TRY(get_worklist(h, shapes, &items, &nitems));
+    BankArgs a{};
+    a.imgs = h->d_imgs;
+    a.freqs = h->d_freqdev;
+    a.units = h->d_unitdev;
+    a.items = items;
+    GB_CU(launch_gabor_fp32(a, nitems, h->max_smem, st));
     return GB_OK;
 }
 
@@ -465,11 +563,22 @@ gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value)
     case GB_OPT_TILE_ROWS:
         if (value != 0 && value != 8 && value != 16 && value != 32 && value != 64)
             return fail(GB_ERR_INVALID_ARG, "GB_OPT_TILE_ROWS takes 0, 8, 16, 32 or 64");
-        h->tile_rows = (int)value;
+        if (h->tile_rows != (int)value) {
+            DeviceGuard g(h->device);
+            cudaDeviceSynchronize();
+            h->tile_rows = (int)value;
+            free_tables(h);
+        }
         return GB_OK;
     case GB_OPT_SEGMENTS:
         if (value < 0 || value > 64) return fail(GB_ERR_INVALID_ARG, "GB_OPT_SEGMENTS takes 0 .. 64");
-        h->segments = (int)value;
+        if (h->segments != (int)value) {
+            DeviceGuard g(h->device);
+            cudaDeviceSynchronize();
+            h->segments = (int)value;
+            for (auto &kv : h->worklists) cudaFree(kv.second.first);
+            h->worklists.clear();
+        }
         return GB_OK;
     default:
         return fail(GB_ERR_INVALID_ARG, "unknown option");

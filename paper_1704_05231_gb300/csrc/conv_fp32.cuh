@@ -1,82 +1,107 @@
-// Register-blocked 1-D Gaussian passes shared by the FP32 bank and SDFT kernels.
+// Register-blocked 1-D Gaussian passes and async-copy helpers shared by the FP32 kernels.
 //
 // Both passes are the real 1-D Gaussian smoothing S * g of the paper's decomposition
 // (Eq. 5-6 along rows, Eq. 7-9 along columns): a thread produces 8 consecutive outputs,
-// walks the taps in chunks of 8 (taps padded with zeros to a multiple of 8) and keeps a
-// 16-sample window in registers, so every shared-memory load feeds 8 FMAs per signal.
+// walks the taps in chunks of 8 (taps zero-padded to a multiple of 8) and keeps a 16-sample
+// window in two register banks used in ping-pong order, so every shared-memory load feeds 8
+// FMAs per signal and no register is copied.
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cstdint>
 
 namespace gb {
 
-__device__ __forceinline__ float4 fma4(float4 w, float t, float4 a)
+__device__ __forceinline__ float4 fmav(float4 w, float t, float4 a)
 {
     return make_float4(fmaf(w.x, t, a.x), fmaf(w.y, t, a.y), fmaf(w.z, t, a.z), fmaf(w.w, t, a.w));
 }
-__device__ __forceinline__ float2 fma2(float2 w, float t, float2 a)
+__device__ __forceinline__ float2 fmav(float2 w, float t, float2 a)
 {
     return make_float2(fmaf(w.x, t, a.x), fmaf(w.y, t, a.y));
 }
-__device__ __forceinline__ float4 fmav(float4 w, float t, float4 a) { return fma4(w, t, a); }
-__device__ __forceinline__ float2 fmav(float2 w, float t, float2 a) { return fma2(w, t, a); }
 
-template <typename V> __device__ __forceinline__ V zero_v();
-template <> __device__ __forceinline__ float4 zero_v<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-template <> __device__ __forceinline__ float2 zero_v<float2>() { return make_float2(0.f, 0.f); }
-
-// Row pass: out[j] = sum_t src[j + t] * taps[t], j < 8, for two interleaved signals
-// (f_c, f_s of Eq. 5).  src: 8 + 8 * nchunks readable float2; taps4: 2 * nchunks float4.
-__device__ __forceinline__ void row_conv8(const float2 *__restrict__ src,
-                                          const float4 *__restrict__ taps4, int nchunks,
-                                          float2 (&acc)[8])
+// acc[j] += sum_d win[j + d] * t[d] for the 8 taps of one chunk; win = lo[0..7] ++ hi[0..7].
+template <typename V>
+__device__ __forceinline__ void conv_step(const V (&lo)[8], const V (&hi)[8], const float4 *t4,
+                                          V (&acc)[8])
 {
-    float2 w[16];
+    const float4 t0 = t4[0], t1 = t4[1];
+    const float t[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
 #pragma unroll
-    for (int i = 0; i < 8; ++i) w[i] = src[i];
-#pragma unroll 2
-    for (int c = 0; c < nchunks; ++c) {
+    for (int d = 0; d < 8; ++d)
 #pragma unroll
-        for (int i = 0; i < 8; ++i) w[8 + i] = src[8 * (c + 1) + i];
-        const float4 t0 = taps4[2 * c], t1 = taps4[2 * c + 1];
-        const float t[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+        for (int j = 0; j < 8; ++j) acc[j] = fmav(j + d < 8 ? lo[j + d] : hi[j + d - 8], t[d], acc[j]);
+}
+
+// Contiguous source (row pass): out[j] = sum_t src[j + t] * taps[t], j < 8.
+// Reads src[0 .. 8 * nchunks + 7].
+template <typename V>
+__device__ __forceinline__ void conv8_linear(const V *__restrict__ src, const float4 *__restrict__ taps4,
+                                             int nchunks, V (&acc)[8])
+{
+    V wa[8], wb[8];
 #pragma unroll
-        for (int d = 0; d < 8; ++d)
+    for (int i = 0; i < 8; ++i) wa[i] = src[i];
+    int c = 0;
+    for (; c + 2 <= nchunks; c += 2) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[j] = fma2(w[j + d], t[d], acc[j]);
+        for (int i = 0; i < 8; ++i) wb[i] = src[8 * (c + 1) + i];
+        conv_step(wa, wb, taps4 + 2 * c, acc);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) w[i] = w[8 + i];
+        for (int i = 0; i < 8; ++i) wa[i] = src[8 * (c + 2) + i];
+        conv_step(wb, wa, taps4 + 2 * (c + 1), acc);
+    }
+    if (c < nchunks) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) wb[i] = src[8 * (c + 1) + i];
+        conv_step(wa, wb, taps4 + 2 * c, acc);
     }
 }
 
-// Column pass over a ring of rows: out[j] = sum_t ring[slot(j + t)][x] * taps[t], j < 8.
-// V = float4 (four signals of an orientation pair) or float2 (one orientation).
-// slot0 and RS are multiples of 8, so an 8-row chunk never wraps.
+// Ring source (column pass): row r of the window is ring[slot(r) * stride], slots advance
+// by 8 per chunk modulo RS.  slot0 and RS are multiples of 8, so a chunk never wraps.
 template <typename V>
-__device__ __forceinline__ void col_conv8(const V *__restrict__ ring, int stride, int RS,
-                                          int slot0, const float4 *__restrict__ taps4,
-                                          int nchunks, V (&acc)[8])
+__device__ __forceinline__ void conv8_ring(const V *__restrict__ ring, int stride, int RS, int slot0,
+                                           const float4 *__restrict__ taps4, int nchunks, V (&acc)[8])
 {
-    V w[16];
+    V wa[8], wb[8];
     int s = slot0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) w[i] = ring[(s + i) * stride];
-#pragma unroll 2
-    for (int c = 0; c < nchunks; ++c) {
+    auto adv = [&]() {
         s += 8;
         if (s >= RS) s -= RS;
+    };
 #pragma unroll
-        for (int i = 0; i < 8; ++i) w[8 + i] = ring[(s + i) * stride];
-        const float4 t0 = taps4[2 * c], t1 = taps4[2 * c + 1];
-        const float t[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+    for (int i = 0; i < 8; ++i) wa[i] = ring[(s + i) * stride];
+    int c = 0;
+    for (; c + 2 <= nchunks; c += 2) {
+        adv();
 #pragma unroll
-        for (int d = 0; d < 8; ++d)
+        for (int i = 0; i < 8; ++i) wb[i] = ring[(s + i) * stride];
+        conv_step(wa, wb, taps4 + 2 * c, acc);
+        adv();
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[j] = fmav(w[j + d], t[d], acc[j]);
+        for (int i = 0; i < 8; ++i) wa[i] = ring[(s + i) * stride];
+        conv_step(wb, wa, taps4 + 2 * (c + 1), acc);
+    }
+    if (c < nchunks) {
+        adv();
 #pragma unroll
-        for (int i = 0; i < 8; ++i) w[i] = w[8 + i];
+        for (int i = 0; i < 8; ++i) wb[i] = ring[(s + i) * stride];
+        conv_step(wa, wb, taps4 + 2 * c, acc);
     }
 }
+
+// 4-byte global -> shared async copy; src_bytes = 0 writes a zero without reading.
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem, int src_bytes)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 __host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
+#include <map>
+#include <utility>
 #include <vector>
 
 #include "gaborbank.h"
@@ -21,24 +23,43 @@ constexpr int kSmemLimit = 227 * 1024;
 struct UnitDev {
     const float2 *phx;  // (cos, sin)(omega cos(theta_a) x), x in [0, Wcap)
     const float2 *phy;  // (cos, sin)(omega sin(theta_a) y), y in [0, Hcap)
+    int s;              // frequency index
     int plane_a;        // output plane of theta_a  (s * n_theta + k)
     int plane_b;        // output plane of pi - theta_a, or -1 when unpaired
+    int pad_;
 };
 
-// Arguments of the fused FP32 bank kernel for one frequency.
-struct GaborArgs {
+// Device view of one frequency: Gaussian taps and the FP32 kernel's tile geometry.
+struct FreqDev {
+    const float *taps;  // Tpad taps S(t - R), zero beyond T
+    int R, T, Tpad;
+    int TH;             // rows per streamed chunk (multiple of 8, <= 64)
+    int RS;             // ring rows (multiple of 8, >= TH + T - 1)
+    int SW;             // staging row width in float2 (>= kStripW + Tpad, = 1 mod 16)
+    int RW;             // raw staging row width in floats (>= kStripW + T - 1, multiple of 4)
+    int pad_;
+};
+
+// One image of a launch.
+struct ImageDev {
     const float *img;
     int64_t pitch;
-    int H, W;
     float2 *out;
-    int64_t plane;       // H * W
-    const float *taps;   // Tpad taps S(t - R), zero beyond T
-    int R, T, Tpad;
-    int TH;              // rows per streamed chunk (multiple of 8, <= 64)
-    int seg_len;         // rows per CTA segment
-    int RS;              // ring rows (multiple of 8, >= TH + T - 1)
-    int SW;              // staging row width in float2 (>= kStripW + Tpad, = 1 mod 16)
+    int H, W;
+};
+
+// One CTA's work: a unit, a strip of 32 columns and a row segment of one image.
+struct WorkItem {
+    int img, unit, strip, y0, y1;
+};
+
+// Arguments of the fused FP32 bank kernel (one launch covers every frequency).
+struct BankArgs {
+    ImageDev img0;            // the image when imgs == nullptr
+    const ImageDev *imgs;     // batch images (device), or nullptr
+    const FreqDev *freqs;
     const UnitDev *units;
+    const WorkItem *items;
 };
 
 // Arguments of the FP32 localized-SDFT kernel (Algorithm 2).
@@ -55,7 +76,7 @@ struct SdftArgs {
     const float2 *tw_x;  // (cos, sin)(2 pi j / Mx), j < Mx
     const float2 *tw_y;  // (cos, sin)(2 pi j / My), j < My
     int TpadX, TpadY;
-    int TH, seg_len, RS, SW;
+    int TH, seg_len, RS, SW, RW;
 };
 
 // One frequency of the plan.
@@ -72,22 +93,16 @@ struct Unit {
     double wc, ws;       // omega cos(theta_a), omega sin(theta_a)
 };
 
-// Launch configuration of one FP32 bank launch.
-struct GaborLaunchCfg {
-    int TH, nseg, seg_len, RS, SW;
-    size_t smem;
-};
-
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_build_gabor_tables(const double *d_unit_w, int nunits, int Wcap, int Hcap,
                                       float2 *phx, float2 *phy, cudaStream_t st);
 cudaError_t launch_build_taps(const double *d_sigma, const int *d_lo, const int *d_T, int nfreq,
                               int tpad_max, float *taps, cudaStream_t st);
 cudaError_t launch_build_twiddles(int M, float2 *tw, cudaStream_t st);
-GaborLaunchCfg gabor_fp32_config(int H, int W, int R, int Tpad, int nunits, int tile_rows,
-                                 int segments, int sm_count);
-cudaError_t launch_gabor_fp32(const GaborArgs &a, int nunits, const GaborLaunchCfg &cfg,
-                              cudaStream_t st);
+// Tile geometry of the FP32 bank kernel for radius R (tile_rows = 0: automatic).
+FreqDev gabor_fp32_geometry(int R, int tile_rows);
+size_t gabor_fp32_smem_bytes(const FreqDev &f);
+cudaError_t launch_gabor_fp32(const BankArgs &a, int nitems, size_t smem, cudaStream_t st);
 cudaError_t gabor_fp32_prepare();
 cudaError_t launch_sdft_fp32(SdftArgs a, int sm_count, cudaStream_t st);
 cudaError_t sdft_fp32_prepare();
@@ -116,6 +131,11 @@ struct gabor_bank {
     float2 *d_phx = nullptr;     // [nunits][Wcap]
     float2 *d_phy = nullptr;     // [nunits][Hcap]
     gb::UnitDev *d_unitdev = nullptr;
+    gb::FreqDev *d_freqdev = nullptr;
+    std::vector<gb::FreqDev> freqdev;       // host copy (taps pointers into d_taps)
+    // work lists of the FP32 bank kernel, keyed by the image shapes of a launch
+    std::map<std::vector<int64_t>, std::pair<gb::WorkItem *, int>> worklists;
+    size_t max_smem = 0;
     int Wcap = 0, Hcap = 0;
     bool tables_ready = false;
     // SDFT tables (rebuilt when sigma / M change)
@@ -125,6 +145,9 @@ struct gabor_bank {
     int sdft_Mx = 0, sdft_My = 0;
     // device status word (bounded waits)
     int *d_status = nullptr;
+    // batch image descriptors
+    gb::ImageDev *d_imgs = nullptr;
+    int imgs_cap = 0;
     // host-buffer staging
     float *d_stage_img = nullptr;
     size_t stage_img_bytes = 0;

@@ -26,11 +26,12 @@ __device__ __forceinline__ int pmod(int a, int m)
     return r < 0 ? r + m : r;
 }
 
-size_t sdft_smem_bytes(int TH, int RS, int SW, int TpadX, int TpadY, int My)
+size_t sdft_smem_bytes(int TH, int RS, int SW, int RW, int TpadX, int TpadY, int My)
 {
     return (size_t)RS * (kStripW + 1) * (sizeof(float2) + sizeof(float4)) +
-           (size_t)TH * SW * sizeof(float2) + (size_t)(SW + 1) * sizeof(float2) +
-           (size_t)(TpadX + 8 + TpadY + 8) * sizeof(float) + (size_t)(My + 1) * sizeof(float2);
+           (size_t)TH * SW * sizeof(float2) + (size_t)2 * TH * RW * sizeof(float) +
+           (size_t)(SW + 1) * sizeof(float2) + (size_t)(TpadX + 8 + TpadY + 8) * sizeof(float) +
+           (size_t)(My + 1) * sizeof(float2);
 }
 
 }  // namespace
@@ -51,7 +52,8 @@ __global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
     float4 *sig = reinterpret_cast<float4 *>(smem_raw);
     float2 *jring = reinterpret_cast<float2 *>(sig + (size_t)a.RS * stride);
     float2 *stage = jring + (size_t)a.RS * stride;
-    float2 *phx = stage + (size_t)a.TH * a.SW;
+    float *raw = reinterpret_cast<float *>(stage + (size_t)a.TH * a.SW);
+    float2 *phx = reinterpret_cast<float2 *>(raw + (size_t)2 * a.TH * a.RW);
     float *tx = reinterpret_cast<float *>(phx + a.SW + 1);
     float *ty = tx + a.TpadX + 8;
     float2 *twy = reinterpret_cast<float2 *>(ty + a.TpadY + 8);
@@ -75,17 +77,51 @@ __global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
     const int ring_origin = ys - My / 2;
     const int ncols = kStripW + Mx - 1;
 
-    auto row_block = [&](int r0, int nrows) {
-        const int warp = tid >> 5, lane = tid & 31;
-        for (int r = warp; r < nrows; r += kThreads / 32) {
-            const int y = r0 + r;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int TH = a.TH;
+    const int need0 = min(ys + TH, ye) + My / 2 - 1;
+    const int npro = (need0 - ring_origin + TH - 1) / TH;
+    const int nch = (ye - ys + TH - 1) / TH;
+    const int nblocks = npro + nch - 1;
+    // Row blocks: the prologue [ys - My/2, need_0), then [need_{k-1}, need_k) per chunk k,
+    // need_k = min(ys + (k+1) TH, ye) + My/2 - 1 (rows y - My/2 .. y + My/2 - 1).
+    auto block_rows = [&](int b, int &start, int &n) {
+        if (b < npro) {
+            start = ring_origin + b * TH;
+            n = min(TH, need0 - start);
+        } else {
+            const int k = b - npro + 1;
+            start = min(ys + k * TH, ye) + My / 2 - 1;
+            n = min(ys + (k + 1) * TH, ye) + My / 2 - 1 - start;
+        }
+    };
+    auto issue = [&](int b) {
+        int start, n;
+        block_rows(b, start, n);
+        float *dst = raw + (size_t)(b & 1) * TH * a.RW;
+        for (int r = warp; r < n; r += kThreads / 32) {
+            const int y = start + r;
             const bool yin = y >= 0 && y < a.H;
             const float *src = a.img + (int64_t)(yin ? y : 0) * a.pitch;
-            float2 *dst = stage + (size_t)r * a.SW;
-            for (int j = lane; j < a.SW; j += 32) {
+            for (int j = lane; j < ncols; j += 32) {
                 const int gx = x0 - Mx / 2 + j;
-                float v = 0.f;
-                if (yin && j < ncols && gx >= 0 && gx < a.W) v = __ldg(src + gx);
+                const bool ok = yin && gx >= 0 && gx < a.W;
+                cp_async4(dst + (size_t)r * a.RW + j, ok ? (const void *)(src + gx) : (const void *)a.img,
+                          ok ? 4 : 0);
+            }
+        }
+        cp_async_commit();
+    };
+    // Row pass of block b (Eq. 19, 21-22): demodulate, smooth, remodulate into J_u.
+    auto row_pass = [&](int b) {
+        int start, n;
+        block_rows(b, start, n);
+        const float *rawb = raw + (size_t)(b & 1) * TH * a.RW;
+        for (int r = warp; r < n; r += kThreads / 32) {
+            float2 *dst = stage + (size_t)r * a.SW;
+            const float *src = rawb + (size_t)r * a.RW;
+            for (int j = lane; j < a.SW; j += 32) {
+                const float v = j < ncols ? src[j] : 0.f;
                 const float2 ph = phx[j];
                 dst[j] = make_float2(v * ph.x, v * ph.y);
             }
@@ -93,12 +129,12 @@ __global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
         __syncthreads();
         const int r = (tid & 7) | ((tid >> 5) << 3);
         const int q = (tid >> 3) & 3;
-        if (r < nrows) {
+        if (r < n) {
             float2 acc[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
-            row_conv8(stage + (size_t)r * a.SW + 8 * q, tx4, a.TpadX / 8, acc);
-            const int y = r0 + r;
+            conv8_linear<float2>(stage + (size_t)r * a.SW + 8 * q, tx4, a.TpadX / 8, acc);
+            const int y = start + r;
             const int slot = (y - ring_origin) % a.RS;
             const bool yin = y >= 0 && y < a.H;
 #pragma unroll
@@ -111,7 +147,6 @@ __global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
                 jring[slot * stride + 8 * q + j] = yin ? make_float2(jr, ji) : make_float2(0.f, 0.f);
             }
         }
-        __syncthreads();
     };
 
     const int nv = My / 2 + 1;
@@ -137,7 +172,7 @@ __global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
                 float4 acc[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-                col_conv8<float4>(sig + xl, stride, a.RS, slot0, ty4, a.TpadY / 8, acc);
+                conv8_ring<float4>(sig + xl, stride, a.RS, slot0, ty4, a.TpadY / 8, acc);
                 if (x < a.W) {
                     const int um = (Mx - u) % Mx, vm = (My - v) % My;
                     const bool fill = !a.half && v > 0 && 2 * v < My;
@@ -169,16 +204,23 @@ __global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
         }
     };
 
-    int next = ring_origin;
-    for (int c = ys; c < ye; c += a.TH) {
-        const int nout = min(a.TH, ye - c);
-        const int need = c + nout + My / 2 - 1;   // rows y - My/2 .. y + My/2 - 1
-        while (next < need) {
-            const int n = min(a.TH, need - next);
-            row_block(next, n);
-            next += n;
+    issue(0);
+    int b = 0;
+    for (int k = 0; k < nch; ++k) {
+        const int last = (k == 0) ? npro : npro + k;
+        for (; b < last; ++b) {
+            if (b + 1 < nblocks) {
+                issue(b + 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            row_pass(b);
         }
-        col_pass(c, nout);
+        __syncthreads();
+        const int c = ys + k * TH;
+        col_pass(c, min(TH, ye - c));
     }
 }
 
@@ -193,12 +235,13 @@ cudaError_t launch_sdft_fp32(SdftArgs a, int sm_count, cudaStream_t st)
     a.TpadX = round_up(a.Mx, 8);
     a.TpadY = round_up(a.My, 8);
     a.SW = stage_width(kStripW + a.TpadX);
+    a.RW = round_up(kStripW + a.Mx - 1, 4);
     int TH = 64;
     size_t smem;
     for (;;) {
         a.TH = TH;
         a.RS = round_up(TH + a.My - 1, 8);
-        smem = sdft_smem_bytes(TH, a.RS, a.SW, a.TpadX, a.TpadY, a.My);
+        smem = sdft_smem_bytes(TH, a.RS, a.SW, a.RW, a.TpadX, a.TpadY, a.My);
         if (smem <= (size_t)kSmemLimit || TH <= 8) break;
         TH /= 2;
     }
