@@ -371,6 +371,7 @@ gb_status gabor_bank_create(gabor_bank_t *out, const double *theta, int n_theta,
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = gabor_fp32_prepare();
     if (e == cudaSuccess) e = sdft_fp32_prepare();
+    if (e == cudaSuccess) e = sdft_tc_prepare();
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&h->d_status), sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -402,6 +403,8 @@ gb_status gabor_bank_destroy(gabor_bank_t h)
     dfree(h->d_status);
     dfree(h->d_stage_img);
     dfree(h->d_imgs);
+    if (h->d_sdft_B) cudaFree(h->d_sdft_B);
+    h->d_sdft_B = nullptr;
     if (h->d_stage_out) cudaFree(h->d_stage_out);
     h->d_stage_out = nullptr;
     delete h;
@@ -492,7 +495,29 @@ gb_status gabor_bank_sdft(gabor_bank_t h, const float *d_img, int H, int W, int6
         GB_CU(launch_sdft_fp32(a, h->sm_count, st));
         return GB_OK;
     }
-    return fail(GB_ERR_UNSUPPORTED, "tensor-core SDFT not available in this build");
+    if (!sdft_tc_supported(Mx, My))
+        return fail(GB_ERR_UNSUPPORTED, "tensor-core SDFT needs Mx * My <= 256");
+    const int bf16 = h->prec == GB_BF16_TC;
+    if (h->sdftB_sigma != sigma || h->sdftB_Mx != Mx || h->sdftB_My != My) {
+        const size_t bytes = (size_t)sdft_tc_b_bytes(Mx, My);
+        if (bytes > h->sdft_B_bytes) {
+            GB_CU(cudaStreamSynchronize(st));
+            if (h->d_sdft_B) cudaFree(h->d_sdft_B);
+            h->d_sdft_B = nullptr;
+            h->sdft_B_bytes = 0;
+            uint4 *p = nullptr;
+            GB_TRY(dalloc(&p, bytes / 16));
+            h->d_sdft_B = p;
+            h->sdft_B_bytes = bytes;
+        }
+        GB_CU(build_sdft_tc_b(h->d_sdft_B, sigma, Mx, My, bf16, &h->sdft_B_unscale, st));
+        h->sdftB_sigma = sigma;
+        h->sdftB_Mx = Mx;
+        h->sdftB_My = My;
+    }
+    GB_CU(launch_sdft_tc(d_img, pitch, H, W, reinterpret_cast<float2 *>(d_out), Mx, My, half_spectrum,
+                         h->d_sdft_B, h->sdft_B_unscale, bf16, h->d_status, h->sm_count, st));
+    return GB_OK;
 }
 
 gb_status gabor_bank_filter_batch(gabor_bank_t h, int n, const float *const *d_imgs,

@@ -106,6 +106,13 @@ cudaError_t launch_gabor_fp32(const BankArgs &a, int nitems, size_t smem, cudaSt
 cudaError_t gabor_fp32_prepare();
 cudaError_t launch_sdft_fp32(SdftArgs a, int sm_count, cudaStream_t st);
 cudaError_t sdft_fp32_prepare();
+// Tensor-core SDFT (windowed-DFT contraction on tcgen05).
+bool sdft_tc_supported(int Mx, int My);
+int sdft_tc_b_bytes(int Mx, int My);
+cudaError_t build_sdft_tc_b(void *Bdev, double sigma, int Mx, int My, int bf16, float *b_unscale, cudaStream_t st);
+cudaError_t sdft_tc_prepare();
+cudaError_t launch_sdft_tc(const float *img, int64_t pitch, int H, int W, float2 *out, int Mx, int My, int half,
+                           const void *Bdev, float b_unscale, int bf16, int *status, int sm_count, cudaStream_t st);
 
 }  // namespace gb
 
@@ -143,6 +150,12 @@ struct gabor_bank {
     float2 *d_sdft_tw = nullptr;    // [2][kMaxSdftM]
     double sdft_sigma = -1.0;
     int sdft_Mx = 0, sdft_My = 0;
+    // tensor-core SDFT operand B (pre-swizzled FP16 / BF16), keyed by (sigma, Mx, My)
+    void *d_sdft_B = nullptr;
+    size_t sdft_B_bytes = 0;
+    float sdft_B_unscale = 1.f;
+    double sdftB_sigma = -1.0;
+    int sdftB_Mx = 0, sdftB_My = 0;
     // device status word (bounded waits)
     int *d_status = nullptr;
     // batch image descriptors

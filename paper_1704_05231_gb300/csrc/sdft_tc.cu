@@ -1,0 +1,380 @@
+// Tensor-core localized sliding DFT (K5): Eq. 17 of arXiv 1704.05231 computed as the dense
+// contraction "window x Gaussian-weighted twiddle matrix" on tcgen05 tensor cores.
+//
+// For a tile of 128 consecutive pixels of one image row, with k = b * Mx + a indexing the
+// Mx x My window and n = 2 * bin + {re, im} indexing the bins (u, v), v in [0, My/2]:
+//
+//   D[p][n] = sum_k A[p][k] B[n][k],  A[p][k] = f(x0 + p - Mx/2 + a, y - My/2 + b) * 2^sA
+//                                      B[n][k] = {Re, Im} exp(-i 2 pi (u a / Mx + v b / My))
+//                                                S(a - Mx/2) S(b - My/2) * 2^sB
+//
+// A (FP16 or BF16, per-tile power-of-two scale sA) is built in shared memory by im2col from a
+// staged FP32 patch; B (built once per plan in FP64 on the GPU, stored pre-swizzled) stays
+// resident in shared memory for the whole persistent CTA.  D accumulates in FP32 in tensor
+// memory, in two passes of NP columns each (double-buffered, 2 x 256 TMEM columns), and is
+// read back by the epilogue warps, rescaled exactly by 2^-(sA+sB), and stored as complex64;
+// bins with v > My/2 are filled from F_{u,v} = F*_{Mx-u, My-v} (Algorithm 2, last loop).
+//
+// Roles (256 threads): warps 0-3 epilogue (TMEM lanes 0-127 = the tile's pixels);
+// warps 4-7 producers (patch load, per-tile scale, im2col); thread 128 issues the MMAs.
+// Every mbarrier wait is bounded; on timeout the CTA records a code in the status word and
+// stops.
+#include <algorithm>
+#include <type_traits>
+
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace gb {
+
+namespace {
+
+constexpr int kTileP = 128;   // pixels per tile (MMA M)
+
+struct TcLayout {
+    uint32_t b_off, a_off, patch_off, koff_off, bar_off, misc_off, total;
+};
+
+__host__ __device__ inline TcLayout tc_layout(int Kp, int NP, int My, int PW)
+{
+    TcLayout L;
+    L.b_off = 0;
+    L.a_off = L.b_off + (uint32_t)(Kp / 64) * (2 * NP) * 128;
+    L.patch_off = L.a_off + (uint32_t)(Kp / 64) * kTileP * 128;
+    L.koff_off = L.patch_off + (uint32_t)My * PW * 4;
+    L.bar_off = (L.koff_off + (uint32_t)Kp * 4 + 7) & ~7u;
+    L.misc_off = L.bar_off + 8 * 8;
+    L.total = L.misc_off + 64;
+    return L;
+}
+
+template <typename T> __device__ __forceinline__ uint16_t to_bits(float v);
+template <> __device__ __forceinline__ uint16_t to_bits<__half>(float v) { return __half_as_ushort(__float2half_rn(v)); }
+template <> __device__ __forceinline__ uint16_t to_bits<__nv_bfloat16>(float v)
+{
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+}  // namespace
+
+struct SdftTcArgs {
+    const float *img;
+    int64_t pitch;
+    int H, W;
+    float2 *out;
+    int64_t plane;
+    int Mx, My, half;
+    int K, Kp, NP, nbins, PW;
+    const uint4 *Bglob;    // pre-swizzled B, b_bytes
+    int b_bytes;
+    float b_unscale;       // 2^-sB
+    int tiles_x, ntiles;
+    int *status;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256, 1) k_sdft_tc(const SdftTcArgs a)
+{
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+    const TcLayout L = tc_layout(a.Kp, a.NP, a.My, a.PW);
+    unsigned char *sB = sm + L.b_off;
+    unsigned char *sA = sm + L.a_off;
+    float *patch = reinterpret_cast<float *>(sm + L.patch_off);
+    int *koff = reinterpret_cast<int *>(sm + L.koff_off);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.bar_off);
+    uint64_t *tmem_full = bars;        // [2]  MMA pass h done          (commit, count 1)
+    uint64_t *tmem_empty = bars + 2;   // [2]  epilogue read pass h     (4 warps)
+    uint64_t *a_empty = bars + 4;      // [1]  all MMAs of a tile done  (commit, count 1)
+    uint64_t *scale_full = bars + 5;   // [2]  tile scale published     (count 1)
+    uint64_t *final_bar = bars + 7;    // [1]  drain                    (commit, count 1)
+    uint32_t *tmem_base_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
+    volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
+    int *escale = reinterpret_cast<int *>(sm + L.misc_off + 8);        // [2]
+    float *pmax = reinterpret_cast<float *>(sm + L.misc_off + 16);      // [4]
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // B: resident for the whole CTA.
+    {
+        uint4 *dst = reinterpret_cast<uint4 *>(sB);
+        for (int i = tid; i < a.b_bytes / 16; i += 256) dst[i] = a.Bglob[i];
+    }
+    for (int k = tid; k < a.Kp; k += 256) {
+        const int b = k / a.Mx, aa = k % a.Mx;
+        koff[k] = k < a.K ? b * a.PW + aa : -1;
+    }
+    if (tid == 0) {
+        mbar_init(&tmem_full[0], 1);
+        mbar_init(&tmem_full[1], 1);
+        mbar_init(&tmem_empty[0], 4);
+        mbar_init(&tmem_empty[1], 4);
+        mbar_init(a_empty, 1);
+        mbar_init(&scale_full[0], 1);
+        mbar_init(&scale_full[1], 1);
+        mbar_init(final_bar, 1);
+        *abort_s = 0;
+        mbar_fence_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_base_s, 512);
+        tmem_relinquish();
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_base_s;
+
+    const int ntiles_cta = a.ntiles > (int)blockIdx.x ? (a.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int PWn = kTileP + a.Mx - 1;
+    const uint32_t idesc = idesc_f16(std::is_same<T, __nv_bfloat16>::value ? 1 : 0, kTileP, a.NP);
+
+    if (warp >= 4) {
+        // ------------------------------------------------------------ producers
+        const int ptid = tid - 128;
+        for (int i = 0; i < ntiles_cta; ++i) {
+            // One collective decision per tile: stop if any role gave up.
+            if (named_barrier_or(1, 128, *abort_s != 0)) break;
+            const int t = blockIdx.x + i * gridDim.x;
+            const int y = t / a.tiles_x, x0 = (t % a.tiles_x) * kTileP;
+            // patch rows y - My/2 + b, columns x0 - Mx/2 + c (zero outside the image)
+            float m = 0.f;
+            for (int idx = ptid; idx < a.My * PWn; idx += 128) {
+                const int b = idx / PWn, c = idx - b * PWn;
+                const int gy = y - a.My / 2 + b, gx = x0 - a.Mx / 2 + c;
+                float v = 0.f;
+                if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) v = __ldg(a.img + (int64_t)gy * a.pitch + gx);
+                patch[b * a.PW + c] = v;
+                m = fmaxf(m, fabsf(v));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) pmax[warp - 4] = m;
+            // A must no longer be read by the previous tile's MMAs.
+            bool failed = i > 0 && !mbar_wait(a_empty, (i - 1) & 1, abort_s);
+            if (named_barrier_or(1, 128, failed)) {
+                if (ptid == 0) { *abort_s = 1; atomicExch(a.status, 2); }
+                break;
+            }
+            const float mx = fmaxf(fmaxf(pmax[0], pmax[1]), fmaxf(pmax[2], pmax[3]));
+            int e = 0;
+            if (mx > 0.f) frexpf(mx, &e);       // mx = f * 2^e, f in [0.5, 1)
+            const float sc = ldexpf(1.f, -e);   // patch * sc in [-1, 1)
+            const int nchunk = kTileP * (a.Kp / 8);
+            for (int cidx = ptid; cidx < nchunk; cidx += 128) {
+                const int p = cidx & (kTileP - 1), kc = cidx >> 7;
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int o0 = koff[8 * kc + 2 * q], o1 = koff[8 * kc + 2 * q + 1];
+                    const float v0 = o0 >= 0 ? patch[o0 + p] * sc : 0.f;
+                    const float v1 = o1 >= 0 ? patch[o1 + p] * sc : 0.f;
+                    w[q] = (uint32_t)to_bits<T>(v0) | ((uint32_t)to_bits<T>(v1) << 16);
+                }
+                *reinterpret_cast<uint4 *>(sA + sw128_offset(kTileP, p, 8 * kc)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+            fence_proxy_async_smem();
+            if (ptid == 0) escale[i & 1] = e;
+            named_barrier(1, 128);
+            if (ptid == 0) {
+                mbar_arrive(&scale_full[i & 1]);
+                bool ok = true;
+                for (int h = 0; h < 2; ++h) {
+                    if (i > 0 && !mbar_wait(&tmem_empty[h], (i - 1) & 1, abort_s)) {
+                        *abort_s = 1;
+                        atomicExch(a.status, 3);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB) + (uint32_t)h * a.NP * 128;
+                    for (int kb = 0; kb < a.Kp / 64; ++kb) {
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t ad = smem_desc_sw128(a0 + kb * kTileP * 128) + 2 * kk;
+                            const uint64_t bd = smem_desc_sw128(b0 + kb * (2 * a.NP) * 128) + 2 * kk;
+                            tc_mma_f16(tmem + 256u * h, ad, bd, idesc, (kb | kk) != 0);
+                        }
+                    }
+                    tc_commit(&tmem_full[h]);
+                }
+                if (ok) tc_commit(a_empty);
+            }
+        }
+        if (ptid == 0) {
+            // Drain: every MMA this thread issued is complete before TMEM is released.
+            tc_commit(final_bar);
+            if (!mbar_wait(final_bar, 0, abort_s)) {
+                // an abort was raised elsewhere or the MMAs never completed: wait once more
+                volatile int dummy = 0;
+                mbar_wait(final_bar, 0, &dummy);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+        for (int i = 0; i < ntiles_cta; ++i) {
+            const int t = blockIdx.x + i * gridDim.x;
+            const int y = t / a.tiles_x, x = (t % a.tiles_x) * kTileP + 32 * warp + lane;
+            float unscale = 0.f;
+            bool ok = true;
+            for (int h = 0; h < 2; ++h) {
+                if (!mbar_wait(&tmem_full[h], i & 1, abort_s)) { ok = false; break; }
+                if (h == 0) {
+                    if (!mbar_wait(&scale_full[i & 1], (i >> 1) & 1, abort_s)) { ok = false; break; }
+                    unscale = ldexpf(a.b_unscale, escale[i & 1]);
+                }
+                tc_fence_after();
+                for (int n0 = 0; n0 < a.NP; n0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + lane_base + 256u * h + n0, v);
+                    if (x < a.W) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int bin = (h * a.NP + n0) / 2 + j;
+                            if (bin < a.nbins) {
+                                const int vv = bin / a.Mx, uu = bin - vv * a.Mx;
+                                const float2 F = make_float2(v[2 * j] * unscale, v[2 * j + 1] * unscale);
+                                float2 *o = a.out + ((int64_t)vv * a.Mx + uu) * a.plane + (int64_t)y * a.W + x;
+                                __stcs(o, F);
+                                if (!a.half && vv > 0 && 2 * vv < a.My) {
+                                    const int um = uu == 0 ? 0 : a.Mx - uu;
+                                    float2 *oc = a.out + ((int64_t)(a.My - vv) * a.Mx + um) * a.plane +
+                                                 (int64_t)y * a.W + x;
+                                    __stcs(oc, make_float2(F.x, -F.y));
+                                }
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tmem_empty[h]);
+            }
+            if (!ok) {
+                if (lane == 0) { *abort_s = 1; atomicExch(a.status, 1); }
+                break;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// ---------------------------------------------------------------- B builder (FP64)
+__global__ void k_build_sdft_b(uint16_t *__restrict__ B, int Mx, int My, int K, int Kp, int NP, int nbins,
+                               double sigma, int sB, int bf16)
+{
+    const int rows = 2 * NP;
+    const int n_el = rows * Kp;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_el; i += gridDim.x * blockDim.x) {
+        const int n = i / Kp, k = i % Kp;
+        const int bin = n >> 1, comp = n & 1;
+        double val = 0.0;
+        if (k < K && bin < nbins) {
+            const int b = k / Mx, aa = k % Mx;
+            const int v = bin / Mx, u = bin % Mx;
+            const int ra = (u * aa) % Mx, rb = (v * b) % My;
+            double s, c;
+            // exp(-i phi), phi = 2 pi (ra / Mx + rb / My)
+            sincospi(2.0 * ((double)ra / Mx + (double)rb / My), &s, &c);
+            const double da = aa - Mx / 2, db = b - My / 2;
+            const double g = exp(-(da * da + db * db) / (2.0 * sigma * sigma)) / (2.0 * 3.141592653589793 * sigma * sigma);
+            val = (comp == 0 ? c : -s) * g;
+            val = ldexp(val, sB);
+        }
+        const float fv = (float)val;
+        const uint16_t bits = bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(fv)) : __half_as_ushort(__float2half_rn(fv));
+        B[sw128_offset(rows, n, k) / 2] = bits;
+    }
+}
+
+bool sdft_tc_supported(int Mx, int My)
+{
+    const int K = Mx * My;
+    if (K > 256) return false;
+    const int Kp = round_up_i(K, 64);
+    const int nbins = (My / 2 + 1) * Mx;
+    const int NP = round_up_i((2 * nbins + 1) / 2, 16);
+    if (NP > 256) return false;
+    const int PW = round_up_i(kTileP + Mx - 1, 4);
+    const TcLayout L = tc_layout(Kp, NP, My, PW);
+    return L.total + 1024 <= (uint32_t)kSmemLimit;
+}
+
+cudaError_t sdft_tc_prepare()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_sdft_tc<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sdft_tc<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    return e;
+}
+
+// Builds B for (sigma, Mx, My) into *Bdev (allocated by the caller with sdft_tc_b_bytes()).
+int sdft_tc_b_bytes(int Mx, int My)
+{
+    const int K = Mx * My, Kp = round_up_i(K, 64);
+    const int nbins = (My / 2 + 1) * Mx;
+    const int NP = round_up_i((2 * nbins + 1) / 2, 16);
+    return Kp * 2 * NP * 2;
+}
+
+cudaError_t build_sdft_tc_b(void *Bdev, double sigma, int Mx, int My, int bf16, float *b_unscale, cudaStream_t st)
+{
+    const int K = Mx * My, Kp = round_up_i(K, 64);
+    const int nbins = (My / 2 + 1) * Mx;
+    const int NP = round_up_i((2 * nbins + 1) / 2, 16);
+    // max |B| = S(0)^2 = 1 / (2 pi sigma^2); scale it into [0.5, 1)
+    const double mx = 1.0 / (2.0 * 3.141592653589793 * sigma * sigma);
+    int e = 0;
+    frexp(mx, &e);
+    const int sB = -e;
+    *b_unscale = (float)ldexp(1.0, -sB);
+    const int n_el = 2 * NP * Kp;
+    k_build_sdft_b<<<(n_el + 255) / 256, 256, 0, st>>>(static_cast<uint16_t *>(Bdev), Mx, My, K, Kp, NP, nbins, sigma,
+                                                        sB, bf16);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sdft_tc(const float *img, int64_t pitch, int H, int W, float2 *out, int Mx, int My, int half,
+                           const void *Bdev, float b_unscale, int bf16, int *status, int sm_count, cudaStream_t st)
+{
+    SdftTcArgs a{};
+    a.img = img;
+    a.pitch = pitch;
+    a.H = H;
+    a.W = W;
+    a.out = out;
+    a.plane = (int64_t)H * W;
+    a.Mx = Mx;
+    a.My = My;
+    a.half = half;
+    a.K = Mx * My;
+    a.Kp = round_up_i(a.K, 64);
+    a.nbins = (My / 2 + 1) * Mx;
+    a.NP = round_up_i((2 * a.nbins + 1) / 2, 16);
+    a.PW = round_up_i(kTileP + Mx - 1, 4);
+    a.Bglob = static_cast<const uint4 *>(Bdev);
+    a.b_bytes = a.Kp * 2 * a.NP * 2;
+    a.b_unscale = b_unscale;
+    a.tiles_x = (W + kTileP - 1) / kTileP;
+    a.ntiles = a.tiles_x * H;
+    a.status = status;
+    const TcLayout L = tc_layout(a.Kp, a.NP, My, a.PW);
+    // at least ~half the SM's shared memory, so one CTA (and one 512-column TMEM block) per SM
+    const size_t smem = std::max<size_t>(L.total + 1024, 120 * 1024);
+    const int grid = std::min(a.ntiles, sm_count);
+    if (bf16)
+        k_sdft_tc<__nv_bfloat16><<<grid, 256, smem, st>>>(a);
+    else
+        k_sdft_tc<__half><<<grid, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gb

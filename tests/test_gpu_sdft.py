@@ -66,3 +66,46 @@ def test_sdft_c3_full_size_sampled(torch_cuda):
     ref = oracle.sdft(img, 4.0, 16, points=(xs, ys))
     scale = float(np.max(np.abs(got)))
     assert float(np.max(np.abs(got[:, :, ys, xs] - ref))) <= FP32_TOL * scale
+
+
+# ---------------------------------------------------------------- tensor-core path
+
+@pytest.mark.parametrize("precision", ["fp16_tc", "bf16_tc"])
+@pytest.mark.parametrize("H,W,M,sigma", [(40, 300, 16, 4.0), (7, 129, 8, 1.5), (64, 64, (8, 16), 2.0),
+                                         (20, 140, 12, 2.0)])
+def test_sdft_tc_parity(torch_cuda, precision, H, W, M, sigma):
+    from tests.helpers import TC_TOL
+    img = synth.pink_noise([8, H, W], H, W)
+    got = run_sdft(torch_cuda, img, sigma, M, precision=precision)
+    My, Mx = (M, M) if isinstance(M, int) else M
+    ref = oracle.sdft(img, sigma, My, Mx)
+    e = rel_err(got, ref)
+    print("TC SDFT", precision, H, W, M, "rel err", e)
+    assert e <= TC_TOL
+
+
+def test_sdft_tc_scaled_input_and_status(torch_cuda):
+    # Per-tile power-of-two scaling: a 1e4-scaled image stays within FP16 range.
+    from paper_1704_05231_gb300 import GaborBank
+    from tests.helpers import TC_TOL
+    torch = torch_cuda
+    img = (synth.pink_noise(12, 33, 200) * 1.0e4).astype(np.float32)
+    with GaborBank(precision="fp16_tc") as gbk:
+        got = gbk.sdft(torch.from_numpy(img).cuda(), 4.0, 16).cpu().numpy()
+        gbk.device_status()
+    ref = oracle.sdft(img, 4.0, 16)
+    assert rel_err(got, ref) <= TC_TOL
+
+
+@pytest.mark.parametrize("precision", ["fp16_tc", "bf16_tc"])
+def test_sdft_tc_c3_sampled_and_vs_fp32(torch_cuda, precision):
+    from tests.helpers import TC_TOL
+    img = synth.pink_noise(0, 512, 512)
+    got = run_sdft(torch_cuda, img, 4.0, 16, precision=precision)
+    f32 = run_sdft(torch_cuda, img, 4.0, 16)
+    assert rel_err(got, f32) <= TC_TOL
+    rng = np.random.default_rng(6)
+    xs, ys = sample_points(rng, 512, 512, 400)
+    ref = oracle.sdft(img, 4.0, 16, points=(xs, ys))
+    scale = float(np.max(np.abs(f32)))
+    assert float(np.max(np.abs(got[:, :, ys, xs] - ref))) <= TC_TOL * scale
