@@ -182,6 +182,66 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def hbm_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def time_device(torch, fn, steps, warmup, flush, stream):
+    """CUDA-event time of fn() per step (ms), L2 flushed before each step, after warm-up."""
+    for _ in range(max(3, warmup)):
+        fn()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        fn()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def sdft_leg(torch, steps, warmup, flush, stream):
+    """Localized SDFT, 512 x 512 1/f noise, 16 x 16 window, sigma 4, all 256 bins: FP32
+    separable path (Algorithm 2) and the tensor-core windowed-DFT contraction."""
+    from paper_1704_05231_gb300 import GaborBank, synth
+    Hs = Ws = 512
+    img = torch.from_numpy(synth.pink_noise(0, Hs, Ws)).cuda()
+    n_out = 256 * Hs * Ws
+    bytes_ = n_out * 8 + Hs * Ws * 4
+    peak, kind = hbm_peak_gbs()
+    res = {"workload": "512x512 1/f noise (seed 0), 16x16 window, sigma 4, 256 bins, complex64 out",
+           "outputs_per_step": n_out}
+    # plain write bandwidth of the same output volume (torch fill kernel), for context
+    fill = torch.empty((16, 16, Hs, Ws), dtype=torch.complex64, device="cuda")
+    fms = statistics.mean(time_device(torch, lambda: fill.zero_(), steps, warmup, flush, stream))
+    res["fill_same_bytes"] = {"ms": fms, "GB/s": n_out * 8 / (fms * 1e-3) / 1e9}
+    del fill
+    ref = None
+    for prec in ("fp32", "fp16_tc", "bf16_tc"):
+        gbk = GaborBank(precision=prec)
+        out = torch.empty((16, 16, Hs, Ws), dtype=torch.complex64, device="cuda")
+        ms = statistics.mean(time_device(torch, lambda: gbk.sdft(img, 4.0, 16, out=out), steps, warmup, flush, stream))
+        gbk.device_status()
+        ent = {"value": n_out / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+               "roofline": {"bound": "hbm", "achieved": bytes_ / (ms * 1e-3) / 1e9, "peak": peak,
+                            "unit": "GB/s", "frac": bytes_ / (ms * 1e-3) / 1e9 / peak, "peak_kind": kind,
+                            "algorithmic_bytes": bytes_}}
+        if ref is None:
+            ref = out.clone()
+        else:
+            ent["rel_err_vs_fp32"] = float((out - ref).abs().max() / ref.abs().max())
+        res[prec] = ent
+        gbk.close()
+        del out
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -266,6 +326,8 @@ def run_ours(args):
             "gpu_launches": 4 * args.steps,
             "clocks": clocks,
             "wall_s": wall}
+    if not args.no_extra:
+        line["sdft"] = sdft_leg(torch, args.steps, args.warmup, flush, stream)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(img, thetas, omegas, sigmas, args.cpu_seconds)
     if rank == 0:
@@ -283,6 +345,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the SDFT leg (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     if args.impl == "reference":

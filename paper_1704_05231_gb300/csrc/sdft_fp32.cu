@@ -31,7 +31,7 @@ size_t sdft_smem_bytes(int TH, int RS, int SW, int RW, int TpadX, int TpadY, int
     return (size_t)RS * (kStripW + 1) * (sizeof(float2) + sizeof(float4)) +
            (size_t)TH * SW * sizeof(float2) + (size_t)2 * TH * RW * sizeof(float) +
            (size_t)(SW + 1) * sizeof(float2) + (size_t)(TpadX + 8 + TpadY + 8) * sizeof(float) +
-           (size_t)(My + 1) * sizeof(float2);
+           (size_t)(My / 2 + 1) * My * sizeof(float2) + (size_t)round_up(RS, 4) * sizeof(int);
 }
 
 }  // namespace
@@ -56,13 +56,18 @@ __global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
     float2 *phx = reinterpret_cast<float2 *>(raw + (size_t)2 * a.TH * a.RW);
     float *tx = reinterpret_cast<float *>(phx + a.SW + 1);
     float *ty = tx + a.TpadX + 8;
-    float2 *twy = reinterpret_cast<float2 *>(ty + a.TpadY + 8);
+    // tw2[v][m] = (cos, sin)(2 pi v m / My): demodulation / remodulation twiddles, v <= My/2
+    float2 *tw2 = reinterpret_cast<float2 *>(ty + a.TpadY + 8);
+    int *nmod = reinterpret_cast<int *>(tw2 + (My / 2 + 1) * My);   // ring slot -> row mod My
     const float4 *tx4 = reinterpret_cast<const float4 *>(tx);
     const float4 *ty4 = reinterpret_cast<const float4 *>(ty);
 
     for (int i = tid; i < a.TpadX + 8; i += kThreads) tx[i] = i < a.TpadX ? a.taps_x[i] : 0.f;
     for (int i = tid; i < a.TpadY + 8; i += kThreads) ty[i] = i < a.TpadY ? a.taps_y[i] : 0.f;
-    for (int i = tid; i < My; i += kThreads) twy[i] = a.tw_y[i];
+    for (int i = tid; i < (My / 2 + 1) * My; i += kThreads) {
+        const int v = i / My, m = i % My;
+        tw2[i] = a.tw_y[(v * m) % My];
+    }
     // Row demodulation phase of staged column j, m = x0 - Mx/2 + j: (cos, sin)(w0 u m).
     for (int j = tid; j <= a.SW; j += kThreads) {
         const int m = x0 - Mx / 2 + j;
@@ -156,12 +161,14 @@ __global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
         const int x = x0 + xl;
         const int base_row = c - My / 2;                     // absolute row of the window start
         const int base_off = pmod(base_row - ring_origin, a.RS);
+        for (int s = tid; s < a.RS; s += kThreads) nmod[s] = pmod(base_row + pmod(s - base_off, a.RS), My);
+        __syncthreads();
         for (int v = 0; v < nv; ++v) {
+            const float2 *twv = tw2 + v * My;
             // Demodulate every ring slot by (cos, sin)(w0 v n) (Eq. 23-24 / 10).
             for (int i = tid; i < a.RS * kStripW; i += kThreads) {
-                const int s = i / kStripW, xx = i % kStripW;
-                const int n = base_row + pmod(s - base_off, a.RS);
-                const float2 t = twy[pmod(v * n, My)];
+                const int s = i >> 5, xx = i & 31;
+                const float2 t = twv[nmod[s]];
                 const float2 J = jring[s * stride + xx];
                 const float fcr = J.x * t.x, fsr = J.x * t.y, fci = J.y * t.x, fsi = J.y * t.y;
                 sig[s * stride + xx] = make_float4(fcr + fsi, fsr - fci, fcr - fsi, fsr + fci);
@@ -183,9 +190,10 @@ __global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int y = c + yb + j;
-                        if (y < c + nout && y < a.H) {
-                            // remodulation by exp(i w0 v yhat), yhat = y - My/2
-                            const float2 t = twy[pmod(v * (y - My / 2), My)];
+                        if (y < c + nout) {
+                            // remodulation by exp(i w0 v yhat), yhat = y - My/2: the first window
+                            // row of output y sits in ring slot slot0 + j
+                            const float2 t = twv[nmod[slot0 + j]];
                             const float P = acc[j].x, Q = acc[j].y, P2 = acc[j].z, Q2 = acc[j].w;
                             const float2 Fa = make_float2(fmaf(t.x, P, t.y * Q), fmaf(t.y, P, -t.x * Q));
                             const int64_t off = (int64_t)y * a.W;

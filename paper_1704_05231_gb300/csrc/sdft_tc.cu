@@ -15,8 +15,9 @@
 // read back by the epilogue warps, rescaled exactly by 2^-(sA+sB), and stored as complex64;
 // bins with v > My/2 are filled from F_{u,v} = F*_{Mx-u, My-v} (Algorithm 2, last loop).
 //
-// Roles (256 threads): warps 0-3 epilogue (TMEM lanes 0-127 = the tile's pixels);
-// warps 4-7 producers (patch load, per-tile scale, im2col); thread 128 issues the MMAs.
+// Roles (384 threads): warps 0-7 epilogue (TMEM lanes 0-127 = the tile's pixels, two warps
+// per lane quadrant splitting the columns); warps 8-11 producers (patch load, per-tile scale,
+// im2col); thread 256 issues the MMAs.
 // Every mbarrier wait is bounded; on timeout the CTA records a code in the status word and
 // stops.
 #include <algorithm>
@@ -45,7 +46,7 @@ __host__ __device__ inline TcLayout tc_layout(int Kp, int NP, int My, int PW)
     L.a_off = L.b_off + (uint32_t)(Kp / 64) * (2 * NP) * 128;
     L.patch_off = L.a_off + (uint32_t)(Kp / 64) * kTileP * 128;
     L.koff_off = L.patch_off + (uint32_t)My * PW * 4;
-    L.bar_off = (L.koff_off + (uint32_t)Kp * 4 + 7) & ~7u;
+    L.bar_off = (L.koff_off + (uint32_t)Kp * 4 + 15) & ~15u;
     L.misc_off = L.bar_off + 8 * 8;
     L.total = L.misc_off + 64;
     return L;
@@ -76,7 +77,7 @@ struct SdftTcArgs {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256, 1) k_sdft_tc(const SdftTcArgs a)
+__global__ void __launch_bounds__(384, 1) k_sdft_tc(const SdftTcArgs a)
 {
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(256, 1) k_sdft_tc(const SdftTcArgs a)
     int *koff = reinterpret_cast<int *>(sm + L.koff_off);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.bar_off);
     uint64_t *tmem_full = bars;        // [2]  MMA pass h done          (commit, count 1)
-    uint64_t *tmem_empty = bars + 2;   // [2]  epilogue read pass h     (4 warps)
+    uint64_t *tmem_empty = bars + 2;   // [2]  epilogue read pass h     (8 warps)
     uint64_t *a_empty = bars + 4;      // [1]  all MMAs of a tile done  (commit, count 1)
     uint64_t *scale_full = bars + 5;   // [2]  tile scale published     (count 1)
     uint64_t *final_bar = bars + 7;    // [1]  drain                    (commit, count 1)
@@ -101,17 +102,17 @@ __global__ void __launch_bounds__(256, 1) k_sdft_tc(const SdftTcArgs a)
     // B: resident for the whole CTA.
     {
         uint4 *dst = reinterpret_cast<uint4 *>(sB);
-        for (int i = tid; i < a.b_bytes / 16; i += 256) dst[i] = a.Bglob[i];
+        for (int i = tid; i < a.b_bytes / 16; i += 384) dst[i] = a.Bglob[i];
     }
-    for (int k = tid; k < a.Kp; k += 256) {
+    for (int k = tid; k < a.Kp; k += 384) {
         const int b = k / a.Mx, aa = k % a.Mx;
         koff[k] = k < a.K ? b * a.PW + aa : -1;
     }
     if (tid == 0) {
         mbar_init(&tmem_full[0], 1);
         mbar_init(&tmem_full[1], 1);
-        mbar_init(&tmem_empty[0], 4);
-        mbar_init(&tmem_empty[1], 4);
+        mbar_init(&tmem_empty[0], 8);
+        mbar_init(&tmem_empty[1], 8);
         mbar_init(a_empty, 1);
         mbar_init(&scale_full[0], 1);
         mbar_init(&scale_full[1], 1);
@@ -133,9 +134,31 @@ __global__ void __launch_bounds__(256, 1) k_sdft_tc(const SdftTcArgs a)
     const int PWn = kTileP + a.Mx - 1;
     const uint32_t idesc = idesc_f16(std::is_same<T, __nv_bfloat16>::value ? 1 : 0, kTileP, a.NP);
 
-    if (warp >= 4) {
+    if (warp >= 8) {
         // ------------------------------------------------------------ producers
-        const int ptid = tid - 128;
+        const int ptid = tid - 256;
+        // The next tile's patch is prefetched into registers (kPre per thread) while the
+        // current tile is converted, so its global-load latency is hidden.
+        constexpr int kPre = 24;
+        const int npatch = a.My * PWn;
+        const bool prefetch = npatch <= 128 * kPre;
+        float pre[kPre];
+        auto load_patch = [&](int t) {
+            const int y = t / a.tiles_x, x0 = (t % a.tiles_x) * kTileP;
+            int b = 0, c = ptid;   // idx = ptid + 128 q = b * PWn + c, PWn > 128
+#pragma unroll
+            for (int q = 0; q < kPre; ++q) {
+                float v = 0.f;
+                if (b < a.My) {
+                    const int gy = y - a.My / 2 + b, gx = x0 - a.Mx / 2 + c;
+                    if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) v = __ldg(a.img + (int64_t)gy * a.pitch + gx);
+                }
+                pre[q] = v;
+                c += 128;
+                if (c >= PWn) { c -= PWn; ++b; }
+            }
+        };
+        if (prefetch && ntiles_cta > 0) load_patch(blockIdx.x);
         for (int i = 0; i < ntiles_cta; ++i) {
             // One collective decision per tile: stop if any role gave up.
             if (named_barrier_or(1, 128, *abort_s != 0)) break;
@@ -143,17 +166,31 @@ __global__ void __launch_bounds__(256, 1) k_sdft_tc(const SdftTcArgs a)
             const int y = t / a.tiles_x, x0 = (t % a.tiles_x) * kTileP;
             // patch rows y - My/2 + b, columns x0 - Mx/2 + c (zero outside the image)
             float m = 0.f;
-            for (int idx = ptid; idx < a.My * PWn; idx += 128) {
-                const int b = idx / PWn, c = idx - b * PWn;
-                const int gy = y - a.My / 2 + b, gx = x0 - a.Mx / 2 + c;
-                float v = 0.f;
-                if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) v = __ldg(a.img + (int64_t)gy * a.pitch + gx);
-                patch[b * a.PW + c] = v;
-                m = fmaxf(m, fabsf(v));
+            if (prefetch) {
+                int b = 0, c = ptid;
+#pragma unroll
+                for (int q = 0; q < kPre; ++q) {
+                    if (b < a.My) {
+                        patch[b * a.PW + c] = pre[q];
+                        m = fmaxf(m, fabsf(pre[q]));
+                    }
+                    c += 128;
+                    if (c >= PWn) { c -= PWn; ++b; }
+                }
+                if (i + 1 < ntiles_cta) load_patch(t + gridDim.x);
+            } else {
+                for (int idx = ptid; idx < npatch; idx += 128) {
+                    const int b = idx / PWn, c = idx - b * PWn;
+                    const int gy = y - a.My / 2 + b, gx = x0 - a.Mx / 2 + c;
+                    float v = 0.f;
+                    if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) v = __ldg(a.img + (int64_t)gy * a.pitch + gx);
+                    patch[b * a.PW + c] = v;
+                    m = fmaxf(m, fabsf(v));
+                }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if (lane == 0) pmax[warp - 4] = m;
+            if (lane == 0) pmax[warp - 8] = m;
             // A must no longer be read by the previous tile's MMAs.
             bool failed = i > 0 && !mbar_wait(a_empty, (i - 1) & 1, abort_s);
             if (named_barrier_or(1, 128, failed)) {
@@ -164,18 +201,35 @@ __global__ void __launch_bounds__(256, 1) k_sdft_tc(const SdftTcArgs a)
             int e = 0;
             if (mx > 0.f) frexpf(mx, &e);       // mx = f * 2^e, f in [0.5, 1)
             const float sc = ldexpf(1.f, -e);   // patch * sc in [-1, 1)
-            const int nchunk = kTileP * (a.Kp / 8);
-            for (int cidx = ptid; cidx < nchunk; cidx += 128) {
-                const int p = cidx & (kTileP - 1), kc = cidx >> 7;
-                uint32_t w[4];
+            if (a.Mx % 8 == 0 && a.K == a.Kp) {
+                // Fast path: thread = pixel p; chunk kc holds a = a0 .. a0 + 7 of window row b.
+                const int p = ptid;
+                int b = 0, a0 = 0;
+#pragma unroll 4
+                for (int kc = 0; kc < a.Kp / 8; ++kc) {
+                    const float *src = patch + b * a.PW + a0 + p;
+                    uint32_t w[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int o0 = koff[8 * kc + 2 * q], o1 = koff[8 * kc + 2 * q + 1];
-                    const float v0 = o0 >= 0 ? patch[o0 + p] * sc : 0.f;
-                    const float v1 = o1 >= 0 ? patch[o1 + p] * sc : 0.f;
-                    w[q] = (uint32_t)to_bits<T>(v0) | ((uint32_t)to_bits<T>(v1) << 16);
+                    for (int q = 0; q < 4; ++q)
+                        w[q] = (uint32_t)to_bits<T>(src[2 * q] * sc) | ((uint32_t)to_bits<T>(src[2 * q + 1] * sc) << 16);
+                    *reinterpret_cast<uint4 *>(sA + sw128_offset(kTileP, p, 8 * kc)) = make_uint4(w[0], w[1], w[2], w[3]);
+                    a0 += 8;
+                    if (a0 == a.Mx) { a0 = 0; ++b; }
                 }
-                *reinterpret_cast<uint4 *>(sA + sw128_offset(kTileP, p, 8 * kc)) = make_uint4(w[0], w[1], w[2], w[3]);
+            } else {
+                const int nchunk = kTileP * (a.Kp / 8);
+                for (int cidx = ptid; cidx < nchunk; cidx += 128) {
+                    const int p = cidx & (kTileP - 1), kc = cidx >> 7;
+                    uint32_t w[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int o0 = koff[8 * kc + 2 * q], o1 = koff[8 * kc + 2 * q + 1];
+                        const float v0 = o0 >= 0 ? patch[o0 + p] * sc : 0.f;
+                        const float v1 = o1 >= 0 ? patch[o1 + p] * sc : 0.f;
+                        w[q] = (uint32_t)to_bits<T>(v0) | ((uint32_t)to_bits<T>(v1) << 16);
+                    }
+                    *reinterpret_cast<uint4 *>(sA + sw128_offset(kTileP, p, 8 * kc)) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
             }
             fence_proxy_async_smem();
             if (ptid == 0) escale[i & 1] = e;
@@ -216,10 +270,13 @@ __global__ void __launch_bounds__(256, 1) k_sdft_tc(const SdftTcArgs a)
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+        // warp w reads TMEM lanes 32 (w % 4) .. +31 (its pixels) and every other 16-column
+        // chunk of each pass, starting at chunk w / 4.
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        const int cgrp = warp >> 2;
         for (int i = 0; i < ntiles_cta; ++i) {
             const int t = blockIdx.x + i * gridDim.x;
-            const int y = t / a.tiles_x, x = (t % a.tiles_x) * kTileP + 32 * warp + lane;
+            const int y = t / a.tiles_x, x = (t % a.tiles_x) * kTileP + 32 * (warp & 3) + lane;
             float unscale = 0.f;
             bool ok = true;
             for (int h = 0; h < 2; ++h) {
@@ -229,27 +286,48 @@ __global__ void __launch_bounds__(256, 1) k_sdft_tc(const SdftTcArgs a)
                     unscale = ldexpf(a.b_unscale, escale[i & 1]);
                 }
                 tc_fence_after();
-                for (int n0 = 0; n0 < a.NP; n0 += 16) {
-                    float v[16];
-                    tmem_ld16(tmem + lane_base + 256u * h + n0, v);
-                    if (x < a.W) {
+                float2 *base = a.out + (int64_t)y * a.W + x;
+                // Store the 8 bins of the 16 accumulator columns starting at column n0.
+                auto emit = [&](const uint32_t (&r)[16], int n0) {
+                    if (x >= a.W) return;
+                    const int bin0 = (h * a.NP + n0) >> 1;
+                    int vv = bin0 / a.Mx, uu = bin0 - vv * a.Mx;
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int bin = (h * a.NP + n0) / 2 + j;
-                            if (bin < a.nbins) {
-                                const int vv = bin / a.Mx, uu = bin - vv * a.Mx;
-                                const float2 F = make_float2(v[2 * j] * unscale, v[2 * j + 1] * unscale);
-                                float2 *o = a.out + ((int64_t)vv * a.Mx + uu) * a.plane + (int64_t)y * a.W + x;
-                                __stcs(o, F);
-                                if (!a.half && vv > 0 && 2 * vv < a.My) {
-                                    const int um = uu == 0 ? 0 : a.Mx - uu;
-                                    float2 *oc = a.out + ((int64_t)(a.My - vv) * a.Mx + um) * a.plane +
-                                                 (int64_t)y * a.W + x;
-                                    __stcs(oc, make_float2(F.x, -F.y));
-                                }
+                    for (int j = 0; j < 8; ++j) {
+                        const int bin = bin0 + j;
+                        if (bin < a.nbins) {
+                            const float2 F = make_float2(__uint_as_float(r[2 * j]) * unscale,
+                                                         __uint_as_float(r[2 * j + 1]) * unscale);
+                            __stcs(base + (int64_t)bin * a.plane, F);
+                            if (!a.half && vv > 0 && 2 * vv < a.My) {
+                                const int um = uu == 0 ? 0 : a.Mx - uu;
+                                __stcs(base + (int64_t)((a.My - vv) * a.Mx + um) * a.plane, make_float2(F.x, -F.y));
                             }
                         }
+                        if (++uu == a.Mx) { uu = 0; ++vv; }
                     }
+                };
+                // Ping-pong register buffers: the next chunk's TMEM load is in flight while
+                // the current chunk is stored.
+                const uint32_t tb = tmem + lane_base + 256u * h;
+                uint32_t ra[16], rb[16];
+                int n0 = 16 * cgrp;
+                if (n0 < a.NP) {
+                    tmem_ld16_async(tb + n0, ra);
+                    tmem_wait_ld();
+                }
+                while (n0 < a.NP) {
+                    const int n1 = n0 + 32;
+                    if (n1 < a.NP) tmem_ld16_async(tb + n1, rb);
+                    emit(ra, n0);
+                    tmem_wait_ld();
+                    n0 = n1;
+                    if (n0 >= a.NP) break;
+                    const int n2 = n0 + 32;
+                    if (n2 < a.NP) tmem_ld16_async(tb + n2, ra);
+                    emit(rb, n0);
+                    tmem_wait_ld();
+                    n0 = n2;
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -371,9 +449,9 @@ cudaError_t launch_sdft_tc(const float *img, int64_t pitch, int H, int W, float2
     const size_t smem = std::max<size_t>(L.total + 1024, 120 * 1024);
     const int grid = std::min(a.ntiles, sm_count);
     if (bf16)
-        k_sdft_tc<__nv_bfloat16><<<grid, 256, smem, st>>>(a);
+        k_sdft_tc<__nv_bfloat16><<<grid, 384, smem, st>>>(a);
     else
-        k_sdft_tc<__half><<<grid, 256, smem, st>>>(a);
+        k_sdft_tc<__half><<<grid, 384, smem, st>>>(a);
     return cudaGetLastError();
 }
 
