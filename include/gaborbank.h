@@ -155,6 +155,24 @@ gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value);
  */
 gb_status gabor_bank_device_status(gabor_bank_t h, void *stream);
 
+/*
+ * gabor_sdft_noalloc - the FP32 localized sliding DFT of gabor_bank_sdft (same arguments and
+ * output layout, FP32 CUDA-core path) for callers that cannot allocate device memory: code
+ * inside a custom allocator or memory pool that forbids cudaMalloc, or an application whose
+ * device-memory budget is fixed before it starts.  No handle is needed and the call allocates
+ * nothing.  The paper has no counterpart; this is a deployment convenience.
+ *
+ * Its tables (Gaussian taps and twiddles) live in one fixed 2 KiB __device__ array of the
+ * library, which every GPU that loads the library holds until the process exits.  Limits:
+ * My, Mx even, 2 .. 64 (GB_ERR_UNSUPPORTED beyond).  The first call on a device does a
+ * one-time set-up on that device (symbol address, kernel attributes); make that first call
+ * before any CUDA stream capture.  Every call rewrites the shared table, so calls that
+ * overlap on the GPU (for example on two streams) race; serialise them on one stream.
+ * Asynchronous like gabor_bank_sdft; errors as gabor_bank_sdft.
+ */
+gb_status gabor_sdft_noalloc(const float *d_img, int H, int W, int64_t pitch, double sigma,
+                             int My, int Mx, int half_spectrum, void *d_out, void *stream);
+
 /* gabor_bank_output_elems - complex elements gabor_bank_filter writes for an H x W image. */
 int64_t gabor_bank_output_elems(gabor_bank_t h, int H, int W);
 

@@ -40,6 +40,7 @@ SIGNATURES = {
     "gabor_bank_output_elems": (_c_i64, [_vp, _c_int, _c_int]),
     "gabor_bank_last_error": (ctypes.c_char_p, []),
     "gabor_bank_version": (ctypes.c_char_p, []),
+    "gabor_sdft_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_i64, _c_dbl, _c_int, _c_int, _c_int, _vp, _vp]),
 }
 
 _lock = threading.Lock()

@@ -330,6 +330,11 @@ gb_status filter_device(gabor_bank *h, const float *d_img, int H, int W, int64_t
 
 }  // namespace
 
+namespace gb {
+// Records the message returned by gabor_bank_last_error() on this host thread.
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace gb
+
 extern "C" {
 
 gb_status gabor_bank_create(gabor_bank_t *out, const double *theta, int n_theta,

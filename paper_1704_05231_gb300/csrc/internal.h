@@ -106,6 +106,8 @@ cudaError_t launch_gabor_fp32(const BankArgs &a, int nitems, size_t smem, cudaSt
 cudaError_t gabor_fp32_prepare();
 cudaError_t launch_sdft_fp32(SdftArgs a, int sm_count, cudaStream_t st);
 cudaError_t sdft_fp32_prepare();
+// Sets the message returned by gabor_bank_last_error() on the calling host thread.
+void set_last_error(const char *msg);
 // Tensor-core SDFT (windowed-DFT contraction on tcgen05).
 bool sdft_tc_supported(int Mx, int My);
 int sdft_tc_b_bytes(int Mx, int My);
