@@ -206,6 +206,31 @@ def time_device(torch, fn, steps, warmup, flush, stream):
     return [a.elapsed_time(b) for a, b in zip(starts, ends)]
 
 
+def bank_tc_leg(torch, d_img, thetas, omegas, sigmas, ref_out, n_out, steps, warmup, flush, stream):
+    """The same bank on tensor cores (FP16 / BF16 operands, FP32 accumulation): outputs/s,
+    rel. error against the FP32 path on this image, HBM roofline of the whole step."""
+    from paper_1704_05231_gb300 import GaborBank
+    peak, kind = hbm_peak_gbs()
+    res = {}
+    ref = ref_out.clone()
+    for prec in ("fp16_tc",):
+        try:
+            gbk = GaborBank(thetas, omegas, sigmas, precision=prec, max_shape=(H, W))
+            out = torch.empty_like(ref)
+            ms = statistics.mean(time_device(torch, lambda: gbk.filter(d_img, out), steps, warmup, flush, stream))
+            gbk.device_status()
+            bytes_ = n_out * 8 + H * W * 4
+            res[prec] = {"value": n_out / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                         "rel_err_vs_fp32": float((out - ref).abs().max() / ref.abs().max()),
+                         "roofline": {"bound": "hbm", "achieved": bytes_ / (ms * 1e-3) / 1e9, "peak": peak,
+                                      "unit": "GB/s", "frac": bytes_ / (ms * 1e-3) / 1e9 / peak,
+                                      "peak_kind": kind, "algorithmic_bytes": bytes_}}
+            gbk.close()
+        except Exception as exc:  # reported, not hidden
+            res[prec] = {"error": str(exc)}
+    return res
+
+
 def sdft_leg(torch, steps, warmup, flush, stream):
     """Localized SDFT, 512 x 512 1/f noise, 16 x 16 window, sigma 4, all 256 bins: FP32
     separable path (Algorithm 2) and the tensor-core windowed-DFT contraction."""
@@ -327,6 +352,8 @@ def run_ours(args):
             "clocks": clocks,
             "wall_s": wall}
     if not args.no_extra:
+        line["tc"] = bank_tc_leg(torch, d_img, thetas, omegas, sigmas, out, n_out, args.steps, args.warmup, flush,
+                                 stream)
         line["sdft"] = sdft_leg(torch, args.steps, args.warmup, flush, stream)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(img, thetas, omegas, sigmas, args.cpu_seconds)

@@ -133,6 +133,7 @@ void free_tables(gabor_bank *h)
     h->freqdev.clear();
     h->Wcap = h->Hcap = 0;
     h->tables_ready = false;
+    h->tc_H = h->tc_W = 0;   // tensor-core unit descriptors point into the phase tables
 }
 
 // Device tables of the plan: taps per frequency, phase tables per unit (K0, FP64).
@@ -309,11 +310,138 @@ gb_status get_worklist(gabor_bank *h, const std::vector<int64_t> &shapes, WorkIt
     return GB_OK;
 }
 
+// Tensor-core bank state: B operands (once per plan) and, per image shape, the intermediate
+// signal buffer, unit descriptors and column work items.
+void free_tc(gabor_bank *h)
+{
+    dfree(h->d_tcB);
+    dfree(h->d_tcfreq);
+    dfree(h->d_tcunit);
+    dfree(h->d_tcsig);
+    dfree(h->d_tcitems);
+    h->tcsig_elems = 0;
+    h->tc_nitems = 0;
+    h->tc_H = h->tc_W = 0;
+    h->tc_ready = false;
+}
+
+gb_status ensure_tc(gabor_bank *h, int H, int W, cudaStream_t st)
+{
+    const int nf = (int)h->freqs.size(), nu = (int)h->units.size();
+    const int bf16 = h->prec == GB_BF16_TC;
+    if (!h->tc_ready) {
+        GB_CU(cudaDeviceSynchronize());
+        size_t total = 0;
+        std::vector<size_t> off_r(nf), off_c(nf);
+        int rmax = 0;
+        for (int s = 0; s < nf; ++s) {
+            const TcGeometry g = gabor_tc_geometry(h->freqs[s].R);
+            off_r[s] = total;
+            total += (size_t)64 * g.Krow;
+            off_c[s] = total;
+            total += (size_t)64 * g.Kcol;
+            h->tc_smem_rows = std::max(h->tc_smem_rows, g.smem_rows);
+            h->tc_smem_cols = std::max(h->tc_smem_cols, g.smem_cols);
+            rmax = std::max(rmax, h->freqs[s].R);
+        }
+        (void)rmax;
+        GB_TRY(dalloc(&h->d_tcB, total));
+        GB_TRY(dalloc(&h->d_tcfreq, (size_t)nf));
+        std::vector<TcFreqDev> fd(nf);
+        for (int s = 0; s < nf; ++s) {
+            const TcGeometry g = gabor_tc_geometry(h->freqs[s].R);
+            float unscale = 1.f;
+            GB_CU(build_gabor_tc_b(h->d_tcB + off_r[s], h->d_tcB + off_c[s], g.R, h->freqs[s].sigma, bf16, &unscale, st));
+            fd[s] = TcFreqDev{h->d_tcB + off_r[s], h->d_tcB + off_c[s], g.R, g.R8, g.Krow, g.Kcol, unscale, unscale};
+        }
+        GB_CU(cudaMemcpy(h->d_tcfreq, fd.data(), nf * sizeof(TcFreqDev), cudaMemcpyHostToDevice));
+        h->tc_ready = true;
+    }
+    if (h->tc_H == H && h->tc_W == W) return GB_OK;
+    GB_CU(cudaDeviceSynchronize());
+    int rmax = 0;
+    for (const Freq &f : h->freqs) rmax = std::max(rmax, f.R);
+    const int Lpad = ((rmax + 64) + 63) / 64 * 64;
+    const int64_t Hp = (int64_t)(H + 63) / 64 * 64 + 2 * Lpad;
+    std::vector<TcUnitDev> ud(nu);
+    int64_t off = 0;
+    const int K = (int)h->theta.size();
+    std::vector<int4> items;
+    for (int i = 0; i < nu; ++i) {
+        const Unit &un = h->units[i];
+        const bool paired = un.k_b >= 0;
+        ud[i].phx = h->d_phx + (size_t)i * h->Wcap;
+        ud[i].phy = h->d_phy + (size_t)i * h->Hcap;
+        ud[i].s = un.s;
+        ud[i].plane_a = un.s * K + un.k_a;
+        ud[i].plane_b = paired ? un.s * K + un.k_b : -1;
+        ud[i].pad_ = 0;
+        ud[i].sig_off = off;
+        off += (int64_t)(paired ? 4 : 2) * W * Hp;
+        const int xw = paired ? 32 : 64;
+        for (int y0 = 0; y0 < H; y0 += 64)
+            for (int x0 = 0; x0 < W; x0 += xw) items.push_back(make_int4(i, x0, y0, 0));
+    }
+    // Most expensive frequencies first (largest K).
+    std::stable_sort(items.begin(), items.end(), [&](const int4 &p, const int4 &q) {
+        return h->freqs[h->units[p.x].s].R > h->freqs[h->units[q.x].s].R;
+    });
+    if ((size_t)off > h->tcsig_elems) {
+        dfree(h->d_tcsig);
+        h->tcsig_elems = 0;
+        GB_TRY(dalloc(&h->d_tcsig, (size_t)off));
+        h->tcsig_elems = (size_t)off;
+    }
+    // Zero the whole intermediate once per layout: the halo rows are never written.
+    GB_CU(cudaMemsetAsync(h->d_tcsig, 0, (size_t)off * sizeof(uint16_t), st));
+    dfree(h->d_tcunit);
+    dfree(h->d_tcitems);
+    GB_TRY(dalloc(&h->d_tcunit, (size_t)nu));
+    GB_TRY(dalloc(&h->d_tcitems, items.size()));
+    GB_CU(cudaMemcpy(h->d_tcunit, ud.data(), nu * sizeof(TcUnitDev), cudaMemcpyHostToDevice));
+    GB_CU(cudaMemcpy(h->d_tcitems, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    h->tc_nitems = (int)items.size();
+    h->tc_H = H;
+    h->tc_W = W;
+    h->tc_Hp = Hp;
+    h->tc_Lpad = Lpad;
+    return GB_OK;
+}
+
+gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int64_t pitch, void *d_out,
+                           cudaStream_t st)
+{
+    if (h->prec == GB_BF16_TC)
+        return fail(GB_ERR_UNSUPPORTED,
+                    "the filter bank on tensor cores runs with FP16 operands (GB_FP16_TC); BF16 operands "
+                    "exceed 2e-3 * max|out| on the bank");
+    for (const Freq &f : h->freqs)
+        if (!gabor_tc_supported(f.R))
+            return fail(GB_ERR_UNSUPPORTED, "tensor-core bank supports radii up to ~120 px");
+    GB_TRY(ensure_tables(h, H, W, st));
+    GB_TRY(ensure_tc(h, H, W, st));
+    TcBankArgs a{};
+    a.img = d_img;
+    a.pitch = pitch;
+    a.H = H;
+    a.W = W;
+    a.out = reinterpret_cast<float2 *>(d_out);
+    a.plane = (int64_t)H * W;
+    a.sig = h->d_tcsig;
+    a.Hp = h->tc_Hp;
+    a.Lpad = h->tc_Lpad;
+    a.freqs = h->d_tcfreq;
+    a.units = h->d_tcunit;
+    a.status = h->d_status;
+    GB_CU(launch_gabor_tc(a, (int)h->units.size(), h->tc_smem_rows, h->tc_smem_cols, h->d_tcitems, h->tc_nitems,
+                          h->prec == GB_BF16_TC, st));
+    return GB_OK;
+}
+
 gb_status filter_device(gabor_bank *h, const float *d_img, int H, int W, int64_t pitch,
                         void *d_out, cudaStream_t st)
 {
-    if (h->prec != GB_FP32)
-        return fail(GB_ERR_UNSUPPORTED, "the filter bank runs in GB_FP32 only on this handle");
+    if (h->prec != GB_FP32) return filter_device_tc(h, d_img, H, W, pitch, d_out, st);
     GB_TRY(ensure_tables(h, H, W, st));
     WorkItem *items = nullptr;
     int n = 0;
@@ -377,6 +505,7 @@ gb_status gabor_bank_create(gabor_bank_t *out, const double *theta, int n_theta,
     if (e == cudaSuccess) e = gabor_fp32_prepare();
     if (e == cudaSuccess) e = sdft_fp32_prepare();
     if (e == cudaSuccess) e = sdft_tc_prepare();
+    if (e == cudaSuccess) e = gabor_tc_prepare();
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&h->d_status), sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -408,6 +537,7 @@ gb_status gabor_bank_destroy(gabor_bank_t h)
     dfree(h->d_status);
     dfree(h->d_stage_img);
     dfree(h->d_imgs);
+    free_tc(h);
     if (h->d_sdft_B) cudaFree(h->d_sdft_B);
     h->d_sdft_B = nullptr;
     if (h->d_stage_out) cudaFree(h->d_stage_out);
@@ -587,6 +717,7 @@ gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value)
             cudaDeviceSynchronize();
             h->reuse = (int)value;
             free_tables(h);
+            free_tc(h);
             build_plan(h);
         }
         return GB_OK;

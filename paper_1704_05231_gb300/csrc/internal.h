@@ -62,6 +62,36 @@ struct BankArgs {
     const WorkItem *items;
 };
 
+// ---- tensor-core bank (gabor_tc.cu) ----
+struct TcFreqDev {
+    const uint16_t *Brow;  // [64][Krow] Toeplitz S(k - x - R), FP16/BF16, K-major SW128
+    const uint16_t *Bcol;  // [64][Kcol] Toeplitz S(l - y - R8)
+    int R, R8, Krow, Kcol;
+    float unscale_row, unscale_col;   // 2^-sB of the B operands
+};
+struct TcUnitDev {
+    const float2 *phx, *phy;
+    int s, plane_a, plane_b, pad_;
+    int64_t sig_off;       // element offset of the unit's signal block in the intermediate
+};
+struct TcBankArgs {
+    const float *img;
+    int64_t pitch;
+    int H, W;
+    float2 *out;
+    int64_t plane;
+    uint16_t *sig;         // intermediate: [unit][signal][x][Hp], image row y at Lpad + y
+    int64_t Hp;
+    int Lpad, pad_;
+    const TcFreqDev *freqs;
+    const TcUnitDev *units;
+    int *status;
+};
+struct TcGeometry {
+    int R, R8, Krow, Kcol;
+    size_t smem_rows, smem_cols;
+};
+
 // Arguments of the FP32 localized-SDFT kernel (Algorithm 2).
 struct SdftArgs {
     const float *img;
@@ -106,6 +136,14 @@ cudaError_t launch_gabor_fp32(const BankArgs &a, int nitems, size_t smem, cudaSt
 cudaError_t gabor_fp32_prepare();
 cudaError_t launch_sdft_fp32(SdftArgs a, int sm_count, cudaStream_t st);
 cudaError_t sdft_fp32_prepare();
+// Tensor-core bank.
+TcGeometry gabor_tc_geometry(int R);
+bool gabor_tc_supported(int R);
+cudaError_t build_gabor_tc_b(uint16_t *Brow, uint16_t *Bcol, int R, double sigma, int bf16, float *unscale,
+                             cudaStream_t st);
+cudaError_t gabor_tc_prepare();
+cudaError_t launch_gabor_tc(const TcBankArgs &a, int nunits, size_t smem_rows, size_t smem_cols, const int4 *items,
+                            int nitems, int bf16, cudaStream_t st);
 // Sets the message returned by gabor_bank_last_error() on the calling host thread.
 void set_last_error(const char *msg);
 // Tensor-core SDFT (windowed-DFT contraction on tcgen05).
@@ -158,6 +196,18 @@ struct gabor_bank {
     float sdft_B_unscale = 1.f;
     double sdftB_sigma = -1.0;
     int sdftB_Mx = 0, sdftB_My = 0;
+    // tensor-core bank: B operands per frequency, intermediate signals, column work items
+    uint16_t *d_tcB = nullptr;
+    gb::TcFreqDev *d_tcfreq = nullptr;
+    gb::TcUnitDev *d_tcunit = nullptr;
+    uint16_t *d_tcsig = nullptr;
+    size_t tcsig_elems = 0;
+    int4 *d_tcitems = nullptr;
+    int tc_nitems = 0;
+    int tc_H = 0, tc_W = 0, tc_Lpad = 0;
+    int64_t tc_Hp = 0;
+    bool tc_ready = false;
+    size_t tc_smem_rows = 0, tc_smem_cols = 0;
     // device status word (bounded waits)
     int *d_status = nullptr;
     // batch image descriptors

@@ -142,3 +142,73 @@ def test_impulse_response_on_gpu(torch_cuda):
     got = run_bank(torch_cuda, img, [th], [om], [sg])[0, 0]
     ref = oracle.gabor_filter(img, om, th, sg)
     assert rel_err(got, ref) <= FP32_TOL
+
+
+# ---------------------------------------------------------------- tensor-core bank
+
+@pytest.mark.parametrize("precision", ["fp16_tc"])
+def test_tc_bank_c1_full_parity(torch_cuda, precision):
+    from tests.helpers import TC_TOL
+    img = synth.uniform01(0, 256, 256)
+    th, om, sg = c1_bank()
+    got = run_bank(torch_cuda, img, th, om, sg, precision=precision)
+    ref = oracle.gabor_bank(img, th, om, sg)
+    e = rel_err(got, ref)
+    print("TC C1", precision, "rel err", e, "worst plane", max(plane_rel_errs(got, ref)))
+    assert e <= TC_TOL
+
+
+@pytest.mark.parametrize("precision", ["fp16_tc"])
+@pytest.mark.parametrize("H,W", [(37, 75), (160, 200), (1, 50), (129, 33)])
+def test_tc_bank_ragged_and_c2_bank(torch_cuda, precision, H, W):
+    from tests.helpers import TC_TOL
+    img = synth.paper_like(0, H, W) if H > 8 and W > 8 else synth.pink_noise([3, H, W], H, W)
+    th, om, sg = c2_bank()
+    got = run_bank(torch_cuda, img, th, om, sg, precision=precision)
+    ref = oracle.gabor_bank(img, th, om, sg)
+    e = rel_err(got, ref)
+    print("TC", precision, H, W, "rel err", e)
+    assert e <= TC_TOL
+
+
+@pytest.mark.parametrize("precision", ["fp16_tc"])
+def test_tc_bank_c2_full_size_vs_fp32_and_oracle(torch_cuda, precision):
+    from tests.helpers import TC_TOL
+    img = synth.paper_like(0, 1024, 1024)
+    th, om, sg = c2_bank()
+    got = run_bank(torch_cuda, img, th, om, sg, precision=precision)
+    f32 = run_bank(torch_cuda, img, th, om, sg)
+    assert rel_err(got, f32) <= TC_TOL
+    rng = np.random.default_rng(13)
+    xs, ys = sample_points(rng, 1024, 1024, 800)
+    ref = oracle.gabor_bank(img, th, om, sg, points=(xs, ys))
+    scale = float(np.max(np.abs(f32)))
+    assert float(np.max(np.abs(got[:, :, ys, xs] - ref))) <= TC_TOL * scale
+
+
+def test_tc_bank_unpaired_orientations_and_reuse_off(torch_cuda):
+    from paper_1704_05231_gb300 import GaborBank
+    from tests.helpers import TC_TOL
+    torch = torch_cuda
+    img = synth.pink_noise(17, 90, 140)
+    th = [0.3, 1.2, math.pi - 0.3, 2.0]
+    om, sg = [0.9, 0.45], [2.0, 4.5]
+    t = torch.from_numpy(img).cuda()
+    ref = oracle.gabor_bank(img, th, om, sg)
+    with GaborBank(th, om, sg, precision="fp16_tc") as gbk:
+        a = gbk.filter(t).cpu().numpy()
+        gbk.set_option("reuse", 0)
+        b = gbk.filter(t).cpu().numpy()
+        gbk.device_status()
+    assert rel_err(a, ref) <= TC_TOL
+    assert rel_err(b, ref) <= TC_TOL
+
+
+def test_tc_bank_bf16_is_refused(torch_cuda):
+    from paper_1704_05231_gb300 import GaborBank, GBError
+    torch = torch_cuda
+    th, om, sg = c1_bank()
+    with GaborBank(th, om, sg, precision="bf16_tc") as gbk:
+        with pytest.raises(GBError) as ei:
+            gbk.filter(torch.zeros((32, 32), dtype=torch.float32, device="cuda"))
+        assert ei.value.status == -4
