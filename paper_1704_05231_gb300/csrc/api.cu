@@ -319,6 +319,9 @@ void free_tc(gabor_bank *h)
     dfree(h->d_tcunit);
     dfree(h->d_tcsig);
     dfree(h->d_tcitems);
+    dfree(h->d_tcrowitems);
+    dfree(h->d_tcfunits);
+    dfree(h->d_tcabsmax);
     h->tcsig_elems = 0;
     h->tc_nitems = 0;
     h->tc_H = h->tc_W = 0;
@@ -333,18 +336,17 @@ gb_status ensure_tc(gabor_bank *h, int H, int W, cudaStream_t st)
         GB_CU(cudaDeviceSynchronize());
         size_t total = 0;
         std::vector<size_t> off_r(nf), off_c(nf);
-        int rmax = 0;
+        h->tc_row_kmax = h->tc_row_pwmax = h->tc_col_kmax = 0;
         for (int s = 0; s < nf; ++s) {
             const TcGeometry g = gabor_tc_geometry(h->freqs[s].R);
             off_r[s] = total;
-            total += (size_t)64 * g.Krow;
+            total += (size_t)gabor_tc_row_tile_x() * g.Krow;
             off_c[s] = total;
-            total += (size_t)64 * g.Kcol;
-            h->tc_smem_rows = std::max(h->tc_smem_rows, g.smem_rows);
-            h->tc_smem_cols = std::max(h->tc_smem_cols, g.smem_cols);
-            rmax = std::max(rmax, h->freqs[s].R);
+            total += (size_t)gabor_tc_col_tile_y() * g.Kcol;
+            h->tc_row_kmax = std::max(h->tc_row_kmax, g.Krow);
+            h->tc_row_pwmax = std::max(h->tc_row_pwmax, g.PW);
+            h->tc_col_kmax = std::max(h->tc_col_kmax, g.Kcol);
         }
-        (void)rmax;
         GB_TRY(dalloc(&h->d_tcB, total));
         GB_TRY(dalloc(&h->d_tcfreq, (size_t)nf));
         std::vector<TcFreqDev> fd(nf);
@@ -355,6 +357,14 @@ gb_status ensure_tc(gabor_bank *h, int H, int W, cudaStream_t st)
             fd[s] = TcFreqDev{h->d_tcB + off_r[s], h->d_tcB + off_c[s], g.R, g.R8, g.Krow, g.Kcol, unscale, unscale};
         }
         GB_CU(cudaMemcpy(h->d_tcfreq, fd.data(), nf * sizeof(TcFreqDev), cudaMemcpyHostToDevice));
+        std::vector<int> fu(2 * nf);
+        for (int s = 0; s < nf; ++s) {
+            fu[s] = h->freqs[s].u1 - h->freqs[s].u0;
+            fu[nf + s] = h->freqs[s].u0;
+        }
+        GB_TRY(dalloc(&h->d_tcfunits, (size_t)2 * nf));
+        GB_TRY(dalloc(&h->d_tcabsmax, (size_t)1));
+        GB_CU(cudaMemcpy(h->d_tcfunits, fu.data(), fu.size() * sizeof(int), cudaMemcpyHostToDevice));
         h->tc_ready = true;
     }
     if (h->tc_H == H && h->tc_W == W) return GB_OK;
@@ -386,6 +396,16 @@ gb_status ensure_tc(gabor_bank *h, int H, int W, cudaStream_t st)
     std::stable_sort(items.begin(), items.end(), [&](const int4 &p, const int4 &q) {
         return h->freqs[h->units[p.x].s].R > h->freqs[h->units[q.x].s].R;
     });
+    std::vector<int> order(nf);
+    for (int s = 0; s < nf; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return h->freqs[p].R > h->freqs[q].R; });
+    std::vector<int4> ritems;
+    const int tx = gabor_tc_row_tile_x(), ty = gabor_tc_row_tile_y();
+    for (int s : order) {
+        if (h->freqs[s].u1 == h->freqs[s].u0) continue;
+        for (int y0 = 0; y0 < H; y0 += ty)
+            for (int x0 = 0; x0 < W; x0 += tx) ritems.push_back(make_int4(s, y0, x0, 0));
+    }
     if ((size_t)off > h->tcsig_elems) {
         dfree(h->d_tcsig);
         h->tcsig_elems = 0;
@@ -396,8 +416,12 @@ gb_status ensure_tc(gabor_bank *h, int H, int W, cudaStream_t st)
     GB_CU(cudaMemsetAsync(h->d_tcsig, 0, (size_t)off * sizeof(uint16_t), st));
     dfree(h->d_tcunit);
     dfree(h->d_tcitems);
+    dfree(h->d_tcrowitems);
     GB_TRY(dalloc(&h->d_tcunit, (size_t)nu));
     GB_TRY(dalloc(&h->d_tcitems, items.size()));
+    GB_TRY(dalloc(&h->d_tcrowitems, ritems.size()));
+    GB_CU(cudaMemcpy(h->d_tcrowitems, ritems.data(), ritems.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    h->tc_nrowitems = (int)ritems.size();
     GB_CU(cudaMemcpy(h->d_tcunit, ud.data(), nu * sizeof(TcUnitDev), cudaMemcpyHostToDevice));
     GB_CU(cudaMemcpy(h->d_tcitems, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
     h->tc_nitems = (int)items.size();
@@ -433,8 +457,13 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.freqs = h->d_tcfreq;
     a.units = h->d_tcunit;
     a.status = h->d_status;
-    GB_CU(launch_gabor_tc(a, (int)h->units.size(), h->tc_smem_rows, h->tc_smem_cols, h->d_tcitems, h->tc_nitems,
-                          h->prec == GB_BF16_TC, st));
+    a.row_kmax = h->tc_row_kmax;
+    a.row_pwmax = h->tc_row_pwmax;
+    a.col_kmax = h->tc_col_kmax;
+    a.absmax = h->d_tcabsmax;
+    const int nf = (int)h->freqs.size();
+    GB_CU(launch_gabor_tc(a, h->d_tcrowitems, h->tc_nrowitems, h->d_tcfunits, h->d_tcfunits + nf, h->d_tcitems,
+                          h->tc_nitems, h->sm_count, st));
     return GB_OK;
 }
 

@@ -86,9 +86,11 @@ struct TcBankArgs {
     const TcFreqDev *freqs;
     const TcUnitDev *units;
     int *status;
+    int row_kmax, row_pwmax, col_kmax, pad2_;
+    int *absmax;           // device word: max |f| of the image as float bits (k_absmax)
 };
 struct TcGeometry {
-    int R, R8, Krow, Kcol;
+    int R, R8, Krow, Kcol, PW;
     size_t smem_rows, smem_cols;
 };
 
@@ -142,8 +144,11 @@ bool gabor_tc_supported(int R);
 cudaError_t build_gabor_tc_b(uint16_t *Brow, uint16_t *Bcol, int R, double sigma, int bf16, float *unscale,
                              cudaStream_t st);
 cudaError_t gabor_tc_prepare();
-cudaError_t launch_gabor_tc(const TcBankArgs &a, int nunits, size_t smem_rows, size_t smem_cols, const int4 *items,
-                            int nitems, int bf16, cudaStream_t st);
+cudaError_t launch_gabor_tc(const TcBankArgs &a, const int4 *row_items, int n_row_items, const int *funits,
+                            const int *funit0, const int4 *col_items, int n_col_items, int sm_count, cudaStream_t st);
+int gabor_tc_row_tile_x();
+int gabor_tc_row_tile_y();
+int gabor_tc_col_tile_y();
 // Sets the message returned by gabor_bank_last_error() on the calling host thread.
 void set_last_error(const char *msg);
 // Tensor-core SDFT (windowed-DFT contraction on tcgen05).
@@ -202,8 +207,13 @@ struct gabor_bank {
     gb::TcUnitDev *d_tcunit = nullptr;
     uint16_t *d_tcsig = nullptr;
     size_t tcsig_elems = 0;
-    int4 *d_tcitems = nullptr;
+    int4 *d_tcitems = nullptr;      // column-pass items
     int tc_nitems = 0;
+    int4 *d_tcrowitems = nullptr;   // row-pass items
+    int tc_nrowitems = 0;
+    int *d_tcfunits = nullptr;      // [n_freq] units per frequency, then [n_freq] first unit
+    int tc_row_kmax = 0, tc_row_pwmax = 0, tc_col_kmax = 0;
+    int *d_tcabsmax = nullptr;
     int tc_H = 0, tc_W = 0, tc_Lpad = 0;
     int64_t tc_Hp = 0;
     bool tc_ready = false;
