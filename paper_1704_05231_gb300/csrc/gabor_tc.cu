@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const TcBankArgs a, co
 // Items: (unit, x0, y0), sorted by frequency; paired units take 32 columns x 4 signals,
 // unpaired ones 64 columns x 2 signals (always 128 A rows).  The producers keep one job of
 // operand loads in flight ahead of the MMA.
-__global__ void __launch_bounds__(384, 1) k_gabor_tc_cols(const TcBankArgs a, const int4 *__restrict__ items,
+__global__ void __launch_bounds__(256, 1) k_gabor_tc_cols(const TcBankArgs a, const int4 *__restrict__ items,
                                                           int nitems)
 {
     extern __shared__ unsigned char smem_dyn[];
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_cols(const TcBankArgs a, co
     float *xch = reinterpret_cast<float *>(sm + L.xch_off);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.bar_off);
     uint64_t *tmem_full = bars;        // [2]
-    uint64_t *tmem_empty = bars + 2;   // [2] 8 epilogue warps
+    uint64_t *tmem_empty = bars + 2;   // [2] 4 epilogue warps
     uint64_t *a_empty = bars + 4;      // [2] commit
     uint64_t *drain = bars + 6;
     uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
@@ -363,8 +363,8 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_cols(const TcBankArgs a, co
     if (tid == 0) {
         mbar_init(&tmem_full[0], 1);
         mbar_init(&tmem_full[1], 1);
-        mbar_init(&tmem_empty[0], 8);
-        mbar_init(&tmem_empty[1], 8);
+        mbar_init(&tmem_empty[0], 4);
+        mbar_init(&tmem_empty[1], 4);
         mbar_init(&a_empty[0], 1);
         mbar_init(&a_empty[1], 1);
         mbar_init(drain, 1);
@@ -382,9 +382,9 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_cols(const TcBankArgs a, co
     const uint32_t idesc = idesc_f16(0, 128, kColTileY);
     const int njobs = nitems > (int)blockIdx.x ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
-    if (warp >= 8) {
+    if (warp >= 4) {
         // -------------------------------------------------------------- producers
-        const int ptid = tid - 256, pwarp = warp - 8;
+        const int ptid = tid - 128;
         auto item = [&](int j) { return items[blockIdx.x + j * gridDim.x]; };
         auto load_g = [&](int s) {
             const TcFreqDev f = a.freqs[s];
@@ -402,18 +402,15 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_cols(const TcBankArgs a, co
             const int64_t lbase = (int64_t)a.Lpad + y0 - f.R8;
             unsigned char *dstA = sA + (j & 1) * abuf;
             const int kch = K / 8;
-            // a warp takes whole A rows n (one signal of one column): lanes walk its 16-byte chunks
-            for (int n = pwarp; n < 128; n += 4) {
-                const int sgi = n >= xw ? (n >= 2 * xw ? (n >= 3 * xw ? 3 : 2) : 1) : 0;
-                const int x = n - sgi * xw;
+            for (int ci = ptid; ci < 128 * kch; ci += 128) {
+                const int n = ci / kch, kc = ci - n * kch;
+                const int sgi = n / xw, x = n - sgi * xw;
                 const bool ok = x0 + x < a.W;
-                const uint16_t *src = a.sig + u.sig_off + ((int64_t)sgi * a.W + (ok ? x0 + x : 0)) * a.Hp + lbase;
-                for (int kc = lane; kc < kch; kc += 32) {
-                    const unsigned sdst = smem_u32(dstA + sw128_offset(128, n, 8 * kc));
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sdst), "l"(src + 8 * kc),
-                                 "r"(ok ? 16 : 0)
-                                 : "memory");
-                }
+                const uint16_t *src =
+                    a.sig + u.sig_off + ((int64_t)sgi * a.W + (ok ? x0 + x : 0)) * a.Hp + lbase + 8 * kc;
+                const unsigned sdst = smem_u32(dstA + sw128_offset(128, n, 8 * kc));
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sdst), "l"(src), "r"(ok ? 16 : 0)
+                             : "memory");
             }
             cp_async_commit();
         };
@@ -480,59 +477,57 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_cols(const TcBankArgs a, co
         }
     } else {
         // -------------------------------------------------------------- epilogue
-        // D[n][y]: TMEM quadrant q = warp & 3 holds rows 32q .. 32q+31; warp >> 2 picks the
-        // half of the 64 output rows this warp handles.
-        //   paired:   quadrant 0 P, 1 Q (theta), 2 P', 3 Q' (pi - theta), x = lane
-        //   unpaired: quadrants 0-1 P (x = 32 (q & 1) + lane), quadrants 2-3 Q
-        const int qd = warp & 3, yh = warp >> 2;
-        const uint32_t lane_base = (uint32_t)(32 * qd) << 16;
+        // D[n][y]: warp w holds rows 32w .. 32w+31.
+        //   paired:   warp 0 P, 1 Q (theta), 2 P', 3 Q' (pi - theta), x = lane
+        //   unpaired: warps 0-1 P (x = 32 (w & 1) + lane), warps 2-3 Q
+        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
         for (int j = 0; j < njobs; ++j) {
             const int4 w = items[blockIdx.x + j * gridDim.x];
             const TcUnitDev u = a.units[w.x];
             const TcFreqDev f = a.freqs[u.s];
             const int x0 = w.y, y0 = w.z, b = j & 1;
             const bool paired = u.plane_b >= 0;
-            const bool is_q = paired ? (qd & 1) : (qd >= 2);
-            const int slot = paired ? (qd >> 1) : (qd & 1);
-            // row phases of this warp's 32 rows: lane l holds row y0 + 32 yh + l
-            const int ry = y0 + 32 * yh + lane;
-            const float2 pyl = ry < a.H ? __ldg(&u.phy[ry]) : make_float2(0.f, 0.f);
+            const bool is_q = paired ? (warp & 1) : (warp >= 2);
+            const int slot = paired ? (warp >> 1) : (warp & 1);
+            // row phases: lane l holds rows y0 + l and y0 + 32 + l
+            const float2 py0 = (y0 + lane < a.H) ? __ldg(&u.phy[y0 + lane]) : make_float2(0.f, 0.f);
+            const float2 py1 = (y0 + 32 + lane < a.H) ? __ldg(&u.phy[y0 + 32 + lane]) : make_float2(0.f, 0.f);
             const bool failed = !mbar_wait(&tmem_full[b], (j >> 1) & 1, abort_s);
-            if (named_barrier_or(2, 256, failed)) {
+            if (named_barrier_or(2, 128, failed)) {
                 if (tid == 0) fail_status(a.status, abort_s, 33);
                 break;
             }
             tc_fence_after();
             const float unscale = f.unscale_col;
-            const uint32_t tb = tmem + lane_base + 64u * b + 32 * yh;
+            const uint32_t tb = tmem + lane_base + 64u * b;
             if (is_q) {
 #pragma unroll 1
-                for (int c0 = 0; c0 < 32; c0 += 16) {
+                for (int c0 = 0; c0 < kColTileY; c0 += 16) {
                     float v[16];
                     tmem_ld16(tb + c0, v);
 #pragma unroll
-                    for (int jj = 0; jj < 16; ++jj)
-                        xch[(slot * kColTileY + 32 * yh + c0 + jj) * 32 + lane] = v[jj] * unscale;
+                    for (int jj = 0; jj < 16; ++jj) xch[(slot * kColTileY + c0 + jj) * 32 + lane] = v[jj] * unscale;
                 }
             }
-            named_barrier(2, 256);
+            named_barrier(2, 128);
             if (!is_q) {
                 const int x = x0 + (paired ? lane : 32 * slot + lane);
                 const int plane = paired ? (slot == 0 ? u.plane_a : u.plane_b) : u.plane_a;
                 float2 *o = a.out + (int64_t)plane * a.plane + x;
 #pragma unroll 1
-                for (int c0 = 0; c0 < 32; c0 += 16) {
+                for (int c0 = 0; c0 < kColTileY; c0 += 16) {
                     float v[16];
                     tmem_ld16(tb + c0, v);
 #pragma unroll
                     for (int jj = 0; jj < 16; ++jj) {
-                        const int r = c0 + jj;                    // row within this warp's half
-                        const float tx = __shfl_sync(0xffffffffu, pyl.x, r);
-                        const float ty = __shfl_sync(0xffffffffu, pyl.y, r);
-                        const int yy = y0 + 32 * yh + r;
+                        const int r = c0 + jj;
+                        const float2 pyr = r < 32 ? py0 : py1;
+                        const float tx = __shfl_sync(0xffffffffu, pyr.x, r & 31);
+                        const float ty = __shfl_sync(0xffffffffu, pyr.y, r & 31);
+                        const int yy = y0 + r;
                         if (x < a.W && yy < a.H) {
                             const float P = v[jj] * unscale;
-                            const float Q = xch[(slot * kColTileY + 32 * yh + r) * 32 + lane];
+                            const float Q = xch[(slot * kColTileY + r) * 32 + lane];
                             // Eq. 7-8 (theta) and Eq. 15-16 (pi - theta)
                             __stcs(o + (int64_t)yy * a.W, make_float2(fmaf(tx, P, ty * Q), fmaf(ty, P, -tx * Q)));
                         }
@@ -540,7 +535,7 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_cols(const TcBankArgs a, co
                 }
             }
             tc_fence_before();
-            named_barrier(2, 256);   // xch is free for the next job
+            named_barrier(2, 128);   // xch is free for the next job
             if (lane == 0) mbar_arrive(&tmem_empty[b]);
         }
     }
@@ -554,14 +549,18 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_cols(const TcBankArgs a, co
 __global__ void k_absmax(const float *__restrict__ img, int64_t pitch, int H, int W, int *__restrict__ out)
 {
     float m = 0.f;
-    const int64_t n = (int64_t)H * W;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t y = i / W, x = i - y * W;
-        m = fmaxf(m, fabsf(__ldg(img + y * pitch + x)));
-    }
+    for (int y = blockIdx.y; y < H; y += gridDim.y)
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < W; x += gridDim.x * blockDim.x)
+            m = fmaxf(m, fabsf(__ldg(img + (int64_t)y * pitch + x)));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_int(m));
+    __shared__ float wm[32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, wm[i]);
+        atomicMax(out, __float_as_int(m));   // one atomic per block
+    }
 }
 
 // ------------------------------------------------------------------------ Toeplitz B (FP64)
@@ -635,8 +634,8 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a, const int4 *row_items, int n_ro
     const size_t smem_c = gabor_tc_smem_cols(a.col_kmax);
     cudaError_t e0 = cudaMemsetAsync(a.absmax, 0, sizeof(int), st);
     if (e0 != cudaSuccess) return e0;
-    k_absmax<<<std::max(1, std::min(sm_count * 4, (int)(((int64_t)a.H * a.W + 1023) / 1024))), 256, 0, st>>>(
-        a.img, a.pitch, a.H, a.W, a.absmax);
+    const dim3 ag(std::max(1, std::min(4, (a.W + 255) / 256)), std::max(1, std::min(a.H, 2 * sm_count)));
+    k_absmax<<<ag, 256, 0, st>>>(a.img, a.pitch, a.H, a.W, a.absmax);
     e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
     if (n_row_items > 0) {
@@ -645,7 +644,7 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a, const int4 *row_items, int n_ro
         if (e != cudaSuccess) return e;
     }
     if (n_col_items > 0) {
-        k_gabor_tc_cols<<<std::min(n_col_items, sm_count), 384, smem_c, st>>>(a, col_items, n_col_items);
+        k_gabor_tc_cols<<<std::min(n_col_items, sm_count), 256, smem_c, st>>>(a, col_items, n_col_items);
         return cudaGetLastError();
     }
     return cudaSuccess;
