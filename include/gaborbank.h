@@ -125,10 +125,13 @@ gb_status gabor_bank_sdft(gabor_bank_t h, const float *d_img, int H, int W, int6
 
 /*
  * gabor_bank_filter_batch - gabor_bank_filter for n independent images of possibly
- * different sizes, in one persistent launch (a device work queue over (image, tile)
- * items).  d_imgs[i], H[i], W[i], pitch[i], d_outs[i] as in gabor_bank_filter; the host
- * arrays are read during the call only.  Asynchronous.  Results are bitwise identical to
- * n separate gabor_bank_filter calls with the same handle.
+ * different sizes, in one persistent launch (one CTA per SM pulls cost-sorted (image, unit,
+ * strip, segment) items from a device work queue).  d_imgs[i], H[i], W[i], pitch[i],
+ * d_outs[i] as in gabor_bank_filter; the host arrays are read during the call only.
+ * Asynchronous.  Results are bitwise identical to n separate gabor_bank_filter calls with the
+ * same handle.  A call whose pointers and shapes equal the previous call's (and whose tables
+ * already exist) enqueues only a memset and the kernel, so it can be captured in a CUDA graph.
+ * FP32 handles: one launch; tensor-core handles: one bank pass per image.
  */
 gb_status gabor_bank_filter_batch(gabor_bank_t h, int n, const float *const *d_imgs,
                                   const int *H, const int *W, const int64_t *pitch,
@@ -147,6 +150,15 @@ typedef enum {
 
 /* gabor_bank_set_option - set an option; GB_ERR_INVALID_ARG on an unknown key or value. */
 gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value);
+
+/*
+ * gabor_bank_set_tiling - tile geometry of the FP32 bank kernel for frequency s (s = -1: all
+ * frequencies): rows per streamed chunk (0 = automatic, or 8, 16, 32, 64) and row segments per
+ * column strip (0 = automatic, or 1 .. 64).  This trades the 2R-row halo recomputed per
+ * segment against load balance; results do not change (the arithmetic of every output is the
+ * same).  Used by the autotuner.  Synchronises the device.  GB_ERR_INVALID_ARG on bad values.
+ */
+gb_status gabor_bank_set_tiling(gabor_bank_t h, int s, int tile_rows, int segments);
 
 /*
  * gabor_bank_device_status - wait for `stream`, then read and clear the handle's device

@@ -36,6 +36,7 @@ SIGNATURES = {
                                          ctypes.POINTER(_c_int), ctypes.POINTER(_c_i64),
                                          ctypes.POINTER(_vp), _vp]),
     "gabor_bank_set_option": (_c_int, [_vp, _c_int, _c_i64]),
+    "gabor_bank_set_tiling": (_c_int, [_vp, _c_int, _c_int, _c_int]),
     "gabor_bank_device_status": (_c_int, [_vp, _vp]),
     "gabor_bank_output_elems": (_c_i64, [_vp, _c_int, _c_int]),
     "gabor_bank_last_error": (ctypes.c_char_p, []),
@@ -137,6 +138,10 @@ class GaborBank:
         _check(self._lib.gabor_bank_set_option(self._h, OPTION[key] if isinstance(key, str) else int(key),
                                                int(value)))
 
+    def set_tiling(self, s, tile_rows, segments):
+        """FP32 kernel tile geometry for frequency s (-1: all); 0 means automatic."""
+        _check(self._lib.gabor_bank_set_tiling(self._h, int(s), int(tile_rows), int(segments)))
+
     def device_status(self, stream=None):
         _check(self._lib.gabor_bank_device_status(self._h, _stream_handle(stream)))
 
@@ -213,6 +218,27 @@ class GaborBank:
                                          1 if half_spectrum else 0, ctypes.c_void_p(out.data_ptr()),
                                          _stream_handle(stream)))
         return out
+
+
+def capture_graph(fn, warmup=1):
+    """Capture `fn` (library calls on the current stream) into a CUDA graph.
+
+    `fn` runs `warmup` times eagerly on a side stream first, so that the library builds its
+    tables and work lists outside the capture; the returned torch.cuda.CUDAGraph replays the
+    launches with `.replay()`.
+    """
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(warmup):
+            fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        fn()
+    return graph
 
 
 def version():

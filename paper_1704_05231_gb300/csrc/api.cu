@@ -183,7 +183,8 @@ gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
     h->freqdev.resize(nf);
     h->max_smem = 0;
     for (int s = 0; s < nf; ++s) {
-        FreqDev fd = gabor_fp32_geometry(h->freqs[s].R, h->tile_rows);
+        const int tr = (s < (int)h->ftile_rows.size() && h->ftile_rows[s] > 0) ? h->ftile_rows[s] : h->tile_rows;
+        FreqDev fd = gabor_fp32_geometry(h->freqs[s].R, tr);
         fd.taps = h->d_taps + (size_t)s * h->tpad_max;
         h->freqdev[s] = fd;
         h->max_smem = std::max(h->max_smem, gabor_fp32_smem_bytes(fd));
@@ -278,8 +279,9 @@ gb_status get_worklist(gabor_bank *h, const std::vector<int64_t> &shapes, WorkIt
         const int nstrips = (Ww + kStripW - 1) / kStripW;
         for (int s = 0; s < (int)h->freqs.size(); ++s) {
             const FreqDev &f = h->freqdev[s];
-            int nseg = h->segments > 0 ? h->segments : 1;
-            if (h->segments <= 0) {
+            const int fseg = (s < (int)h->fsegments.size() && h->fsegments[s] > 0) ? h->fsegments[s] : h->segments;
+            int nseg = fseg > 0 ? fseg : 1;
+            if (fseg <= 0) {
                 const int min_len = std::max(f.TH, 2 * f.R);
                 while (strip_cost(s, true, Hh, nseg) > cap && Hh / (nseg + 1) >= min_len) ++nseg;
             }
@@ -400,7 +402,8 @@ gb_status ensure_tc(gabor_bank *h, int H, int W, cudaStream_t st)
     for (int s = 0; s < nf; ++s) order[s] = s;
     std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return h->freqs[p].R > h->freqs[q].R; });
     std::vector<int4> ritems;
-    const int tx = gabor_tc_row_tile_x(), ty = gabor_tc_row_tile_y();
+    const int tx = gabor_tc_row_tile_x(), ty = gabor_tc_row_tile_y(rmax);
+    h->tc_row_ty = ty;
     for (int s : order) {
         if (h->freqs[s].u1 == h->freqs[s].u0) continue;
         for (int y0 = 0; y0 < H; y0 += ty)
@@ -461,6 +464,7 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.row_pwmax = h->tc_row_pwmax;
     a.col_kmax = h->tc_col_kmax;
     a.absmax = h->d_tcabsmax;
+    a.row_ty = h->tc_row_ty;
     const int nf = (int)h->freqs.size();
     GB_CU(launch_gabor_tc(a, h->d_tcrowitems, h->tc_nrowitems, h->d_tcfunits, h->d_tcfunits + nf, h->d_tcitems,
                           h->tc_nitems, h->sm_count, st));
@@ -481,7 +485,8 @@ gb_status filter_device(gabor_bank *h, const float *d_img, int H, int W, int64_t
     a.freqs = h->d_freqdev;
     a.units = h->d_unitdev;
     a.items = items;
-    GB_CU(launch_gabor_fp32(a, n, h->max_smem, st));
+    a.counter = h->d_counter;
+    GB_CU(launch_gabor_fp32(a, n, h->max_smem, h->sm_count, st));
     return GB_OK;
 }
 
@@ -537,9 +542,11 @@ gb_status gabor_bank_create(gabor_bank_t *out, const double *theta, int n_theta,
     if (e == cudaSuccess) e = gabor_tc_prepare();
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&h->d_status), sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&h->d_counter), sizeof(int));
     if (e != cudaSuccess) {
         cudaGetLastError();
         dfree(h->d_status);
+        dfree(h->d_counter);
         delete h;
         return fail(GB_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
     }
@@ -564,6 +571,7 @@ gb_status gabor_bank_destroy(gabor_bank_t h)
     dfree(h->d_sdft_taps);
     dfree(h->d_sdft_tw);
     dfree(h->d_status);
+    dfree(h->d_counter);
     dfree(h->d_stage_img);
     dfree(h->d_imgs);
     free_tc(h);
@@ -698,8 +706,11 @@ gb_status gabor_bank_filter_batch(gabor_bank_t h, int n, const float *const *d_i
     GB_TRY(check_sticky());
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (n == 0) return GB_OK;
-    if (h->prec != GB_FP32)
-        return fail(GB_ERR_UNSUPPORTED, "the filter bank runs in GB_FP32 only on this handle");
+    if (h->prec != GB_FP32) {
+        // tensor-core handles: one bank pass (row and column kernels) per image
+        for (int i = 0; i < n; ++i) GB_TRY(filter_device_tc(h, d_imgs[i], H[i], W[i], pitch[i], d_outs[i], st));
+        return GB_OK;
+    }
     int Hm = 0, Wm = 0;
     for (int i = 0; i < n; ++i) {
         Hm = std::max(Hm, H[i]);
@@ -713,6 +724,7 @@ gb_status gabor_bank_filter_batch(gabor_bank_t h, int n, const float *const *d_i
         h->imgs_cap = 0;
         GB_TRY(dalloc(&h->d_imgs, (size_t)n));
         h->imgs_cap = n;
+        h->last_imgs.clear();
     }
     std::vector<ImageDev> imgs(n);
     std::vector<int64_t> shapes(2 * (size_t)n);
@@ -721,8 +733,16 @@ gb_status gabor_bank_filter_batch(gabor_bank_t h, int n, const float *const *d_i
         shapes[2 * i] = H[i];
         shapes[2 * i + 1] = W[i];
     }
-    // Pageable source: the copy is complete (staged) when the call returns.
-    GB_CU(cudaMemcpyAsync(h->d_imgs, imgs.data(), n * sizeof(ImageDev), cudaMemcpyHostToDevice, st));
+    // Upload the descriptors only when they changed since the last batch call, so that a
+    // repeated call (for example under CUDA graph capture) issues no host-to-device copy.
+    bool same = h->last_imgs.size() == (size_t)n;
+    for (int i = 0; same && i < n; ++i)
+        same = std::memcmp(&h->last_imgs[i], &imgs[i], sizeof(ImageDev)) == 0;
+    if (!same) {
+        // Pageable source: the copy is complete (staged) when the call returns.
+        GB_CU(cudaMemcpyAsync(h->d_imgs, imgs.data(), n * sizeof(ImageDev), cudaMemcpyHostToDevice, st));
+        h->last_imgs = imgs;
+    }
     WorkItem *items = nullptr;
     int nitems = 0;
     GB_TRY(get_worklist(h, shapes, &items, &nitems));
@@ -731,7 +751,8 @@ gb_status gabor_bank_filter_batch(gabor_bank_t h, int n, const float *const *d_i
     a.freqs = h->d_freqdev;
     a.units = h->d_unitdev;
     a.items = items;
-    GB_CU(launch_gabor_fp32(a, nitems, h->max_smem, st));
+    a.counter = h->d_counter;
+    GB_CU(launch_gabor_fp32(a, nitems, h->max_smem, h->sm_count, st));
     return GB_OK;
 }
 
@@ -773,6 +794,27 @@ gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value)
     default:
         return fail(GB_ERR_INVALID_ARG, "unknown option");
     }
+}
+
+gb_status gabor_bank_set_tiling(gabor_bank_t h, int s, int tile_rows, int segments)
+{
+    if (!h) return fail(GB_ERR_INVALID_ARG, "NULL handle");
+    const int nf = (int)h->freqs.size();
+    if (s < -1 || s >= nf) return fail(GB_ERR_INVALID_ARG, "frequency index out of range");
+    if (tile_rows != 0 && tile_rows != 8 && tile_rows != 16 && tile_rows != 32 && tile_rows != 64)
+        return fail(GB_ERR_INVALID_ARG, "tile_rows takes 0, 8, 16, 32 or 64");
+    if (segments < 0 || segments > 64) return fail(GB_ERR_INVALID_ARG, "segments takes 0 .. 64");
+    DeviceGuard g(h->device);
+    cudaDeviceSynchronize();
+    h->ftile_rows.resize(nf, 0);
+    h->fsegments.resize(nf, 0);
+    for (int i = 0; i < nf; ++i) {
+        if (s != -1 && i != s) continue;
+        h->ftile_rows[i] = tile_rows;
+        h->fsegments[i] = segments;
+    }
+    free_tables(h);   // tile geometry and work lists are rebuilt on the next call
+    return GB_OK;
 }
 
 gb_status gabor_bank_device_status(gabor_bank_t h, void *stream)

@@ -22,20 +22,26 @@ __device__ __forceinline__ float2 fmav(float2 w, float t, float2 a)
 }
 
 // acc[j] += sum_d win[j + d] * t[d] for the 8 taps of one chunk; win = lo[0..7] ++ hi[0..7].
+// The products that only need `lo` come first, so the loads of `hi` (issued just before the
+// call) have 36 FMA groups of slack; j runs innermost so consecutive FMAs are independent.
 template <typename V>
-__device__ __forceinline__ void conv_step(const V (&lo)[8], const V (&hi)[8], const float4 *t4,
+__device__ __forceinline__ void conv_step(const V (&lo)[8], const V (&hi)[8], const float4 t0, const float4 t1,
                                           V (&acc)[8])
 {
-    const float4 t0 = t4[0], t1 = t4[1];
     const float t[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
 #pragma unroll
     for (int d = 0; d < 8; ++d)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j] = fmav(j + d < 8 ? lo[j + d] : hi[j + d - 8], t[d], acc[j]);
+        for (int j = 0; j < 8 - d; ++j) acc[j] = fmav(lo[j + d], t[d], acc[j]);
+#pragma unroll
+    for (int d = 1; d < 8; ++d)
+#pragma unroll
+        for (int j = 8 - d; j < 8; ++j) acc[j] = fmav(hi[j + d - 8], t[d], acc[j]);
 }
 
 // Contiguous source (row pass): out[j] = sum_t src[j + t] * taps[t], j < 8.
-// Reads src[0 .. 8 * nchunks + 7].
+// Reads src[0 .. 8 * nchunks + 7].  Window and taps of the next chunk are loaded one chunk
+// ahead; two register banks alternate (no copies).
 template <typename V>
 __device__ __forceinline__ void conv8_linear(const V *__restrict__ src, const float4 *__restrict__ taps4,
                                              int nchunks, V (&acc)[8])
@@ -43,19 +49,23 @@ __device__ __forceinline__ void conv8_linear(const V *__restrict__ src, const fl
     V wa[8], wb[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) wa[i] = src[i];
+    float4 t0 = taps4[0], t1 = taps4[1];
     int c = 0;
     for (; c + 2 <= nchunks; c += 2) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) wb[i] = src[8 * (c + 1) + i];
-        conv_step(wa, wb, taps4 + 2 * c, acc);
+        const float4 u0 = taps4[2 * c + 2], u1 = taps4[2 * c + 3];
+        conv_step(wa, wb, t0, t1, acc);
 #pragma unroll
         for (int i = 0; i < 8; ++i) wa[i] = src[8 * (c + 2) + i];
-        conv_step(wb, wa, taps4 + 2 * (c + 1), acc);
+        t0 = taps4[2 * c + 4];
+        t1 = taps4[2 * c + 5];
+        conv_step(wb, wa, u0, u1, acc);
     }
     if (c < nchunks) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) wb[i] = src[8 * (c + 1) + i];
-        conv_step(wa, wb, taps4 + 2 * c, acc);
+        conv_step(wa, wb, t0, t1, acc);
     }
 }
 
@@ -73,22 +83,26 @@ __device__ __forceinline__ void conv8_ring(const V *__restrict__ ring, int strid
     };
 #pragma unroll
     for (int i = 0; i < 8; ++i) wa[i] = ring[(s + i) * stride];
+    float4 t0 = taps4[0], t1 = taps4[1];
     int c = 0;
     for (; c + 2 <= nchunks; c += 2) {
         adv();
 #pragma unroll
         for (int i = 0; i < 8; ++i) wb[i] = ring[(s + i) * stride];
-        conv_step(wa, wb, taps4 + 2 * c, acc);
+        const float4 u0 = taps4[2 * c + 2], u1 = taps4[2 * c + 3];
+        conv_step(wa, wb, t0, t1, acc);
         adv();
 #pragma unroll
         for (int i = 0; i < 8; ++i) wa[i] = ring[(s + i) * stride];
-        conv_step(wb, wa, taps4 + 2 * (c + 1), acc);
+        t0 = taps4[2 * c + 4];
+        t1 = taps4[2 * c + 5];
+        conv_step(wb, wa, u0, u1, acc);
     }
     if (c < nchunks) {
         adv();
 #pragma unroll
         for (int i = 0; i < 8; ++i) wb[i] = ring[(s + i) * stride];
-        conv_step(wa, wb, taps4 + 2 * c, acc);
+        conv_step(wa, wb, t0, t1, acc);
     }
 }
 

@@ -72,16 +72,14 @@ FreqDev gabor_fp32_geometry(int R, int tile_rows)
     for (;;) {
         f.TH = TH;
         f.RS = round_up(TH + f.T - 1, 8);
-        if (gabor_fp32_smem_bytes(f) <= (size_t)kSmemLimit || TH <= 8) break;
+        if (gabor_fp32_smem_bytes(f) <= (size_t)(kSmemLimit - kStaticSmemReserve) || TH <= 8) break;
         TH /= 2;
     }
     return f;
 }
 
-__global__ void __launch_bounds__(kThreads) k_gabor_fp32(const BankArgs a)
+__device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkItem it, unsigned char *smem_raw)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const WorkItem it = a.items[blockIdx.x];
     const UnitDev u = a.units[it.unit];
     const FreqDev f = a.freqs[u.s];
     const ImageDev im = a.imgs ? a.imgs[it.img] : a.img0;
@@ -254,16 +252,41 @@ __global__ void __launch_bounds__(kThreads) k_gabor_fp32(const BankArgs a)
     }
 }
 
-cudaError_t gabor_fp32_prepare()
+// Persistent CTAs pull work items (cost-sorted, largest first) from a device counter that the
+// launcher zeroes before the launch.
+__global__ void __launch_bounds__(kThreads) k_gabor_fp32(const BankArgs a)
 {
-    return cudaFuncSetAttribute(k_gabor_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kSmemLimit);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int next_item;
+    for (;;) {
+        if (threadIdx.x == 0) next_item = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int item = next_item;
+        if (item >= a.nitems) break;
+        gabor_fp32_item(a, a.items[item], smem_raw);
+        __syncthreads();   // shared memory is reused by the next item
+    }
 }
 
-cudaError_t launch_gabor_fp32(const BankArgs &a, int nitems, size_t smem, cudaStream_t st)
+cudaError_t gabor_fp32_prepare()
+{
+    // the kernel's own static shared memory (the work-queue word) counts against the limit
+    return cudaFuncSetAttribute(k_gabor_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kSmemLimit - kStaticSmemReserve);
+}
+
+cudaError_t launch_gabor_fp32(const BankArgs &a0, int nitems, size_t smem, int sm_count, cudaStream_t st)
 {
     if (nitems <= 0) return cudaSuccess;
-    k_gabor_fp32<<<nitems, kThreads, smem, st>>>(a);
+    BankArgs a = a0;
+    a.nitems = nitems;
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    int cps = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k_gabor_fp32, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(nitems, std::max(1, cps) * sm_count);
+    k_gabor_fp32<<<grid, kThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

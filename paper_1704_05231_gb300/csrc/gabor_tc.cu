@@ -34,7 +34,7 @@ namespace gb {
 namespace {
 
 constexpr int kRowTileX = 128;   // row kernel: image columns per tile (MMA M)
-constexpr int kRowTileY = 64;    // row kernel: image rows per tile (MMA N = 2 x 64)
+constexpr int kRowTileYMax = 64; // row kernel: image rows per tile (64, or 32 for large radii; MMA N = 2 x rows)
 constexpr int kColTileY = 64;    // column kernel: output rows per tile (MMA N)
 
 __device__ __forceinline__ uint16_t h16(float v) { return __half_as_ushort(__float2half_rn(v)); }
@@ -49,13 +49,13 @@ struct RowSmem {
     uint32_t t_off, dm_off, patch_off, ph_off, bar_off, misc_off, total;
 };
 
-__host__ __device__ inline RowSmem row_smem(int K, int PW)
+__host__ __device__ inline RowSmem row_smem(int K, int PW, int TY)
 {
     RowSmem L;
     L.t_off = 0;
     L.dm_off = L.t_off + (uint32_t)kRowTileX * K * 2;
-    L.patch_off = L.dm_off + (uint32_t)(2 * kRowTileY) * K * 2;
-    L.ph_off = L.patch_off + (uint32_t)kRowTileY * (round_up(PW, 8) + 4) * 4;
+    L.patch_off = L.dm_off + (uint32_t)(2 * TY) * K * 2;
+    L.ph_off = L.patch_off + (uint32_t)TY * (round_up(PW, 8) + 4) * 4;
     L.bar_off = (L.ph_off + (uint32_t)PW * 8 + 15) & ~15u;
     L.misc_off = L.bar_off + 8 * 8;
     L.total = L.misc_off + 64;
@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const TcBankArgs a, co
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const RowSmem L = row_smem(a.row_kmax, a.row_pwmax);
+    const int TY = a.row_ty;                 // image rows per tile
+    const RowSmem L = row_smem(a.row_kmax, a.row_pwmax, TY);
     unsigned char *sT = sm + L.t_off;
     unsigned char *sDm = sm + L.dm_off;
     float *patch = reinterpret_cast<float *>(sm + L.patch_off);
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const TcBankArgs a, co
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_s;
-    const uint32_t idesc = idesc_f16(0, kRowTileX, 2 * kRowTileY);
+    const uint32_t idesc = idesc_f16(0, kRowTileX, 2 * TY);
     int e = 0;
     {
         const float mx = __int_as_float(*a.absmax);
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const TcBankArgs a, co
                 cur_s = s;
             }
             // patch rows y0 .. y0 + 63, columns x0 - R .. x0 + 127 + R (zero outside the image)
-            for (int r = pwarp; r < kRowTileY; r += NP / 32) {
+            for (int r = pwarp; r < TY; r += NP / 32) {
                 const int y = y0 + r;
                 const bool yin = y < a.H;
                 const float *src = a.img + (int64_t)(yin ? y : 0) * a.pitch;
@@ -190,8 +191,8 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const TcBankArgs a, co
                 // patch rows, broadcast phases, conflict-free swizzled stores).
                 const int kch = K / 8;
 #pragma unroll 2
-                for (int ci = ptid; ci < 2 * kRowTileY * kch; ci += NP) {
-                    const int n = ci & 127, kc = ci >> 7;
+                for (int ci = ptid; ci < 2 * TY * kch; ci += NP) {
+                    const int n = ci % (2 * TY), kc = ci / (2 * TY);
                     const int r = n >> 1, sg = n & 1;
                     const int k0 = 8 * kc;
                     uint32_t wv[4];
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const TcBankArgs a, co
                             wv[qq] = (uint32_t)h16(vv[0]) | ((uint32_t)h16(vv[1]) << 16);
                         }
                     }
-                    *reinterpret_cast<uint4 *>(sDm + sw128_offset(2 * kRowTileY, n, k0)) =
+                    *reinterpret_cast<uint4 *>(sDm + sw128_offset(2 * TY, n, k0)) =
                         make_uint4(wv[0], wv[1], wv[2], wv[3]);
                 }
                 fence_proxy_async_smem();
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const TcBankArgs a, co
 #pragma unroll
                             for (int kk = 0; kk < 4; ++kk)
                                 tc_mma_f16(tmem + 128u * b, smem_desc_sw128(a0 + kb * kRowTileX * 128) + 2 * kk,
-                                           smem_desc_sw128(b0 + kb * (2 * kRowTileY) * 128) + 2 * kk, idesc,
+                                           smem_desc_sw128(b0 + kb * (2 * TY) * 128) + 2 * kk, idesc,
                                            (kb | kk) != 0);
                         tc_commit(&tmem_full[b]);
                         tc_commit(dm_empty);
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const TcBankArgs a, co
                 uint16_t *dst0 = a.sig + u.sig_off + (int64_t)(xin ? gx : 0) * a.Hp + a.Lpad + y0;
                 const int64_t sstride = (int64_t)a.W * a.Hp;   // between signals of the unit
 #pragma unroll 1
-                for (int c0 = 0; c0 < 2 * kRowTileY; c0 += 16) {
+                for (int c0 = 0; c0 < 2 * TY; c0 += 16) {
                     float v[16];
                     tmem_ld16(tmem + lane_base + 128u * b + c0, v);
                     const int r0 = c0 >> 1;
@@ -585,12 +586,12 @@ TcGeometry gabor_tc_geometry(int R)
     g.Krow = round_up(kRowTileX + 2 * R, 64);
     g.Kcol = round_up(kColTileY + g.R8 + R, 64);
     g.PW = round_up(kRowTileX + 2 * R, 4);
-    g.smem_rows = 1024 + row_smem(g.Krow, g.PW).total;
+    g.smem_rows = 1024 + row_smem(g.Krow, g.PW, kRowTileYMax / 2).total;
     g.smem_cols = 1024 + col_smem(g.Kcol).total;
     return g;
 }
 
-size_t gabor_tc_smem_rows(int Kmax, int PWmax) { return 1024 + row_smem(Kmax, PWmax).total; }
+size_t gabor_tc_smem_rows(int Kmax, int PWmax, int TY) { return 1024 + row_smem(Kmax, PWmax, TY).total; }
 size_t gabor_tc_smem_cols(int Kmax) { return 1024 + col_smem(Kmax).total; }
 
 bool gabor_tc_supported(int R)
@@ -600,7 +601,11 @@ bool gabor_tc_supported(int R)
 }
 
 int gabor_tc_row_tile_x() { return kRowTileX; }
-int gabor_tc_row_tile_y() { return kRowTileY; }
+int gabor_tc_row_tile_y(int Rmax)
+{
+    const TcGeometry g = gabor_tc_geometry(Rmax);
+    return (1024 + row_smem(g.Krow, g.PW, kRowTileYMax).total <= (size_t)kSmemLimit) ? kRowTileYMax : kRowTileYMax / 2;
+}
 int gabor_tc_col_tile_y() { return kColTileY; }
 
 cudaError_t build_gabor_tc_b(uint16_t *Brow, uint16_t *Bcol, int R, double sigma, int bf16, float *unscale,
@@ -630,7 +635,7 @@ cudaError_t gabor_tc_prepare()
 cudaError_t launch_gabor_tc(const TcBankArgs &a, const int4 *row_items, int n_row_items, const int *funits,
                             const int *funit0, const int4 *col_items, int n_col_items, int sm_count, cudaStream_t st)
 {
-    const size_t smem_r = gabor_tc_smem_rows(a.row_kmax, a.row_pwmax);
+    const size_t smem_r = gabor_tc_smem_rows(a.row_kmax, a.row_pwmax, a.row_ty);
     const size_t smem_c = gabor_tc_smem_cols(a.col_kmax);
     cudaError_t e0 = cudaMemsetAsync(a.absmax, 0, sizeof(int), st);
     if (e0 != cudaSuccess) return e0;

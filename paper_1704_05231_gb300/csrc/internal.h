@@ -17,6 +17,7 @@ constexpr int kThreads = 256;      // threads per CTA of the FP32 kernels
 constexpr int kMaxRadius = 160;    // largest Gaussian radius of the fused FP32 bank kernel
 constexpr int kMaxSdftM = 64;      // largest SDFT window side
 constexpr int kSmemLimit = 227 * 1024;
+constexpr int kStaticSmemReserve = 256;   // static shared memory kept free next to the dynamic part
 
 // Device view of one horizontal pass ("row unit") of the bank: the pass of orientation
 // theta_a at frequency omega_s, and the orientation pi - theta_a that reuses it (Eq. 13-16).
@@ -60,6 +61,8 @@ struct BankArgs {
     const FreqDev *freqs;
     const UnitDev *units;
     const WorkItem *items;
+    int *counter;             // work-queue head (zeroed before each launch)
+    int nitems;
 };
 
 // ---- tensor-core bank (gabor_tc.cu) ----
@@ -86,7 +89,7 @@ struct TcBankArgs {
     const TcFreqDev *freqs;
     const TcUnitDev *units;
     int *status;
-    int row_kmax, row_pwmax, col_kmax, pad2_;
+    int row_kmax, row_pwmax, col_kmax, row_ty;
     int *absmax;           // device word: max |f| of the image as float bits (k_absmax)
 };
 struct TcGeometry {
@@ -134,7 +137,7 @@ cudaError_t launch_build_twiddles(int M, float2 *tw, cudaStream_t st);
 // Tile geometry of the FP32 bank kernel for radius R (tile_rows = 0: automatic).
 FreqDev gabor_fp32_geometry(int R, int tile_rows);
 size_t gabor_fp32_smem_bytes(const FreqDev &f);
-cudaError_t launch_gabor_fp32(const BankArgs &a, int nitems, size_t smem, cudaStream_t st);
+cudaError_t launch_gabor_fp32(const BankArgs &a, int nitems, size_t smem, int sm_count, cudaStream_t st);
 cudaError_t gabor_fp32_prepare();
 cudaError_t launch_sdft_fp32(SdftArgs a, int sm_count, cudaStream_t st);
 cudaError_t sdft_fp32_prepare();
@@ -147,7 +150,7 @@ cudaError_t gabor_tc_prepare();
 cudaError_t launch_gabor_tc(const TcBankArgs &a, const int4 *row_items, int n_row_items, const int *funits,
                             const int *funit0, const int4 *col_items, int n_col_items, int sm_count, cudaStream_t st);
 int gabor_tc_row_tile_x();
-int gabor_tc_row_tile_y();
+int gabor_tc_row_tile_y(int Rmax);
 int gabor_tc_col_tile_y();
 // Sets the message returned by gabor_bank_last_error() on the calling host thread.
 void set_last_error(const char *msg);
@@ -175,6 +178,9 @@ struct gabor_bank {
     int reuse = 1;
     int tile_rows = 0;
     int segments = 0;
+    std::vector<int> ftile_rows, fsegments;   // per-frequency overrides (0 = global / automatic)
+    int *d_counter = nullptr;                 // work-queue head of the FP32 bank kernel
+    std::vector<gb::ImageDev> last_imgs;      // batch descriptors last uploaded
     // device tables
     double *d_unit_w = nullptr;  // [nunits][2] (omega cos / pi, omega sin / pi)
     double *d_sigma = nullptr;
@@ -214,6 +220,7 @@ struct gabor_bank {
     int *d_tcfunits = nullptr;      // [n_freq] units per frequency, then [n_freq] first unit
     int tc_row_kmax = 0, tc_row_pwmax = 0, tc_col_kmax = 0;
     int *d_tcabsmax = nullptr;
+    int tc_row_ty = 64;
     int tc_H = 0, tc_W = 0, tc_Lpad = 0;
     int64_t tc_Hp = 0;
     bool tc_ready = false;

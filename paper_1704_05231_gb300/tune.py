@@ -1,0 +1,115 @@
+"""Autotuner for the tile geometry of the FP32 filter-bank kernel.
+
+For every frequency of a plan it picks the rows per streamed chunk (TH) and the number of row
+segments per column strip by timing the whole bank on the caller's images (coordinate
+descent over the frequencies, CUDA events, L2 flushed between timings).  The choice trades
+the 2R-row vertical halo recomputed per segment against load balance across the SMs; it does
+not change any result (every output's arithmetic is the same).  Choices are cached in a JSON
+file keyed by GPU name, image-size classes, radii, orientation count and precision.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import statistics
+
+TILE_ROWS = (0, 32, 64)
+SEGMENTS = (0, 1, 2, 4, 8)
+
+
+def default_cache_path():
+    return os.environ.get("GABORBANK_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "gaborbank_tune.json"))
+
+
+def size_class(n):
+    return 1 << max(0, int(n - 1).bit_length())
+
+
+def cache_key(gbk, shapes, gpu_name):
+    radii = [int(math.ceil(3.0 * s - 1e-9)) for s in gbk.sigmas]
+    classes = sorted({(size_class(h), size_class(w)) for h, w in shapes})
+    return f"{gpu_name}|{classes}|R={radii}|N={len(gbk.thetas)}|{gbk.precision}"
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save(path, data):
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def autotune(gbk, imgs, cache_path=None, steps=3, use_cache=True):
+    """Choose (tile_rows, segments) per frequency for `imgs` (a CUDA tensor or a list of them).
+
+    Applies the choice to `gbk` and returns {"key", "tiling": [[tile_rows, segments], ...],
+    "ms"}.  Only the FP32 path has a tunable geometry; other precisions return the defaults.
+    """
+    import torch
+    batch = isinstance(imgs, (list, tuple))
+    ims = list(imgs) if batch else [imgs]
+    shapes = [tuple(t.shape) for t in ims]
+    nf = len(gbk.omegas)
+    if gbk.precision != "fp32" or nf == 0:
+        return {"key": None, "tiling": [[0, 0]] * nf, "ms": None}
+    path = cache_path or default_cache_path()
+    key = cache_key(gbk, shapes, torch.cuda.get_device_name())
+    cache = _load(path) if use_cache else {}
+    if key in cache:
+        for s, (tr, sg) in enumerate(cache[key]["tiling"]):
+            gbk.set_tiling(s, tr, sg)
+        return dict(cache[key], key=key, cached=True)
+
+    outs = [torch.empty(gbk.out_shape(*sh), dtype=torch.complex64, device=t.device) for t, sh in zip(ims, shapes)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=ims[0].device)
+
+    def run():
+        if batch:
+            gbk.filter_batch(ims, outs)
+        else:
+            gbk.filter(ims[0], outs[0])
+
+    def timed():
+        run()                       # rebuilds tables / work lists after a tiling change
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            run()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    tiling = [[0, 0] for _ in range(nf)]
+    best_ms = timed()
+    for s in sorted(range(nf), key=lambda i: -gbk.sigmas[i]):
+        for tr in TILE_ROWS:
+            for sg in SEGMENTS:
+                if [tr, sg] == tiling[s]:
+                    continue
+                gbk.set_tiling(s, tr, sg)
+                ms = timed()
+                if ms < best_ms:
+                    best_ms = ms
+                    tiling[s] = [tr, sg]
+        gbk.set_tiling(s, *tiling[s])
+    entry = {"tiling": tiling, "ms": best_ms}
+    if use_cache:
+        cache = _load(path)
+        cache[key] = entry
+        _save(path, cache)
+    return dict(entry, key=key, cached=False)
