@@ -267,6 +267,89 @@ def sdft_leg(torch, steps, warmup, flush, stream):
     return res
 
 
+def ablation_leg(torch, d_img, thetas, omegas, sigmas, steps, warmup, flush, stream):
+    """Orientation reuse on and off (J_{pi-theta} = J*_theta, Eq. 13-16): the GPU analogue of
+    the paper's reuse speed-up, FP32 and FP16-TC, same image and bank as the main line."""
+    from paper_1704_05231_gb300 import GaborBank
+    res = {}
+    for prec in ("fp32", "fp16_tc"):
+        gbk = GaborBank(thetas, omegas, sigmas, precision=prec, max_shape=(H, W))
+        out = torch.empty(gbk.out_shape(H, W), dtype=torch.complex64, device="cuda")
+        ent = {}
+        for reuse in (1, 0):
+            gbk.set_option("reuse", reuse)
+            ms = statistics.mean(time_device(torch, lambda: gbk.filter(d_img, out), steps, warmup, flush, stream))
+            ent["reuse" if reuse else "no_reuse"] = {"ms_per_step": ms, "value": len(thetas) * len(omegas) * H * W / (ms * 1e-3)}
+        ent["speedup_from_reuse"] = ent["no_reuse"]["ms_per_step"] / ent["reuse"]["ms_per_step"]
+        gbk.close()
+        res[prec] = ent
+    return res
+
+
+def batch_leg(torch, steps, warmup, flush, stream):
+    """64 uneven 1/f-noise images (sides uniform in [128, 2048], seed 1), 8 orientations x 5
+    octave frequencies (sigma = pi/omega, R up to 96): one persistent launch per step for FP32
+    (tile geometry from the autotuner), replayed from a captured CUDA graph; the FP16-TC bank
+    runs one row and one column pass per image in the same graph."""
+    from paper_1704_05231_gb300 import GaborBank, synth
+    from paper_1704_05231_gb300.bank import capture_graph
+    from paper_1704_05231_gb300.tune import autotune
+    shapes = synth.batch_shapes(1, 64, 128, 2048)
+    imgs = [synth.pink_noise_device(1000 + i, h, w) for i, (h, w) in enumerate(shapes)]
+    th, om, sg = synth.octave_bank(8, 5)
+    n_out = sum(len(th) * len(om) * h * w for h, w in shapes)
+    flops = sum(algorithmic_flops(th, om, sg, h, w) for h, w in shapes)
+    res = {"workload": "64 images, sides U[128,2048] (seed 1), 1/f noise made on the device; 8 orientations "
+                       "k*pi/8 x 5 frequencies pi/2..pi/32, sigma=pi/omega",
+           "outputs_per_step": n_out, "pixels": sum(h * w for h, w in shapes)}
+    peak_hbm, kind = hbm_peak_gbs()
+    peak_alu, _, _ = fp32_peak_tflops(torch)
+    for prec in ("fp32", "fp16_tc"):
+        gbk = GaborBank(th, om, sg, precision=prec, max_shape=(2048, 2048))
+        outs = [torch.empty(gbk.out_shape(h, w), dtype=torch.complex64, device="cuda") for h, w in shapes]
+        ent = {}
+        if prec == "fp32":
+            t = autotune(gbk, imgs, steps=1, tile_rows=(0,), segments=(0, 1, 2, 4))
+            ent["tiling"] = t["tiling"]
+        graph = capture_graph(lambda: gbk.filter_batch(imgs, outs))
+        ms = statistics.mean(time_device(torch, graph.replay, steps, warmup, flush, stream))
+        gbk.device_status()
+        ent.update({"value": n_out / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                    "launches_per_step": 1 if prec == "fp32" else 3 * len(shapes)})
+        if prec == "fp32":
+            a = flops / (ms * 1e-3) / 1e12
+            ent["roofline"] = {"bound": "alu", "achieved": a, "peak": peak_alu, "unit": "TFLOP/s", "frac": a / peak_alu}
+        else:
+            b = n_out * 8 + res["pixels"] * 4
+            a = b / (ms * 1e-3) / 1e9
+            ent["roofline"] = {"bound": "hbm", "achieved": a, "peak": peak_hbm, "unit": "GB/s", "frac": a / peak_hbm,
+                               "peak_kind": kind}
+        res[prec] = ent
+        del graph, outs
+        gbk.close()
+        torch.cuda.empty_cache()
+    return res
+
+
+def serve_leg(args):
+    """Served stream: Poisson arrivals at 0.7x the closed-loop saturation rate, 256-4096 px
+    sides, 90% banks / 10% 16x16 SDFT, 96 GiB budget, 4 slots (continuous batching)."""
+    from paper_1704_05231_gb300 import serve
+    pool = serve.ImagePool(n=4, side=4096, seed=3)
+    res = {"workload": f"{args.serve_warm} warm-up + {args.serve_n} measured requests (seed 2), sides log-U[256,4096], "
+                       "banks N~U{4..8} x S~U{2..5} octaves sigma=pi/omega, 10% SDFT M=16 sigma=4; images are "
+                       "crops of device-resident 4096^2 1/f noise; outputs stay in device memory",
+           "budget_gib": 96, "slots": 4}
+    for prec in ("fp32", "fp16_tc"):
+        r = serve.measure(prec, n_warm=args.serve_warm, n_meas=args.serve_n, rate_fracs=(0.7,), pool=pool,
+                          n_sat=min(300, args.serve_n), log=lambda m: print(m, file=sys.stderr, flush=True))
+        s = r["rates"][0.7]
+        res[prec] = {"saturation_req_s": r["saturation_req_s"], "rate_req_s": s["rate_req_s"],
+                     "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"], "outputs_per_s": s["outputs_per_s"],
+                     "served": s["served"], "rejected": s["rejected"]}
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -290,6 +373,10 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
+    tiling = None
+    if not args.no_tune:
+        from paper_1704_05231_gb300.tune import autotune
+        tiling = autotune(gbk, d_img, steps=3)["tiling"]
     for _ in range(max(3, args.warmup)):
         gbk.filter(d_img, out)
     torch.cuda.synchronize()
@@ -339,22 +426,27 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config({"path": "FP32 CUDA-core fused bank kernel", "parallelism": f"replicas x{world}"}),
+            "config": workload_config({"path": "FP32 CUDA-core fused bank kernel", "parallelism": f"replicas x{world}",
+                                       "tiling": tiling}),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_gabor_fp32 (4 launches per step, one per frequency)",
+                         "kernel": "k_gabor_fp32 (one persistent launch per step)",
                          "peak_note": f"derived: {sms} SMs x 128 FP32 lanes x 2 FLOP x {mhz:.0f} MHz",
                          "algorithmic": "(3N+1)(2R+1) FMA per pixel per frequency"},
             "e2e": None if args.no_e2e else {
                 "value": n_out / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H * W * 4,
                 "d2h_bytes_per_step": n_out * 8, "path": "gabor_bank_filter_host, pinned buffers"},
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": args.steps,
             "clocks": clocks,
             "wall_s": wall}
     if not args.no_extra:
         line["tc"] = bank_tc_leg(torch, d_img, thetas, omegas, sigmas, out, n_out, args.steps, args.warmup, flush,
                                  stream)
         line["sdft"] = sdft_leg(torch, args.steps, args.warmup, flush, stream)
+        line["ablation"] = ablation_leg(torch, d_img, thetas, omegas, sigmas, args.steps, args.warmup, flush, stream)
+        line["batch"] = batch_leg(torch, min(args.steps, 5), 3, flush, stream)
+    if not args.no_serve and world == 1:
+        line["serve"] = serve_leg(args)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(img, thetas, omegas, sigmas, args.cpu_seconds)
     if rank == 0:
@@ -374,6 +466,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--no-extra", action="store_true", help="skip the SDFT leg (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-tune", action="store_true", help="default tile geometry instead of the autotuner's")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-stream leg")
+    ap.add_argument("--serve-n", type=int, default=2000, help="measured requests of the served stream")
+    ap.add_argument("--serve-warm", type=int, default=200)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -84,10 +84,15 @@ gb_status gabor_bank_destroy(gabor_bank_t h);
  *
  * d_img  device FP32 image, H x W, row stride `pitch` elements (pitch >= W).
  * d_out  device complex64 buffer of n_freq * n_theta * H * W elements (8 bytes each):
- *        out[s][k][y][x] = F_{omega_s, theta_k, sigma_s}(x, y).  16-byte aligned.
+ *        out[s][k][y][x] = F_{omega_s, theta_k, sigma_s}(x, y).  8-byte aligned.
  * stream cudaStream_t or NULL.
+ * A call needs no per-image-shape device data: after the handle's first call (which builds
+ * its tables), calls on new image shapes up to max_H x max_W allocate nothing, except that a
+ * GB_FP16_TC handle without a workspace (gabor_bank_set_workspace) grows its own
+ * intermediate buffer when an image needs more than it holds.
  * Asynchronous.  Errors: GB_ERR_INVALID_ARG (NULL, H/W <= 0, pitch < W, misaligned),
- * GB_ERR_UNSUPPORTED (radius above the library limit of 256 px), GB_ERR_CUDA.
+ * GB_ERR_UNSUPPORTED (BF16 bank, or a radius above 120 px on tensor cores), GB_ERR_BUDGET
+ * (attached workspace too small), GB_ERR_CUDA.  gabor_bank_create refuses radii above 160 px.
  */
 gb_status gabor_bank_filter(gabor_bank_t h, const float *d_img, int H, int W, int64_t pitch,
                             void *d_out, void *stream);
@@ -115,7 +120,7 @@ gb_status gabor_bank_filter_host(gabor_bank_t h, const float *h_img, int H, int 
  * half_spectrum  0: d_out holds My * Mx planes, out[v][u][y][x].
  *                1: only v = 0 .. My/2 are written, out[v][u][y][x] with My/2 + 1 planes
  *                   of v; the rest follow from F_{u,v} = F*_{(Mx-u)%Mx,(My-v)%My}.
- * d_out          device complex64, 16-byte aligned.
+ * d_out          device complex64, 8-byte aligned.
  * The handle's precision selects the FP32 separable path (Algorithm 2) or the tensor-core
  * windowed-DFT contraction.  Asynchronous.  Errors as gabor_bank_filter.
  */
@@ -168,6 +173,17 @@ gb_status gabor_bank_set_tiling(gabor_bank_t h, int s, int tile_rows, int segmen
 gb_status gabor_bank_device_status(gabor_bank_t h, void *stream);
 
 /*
+ * gabor_bank_selftest_wait - failure-detection self-test of the bounded device waits.  Enqueues
+ * a one-warp kernel whose thread 0 waits on a shared-memory mbarrier with the same bounded
+ * wait the tensor-core kernels use.  signal = 1: the barrier is signalled first and the wait
+ * succeeds.  signal = 0: nothing signals it; the wait gives up after limit_ms (0 < limit_ms
+ * <= 2000), writes code 90 to the handle's device status word and the kernel returns, leaving
+ * the CUDA context usable.  gabor_bank_device_status then reports GB_ERR_TIMEOUT.  The paper
+ * has no counterpart; this checks the library's own error path.  Asynchronous.
+ */
+gb_status gabor_bank_selftest_wait(gabor_bank_t h, int signal, double limit_ms, void *stream);
+
+/*
  * gabor_sdft_noalloc - the FP32 localized sliding DFT of gabor_bank_sdft (same arguments and
  * output layout, FP32 CUDA-core path) for callers that cannot allocate device memory: code
  * inside a custom allocator or memory pool that forbids cudaMalloc, or an application whose
@@ -184,6 +200,53 @@ gb_status gabor_bank_device_status(gabor_bank_t h, void *stream);
  */
 gb_status gabor_sdft_noalloc(const float *d_img, int H, int W, int64_t pitch, double sigma,
                              int My, int Mx, int half_spectrum, void *d_out, void *stream);
+
+/*
+ * gabor_bank_workspace_bytes - device bytes of intermediate a GB_FP16_TC / GB_BF16_TC handle
+ * needs to filter an H x W image: the FP16 column signals of Eq. 10 between the row and the
+ * column pass (4 signals per paired orientation, 2 per unpaired one, each image column
+ * padded by zero rows above and below).  0 for FP32 handles (their intermediates stay on
+ * chip) and for invalid arguments.  Host-only; no device work.
+ */
+int64_t gabor_bank_workspace_bytes(gabor_bank_t h, int H, int W);
+
+/*
+ * gabor_bank_set_workspace - make the handle use the caller's device buffer d_ws (16-byte
+ * aligned, `bytes` long) as its tensor-core intermediate from the next call on, instead of a
+ * buffer of its own; d_ws = NULL, bytes = 0 returns to the handle's own buffer.  The caller
+ * keeps ownership and must keep the buffer alive and unused by other work while calls that
+ * use it run.  Several handles may share one workspace when their calls are ordered (one
+ * stream).  A filter call whose image needs more than `bytes` fails with GB_ERR_BUDGET.
+ * Host-only; no device work.  GB_ERR_INVALID_ARG on a NULL handle, misalignment or a
+ * non-positive size.
+ */
+gb_status gabor_bank_set_workspace(gabor_bank_t h, void *d_ws, int64_t bytes);
+
+/*
+ * Device-memory arena: one allocation made at creation, handed out in 256-byte aligned
+ * ranges (first fit by address, neighbours merged on free).  Used to admit work by a fixed
+ * HBM budget: an allocation that does not fit fails at once with GB_ERR_BUDGET instead of
+ * growing device memory.  Book-keeping is host-only and thread-safe; the arena never
+ * synchronises, so a range may be freed only when the device work that uses it has
+ * finished (or when later users are ordered after it on one stream).
+ */
+typedef struct gabor_arena *gabor_arena_t;
+
+/* gabor_arena_create - cudaMalloc `bytes` (> 0) on the current device.
+   GB_ERR_OUT_OF_MEMORY if the device cannot provide it. */
+gb_status gabor_arena_create(gabor_arena_t *out, int64_t bytes);
+/* gabor_arena_wrap - an arena over caller-owned device memory d_base (256-byte aligned,
+   `bytes` long); gabor_arena_destroy then leaves the memory to the caller. */
+gb_status gabor_arena_wrap(gabor_arena_t *out, void *d_base, int64_t bytes);
+/* gabor_arena_alloc - *d_ptr = a free range of `bytes` (> 0), or GB_ERR_BUDGET (and NULL). */
+gb_status gabor_arena_alloc(gabor_arena_t a, int64_t bytes, void **d_ptr);
+/* gabor_arena_free - return a range from gabor_arena_alloc; GB_ERR_INVALID_ARG otherwise. */
+gb_status gabor_arena_free(gabor_arena_t a, void *d_ptr);
+/* gabor_arena_stats - capacity, bytes in use and the largest free range (any may be NULL). */
+gb_status gabor_arena_stats(gabor_arena_t a, int64_t *capacity, int64_t *in_use, int64_t *largest_free);
+/* gabor_arena_destroy - free the arena (and its device allocation if gabor_arena_create made
+   it); outstanding ranges become invalid.  NULL is allowed. */
+gb_status gabor_arena_destroy(gabor_arena_t a);
 
 /* gabor_bank_output_elems - complex elements gabor_bank_filter writes for an H x W image. */
 int64_t gabor_bank_output_elems(gabor_bank_t h, int H, int W);

@@ -6,11 +6,11 @@ cheap: the library is loaded on first use of ``GaborBank``.
 """
 from __future__ import annotations
 
-__all__ = ["GaborBank", "GBError", "load_library"]
+__all__ = ["Arena", "GaborBank", "GBError", "load_library"]
 
 
 def __getattr__(name):
-    if name in ("GaborBank", "GBError", "load_library"):
+    if name in ("Arena", "GaborBank", "GBError", "load_library"):
         from . import bank
         return getattr(bank, name)
     raise AttributeError(name)

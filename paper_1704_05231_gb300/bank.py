@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libgaborbank.so")
 GB_OK = 0
 STATUS = {0: "GB_OK", -1: "GB_ERR_INVALID_ARG", -2: "GB_ERR_OUT_OF_MEMORY", -3: "GB_ERR_CUDA",
           -4: "GB_ERR_UNSUPPORTED", -5: "GB_ERR_BUDGET", -6: "GB_ERR_TIMEOUT"}
+STATUS_CODE = {v: k for k, v in STATUS.items()}
 PRECISION = {"fp32": 0, "fp16_tc": 1, "bf16_tc": 2}
 OPTION = {"reuse": 1, "tile_rows": 2, "segments": 3}
 
@@ -42,6 +43,16 @@ SIGNATURES = {
     "gabor_bank_last_error": (ctypes.c_char_p, []),
     "gabor_bank_version": (ctypes.c_char_p, []),
     "gabor_sdft_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_i64, _c_dbl, _c_int, _c_int, _c_int, _vp, _vp]),
+    "gabor_bank_selftest_wait": (_c_int, [_vp, _c_int, _c_dbl, _vp]),
+    "gabor_bank_workspace_bytes": (_c_i64, [_vp, _c_int, _c_int]),
+    "gabor_bank_set_workspace": (_c_int, [_vp, _vp, _c_i64]),
+    "gabor_arena_create": (_c_int, [ctypes.POINTER(_vp), _c_i64]),
+    "gabor_arena_wrap": (_c_int, [ctypes.POINTER(_vp), _vp, _c_i64]),
+    "gabor_arena_alloc": (_c_int, [_vp, _c_i64, ctypes.POINTER(_vp)]),
+    "gabor_arena_free": (_c_int, [_vp, _vp]),
+    "gabor_arena_stats": (_c_int, [_vp, ctypes.POINTER(_c_i64), ctypes.POINTER(_c_i64),
+                                   ctypes.POINTER(_c_i64)]),
+    "gabor_arena_destroy": (_c_int, [_vp]),
 }
 
 _lock = threading.Lock()
@@ -145,6 +156,18 @@ class GaborBank:
     def device_status(self, stream=None):
         _check(self._lib.gabor_bank_device_status(self._h, _stream_handle(stream)))
 
+    def selftest_wait(self, signal, limit_ms=5.0, stream=None):
+        """Run the bounded-wait self-test kernel (see gabor_bank_selftest_wait)."""
+        _check(self._lib.gabor_bank_selftest_wait(self._h, int(signal), float(limit_ms), _stream_handle(stream)))
+
+    def workspace_bytes(self, H, W):
+        """Device bytes of tensor-core intermediate an H x W image needs (0 for FP32)."""
+        return int(self._lib.gabor_bank_workspace_bytes(self._h, int(H), int(W)))
+
+    def set_workspace(self, ptr, nbytes):
+        """Use caller-owned device memory (raw pointer) as the intermediate; (0, 0) resets."""
+        _check(self._lib.gabor_bank_set_workspace(self._h, ctypes.c_void_p(ptr or None), int(nbytes)))
+
     # -- shapes
     def out_shape(self, H, W):
         return (len(self.omegas), len(self.thetas), H, W)
@@ -218,6 +241,62 @@ class GaborBank:
                                          1 if half_spectrum else 0, ctypes.c_void_p(out.data_ptr()),
                                          _stream_handle(stream)))
         return out
+
+
+class Arena:
+    """Fixed-budget device memory (gabor_arena_*) over one torch-owned buffer.
+
+    alloc(nbytes) returns a byte offset into `buffer` or None when no free range fits (the
+    budget is exhausted); view(off, shape, dtype) is a tensor over that range.
+    """
+
+    def __init__(self, nbytes, device=None):
+        import torch
+        lib = load_library()
+        self.buffer = torch.empty(int(nbytes), dtype=torch.uint8, device=device or "cuda")
+        h = ctypes.c_void_p()
+        _check(lib.gabor_arena_wrap(ctypes.byref(h), ctypes.c_void_p(self.buffer.data_ptr()), int(nbytes)))
+        self._h = h
+        self._lib = lib
+        self.base = self.buffer.data_ptr()
+
+    def alloc(self, nbytes):
+        p = ctypes.c_void_p()
+        rc = self._lib.gabor_arena_alloc(self._h, int(nbytes), ctypes.byref(p))
+        if rc == STATUS_CODE["GB_ERR_BUDGET"]:
+            return None
+        _check(rc)
+        return p.value - self.base
+
+    def free(self, off):
+        _check(self._lib.gabor_arena_free(self._h, ctypes.c_void_p(self.base + off)))
+
+    def stats(self):
+        c, u, f = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(self._lib.gabor_arena_stats(self._h, ctypes.byref(c), ctypes.byref(u), ctypes.byref(f)))
+        return {"capacity": c.value, "in_use": u.value, "largest_free": f.value}
+
+    def ptr(self, off):
+        return self.base + off
+
+    def view(self, off, shape, dtype):
+        import torch
+        n = 1
+        for d in shape:
+            n *= int(d)
+        nbytes = n * torch.empty((), dtype=dtype).element_size()
+        return self.buffer[off:off + nbytes].view(dtype).view(*shape)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gabor_arena_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def capture_graph(fn, warmup=1):

@@ -75,7 +75,7 @@ void dfree(T *&p)
 int radius_of(double sigma, double rf) { return (int)std::ceil(rf * sigma - 1e-9); }
 
 // Pairs theta with pi - theta (Algorithm 1: J_{pi - theta} = J*_theta) and lays out the
-// units of every frequency.
+// units of every frequency: paired units first, then unpaired ones, each in theta order.
 void build_plan(gabor_bank *h)
 {
     h->freqs.clear();
@@ -92,6 +92,7 @@ void build_plan(gabor_bank *h)
         h->tpad_max = std::max(h->tpad_max, f.Tpad);
         f.u0 = (int)h->units.size();
         std::vector<char> used(K, 0);
+        std::vector<Unit> fu;
         for (int k = 0; k < K; ++k) {
             if (used[k]) continue;
             used[k] = 1;
@@ -110,8 +111,10 @@ void build_plan(gabor_bank *h)
             }
             u.wc = f.omega * std::cos(h->theta[k]);
             u.ws = f.omega * std::sin(h->theta[k]);
-            h->units.push_back(u);
+            fu.push_back(u);
         }
+        std::stable_partition(fu.begin(), fu.end(), [](const Unit &u) { return u.k_b >= 0; });
+        h->units.insert(h->units.end(), fu.begin(), fu.end());
         f.u1 = (int)h->units.size();
         h->freqs.push_back(f);
     }
@@ -133,7 +136,7 @@ void free_tables(gabor_bank *h)
     h->freqdev.clear();
     h->Wcap = h->Hcap = 0;
     h->tables_ready = false;
-    h->tc_H = h->tc_W = 0;   // tensor-core unit descriptors point into the phase tables
+    h->tc_H = h->tc_W = 0;   // the tensor-core intermediate's halo is re-zeroed on next use
 }
 
 // Device tables of the plan: taps per frequency, phase tables per unit (K0, FP64).
@@ -248,6 +251,78 @@ gb_status validate_image(const void *img, int H, int W, int64_t pitch, const voi
     return GB_OK;
 }
 
+// Cost of one work item in FMA lanes: `rows` output rows of a 32-column strip, plus the
+// 2R-row prologue of its horizontal pass.
+double item_cost(const FreqDev &f, bool paired, double rows)
+{
+    return 32.0 * f.Tpad * (rows * (paired ? 4 : 2) + (rows + 2 * f.R) * 2);
+}
+
+// Row segments per column strip of frequency s on an Hh-row image: the per-frequency
+// override, else as many as keep one item under `cap` (and segments at least max(TH, 2R)
+// rows long).
+int segments_of(const gabor_bank *h, int s, int Hh, double cap)
+{
+    const FreqDev &f = h->freqdev[s];
+    const int fseg = (s < (int)h->fsegments.size() && h->fsegments[s] > 0) ? h->fsegments[s] : h->segments;
+    int nseg = fseg > 0 ? fseg : 1;
+    if (fseg <= 0) {
+        const int min_len = std::max(f.TH, 2 * f.R);
+        while (item_cost(f, true, (double)Hh / nseg) > cap && Hh / (nseg + 1) >= min_len) ++nseg;
+    }
+    return std::max(1, std::min(nseg, Hh));
+}
+
+// Item-size cap of a launch over `shapes`: a third of one SM's share of the whole launch.
+double item_cap(const gabor_bank *h, const std::vector<int64_t> &shapes)
+{
+    double total = 0;
+    for (size_t i = 0; i + 1 < shapes.size(); i += 2) {
+        const int nstrips = (int)((shapes[i + 1] + kStripW - 1) / kStripW);
+        for (const Unit &u : h->units) total += nstrips * item_cost(h->freqdev[u.s], u.k_b >= 0, (double)shapes[i]);
+    }
+    return total / std::max(1, h->sm_count) / 3.0;
+}
+
+// Work items of a single-image launch as groups decoded by the kernel (no device list):
+// one group per (frequency, pairing), largest item first.  Returns false when the plan has
+// more groups than the kernel arguments hold.
+bool single_image_groups(const gabor_bank *h, int H, int W, BankArgs &a, int *nitems)
+{
+    const double cap = item_cap(h, {H, W});
+    const int nstrips = (W + kStripW - 1) / kStripW;
+    struct G { double cost; ItemGroup g; int n; };
+    std::vector<G> gs;
+    for (int s = 0; s < (int)h->freqs.size(); ++s) {
+        const int nseg = segments_of(h, s, H, cap);
+        const int seg_len = (H + nseg - 1) / nseg;
+        const int nseg_used = (H + seg_len - 1) / seg_len;
+        int np = 0;
+        for (int u = h->freqs[s].u0; u < h->freqs[s].u1; ++u) np += h->units[u].k_b >= 0;
+        const int nu = h->freqs[s].u1 - h->freqs[s].u0;
+        for (int pass = 0; pass < 2; ++pass) {
+            const int cnt = pass == 0 ? np : nu - np;
+            if (cnt == 0) continue;
+            G g;
+            g.cost = item_cost(h->freqdev[s], pass == 0, seg_len);
+            g.g = ItemGroup{0, h->freqs[s].u0 + (pass == 0 ? 0 : np), nstrips, nseg_used, seg_len};
+            g.n = cnt * nstrips * nseg_used;
+            gs.push_back(g);
+        }
+    }
+    if (gs.size() > (size_t)kMaxGroups) return false;
+    std::stable_sort(gs.begin(), gs.end(), [](const G &p, const G &q) { return p.cost > q.cost; });
+    int first = 0;
+    for (size_t i = 0; i < gs.size(); ++i) {
+        a.groups[i] = gs[i].g;
+        a.groups[i].first = first;
+        first += gs[i].n;
+    }
+    a.ngroups = (int)gs.size();
+    *nitems = first;
+    return true;
+}
+
 // Work list of one launch over `shapes` (H, W pairs): every (image, unit, strip, segment),
 // most expensive first.  Segments are cut so that no item exceeds ~1/3 of an SM's share.
 gb_status get_worklist(gabor_bank *h, const std::vector<int64_t> &shapes, WorkItem **items, int *n)
@@ -261,40 +336,20 @@ gb_status get_worklist(gabor_bank *h, const std::vector<int64_t> &shapes, WorkIt
     const int nimg = (int)shapes.size() / 2;
     struct Cand { double cost; WorkItem w; };
     std::vector<Cand> cands;
-    // cost of one full-height column strip of a unit, in FMA lanes
-    auto strip_cost = [&](int s, bool paired, int Hh, int nseg) {
-        const FreqDev &f = h->freqdev[s];
-        const double seg = (double)Hh / nseg;
-        return 32.0 * f.Tpad * (seg * (paired ? 4 : 2) + (seg + 2 * f.R) * 2);
-    };
-    double total = 0;
-    for (int i = 0; i < nimg; ++i) {
-        const int Hh = (int)shapes[2 * i], Ww = (int)shapes[2 * i + 1];
-        const int nstrips = (Ww + kStripW - 1) / kStripW;
-        for (const Unit &u : h->units) total += nstrips * strip_cost(u.s, u.k_b >= 0, Hh, 1);
-    }
-    const double cap = total / std::max(1, h->sm_count) / 3.0;
+    const double cap = item_cap(h, shapes);
     for (int i = 0; i < nimg; ++i) {
         const int Hh = (int)shapes[2 * i], Ww = (int)shapes[2 * i + 1];
         const int nstrips = (Ww + kStripW - 1) / kStripW;
         for (int s = 0; s < (int)h->freqs.size(); ++s) {
             const FreqDev &f = h->freqdev[s];
-            const int fseg = (s < (int)h->fsegments.size() && h->fsegments[s] > 0) ? h->fsegments[s] : h->segments;
-            int nseg = fseg > 0 ? fseg : 1;
-            if (fseg <= 0) {
-                const int min_len = std::max(f.TH, 2 * f.R);
-                while (strip_cost(s, true, Hh, nseg) > cap && Hh / (nseg + 1) >= min_len) ++nseg;
-            }
-            nseg = std::max(1, std::min(nseg, Hh));
-            const int seg_len = (Hh + nseg - 1) / nseg;
+            const int seg_len = (Hh + segments_of(h, s, Hh, cap) - 1) / segments_of(h, s, Hh, cap);
             for (int ui = h->freqs[s].u0; ui < h->freqs[s].u1; ++ui) {
                 const bool paired = h->units[ui].k_b >= 0;
                 for (int st = 0; st < nstrips; ++st)
                     for (int y0 = 0; y0 < Hh; y0 += seg_len) {
                         Cand c;
                         c.w = WorkItem{i, ui, st, y0, std::min(Hh, y0 + seg_len)};
-                        const double rows = c.w.y1 - c.w.y0;
-                        c.cost = 32.0 * f.Tpad * (rows * (paired ? 4 : 2) + (rows + 2 * f.R) * 2);
+                        c.cost = item_cost(f, paired, c.w.y1 - c.w.y0);
                         cands.push_back(c);
                     }
             }
@@ -312,73 +367,85 @@ gb_status get_worklist(gabor_bank *h, const std::vector<int64_t> &shapes, WorkIt
     return GB_OK;
 }
 
-// Tensor-core bank state: B operands (once per plan) and, per image shape, the intermediate
-// signal buffer, unit descriptors and column work items.
+// Tensor-core bank state: B operands, frequency and unit descriptors (once per plan; unit
+// descriptors again when the phase tables move) and the library-owned intermediate.
 void free_tc(gabor_bank *h)
 {
     dfree(h->d_tcB);
     dfree(h->d_tcfreq);
     dfree(h->d_tcunit);
     dfree(h->d_tcsig);
-    dfree(h->d_tcitems);
-    dfree(h->d_tcrowitems);
-    dfree(h->d_tcfunits);
+    dfree(h->d_tcforder);
     dfree(h->d_tcabsmax);
     h->tcsig_elems = 0;
-    h->tc_nitems = 0;
     h->tc_H = h->tc_W = 0;
     h->tc_ready = false;
 }
 
-gb_status ensure_tc(gabor_bank *h, int H, int W, cudaStream_t st)
+// Lpad (rows of zero halo above the image in the intermediate) of the plan.
+int tc_lpad(const gabor_bank *h)
+{
+    int rmax = 0;
+    for (const Freq &f : h->freqs) rmax = std::max(rmax, f.R);
+    return ((rmax + 64) + 63) / 64 * 64;
+}
+
+// Elements of the intermediate for an H x W image: every column signal of every unit, one
+// column of Hp = round64(H) + 2 Lpad rows per image column.
+int64_t tc_sig_elems(const gabor_bank *h, int H, int W)
+{
+    const int64_t Hp = (int64_t)(H + 63) / 64 * 64 + 2 * tc_lpad(h);
+    int64_t nsig = 0;
+    for (const Unit &u : h->units) nsig += u.k_b >= 0 ? 4 : 2;
+    return nsig * W * Hp;
+}
+
+gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
 {
     const int nf = (int)h->freqs.size(), nu = (int)h->units.size();
     const int bf16 = h->prec == GB_BF16_TC;
-    if (!h->tc_ready) {
-        GB_CU(cudaDeviceSynchronize());
-        size_t total = 0;
-        std::vector<size_t> off_r(nf), off_c(nf);
-        h->tc_row_kmax = h->tc_row_pwmax = h->tc_col_kmax = 0;
-        for (int s = 0; s < nf; ++s) {
-            const TcGeometry g = gabor_tc_geometry(h->freqs[s].R);
-            off_r[s] = total;
-            total += (size_t)gabor_tc_row_tile_x() * g.Krow;
-            off_c[s] = total;
-            total += (size_t)gabor_tc_col_tile_y() * g.Kcol;
-            h->tc_row_kmax = std::max(h->tc_row_kmax, g.Krow);
-            h->tc_row_pwmax = std::max(h->tc_row_pwmax, g.PW);
-            h->tc_col_kmax = std::max(h->tc_col_kmax, g.Kcol);
-        }
-        GB_TRY(dalloc(&h->d_tcB, total));
-        GB_TRY(dalloc(&h->d_tcfreq, (size_t)nf));
-        std::vector<TcFreqDev> fd(nf);
-        for (int s = 0; s < nf; ++s) {
-            const TcGeometry g = gabor_tc_geometry(h->freqs[s].R);
-            float unscale = 1.f;
-            GB_CU(build_gabor_tc_b(h->d_tcB + off_r[s], h->d_tcB + off_c[s], g.R, h->freqs[s].sigma, bf16, &unscale, st));
-            fd[s] = TcFreqDev{h->d_tcB + off_r[s], h->d_tcB + off_c[s], g.R, g.R8, g.Krow, g.Kcol, unscale, unscale};
-        }
-        GB_CU(cudaMemcpy(h->d_tcfreq, fd.data(), nf * sizeof(TcFreqDev), cudaMemcpyHostToDevice));
-        std::vector<int> fu(2 * nf);
-        for (int s = 0; s < nf; ++s) {
-            fu[s] = h->freqs[s].u1 - h->freqs[s].u0;
-            fu[nf + s] = h->freqs[s].u0;
-        }
-        GB_TRY(dalloc(&h->d_tcfunits, (size_t)2 * nf));
-        GB_TRY(dalloc(&h->d_tcabsmax, (size_t)1));
-        GB_CU(cudaMemcpy(h->d_tcfunits, fu.data(), fu.size() * sizeof(int), cudaMemcpyHostToDevice));
-        h->tc_ready = true;
-    }
-    if (h->tc_H == H && h->tc_W == W) return GB_OK;
-    GB_CU(cudaDeviceSynchronize());
+    if (h->tc_ready) return GB_OK;
+    size_t total = 0;
+    std::vector<size_t> off_r(nf), off_c(nf);
+    h->tc_row_kmax = h->tc_row_pwmax = h->tc_col_kmax = 0;
     int rmax = 0;
-    for (const Freq &f : h->freqs) rmax = std::max(rmax, f.R);
-    const int Lpad = ((rmax + 64) + 63) / 64 * 64;
-    const int64_t Hp = (int64_t)(H + 63) / 64 * 64 + 2 * Lpad;
+    for (int s = 0; s < nf; ++s) {
+        const TcGeometry g = gabor_tc_geometry(h->freqs[s].R);
+        off_r[s] = total;
+        total += (size_t)gabor_tc_row_tile_x() * g.Krow;
+        off_c[s] = total;
+        total += (size_t)gabor_tc_col_tile_y() * g.Kcol;
+        h->tc_row_kmax = std::max(h->tc_row_kmax, g.Krow);
+        h->tc_row_pwmax = std::max(h->tc_row_pwmax, g.PW);
+        h->tc_col_kmax = std::max(h->tc_col_kmax, g.Kcol);
+        rmax = std::max(rmax, h->freqs[s].R);
+    }
+    h->tc_row_ty = gabor_tc_row_tile_y(rmax);
+    // every frequency has the same units (the pairing depends on theta only)
+    h->tc_nu_f = nf > 0 ? h->freqs[0].u1 - h->freqs[0].u0 : 0;
+    h->tc_np_f = 0;
+    for (int u = 0; u < h->tc_nu_f; ++u) h->tc_np_f += h->units[u].k_b >= 0;
+    h->tc_nsig = 0;
+    for (const Unit &u : h->units) h->tc_nsig += u.k_b >= 0 ? 4 : 2;
+    GB_TRY(dalloc(&h->d_tcB, total));
+    GB_TRY(dalloc(&h->d_tcfreq, (size_t)nf));
+    GB_TRY(dalloc(&h->d_tcforder, (size_t)nf));
+    GB_TRY(dalloc(&h->d_tcabsmax, (size_t)1));
+    GB_TRY(dalloc(&h->d_tcunit, (size_t)nu));
+    std::vector<TcFreqDev> fd(nf);
+    for (int s = 0; s < nf; ++s) {
+        const TcGeometry g = gabor_tc_geometry(h->freqs[s].R);
+        float unscale = 1.f;
+        GB_CU(build_gabor_tc_b(h->d_tcB + off_r[s], h->d_tcB + off_c[s], g.R, h->freqs[s].sigma, bf16, &unscale, st));
+        fd[s] = TcFreqDev{h->d_tcB + off_r[s], h->d_tcB + off_c[s], g.R, g.R8, g.Krow, g.Kcol, unscale, unscale,
+                          h->freqs[s].u0, 0};
+    }
+    std::vector<int> order(nf);
+    for (int s = 0; s < nf; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return h->freqs[p].R > h->freqs[q].R; });
     std::vector<TcUnitDev> ud(nu);
-    int64_t off = 0;
     const int K = (int)h->theta.size();
-    std::vector<int4> items;
+    int64_t sig = 0;
     for (int i = 0; i < nu; ++i) {
         const Unit &un = h->units[i];
         const bool paired = un.k_b >= 0;
@@ -388,50 +455,13 @@ gb_status ensure_tc(gabor_bank *h, int H, int W, cudaStream_t st)
         ud[i].plane_a = un.s * K + un.k_a;
         ud[i].plane_b = paired ? un.s * K + un.k_b : -1;
         ud[i].pad_ = 0;
-        ud[i].sig_off = off;
-        off += (int64_t)(paired ? 4 : 2) * W * Hp;
-        const int xw = paired ? 32 : 64;
-        for (int y0 = 0; y0 < H; y0 += 64)
-            for (int x0 = 0; x0 < W; x0 += xw) items.push_back(make_int4(i, x0, y0, 0));
+        ud[i].sig_idx = sig;
+        sig += paired ? 4 : 2;
     }
-    // Most expensive frequencies first (largest K).
-    std::stable_sort(items.begin(), items.end(), [&](const int4 &p, const int4 &q) {
-        return h->freqs[h->units[p.x].s].R > h->freqs[h->units[q.x].s].R;
-    });
-    std::vector<int> order(nf);
-    for (int s = 0; s < nf; ++s) order[s] = s;
-    std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return h->freqs[p].R > h->freqs[q].R; });
-    std::vector<int4> ritems;
-    const int tx = gabor_tc_row_tile_x(), ty = gabor_tc_row_tile_y(rmax);
-    h->tc_row_ty = ty;
-    for (int s : order) {
-        if (h->freqs[s].u1 == h->freqs[s].u0) continue;
-        for (int y0 = 0; y0 < H; y0 += ty)
-            for (int x0 = 0; x0 < W; x0 += tx) ritems.push_back(make_int4(s, y0, x0, 0));
-    }
-    if ((size_t)off > h->tcsig_elems) {
-        dfree(h->d_tcsig);
-        h->tcsig_elems = 0;
-        GB_TRY(dalloc(&h->d_tcsig, (size_t)off));
-        h->tcsig_elems = (size_t)off;
-    }
-    // Zero the whole intermediate once per layout: the halo rows are never written.
-    GB_CU(cudaMemsetAsync(h->d_tcsig, 0, (size_t)off * sizeof(uint16_t), st));
-    dfree(h->d_tcunit);
-    dfree(h->d_tcitems);
-    dfree(h->d_tcrowitems);
-    GB_TRY(dalloc(&h->d_tcunit, (size_t)nu));
-    GB_TRY(dalloc(&h->d_tcitems, items.size()));
-    GB_TRY(dalloc(&h->d_tcrowitems, ritems.size()));
-    GB_CU(cudaMemcpy(h->d_tcrowitems, ritems.data(), ritems.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    h->tc_nrowitems = (int)ritems.size();
+    GB_CU(cudaMemcpy(h->d_tcfreq, fd.data(), nf * sizeof(TcFreqDev), cudaMemcpyHostToDevice));
+    GB_CU(cudaMemcpy(h->d_tcforder, order.data(), nf * sizeof(int), cudaMemcpyHostToDevice));
     GB_CU(cudaMemcpy(h->d_tcunit, ud.data(), nu * sizeof(TcUnitDev), cudaMemcpyHostToDevice));
-    GB_CU(cudaMemcpy(h->d_tcitems, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    h->tc_nitems = (int)items.size();
-    h->tc_H = H;
-    h->tc_W = W;
-    h->tc_Hp = Hp;
-    h->tc_Lpad = Lpad;
+    h->tc_ready = true;
     return GB_OK;
 }
 
@@ -445,8 +475,48 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     for (const Freq &f : h->freqs)
         if (!gabor_tc_supported(f.R))
             return fail(GB_ERR_UNSUPPORTED, "tensor-core bank supports radii up to ~120 px");
+    const int nf = (int)h->freqs.size();
+    const int64_t ny64 = (H + 63) / 64, nx32 = (W + 31) / 32, nx64 = (W + 63) / 64;
+    // the unit descriptors point into the phase tables: (re)build them with the tables
+    const bool tables_move = !(h->tables_ready && W <= h->Wcap && H <= h->Hcap);
     GB_TRY(ensure_tables(h, H, W, st));
-    GB_TRY(ensure_tc(h, H, W, st));
+    if (tables_move) free_tc(h);
+    GB_TRY(ensure_tc(h, st));
+    const int ty = h->tc_row_ty;
+    const int64_t row_cnt = (int64_t)((H + ty - 1) / ty) * ((W + 127) / 128);
+    const int64_t col_cnt = ny64 * (h->tc_np_f * nx32 + (h->tc_nu_f - h->tc_np_f) * nx64);
+    if ((int64_t)nf * std::max(row_cnt, col_cnt) > (int64_t)1 << 30)
+        return fail(GB_ERR_UNSUPPORTED, "image too large for the tensor-core bank");
+    const int Lpad = tc_lpad(h);
+    const int64_t Hp = ny64 * 64 + 2 * Lpad;
+    const int64_t need = tc_sig_elems(h, H, W);
+    uint16_t *sig = h->ws_ptr;
+    bool zero_halo = true;   // a caller-owned workspace may hold anything
+    if (!sig) {
+        if ((size_t)need > h->tcsig_elems) {
+            // earlier work of this handle (on `st`) may still read the old buffer
+            GB_CU(cudaStreamSynchronize(st));
+            dfree(h->d_tcsig);
+            h->tcsig_elems = 0;
+            h->tc_H = h->tc_W = 0;
+            GB_TRY(dalloc(&h->d_tcsig, (size_t)need));
+            h->tcsig_elems = (size_t)need;
+        }
+        sig = h->d_tcsig;
+        zero_halo = h->tc_H != H || h->tc_W != W;
+    } else if ((size_t)need * sizeof(uint16_t) > h->ws_bytes) {
+        return fail(GB_ERR_BUDGET, "workspace too small: this image needs " +
+                                       std::to_string(need * (int64_t)sizeof(uint16_t)) + " bytes");
+    }
+    if (zero_halo && need > 0) {
+        // The row pass writes rows [Lpad, Lpad + round_up(H, TY)) of every column signal; the
+        // column pass reads up to Lpad + R8 rows beyond that, which must be zero.
+        const size_t rows = (size_t)h->tc_nsig * W;
+        GB_CU(cudaMemset2DAsync(sig, (size_t)Hp * 2, 0, (size_t)Lpad * 2, rows, st));
+        GB_CU(cudaMemset2DAsync(sig + Lpad + H, (size_t)Hp * 2, 0, (size_t)(Hp - Lpad - H) * 2, rows, st));
+    }
+    h->tc_H = h->ws_ptr ? 0 : H;
+    h->tc_W = h->ws_ptr ? 0 : W;
     TcBankArgs a{};
     a.img = d_img;
     a.pitch = pitch;
@@ -454,9 +524,9 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.W = W;
     a.out = reinterpret_cast<float2 *>(d_out);
     a.plane = (int64_t)H * W;
-    a.sig = h->d_tcsig;
-    a.Hp = h->tc_Hp;
-    a.Lpad = h->tc_Lpad;
+    a.sig = sig;
+    a.Hp = Hp;
+    a.Lpad = Lpad;
     a.freqs = h->d_tcfreq;
     a.units = h->d_tcunit;
     a.status = h->d_status;
@@ -464,10 +534,18 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.row_pwmax = h->tc_row_pwmax;
     a.col_kmax = h->tc_col_kmax;
     a.absmax = h->d_tcabsmax;
-    a.row_ty = h->tc_row_ty;
-    const int nf = (int)h->freqs.size();
-    GB_CU(launch_gabor_tc(a, h->d_tcrowitems, h->tc_nrowitems, h->d_tcfunits, h->d_tcfunits + nf, h->d_tcitems,
-                          h->tc_nitems, h->sm_count, st));
+    a.row_ty = ty;
+    a.forder = h->d_tcforder;
+    a.nf = nf;
+    a.nu_f = h->tc_nu_f;
+    a.np_f = h->tc_np_f;
+    a.row_nx = (W + 127) / 128;
+    a.row_cnt = (int)row_cnt;
+    a.col_ny = (int)ny64;
+    a.col_nx32 = (int)nx32;
+    a.col_nx64 = (int)nx64;
+    a.col_cnt = (int)col_cnt;
+    GB_CU(launch_gabor_tc(a, h->sm_count, st));
     return GB_OK;
 }
 
@@ -476,15 +554,16 @@ gb_status filter_device(gabor_bank *h, const float *d_img, int H, int W, int64_t
 {
     if (h->prec != GB_FP32) return filter_device_tc(h, d_img, H, W, pitch, d_out, st);
     GB_TRY(ensure_tables(h, H, W, st));
-    WorkItem *items = nullptr;
-    int n = 0;
-    GB_TRY(get_worklist(h, {H, W}, &items, &n));
     BankArgs a{};
+    int n = 0;
+    if (!single_image_groups(h, H, W, a, &n)) {
+        a.ngroups = 0;
+        GB_TRY(get_worklist(h, {H, W}, const_cast<WorkItem **>(&a.items), &n));
+    }
     a.img0 = ImageDev{d_img, pitch, reinterpret_cast<float2 *>(d_out), H, W};
     a.imgs = nullptr;
     a.freqs = h->d_freqdev;
     a.units = h->d_unitdev;
-    a.items = items;
     a.counter = h->d_counter;
     GB_CU(launch_gabor_fp32(a, n, h->max_smem, h->sm_count, st));
     return GB_OK;
@@ -826,6 +905,41 @@ gb_status gabor_bank_device_status(gabor_bank_t h, void *stream)
     GB_CU(cudaMemcpy(&v, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     GB_CU(cudaMemset(h->d_status, 0, sizeof(int)));
     if (v != 0) return fail(GB_ERR_TIMEOUT, "a bounded device wait gave up (code " + std::to_string(v) + ")");
+    return GB_OK;
+}
+
+gb_status gabor_bank_selftest_wait(gabor_bank_t h, int signal, double limit_ms, void *stream)
+{
+    if (!h) return fail(GB_ERR_INVALID_ARG, "NULL handle");
+    if (signal != 0 && signal != 1) return fail(GB_ERR_INVALID_ARG, "signal must be 0 or 1");
+    if (!(limit_ms > 0.0 && limit_ms <= 2000.0)) return fail(GB_ERR_INVALID_ARG, "limit_ms must be in (0, 2000]");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(GB_ERR_CUDA, "cannot select the handle's device");
+    GB_TRY(check_sticky());
+    GB_CU(launch_wait_selftest(h->d_status, signal, (unsigned long long)(limit_ms * 1e6),
+                               static_cast<cudaStream_t>(stream)));
+    return GB_OK;
+}
+
+int64_t gabor_bank_workspace_bytes(gabor_bank_t h, int H, int W)
+{
+    if (!h || H <= 0 || W <= 0) return 0;
+    if (h->prec == GB_FP32 || h->units.empty()) return 0;
+    return tc_sig_elems(h, H, W) * (int64_t)sizeof(uint16_t);
+}
+
+gb_status gabor_bank_set_workspace(gabor_bank_t h, void *d_ws, int64_t bytes)
+{
+    if (!h) return fail(GB_ERR_INVALID_ARG, "NULL handle");
+    if (d_ws == nullptr) {
+        if (bytes != 0) return fail(GB_ERR_INVALID_ARG, "NULL workspace with a non-zero size");
+    } else {
+        if (bytes <= 0) return fail(GB_ERR_INVALID_ARG, "workspace size must be positive");
+        if (reinterpret_cast<uintptr_t>(d_ws) % 16) return fail(GB_ERR_INVALID_ARG, "workspace not 16-byte aligned");
+    }
+    h->ws_ptr = static_cast<uint16_t *>(d_ws);
+    h->ws_bytes = d_ws ? (size_t)bytes : 0;
+    h->tc_H = h->tc_W = 0;
     return GB_OK;
 }
 

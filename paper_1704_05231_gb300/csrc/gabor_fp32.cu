@@ -252,9 +252,21 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
     }
 }
 
+// Work item `item` of a single-image launch, decoded from the groups (uniform per CTA).
+__device__ __forceinline__ WorkItem decode_item(const BankArgs &a, int item)
+{
+    int g = 0;
+    while (g + 1 < a.ngroups && item >= a.groups[g + 1].first) ++g;
+    const ItemGroup &G = a.groups[g];
+    const int local = item - G.first;
+    const int seg = local % G.nseg, rest = local / G.nseg;
+    const int y0 = seg * G.seg_len;
+    return WorkItem{0, G.u0 + rest / G.nstrips, rest % G.nstrips, y0, min(a.img0.H, y0 + G.seg_len)};
+}
+
 // Persistent CTAs pull work items (cost-sorted, largest first) from a device counter that the
 // launcher zeroes before the launch.
-__global__ void __launch_bounds__(kThreads) k_gabor_fp32(const BankArgs a)
+__global__ void __launch_bounds__(kThreads) k_gabor_fp32(const __grid_constant__ BankArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int next_item;
@@ -263,7 +275,7 @@ __global__ void __launch_bounds__(kThreads) k_gabor_fp32(const BankArgs a)
         __syncthreads();
         const int item = next_item;
         if (item >= a.nitems) break;
-        gabor_fp32_item(a, a.items[item], smem_raw);
+        gabor_fp32_item(a, a.items ? a.items[item] : decode_item(a, item), smem_raw);
         __syncthreads();   // shared memory is reused by the next item
     }
 }

@@ -80,13 +80,40 @@ __host__ __device__ inline ColSmem col_smem(int K)
 
 }  // namespace
 
+// ------------------------------------------------------------------------- work items
+// Items are decoded from the image shape: per frequency (largest radius first), the row pass
+// has row_cnt tiles (TY rows x 128 columns); the column pass has, per unit, col_ny tiles of
+// 64 rows x 32 columns (paired units, listed first) or x 64 columns (unpaired units).
+struct RowItem {
+    int s, y0, x0;
+};
+struct ColItem {
+    int unit, x0, y0;
+};
+__device__ __forceinline__ RowItem row_item(const TcBankArgs &a, int it)
+{
+    const int g = it / a.row_cnt, local = it - g * a.row_cnt;
+    return RowItem{__ldg(a.forder + g), (local / a.row_nx) * a.row_ty, (local % a.row_nx) * kRowTileX};
+}
+__device__ __forceinline__ ColItem col_item(const TcBankArgs &a, int it)
+{
+    const int g = it / a.col_cnt;
+    int local = it - g * a.col_cnt;
+    const int u0 = a.freqs[__ldg(a.forder + g)].u0;
+    const int paired_items = a.np_f * a.col_ny * a.col_nx32;
+    const bool paired = local < paired_items;
+    if (!paired) local -= paired_items;
+    const int nx = paired ? a.col_nx32 : a.col_nx64;
+    const int per = a.col_ny * nx, q = local / per, r = local - q * per;
+    return ColItem{u0 + (paired ? 0 : a.np_f) + q, (r % nx) * (paired ? 32 : 64), (r / nx) * kColTileY};
+}
+
 // ------------------------------------------------------------------------------ row pass
 // Items: (frequency s, tile y, tile x), sorted by frequency; each item runs every unit of s.
 // The input scale 2^-e (|f| 2^-e < 1, FP16 range) comes from k_absmax for the whole image.
-__global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const TcBankArgs a, const int4 *__restrict__ items,
-                                                          int nitems, const int *__restrict__ funits,
-                                                          const int *__restrict__ funit0)
+__global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const __grid_constant__ TcBankArgs a)
 {
+    const int nitems = a.nf * a.row_cnt;
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -137,8 +164,8 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const TcBankArgs a, co
         int cur_s = -1, job = 0;
         for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
             if (named_barrier_or(1, NP, *abort_s != 0)) break;
-            const int4 w = items[it];
-            const int s = w.x, y0 = w.y, x0 = w.z;
+            const RowItem w = row_item(a, it);
+            const int s = w.s, y0 = w.y0, x0 = w.x0;
             const TcFreqDev f = a.freqs[s];
             const int R = f.R, K = f.Krow;
             const int ncols = kRowTileX + 2 * R, PW = round_up(ncols, 4);
@@ -168,7 +195,7 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const TcBankArgs a, co
             }
             cp_async_commit();
             cp_async_wait<0>();
-            const int u0 = funit0[s], nu = funits[s];
+            const int u0 = f.u0, nu = a.nu_f;
             bool stop = false;
             for (int q = 0; q < nu; ++q, ++job) {
                 const TcUnitDev u = a.units[u0 + q];
@@ -262,13 +289,13 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const TcBankArgs a, co
         const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
         int job = 0;
         for (int it = blockIdx.x; it < nitems && !*abort_s; it += gridDim.x) {
-            const int4 w = items[it];
-            const int s = w.x, y0 = w.y, x0 = w.z;
-            const TcFreqDev f = a.freqs[s];
+            const RowItem w = row_item(a, it);
+            const int y0 = w.y0;
+            const TcFreqDev f = a.freqs[w.s];
             const float unscale = ldexpf(f.unscale_row, e);
-            const int gx = x0 + x;
+            const int gx = w.x0 + x;
             const bool xin = gx < a.W;
-            const int u0 = funit0[s], nu = funits[s];
+            const int u0 = f.u0, nu = a.nu_f;
             bool ok = true;
             for (int q = 0; q < nu; ++q, ++job) {
                 const TcUnitDev u = a.units[u0 + q];
@@ -283,8 +310,8 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const TcBankArgs a, co
                 }
                 tc_fence_after();
                 const bool paired = u.plane_b >= 0;
-                uint16_t *dst0 = a.sig + u.sig_off + (int64_t)(xin ? gx : 0) * a.Hp + a.Lpad + y0;
                 const int64_t sstride = (int64_t)a.W * a.Hp;   // between signals of the unit
+                uint16_t *dst0 = a.sig + u.sig_idx * sstride + (int64_t)(xin ? gx : 0) * a.Hp + a.Lpad + y0;
 #pragma unroll 1
                 for (int c0 = 0; c0 < 2 * TY; c0 += 16) {
                     float v[16];
@@ -342,9 +369,9 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const TcBankArgs a, co
 // Items: (unit, x0, y0), sorted by frequency; paired units take 32 columns x 4 signals,
 // unpaired ones 64 columns x 2 signals (always 128 A rows).  The producers keep one job of
 // operand loads in flight ahead of the MMA.
-__global__ void __launch_bounds__(256, 1) k_gabor_tc_cols(const TcBankArgs a, const int4 *__restrict__ items,
-                                                          int nitems)
+__global__ void __launch_bounds__(256, 1) k_gabor_tc_cols(const __grid_constant__ TcBankArgs a)
 {
+    const int nitems = a.nf * a.col_cnt;
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -386,7 +413,7 @@ __global__ void __launch_bounds__(256, 1) k_gabor_tc_cols(const TcBankArgs a, co
     if (warp >= 4) {
         // -------------------------------------------------------------- producers
         const int ptid = tid - 128;
-        auto item = [&](int j) { return items[blockIdx.x + j * gridDim.x]; };
+        auto item = [&](int j) { return col_item(a, blockIdx.x + j * gridDim.x); };
         auto load_g = [&](int s) {
             const TcFreqDev f = a.freqs[s];
             const uint4 *src = reinterpret_cast<const uint4 *>(f.Bcol);
@@ -395,10 +422,10 @@ __global__ void __launch_bounds__(256, 1) k_gabor_tc_cols(const TcBankArgs a, co
         };
         // cp.async of job j's A operand into buffer j & 1 (zero rows beyond the image).
         auto issue = [&](int j) {
-            const int4 w = item(j);
-            const TcUnitDev u = a.units[w.x];
+            const ColItem w = item(j);
+            const TcUnitDev u = a.units[w.unit];
             const TcFreqDev f = a.freqs[u.s];
-            const int x0 = w.y, y0 = w.z, K = f.Kcol;
+            const int x0 = w.x0, y0 = w.y0, K = f.Kcol;
             const int xw = u.plane_b >= 0 ? 32 : 64;
             const int64_t lbase = (int64_t)a.Lpad + y0 - f.R8;
             unsigned char *dstA = sA + (j & 1) * abuf;
@@ -408,14 +435,14 @@ __global__ void __launch_bounds__(256, 1) k_gabor_tc_cols(const TcBankArgs a, co
                 const int sgi = n / xw, x = n - sgi * xw;
                 const bool ok = x0 + x < a.W;
                 const uint16_t *src =
-                    a.sig + u.sig_off + ((int64_t)sgi * a.W + (ok ? x0 + x : 0)) * a.Hp + lbase + 8 * kc;
+                    a.sig + ((u.sig_idx + sgi) * a.W + (ok ? x0 + x : 0)) * a.Hp + lbase + 8 * kc;
                 const unsigned sdst = smem_u32(dstA + sw128_offset(128, n, 8 * kc));
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sdst), "l"(src), "r"(ok ? 16 : 0)
                              : "memory");
             }
             cp_async_commit();
         };
-        auto freq_of = [&](int j) { return a.units[item(j).x].s; };
+        auto freq_of = [&](int j) { return a.units[item(j).unit].s; };
         if (njobs > 0) {
             load_g(freq_of(0));
             issue(0);
@@ -483,10 +510,10 @@ __global__ void __launch_bounds__(256, 1) k_gabor_tc_cols(const TcBankArgs a, co
         //   unpaired: warps 0-1 P (x = 32 (w & 1) + lane), warps 2-3 Q
         const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
         for (int j = 0; j < njobs; ++j) {
-            const int4 w = items[blockIdx.x + j * gridDim.x];
-            const TcUnitDev u = a.units[w.x];
+            const ColItem w = col_item(a, blockIdx.x + j * gridDim.x);
+            const TcUnitDev u = a.units[w.unit];
             const TcFreqDev f = a.freqs[u.s];
-            const int x0 = w.y, y0 = w.z, b = j & 1;
+            const int x0 = w.x0, y0 = w.y0, b = j & 1;
             const bool paired = u.plane_b >= 0;
             const bool is_q = paired ? (warp & 1) : (warp >= 2);
             const int slot = paired ? (warp >> 1) : (warp & 1);
@@ -632,9 +659,9 @@ cudaError_t gabor_tc_prepare()
     return e;
 }
 
-cudaError_t launch_gabor_tc(const TcBankArgs &a, const int4 *row_items, int n_row_items, const int *funits,
-                            const int *funit0, const int4 *col_items, int n_col_items, int sm_count, cudaStream_t st)
+cudaError_t launch_gabor_tc(const TcBankArgs &a, int sm_count, cudaStream_t st)
 {
+    const int n_row_items = a.nf * a.row_cnt, n_col_items = a.nf * a.col_cnt;
     const size_t smem_r = gabor_tc_smem_rows(a.row_kmax, a.row_pwmax, a.row_ty);
     const size_t smem_c = gabor_tc_smem_cols(a.col_kmax);
     cudaError_t e0 = cudaMemsetAsync(a.absmax, 0, sizeof(int), st);
@@ -644,12 +671,12 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a, const int4 *row_items, int n_ro
     e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
     if (n_row_items > 0) {
-        k_gabor_tc_rows<<<std::min(n_row_items, sm_count), 384, smem_r, st>>>(a, row_items, n_row_items, funits, funit0);
+        k_gabor_tc_rows<<<std::min(n_row_items, sm_count), 384, smem_r, st>>>(a);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (n_col_items > 0) {
-        k_gabor_tc_cols<<<std::min(n_col_items, sm_count), 256, smem_c, st>>>(a, col_items, n_col_items);
+        k_gabor_tc_cols<<<std::min(n_col_items, sm_count), 256, smem_c, st>>>(a);
         return cudaGetLastError();
     }
     return cudaSuccess;

@@ -54,15 +54,27 @@ struct WorkItem {
     int img, unit, strip, y0, y1;
 };
 
-// Arguments of the fused FP32 bank kernel (one launch covers every frequency).
+// A run of work items of one image that share a frequency and a pairing: `nunits` units
+// from u0 on, each cut into nstrips strips x nseg row segments of seg_len rows.  Item
+// first + ((q * nstrips) + strip) * nseg + seg is unit u0 + q, that strip and segment.
+struct ItemGroup {
+    int first, u0, nstrips, nseg, seg_len;
+};
+constexpr int kMaxGroups = 64;
+
+// Arguments of the fused FP32 bank kernel (one launch covers every frequency).  Work items
+// come from a device list (`items`, batches) or, for one image, are decoded from `groups`
+// (largest item cost first), so that a single-image call needs no per-shape device data.
 struct BankArgs {
     ImageDev img0;            // the image when imgs == nullptr
     const ImageDev *imgs;     // batch images (device), or nullptr
     const FreqDev *freqs;
     const UnitDev *units;
-    const WorkItem *items;
+    const WorkItem *items;    // nullptr: decode from groups
     int *counter;             // work-queue head (zeroed before each launch)
     int nitems;
+    int ngroups;
+    ItemGroup groups[kMaxGroups];
 };
 
 // ---- tensor-core bank (gabor_tc.cu) ----
@@ -71,11 +83,12 @@ struct TcFreqDev {
     const uint16_t *Bcol;  // [64][Kcol] Toeplitz S(l - y - R8)
     int R, R8, Krow, Kcol;
     float unscale_row, unscale_col;   // 2^-sB of the B operands
+    int u0, pad_;          // first unit of the frequency
 };
 struct TcUnitDev {
     const float2 *phx, *phy;
     int s, plane_a, plane_b, pad_;
-    int64_t sig_off;       // element offset of the unit's signal block in the intermediate
+    int64_t sig_idx;       // first signal of the unit; its block starts at sig_idx * W * Hp
 };
 struct TcBankArgs {
     const float *img;
@@ -91,6 +104,12 @@ struct TcBankArgs {
     int *status;
     int row_kmax, row_pwmax, col_kmax, row_ty;
     int *absmax;           // device word: max |f| of the image as float bits (k_absmax)
+    // Work items, decoded from the image shape: frequencies in the order forder[] (largest
+    // radius first); every frequency has nu_f units, the first np_f of them paired.
+    const int *forder;
+    int nf, nu_f, np_f;
+    int row_nx, row_cnt;   // row pass: 128-column tiles per tile row, items per frequency
+    int col_ny, col_nx32, col_nx64, col_cnt;   // column pass: 64-row tiles, x tiles, items per frequency
 };
 struct TcGeometry {
     int R, R8, Krow, Kcol, PW;
@@ -147,11 +166,12 @@ bool gabor_tc_supported(int R);
 cudaError_t build_gabor_tc_b(uint16_t *Brow, uint16_t *Bcol, int R, double sigma, int bf16, float *unscale,
                              cudaStream_t st);
 cudaError_t gabor_tc_prepare();
-cudaError_t launch_gabor_tc(const TcBankArgs &a, const int4 *row_items, int n_row_items, const int *funits,
-                            const int *funit0, const int4 *col_items, int n_col_items, int sm_count, cudaStream_t st);
+cudaError_t launch_gabor_tc(const TcBankArgs &a, int sm_count, cudaStream_t st);
 int gabor_tc_row_tile_x();
 int gabor_tc_row_tile_y(int Rmax);
 int gabor_tc_col_tile_y();
+// Bounded-wait self-test (selftest.cu).
+cudaError_t launch_wait_selftest(int *status, int signal, unsigned long long limit_ns, cudaStream_t st);
 // Sets the message returned by gabor_bank_last_error() on the calling host thread.
 void set_last_error(const char *msg);
 // Tensor-core SDFT (windowed-DFT contraction on tcgen05).
@@ -207,17 +227,17 @@ struct gabor_bank {
     float sdft_B_unscale = 1.f;
     double sdftB_sigma = -1.0;
     int sdftB_Mx = 0, sdftB_My = 0;
-    // tensor-core bank: B operands per frequency, intermediate signals, column work items
+    // tensor-core bank: B operands per frequency, unit descriptors, intermediate signals
     uint16_t *d_tcB = nullptr;
     gb::TcFreqDev *d_tcfreq = nullptr;
     gb::TcUnitDev *d_tcunit = nullptr;
-    uint16_t *d_tcsig = nullptr;
+    uint16_t *d_tcsig = nullptr;    // library-owned intermediate (when no workspace is attached)
     size_t tcsig_elems = 0;
-    int4 *d_tcitems = nullptr;      // column-pass items
-    int tc_nitems = 0;
-    int4 *d_tcrowitems = nullptr;   // row-pass items
-    int tc_nrowitems = 0;
-    int *d_tcfunits = nullptr;      // [n_freq] units per frequency, then [n_freq] first unit
+    uint16_t *ws_ptr = nullptr;     // caller-owned workspace (gabor_bank_set_workspace), or nullptr
+    size_t ws_bytes = 0;
+    int *d_tcforder = nullptr;      // frequencies, largest radius first
+    int tc_nsig = 0;                // column signals of all units
+    int tc_nu_f = 0, tc_np_f = 0;   // units per frequency, paired units per frequency
     int tc_row_kmax = 0, tc_row_pwmax = 0, tc_col_kmax = 0;
     int *d_tcabsmax = nullptr;
     int tc_row_ty = 64;

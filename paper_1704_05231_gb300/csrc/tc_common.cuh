@@ -49,20 +49,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Waits for the phase with the given parity to complete.  Returns false on timeout or when
-// *abort becomes non-zero (another role gave up).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort)
+// Waits for the phase with the given parity to complete.  Returns false after limit_ns of
+// %globaltimer (or, as a backstop, 2^30 polls) or when *abort becomes non-zero (another role
+// gave up).
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, volatile int *abort,
+                                              unsigned long long limit_ns)
 {
     const uint32_t b = smem_u32(bar);
     if (mbar_try_wait(b, parity)) return true;
     const unsigned long long t0 = globaltimer();
-    for (uint32_t i = 1;; ++i) {
+    for (uint32_t i = 1; i < (1u << 30); ++i) {
         if (mbar_try_wait(b, parity)) return true;
         if ((i & 255) == 0) {
             if (*abort) return false;
-            if (globaltimer() - t0 > kWaitLimitNs) return false;
+            if (globaltimer() - t0 > limit_ns) return false;
         }
     }
+    return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort)
+{
+    return mbar_wait_for(bar, parity, abort, kWaitLimitNs);
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem()

@@ -117,3 +117,26 @@ def request_stream(seed: int = 2, n: int = 2200, rate_hz: float = 100.0,
             reqs.append(dict(t=float(t[i]), H=H, W=W, kind="bank", thetas=th, omegas=om,
                              sigmas=sg, seed=[seed, i]))
     return reqs
+
+
+def pink_noise_device(seed: int, H: int, W: int, device="cuda"):
+    """1/f-amplitude noise normalised to [0, 1] as a float32 CUDA tensor, made on the device.
+
+    The same construction as ``pink_noise`` (white Gaussian noise, spectrum times
+    1/max(|f|, 1/max(H, W)), DC removed, min-max normalised) with torch's seeded device
+    generator, for inputs too large to synthesise on the host in time (the served stream's
+    4096 x 4096 source images).  Values differ from ``pink_noise`` for the same seed.
+    """
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    white = torch.randn((H, W), generator=g, device=device, dtype=torch.float32)
+    spec = torch.fft.rfft2(white)
+    fy = torch.fft.fftfreq(H, device=device)[:, None]
+    fx = torch.fft.rfftfreq(W, device=device)[None, :]
+    f = torch.sqrt(fx * fx + fy * fy)
+    spec = spec / torch.clamp(f, min=1.0 / max(H, W))
+    spec[0, 0] = 0
+    a = torch.fft.irfft2(spec, s=(H, W))
+    lo, hi = a.min(), a.max()
+    return ((a - lo) / torch.clamp(hi - lo, min=1e-30)).contiguous()

@@ -49,11 +49,12 @@ def _save(path, data):
     os.replace(tmp, path)
 
 
-def autotune(gbk, imgs, cache_path=None, steps=3, use_cache=True):
+def autotune(gbk, imgs, cache_path=None, steps=3, use_cache=True, tile_rows=TILE_ROWS, segments=SEGMENTS):
     """Choose (tile_rows, segments) per frequency for `imgs` (a CUDA tensor or a list of them).
 
     Applies the choice to `gbk` and returns {"key", "tiling": [[tile_rows, segments], ...],
-    "ms"}.  Only the FP32 path has a tunable geometry; other precisions return the defaults.
+    "ms"}.  `tile_rows` and `segments` are the candidate values searched.  Only the FP32 path
+    has a tunable geometry; other precisions return the defaults.
     """
     import torch
     batch = isinstance(imgs, (list, tuple))
@@ -63,7 +64,7 @@ def autotune(gbk, imgs, cache_path=None, steps=3, use_cache=True):
     if gbk.precision != "fp32" or nf == 0:
         return {"key": None, "tiling": [[0, 0]] * nf, "ms": None}
     path = cache_path or default_cache_path()
-    key = cache_key(gbk, shapes, torch.cuda.get_device_name())
+    key = cache_key(gbk, shapes, torch.cuda.get_device_name()) + f"|{list(tile_rows)}|{list(segments)}"
     cache = _load(path) if use_cache else {}
     if key in cache:
         for s, (tr, sg) in enumerate(cache[key]["tiling"]):
@@ -97,8 +98,8 @@ def autotune(gbk, imgs, cache_path=None, steps=3, use_cache=True):
     tiling = [[0, 0] for _ in range(nf)]
     best_ms = timed()
     for s in sorted(range(nf), key=lambda i: -gbk.sigmas[i]):
-        for tr in TILE_ROWS:
-            for sg in SEGMENTS:
+        for tr in tile_rows:
+            for sg in segments:
                 if [tr, sg] == tiling[s]:
                     continue
                 gbk.set_tiling(s, tr, sg)

@@ -1,0 +1,101 @@
+"""Served stream (continuous batching over CUDA streams, HBM-budget admission).
+
+Each request's result must be the same alone and in the mix: the kernels' arithmetic for
+an output does not depend on what else runs, so the comparison is bitwise.  A small sample
+is also checked against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests.helpers import FP32_TOL, TC_TOL, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pool():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1704_05231_gb300.serve import ImagePool
+    return ImagePool(n=2, side=512, seed=4)
+
+
+def _collect(store):
+    def cb(req, out):
+        store[req["rid"]] = out.cpu().numpy()
+    return cb
+
+
+def _reqs(n=24, seed=5):
+    from paper_1704_05231_gb300.serve import served_stream
+    reqs = served_stream(seed=seed, n=n, lo=40, hi=400, p_sdft=0.25)
+    for i, r in enumerate(reqs):
+        r["rid"] = i
+    return reqs
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16_tc"])
+def test_alone_equals_mix_bitwise(pool, precision):
+    from paper_1704_05231_gb300.serve import Server, summarize, with_rate
+    reqs = _reqs()
+    srv = Server(precision=precision, slots=3, budget_bytes=1 << 30, max_side=512, pool=pool)
+    try:
+        srv.prepare(reqs)
+        alone, mix = {}, {}
+        for r in reqs:
+            srv.run([dict(r, t=0.0)], on_done=_collect(alone))
+        recs = srv.run(with_rate(reqs, 3000.0), on_done=_collect(mix))
+    finally:
+        srv.close()
+    assert len(alone) == len(mix) == len(reqs)
+    for i in range(len(reqs)):
+        assert alone[i].shape == mix[i].shape
+        assert np.array_equal(alone[i], mix[i]), f"request {i} differs in the mix"
+    s = summarize(recs)
+    assert s["served"] == len(reqs) and s["rejected"] == 0
+    # requests ran concurrently: some request was admitted before an earlier one finished
+    overlap = sum(1 for a in recs for b in recs
+                  if a["rid"] < b["rid"] and b["t_admit"] < a["t_done"] and a["t_admit"] < b["t_done"])
+    print(precision, s, "overlapping pairs", overlap)
+    assert overlap > 0
+
+
+def test_budget_admission_and_rejection(pool):
+    from paper_1704_05231_gb300.serve import Server, closed_loop, request_outputs
+    reqs = _reqs(n=10, seed=6)
+    need = max(request_outputs(r) * 8 for r in reqs)
+    big = dict(reqs[0], H=512, W=512, kind="sdft", M=16, sigma=4.0, rid=len(reqs))
+    srv = Server(precision="fp32", slots=3, budget_bytes=need + (1 << 20), max_side=512, pool=pool)
+    try:
+        srv.prepare(reqs)
+        alone, mix = {}, {}
+        for r in reqs:
+            srv.run([dict(r, t=0.0)], on_done=_collect(alone))
+        recs = srv.run(closed_loop(reqs + [big]), on_done=_collect(mix))
+        assert srv.arena.stats()["in_use"] == 0
+    finally:
+        srv.close()
+    assert recs[-1].get("rejected")      # 512 x 512 x 256 planes exceeds the budget
+    for i in range(len(reqs)):
+        assert np.array_equal(alone[i], mix[i])
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", FP32_TOL), ("fp16_tc", TC_TOL)])
+def test_served_results_match_oracle(pool, precision, tol):
+    from paper_1704_05231_gb300.serve import Server, closed_loop
+    from paper_1704_05231_gb300.synth import octave_bank
+    th, om, sg = octave_bank(5, 3)
+    reqs = [dict(t=0.0, rid=0, kind="bank", H=70, W=96, thetas=th, omegas=om, sigmas=sg, seed=[9, 0]),
+            dict(t=0.0, rid=1, kind="sdft", H=48, W=60, M=16, sigma=4.0, seed=[9, 1])]
+    srv = Server(precision=precision, slots=2, budget_bytes=256 << 20, max_side=512, pool=pool)
+    got = {}
+    try:
+        srv.run(closed_loop(reqs), on_done=_collect(got))
+        imgs = [srv.pool.crop(r).cpu().numpy() for r in reqs]
+    finally:
+        srv.close()
+    ref0 = oracle.gabor_bank(np.ascontiguousarray(imgs[0]), th, om, sg)
+    assert rel_err(got[0], ref0) <= tol
+    ref1 = oracle.sdft(np.ascontiguousarray(imgs[1]), 4.0, 16)
+    assert rel_err(got[1], ref1) <= tol
