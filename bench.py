@@ -28,6 +28,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "Gabor bank pixel·filter outputs/s, plain vs TC at ≤2e-3 rel err; serve p99 ms"
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_gabor_fp32 launch on this
+# workload from an ncu capture of the current kernel; None once the kernel changes.
+K_GABOR_FP32_TRAFFIC = None
 UNIT = "outputs/s"
 H = W = 1024
 
@@ -73,6 +76,65 @@ def fp32_peak_tflops(torch):
     except Exception:
         pass
     return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
+
+
+class NvmlClockSampler:
+    """SM clock and clock-event reasons read through NVML (libnvidia-ml, read-only queries)
+    every `period_s` from a host thread during the timed region, plus once at its start and
+    end, so that even a region of a few milliseconds has samples."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, torch, dev, period_s=0.002):
+        import ctypes
+        import threading
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        uuid = ("GPU-" + str(torch.cuda.get_device_properties(dev).uuid)).encode()
+        if self.lib.nvmlDeviceGetHandleByUUID(ctypes.c_char_p(uuid), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("NVML handle not found")
+        self.reason_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.period = period_s
+        self.samples = []
+        self.stop_ev = threading.Event()
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+
+    def _sample(self):
+        c, r = self.ct.c_uint(), self.ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, 1, self.ct.byref(c)) == 0 and \
+                self.reason_fn(self.h, self.ct.byref(r)) == 0:
+            self.samples.append((c.value, r.value))
+
+    def _loop(self):
+        while not self.stop_ev.is_set():
+            self._sample()
+            self.stop_ev.wait(self.period)
+
+    def start(self):
+        self._sample()
+        self.thread.start()
+
+    def stop(self):
+        self.stop_ev.set()
+        self.thread.join()
+        self._sample()
+        mx = self.ct.c_uint()
+        sm_max = float(mx.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, self.ct.byref(mx)) == 0 else None
+        sm = [c for c, _ in self.samples]
+        reasons = sorted({n for _, r in self.samples for bit, n in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": sm_max, "reasons": reasons,
+                "samples": len(self.samples), "source": "nvml"}
+
+
+def clock_sampler(torch, dev):
+    try:
+        return NvmlClockSampler(torch, dev)
+    except Exception:
+        return ClockSampler(dev)
 
 
 class ClockSampler:
@@ -341,13 +403,32 @@ def serve_leg(args):
                        "crops of device-resident 4096^2 1/f noise; outputs stay in device memory",
            "budget_gib": 96, "slots": 4}
     for prec in ("fp32", "fp16_tc"):
-        r = serve.measure(prec, n_warm=args.serve_warm, n_meas=args.serve_n, rate_fracs=(0.7,), pool=pool,
+        r = serve.measure(prec, n_warm=args.serve_warm, n_meas=args.serve_n, rate_fracs=(0.7, 0.5, 0.9), pool=pool,
                           n_sat=min(300, args.serve_n), log=lambda m: print(m, file=sys.stderr, flush=True))
-        s = r["rates"][0.7]
-        res[prec] = {"saturation_req_s": r["saturation_req_s"], "rate_req_s": s["rate_req_s"],
-                     "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"], "outputs_per_s": s["outputs_per_s"],
-                     "served": s["served"], "rejected": s["rejected"]}
+        ent = {"saturation_req_s": r["saturation_req_s"]}
+        for frac, s in r["rates"].items():
+            ent[f"{frac:.1f}x"] = {"rate_req_s": s["rate_req_s"], "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"],
+                                   "outputs_per_s": s["outputs_per_s"], "served": s["served"],
+                                   "rejected": s["rejected"]}
+        ent.update({k: ent["0.7x"][k] for k in ("p50_ms", "p99_ms", "outputs_per_s")})
+        res[prec] = ent
     return res
+
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's step time (ms): every replica runs the same work, so the job's
+    step ends when the last one does."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(n_out_per_rank, world, ms):
+    """Whole-job outputs/s: every rank filters its own image (weak scaling, no exchange)."""
+    return n_out_per_rank * world / (ms * 1e-3)
 
 
 def run_ours(args):
@@ -383,7 +464,7 @@ def run_ours(args):
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    sampler = ClockSampler(local)
+    sampler = clock_sampler(torch, local)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -401,11 +482,8 @@ def run_ours(args):
     clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = statistics.mean(step_ms)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n_out * world / (ms * 1e-3)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = replica_throughput(n_out, world, ms)
 
     # End to end through the C ABI on host buffers (pinned): H2D image, bank, D2H result.
     e2e_s = float("nan")
@@ -429,7 +507,7 @@ def run_ours(args):
             "config": workload_config({"path": "FP32 CUDA-core fused bank kernel", "parallelism": f"replicas x{world}",
                                        "tiling": tiling}),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": K_GABOR_FP32_TRAFFIC,
                          "kernel": "k_gabor_fp32 (one persistent launch per step)",
                          "peak_note": f"derived: {sms} SMs x 128 FP32 lanes x 2 FLOP x {mhz:.0f} MHz",
                          "algorithmic": "(3N+1)(2R+1) FMA per pixel per frequency"},
@@ -439,13 +517,17 @@ def run_ours(args):
             "gpu_launches": args.steps,
             "clocks": clocks,
             "wall_s": wall}
-    if not args.no_extra:
+    legs = set() if args.no_extra else set(args.legs.split(","))
+    if "tc" in legs:
         line["tc"] = bank_tc_leg(torch, d_img, thetas, omegas, sigmas, out, n_out, args.steps, args.warmup, flush,
                                  stream)
+    if "sdft" in legs:
         line["sdft"] = sdft_leg(torch, args.steps, args.warmup, flush, stream)
+    if "ablation" in legs:
         line["ablation"] = ablation_leg(torch, d_img, thetas, omegas, sigmas, args.steps, args.warmup, flush, stream)
+    if "batch" in legs:
         line["batch"] = batch_leg(torch, min(args.steps, 5), 3, flush, stream)
-    if not args.no_serve and world == 1:
+    if "serve" in legs and not args.no_serve and world == 1:
         line["serve"] = serve_leg(args)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(img, thetas, omegas, sigmas, args.cpu_seconds)
@@ -464,10 +546,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
-    ap.add_argument("--no-extra", action="store_true", help="skip the SDFT leg (profiling runs)")
+    ap.add_argument("--no-extra", action="store_true", help="skip every extra leg (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-tune", action="store_true", help="default tile geometry instead of the autotuner's")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream leg")
+    ap.add_argument("--legs", default="tc,sdft,ablation,batch,serve",
+                    help="comma list of extra legs: tc, sdft, ablation, batch, serve")
     ap.add_argument("--serve-n", type=int, default=2000, help="measured requests of the served stream")
     ap.add_argument("--serve-warm", type=int, default=200)
     args = ap.parse_args()

@@ -91,7 +91,7 @@ gb_status gabor_bank_destroy(gabor_bank_t h);
  * GB_FP16_TC handle without a workspace (gabor_bank_set_workspace) grows its own
  * intermediate buffer when an image needs more than it holds.
  * Asynchronous.  Errors: GB_ERR_INVALID_ARG (NULL, H/W <= 0, pitch < W, misaligned),
- * GB_ERR_UNSUPPORTED (BF16 bank, or a radius above 120 px on tensor cores), GB_ERR_BUDGET
+ * GB_ERR_UNSUPPORTED (BF16 bank, or a radius above 96 px on tensor cores), GB_ERR_BUDGET
  * (attached workspace too small), GB_ERR_CUDA.  gabor_bank_create refuses radii above 160 px.
  */
 gb_status gabor_bank_filter(gabor_bank_t h, const float *d_img, int H, int W, int64_t pitch,

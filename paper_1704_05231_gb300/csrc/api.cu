@@ -474,7 +474,7 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
                     "exceed 2e-3 * max|out| on the bank");
     for (const Freq &f : h->freqs)
         if (!gabor_tc_supported(f.R))
-            return fail(GB_ERR_UNSUPPORTED, "tensor-core bank supports radii up to ~120 px");
+            return fail(GB_ERR_UNSUPPORTED, "tensor-core bank supports radii up to 96 px");
     const int nf = (int)h->freqs.size();
     const int64_t ny64 = (H + 63) / 64, nx32 = (W + 31) / 32, nx64 = (W + 63) / 64;
     // the unit descriptors point into the phase tables: (re)build them with the tables
@@ -509,11 +509,14 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
                                        std::to_string(need * (int64_t)sizeof(uint16_t)) + " bytes");
     }
     if (zero_halo && need > 0) {
-        // The row pass writes rows [Lpad, Lpad + round_up(H, TY)) of every column signal; the
-        // column pass reads up to Lpad + R8 rows beyond that, which must be zero.
-        const size_t rows = (size_t)h->tc_nsig * W;
-        GB_CU(cudaMemset2DAsync(sig, (size_t)Hp * 2, 0, (size_t)Lpad * 2, rows, st));
-        GB_CU(cudaMemset2DAsync(sig + Lpad + H, (size_t)Hp * 2, 0, (size_t)(Hp - Lpad - H) * 2, rows, st));
+        // Layout [signal][Hp / 8][W][8].  The row pass writes rows [Lpad, Lpad + round_up(H, TY))
+        // of every signal (zeros below row H); the column pass reads up to R8 rows beyond, so
+        // the blocks of rows [0, Lpad) and [Lpad + round_up(H, 8), Hp) must be zero.
+        const size_t sig_bytes = (size_t)Hp * W * 2, blk = (size_t)W * 16;
+        const int64_t back = (Lpad + ((int64_t)H + 7) / 8 * 8) / 8;
+        GB_CU(cudaMemset2DAsync(sig, sig_bytes, 0, (size_t)(Lpad / 8) * blk, (size_t)h->tc_nsig, st));
+        GB_CU(cudaMemset2DAsync(reinterpret_cast<char *>(sig) + back * blk, sig_bytes, 0,
+                                (size_t)(Hp / 8 - back) * blk, (size_t)h->tc_nsig, st));
     }
     h->tc_H = h->ws_ptr ? 0 : H;
     h->tc_W = h->ws_ptr ? 0 : W;

@@ -12,13 +12,30 @@
 
 namespace gb {
 
+// Two independent round-to-nearest FMAs in one packed FP32x2 instruction (sm_100+): the same
+// results as two fmaf calls, half the issue slots.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{\n.reg .b64 ra, rb, rc, rd;\n"
+        "mov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\nmov.b64 rc, {%6, %7};\n"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n"
+        "mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
 __device__ __forceinline__ float4 fmav(float4 w, float t, float4 a)
 {
-    return make_float4(fmaf(w.x, t, a.x), fmaf(w.y, t, a.y), fmaf(w.z, t, a.z), fmaf(w.w, t, a.w));
+    const float2 tt = make_float2(t, t);
+    const float2 lo = ffma2(make_float2(w.x, w.y), tt, make_float2(a.x, a.y));
+    const float2 hi = ffma2(make_float2(w.z, w.w), tt, make_float2(a.z, a.w));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 __device__ __forceinline__ float2 fmav(float2 w, float t, float2 a)
 {
-    return make_float2(fmaf(w.x, t, a.x), fmaf(w.y, t, a.y));
+    return ffma2(w, make_float2(t, t), a);
 }
 
 // acc[j] += sum_d win[j + d] * t[d] for the 8 taps of one chunk; win = lo[0..7] ++ hi[0..7].

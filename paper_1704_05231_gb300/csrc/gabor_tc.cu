@@ -11,8 +11,9 @@
 //                  (thread = one image column): J = remodulation (Eq. 5-6), the column
 //                  signals of Eq. 10, f_cr + f_si, f_sr - f_ci (theta) and f_cr - f_si,
 //                  f_sr + f_ci (pi - theta, Eq. 15-16: J_{pi-theta} = J*_theta costs nothing),
-//                  written as FP16 with image rows contiguous (16-byte stores) to an
-//                  intermediate that stays in L2.
+//                  written as FP16 to an intermediate laid out [signal][y / 8][x][8]: a
+//                  thread's 8 rows of one column are one 16-byte block and a warp's stores
+//                  cover 32 consecutive blocks.
 //   column kernel  D[(signal, x)][y] = sum_l Sig[(signal, x)][l] G[y][l],  G[y][l] = S(l - y - R8)
 //                  -> P, Q, P', Q' (Eq. 9).  Epilogue: F = remodulation by (cos, sin)(w^s y)
 //                  (Eq. 7-8, 15-16), complex64 stores with coalesced rows.
@@ -37,7 +38,12 @@ constexpr int kRowTileX = 128;   // row kernel: image columns per tile (MMA M)
 constexpr int kRowTileYMax = 64; // row kernel: image rows per tile (64, or 32 for large radii; MMA N = 2 x rows)
 constexpr int kColTileY = 64;    // column kernel: output rows per tile (MMA N)
 
-__device__ __forceinline__ uint16_t h16(float v) { return __half_as_ushort(__float2half_rn(v)); }
+// (lo, hi) rounded to FP16 in one 32-bit word, lo in the low half (one cvt.rn.f16x2.f32).
+__device__ __forceinline__ uint32_t h2pack(float lo, float hi)
+{
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
 
 __device__ __forceinline__ void fail_status(int *status, volatile int *flag, int code)
 {
@@ -45,8 +51,13 @@ __device__ __forceinline__ void fail_status(int *status, volatile int *flag, int
     atomicExch(status, code);
 }
 
+// Per-CTA copy of the plan's descriptors (frequency order, frequencies, units) when they fit.
+constexpr int kDescMaxFreqs = 32, kDescMaxUnits = 128;
+constexpr uint32_t kDescBytes = (kDescMaxFreqs * 4 + kDescMaxFreqs * sizeof(TcFreqDev) +
+                                 kDescMaxUnits * sizeof(TcUnitDev) + 127) / 128 * 128;
+
 struct RowSmem {
-    uint32_t t_off, dm_off, patch_off, ph_off, bar_off, misc_off, total;
+    uint32_t t_off, dm_off, patch_off, ph_off, desc_off, bar_off, misc_off, total;
 };
 
 __host__ __device__ inline RowSmem row_smem(int K, int PW, int TY)
@@ -56,26 +67,39 @@ __host__ __device__ inline RowSmem row_smem(int K, int PW, int TY)
     L.dm_off = L.t_off + (uint32_t)kRowTileX * K * 2;
     L.patch_off = L.dm_off + (uint32_t)(2 * TY) * K * 2;
     L.ph_off = L.patch_off + (uint32_t)TY * (round_up(PW, 8) + 4) * 4;
-    L.bar_off = (L.ph_off + (uint32_t)PW * 8 + 15) & ~15u;
+    L.desc_off = (L.ph_off + 2u * PW * 8 + 15) & ~15u;
+    L.bar_off = L.desc_off + kDescBytes;
     L.misc_off = L.bar_off + 8 * 8;
     L.total = L.misc_off + 64;
     return L;
 }
 
 struct ColSmem {
-    uint32_t g_off, a_off, xch_off, bar_off, misc_off, total;
+    uint32_t g_off, a_off, xch_off, desc_off, bar_off, misc_off, total;
 };
 
-__host__ __device__ inline ColSmem col_smem(int K)
+constexpr int kColMaxStages = 4;   // A-operand buffers of the column kernel (at most)
+constexpr int kColAcc = 4;         // TMEM accumulators (64 columns each) of the column kernel
+
+__host__ __device__ inline ColSmem col_smem(int K, int nst)
 {
     ColSmem L;
     L.g_off = 0;
     L.a_off = L.g_off + (uint32_t)kColTileY * K * 2;
-    L.xch_off = L.a_off + 2u * 128 * K * 2;
-    L.bar_off = L.xch_off + 2u * kColTileY * 32 * 4;
-    L.misc_off = L.bar_off + 8 * 8;
+    L.xch_off = L.a_off + (uint32_t)nst * 128 * K * 2;
+    L.desc_off = L.xch_off + 4u * kColTileY * 32 * 4;
+    L.bar_off = L.desc_off + kDescBytes;
+    L.misc_off = L.bar_off + 16 * 8;
     L.total = L.misc_off + 64;
     return L;
+}
+
+// A buffers of the column kernel for K: 3 when shared memory allows, else 2 (0: does not fit).
+__host__ __device__ inline int col_stages(int K)
+{
+    for (int n = 3; n >= 2; --n)
+        if (1024 + col_smem(K, n).total <= (uint32_t)kSmemLimit) return n;
+    return 0;
 }
 
 }  // namespace
@@ -90,16 +114,39 @@ struct RowItem {
 struct ColItem {
     int unit, x0, y0;
 };
-__device__ __forceinline__ RowItem row_item(const TcBankArgs &a, int it)
+// The plan's descriptors as the kernel reads them: shared-memory copies when they fit.
+struct TcDesc {
+    const int *forder;
+    const TcFreqDev *freqs;
+    const TcUnitDev *units;
+};
+// Copies the descriptors into `smem` (kDescBytes) when the plan is small enough; every thread
+// of the CTA calls it, and a barrier must follow before the copies are read.
+__device__ __forceinline__ TcDesc load_desc(const TcBankArgs &a, unsigned char *smem)
+{
+    const int nu = a.nf * a.nu_f;
+    if (a.nf > kDescMaxFreqs || nu > kDescMaxUnits) return TcDesc{a.forder, a.freqs, a.units};
+    int *fo = reinterpret_cast<int *>(smem);
+    TcFreqDev *fr = reinterpret_cast<TcFreqDev *>(smem + kDescMaxFreqs * 4);
+    TcUnitDev *un = reinterpret_cast<TcUnitDev *>(smem + kDescMaxFreqs * 4 + kDescMaxFreqs * sizeof(TcFreqDev));
+    const int nw_f = a.nf * (int)(sizeof(TcFreqDev) / 4), nw_u = nu * (int)(sizeof(TcUnitDev) / 4);
+    for (int i = threadIdx.x; i < a.nf; i += blockDim.x) fo[i] = a.forder[i];
+    for (int i = threadIdx.x; i < nw_f; i += blockDim.x)
+        reinterpret_cast<int *>(fr)[i] = reinterpret_cast<const int *>(a.freqs)[i];
+    for (int i = threadIdx.x; i < nw_u; i += blockDim.x)
+        reinterpret_cast<int *>(un)[i] = reinterpret_cast<const int *>(a.units)[i];
+    return TcDesc{fo, fr, un};
+}
+__device__ __forceinline__ RowItem row_item(const TcBankArgs &a, const TcDesc &d, int it)
 {
     const int g = it / a.row_cnt, local = it - g * a.row_cnt;
-    return RowItem{__ldg(a.forder + g), (local / a.row_nx) * a.row_ty, (local % a.row_nx) * kRowTileX};
+    return RowItem{d.forder[g], (local / a.row_nx) * a.row_ty, (local % a.row_nx) * kRowTileX};
 }
-__device__ __forceinline__ ColItem col_item(const TcBankArgs &a, int it)
+__device__ __forceinline__ ColItem col_item(const TcBankArgs &a, const TcDesc &d, int it)
 {
     const int g = it / a.col_cnt;
     int local = it - g * a.col_cnt;
-    const int u0 = a.freqs[__ldg(a.forder + g)].u0;
+    const int u0 = d.freqs[d.forder[g]].u0;
     const int paired_items = a.np_f * a.col_ny * a.col_nx32;
     const bool paired = local < paired_items;
     if (!paired) local -= paired_items;
@@ -110,8 +157,11 @@ __device__ __forceinline__ ColItem col_item(const TcBankArgs &a, int it)
 
 // ------------------------------------------------------------------------------ row pass
 // Items: (frequency s, tile y, tile x), sorted by frequency; each item runs every unit of s.
-// The input scale 2^-e (|f| 2^-e < 1, FP16 range) comes from k_absmax for the whole image.
-__global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const __grid_constant__ TcBankArgs a)
+// The input scale 2^-e (|f| 2^-e < 1, FP16 range) comes from k_absmax for the whole image; it
+// is applied to the staged patch (a power of two: exact).  Warps 8-15 stage operands (the
+// phases of the next unit arrive by cp.async while the current unit's operand is built);
+// warps 0-7 are the epilogue, two per TMEM lane quarter, each taking half of the rows.
+__global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant__ TcBankArgs a)
 {
     const int nitems = a.nf * a.row_cnt;
     extern __shared__ unsigned char smem_dyn[];
@@ -122,20 +172,21 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const __grid_constant_
     unsigned char *sT = sm + L.t_off;
     unsigned char *sDm = sm + L.dm_off;
     float *patch = reinterpret_cast<float *>(sm + L.patch_off);
-    float2 *ph = reinterpret_cast<float2 *>(sm + L.ph_off);
+    float *phbuf = reinterpret_cast<float *>(sm + L.ph_off);   // [2 slots][cos, sin][PWmax]
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.bar_off);
     uint64_t *tmem_full = bars;        // [2] commit
-    uint64_t *tmem_empty = bars + 2;   // [2] 4 epilogue warps
+    uint64_t *tmem_empty = bars + 2;   // [2] 8 epilogue warps
     uint64_t *dm_empty = bars + 4;     // [1] commit: the MMA reading Dm is done
     uint64_t *drain = bars + 5;
     uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
+    const TcDesc D = load_desc(a, sm + L.desc_off);
 
     if (tid == 0) {
         mbar_init(&tmem_full[0], 1);
         mbar_init(&tmem_full[1], 1);
-        mbar_init(&tmem_empty[0], 4);
-        mbar_init(&tmem_empty[1], 4);
+        mbar_init(&tmem_empty[0], 8);
+        mbar_init(&tmem_empty[1], 8);
         mbar_init(dm_empty, 1);
         mbar_init(drain, 1);
         *abort_s = 0;
@@ -156,20 +207,34 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const __grid_constant_
         if (mx > 0.f) frexpf(mx, &e);   // mx = m 2^e, m in [0.5, 1)
     }
 
-    if (warp >= 4) {
+    if (warp >= 8) {
         // -------------------------------------------------------------- producers
-        constexpr int NP = 256;                 // producer threads (warps 4-11)
-        const int ptid = tid - 128, pwarp = warp - 4;
+        constexpr int NP = 256;                 // producer threads (warps 8-15)
+        const int ptid = tid - 256, pwarp = warp - 8;
         const float sc = ldexpf(1.f, -e);
         int cur_s = -1, job = 0;
+        // cp.async of unit u's phases cos(w^c x), sin(w^c x) for the tile's columns into
+        // phbuf[slot][0][.] and phbuf[slot][1][.]
+        auto issue_phases = [&](const TcUnitDev &u, int x0, int R, int PW, int ncols, int slot) {
+            float *dst = phbuf + slot * 2 * a.row_pwmax;
+            const float *src = reinterpret_cast<const float *>(u.phx);
+            for (int i = ptid; i < 2 * PW; i += NP) {
+                const int c = i >> 1, cs = i & 1;
+                const int gx = x0 - R + c;
+                const bool ok = c < ncols && gx >= 0 && gx < a.W;
+                cp_async4(dst + cs * a.row_pwmax + c, ok ? (const void *)(src + 2 * gx + cs) : (const void *)src, ok ? 4 : 0);
+            }
+            cp_async_commit();
+        };
         for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
             if (named_barrier_or(1, NP, *abort_s != 0)) break;
-            const RowItem w = row_item(a, it);
+            const RowItem w = row_item(a, D, it);
             const int s = w.s, y0 = w.y0, x0 = w.x0;
-            const TcFreqDev f = a.freqs[s];
+            const TcFreqDev f = D.freqs[s];
             const int R = f.R, K = f.Krow;
             const int ncols = kRowTileX + 2 * R, PW = round_up(ncols, 4);
             const int PWs = round_up(PW, 8) + 4;     // row stride: 16-byte rows fall on distinct banks
+            const int u0 = f.u0, nu = a.nu_f;
             // The previous item's last MMA (which read Dm, and T) must be complete.
             bool failed = job > 0 && !mbar_wait(dm_empty, (job - 1) & 1, abort_s);
             if (named_barrier_or(1, NP, failed)) {
@@ -182,7 +247,7 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const __grid_constant_
                 for (int i = ptid; i < kRowTileX * K * 2 / 16; i += NP) dst[i] = src[i];
                 cur_s = s;
             }
-            // patch rows y0 .. y0 + 63, columns x0 - R .. x0 + 127 + R (zero outside the image)
+            // patch rows y0 .. y0 + TY - 1, columns x0 - R .. x0 + 127 + R (zero outside the image)
             for (int r = pwarp; r < TY; r += NP / 32) {
                 const int y = y0 + r;
                 const bool yin = y < a.H;
@@ -194,11 +259,13 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const __grid_constant_
                 }
             }
             cp_async_commit();
+            issue_phases(D.units[u0], x0, R, PW, ncols, 0);
             cp_async_wait<0>();
-            const int u0 = f.u0, nu = a.nu_f;
+            // input scale 2^-e on the thread's own patch elements (exact)
+            for (int r = pwarp; r < TY; r += NP / 32)
+                for (int c = lane; c < PW; c += 32) patch[r * PWs + c] *= sc;
             bool stop = false;
             for (int q = 0; q < nu; ++q, ++job) {
-                const TcUnitDev u = a.units[u0 + q];
                 const int b = job & 1;
                 // Dm is read by the previous job's MMA.
                 failed = q > 0 && !mbar_wait(dm_empty, (job - 1) & 1, abort_s);
@@ -207,52 +274,45 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const __grid_constant_
                     stop = true;
                     break;
                 }
-                // demodulation phases times the input scale (Eq. 5)
-                for (int c = ptid; c < PW; c += NP) {
-                    const int gx = x0 - R + c;
-                    const float2 v = (c < ncols && gx >= 0 && gx < a.W) ? u.phx[gx] : make_float2(0.f, 0.f);
-                    ph[c] = make_float2(v.x * sc, v.y * sc);
+                // prefetch the next unit's phases (its buffer was read by job - 1's operand build)
+                if (q + 1 < nu) {
+                    issue_phases(D.units[u0 + q + 1], x0, R, PW, ncols, (q + 1) & 1);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
                 }
-                named_barrier(1, NP);
-                // Dm[n = 2r + sg][k]: a warp takes 32 rows n of one 8-k chunk (conflict-free
-                // patch rows, broadcast phases, conflict-free swizzled stores).
-                const int kch = K / 8;
+                named_barrier(1, NP);    // this unit's phases (and the scaled patch) are visible
+                // Dm[n = 2r + sg][k] = patch[r][k] (cos | sin)[k]: thread ptid keeps row
+                // n = ptid mod 2TY and walks its 8-k chunks (broadcast phases, conflict-free
+                // patch rows and swizzled stores).
+                {
+                    const int n = ptid % (2 * TY), r = n >> 1, sg = n & 1;
+                    const float *prow = patch + r * PWs;
+                    const float *phr = phbuf + ((q & 1) * 2 + sg) * a.row_pwmax;
+                    const int kch = K / 8, kstep = NP / (2 * TY);
 #pragma unroll 2
-                for (int ci = ptid; ci < 2 * TY * kch; ci += NP) {
-                    const int n = ci % (2 * TY), kc = ci / (2 * TY);
-                    const int r = n >> 1, sg = n & 1;
-                    const int k0 = 8 * kc;
-                    uint32_t wv[4];
-                    if (k0 + 8 <= PW) {
-                        const float4 p0 = *reinterpret_cast<const float4 *>(patch + r * PWs + k0);
-                        const float4 p1 = *reinterpret_cast<const float4 *>(patch + r * PWs + k0 + 4);
-                        const float pv[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+                    for (int kc = ptid / (2 * TY); kc < kch; kc += kstep) {
+                        const int k0 = 8 * kc;
+                        uint32_t wv[4];
+                        if (k0 + 8 <= PW) {
+                            const float4 p0 = *reinterpret_cast<const float4 *>(prow + k0);
+                            const float4 p1 = *reinterpret_cast<const float4 *>(prow + k0 + 4);
+                            const float4 h0 = *reinterpret_cast<const float4 *>(phr + k0);
+                            const float4 h1 = *reinterpret_cast<const float4 *>(phr + k0 + 4);
+                            wv[0] = h2pack(p0.x * h0.x, p0.y * h0.y);
+                            wv[1] = h2pack(p0.z * h0.z, p0.w * h0.w);
+                            wv[2] = h2pack(p1.x * h1.x, p1.y * h1.y);
+                            wv[3] = h2pack(p1.z * h1.z, p1.w * h1.w);
+                        } else {
+                            float vv[8];
 #pragma unroll
-                        for (int qq = 0; qq < 4; ++qq) {
-                            const float2 h0 = ph[k0 + 2 * qq], h1 = ph[k0 + 2 * qq + 1];
-                            const float v0 = pv[2 * qq] * (sg ? h0.y : h0.x);
-                            const float v1 = pv[2 * qq + 1] * (sg ? h1.y : h1.x);
-                            wv[qq] = (uint32_t)h16(v0) | ((uint32_t)h16(v1) << 16);
+                            for (int t = 0; t < 8; ++t) vv[t] = (k0 + t < PW) ? prow[k0 + t] * phr[k0 + t] : 0.f;
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) wv[t] = h2pack(vv[2 * t], vv[2 * t + 1]);
                         }
-                    } else {
-#pragma unroll
-                        for (int qq = 0; qq < 4; ++qq) {
-                            float vv[2];
-#pragma unroll
-                            for (int t2 = 0; t2 < 2; ++t2) {
-                                const int k = k0 + 2 * qq + t2;
-                                float v = 0.f;
-                                if (k < PW) {
-                                    const float2 h = ph[k];
-                                    v = patch[r * PWs + k] * (sg ? h.y : h.x);
-                                }
-                                vv[t2] = v;
-                            }
-                            wv[qq] = (uint32_t)h16(vv[0]) | ((uint32_t)h16(vv[1]) << 16);
-                        }
+                        *reinterpret_cast<uint4 *>(sDm + sw128_offset(2 * TY, n, k0)) =
+                            make_uint4(wv[0], wv[1], wv[2], wv[3]);
                     }
-                    *reinterpret_cast<uint4 *>(sDm + sw128_offset(2 * TY, n, k0)) =
-                        make_uint4(wv[0], wv[1], wv[2], wv[3]);
                 }
                 fence_proxy_async_smem();
                 named_barrier(1, NP);
@@ -275,6 +335,7 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const __grid_constant_
             }
             if (stop) break;
         }
+        cp_async_wait<0>();
         if (ptid == 0) {
             tc_commit(drain);
             if (!mbar_wait(drain, 0, abort_s)) {
@@ -284,25 +345,28 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const __grid_constant_
         }
     } else {
         // -------------------------------------------------------------- epilogue
-        // Thread = image column x0 + x (TMEM lane x); accumulator columns 2r + {c, s}.
-        const int x = 32 * warp + lane;
-        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+        // Thread = image column x0 + x (TMEM lane x); accumulator columns 2r + {c, s}.  Warp
+        // w reads lane quarter w & 3 and rows [half TY/2, half TY/2 + TY/2), half = w >> 2.
+        const int quarter = warp & 3, half = warp >> 2;
+        const int x = 32 * quarter + lane;
+        const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+        const int rbase = half * (TY / 2);
         int job = 0;
         for (int it = blockIdx.x; it < nitems && !*abort_s; it += gridDim.x) {
-            const RowItem w = row_item(a, it);
+            const RowItem w = row_item(a, D, it);
             const int y0 = w.y0;
-            const TcFreqDev f = a.freqs[w.s];
+            const TcFreqDev f = D.freqs[w.s];
             const float unscale = ldexpf(f.unscale_row, e);
             const int gx = w.x0 + x;
             const bool xin = gx < a.W;
             const int u0 = f.u0, nu = a.nu_f;
             bool ok = true;
             for (int q = 0; q < nu; ++q, ++job) {
-                const TcUnitDev u = a.units[u0 + q];
+                const TcUnitDev u = D.units[u0 + q];
                 const int b = job & 1;
-                // row phases of the tile, lane l holds rows l and l + 32 (broadcast by shuffle)
-                const float2 py0 = (y0 + lane < a.H) ? __ldg(&u.phy[y0 + lane]) : make_float2(0.f, 0.f);
-                const float2 py1 = (y0 + 32 + lane < a.H) ? __ldg(&u.phy[y0 + 32 + lane]) : make_float2(0.f, 0.f);
+                // row phases of the warp's rows: lane l holds row rbase + l (broadcast by shuffle)
+                const int yl = y0 + rbase + lane;
+                const float2 pyl = (lane < TY / 2 && yl < a.H) ? __ldg(&u.phy[yl]) : make_float2(0.f, 0.f);
                 const float2 px = xin ? __ldg(&u.phx[gx]) : make_float2(0.f, 0.f);
                 if (!mbar_wait(&tmem_full[b], (job >> 1) & 1, abort_s)) {
                     ok = false;
@@ -311,41 +375,44 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const __grid_constant_
                 tc_fence_after();
                 const bool paired = u.plane_b >= 0;
                 const int64_t sstride = (int64_t)a.W * a.Hp;   // between signals of the unit
-                uint16_t *dst0 = a.sig + u.sig_idx * sstride + (int64_t)(xin ? gx : 0) * a.Hp + a.Lpad + y0;
+                const int64_t bstride = (int64_t)a.W * 8;      // between 8-row blocks
+                uint16_t *dst0 = a.sig + u.sig_idx * sstride + (int64_t)((a.Lpad + y0) >> 3) * bstride +
+                                 (int64_t)(xin ? gx : 0) * 8;
 #pragma unroll 1
-                for (int c0 = 0; c0 < 2 * TY; c0 += 16) {
+                for (int c0 = 2 * rbase; c0 < 2 * rbase + TY; c0 += 16) {
                     float v[16];
                     tmem_ld16(tmem + lane_base + 128u * b + c0, v);
                     const int r0 = c0 >> 1;
                     uint32_t pk[4][4];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int r = r0 + j;
-                        const float2 pyr = r < 32 ? py0 : py1;
-                        const float2 cy = make_float2(__shfl_sync(0xffffffffu, pyr.x, r & 31),
-                                                      __shfl_sync(0xffffffffu, pyr.y, r & 31));
-                        const float A = v[2 * j] * unscale, B = v[2 * j + 1] * unscale;
-                        // Eq. 5-6: Re J = cos A + sin B, Im J = sin A - cos B
-                        const float jr = fmaf(px.x, A, px.y * B), ji = fmaf(px.y, A, -px.x * B);
-                        // Eq. 10
-                        const float fcr = jr * cy.x, fsr = jr * cy.y, fci = ji * cy.x, fsi = ji * cy.y;
-                        const uint32_t s0 = h16(fcr + fsi), s1 = h16(fsr - fci);
-                        const uint32_t s2 = h16(fcr - fsi), s3 = h16(fsr + fci);
-                        if ((j & 1) == 0) {
-                            pk[0][j >> 1] = s0; pk[1][j >> 1] = s1; pk[2][j >> 1] = s2; pk[3][j >> 1] = s3;
-                        } else {
-                            pk[0][j >> 1] |= s0 << 16; pk[1][j >> 1] |= s1 << 16;
-                            pk[2][j >> 1] |= s2 << 16; pk[3][j >> 1] |= s3 << 16;
+                    for (int jp = 0; jp < 4; ++jp) {
+                        float sgl[2][4];
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) {
+                            const int j = 2 * jp + t;
+                            const int rl = r0 + j - rbase;
+                            const float2 cy = make_float2(__shfl_sync(0xffffffffu, pyl.x, rl),
+                                                          __shfl_sync(0xffffffffu, pyl.y, rl));
+                            const float A = v[2 * j] * unscale, B = v[2 * j + 1] * unscale;
+                            // Eq. 5-6: Re J = cos A + sin B, Im J = sin A - cos B
+                            const float jr = fmaf(px.x, A, px.y * B), ji = fmaf(px.y, A, -px.x * B);
+                            // Eq. 10
+                            const float fcr = jr * cy.x, fsr = jr * cy.y, fci = ji * cy.x, fsi = ji * cy.y;
+                            sgl[t][0] = fcr + fsi;
+                            sgl[t][1] = fsr - fci;
+                            sgl[t][2] = fcr - fsi;
+                            sgl[t][3] = fsr + fci;
                         }
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) pk[g][jp] = h2pack(sgl[0][g], sgl[1][g]);
                     }
                     if (xin) {
-                        *reinterpret_cast<uint4 *>(dst0 + r0) = make_uint4(pk[0][0], pk[0][1], pk[0][2], pk[0][3]);
-                        *reinterpret_cast<uint4 *>(dst0 + sstride + r0) = make_uint4(pk[1][0], pk[1][1], pk[1][2], pk[1][3]);
+                        uint16_t *d = dst0 + (int64_t)(r0 >> 3) * bstride;   // lanes: consecutive 16-byte blocks
+                        *reinterpret_cast<uint4 *>(d) = make_uint4(pk[0][0], pk[0][1], pk[0][2], pk[0][3]);
+                        *reinterpret_cast<uint4 *>(d + sstride) = make_uint4(pk[1][0], pk[1][1], pk[1][2], pk[1][3]);
                         if (paired) {
-                            *reinterpret_cast<uint4 *>(dst0 + 2 * sstride + r0) =
-                                make_uint4(pk[2][0], pk[2][1], pk[2][2], pk[2][3]);
-                            *reinterpret_cast<uint4 *>(dst0 + 3 * sstride + r0) =
-                                make_uint4(pk[3][0], pk[3][1], pk[3][2], pk[3][3]);
+                            *reinterpret_cast<uint4 *>(d + 2 * sstride) = make_uint4(pk[2][0], pk[2][1], pk[2][2], pk[2][3]);
+                            *reinterpret_cast<uint4 *>(d + 3 * sstride) = make_uint4(pk[3][0], pk[3][1], pk[3][2], pk[3][3]);
                         }
                     }
                 }
@@ -367,40 +434,43 @@ __global__ void __launch_bounds__(384, 1) k_gabor_tc_rows(const __grid_constant_
 
 // --------------------------------------------------------------------------- column pass
 // Items: (unit, x0, y0), sorted by frequency; paired units take 32 columns x 4 signals,
-// unpaired ones 64 columns x 2 signals (always 128 A rows).  The producers keep one job of
-// operand loads in flight ahead of the MMA.
-__global__ void __launch_bounds__(256, 1) k_gabor_tc_cols(const __grid_constant__ TcBankArgs a)
+// unpaired ones 64 columns x 2 signals (always 128 A rows).  The producers keep NST - 1 jobs
+// of operand loads in flight ahead of the MMA (NST A buffers).  Epilogue: every warp moves
+// its TMEM lane quarter (one signal for 32 columns) to shared memory and releases the
+// accumulator; then each warp remodulates 16 of the 64 rows for every column of the tile.
+__global__ void __launch_bounds__(512, 1) k_gabor_tc_cols(const __grid_constant__ TcBankArgs a)
 {
     const int nitems = a.nf * a.col_cnt;
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const ColSmem L = col_smem(a.col_kmax);
+    const int NST = a.col_nst;
+    const ColSmem L = col_smem(a.col_kmax, NST);
     unsigned char *sG = sm + L.g_off;
-    unsigned char *sA = sm + L.a_off;                 // [2] buffers of 128 x Kmax
-    float *xch = reinterpret_cast<float *>(sm + L.xch_off);
+    unsigned char *sA = sm + L.a_off;                 // [NST] buffers of 128 x Kmax
+    float *xch = reinterpret_cast<float *>(sm + L.xch_off);   // [4 quarters][64 rows][32 lanes]
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.bar_off);
-    uint64_t *tmem_full = bars;        // [2]
-    uint64_t *tmem_empty = bars + 2;   // [2] 4 epilogue warps
-    uint64_t *a_empty = bars + 4;      // [2] commit
-    uint64_t *drain = bars + 6;
+    uint64_t *tmem_full = bars;                  // [kColAcc] commit
+    uint64_t *tmem_empty = bars + kColAcc;       // [kColAcc] 8 epilogue warps
+    uint64_t *a_empty = bars + 2 * kColAcc;      // [kColMaxStages] commit
+    uint64_t *drain = bars + 2 * kColAcc + kColMaxStages;
     uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
     const uint32_t abuf = 128u * a.col_kmax * 2;
+    const TcDesc D = load_desc(a, sm + L.desc_off);
 
     if (tid == 0) {
-        mbar_init(&tmem_full[0], 1);
-        mbar_init(&tmem_full[1], 1);
-        mbar_init(&tmem_empty[0], 4);
-        mbar_init(&tmem_empty[1], 4);
-        mbar_init(&a_empty[0], 1);
-        mbar_init(&a_empty[1], 1);
+        for (int i = 0; i < kColAcc; ++i) {
+            mbar_init(&tmem_full[i], 1);
+            mbar_init(&tmem_empty[i], 8);
+        }
+        for (int i = 0; i < kColMaxStages; ++i) mbar_init(&a_empty[i], 1);
         mbar_init(drain, 1);
         *abort_s = 0;
         mbar_fence_init();
     }
     if (warp == 0) {
-        tmem_alloc(tmem_s, 128);
+        tmem_alloc(tmem_s, 64 * kColAcc);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -410,89 +480,98 @@ __global__ void __launch_bounds__(256, 1) k_gabor_tc_cols(const __grid_constant_
     const uint32_t idesc = idesc_f16(0, 128, kColTileY);
     const int njobs = nitems > (int)blockIdx.x ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
-    if (warp >= 4) {
+    if (warp >= 8) {
         // -------------------------------------------------------------- producers
-        const int ptid = tid - 128;
-        auto item = [&](int j) { return col_item(a, blockIdx.x + j * gridDim.x); };
+        constexpr int NP = 256;   // producer threads (warps 8-15)
+        const int ptid = tid - 256;
+        auto item = [&](int j) { return col_item(a, D, blockIdx.x + j * gridDim.x); };
         auto load_g = [&](int s) {
-            const TcFreqDev f = a.freqs[s];
+            const TcFreqDev f = D.freqs[s];
             const uint4 *src = reinterpret_cast<const uint4 *>(f.Bcol);
             uint4 *dst = reinterpret_cast<uint4 *>(sG);
-            for (int i = ptid; i < kColTileY * f.Kcol * 2 / 16; i += 128) dst[i] = src[i];
+            for (int i = ptid; i < kColTileY * f.Kcol * 2 / 16; i += NP) dst[i] = src[i];
         };
-        // cp.async of job j's A operand into buffer j & 1 (zero rows beyond the image).
+        // cp.async of job j's A operand into buffer j % NST (zero rows beyond the image).
+        // Thread ptid owns A row n = ptid % 128 (signal n / xw, column x0 + n % xw) and copies
+        // every second of its K / 8 16-byte chunks; a warp reads 32 consecutive columns of one
+        // 8-row block.
         auto issue = [&](int j) {
             const ColItem w = item(j);
-            const TcUnitDev u = a.units[w.unit];
-            const TcFreqDev f = a.freqs[u.s];
-            const int x0 = w.x0, y0 = w.y0, K = f.Kcol;
+            const TcUnitDev u = D.units[w.unit];
+            const TcFreqDev f = D.freqs[u.s];
             const int xw = u.plane_b >= 0 ? 32 : 64;
-            const int64_t lbase = (int64_t)a.Lpad + y0 - f.R8;
-            unsigned char *dstA = sA + (j & 1) * abuf;
-            const int kch = K / 8;
-            for (int ci = ptid; ci < 128 * kch; ci += 128) {
-                const int n = ci / kch, kc = ci - n * kch;
-                const int sgi = n / xw, x = n - sgi * xw;
-                const bool ok = x0 + x < a.W;
-                const uint16_t *src =
-                    a.sig + ((u.sig_idx + sgi) * a.W + (ok ? x0 + x : 0)) * a.Hp + lbase + 8 * kc;
-                const unsigned sdst = smem_u32(dstA + sw128_offset(128, n, 8 * kc));
+            const int n = ptid & 127, sgi = n / xw, x = w.x0 + n - sgi * xw;
+            const bool ok = x < a.W;
+            const int64_t bstride = (int64_t)a.W * 8;   // between 8-row blocks
+            const int64_t yb0 = ((int64_t)a.Lpad + w.y0 - f.R8) >> 3;   // first 8-row block of the window
+            const int kc0 = ptid >> 7;
+            const uint16_t *src = a.sig + (u.sig_idx + sgi) * ((int64_t)a.W * a.Hp) + (yb0 + kc0) * bstride +
+                                  (int64_t)(ok ? x : 0) * 8;
+            const unsigned sbase = smem_u32(sA + (j % NST) * abuf);
+            const int kch = f.Kcol / 8;
+            for (int kc = kc0; kc < kch; kc += 2, src += 2 * bstride) {
+                const unsigned sdst = sbase + sw128_offset(128, n, 8 * kc);
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sdst), "l"(src), "r"(ok ? 16 : 0)
                              : "memory");
             }
             cp_async_commit();
         };
-        auto freq_of = [&](int j) { return a.units[item(j).unit].s; };
-        if (njobs > 0) {
-            load_g(freq_of(0));
-            issue(0);
+        // every group count below is uniform: jobs past the end commit empty groups
+        for (int p = 0; p < NST - 1; ++p) {
+            if (p < njobs) issue(p);
+            else cp_async_commit();
         }
+        int cur_s = -1;
         for (int j = 0; j < njobs; ++j) {
-            if (named_barrier_or(1, 128, *abort_s != 0)) break;
-            const int sj = freq_of(j);
-            const bool has_next = j + 1 < njobs;
-            const bool same = has_next && freq_of(j + 1) == sj;
+            if (named_barrier_or(1, NP, *abort_s != 0)) break;
+            // G of job j's frequency: every earlier MMA must be done with the previous G
+            const int sj = D.units[item(j).unit].s;
             bool failed = false;
-            if (same) {
-                // buffer (j+1)&1 was read by job j-1's MMA
-                failed = j >= 1 && !mbar_wait(&a_empty[(j + 1) & 1], ((j - 1) >> 1) & 1, abort_s);
-                if (named_barrier_or(1, 128, failed)) {
-                    if (ptid == 0) fail_status(a.status, abort_s, 31);
+            if (sj != cur_s) {
+                failed = j >= 1 && !mbar_wait(&a_empty[(j - 1) % NST], ((j - 1) / NST) & 1, abort_s);
+                if (named_barrier_or(1, NP, failed)) {
+                    if (ptid == 0) fail_status(a.status, abort_s, 34);
                     break;
                 }
-                issue(j + 1);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
+                load_g(sj);
+                cur_s = sj;
             }
+            // job j's operand has landed (NST - 2 younger groups may still be in flight)
+            if (NST >= 3)
+                cp_async_wait<1>();
+            else
+                cp_async_wait<0>();
             fence_proxy_async_smem();
-            named_barrier(1, 128);
+            named_barrier(1, NP);
             if (ptid == 0) {
-                const int b = j & 1;
-                const TcFreqDev f = a.freqs[sj];
-                if (j >= 2 && !mbar_wait(&tmem_empty[b], ((j - 2) >> 1) & 1, abort_s)) {
+                const int b = j % kColAcc;
+                const TcFreqDev f = D.freqs[sj];
+                if (j >= kColAcc && !mbar_wait(&tmem_empty[b], ((j - kColAcc) / kColAcc) & 1, abort_s)) {
                     fail_status(a.status, abort_s, 32);
                 } else {
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(sA + b * abuf), g0 = smem_u32(sG);
+                    const uint32_t a0 = smem_u32(sA + (j % NST) * abuf), g0 = smem_u32(sG);
                     for (int kb = 0; kb < f.Kcol / 64; ++kb)
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)
                             tc_mma_f16(tmem + 64u * b, smem_desc_sw128(a0 + kb * 128 * 128) + 2 * kk,
                                        smem_desc_sw128(g0 + kb * kColTileY * 128) + 2 * kk, idesc, (kb | kk) != 0);
                     tc_commit(&tmem_full[b]);
-                    tc_commit(&a_empty[b]);
+                    tc_commit(&a_empty[j % NST]);
                 }
             }
-            if (has_next && !same) {
-                // frequency change: G and both buffers are free once job j's MMA completed
-                failed = !mbar_wait(&a_empty[j & 1], (j >> 1) & 1, abort_s);
-                if (named_barrier_or(1, 128, failed)) {
-                    if (ptid == 0) fail_status(a.status, abort_s, 34);
+            // refill: job j + NST - 1 goes into the buffer that job j - 1's MMA read (that MMA
+            // runs while job j's is queued behind it)
+            const int jn = j + NST - 1;
+            if (jn < njobs) {
+                failed = j >= 1 && !mbar_wait(&a_empty[(j - 1) % NST], ((j - 1) / NST) & 1, abort_s);
+                if (named_barrier_or(1, NP, failed)) {
+                    if (ptid == 0) fail_status(a.status, abort_s, 31);
                     break;
                 }
-                load_g(freq_of(j + 1));
-                issue(j + 1);
+                issue(jn);
+            } else {
+                cp_async_commit();
             }
         }
         cp_async_wait<0>();
@@ -505,72 +584,80 @@ __global__ void __launch_bounds__(256, 1) k_gabor_tc_cols(const __grid_constant_
         }
     } else {
         // -------------------------------------------------------------- epilogue
-        // D[n][y]: warp w holds rows 32w .. 32w+31.
-        //   paired:   warp 0 P, 1 Q (theta), 2 P', 3 Q' (pi - theta), x = lane
-        //   unpaired: warps 0-1 P (x = 32 (w & 1) + lane), warps 2-3 Q
-        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+        // D[n][y]: lane quarter q holds rows 32q .. 32q+31 of n.
+        //   paired:   quarter 0 P, 1 Q (theta), 2 P', 3 Q' (pi - theta), x = lane
+        //   unpaired: quarters 0-1 P (x = 32 q + lane), quarters 2-3 Q
+        // Warps w and w + 4 read quarter w & 3 (columns y split in halves); then warp w
+        // remodulates rows 8w .. 8w+7 of the tile.
+        const int quarter = warp & 3, half = warp >> 2;
+        const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
         for (int j = 0; j < njobs; ++j) {
-            const ColItem w = col_item(a, blockIdx.x + j * gridDim.x);
-            const TcUnitDev u = a.units[w.unit];
-            const TcFreqDev f = a.freqs[u.s];
-            const int x0 = w.x0, y0 = w.y0, b = j & 1;
+            const ColItem w = col_item(a, D, blockIdx.x + j * gridDim.x);
+            const TcUnitDev u = D.units[w.unit];
+            const TcFreqDev f = D.freqs[u.s];
+            const int x0 = w.x0, y0 = w.y0, b = j % kColAcc;
             const bool paired = u.plane_b >= 0;
-            const bool is_q = paired ? (warp & 1) : (warp >= 2);
-            const int slot = paired ? (warp >> 1) : (warp & 1);
-            // row phases: lane l holds rows y0 + l and y0 + 32 + l
-            const float2 py0 = (y0 + lane < a.H) ? __ldg(&u.phy[y0 + lane]) : make_float2(0.f, 0.f);
-            const float2 py1 = (y0 + 32 + lane < a.H) ? __ldg(&u.phy[y0 + 32 + lane]) : make_float2(0.f, 0.f);
-            const bool failed = !mbar_wait(&tmem_full[b], (j >> 1) & 1, abort_s);
-            if (named_barrier_or(2, 128, failed)) {
+            // row phases: lane l holds row y0 + 8 warp + (l & 7)
+            const int yr = y0 + 8 * warp + (lane & 7);
+            const float2 pyr = yr < a.H ? __ldg(&u.phy[yr]) : make_float2(0.f, 0.f);
+            const bool failed = !mbar_wait(&tmem_full[b], (j / kColAcc) & 1, abort_s);
+            if (named_barrier_or(2, 256, failed)) {
                 if (tid == 0) fail_status(a.status, abort_s, 33);
                 break;
             }
             tc_fence_after();
             const float unscale = f.unscale_col;
             const uint32_t tb = tmem + lane_base + 64u * b;
-            if (is_q) {
+            float *xq = xch + quarter * (kColTileY * 32) + lane;
 #pragma unroll 1
-                for (int c0 = 0; c0 < kColTileY; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(tb + c0, v);
+            for (int c0 = half * (kColTileY / 2); c0 < (half + 1) * (kColTileY / 2); c0 += 16) {
+                float v[16];
+                tmem_ld16(tb + c0, v);
 #pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) xch[(slot * kColTileY + c0 + jj) * 32 + lane] = v[jj] * unscale;
-                }
+                for (int jj = 0; jj < 16; ++jj) xq[(c0 + jj) * 32] = v[jj] * unscale;
             }
-            named_barrier(2, 128);
-            if (!is_q) {
-                const int x = x0 + (paired ? lane : 32 * slot + lane);
-                const int plane = paired ? (slot == 0 ? u.plane_a : u.plane_b) : u.plane_a;
-                float2 *o = a.out + (int64_t)plane * a.plane + x;
-#pragma unroll 1
-                for (int c0 = 0; c0 < kColTileY; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(tb + c0, v);
-#pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) {
-                        const int r = c0 + jj;
-                        const float2 pyr = r < 32 ? py0 : py1;
-                        const float tx = __shfl_sync(0xffffffffu, pyr.x, r & 31);
-                        const float ty = __shfl_sync(0xffffffffu, pyr.y, r & 31);
-                        const int yy = y0 + r;
-                        if (x < a.W && yy < a.H) {
-                            const float P = v[jj] * unscale;
-                            const float Q = xch[(slot * kColTileY + r) * 32 + lane];
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tmem_empty[b]);   // the accumulator is free again
+            named_barrier(2, 256);
+            const float *xr = xch + (8 * warp) * 32 + lane;
+#pragma unroll 4
+            for (int r = 0; r < 8; ++r) {
+                const int yy = y0 + 8 * warp + r;
+                const float tx = __shfl_sync(0xffffffffu, pyr.x, r);
+                const float ty = __shfl_sync(0xffffffffu, pyr.y, r);
+                if (yy < a.H) {
+                    if (paired) {
+                        const int x = x0 + lane;
+                        if (x < a.W) {
+                            const float P = xr[r * 32], Q = xr[(kColTileY + r) * 32];
+                            const float P2 = xr[(2 * kColTileY + r) * 32], Q2 = xr[(3 * kColTileY + r) * 32];
+                            float2 *o = a.out + (int64_t)yy * a.W + x;
                             // Eq. 7-8 (theta) and Eq. 15-16 (pi - theta)
-                            __stcs(o + (int64_t)yy * a.W, make_float2(fmaf(tx, P, ty * Q), fmaf(ty, P, -tx * Q)));
+                            __stcs(o + (int64_t)u.plane_a * a.plane, make_float2(fmaf(tx, P, ty * Q), fmaf(ty, P, -tx * Q)));
+                            __stcs(o + (int64_t)u.plane_b * a.plane,
+                                   make_float2(fmaf(tx, P2, ty * Q2), fmaf(ty, P2, -tx * Q2)));
+                        }
+                    } else {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int x = x0 + 32 * h + lane;
+                            if (x < a.W) {
+                                const float P = xr[(h * kColTileY + r) * 32], Q = xr[((2 + h) * kColTileY + r) * 32];
+                                __stcs(a.out + (int64_t)u.plane_a * a.plane + (int64_t)yy * a.W + x,
+                                       make_float2(fmaf(tx, P, ty * Q), fmaf(ty, P, -tx * Q)));
+                            }
                         }
                     }
                 }
             }
-            tc_fence_before();
-            named_barrier(2, 128);   // xch is free for the next job
-            if (lane == 0) mbar_arrive(&tmem_empty[b]);
+            named_barrier(2, 256);   // xch is free for the next job
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, 128);
+    if (warp == 0) tmem_dealloc(tmem, 64 * kColAcc);
 }
 
 // Largest |f| of the image as float bits (non-negative floats order like their integers).
@@ -614,12 +701,12 @@ TcGeometry gabor_tc_geometry(int R)
     g.Kcol = round_up(kColTileY + g.R8 + R, 64);
     g.PW = round_up(kRowTileX + 2 * R, 4);
     g.smem_rows = 1024 + row_smem(g.Krow, g.PW, kRowTileYMax / 2).total;
-    g.smem_cols = 1024 + col_smem(g.Kcol).total;
+    g.smem_cols = col_stages(g.Kcol) ? 1024 + col_smem(g.Kcol, col_stages(g.Kcol)).total : (size_t)kSmemLimit + 1;
     return g;
 }
 
 size_t gabor_tc_smem_rows(int Kmax, int PWmax, int TY) { return 1024 + row_smem(Kmax, PWmax, TY).total; }
-size_t gabor_tc_smem_cols(int Kmax) { return 1024 + col_smem(Kmax).total; }
+size_t gabor_tc_smem_cols(int Kmax) { return 1024 + col_smem(Kmax, col_stages(Kmax)).total; }
 
 bool gabor_tc_supported(int R)
 {
@@ -659,8 +746,11 @@ cudaError_t gabor_tc_prepare()
     return e;
 }
 
-cudaError_t launch_gabor_tc(const TcBankArgs &a, int sm_count, cudaStream_t st)
+cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
 {
+    TcBankArgs a = a0;
+    a.col_nst = col_stages(a.col_kmax);
+    if (a.col_nst < 2) return cudaErrorInvalidValue;
     const int n_row_items = a.nf * a.row_cnt, n_col_items = a.nf * a.col_cnt;
     const size_t smem_r = gabor_tc_smem_rows(a.row_kmax, a.row_pwmax, a.row_ty);
     const size_t smem_c = gabor_tc_smem_cols(a.col_kmax);
@@ -671,12 +761,12 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a, int sm_count, cudaStream_t st)
     e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
     if (n_row_items > 0) {
-        k_gabor_tc_rows<<<std::min(n_row_items, sm_count), 384, smem_r, st>>>(a);
+        k_gabor_tc_rows<<<std::min(n_row_items, sm_count), 512, smem_r, st>>>(a);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (n_col_items > 0) {
-        k_gabor_tc_cols<<<std::min(n_col_items, sm_count), 256, smem_c, st>>>(a);
+        k_gabor_tc_cols<<<std::min(n_col_items, sm_count), 512, smem_c, st>>>(a);
         return cudaGetLastError();
     }
     return cudaSuccess;

@@ -96,7 +96,7 @@ struct TcBankArgs {
     int H, W;
     float2 *out;
     int64_t plane;
-    uint16_t *sig;         // intermediate: [unit][signal][x][Hp], image row y at Lpad + y
+    uint16_t *sig;         // intermediate: [signal][Hp / 8][W][8], image row y at Lpad + y
     int64_t Hp;
     int Lpad, pad_;
     const TcFreqDev *freqs;
@@ -110,6 +110,8 @@ struct TcBankArgs {
     int nf, nu_f, np_f;
     int row_nx, row_cnt;   // row pass: 128-column tiles per tile row, items per frequency
     int col_ny, col_nx32, col_nx64, col_cnt;   // column pass: 64-row tiles, x tiles, items per frequency
+    int col_nst;           // A-operand buffers of the column kernel (set by the launcher)
+    int pad2_;
 };
 struct TcGeometry {
     int R, R8, Krow, Kcol, PW;
