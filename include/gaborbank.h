@@ -173,6 +173,16 @@ gb_status gabor_bank_set_tiling(gabor_bank_t h, int s, int tile_rows, int segmen
 gb_status gabor_bank_device_status(gabor_bank_t h, void *stream);
 
 /*
+ * gabor_fp32_fma_probe - FP32 CUDA-core throughput probe (the measured peak that the FP32
+ * bank's roofline fraction divides by; the paper has no counterpart).  Enqueues `blocks` CTAs
+ * of 256 threads on the current device; every thread runs 16 independent FMA chains for
+ * `iters` iterations: 32 * iters FLOP per thread, scalar fmaf (packed = 0) or packed FP32x2
+ * FMA (packed = 1).  d_out: a device float the kernel may write.  Time it with CUDA events.
+ * Asynchronous.  GB_ERR_INVALID_ARG on NULL or non-positive arguments.
+ */
+gb_status gabor_fp32_fma_probe(void *d_out, int blocks, int iters, int packed, void *stream);
+
+/*
  * gabor_bank_selftest_wait - failure-detection self-test of the bounded device waits.  Enqueues
  * a one-warp kernel whose thread 0 waits on a shared-memory mbarrier with the same bounded
  * wait the tensor-core kernels use.  signal = 1: the barrier is signalled first and the wait

@@ -44,6 +44,7 @@ SIGNATURES = {
     "gabor_bank_version": (ctypes.c_char_p, []),
     "gabor_sdft_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_i64, _c_dbl, _c_int, _c_int, _c_int, _vp, _vp]),
     "gabor_bank_selftest_wait": (_c_int, [_vp, _c_int, _c_dbl, _vp]),
+    "gabor_fp32_fma_probe": (_c_int, [_vp, _c_int, _c_int, _c_int, _vp]),
     "gabor_bank_workspace_bytes": (_c_i64, [_vp, _c_int, _c_int]),
     "gabor_bank_set_workspace": (_c_int, [_vp, _vp, _c_i64]),
     "gabor_arena_create": (_c_int, [ctypes.POINTER(_vp), _c_i64]),
@@ -297,6 +298,33 @@ class Arena:
             self.close()
         except Exception:
             pass
+
+
+def fp32_fma_peak(iters=4096, waves=8, steps=5):
+    """Measured FP32 CUDA-core throughput (TFLOP/s) of the library's FMA probe on the current
+    device: {"scalar": ..., "packed": ..., "peak": max of the two}."""
+    import torch
+    lib = load_library()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = sms * waves   # 8 CTAs of 256 threads fill an SM's 64 warps
+    out = torch.zeros(1, dtype=torch.float32, device="cuda")
+    st = _stream_handle(None)
+    res = {}
+    for name, packed in (("scalar", 0), ("packed", 1)):
+        _check(lib.gabor_fp32_fma_probe(ctypes.c_void_p(out.data_ptr()), blocks, iters, packed, st))
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            _check(lib.gabor_fp32_fma_probe(ctypes.c_void_p(out.data_ptr()), blocks, iters, packed, st))
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+        res[name] = blocks * 256 * 32.0 * iters / (best * 1e-3) / 1e12
+    res["peak"] = max(res["scalar"], res["packed"])
+    return res
 
 
 def capture_graph(fn, warmup=1):

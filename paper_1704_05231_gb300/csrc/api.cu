@@ -911,6 +911,15 @@ gb_status gabor_bank_device_status(gabor_bank_t h, void *stream)
     return GB_OK;
 }
 
+gb_status gabor_fp32_fma_probe(void *d_out, int blocks, int iters, int packed, void *stream)
+{
+    if (!d_out || blocks <= 0 || iters <= 0 || (packed != 0 && packed != 1))
+        return fail(GB_ERR_INVALID_ARG, "bad probe arguments");
+    GB_TRY(check_sticky());
+    GB_CU(launch_fma_peak(static_cast<float *>(d_out), blocks, iters, packed, static_cast<cudaStream_t>(stream)));
+    return GB_OK;
+}
+
 gb_status gabor_bank_selftest_wait(gabor_bank_t h, int signal, double limit_ms, void *stream)
 {
     if (!h) return fail(GB_ERR_INVALID_ARG, "NULL handle");

@@ -172,6 +172,8 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a, int sm_count, cudaStream_t st);
 int gabor_tc_row_tile_x();
 int gabor_tc_row_tile_y(int Rmax);
 int gabor_tc_col_tile_y();
+// FP32 FMA throughput probe (peak.cu).
+cudaError_t launch_fma_peak(float *out, int blocks, int iters, int packed, cudaStream_t st);
 // Bounded-wait self-test (selftest.cu).
 cudaError_t launch_wait_selftest(int *status, int signal, unsigned long long limit_ns, cudaStream_t st);
 // Sets the message returned by gabor_bank_last_error() on the calling host thread.
