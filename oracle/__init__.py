@@ -67,6 +67,10 @@ def _load():
                 _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                 _ip, _ip, ctypes.c_long, _dp, ctypes.c_int]
+            lib.oracle_gabor_direct_b.restype = ctypes.c_int
+            lib.oracle_gabor_direct_b.argtypes = lib.oracle_gabor_direct.argtypes + [ctypes.c_int]
+            lib.oracle_sdft_direct_b.restype = ctypes.c_int
+            lib.oracle_sdft_direct_b.argtypes = lib.oracle_sdft_direct.argtypes + [ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -109,12 +113,17 @@ def radius(sigma, radius_factor=3.0):
     return _load().oracle_radius(float(sigma), float(radius_factor))
 
 
+BOUNDARY = {"zero": 0, "replicate": 1, "mirror": 2}
+
+
 def gabor_filter(img, omega, theta, sigma, radius_factor=3.0, support=None, points=None,
-                 threads=0):
+                 threads=0, boundary="zero"):
     """One 2-D complex Gabor output F_{omega,theta,sigma} by the direct sum of Eq. 1.
 
     support: optional ((dx_lo, dx_hi), (dy_lo, dy_hi)) for dx = x-k, dy = y-l; the default
     is the square |dx|, |dy| <= R.  points: optional (xs, ys) to evaluate a subset.
+    boundary: how the image extends beyond its edges: 'zero', 'replicate' (edge pixel
+    repeated) or 'mirror' (mirrored about the pixel edges, f(-1) = f(0)).
     Returns complex128 (H, W), or (npts,) with points.
     """
     lib = _load()
@@ -128,20 +137,23 @@ def gabor_filter(img, omega, theta, sigma, radius_factor=3.0, support=None, poin
     xs, ys, n = _points(points)
     nout = n if xs is not None else H * W
     out = np.empty(2 * nout, dtype=np.float64)
-    rc = lib.oracle_gabor_direct(_ptr(re), _ptr(im), H, W, float(omega), float(theta),
-                                 float(sigma), int(xl), int(xh), int(yl), int(yh),
-                                 _ptr(xs, _ip), _ptr(ys, _ip), n, _ptr(out), int(threads))
+    rc = lib.oracle_gabor_direct_b(_ptr(re), _ptr(im), H, W, float(omega), float(theta),
+                                   float(sigma), int(xl), int(xh), int(yl), int(yh),
+                                   _ptr(xs, _ip), _ptr(ys, _ip), n, _ptr(out), int(threads),
+                                   BOUNDARY[boundary])
     if rc != 0:
         raise ValueError(f"oracle_gabor_direct failed ({rc})")
     out = out.view(np.complex128)
     return out if xs is not None else out.reshape(H, W)
 
 
-def gabor_bank(img, thetas, omegas, sigmas, radius_factor=3.0, points=None, threads=0):
+def gabor_bank(img, thetas, omegas, sigmas, radius_factor=3.0, points=None, threads=0,
+               boundary="zero"):
     """The bank of Algorithm 1's output: complex128 [n_freq][n_theta][H][W] (or [..][npts])."""
     res = []
     for om, sg in zip(omegas, sigmas):
-        res.append([gabor_filter(img, om, th, sg, radius_factor, points=points, threads=threads)
+        res.append([gabor_filter(img, om, th, sg, radius_factor, points=points, threads=threads,
+                                 boundary=boundary)
                     for th in thetas])
     return np.array(res)
 
@@ -173,12 +185,12 @@ def gabor_cols(J, omega, theta, sigma, radius_factor=3.0, threads=0):
     return out.view(np.complex128).reshape(H, W)
 
 
-def sdft(img, sigma, My, Mx=None, support=None, points=None, threads=0):
+def sdft(img, sigma, My, Mx=None, support=None, points=None, threads=0, boundary="zero"):
     """The 2-D localized SDFT of Eq. 17 by direct summation.
 
     Returns complex128 [My][Mx][H][W] (or [My][Mx][npts]); bin [v][u] has u along x.
     support: optional ((a_lo, a_hi), (b_lo, b_hi)) window offsets from (xhat, yhat); the
-    default is the M_x x M_y window [0, Mx) x [0, My).
+    default is the M_x x M_y window [0, Mx) x [0, My).  boundary as in gabor_filter.
     """
     lib = _load()
     Mx = My if Mx is None else Mx
@@ -191,9 +203,9 @@ def sdft(img, sigma, My, Mx=None, support=None, points=None, threads=0):
     xs, ys, n = _points(points)
     nout = n if xs is not None else H * W
     out = np.empty(2 * nout * Mx * My, dtype=np.float64)
-    rc = lib.oracle_sdft_direct(_ptr(re), _ptr(im), H, W, float(sigma), int(My), int(Mx),
-                                int(al), int(ah), int(bl), int(bh), _ptr(xs, _ip), _ptr(ys, _ip),
-                                n, _ptr(out), int(threads))
+    rc = lib.oracle_sdft_direct_b(_ptr(re), _ptr(im), H, W, float(sigma), int(My), int(Mx),
+                                  int(al), int(ah), int(bl), int(bh), _ptr(xs, _ip), _ptr(ys, _ip),
+                                  n, _ptr(out), int(threads), BOUNDARY[boundary])
     if rc != 0:
         raise ValueError(f"oracle_sdft_direct failed ({rc})")
     out = out.view(np.complex128)

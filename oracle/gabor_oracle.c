@@ -22,7 +22,9 @@
  *   - S_sigma(d) = exp(-d^2 / (2 sigma^2)) / (sqrt(2 pi) sigma), the sampled continuous
  *     density, not renormalised after truncation (the paper only says "Gaussian with zero
  *     mean and standard deviation sigma", Sec. II).
- *   - The image is zero outside [0,W) x [0,H); the output has the input's size.
+ *   - The image is zero outside [0,W) x [0,H) (boundary 0); boundary 1 extends it by
+ *     repeating the edge pixel, boundary 2 by mirroring about the pixel edges (f(-1) = f(0),
+ *     f(W) = f(W-1), period 2W).  The output has the input's size.
  *   - Gabor support: |x-k| <= R and |y-l| <= R with R = ceil(rf * sigma - 1e-9), rf = 3
  *     by default (the cut-off of Sec. III applied to the Gabor filter as well).
  *   - SDFT support: the M_x x M_y window, m - xhat in [0, M_x), n - yhat in [0, M_y), with
@@ -52,6 +54,20 @@ int oracle_radius(double sigma, double rf)
     return (int)ceil(rf * sigma - 1e-9);
 }
 
+/* Index of the image sample that position i (of n) reads under the boundary rule, or -1 for
+ * a zero sample. */
+static int ext_index(int i, int n, int boundary)
+{
+    if (i >= 0 && i < n) return i;
+    if (boundary == 1) return i < 0 ? 0 : n - 1;
+    if (boundary == 2) {
+        int m = i % (2 * n);
+        if (m < 0) m += 2 * n;
+        return m < n ? m : 2 * n - 1 - m;
+    }
+    return -1;
+}
+
 static void set_threads(int nthreads)
 {
 #ifdef _OPENMP
@@ -71,13 +87,14 @@ static void set_threads(int nthreads)
  * px/py: npts output pixel coordinates, or NULL for all H*W pixels in row-major order.
  * out:   2*n doubles, (re, im) interleaved.
  */
-int oracle_gabor_direct(const double *f_re, const double *f_im, int H, int W,
-                        double omega, double theta, double sigma,
-                        int dx_lo, int dx_hi, int dy_lo, int dy_hi,
-                        const int *px, const int *py, long npts,
-                        double *out, int nthreads)
+int oracle_gabor_direct_b(const double *f_re, const double *f_im, int H, int W,
+                          double omega, double theta, double sigma,
+                          int dx_lo, int dx_hi, int dy_lo, int dy_hi,
+                          const int *px, const int *py, long npts,
+                          double *out, int nthreads, int boundary)
 {
     if (H <= 0 || W <= 0 || sigma <= 0.0 || dx_hi < dx_lo || dy_hi < dy_lo) return -1;
+    if (boundary < 0 || boundary > 2) return -1;
     const int nx = dx_hi - dx_lo + 1, ny = dy_hi - dy_lo + 1;
     double *kr = (double *)malloc(sizeof(double) * (size_t)nx * ny);
     double *ki = (double *)malloc(sizeof(double) * (size_t)nx * ny);
@@ -101,11 +118,11 @@ int oracle_gabor_direct(const double *f_re, const double *f_im, int H, int W,
         const int y = px ? py[p] : (int)(p / W);
         double sr = 0.0, si = 0.0;
         for (int j = 0; j < ny; ++j) {
-            const int l = y - (dy_lo + j);
-            if (l < 0 || l >= H) continue;
+            const int l = ext_index(y - (dy_lo + j), H, boundary);
+            if (l < 0) continue;
             for (int i = 0; i < nx; ++i) {
-                const int k = x - (dx_lo + i);
-                if (k < 0 || k >= W) continue;
+                const int k = ext_index(x - (dx_lo + i), W, boundary);
+                if (k < 0) continue;
                 const double a = f_re[(size_t)l * W + k];
                 const double b = f_im ? f_im[(size_t)l * W + k] : 0.0;
                 const double cr = kr[(size_t)j * nx + i], ci = ki[(size_t)j * nx + i];
@@ -119,6 +136,16 @@ int oracle_gabor_direct(const double *f_re, const double *f_im, int H, int W,
     free(kr);
     free(ki);
     return 0;
+}
+
+int oracle_gabor_direct(const double *f_re, const double *f_im, int H, int W,
+                        double omega, double theta, double sigma,
+                        int dx_lo, int dx_hi, int dy_lo, int dy_hi,
+                        const int *px, const int *py, long npts,
+                        double *out, int nthreads)
+{
+    return oracle_gabor_direct_b(f_re, f_im, H, W, omega, theta, sigma, dx_lo, dx_hi, dy_lo, dy_hi,
+                                 px, py, npts, out, nthreads, 0);
 }
 
 /*
@@ -193,14 +220,14 @@ int oracle_gabor_cols(const double *J, int H, int W,
  *
  * out: [My][Mx][n][2] doubles, n = npts or H*W.
  */
-int oracle_sdft_direct(const double *f_re, const double *f_im, int H, int W,
-                       double sigma, int My, int Mx,
-                       int a_lo, int a_hi, int b_lo, int b_hi,
-                       const int *px, const int *py, long npts,
-                       double *out, int nthreads)
+int oracle_sdft_direct_b(const double *f_re, const double *f_im, int H, int W,
+                         double sigma, int My, int Mx,
+                         int a_lo, int a_hi, int b_lo, int b_hi,
+                         const int *px, const int *py, long npts,
+                         double *out, int nthreads, int boundary)
 {
     if (H <= 0 || W <= 0 || sigma <= 0.0 || Mx <= 0 || My <= 0 || (Mx & 1) || (My & 1)
-        || a_hi < a_lo || b_hi < b_lo)
+        || a_hi < a_lo || b_hi < b_lo || boundary < 0 || boundary > 2)
         return -1;
     const int na = a_hi - a_lo + 1, nb = b_hi - b_lo + 1;
     const size_t nw = (size_t)na * nb;
@@ -234,11 +261,11 @@ int oracle_sdft_direct(const double *f_re, const double *f_im, int H, int W,
                 double sr = 0.0, si = 0.0;
                 const size_t base = ((size_t)v * Mx + u) * nw;
                 for (int j = 0; j < nb; ++j) {
-                    const int yy = yh + b_lo + j;
-                    if (yy < 0 || yy >= H) continue;
+                    const int yy = ext_index(yh + b_lo + j, H, boundary);
+                    if (yy < 0) continue;
                     for (int i = 0; i < na; ++i) {
-                        const int xx = xh + a_lo + i;
-                        if (xx < 0 || xx >= W) continue;
+                        const int xx = ext_index(xh + a_lo + i, W, boundary);
+                        if (xx < 0) continue;
                         const double a = f_re[(size_t)yy * W + xx];
                         const double b = f_im ? f_im[(size_t)yy * W + xx] : 0.0;
                         const double cr = wr[base + (size_t)j * na + i];
@@ -255,4 +282,14 @@ int oracle_sdft_direct(const double *f_re, const double *f_im, int H, int W,
     free(wr);
     free(wi);
     return 0;
+}
+
+int oracle_sdft_direct(const double *f_re, const double *f_im, int H, int W,
+                       double sigma, int My, int Mx,
+                       int a_lo, int a_hi, int b_lo, int b_hi,
+                       const int *px, const int *py, long npts,
+                       double *out, int nthreads)
+{
+    return oracle_sdft_direct_b(f_re, f_im, H, W, sigma, My, Mx, a_lo, a_hi, b_lo, b_hi, px, py, npts,
+                                out, nthreads, 0);
 }

@@ -292,3 +292,48 @@ def test_points_subset_matches_full():
     D = oracle.sdft(f, 1.5, 8)
     Dp = oracle.sdft(f, 1.5, 8, points=(xs, ys))
     assert np.array_equal(Dp, D[:, :, ys, xs])
+
+
+# ---------------------------------------------------------------- boundary modes
+# The boundary rule is the image extension; with it the filter is the zero-padded filter of
+# the explicitly extended image (numpy.pad: 'edge' = replicate, 'symmetric' = mirror about the
+# pixel edges), cropped.  Padding wider than the image (R > W) checks the periodic mirror.
+_PAD = {"replicate": "edge", "mirror": "symmetric"}
+
+
+@pytest.mark.parametrize("boundary", ["replicate", "mirror"])
+@pytest.mark.parametrize("H,W,sigma", [(12, 17, 1.5), (5, 3, 2.5)])
+def test_boundary_equals_zero_padded_extended_image(boundary, H, W, sigma):
+    rng = np.random.default_rng(31)
+    img = rng.random((H, W))
+    R = oracle.radius(sigma)
+    ext = np.pad(img, R, mode=_PAD[boundary])
+    for theta, omega in [(0.3, 0.9), (2.0, 0.4)]:
+        got = oracle.gabor_filter(img, omega, theta, sigma, boundary=boundary)
+        ref = oracle.gabor_filter(ext, omega, theta, sigma)[R:R + H, R:R + W]
+        assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("boundary", ["replicate", "mirror"])
+def test_boundary_constant_image_is_the_interior_closed_form(boundary):
+    # An extended constant image is constant everywhere, so every pixel (border included)
+    # sees the same sum: F = c * Ghat_R(-w cos t) Ghat_R(-w sin t).
+    c, omega, theta, sigma = 0.7, 0.8, 0.45, 2.0
+    R = oracle.radius(sigma)
+    d = np.arange(-R, R + 1)
+    g = np.array([oracle.gauss(k, sigma) for k in d])
+    gx = np.sum(g * np.exp(1j * omega * np.cos(theta) * d))
+    gy = np.sum(g * np.exp(1j * omega * np.sin(theta) * d))
+    got = oracle.gabor_filter(np.full((9, 11), c), omega, theta, sigma, boundary=boundary)
+    assert np.max(np.abs(got - c * gx * gy)) <= 1e-13
+
+
+@pytest.mark.parametrize("boundary", ["replicate", "mirror"])
+def test_sdft_boundary_equals_zero_padded_extended_image(boundary):
+    rng = np.random.default_rng(32)
+    img = rng.random((10, 13))
+    M = 8
+    ext = np.pad(img, M, mode=_PAD[boundary])
+    got = oracle.sdft(img, 2.0, M, boundary=boundary)
+    ref = oracle.sdft(ext, 2.0, M)[:, :, M:M + 10, M:M + 13]
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
