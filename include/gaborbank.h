@@ -150,8 +150,26 @@ typedef enum {
     /* Rows per streamed chunk in the FP32 bank kernel: 0 = automatic, else 16, 32 or 64. */
     GB_OPT_TILE_ROWS = 2,
     /* Row segments per image column strip: 0 = automatic, else 1 .. 64. */
-    GB_OPT_SEGMENTS = 3
+    GB_OPT_SEGMENTS = 3,
+    /* How the image extends beyond its edges (gb_boundary; default GB_BOUNDARY_ZERO).  Applies
+       to gabor_bank_filter, _filter_host, _filter_batch and gabor_bank_sdft. */
+    GB_OPT_BOUNDARY = 4,
+    /* Bank output layout (gb_layout; default GB_LAYOUT_PLANES). */
+    GB_OPT_LAYOUT = 5
 } gb_option;
+
+/* Image extension rules (GB_OPT_BOUNDARY).  The paper leaves the border unstated. */
+typedef enum {
+    GB_BOUNDARY_ZERO = 0,      /* f = 0 outside [0, W) x [0, H) */
+    GB_BOUNDARY_REPLICATE = 1, /* the nearest edge pixel */
+    GB_BOUNDARY_MIRROR = 2     /* mirrored about the pixel edges: f(-1) = f(0), f(W) = f(W-1), period 2W */
+} gb_boundary;
+
+/* Bank output layouts (GB_OPT_LAYOUT); both hold n_freq * n_theta * H * W complex64. */
+typedef enum {
+    GB_LAYOUT_PLANES = 0,      /* out[s][k][y][x]: one H x W plane per filter */
+    GB_LAYOUT_PIXELS = 1       /* out[y][x][s][k]: the n_freq x n_theta feature vector of each pixel */
+} gb_layout;
 
 /* gabor_bank_set_option - set an option; GB_ERR_INVALID_ARG on an unknown key or value. */
 gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value);

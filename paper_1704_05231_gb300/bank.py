@@ -20,7 +20,9 @@ STATUS = {0: "GB_OK", -1: "GB_ERR_INVALID_ARG", -2: "GB_ERR_OUT_OF_MEMORY", -3: 
           -4: "GB_ERR_UNSUPPORTED", -5: "GB_ERR_BUDGET", -6: "GB_ERR_TIMEOUT"}
 STATUS_CODE = {v: k for k, v in STATUS.items()}
 PRECISION = {"fp32": 0, "fp16_tc": 1, "bf16_tc": 2}
-OPTION = {"reuse": 1, "tile_rows": 2, "segments": 3}
+OPTION = {"reuse": 1, "tile_rows": 2, "segments": 3, "boundary": 4, "layout": 5}
+BOUNDARY = {"zero": 0, "replicate": 1, "mirror": 2}
+LAYOUT = {"planes": 0, "pixels": 1}
 
 # Every entry point the header declares, with its ctypes signature.
 _c_int, _c_dbl, _c_i64, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p
@@ -104,11 +106,12 @@ class GaborBank:
 
     thetas: orientations (rad); omegas, sigmas: one (omega, sigma) per frequency.
     precision: 'fp32', 'fp16_tc' or 'bf16_tc'.  An empty bank (no thetas / omegas) makes an
-    SDFT-only handle.
+    SDFT-only handle.  boundary: 'zero', 'replicate' or 'mirror' (image extension); layout:
+    'planes' (out[s][k][y][x]) or 'pixels' (out[y][x][s][k]).
     """
 
     def __init__(self, thetas=(), omegas=(), sigmas=(), radius_factor=3.0, precision="fp32",
-                 max_shape=(0, 0)):
+                 max_shape=(0, 0), boundary="zero", layout="planes"):
         lib = load_library()
         if len(omegas) != len(sigmas):
             raise ValueError("omegas and sigmas must have the same length")
@@ -123,6 +126,12 @@ class GaborBank:
                                      PRECISION[precision], int(max_shape[0]), int(max_shape[1])))
         self._h = h
         self._lib = lib
+        self.layout = "planes"
+        if boundary != "zero":
+            self.set_option("boundary", BOUNDARY[boundary])
+        if layout != "planes":
+            self.set_option("layout", LAYOUT[layout])
+            self.layout = layout
 
     # -- lifecycle
     def close(self):
@@ -147,8 +156,14 @@ class GaborBank:
         return self._h
 
     def set_option(self, key, value):
+        if key == "boundary" and isinstance(value, str):
+            value = BOUNDARY[value]
+        if key == "layout" and isinstance(value, str):
+            value = LAYOUT[value]
         _check(self._lib.gabor_bank_set_option(self._h, OPTION[key] if isinstance(key, str) else int(key),
                                                int(value)))
+        if key in ("layout", OPTION["layout"]):
+            self.layout = "pixels" if int(value) == 1 else "planes"
 
     def set_tiling(self, s, tile_rows, segments):
         """FP32 kernel tile geometry for frequency s (-1: all); 0 means automatic."""
@@ -171,6 +186,8 @@ class GaborBank:
 
     # -- shapes
     def out_shape(self, H, W):
+        if self.layout == "pixels":
+            return (H, W, len(self.omegas), len(self.thetas))
         return (len(self.omegas), len(self.thetas), H, W)
 
     # -- compute

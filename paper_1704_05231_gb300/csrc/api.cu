@@ -118,6 +118,11 @@ void build_plan(gabor_bank *h)
         f.u1 = (int)h->units.size();
         h->freqs.push_back(f);
     }
+    // Phase tables also cover the positions a non-zero boundary rule reads beyond the image:
+    // up to R + 128 columns (a 128-column tensor-core tile plus its halo) and rows.
+    int rmax = 0;
+    for (const Freq &f : h->freqs) rmax = std::max(rmax, f.R);
+    h->ph_margin = (rmax + 63) / 64 * 64 + 128;
 }
 
 void free_tables(gabor_bank *h)
@@ -155,8 +160,9 @@ gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
     GB_TRY(dalloc(&h->d_lo, (size_t)nf));
     GB_TRY(dalloc(&h->d_T, (size_t)nf));
     GB_TRY(dalloc(&h->d_taps, (size_t)nf * h->tpad_max));
-    GB_TRY(dalloc(&h->d_phx, (size_t)nu * Wcap));
-    GB_TRY(dalloc(&h->d_phy, (size_t)nu * Hcap));
+    const int mg = h->ph_margin;
+    GB_TRY(dalloc(&h->d_phx, (size_t)nu * (Wcap + 2 * mg)));
+    GB_TRY(dalloc(&h->d_phy, (size_t)nu * (Hcap + 2 * mg)));
     GB_TRY(dalloc(&h->d_unitdev, (size_t)nu));
     GB_TRY(dalloc(&h->d_freqdev, (size_t)nf));
     std::vector<double> w(2 * nu), sg(nf);
@@ -166,8 +172,8 @@ gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
         w[2 * i] = h->units[i].wc / M_PI;
         w[2 * i + 1] = h->units[i].ws / M_PI;
         const int K = (int)h->theta.size();
-        ud[i].phx = h->d_phx + (size_t)i * Wcap;
-        ud[i].phy = h->d_phy + (size_t)i * Hcap;
+        ud[i].phx = h->d_phx + (size_t)i * (Wcap + 2 * mg) + mg;
+        ud[i].phy = h->d_phy + (size_t)i * (Hcap + 2 * mg) + mg;
         ud[i].s = h->units[i].s;
         ud[i].pad_ = 0;
         ud[i].plane_a = h->units[i].s * K + h->units[i].k_a;
@@ -194,7 +200,7 @@ gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
     }
     GB_CU(cudaMemcpy(h->d_freqdev, h->freqdev.data(), nf * sizeof(FreqDev), cudaMemcpyHostToDevice));
     GB_CU(launch_build_taps(h->d_sigma, h->d_lo, h->d_T, nf, h->tpad_max, h->d_taps, st));
-    GB_CU(launch_build_gabor_tables(h->d_unit_w, nu, Wcap, Hcap, h->d_phx, h->d_phy, st));
+    GB_CU(launch_build_gabor_tables(h->d_unit_w, nu, Wcap, Hcap, mg, h->d_phx, h->d_phy, st));
     h->Wcap = Wcap;
     h->Hcap = Hcap;
     h->tables_ready = true;
@@ -376,7 +382,8 @@ void free_tc(gabor_bank *h)
     dfree(h->d_tcunit);
     dfree(h->d_tcsig);
     dfree(h->d_tcforder);
-    dfree(h->d_tcabsmax);
+    dfree(h->d_tcminmax);
+    dfree(h->d_tcpre);
     h->tcsig_elems = 0;
     h->tc_H = h->tc_W = 0;
     h->tc_ready = false;
@@ -398,6 +405,13 @@ int64_t tc_sig_elems(const gabor_bank *h, int H, int W)
     int64_t nsig = 0;
     for (const Unit &u : h->units) nsig += u.k_b >= 0 ? 4 : 2;
     return nsig * W * Hp;
+}
+
+// Workspace bytes of a tensor-core call: the intermediate signals, then the F[1] tables A, B.
+int64_t tc_sig_bytes(const gabor_bank *h, int H, int W) { return (tc_sig_elems(h, H, W) * 2 + 255) / 256 * 256; }
+int64_t tc_ws_bytes(const gabor_bank *h, int H, int W)
+{
+    return tc_sig_bytes(h, H, W) + (int64_t)h->units.size() * ((int64_t)W + H) * (int64_t)sizeof(float2);
 }
 
 gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
@@ -430,7 +444,7 @@ gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
     GB_TRY(dalloc(&h->d_tcB, total));
     GB_TRY(dalloc(&h->d_tcfreq, (size_t)nf));
     GB_TRY(dalloc(&h->d_tcforder, (size_t)nf));
-    GB_TRY(dalloc(&h->d_tcabsmax, (size_t)1));
+    GB_TRY(dalloc(&h->d_tcminmax, (size_t)2));
     GB_TRY(dalloc(&h->d_tcunit, (size_t)nu));
     std::vector<TcFreqDev> fd(nf);
     for (int s = 0; s < nf; ++s) {
@@ -449,8 +463,8 @@ gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
     for (int i = 0; i < nu; ++i) {
         const Unit &un = h->units[i];
         const bool paired = un.k_b >= 0;
-        ud[i].phx = h->d_phx + (size_t)i * h->Wcap;
-        ud[i].phy = h->d_phy + (size_t)i * h->Hcap;
+        ud[i].phx = h->d_phx + (size_t)i * (h->Wcap + 2 * h->ph_margin) + h->ph_margin;
+        ud[i].phy = h->d_phy + (size_t)i * (h->Hcap + 2 * h->ph_margin) + h->ph_margin;
         ud[i].s = un.s;
         ud[i].plane_a = un.s * K + un.k_a;
         ud[i].plane_b = paired ? un.s * K + un.k_b : -1;
@@ -461,6 +475,10 @@ gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
     GB_CU(cudaMemcpy(h->d_tcfreq, fd.data(), nf * sizeof(TcFreqDev), cudaMemcpyHostToDevice));
     GB_CU(cudaMemcpy(h->d_tcforder, order.data(), nf * sizeof(int), cudaMemcpyHostToDevice));
     GB_CU(cudaMemcpy(h->d_tcunit, ud.data(), nu * sizeof(TcUnitDev), cudaMemcpyHostToDevice));
+    h->tc_pre_stride = 2 * rmax + 2;
+    GB_TRY(dalloc(&h->d_tcpre, (size_t)nu * 2 * h->tc_pre_stride));
+    GB_CU(build_gabor_tc_prefix(h->d_unit_w, h->d_tcunit, h->d_tcfreq, h->d_sigma, nu, h->tc_pre_stride,
+                                h->d_tcpre, st));
     h->tc_ready = true;
     return GB_OK;
 }
@@ -483,13 +501,19 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     if (tables_move) free_tc(h);
     GB_TRY(ensure_tc(h, st));
     const int ty = h->tc_row_ty;
-    const int64_t row_cnt = (int64_t)((H + ty - 1) / ty) * ((W + 127) / 128);
+    // Non-zero boundary rules: the row pass also produces the halo rows [-R, 0) and
+    // [H, H + R) of the column signals, from the extended image.
+    int rmax = 0;
+    for (const Freq &f : h->freqs) rmax = std::max(rmax, f.R);
+    const int ypad = h->boundary == kBoundaryZero ? 0 : (rmax + ty - 1) / ty * ty;
+    const int64_t row_cnt = (int64_t)((H + 2 * ypad + ty - 1) / ty) * ((W + 127) / 128);
     const int64_t col_cnt = ny64 * (h->tc_np_f * nx32 + (h->tc_nu_f - h->tc_np_f) * nx64);
     if ((int64_t)nf * std::max(row_cnt, col_cnt) > (int64_t)1 << 30)
         return fail(GB_ERR_UNSUPPORTED, "image too large for the tensor-core bank");
     const int Lpad = tc_lpad(h);
     const int64_t Hp = ny64 * 64 + 2 * Lpad;
-    const int64_t need = tc_sig_elems(h, H, W);
+    const int64_t need_bytes = tc_ws_bytes(h, H, W);
+    const int64_t need = (need_bytes + 1) / 2;   // in 16-bit elements
     uint16_t *sig = h->ws_ptr;
     bool zero_halo = true;   // a caller-owned workspace may hold anything
     if (!sig) {
@@ -504,10 +528,11 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
         }
         sig = h->d_tcsig;
         zero_halo = h->tc_H != H || h->tc_W != W;
-    } else if ((size_t)need * sizeof(uint16_t) > h->ws_bytes) {
-        return fail(GB_ERR_BUDGET, "workspace too small: this image needs " +
-                                       std::to_string(need * (int64_t)sizeof(uint16_t)) + " bytes");
+    } else if ((size_t)need_bytes > h->ws_bytes) {
+        return fail(GB_ERR_BUDGET, "workspace too small: this image needs " + std::to_string(need_bytes) + " bytes");
     }
+    float2 *onesA = reinterpret_cast<float2 *>(reinterpret_cast<char *>(sig) + tc_sig_bytes(h, H, W));
+    float2 *onesB = onesA + (int64_t)h->units.size() * W;
     if (zero_halo && need > 0) {
         // Layout [signal][Hp / 8][W][8].  The row pass writes rows [Lpad, Lpad + round_up(H, TY))
         // of every signal (zeros below row H); the column pass reads up to R8 rows beyond, so
@@ -536,7 +561,11 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.row_kmax = h->tc_row_kmax;
     a.row_pwmax = h->tc_row_pwmax;
     a.col_kmax = h->tc_col_kmax;
-    a.absmax = h->d_tcabsmax;
+    a.minmax = h->d_tcminmax;
+    a.onesA = onesA;
+    a.onesB = onesB;
+    a.ones_pre = h->d_tcpre;
+    a.ones_stride = h->tc_pre_stride;
     a.row_ty = ty;
     a.forder = h->d_tcforder;
     a.nf = nf;
@@ -548,6 +577,10 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.col_nx32 = (int)nx32;
     a.col_nx64 = (int)nx64;
     a.col_cnt = (int)col_cnt;
+    a.bmode = h->boundary;
+    a.layout = h->layout;
+    a.nplanes = (int)(h->omega.size() * h->theta.size());
+    a.row_y0 = -ypad;
     GB_CU(launch_gabor_tc(a, h->sm_count, st));
     return GB_OK;
 }
@@ -568,6 +601,9 @@ gb_status filter_device(gabor_bank *h, const float *d_img, int H, int W, int64_t
     a.freqs = h->d_freqdev;
     a.units = h->d_unitdev;
     a.counter = h->d_counter;
+    a.bmode = h->boundary;
+    a.layout = h->layout;
+    a.nplanes = (int)(h->omega.size() * h->theta.size());
     GB_CU(launch_gabor_fp32(a, n, h->max_smem, h->sm_count, st));
     return GB_OK;
 }
@@ -741,6 +777,7 @@ gb_status gabor_bank_sdft(gabor_bank_t h, const float *d_img, int H, int W, int6
     a.Mx = Mx;
     a.My = My;
     a.half = half_spectrum;
+    a.bmode = h->boundary;
     a.taps_x = h->d_sdft_taps;
     a.taps_y = h->d_sdft_taps + (kMaxSdftM + 8);
     a.tw_x = h->d_sdft_tw;
@@ -770,7 +807,7 @@ gb_status gabor_bank_sdft(gabor_bank_t h, const float *d_img, int H, int W, int6
         h->sdftB_My = My;
     }
     GB_CU(launch_sdft_tc(d_img, pitch, H, W, reinterpret_cast<float2 *>(d_out), Mx, My, half_spectrum,
-                         h->d_sdft_B, h->sdft_B_unscale, bf16, h->d_status, h->sm_count, st));
+                         h->d_sdft_B, h->sdft_B_unscale, bf16, h->boundary, h->d_status, h->sm_count, st));
     return GB_OK;
 }
 
@@ -834,6 +871,9 @@ gb_status gabor_bank_filter_batch(gabor_bank_t h, int n, const float *const *d_i
     a.units = h->d_unitdev;
     a.items = items;
     a.counter = h->d_counter;
+    a.bmode = h->boundary;
+    a.layout = h->layout;
+    a.nplanes = (int)(h->omega.size() * h->theta.size());
     GB_CU(launch_gabor_fp32(a, nitems, h->max_smem, h->sm_count, st));
     return GB_OK;
 }
@@ -862,6 +902,17 @@ gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value)
             h->tile_rows = (int)value;
             free_tables(h);
         }
+        return GB_OK;
+    case GB_OPT_BOUNDARY:
+        if (value < GB_BOUNDARY_ZERO || value > GB_BOUNDARY_MIRROR)
+            return fail(GB_ERR_INVALID_ARG, "GB_OPT_BOUNDARY takes GB_BOUNDARY_ZERO, _REPLICATE or _MIRROR");
+        h->boundary = (int)value;
+        h->tc_H = h->tc_W = 0;   // the tensor-core intermediate's halo rows change meaning
+        return GB_OK;
+    case GB_OPT_LAYOUT:
+        if (value != GB_LAYOUT_PLANES && value != GB_LAYOUT_PIXELS)
+            return fail(GB_ERR_INVALID_ARG, "GB_OPT_LAYOUT takes GB_LAYOUT_PLANES or GB_LAYOUT_PIXELS");
+        h->layout = (int)value;
         return GB_OK;
     case GB_OPT_SEGMENTS:
         if (value < 0 || value > 64) return fail(GB_ERR_INVALID_ARG, "GB_OPT_SEGMENTS takes 0 .. 64");
@@ -937,7 +988,7 @@ int64_t gabor_bank_workspace_bytes(gabor_bank_t h, int H, int W)
 {
     if (!h || H <= 0 || W <= 0) return 0;
     if (h->prec == GB_FP32 || h->units.empty()) return 0;
-    return tc_sig_elems(h, H, W) * (int64_t)sizeof(uint16_t);
+    return tc_ws_bytes(h, H, W);
 }
 
 gb_status gabor_bank_set_workspace(gabor_bank_t h, void *d_ws, int64_t bytes)

@@ -78,6 +78,13 @@ FreqDev gabor_fp32_geometry(int R, int tile_rows)
     return f;
 }
 
+// Offset of output (plane p, row 0, column x): plane-major out[p][y][x] or pixel-major
+// out[y][x][p] (the n_freq x n_theta feature vector of a pixel contiguous).
+__device__ __forceinline__ int64_t out_offset(const BankArgs &a, int p, int64_t plane, int x)
+{
+    return a.layout ? (int64_t)x * a.nplanes + p : (int64_t)p * plane + x;
+}
+
 __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkItem it, unsigned char *smem_raw)
 {
     const UnitDev u = a.units[it.unit];
@@ -93,13 +100,17 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
     const int ncols = kStripW + f.T - 1;        // input columns x0 - R .. x0 + 31 + R
     const int nchunks = f.Tpad / 8;
     const int64_t plane = (int64_t)im.H * im.W;
+    const int64_t ystride = a.layout ? (int64_t)im.W * a.nplanes : (int64_t)im.W;   // between output rows
     const Smem sm = carve(smem_raw, f);
     const float4 *taps4 = reinterpret_cast<const float4 *>(sm.taps);
 
     for (int i = tid; i < f.Tpad + 8; i += kThreads) sm.taps[i] = i < f.Tpad ? f.taps[i] : 0.f;
+    // Demodulation phases at the staged positions (beyond the image only for non-zero rules,
+    // whose extended samples are demodulated at their own positions).
+    const bool ext = a.bmode != kBoundaryZero;
     for (int j = tid; j <= SW; j += kThreads) {
         const int gx = x0 - R + j;
-        sm.phx[j] = (j < ncols && gx >= 0 && gx < im.W) ? u.phx[gx] : make_float2(0.f, 0.f);
+        sm.phx[j] = (j < ncols && (ext || (gx >= 0 && gx < im.W))) ? u.phx[gx] : make_float2(0.f, 0.f);
     }
     for (int i = tid; i < RS * stride; i += kThreads) sm.ring4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
@@ -126,13 +137,12 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
         block_rows(b, start, n);
         float *dst = sm.raw + (size_t)(b & 1) * TH * RW;
         for (int r = warp; r < n; r += kThreads / 32) {
-            const int y = start + r;
-            const bool yin = y >= 0 && y < im.H;
-            const float *src = im.img + (int64_t)(yin ? y : 0) * im.pitch;
+            const int yy = ext_coord(start + r, im.H, a.bmode);   // -1: zero row
+            const float *src = im.img + (int64_t)(yy >= 0 ? yy : 0) * im.pitch;
             for (int j = lane; j < ncols; j += 32) {
-                const int gx = x0 - R + j;
-                const bool ok = yin && gx >= 0 && gx < im.W;
-                cp_async4(dst + (size_t)r * RW + j, ok ? (const void *)(src + gx) : (const void *)im.img,
+                const int xx = ext_coord(x0 - R + j, im.W, a.bmode);
+                const bool ok = yy >= 0 && xx >= 0;
+                cp_async4(dst + (size_t)r * RW + j, ok ? (const void *)(src + xx) : (const void *)im.img,
                           ok ? 4 : 0);
             }
         }
@@ -164,7 +174,7 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
             conv8_linear<float2>(sm.stage + (size_t)r * SW + 8 * q, taps4, nchunks, acc);
             const int y = start + r;
             const int base = ((y - ring_origin) % RS) * stride + 8 * q;
-            const bool yin = y >= 0 && y < im.H;
+            const bool yin = ext || (y >= 0 && y < im.H);
             const float2 cy = yin ? u.phy[y] : make_float2(0.f, 0.f);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -195,8 +205,8 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
             for (int j = 0; j < 8; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
             conv8_ring<float4>(sm.ring4 + xl, stride, RS, slot0, taps4, nchunks, acc);
             if (x < im.W) {
-                float2 *oa = im.out + (int64_t)u.plane_a * plane + x;
-                float2 *ob = im.out + (int64_t)u.plane_b * plane + x;
+                float2 *oa = im.out + out_offset(a, u.plane_a, plane, x);
+                float2 *ob = im.out + out_offset(a, u.plane_b, plane, x);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int y = c + yb + j;
@@ -204,9 +214,9 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
                         const float2 cy = u.phy[y];
                         const float P = acc[j].x, Q = acc[j].y, P2 = acc[j].z, Q2 = acc[j].w;
                         // Eq. 7-8 and Eq. 15-16
-                        __stcs(oa + (int64_t)y * im.W,
+                        __stcs(oa + (int64_t)y * ystride,
                                make_float2(fmaf(cy.x, P, cy.y * Q), fmaf(cy.y, P, -cy.x * Q)));
-                        __stcs(ob + (int64_t)y * im.W,
+                        __stcs(ob + (int64_t)y * ystride,
                                make_float2(fmaf(cy.x, P2, cy.y * Q2), fmaf(cy.y, P2, -cy.x * Q2)));
                     }
                 }
@@ -217,14 +227,14 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
             for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
             conv8_ring<float2>(sm.ring2 + xl, stride, RS, slot0, taps4, nchunks, acc);
             if (x < im.W) {
-                float2 *oa = im.out + (int64_t)u.plane_a * plane + x;
+                float2 *oa = im.out + out_offset(a, u.plane_a, plane, x);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int y = c + yb + j;
                     if (yb + j < nout) {
                         const float2 cy = u.phy[y];
                         const float P = acc[j].x, Q = acc[j].y;
-                        __stcs(oa + (int64_t)y * im.W,
+                        __stcs(oa + (int64_t)y * ystride,
                                make_float2(fmaf(cy.x, P, cy.y * Q), fmaf(cy.y, P, -cy.x * Q)));
                     }
                 }

@@ -140,7 +140,7 @@ __device__ __forceinline__ TcDesc load_desc(const TcBankArgs &a, unsigned char *
 __device__ __forceinline__ RowItem row_item(const TcBankArgs &a, const TcDesc &d, int it)
 {
     const int g = it / a.row_cnt, local = it - g * a.row_cnt;
-    return RowItem{d.forder[g], (local / a.row_nx) * a.row_ty, (local % a.row_nx) * kRowTileX};
+    return RowItem{d.forder[g], a.row_y0 + (local / a.row_nx) * a.row_ty, (local % a.row_nx) * kRowTileX};
 }
 __device__ __forceinline__ ColItem col_item(const TcBankArgs &a, const TcDesc &d, int it)
 {
@@ -155,10 +155,40 @@ __device__ __forceinline__ ColItem col_item(const TcBankArgs &a, const TcDesc &d
     return ColItem{u0 + (paired ? 0 : a.np_f) + q, (r % nx) * (paired ? 32 : 64), (r / nx) * kColTileY};
 }
 
+// Output element (plane p, row y, column x): plane-major out[p][y][x] or pixel-major out[y][x][p].
+__device__ __forceinline__ int64_t tc_out_offset(const TcBankArgs &a, int p, int y, int x)
+{
+    const int64_t pix = (int64_t)y * a.W + x;
+    return a.layout ? pix * a.nplanes + p : (int64_t)p * a.plane + pix;
+}
+
+// Order-preserving unsigned keys of floats (for atomic min / max over signed values).
+__device__ __forceinline__ unsigned fkey(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_value(unsigned k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// The centre c = (min + max) / 2 the passes subtract from the image, and e with
+// max|f - c| = m 2^e, m in [0.5, 1) (FP16 operands get the exact scale 2^-e).
+__device__ __forceinline__ void image_centre(const TcBankArgs &a, float &c, int &e)
+{
+    const float lo = fkey_value(~a.minmax[0]), hi = fkey_value(a.minmax[1]);
+    c = hi >= lo ? 0.5f * (lo + hi) : 0.f;
+    const float m = hi >= lo ? fmaxf(hi - c, c - lo) : 0.f;
+    e = 0;
+    if (m > 0.f) frexpf(m, &e);
+}
+
 // ------------------------------------------------------------------------------ row pass
 // Items: (frequency s, tile y, tile x), sorted by frequency; each item runs every unit of s.
-// The input scale 2^-e (|f| 2^-e < 1, FP16 range) comes from k_absmax for the whole image; it
-// is applied to the staged patch (a power of two: exact).  Warps 8-15 stage operands (the
+// The image centre c and the scale 2^-e (|f - c| 2^-e < 1, FP16 range) come from k_minmax; the
+// is applied to the staged patch after the image centre c is subtracted (the column pass adds
+// c F[1] back).  Warps 8-15 stage operands (the
 // phases of the next unit arrive by cp.async while the current unit's operand is built);
 // warps 0-7 are the epilogue, two per TMEM lane quarter, each taking half of the rows.
 __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant__ TcBankArgs a)
@@ -201,11 +231,9 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
     tc_fence_after();
     const uint32_t tmem = *tmem_s;
     const uint32_t idesc = idesc_f16(0, kRowTileX, 2 * TY);
-    int e = 0;
-    {
-        const float mx = __int_as_float(*a.absmax);
-        if (mx > 0.f) frexpf(mx, &e);   // mx = m 2^e, m in [0.5, 1)
-    }
+    float cen;
+    int e;
+    image_centre(a, cen, e);
 
     if (warp >= 8) {
         // -------------------------------------------------------------- producers
@@ -221,7 +249,8 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
             for (int i = ptid; i < 2 * PW; i += NP) {
                 const int c = i >> 1, cs = i & 1;
                 const int gx = x0 - R + c;
-                const bool ok = c < ncols && gx >= 0 && gx < a.W;
+                // beyond the image only for non-zero rules (extended samples keep their own phase)
+                const bool ok = c < ncols && (a.bmode != kBoundaryZero || (gx >= 0 && gx < a.W));
                 cp_async4(dst + cs * a.row_pwmax + c, ok ? (const void *)(src + 2 * gx + cs) : (const void *)src, ok ? 4 : 0);
             }
             cp_async_commit();
@@ -249,21 +278,25 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
             }
             // patch rows y0 .. y0 + TY - 1, columns x0 - R .. x0 + 127 + R (zero outside the image)
             for (int r = pwarp; r < TY; r += NP / 32) {
-                const int y = y0 + r;
-                const bool yin = y < a.H;
-                const float *src = a.img + (int64_t)(yin ? y : 0) * a.pitch;
+                const int yy = ext_coord(y0 + r, a.H, a.bmode);   // -1: zero row
+                const float *src = a.img + (int64_t)(yy >= 0 ? yy : 0) * a.pitch;
                 for (int c = lane; c < PW; c += 32) {
-                    const int gx = x0 - R + c;
-                    const bool ok = yin && c < ncols && gx >= 0 && gx < a.W;
-                    cp_async4(patch + r * PWs + c, ok ? (const void *)(src + gx) : (const void *)a.img, ok ? 4 : 0);
+                    const int xx = ext_coord(x0 - R + c, a.W, a.bmode);
+                    const bool ok = yy >= 0 && c < ncols && xx >= 0;
+                    cp_async4(patch + r * PWs + c, ok ? (const void *)(src + xx) : (const void *)a.img, ok ? 4 : 0);
                 }
             }
             cp_async_commit();
             issue_phases(D.units[u0], x0, R, PW, ncols, 0);
             cp_async_wait<0>();
-            // input scale 2^-e on the thread's own patch elements (exact)
-            for (int r = pwarp; r < TY; r += NP / 32)
-                for (int c = lane; c < PW; c += 32) patch[r * PWs + c] *= sc;
+            // (f - c) 2^-e on the thread's own patch elements; zero samples stay zero
+            for (int r = pwarp; r < TY; r += NP / 32) {
+                const bool yok = ext_coord(y0 + r, a.H, a.bmode) >= 0;
+                for (int c = lane; c < PW; c += 32) {
+                    const bool ok = yok && c < ncols && ext_coord(x0 - R + c, a.W, a.bmode) >= 0;
+                    patch[r * PWs + c] = ok ? (patch[r * PWs + c] - cen) * sc : 0.f;
+                }
+            }
             bool stop = false;
             for (int q = 0; q < nu; ++q, ++job) {
                 const int b = job & 1;
@@ -366,7 +399,8 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
                 const int b = job & 1;
                 // row phases of the warp's rows: lane l holds row rbase + l (broadcast by shuffle)
                 const int yl = y0 + rbase + lane;
-                const float2 pyl = (lane < TY / 2 && yl < a.H) ? __ldg(&u.phy[yl]) : make_float2(0.f, 0.f);
+                const bool yok = a.bmode != kBoundaryZero || yl < a.H;
+                const float2 pyl = (lane < TY / 2 && yok) ? __ldg(&u.phy[yl]) : make_float2(0.f, 0.f);
                 const float2 px = xin ? __ldg(&u.phx[gx]) : make_float2(0.f, 0.f);
                 if (!mbar_wait(&tmem_full[b], (job >> 1) & 1, abort_s)) {
                     ok = false;
@@ -458,6 +492,9 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_cols(const __grid_constant_
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
     const uint32_t abuf = 128u * a.col_kmax * 2;
     const TcDesc D = load_desc(a, sm + L.desc_off);
+    float cen;
+    int e_unused;
+    image_centre(a, cen, e_unused);
 
     if (tid == 0) {
         for (int i = 0; i < kColAcc; ++i) {
@@ -600,6 +637,11 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_cols(const __grid_constant_
             // row phases: lane l holds row y0 + 8 warp + (l & 7)
             const int yr = y0 + 8 * warp + (lane & 7);
             const float2 pyr = yr < a.H ? __ldg(&u.phy[yr]) : make_float2(0.f, 0.f);
+            // c B(y) for the same rows; A(x) for the lane's columns (the F[1] correction)
+            const float2 byr = yr < a.H ? __ldg(&a.onesB[(int64_t)w.unit * a.H + yr]) : make_float2(0.f, 0.f);
+            const int xa0 = x0 + lane, xa1 = x0 + 32 + lane;
+            const float2 ax0 = xa0 < a.W ? __ldg(&a.onesA[(int64_t)w.unit * a.W + xa0]) : make_float2(0.f, 0.f);
+            const float2 ax1 = (!paired && xa1 < a.W) ? __ldg(&a.onesA[(int64_t)w.unit * a.W + xa1]) : make_float2(0.f, 0.f);
             const bool failed = !mbar_wait(&tmem_full[b], (j / kColAcc) & 1, abort_s);
             if (named_barrier_or(2, 256, failed)) {
                 if (tid == 0) fail_status(a.status, abort_s, 33);
@@ -626,26 +668,33 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_cols(const __grid_constant_
                 const int yy = y0 + 8 * warp + r;
                 const float tx = __shfl_sync(0xffffffffu, pyr.x, r);
                 const float ty = __shfl_sync(0xffffffffu, pyr.y, r);
+                const float cbr = cen * __shfl_sync(0xffffffffu, byr.x, r);   // c B(y)
+                const float cbi = cen * __shfl_sync(0xffffffffu, byr.y, r);
                 if (yy < a.H) {
                     if (paired) {
                         const int x = x0 + lane;
                         if (x < a.W) {
                             const float P = xr[r * 32], Q = xr[(kColTileY + r) * 32];
                             const float P2 = xr[(2 * kColTileY + r) * 32], Q2 = xr[(3 * kColTileY + r) * 32];
-                            float2 *o = a.out + (int64_t)yy * a.W + x;
-                            // Eq. 7-8 (theta) and Eq. 15-16 (pi - theta)
-                            __stcs(o + (int64_t)u.plane_a * a.plane, make_float2(fmaf(tx, P, ty * Q), fmaf(ty, P, -tx * Q)));
-                            __stcs(o + (int64_t)u.plane_b * a.plane,
-                                   make_float2(fmaf(tx, P2, ty * Q2), fmaf(ty, P2, -tx * Q2)));
+                            // Eq. 7-8 (theta) and Eq. 15-16 (pi - theta), plus c A(x) B(y) and
+                            // c conj(A(x)) B(y) (the response to c moves w^c to -w^c)
+                            __stcs(a.out + tc_out_offset(a, u.plane_a, yy, x),
+                                   make_float2(fmaf(tx, P, ty * Q) + (ax0.x * cbr - ax0.y * cbi),
+                                               fmaf(ty, P, -tx * Q) + (ax0.x * cbi + ax0.y * cbr)));
+                            __stcs(a.out + tc_out_offset(a, u.plane_b, yy, x),
+                                   make_float2(fmaf(tx, P2, ty * Q2) + (ax0.x * cbr + ax0.y * cbi),
+                                               fmaf(ty, P2, -tx * Q2) + (ax0.x * cbi - ax0.y * cbr)));
                         }
                     } else {
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const int x = x0 + 32 * h + lane;
+                            const float2 ax = h ? ax1 : ax0;
                             if (x < a.W) {
                                 const float P = xr[(h * kColTileY + r) * 32], Q = xr[((2 + h) * kColTileY + r) * 32];
-                                __stcs(a.out + (int64_t)u.plane_a * a.plane + (int64_t)yy * a.W + x,
-                                       make_float2(fmaf(tx, P, ty * Q), fmaf(ty, P, -tx * Q)));
+                                __stcs(a.out + tc_out_offset(a, u.plane_a, yy, x),
+                                       make_float2(fmaf(tx, P, ty * Q) + (ax.x * cbr - ax.y * cbi),
+                                                   fmaf(ty, P, -tx * Q) + (ax.x * cbi + ax.y * cbr)));
                             }
                         }
                     }
@@ -660,26 +709,89 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_cols(const __grid_constant_
     if (warp == 0) tmem_dealloc(tmem, 64 * kColAcc);
 }
 
-// Largest |f| of the image as float bits (non-negative floats order like their integers).
-__global__ void k_absmax(const float *__restrict__ img, int64_t pitch, int H, int W, int *__restrict__ out)
+// Min and max of the image as order-preserving keys, out[0] = ~min key and out[1] = max key
+// (both words start at zero; one atomicMax pair per block).
+__global__ void k_minmax(const float *__restrict__ img, int64_t pitch, int H, int W, unsigned *__restrict__ out)
 {
-    float m = 0.f;
+    unsigned lo = 0xffffffffu, hi = 0u;
     for (int y = blockIdx.y; y < H; y += gridDim.y)
-        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < W; x += gridDim.x * blockDim.x)
-            m = fmaxf(m, fabsf(__ldg(img + (int64_t)y * pitch + x)));
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < W; x += gridDim.x * blockDim.x) {
+            const unsigned k = fkey(__ldg(img + (int64_t)y * pitch + x));
+            lo = min(lo, k);
+            hi = max(hi, k);
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    __shared__ float wm[32];
-    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    __shared__ unsigned wlo[32], whi[32];
+    if ((threadIdx.x & 31) == 0) {
+        wlo[threadIdx.x >> 5] = lo;
+        whi[threadIdx.x >> 5] = hi;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, wm[i]);
-        atomicMax(out, __float_as_int(m));   // one atomic per block
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+            lo = min(lo, wlo[i]);
+            hi = max(hi, whi[i]);
+        }
+        atomicMax(out, ~lo);
+        atomicMax(out + 1, hi);
     }
 }
 
-// ------------------------------------------------------------------------ Toeplitz B (FP64)
-// M[j][k] = S(k - j - off) * 2^sB for |k - j - off| <= R, `rows` rows, K-major SW128, FP16.
+// pre[u][0][j] = sum_{d=-R}^{-R+j-1} S(d) exp(i w^c d), pre[u][1][j] the same with w^s,
+// j = 0 .. 2R+1 (FP64, phases reduced exactly: w d = pi (w / pi) d mod 2 pi).  One thread per
+// (unit, direction).
+__global__ void k_build_prefix(const double *__restrict__ unit_w, const TcUnitDev *__restrict__ units,
+                               const TcFreqDev *__restrict__ freqs, const double *__restrict__ sigma, int nunits,
+                               int stride, double2 *__restrict__ pre)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * nunits) return;
+    const int u = i >> 1, dir = i & 1;
+    const int s = units[u].s, R = freqs[s].R;
+    const double sg = sigma[s], w = unit_w[2 * u + dir];
+    double2 *p = pre + ((int64_t)u * 2 + dir) * stride;
+    double re = 0.0, im = 0.0;
+    p[0] = make_double2(0.0, 0.0);
+    for (int d = -R; d <= R; ++d) {
+        double sn, cs;
+        sincospi(fmod(w * d, 2.0), &sn, &cs);
+        const double g = exp(-(double)d * d / (2.0 * sg * sg)) / (2.5066282746310002 * sg);
+        re += g * cs;
+        im += g * sn;
+        p[d + R + 1] = make_double2(re, im);
+    }
+}
+
+// A[u][x] = sum over the in-image (zero rule) or all (other rules) taps d of S(d) exp(i w^c d),
+// B[u][y] likewise along y: F[1](x, y) = A(x) B(y) for the unit's orientation.
+__global__ void k_ones(const TcBankArgs a, const TcUnitDev *__restrict__ units, const TcFreqDev *__restrict__ freqs,
+                       int nunits, float2 *__restrict__ A, float2 *__restrict__ B)
+{
+    const int64_t n = (int64_t)nunits * (a.W + a.H);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int u = (int)(i / (a.W + a.H)), p = (int)(i % (a.W + a.H));
+        const bool is_x = p < a.W;
+        const int pos = is_x ? p : p - a.W, n1 = is_x ? a.W : a.H;
+        const int R = freqs[units[u].s].R;
+        const double2 *pr = a.ones_pre + ((int64_t)u * 2 + (is_x ? 0 : 1)) * a.ones_stride;
+        int lo = -R, hi = R;
+        if (a.bmode == kBoundaryZero) {   // taps d with 0 <= pos - d < n1
+            lo = max(-R, pos - (n1 - 1));
+            hi = min(R, pos);
+        }
+        const double2 v = make_double2(pr[hi + R + 1].x - pr[lo + R].x, pr[hi + R + 1].y - pr[lo + R].y);
+        const float2 f = make_float2((float)v.x, (float)v.y);
+        if (is_x)
+            A[(int64_t)u * a.W + pos] = f;
+        else
+            B[(int64_t)u * a.H + pos] = f;
+    }
+}
+
 __global__ void k_build_toeplitz(uint16_t *__restrict__ B, int rows, int K, int off, int R, double sigma, int sB)
 {
     const int n = rows * K;
@@ -739,6 +851,14 @@ cudaError_t build_gabor_tc_b(uint16_t *Brow, uint16_t *Bcol, int R, double sigma
     return cudaGetLastError();
 }
 
+cudaError_t build_gabor_tc_prefix(const double *unit_w, const TcUnitDev *units, const TcFreqDev *freqs,
+                                  const double *sigma, int nunits, int stride, double2 *pre, cudaStream_t st)
+{
+    if (nunits == 0) return cudaSuccess;
+    k_build_prefix<<<(2 * nunits + 63) / 64, 64, 0, st>>>(unit_w, units, freqs, sigma, nunits, stride, pre);
+    return cudaGetLastError();
+}
+
 cudaError_t gabor_tc_prepare()
 {
     cudaError_t e = cudaFuncSetAttribute(k_gabor_tc_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
@@ -754,12 +874,21 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
     const int n_row_items = a.nf * a.row_cnt, n_col_items = a.nf * a.col_cnt;
     const size_t smem_r = gabor_tc_smem_rows(a.row_kmax, a.row_pwmax, a.row_ty);
     const size_t smem_c = gabor_tc_smem_cols(a.col_kmax);
-    cudaError_t e0 = cudaMemsetAsync(a.absmax, 0, sizeof(int), st);
+    cudaError_t e0 = cudaMemsetAsync(a.minmax, 0, 2 * sizeof(unsigned), st);
     if (e0 != cudaSuccess) return e0;
     const dim3 ag(std::max(1, std::min(4, (a.W + 255) / 256)), std::max(1, std::min(a.H, 2 * sm_count)));
-    k_absmax<<<ag, 256, 0, st>>>(a.img, a.pitch, a.H, a.W, a.absmax);
+    k_minmax<<<ag, 256, 0, st>>>(a.img, a.pitch, a.H, a.W, a.minmax);
     e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
+    {
+        const int nu = a.nf * a.nu_f;
+        const int64_t n = (int64_t)nu * (a.W + a.H);
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4 * sm_count));
+        k_ones<<<blocks, 256, 0, st>>>(a, a.units, a.freqs, nu, const_cast<float2 *>(a.onesA),
+                                       const_cast<float2 *>(a.onesB));
+        e0 = cudaGetLastError();
+        if (e0 != cudaSuccess) return e0;
+    }
     if (n_row_items > 0) {
         k_gabor_tc_rows<<<std::min(n_row_items, sm_count), 512, smem_r, st>>>(a);
         cudaError_t e = cudaGetLastError();

@@ -19,11 +19,30 @@ constexpr int kMaxSdftM = 64;      // largest SDFT window side
 constexpr int kSmemLimit = 227 * 1024;
 constexpr int kStaticSmemReserve = 256;   // static shared memory kept free next to the dynamic part
 
+// Boundary rules for the image beyond its edges.
+enum BoundaryMode { kBoundaryZero = 0, kBoundaryReplicate = 1, kBoundaryMirror = 2 };
+
+// The image row / column that position i (of n) reads: i itself inside [0, n); outside, the
+// edge sample (replicate) or the sample mirrored about the pixel edges, f(-1) = f(0),
+// f(n) = f(n - 1), period 2n (mirror); -1 (a zero sample) for the zero rule.
+__host__ __device__ inline int ext_coord(int i, int n, int mode)
+{
+    if (i >= 0 && i < n) return i;
+    if (mode == kBoundaryReplicate) return i < 0 ? 0 : n - 1;
+    if (mode == kBoundaryMirror) {
+        const int p = 2 * n;
+        int m = i % p;
+        if (m < 0) m += p;
+        return m < n ? m : p - 1 - m;
+    }
+    return -1;
+}
+
 // Device view of one horizontal pass ("row unit") of the bank: the pass of orientation
 // theta_a at frequency omega_s, and the orientation pi - theta_a that reuses it (Eq. 13-16).
 struct UnitDev {
-    const float2 *phx;  // (cos, sin)(omega cos(theta_a) x), x in [0, Wcap)
-    const float2 *phy;  // (cos, sin)(omega sin(theta_a) y), y in [0, Hcap)
+    const float2 *phx;  // (cos, sin)(omega cos(theta_a) x), x in [-mg, Wcap + mg)
+    const float2 *phy;  // (cos, sin)(omega sin(theta_a) y), y in [-mg, Hcap + mg)
     int s;              // frequency index
     int plane_a;        // output plane of theta_a  (s * n_theta + k)
     int plane_b;        // output plane of pi - theta_a, or -1 when unpaired
@@ -74,6 +93,9 @@ struct BankArgs {
     int *counter;             // work-queue head (zeroed before each launch)
     int nitems;
     int ngroups;
+    int bmode;                // BoundaryMode
+    int layout;               // 0: out[plane][y][x], 1: out[y][x][plane]
+    int nplanes;              // n_freq * n_theta
     ItemGroup groups[kMaxGroups];
 };
 
@@ -103,7 +125,14 @@ struct TcBankArgs {
     const TcUnitDev *units;
     int *status;
     int row_kmax, row_pwmax, col_kmax, row_ty;
-    int *absmax;           // device word: max |f| of the image as float bits (k_absmax)
+    unsigned *minmax;      // device words: ~(min key) and max key of the image (k_minmax)
+    // F[1] = A(x) B(y), the bank's response to the image indicator (or to the constant 1 under
+    // a non-zero boundary rule): the passes filter f - c and add c A(x) B(y) back.
+    const float2 *onesA;   // [unit][W]
+    const float2 *onesB;   // [unit][H]
+    const double2 *ones_pre;   // [unit][2][2 Rmax + 2] prefix sums of S(d) exp(i w^{c|s} d)
+    int ones_stride;           // 2 Rmax + 2
+    int pad3_;
     // Work items, decoded from the image shape: frequencies in the order forder[] (largest
     // radius first); every frequency has nu_f units, the first np_f of them paired.
     const int *forder;
@@ -111,6 +140,10 @@ struct TcBankArgs {
     int row_nx, row_cnt;   // row pass: 128-column tiles per tile row, items per frequency
     int col_ny, col_nx32, col_nx64, col_cnt;   // column pass: 64-row tiles, x tiles, items per frequency
     int col_nst;           // A-operand buffers of the column kernel (set by the launcher)
+    int bmode;             // BoundaryMode
+    int layout;            // 0: out[plane][y][x], 1: out[y][x][plane]
+    int nplanes;           // n_freq * n_theta
+    int row_y0;            // first image row of the row pass (< 0: halo rows for non-zero rules)
     int pad2_;
 };
 struct TcGeometry {
@@ -133,6 +166,7 @@ struct SdftArgs {
     const float2 *tw_y;  // (cos, sin)(2 pi j / My), j < My
     int TpadX, TpadY;
     int TH, seg_len, RS, SW, RW;
+    int bmode;           // BoundaryMode
 };
 
 // One frequency of the plan.
@@ -150,7 +184,8 @@ struct Unit {
 };
 
 // Kernel launchers (defined in the .cu files).
-cudaError_t launch_build_gabor_tables(const double *d_unit_w, int nunits, int Wcap, int Hcap,
+// Phase tables for positions -mg .. cap + mg - 1 (rows of cap + 2 mg entries per unit).
+cudaError_t launch_build_gabor_tables(const double *d_unit_w, int nunits, int Wcap, int Hcap, int mg,
                                       float2 *phx, float2 *phy, cudaStream_t st);
 cudaError_t launch_build_taps(const double *d_sigma, const int *d_lo, const int *d_T, int nfreq,
                               int tpad_max, float *taps, cudaStream_t st);
@@ -169,6 +204,9 @@ cudaError_t build_gabor_tc_b(uint16_t *Brow, uint16_t *Bcol, int R, double sigma
                              cudaStream_t st);
 cudaError_t gabor_tc_prepare();
 cudaError_t launch_gabor_tc(const TcBankArgs &a, int sm_count, cudaStream_t st);
+// Prefix sums of S(d) exp(i w^c d) and S(d) exp(i w^s d), d = -R .. R, per unit (FP64).
+cudaError_t build_gabor_tc_prefix(const double *unit_w, const TcUnitDev *units, const TcFreqDev *freqs,
+                                  const double *sigma, int nunits, int stride, double2 *pre, cudaStream_t st);
 int gabor_tc_row_tile_x();
 int gabor_tc_row_tile_y(int Rmax);
 int gabor_tc_col_tile_y();
@@ -184,7 +222,8 @@ int sdft_tc_b_bytes(int Mx, int My);
 cudaError_t build_sdft_tc_b(void *Bdev, double sigma, int Mx, int My, int bf16, float *b_unscale, cudaStream_t st);
 cudaError_t sdft_tc_prepare();
 cudaError_t launch_sdft_tc(const float *img, int64_t pitch, int H, int W, float2 *out, int Mx, int My, int half,
-                           const void *Bdev, float b_unscale, int bf16, int *status, int sm_count, cudaStream_t st);
+                           const void *Bdev, float b_unscale, int bf16, int bmode, int *status, int sm_count,
+                           cudaStream_t st);
 
 }  // namespace gb
 
@@ -202,6 +241,9 @@ struct gabor_bank {
     int reuse = 1;
     int tile_rows = 0;
     int segments = 0;
+    int boundary = 0;                         // gb::BoundaryMode
+    int layout = 0;                           // 0 plane-major, 1 pixel-major bank output
+    int ph_margin = 0;                        // phase-table entries before 0 and after the capacity
     std::vector<int> ftile_rows, fsegments;   // per-frequency overrides (0 = global / automatic)
     int *d_counter = nullptr;                 // work-queue head of the FP32 bank kernel
     std::vector<gb::ImageDev> last_imgs;      // batch descriptors last uploaded
@@ -210,8 +252,8 @@ struct gabor_bank {
     double *d_sigma = nullptr;
     int *d_lo = nullptr, *d_T = nullptr;
     float *d_taps = nullptr;     // [n_freq][tpad_max]
-    float2 *d_phx = nullptr;     // [nunits][Wcap]
-    float2 *d_phy = nullptr;     // [nunits][Hcap]
+    float2 *d_phx = nullptr;     // [nunits][Wcap + 2 ph_margin], position x at ph_margin + x
+    float2 *d_phy = nullptr;     // [nunits][Hcap + 2 ph_margin]
     gb::UnitDev *d_unitdev = nullptr;
     gb::FreqDev *d_freqdev = nullptr;
     std::vector<gb::FreqDev> freqdev;       // host copy (taps pointers into d_taps)
@@ -243,7 +285,9 @@ struct gabor_bank {
     int tc_nsig = 0;                // column signals of all units
     int tc_nu_f = 0, tc_np_f = 0;   // units per frequency, paired units per frequency
     int tc_row_kmax = 0, tc_row_pwmax = 0, tc_col_kmax = 0;
-    int *d_tcabsmax = nullptr;
+    unsigned *d_tcminmax = nullptr;   // [2] image min / max keys
+    double2 *d_tcpre = nullptr;       // prefix sums of the kernel taps per unit (F[1] tables)
+    int tc_pre_stride = 0;
     int tc_row_ty = 64;
     int tc_H = 0, tc_W = 0, tc_Lpad = 0;
     int64_t tc_Hp = 0;

@@ -74,6 +74,7 @@ struct SdftTcArgs {
     float b_unscale;       // 2^-sB
     int tiles_x, ntiles;
     int *status;
+    int bmode;             // BoundaryMode of the image beyond its edges
 };
 
 template <typename T>
@@ -151,7 +152,8 @@ __global__ void __launch_bounds__(384, 1) k_sdft_tc(const SdftTcArgs a)
                 float v = 0.f;
                 if (b < a.My) {
                     const int gy = y - a.My / 2 + b, gx = x0 - a.Mx / 2 + c;
-                    if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) v = __ldg(a.img + (int64_t)gy * a.pitch + gx);
+                    const int yy = ext_coord(gy, a.H, a.bmode), xx = ext_coord(gx, a.W, a.bmode);
+                    if (yy >= 0 && xx >= 0) v = __ldg(a.img + (int64_t)yy * a.pitch + xx);
                 }
                 pre[q] = v;
                 c += 128;
@@ -183,7 +185,8 @@ __global__ void __launch_bounds__(384, 1) k_sdft_tc(const SdftTcArgs a)
                     const int b = idx / PWn, c = idx - b * PWn;
                     const int gy = y - a.My / 2 + b, gx = x0 - a.Mx / 2 + c;
                     float v = 0.f;
-                    if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) v = __ldg(a.img + (int64_t)gy * a.pitch + gx);
+                    const int yy = ext_coord(gy, a.H, a.bmode), xx = ext_coord(gx, a.W, a.bmode);
+                    if (yy >= 0 && xx >= 0) v = __ldg(a.img + (int64_t)yy * a.pitch + xx);
                     patch[b * a.PW + c] = v;
                     m = fmaxf(m, fabsf(v));
                 }
@@ -421,9 +424,11 @@ cudaError_t build_sdft_tc_b(void *Bdev, double sigma, int Mx, int My, int bf16, 
 }
 
 cudaError_t launch_sdft_tc(const float *img, int64_t pitch, int H, int W, float2 *out, int Mx, int My, int half,
-                           const void *Bdev, float b_unscale, int bf16, int *status, int sm_count, cudaStream_t st)
+                           const void *Bdev, float b_unscale, int bf16, int bmode, int *status, int sm_count,
+                           cudaStream_t st)
 {
     SdftTcArgs a{};
+    a.bmode = bmode;
     a.img = img;
     a.pitch = pitch;
     a.H = H;

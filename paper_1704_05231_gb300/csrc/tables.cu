@@ -13,25 +13,26 @@
 namespace gb {
 
 __global__ void k_build_gabor_tables(const double *__restrict__ unit_w, int nunits, int Wcap,
-                                     int Hcap, float2 *__restrict__ phx, float2 *__restrict__ phy)
+                                     int Hcap, int mg, float2 *__restrict__ phx, float2 *__restrict__ phy)
 {
-    const int64_t per = (int64_t)Wcap + Hcap;
+    const int64_t wx = (int64_t)Wcap + 2 * mg, wy = (int64_t)Hcap + 2 * mg;
+    const int64_t per = wx + wy;
     const int64_t n = per * nunits;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int u = (int)(i / per);
         const int64_t p = i % per;
-        const bool is_x = p < Wcap;
+        const bool is_x = p < wx;
         const double c = is_x ? unit_w[2 * u] : unit_w[2 * u + 1];
-        const double pos = (double)(is_x ? p : p - Wcap);
+        const double pos = (double)((is_x ? p : p - wx) - mg);   // may be negative
         double r = fmod(c * pos, 2.0);
         double s, co;
         sincospi(r, &s, &co);
         const float2 v = make_float2((float)co, (float)s);
         if (is_x)
-            phx[(int64_t)u * Wcap + p] = v;
+            phx[(int64_t)u * wx + p] = v;
         else
-            phy[(int64_t)u * Hcap + (p - Wcap)] = v;
+            phy[(int64_t)u * wy + (p - wx)] = v;
     }
 }
 
@@ -64,13 +65,13 @@ __global__ void k_build_twiddles(int M, float2 *__restrict__ tw)
     }
 }
 
-cudaError_t launch_build_gabor_tables(const double *d_unit_w, int nunits, int Wcap, int Hcap,
+cudaError_t launch_build_gabor_tables(const double *d_unit_w, int nunits, int Wcap, int Hcap, int mg,
                                       float2 *phx, float2 *phy, cudaStream_t st)
 {
     if (nunits == 0) return cudaSuccess;
-    const int64_t n = ((int64_t)Wcap + Hcap) * nunits;
+    const int64_t n = ((int64_t)Wcap + Hcap + 4 * mg) * nunits;
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
-    k_build_gabor_tables<<<blocks, 256, 0, st>>>(d_unit_w, nunits, Wcap, Hcap, phx, phy);
+    k_build_gabor_tables<<<blocks, 256, 0, st>>>(d_unit_w, nunits, Wcap, Hcap, mg, phx, phy);
     return cudaGetLastError();
 }
 
