@@ -67,6 +67,13 @@ def _load():
                 _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                 _ip, _ip, ctypes.c_long, _dp, ctypes.c_int]
+            lib.oracle_iir_smooth.restype = ctypes.c_int
+            lib.oracle_iir_smooth.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp]
+            lib.oracle_iir_gabor.restype = ctypes.c_int
+            lib.oracle_iir_gabor.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int, _dp, ctypes.c_int]
+            lib.oracle_iir_pad.restype = ctypes.c_int
+            lib.oracle_iir_pad.argtypes = [ctypes.c_double]
             lib.oracle_gabor_direct_b.restype = ctypes.c_int
             lib.oracle_gabor_direct_b.argtypes = lib.oracle_gabor_direct.argtypes + [ctypes.c_int]
             lib.oracle_sdft_direct_b.restype = ctypes.c_int
@@ -212,5 +219,53 @@ def sdft(img, sigma, My, Mx=None, support=None, points=None, threads=0, boundary
     return out.reshape(My, Mx, nout) if xs is not None else out.reshape(My, Mx, H, W)
 
 
+def iir_smooth(x, sigma, boundary="zero"):
+    """The Young-van Vliet recursive Gaussian (forward then backward) of a real 1-D signal."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    rc = lib.oracle_iir_smooth(_ptr(x), int(x.size), float(sigma), BOUNDARY[boundary], _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_iir_smooth failed ({rc})")
+    return out
+
+
+def iir_pad(sigma):
+    """Samples the recursive passes extend each signal by on both sides."""
+    return _load().oracle_iir_pad(float(sigma))
+
+
+def iir_gabor_filter(img, omega, theta, sigma, boundary="zero", threads=0):
+    """Algorithm 1 with the recursive Gaussian smoother (complex128 (H, W))."""
+    lib = _load()
+    f = np.ascontiguousarray(img, dtype=np.float64)
+    H, W = f.shape
+    out = np.empty(2 * H * W, dtype=np.float64)
+    rc = lib.oracle_iir_gabor(_ptr(f), H, W, float(omega), float(theta), float(sigma), BOUNDARY[boundary],
+                              _ptr(out), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle_iir_gabor failed ({rc})")
+    return out.view(np.complex128).reshape(H, W)
+
+
+def iir_gabor_bank(img, thetas, omegas, sigmas, boundary="zero", threads=0):
+    """complex128 [n_freq][n_theta][H][W] with the recursive smoother."""
+    return np.array([[iir_gabor_filter(img, om, th, sg, boundary, threads) for th in thetas]
+                     for om, sg in zip(omegas, sigmas)])
+
+
+def ser_db(fast, exact):
+    """Signal-to-error ratio of Sec. IV-C for the real and the imaginary parts (dB):
+    10 log10(sum part(F)^2 / sum (part(F) - part(F_t))^2), F the fast result, F_t the FIR one."""
+    fast = np.asarray(fast)
+    exact = np.asarray(exact)
+    res = []
+    for part in (np.real, np.imag):
+        num = float(np.sum(part(fast) ** 2))
+        den = float(np.sum((part(fast) - part(exact)) ** 2))
+        res.append(10.0 * np.log10(num / den) if den > 0 else float("inf"))
+    return tuple(res)
+
+
 __all__ = ["build", "gauss", "radius", "gabor_filter", "gabor_bank", "gabor_rows",
-           "gabor_cols", "sdft"]
+           "gabor_cols", "sdft", "iir_smooth", "iir_pad", "iir_gabor_filter", "iir_gabor_bank", "ser_db"]

@@ -337,3 +337,66 @@ def test_sdft_boundary_equals_zero_padded_extended_image(boundary):
     got = oracle.sdft(img, 2.0, M, boundary=boundary)
     ref = oracle.sdft(ext, 2.0, M)[:, :, M:M + 10, M:M + 13]
     assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------- recursive (IIR) variant
+# The Young-van Vliet recursion is a linear, shift-invariant, zero-phase smoother with unit
+# DC gain that approximates S_sigma; the IIR Gabor variant is Algorithm 1 with it.
+
+@pytest.mark.parametrize("sigma", [1.0, 2.0, 4.0, 8.0, 16.0, 32.0])
+def test_iir_smoother_gain_phase_and_shape(sigma):
+    n = 8 * int(12 * sigma) + 64
+    c = n // 2
+    x = np.zeros(n)
+    x[c] = 1.0
+    h = oracle.iir_smooth(x, sigma)
+    d = np.arange(n) - c
+    g = np.exp(-d ** 2 / (2 * sigma ** 2)) / (math.sqrt(2 * math.pi) * sigma)
+    assert abs(h.sum() - 1.0) <= 1e-10                          # unit DC gain
+    k = min(200, c - 1)
+    assert np.max(np.abs(h[c + 1:c + k] - h[c - 1:c - k:-1])) <= 1e-13   # zero phase
+    # the core follows S_sigma (peak height 1 / (sqrt(2 pi) sigma) within 6%); the recursion's
+    # exponential tails are heavier than the Gaussian's, so no second-moment match is expected
+    assert abs(h[c] / g[c] - 1.0) <= 0.06
+    assert np.max(np.abs(h - g)) <= (0.1 if sigma < 4 else 0.04) * g.max()
+    assert np.allclose(oracle.iir_smooth(np.ones(4 * n), sigma)[n:3 * n], 1.0, atol=1e-10)
+
+
+def test_iir_gabor_equals_direct_sum_with_the_recursive_kernel():
+    # Linearity and shift invariance: the decomposition (Eq. 5-10) with the recursive smoother
+    # equals the direct 2-D sum of Eq. 1 whose kernel uses the smoother's impulse response h.
+    rng = np.random.default_rng(41)
+    H, W, sigma, omega, theta = 14, 19, 2.0, 0.9, 0.7
+    img = rng.random((H, W))
+    P = oracle.iir_pad(sigma)
+    n = 2 * P + 1
+    imp = np.zeros(4 * n)
+    imp[2 * n] = 1.0
+    h = oracle.iir_smooth(imp, sigma)[2 * n - P:2 * n + P + 1]      # h(d), d = -P .. P
+    d = np.arange(-P, P + 1)
+    kx = h * np.exp(1j * omega * math.cos(theta) * d)
+    ky = h * np.exp(1j * omega * math.sin(theta) * d)
+    ref = np.zeros((H, W), dtype=np.complex128)
+    for y in range(H):
+        for x in range(W):
+            ks = x - d            # k = x - dx
+            ls = y - d
+            vx = (ks >= 0) & (ks < W)
+            vy = (ls >= 0) & (ls < H)
+            ref[y, x] = np.sum(ky[vy][:, None] * kx[vx][None, :] * img[np.ix_(ls[vy], ks[vx])])
+    got = oracle.iir_gabor_filter(img, omega, theta, sigma)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_iir_gabor_symmetries_and_approach_to_fir():
+    from paper_1704_05231_gb300 import synth
+    img = synth.pink_noise(3, 40, 52)
+    a = oracle.iir_gabor_filter(img, 0.8, 0.4, 3.0)
+    assert np.max(np.abs(oracle.iir_gabor_filter(img, 0.8, 0.4 + math.pi, 3.0) - np.conj(a))) <= 1e-13
+    m = oracle.iir_gabor_filter(np.ascontiguousarray(img[:, ::-1]), 0.8, 0.4, 3.0)
+    c = oracle.iir_gabor_filter(img, 0.8, math.pi - 0.4, 3.0)
+    assert np.max(np.abs(c - m[:, ::-1])) <= 1e-13 * np.max(np.abs(c))
+    # the recursive Gaussian approaches S_sigma as sigma grows: SER rises (imaginary parts)
+    sers = [oracle.ser_db(oracle.iir_gabor_filter(img, math.pi / (2 * s), 0.5, s),
+                          oracle.gabor_filter(img, math.pi / (2 * s), 0.5, s))[1] for s in (2.0, 4.0, 8.0)]
+    assert sers[0] > 12 and sers[0] < sers[1] < sers[2]
