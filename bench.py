@@ -364,6 +364,39 @@ def ablation_leg(torch, d_img, thetas, omegas, sigmas, steps, warmup, flush, str
     return res
 
 
+def iir_leg(torch, d_img, thetas, omegas, sigmas, fir_out, steps, warmup, flush, stream):
+    """The recursive-Gaussian bank (Young-van Vliet, the paper's own smoother; cost per output
+    independent of sigma) on the paper-size bank and on the 64-image batch: time, outputs/s and
+    the SER of Sec. IV-C of each frequency's outputs against the exact FIR bank on the GPU."""
+    from paper_1704_05231_gb300 import GaborBank, synth
+    res = {}
+    gbk = GaborBank(thetas, omegas, sigmas, smoother="iir", max_shape=(H, W))
+    out = torch.empty(gbk.out_shape(H, W), dtype=torch.complex64, device="cuda")
+    ms = statistics.mean(time_device(torch, lambda: gbk.filter(d_img, out), steps, warmup, flush, stream))
+    n_out = len(thetas) * len(omegas) * H * W
+    ser = []
+    for s in range(len(omegas)):
+        f, t = out[s], fir_out[s]
+        ser.append([10 * math.log10(float((part(f) ** 2).sum() / ((part(f) - part(t)) ** 2).sum()))
+                    for part in (torch.real, torch.imag)])
+    res["paper_bank"] = {"ms_per_step": ms, "value": n_out / (ms * 1e-3), "unit": UNIT,
+                         "ser_db_re_im_per_frequency": ser}
+    gbk.close()
+    del out
+    shapes = synth.batch_shapes(1, 64, 128, 2048)
+    imgs = [synth.pink_noise_device(1000 + i, h, w) for i, (h, w) in enumerate(shapes)]
+    th, om, sg = synth.octave_bank(8, 5)
+    gbk = GaborBank(th, om, sg, smoother="iir", max_shape=(2048, 2048))
+    outs = [torch.empty(gbk.out_shape(h, w), dtype=torch.complex64, device="cuda") for h, w in shapes]
+    ms = statistics.mean(time_device(torch, lambda: gbk.filter_batch(imgs, outs), min(steps, 3), 3, flush, stream))
+    n_out = sum(len(th) * len(om) * h * w for h, w in shapes)
+    res["batch_64"] = {"ms_per_step": ms, "value": n_out / (ms * 1e-3), "unit": UNIT, "launches_per_step": 2 * len(shapes)}
+    gbk.close()
+    del outs, imgs
+    torch.cuda.empty_cache()
+    return res
+
+
 def batch_leg(torch, steps, warmup, flush, stream):
     """64 uneven 1/f-noise images (sides uniform in [128, 2048], seed 1), 8 orientations x 5
     octave frequencies (sigma = pi/omega, R up to 96): one persistent launch per step for FP32
@@ -543,6 +576,8 @@ def run_ours(args):
         line["ablation"] = ablation_leg(torch, d_img, thetas, omegas, sigmas, args.steps, args.warmup, flush, stream)
     if "batch" in legs:
         line["batch"] = batch_leg(torch, min(args.steps, 5), 3, flush, stream)
+    if "iir" in legs:
+        line["iir"] = iir_leg(torch, d_img, thetas, omegas, sigmas, out, args.steps, args.warmup, flush, stream)
     if "serve" in legs and not args.no_serve and world == 1:
         line["serve"] = serve_leg(args)
     if rank == 0 and not args.no_cpu_baseline:
@@ -566,8 +601,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-tune", action="store_true", help="default tile geometry instead of the autotuner's")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream leg")
-    ap.add_argument("--legs", default="tc,sdft,ablation,batch,serve",
-                    help="comma list of extra legs: tc, sdft, ablation, batch, serve")
+    ap.add_argument("--legs", default="tc,sdft,ablation,batch,iir,serve",
+                    help="comma list of extra legs: tc, sdft, ablation, batch, iir, serve")
     ap.add_argument("--serve-n", type=int, default=2000, help="measured requests of the served stream")
     ap.add_argument("--serve-warm", type=int, default=200)
     args = ap.parse_args()

@@ -155,8 +155,21 @@ typedef enum {
        to gabor_bank_filter, _filter_host, _filter_batch and gabor_bank_sdft. */
     GB_OPT_BOUNDARY = 4,
     /* Bank output layout (gb_layout; default GB_LAYOUT_PLANES). */
-    GB_OPT_LAYOUT = 5
+    GB_OPT_LAYOUT = 5,
+    /* The 1-D Gaussian of the bank's passes (gb_smoother; default GB_SMOOTHER_FIR). */
+    GB_OPT_SMOOTHER = 6
 } gb_option;
+
+/* 1-D Gaussian smoothers (GB_OPT_SMOOTHER). */
+typedef enum {
+    GB_SMOOTHER_FIR = 0,       /* S_sigma truncated at R: exact against Eq. 1 (all precisions) */
+    GB_SMOOTHER_IIR = 1        /* Young-van Vliet third-order forward / backward recursion (the
+                                  smoother of Sec. II): approximate, cost independent of sigma; FP32
+                                  handles, sigma >= 0.5.  Each signal is extended by ceil(12 sigma) + 32
+                                  samples per side under the boundary rule; the recursions start from
+                                  zero state.  Uses a library-owned workspace of about
+                                  (n_signals + 2 n_units) * (H + P) * (W + P) * 4 bytes. */
+} gb_smoother;
 
 /* Image extension rules (GB_OPT_BOUNDARY).  The paper leaves the border unstated. */
 typedef enum {

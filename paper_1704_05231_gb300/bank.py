@@ -20,7 +20,8 @@ STATUS = {0: "GB_OK", -1: "GB_ERR_INVALID_ARG", -2: "GB_ERR_OUT_OF_MEMORY", -3: 
           -4: "GB_ERR_UNSUPPORTED", -5: "GB_ERR_BUDGET", -6: "GB_ERR_TIMEOUT"}
 STATUS_CODE = {v: k for k, v in STATUS.items()}
 PRECISION = {"fp32": 0, "fp16_tc": 1, "bf16_tc": 2}
-OPTION = {"reuse": 1, "tile_rows": 2, "segments": 3, "boundary": 4, "layout": 5}
+OPTION = {"reuse": 1, "tile_rows": 2, "segments": 3, "boundary": 4, "layout": 5, "smoother": 6}
+SMOOTHER = {"fir": 0, "iir": 1}
 BOUNDARY = {"zero": 0, "replicate": 1, "mirror": 2}
 LAYOUT = {"planes": 0, "pixels": 1}
 
@@ -107,11 +108,12 @@ class GaborBank:
     thetas: orientations (rad); omegas, sigmas: one (omega, sigma) per frequency.
     precision: 'fp32', 'fp16_tc' or 'bf16_tc'.  An empty bank (no thetas / omegas) makes an
     SDFT-only handle.  boundary: 'zero', 'replicate' or 'mirror' (image extension); layout:
-    'planes' (out[s][k][y][x]) or 'pixels' (out[y][x][s][k]).
+    'planes' (out[s][k][y][x]) or 'pixels' (out[y][x][s][k]); smoother: 'fir' (truncated
+    Gaussian, exact) or 'iir' (recursive Gaussian, FP32 only).
     """
 
     def __init__(self, thetas=(), omegas=(), sigmas=(), radius_factor=3.0, precision="fp32",
-                 max_shape=(0, 0), boundary="zero", layout="planes"):
+                 max_shape=(0, 0), boundary="zero", layout="planes", smoother="fir"):
         lib = load_library()
         if len(omegas) != len(sigmas):
             raise ValueError("omegas and sigmas must have the same length")
@@ -132,6 +134,8 @@ class GaborBank:
         if layout != "planes":
             self.set_option("layout", LAYOUT[layout])
             self.layout = layout
+        if smoother != "fir":
+            self.set_option("smoother", SMOOTHER[smoother])
 
     # -- lifecycle
     def close(self):
@@ -160,6 +164,8 @@ class GaborBank:
             value = BOUNDARY[value]
         if key == "layout" and isinstance(value, str):
             value = LAYOUT[value]
+        if key == "smoother" and isinstance(value, str):
+            value = SMOOTHER[value]
         _check(self._lib.gabor_bank_set_option(self._h, OPTION[key] if isinstance(key, str) else int(key),
                                                int(value)))
         if key in ("layout", OPTION["layout"]):

@@ -74,6 +74,29 @@ void dfree(T *&p)
 
 int radius_of(double sigma, double rf) { return (int)std::ceil(rf * sigma - 1e-9); }
 
+// Samples a recursive pass extends a signal by on each side.
+int iir_pad(double sigma) { return (int)std::ceil(12.0 * sigma) + 32; }
+
+// Young and van Vliet's recursive Gaussian (Signal Processing 44, 1995): q from sigma (two
+// fitted branches), the third-order coefficients b0..b3 and the gain B; c = {B, b1/b0, b2/b0,
+// b3/b0} for w[n] = B x[n] + (b1 w[n-1] + b2 w[n-2] + b3 w[n-3]) / b0.
+IirFreq iir_coefficients(double sigma)
+{
+    const double q = sigma >= 2.5 ? 0.98711 * sigma - 0.96330 : 3.97156 - 4.14554 * std::sqrt(1.0 - 0.26891 * sigma);
+    const double q2 = q * q, q3 = q2 * q;
+    const double b0 = 1.57825 + 2.44413 * q + 1.4281 * q2 + 0.422205 * q3;
+    const double b1 = 2.44413 * q + 2.85619 * q2 + 1.26661 * q3;
+    const double b2 = -(1.4281 * q2 + 1.26661 * q3);
+    const double b3 = 0.422205 * q3;
+    IirFreq f{};
+    f.c[0] = (float)(1.0 - (b1 + b2 + b3) / b0);
+    f.c[1] = (float)(b1 / b0);
+    f.c[2] = (float)(b2 / b0);
+    f.c[3] = (float)(b3 / b0);
+    f.P = iir_pad(sigma);
+    return f;
+}
+
 // Pairs theta with pi - theta (Algorithm 1: J_{pi - theta} = J*_theta) and lays out the
 // units of every frequency: paired units first, then unpaired ones, each in theta order.
 void build_plan(gabor_bank *h)
@@ -121,7 +144,7 @@ void build_plan(gabor_bank *h)
     // Phase tables also cover the positions a non-zero boundary rule reads beyond the image:
     // up to R + 128 columns (a 128-column tensor-core tile plus its halo) and rows.
     int rmax = 0;
-    for (const Freq &f : h->freqs) rmax = std::max(rmax, f.R);
+    for (const Freq &f : h->freqs) rmax = std::max(rmax, std::max(f.R, iir_pad(f.sigma)));
     h->ph_margin = (rmax + 63) / 64 * 64 + 128;
 }
 
@@ -168,6 +191,7 @@ gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
     std::vector<double> w(2 * nu), sg(nf);
     std::vector<int> lo(nf), T(nf);
     std::vector<UnitDev> ud(nu);
+    int sig = 0;
     for (int i = 0; i < nu; ++i) {
         w[2 * i] = h->units[i].wc / M_PI;
         w[2 * i + 1] = h->units[i].ws / M_PI;
@@ -175,7 +199,8 @@ gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
         ud[i].phx = h->d_phx + (size_t)i * (Wcap + 2 * mg) + mg;
         ud[i].phy = h->d_phy + (size_t)i * (Hcap + 2 * mg) + mg;
         ud[i].s = h->units[i].s;
-        ud[i].pad_ = 0;
+        ud[i].sig = sig;
+        sig += h->units[i].k_b >= 0 ? 4 : 2;
         ud[i].plane_a = h->units[i].s * K + h->units[i].k_a;
         ud[i].plane_b = h->units[i].k_b >= 0 ? h->units[i].s * K + h->units[i].k_b : -1;
     }
@@ -585,9 +610,63 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     return GB_OK;
 }
 
+// The bank with the recursive Gaussian (GB_SMOOTHER_IIR): row and column recursions through a
+// library-owned workspace.
+gb_status filter_device_iir(gabor_bank *h, const float *d_img, int H, int W, int64_t pitch, void *d_out,
+                            cudaStream_t st)
+{
+    if (h->prec != GB_FP32)
+        return fail(GB_ERR_UNSUPPORTED, "the recursive Gaussian runs on the FP32 path only");
+    for (const Freq &f : h->freqs)
+        if (f.sigma < 0.5) return fail(GB_ERR_UNSUPPORTED, "the recursive Gaussian needs sigma >= 0.5");
+    GB_TRY(ensure_tables(h, H, W, st));
+    const int nf = (int)h->freqs.size();
+    if (!h->d_iirfreq) {
+        std::vector<IirFreq> fq(nf);
+        for (int s = 0; s < nf; ++s) fq[s] = iir_coefficients(h->freqs[s].sigma);
+        GB_TRY(dalloc(&h->d_iirfreq, (size_t)nf));
+        GB_CU(cudaMemcpy(h->d_iirfreq, fq.data(), nf * sizeof(IirFreq), cudaMemcpyHostToDevice));
+    }
+    int pmax = 0, nsig = 0;
+    for (const Freq &f : h->freqs) pmax = std::max(pmax, iir_pad(f.sigma));
+    for (const Unit &u : h->units) nsig += u.k_b >= 0 ? 4 : 2;
+    const bool ext = h->boundary != kBoundaryZero;
+    IirArgs a{};
+    a.img = d_img;
+    a.pitch = pitch;
+    a.H = H;
+    a.W = W;
+    a.out = reinterpret_cast<float2 *>(d_out);
+    a.layout = h->layout;
+    a.nplanes = (int)(h->omega.size() * h->theta.size());
+    a.bmode = h->boundary;
+    a.units = h->d_unitdev;
+    a.freqs = h->d_iirfreq;
+    a.Py = ext ? pmax : 0;
+    a.Hr = H + 2 * a.Py;
+    a.Wxmax = (ext ? pmax : 0) + W + pmax;
+    a.Hcmax = (ext ? pmax : 0) + H + pmax;
+    const size_t row_tmp = (size_t)h->units.size() * a.Hr * a.Wxmax * sizeof(float2);
+    const size_t col_tmp = (size_t)nsig * a.Hcmax * W * sizeof(float);
+    const size_t tmp_bytes = (std::max(row_tmp, col_tmp) + 255) / 256 * 256;
+    const size_t need = tmp_bytes + (size_t)nsig * a.Hr * W * sizeof(float);
+    if (need > h->iirws_bytes) {
+        GB_CU(cudaStreamSynchronize(st));   // earlier work of this handle may still use it
+        dfree(h->d_iirws);
+        h->iirws_bytes = 0;
+        GB_TRY(dalloc(&h->d_iirws, need));
+        h->iirws_bytes = need;
+    }
+    a.tmp = reinterpret_cast<float2 *>(h->d_iirws);
+    a.sig = reinterpret_cast<float *>(h->d_iirws + tmp_bytes);
+    GB_CU(launch_gabor_iir(a, (int)h->units.size(), st));
+    return GB_OK;
+}
+
 gb_status filter_device(gabor_bank *h, const float *d_img, int H, int W, int64_t pitch,
                         void *d_out, cudaStream_t st)
 {
+    if (h->smoother == GB_SMOOTHER_IIR) return filter_device_iir(h, d_img, H, W, pitch, d_out, st);
     if (h->prec != GB_FP32) return filter_device_tc(h, d_img, H, W, pitch, d_out, st);
     GB_TRY(ensure_tables(h, H, W, st));
     BankArgs a{};
@@ -658,6 +737,7 @@ gb_status gabor_bank_create(gabor_bank_t *out, const double *theta, int n_theta,
     if (e == cudaSuccess) e = sdft_fp32_prepare();
     if (e == cudaSuccess) e = sdft_tc_prepare();
     if (e == cudaSuccess) e = gabor_tc_prepare();
+    if (e == cudaSuccess) e = gabor_iir_prepare();
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&h->d_status), sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&h->d_counter), sizeof(int));
@@ -692,6 +772,8 @@ gb_status gabor_bank_destroy(gabor_bank_t h)
     dfree(h->d_counter);
     dfree(h->d_stage_img);
     dfree(h->d_imgs);
+    dfree(h->d_iirfreq);
+    dfree(h->d_iirws);
     free_tc(h);
     if (h->d_sdft_B) cudaFree(h->d_sdft_B);
     h->d_sdft_B = nullptr;
@@ -825,9 +907,9 @@ gb_status gabor_bank_filter_batch(gabor_bank_t h, int n, const float *const *d_i
     GB_TRY(check_sticky());
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (n == 0) return GB_OK;
-    if (h->prec != GB_FP32) {
-        // tensor-core handles: one bank pass (row and column kernels) per image
-        for (int i = 0; i < n; ++i) GB_TRY(filter_device_tc(h, d_imgs[i], H[i], W[i], pitch[i], d_outs[i], st));
+    if (h->prec != GB_FP32 || h->smoother == GB_SMOOTHER_IIR) {
+        // tensor-core handles and the recursive smoother: one bank pass per image
+        for (int i = 0; i < n; ++i) GB_TRY(filter_device(h, d_imgs[i], H[i], W[i], pitch[i], d_outs[i], st));
         return GB_OK;
     }
     int Hm = 0, Wm = 0;
@@ -908,6 +990,11 @@ gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value)
             return fail(GB_ERR_INVALID_ARG, "GB_OPT_BOUNDARY takes GB_BOUNDARY_ZERO, _REPLICATE or _MIRROR");
         h->boundary = (int)value;
         h->tc_H = h->tc_W = 0;   // the tensor-core intermediate's halo rows change meaning
+        return GB_OK;
+    case GB_OPT_SMOOTHER:
+        if (value != GB_SMOOTHER_FIR && value != GB_SMOOTHER_IIR)
+            return fail(GB_ERR_INVALID_ARG, "GB_OPT_SMOOTHER takes GB_SMOOTHER_FIR or GB_SMOOTHER_IIR");
+        h->smoother = (int)value;
         return GB_OK;
     case GB_OPT_LAYOUT:
         if (value != GB_LAYOUT_PLANES && value != GB_LAYOUT_PIXELS)

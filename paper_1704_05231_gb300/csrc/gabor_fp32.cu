@@ -136,14 +136,23 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
         int start, n;
         block_rows(b, start, n);
         float *dst = sm.raw + (size_t)(b & 1) * TH * RW;
-        for (int r = warp; r < n; r += kThreads / 32) {
-            const int yy = ext_coord(start + r, im.H, a.bmode);   // -1: zero row
-            const float *src = im.img + (int64_t)(yy >= 0 ? yy : 0) * im.pitch;
-            for (int j = lane; j < ncols; j += 32) {
-                const int xx = ext_coord(x0 - R + j, im.W, a.bmode);
-                const bool ok = yy >= 0 && xx >= 0;
-                cp_async4(dst + (size_t)r * RW + j, ok ? (const void *)(src + xx) : (const void *)im.img,
-                          ok ? 4 : 0);
+        if (!ext) {
+            for (int r = warp; r < n; r += kThreads / 32) {
+                const int y = start + r;
+                const bool yin = y >= 0 && y < im.H;
+                const float *src = im.img + (int64_t)(yin ? y : 0) * im.pitch;
+                for (int j = lane; j < ncols; j += 32) {
+                    const int gx = x0 - R + j;
+                    const bool ok = yin && gx >= 0 && gx < im.W;
+                    cp_async4(dst + (size_t)r * RW + j, ok ? (const void *)(src + gx) : (const void *)im.img,
+                              ok ? 4 : 0);
+                }
+            }
+        } else {
+            for (int r = warp; r < n; r += kThreads / 32) {
+                const float *src = im.img + (int64_t)ext_coord(start + r, im.H, a.bmode) * im.pitch;
+                for (int j = lane; j < ncols; j += 32)
+                    cp_async4(dst + (size_t)r * RW + j, src + ext_coord(x0 - R + j, im.W, a.bmode), 4);
             }
         }
         cp_async_commit();

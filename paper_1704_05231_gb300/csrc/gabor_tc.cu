@@ -277,13 +277,26 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
                 cur_s = s;
             }
             // patch rows y0 .. y0 + TY - 1, columns x0 - R .. x0 + 127 + R (zero outside the image)
-            for (int r = pwarp; r < TY; r += NP / 32) {
-                const int yy = ext_coord(y0 + r, a.H, a.bmode);   // -1: zero row
-                const float *src = a.img + (int64_t)(yy >= 0 ? yy : 0) * a.pitch;
-                for (int c = lane; c < PW; c += 32) {
-                    const int xx = ext_coord(x0 - R + c, a.W, a.bmode);
-                    const bool ok = yy >= 0 && c < ncols && xx >= 0;
-                    cp_async4(patch + r * PWs + c, ok ? (const void *)(src + xx) : (const void *)a.img, ok ? 4 : 0);
+            if (a.bmode == kBoundaryZero) {
+                for (int r = pwarp; r < TY; r += NP / 32) {
+                    const int y = y0 + r;
+                    const bool yin = y >= 0 && y < a.H;
+                    const float *src = a.img + (int64_t)(yin ? y : 0) * a.pitch;
+                    for (int c = lane; c < PW; c += 32) {
+                        const int gx = x0 - R + c;
+                        const bool ok = yin && c < ncols && gx >= 0 && gx < a.W;
+                        cp_async4(patch + r * PWs + c, ok ? (const void *)(src + gx) : (const void *)a.img, ok ? 4 : 0);
+                    }
+                }
+            } else {
+                for (int r = pwarp; r < TY; r += NP / 32) {
+                    const float *src = a.img + (int64_t)ext_coord(y0 + r, a.H, a.bmode) * a.pitch;
+                    for (int c = lane; c < PW; c += 32) {
+                        const bool ok = c < ncols;
+                        cp_async4(patch + r * PWs + c,
+                                  ok ? (const void *)(src + ext_coord(x0 - R + c, a.W, a.bmode)) : (const void *)a.img,
+                                  ok ? 4 : 0);
+                    }
                 }
             }
             cp_async_commit();
@@ -291,9 +304,11 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
             cp_async_wait<0>();
             // (f - c) 2^-e on the thread's own patch elements; zero samples stay zero
             for (int r = pwarp; r < TY; r += NP / 32) {
-                const bool yok = ext_coord(y0 + r, a.H, a.bmode) >= 0;
+                const int y = y0 + r;
+                const bool yok = a.bmode != kBoundaryZero || (y >= 0 && y < a.H);
                 for (int c = lane; c < PW; c += 32) {
-                    const bool ok = yok && c < ncols && ext_coord(x0 - R + c, a.W, a.bmode) >= 0;
+                    const int gx = x0 - R + c;
+                    const bool ok = yok && c < ncols && (a.bmode != kBoundaryZero || (gx >= 0 && gx < a.W));
                     patch[r * PWs + c] = ok ? (patch[r * PWs + c] - cen) * sc : 0.f;
                 }
             }

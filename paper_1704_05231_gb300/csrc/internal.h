@@ -46,7 +46,7 @@ struct UnitDev {
     int s;              // frequency index
     int plane_a;        // output plane of theta_a  (s * n_theta + k)
     int plane_b;        // output plane of pi - theta_a, or -1 when unpaired
-    int pad_;
+    int sig;            // first column signal of the unit in the recursive path's buffers
 };
 
 // Device view of one frequency: Gaussian taps and the FP32 kernel's tile geometry.
@@ -151,6 +151,27 @@ struct TcGeometry {
     size_t smem_rows, smem_cols;
 };
 
+// ---- recursive-Gaussian bank (gabor_iir.cu) ----
+// Young-van Vliet coefficients of one frequency: w[n] = c0 x[n] + c1 w[n-1] + c2 w[n-2] +
+// c3 w[n-3] (and the same backward), and the extension P on each side of a signal.
+struct IirFreq {
+    float c[4];
+    int P;
+    int pad_[3];
+};
+struct IirArgs {
+    const float *img;
+    int64_t pitch;
+    int H, W;
+    float2 *out;
+    int layout, nplanes, bmode, pad_;
+    const UnitDev *units;
+    const IirFreq *freqs;
+    float2 *tmp;           // scratch: row forward outputs [unit][Hr][Wxmax], then column ones [signal][Hcmax][W]
+    float *sig;            // column signals [signal][Hr][W], row r at y = r - Py
+    int Hr, Py, Wxmax, Hcmax;
+};
+
 // Arguments of the FP32 localized-SDFT kernel (Algorithm 2).
 struct SdftArgs {
     const float *img;
@@ -210,6 +231,9 @@ cudaError_t build_gabor_tc_prefix(const double *unit_w, const TcUnitDev *units, 
 int gabor_tc_row_tile_x();
 int gabor_tc_row_tile_y(int Rmax);
 int gabor_tc_col_tile_y();
+// Recursive-Gaussian bank (gabor_iir.cu).
+cudaError_t gabor_iir_prepare();
+cudaError_t launch_gabor_iir(const IirArgs &a, int nunits, cudaStream_t st);
 // FP32 FMA throughput probe (peak.cu).
 cudaError_t launch_fma_peak(float *out, int blocks, int iters, int packed, cudaStream_t st);
 // Bounded-wait self-test (selftest.cu).
@@ -242,6 +266,7 @@ struct gabor_bank {
     int tile_rows = 0;
     int segments = 0;
     int boundary = 0;                         // gb::BoundaryMode
+    int smoother = 0;                         // 0 truncated Gaussian (FIR), 1 recursive Gaussian (IIR)
     int layout = 0;                           // 0 plane-major, 1 pixel-major bank output
     int ph_margin = 0;                        // phase-table entries before 0 and after the capacity
     std::vector<int> ftile_rows, fsegments;   // per-frequency overrides (0 = global / automatic)
@@ -293,6 +318,10 @@ struct gabor_bank {
     int64_t tc_Hp = 0;
     bool tc_ready = false;
     size_t tc_smem_rows = 0, tc_smem_cols = 0;
+    // recursive-Gaussian path: coefficients per frequency and a library-owned workspace
+    gb::IirFreq *d_iirfreq = nullptr;
+    unsigned char *d_iirws = nullptr;
+    size_t iirws_bytes = 0;
     // device status word (bounded waits)
     int *d_status = nullptr;
     // batch image descriptors

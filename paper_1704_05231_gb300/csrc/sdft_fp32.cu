@@ -104,14 +104,23 @@ __global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
         int start, n;
         block_rows(b, start, n);
         float *dst = raw + (size_t)(b & 1) * TH * a.RW;
-        for (int r = warp; r < n; r += kThreads / 32) {
-            const int yy = ext_coord(start + r, a.H, a.bmode);   // -1: zero row
-            const float *src = a.img + (int64_t)(yy >= 0 ? yy : 0) * a.pitch;
-            for (int j = lane; j < ncols; j += 32) {
-                const int xx = ext_coord(x0 - Mx / 2 + j, a.W, a.bmode);
-                const bool ok = yy >= 0 && xx >= 0;
-                cp_async4(dst + (size_t)r * a.RW + j, ok ? (const void *)(src + xx) : (const void *)a.img,
-                          ok ? 4 : 0);
+        if (a.bmode == kBoundaryZero) {
+            for (int r = warp; r < n; r += kThreads / 32) {
+                const int y = start + r;
+                const bool yin = y >= 0 && y < a.H;
+                const float *src = a.img + (int64_t)(yin ? y : 0) * a.pitch;
+                for (int j = lane; j < ncols; j += 32) {
+                    const int gx = x0 - Mx / 2 + j;
+                    const bool ok = yin && gx >= 0 && gx < a.W;
+                    cp_async4(dst + (size_t)r * a.RW + j, ok ? (const void *)(src + gx) : (const void *)a.img,
+                              ok ? 4 : 0);
+                }
+            }
+        } else {
+            for (int r = warp; r < n; r += kThreads / 32) {
+                const float *src = a.img + (int64_t)ext_coord(start + r, a.H, a.bmode) * a.pitch;
+                for (int j = lane; j < ncols; j += 32)
+                    cp_async4(dst + (size_t)r * a.RW + j, src + ext_coord(x0 - Mx / 2 + j, a.W, a.bmode), 4);
             }
         }
         cp_async_commit();

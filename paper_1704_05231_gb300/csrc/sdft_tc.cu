@@ -77,7 +77,8 @@ struct SdftTcArgs {
     int bmode;             // BoundaryMode of the image beyond its edges
 };
 
-template <typename T>
+// EXT: a non-zero boundary rule (compile-time, so the zero rule keeps its lean load path).
+template <typename T, bool EXT>
 __global__ void __launch_bounds__(384, 1) k_sdft_tc(const SdftTcArgs a)
 {
     extern __shared__ unsigned char smem_dyn[];
@@ -152,8 +153,11 @@ __global__ void __launch_bounds__(384, 1) k_sdft_tc(const SdftTcArgs a)
                 float v = 0.f;
                 if (b < a.My) {
                     const int gy = y - a.My / 2 + b, gx = x0 - a.Mx / 2 + c;
-                    const int yy = ext_coord(gy, a.H, a.bmode), xx = ext_coord(gx, a.W, a.bmode);
-                    if (yy >= 0 && xx >= 0) v = __ldg(a.img + (int64_t)yy * a.pitch + xx);
+                    if (!EXT) {
+                        if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) v = __ldg(a.img + (int64_t)gy * a.pitch + gx);
+                    } else {
+                        v = __ldg(a.img + (int64_t)ext_coord(gy, a.H, a.bmode) * a.pitch + ext_coord(gx, a.W, a.bmode));
+                    }
                 }
                 pre[q] = v;
                 c += 128;
@@ -185,8 +189,11 @@ __global__ void __launch_bounds__(384, 1) k_sdft_tc(const SdftTcArgs a)
                     const int b = idx / PWn, c = idx - b * PWn;
                     const int gy = y - a.My / 2 + b, gx = x0 - a.Mx / 2 + c;
                     float v = 0.f;
-                    const int yy = ext_coord(gy, a.H, a.bmode), xx = ext_coord(gx, a.W, a.bmode);
-                    if (yy >= 0 && xx >= 0) v = __ldg(a.img + (int64_t)yy * a.pitch + xx);
+                    if (!EXT) {
+                        if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) v = __ldg(a.img + (int64_t)gy * a.pitch + gx);
+                    } else {
+                        v = __ldg(a.img + (int64_t)ext_coord(gy, a.H, a.bmode) * a.pitch + ext_coord(gx, a.W, a.bmode));
+                    }
                     patch[b * a.PW + c] = v;
                     m = fmaxf(m, fabsf(v));
                 }
@@ -391,9 +398,13 @@ bool sdft_tc_supported(int Mx, int My)
 
 cudaError_t sdft_tc_prepare()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_sdft_tc<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    cudaError_t e = cudaFuncSetAttribute(k_sdft_tc<__half, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_sdft_tc<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+        e = cudaFuncSetAttribute(k_sdft_tc<__nv_bfloat16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sdft_tc<__half, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sdft_tc<__nv_bfloat16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     return e;
 }
 
@@ -453,10 +464,11 @@ cudaError_t launch_sdft_tc(const float *img, int64_t pitch, int H, int W, float2
     // at least ~half the SM's shared memory, so one CTA (and one 512-column TMEM block) per SM
     const size_t smem = std::max<size_t>(L.total + 1024, 120 * 1024);
     const int grid = std::min(a.ntiles, sm_count);
+    const bool ext = bmode != kBoundaryZero;
     if (bf16)
-        k_sdft_tc<__nv_bfloat16><<<grid, 384, smem, st>>>(a);
+        (ext ? k_sdft_tc<__nv_bfloat16, true> : k_sdft_tc<__nv_bfloat16, false>)<<<grid, 384, smem, st>>>(a);
     else
-        k_sdft_tc<__half><<<grid, 384, smem, st>>>(a);
+        (ext ? k_sdft_tc<__half, true> : k_sdft_tc<__half, false>)<<<grid, 384, smem, st>>>(a);
     return cudaGetLastError();
 }
 
