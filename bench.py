@@ -342,6 +342,25 @@ def sdft_leg(torch, steps, warmup, flush, stream):
         res[prec] = ent
         gbk.close()
         del out
+    # Non-square windows (My x Mx, same 256 bins): the FP32 kernel always runs the horizontal
+    # pass first; its FMA count differs by window orientation, its output bytes do not.
+    from paper_1704_05231_gb300 import GBError
+    for (My, Mx) in ((8, 32), (32, 8)):
+        # FP32: both pass orders (Sec. III-B filter order) and the automatic choice
+        for prec, order in (("fp32", 1), ("fp32", 2), ("fp32", 0), ("fp16_tc", 0)):
+            gbk = GaborBank(precision=prec)
+            gbk.set_option("sdft_order", order)
+            out = torch.empty((My, Mx, Hs, Ws), dtype=torch.complex64, device="cuda")
+            key = f"{prec}_{My}x{Mx}" + {0: "_auto", 1: "_horizontal_first", 2: "_vertical_first"}[order]
+            try:
+                ms = statistics.mean(time_device(torch, lambda: gbk.sdft(img, 4.0, (My, Mx), out=out), steps,
+                                                 warmup, flush, stream))
+                res[key] = {"ms_per_step": ms, "value": n_out / (ms * 1e-3),
+                            "hbm_frac": bytes_ / (ms * 1e-3) / 1e9 / peak}
+            except GBError as exc:   # reported, not hidden
+                res[key] = {"unsupported": str(exc)}
+            gbk.close()
+            del out
     return res
 
 

@@ -157,7 +157,14 @@ typedef enum {
     /* Bank output layout (gb_layout; default GB_LAYOUT_PLANES). */
     GB_OPT_LAYOUT = 5,
     /* The 1-D Gaussian of the bank's passes (gb_smoother; default GB_SMOOTHER_FIR). */
-    GB_OPT_SMOOTHER = 6
+    GB_OPT_SMOOTHER = 6,
+    /* Pass order of the FP32 SDFT (Sec. III-B): 0 = automatic (horizontal first), 1 =
+       horizontal first, 2 = vertical first.  Vertical first needs fewer FMAs when My > Mx but
+       runs on a transposed copy of the image (a handle-owned buffer of H * W floats) with
+       stores across output rows, which costs more than it saves on this store-bound kernel.
+       Full spectra only (half_spectrum = 1 always runs horizontal first).  Results agree to
+       FP32 rounding. */
+    GB_OPT_SDFT_ORDER = 7
 } gb_option;
 
 /* 1-D Gaussian smoothers (GB_OPT_SMOOTHER). */

@@ -774,6 +774,7 @@ gb_status gabor_bank_destroy(gabor_bank_t h)
     dfree(h->d_imgs);
     dfree(h->d_iirfreq);
     dfree(h->d_iirws);
+    dfree(h->d_transp);
     free_tc(h);
     if (h->d_sdft_B) cudaFree(h->d_sdft_B);
     h->d_sdft_B = nullptr;
@@ -865,11 +866,41 @@ gb_status gabor_bank_sdft(gabor_bank_t h, const float *d_img, int H, int W, int6
     a.tw_x = h->d_sdft_tw;
     a.tw_y = h->d_sdft_tw + kMaxSdftM;
     if (h->prec == GB_FP32) {
+        // Filter order (Sec. III-B).  Vertical first (a transposed problem) saves FMAs when
+        // My > Mx (the first FIR pass along the longer side), but its stores run across the
+        // output rows; the kernel is bound by its stores, so the automatic order is
+        // horizontal first and vertical first is taken only on request.
+        const bool yfirst = !half_spectrum && h->sdft_order == 2;
+        if (yfirst) {
+            if ((size_t)H * W > h->transp_elems) {
+                GB_CU(cudaStreamSynchronize(st));   // earlier work of this handle may still read it
+                dfree(h->d_transp);
+                h->transp_elems = 0;
+                GB_TRY(dalloc(&h->d_transp, (size_t)H * W));
+                h->transp_elems = (size_t)H * W;
+            }
+            GB_CU(launch_transpose(d_img, pitch, H, W, h->d_transp, st));
+            SdftArgs t = a;
+            t.img = h->d_transp;
+            t.pitch = H;
+            t.H = W;
+            t.W = H;
+            t.Mx = My;
+            t.My = Mx;
+            t.taps_x = a.taps_y;
+            t.taps_y = a.taps_x;
+            t.tw_x = a.tw_y;
+            t.tw_y = a.tw_x;
+            t.trans = 1;
+            GB_CU(launch_sdft_fp32(t, h->sm_count, st));
+            return GB_OK;
+        }
         GB_CU(launch_sdft_fp32(a, h->sm_count, st));
         return GB_OK;
     }
     if (!sdft_tc_supported(Mx, My))
-        return fail(GB_ERR_UNSUPPORTED, "tensor-core SDFT needs Mx * My <= 256");
+        return fail(GB_ERR_UNSUPPORTED, "tensor-core SDFT: the window's operands do not fit in shared memory "
+                                        "(Mx * My <= 256 and (My / 2 + 1) * Mx bins within the limit)");
     const int bf16 = h->prec == GB_BF16_TC;
     if (h->sdftB_sigma != sigma || h->sdftB_Mx != Mx || h->sdftB_My != My) {
         const size_t bytes = (size_t)sdft_tc_b_bytes(Mx, My);
@@ -990,6 +1021,10 @@ gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value)
             return fail(GB_ERR_INVALID_ARG, "GB_OPT_BOUNDARY takes GB_BOUNDARY_ZERO, _REPLICATE or _MIRROR");
         h->boundary = (int)value;
         h->tc_H = h->tc_W = 0;   // the tensor-core intermediate's halo rows change meaning
+        return GB_OK;
+    case GB_OPT_SDFT_ORDER:
+        if (value < 0 || value > 2) return fail(GB_ERR_INVALID_ARG, "GB_OPT_SDFT_ORDER takes 0, 1 or 2");
+        h->sdft_order = (int)value;
         return GB_OK;
     case GB_OPT_SMOOTHER:
         if (value != GB_SMOOTHER_FIR && value != GB_SMOOTHER_IIR)

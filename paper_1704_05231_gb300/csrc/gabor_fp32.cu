@@ -85,6 +85,8 @@ __device__ __forceinline__ int64_t out_offset(const BankArgs &a, int p, int64_t 
     return a.layout ? (int64_t)x * a.nplanes + p : (int64_t)p * plane + x;
 }
 
+constexpr int kBankThreads = 512;   // 16 warps per CTA (one CTA per SM)
+
 __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkItem it, unsigned char *smem_raw)
 {
     const UnitDev u = a.units[it.unit];
@@ -104,15 +106,15 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
     const Smem sm = carve(smem_raw, f);
     const float4 *taps4 = reinterpret_cast<const float4 *>(sm.taps);
 
-    for (int i = tid; i < f.Tpad + 8; i += kThreads) sm.taps[i] = i < f.Tpad ? f.taps[i] : 0.f;
+    for (int i = tid; i < f.Tpad + 8; i += kBankThreads) sm.taps[i] = i < f.Tpad ? f.taps[i] : 0.f;
     // Demodulation phases at the staged positions (beyond the image only for non-zero rules,
     // whose extended samples are demodulated at their own positions).
     const bool ext = a.bmode != kBoundaryZero;
-    for (int j = tid; j <= SW; j += kThreads) {
+    for (int j = tid; j <= SW; j += kBankThreads) {
         const int gx = x0 - R + j;
         sm.phx[j] = (j < ncols && (ext || (gx >= 0 && gx < im.W))) ? u.phx[gx] : make_float2(0.f, 0.f);
     }
-    for (int i = tid; i < RS * stride; i += kThreads) sm.ring4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = tid; i < RS * stride; i += kBankThreads) sm.ring4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
     // Row blocks: the prologue [ys - R, need_0) in pieces of TH rows, then one block per
     // later chunk k covering [need_{k-1}, need_k), need_k = min(ys + (k+1) TH, ye) + R.
@@ -137,7 +139,7 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
         block_rows(b, start, n);
         float *dst = sm.raw + (size_t)(b & 1) * TH * RW;
         if (!ext) {
-            for (int r = warp; r < n; r += kThreads / 32) {
+            for (int r = warp; r < n; r += kBankThreads / 32) {
                 const int y = start + r;
                 const bool yin = y >= 0 && y < im.H;
                 const float *src = im.img + (int64_t)(yin ? y : 0) * im.pitch;
@@ -149,7 +151,7 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
                 }
             }
         } else {
-            for (int r = warp; r < n; r += kThreads / 32) {
+            for (int r = warp; r < n; r += kBankThreads / 32) {
                 const float *src = im.img + (int64_t)ext_coord(start + r, im.H, a.bmode) * im.pitch;
                 for (int j = lane; j < ncols; j += 32)
                     cp_async4(dst + (size_t)r * RW + j, src + ext_coord(x0 - R + j, im.W, a.bmode), 4);
@@ -164,7 +166,7 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
         block_rows(b, start, n);
         const float *rawb = sm.raw + (size_t)(b & 1) * TH * RW;
         // demodulation f_c, f_s of Eq. 5 into the float2 stage
-        for (int r = warp; r < n; r += kThreads / 32) {
+        for (int r = warp; r < n; r += kBankThreads / 32) {
             float2 *dst = sm.stage + (size_t)r * SW;
             const float *src = rawb + (size_t)r * RW;
             for (int j = lane; j < SW; j += 32) {
@@ -174,21 +176,36 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
             }
         }
         __syncthreads();
-        const int r = (tid & 7) | ((tid >> 5) << 3);
-        const int q = (tid >> 3) & 3;
-        if (r < n) {
+        // 16 (row, 8-column group) outputs per warp, 64 rows x 4 groups in all; the two half
+        // warps take the two halves of the tap chunks and add them with one shuffle.
+        const int hl = lane & 15, half = lane >> 4;
+        const int r = (hl & 7) | ((warp & 7) << 3);
+        const int q = (hl >> 3) | ((warp >> 3) << 1);
+        // Warp-uniform: the warp's 8 rows start inside the block (rows < TH, so every stage read
+        // is in bounds); rows r >= n are computed but not stored.
+        if (8 * (warp & 7) < n) {
             float2 acc[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
-            conv8_linear<float2>(sm.stage + (size_t)r * SW + 8 * q, taps4, nchunks, acc);
+            const int nh = (nchunks + 1) >> 1, c0 = half ? nh : 0;
+            conv8_linear<float2>(sm.stage + (size_t)r * SW + 8 * q + 8 * c0, taps4 + 2 * c0,
+                                 half ? nchunks - nh : nh, acc);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, 16);
+                acc[j].y += __shfl_xor_sync(0xffffffffu, acc[j].y, 16);
+            }
             const int y = start + r;
             const int base = ((y - ring_origin) % RS) * stride + 8 * q;
             const bool yin = ext || (y >= 0 && y < im.H);
             const float2 cy = yin ? u.phy[y] : make_float2(0.f, 0.f);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int jj = 0; jj < 4; ++jj) {
+                if (r >= n) break;
+                const int j = jj + 4 * half;   // each half warp finishes 4 of the 8 outputs
+                const float2 aj = half ? acc[jj + 4] : acc[jj];
                 const float2 px = sm.phx[R + 8 * q + j];
-                const float A = acc[j].x, B = acc[j].y;
+                const float A = aj.x, B = aj.y;
                 // Eq. 5-6: Re J = cos A + sin B, Im J = sin A - cos B
                 const float jr = fmaf(px.x, A, px.y * B);
                 const float ji = fmaf(px.y, A, -px.x * B);
@@ -203,30 +220,29 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
     };
 
     // Vertical pass for output rows [c, c + nout).
+    // Paired units: warps 0-7 smooth (P, Q) of theta_a and warps 8-15 (P', Q') of pi - theta_a
+    // (the .xy / .zw halves of the ring's float4), 8 rows each; unpaired units use warps 0-7.
     auto col_pass = [&](int c, int nout) {
-        const int xl = lane, yb = 8 * warp;
+        const int xl = lane, sub = warp >> 3, yb = 8 * (warp & 7);
         const int x = x0 + xl;
-        if (yb >= nout) return;
+        if (yb >= nout || (!paired && sub)) return;
         const int slot0 = (c - ys + yb) % RS;
         if (paired) {
-            float4 acc[8];
+            float2 acc[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-            conv8_ring<float4>(sm.ring4 + xl, stride, RS, slot0, taps4, nchunks, acc);
+            for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
+            conv8_ring<float2>(sm.ring2 + 2 * xl + sub, 2 * stride, RS, slot0, taps4, nchunks, acc);
             if (x < im.W) {
-                float2 *oa = im.out + out_offset(a, u.plane_a, plane, x);
-                float2 *ob = im.out + out_offset(a, u.plane_b, plane, x);
+                float2 *o = im.out + out_offset(a, sub ? u.plane_b : u.plane_a, plane, x);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int y = c + yb + j;
                     if (yb + j < nout) {
                         const float2 cy = u.phy[y];
-                        const float P = acc[j].x, Q = acc[j].y, P2 = acc[j].z, Q2 = acc[j].w;
-                        // Eq. 7-8 and Eq. 15-16
-                        __stcs(oa + (int64_t)y * ystride,
+                        const float P = acc[j].x, Q = acc[j].y;
+                        // Eq. 7-8 (theta_a) or Eq. 15-16 (pi - theta_a)
+                        __stcs(o + (int64_t)y * ystride,
                                make_float2(fmaf(cy.x, P, cy.y * Q), fmaf(cy.y, P, -cy.x * Q)));
-                        __stcs(ob + (int64_t)y * ystride,
-                               make_float2(fmaf(cy.x, P2, cy.y * Q2), fmaf(cy.y, P2, -cy.x * Q2)));
                     }
                 }
             }
@@ -285,7 +301,7 @@ __device__ __forceinline__ WorkItem decode_item(const BankArgs &a, int item)
 
 // Persistent CTAs pull work items (cost-sorted, largest first) from a device counter that the
 // launcher zeroes before the launch.
-__global__ void __launch_bounds__(kThreads) k_gabor_fp32(const __grid_constant__ BankArgs a)
+__global__ void __launch_bounds__(kBankThreads) k_gabor_fp32(const __grid_constant__ BankArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int next_item;
@@ -314,10 +330,10 @@ cudaError_t launch_gabor_fp32(const BankArgs &a0, int nitems, size_t smem, int s
     cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     int cps = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k_gabor_fp32, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k_gabor_fp32, kBankThreads, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(nitems, std::max(1, cps) * sm_count);
-    k_gabor_fp32<<<grid, kThreads, smem, st>>>(a);
+    k_gabor_fp32<<<grid, kBankThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

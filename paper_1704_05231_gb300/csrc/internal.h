@@ -188,6 +188,7 @@ struct SdftArgs {
     int TpadX, TpadY;
     int TH, seg_len, RS, SW, RW;
     int bmode;           // BoundaryMode
+    int trans;           // 1: a transposed problem (vertical pass first); outputs are written back transposed
 };
 
 // One frequency of the plan.
@@ -218,6 +219,8 @@ cudaError_t launch_gabor_fp32(const BankArgs &a, int nitems, size_t smem, int sm
 cudaError_t gabor_fp32_prepare();
 cudaError_t launch_sdft_fp32(SdftArgs a, int sm_count, cudaStream_t st);
 cudaError_t sdft_fp32_prepare();
+// dst (W x H) = the transpose of an H x W image with row pitch `pitch`.
+cudaError_t launch_transpose(const float *src, int64_t pitch, int H, int W, float *dst, cudaStream_t st);
 // Tensor-core bank.
 TcGeometry gabor_tc_geometry(int R);
 bool gabor_tc_supported(int R);
@@ -267,6 +270,9 @@ struct gabor_bank {
     int segments = 0;
     int boundary = 0;                         // gb::BoundaryMode
     int smoother = 0;                         // 0 truncated Gaussian (FIR), 1 recursive Gaussian (IIR)
+    int sdft_order = 0;                       // 0 automatic, 1 horizontal pass first, 2 vertical first
+    float *d_transp = nullptr;                // transposed image for the vertical-first SDFT
+    size_t transp_elems = 0;
     int layout = 0;                           // 0 plane-major, 1 pixel-major bank output
     int ph_margin = 0;                        // phase-table entries before 0 and after the capacity
     std::vector<int> ftile_rows, fsegments;   // per-frequency overrides (0 = global / automatic)

@@ -13,6 +13,11 @@
 //                             exp(i w0 v yhat) and store F_{u,v}, F_{Mx-u,v};
 //     conjugate fill          F_{(Mx-u)%Mx, My-v} = F*_{u,v} and F_{u, My-v} = F*_{Mx-u,v}
 //                             for 0 < v < My/2 (Algorithm 2, last loop).
+//
+// Filter order (Sec. III-B): the pass over the first axis runs for M/2 + 1 frequencies, the
+// second for all M of the first times M/2 + 1 of its own.  With the FIR passes used here the
+// first pass needs fewer FMAs along the longer window side; on request (vertical first) the
+// host runs this kernel on the transposed image and the stores transpose back.
 #include "internal.h"
 #include "conv_fp32.cuh"
 
@@ -164,6 +169,11 @@ __global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
 
     const int nv = My / 2 + 1;
     const int64_t plane = a.plane;
+    // Output addressing: the kernel's (u, v, y, x), or for a transposed problem (the vertical
+    // pass first, run on the transposed image) the original bin (u, v) -> (v, u) and pixel
+    // (x, y) -> (y, x) of an H' = W, W' = H original.
+    const int64_t step_y = a.trans ? 1 : a.W, step_x = a.trans ? a.H : 1;
+    auto plane_of = [&](int uu, int vv) -> int64_t { return a.trans ? (int64_t)uu * My + vv : (int64_t)vv * Mx + uu; };
     auto col_pass = [&](int c, int nout) {
         const int xl = tid & 31, yg = tid >> 5;
         const int x = x0 + xl;
@@ -191,10 +201,10 @@ __global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
                 if (x < a.W) {
                     const int um = (Mx - u) % Mx, vm = (My - v) % My;
                     const bool fill = !a.half && v > 0 && 2 * v < My;
-                    float2 *o_uv = a.out + ((int64_t)v * Mx + u) * plane + x;
-                    float2 *o_mv = a.out + ((int64_t)v * Mx + um) * plane + x;
-                    float2 *o_mm = a.out + ((int64_t)vm * Mx + um) * plane + x;
-                    float2 *o_um = a.out + ((int64_t)vm * Mx + u) * plane + x;
+                    float2 *o_uv = a.out + plane_of(u, v) * plane + x * step_x;
+                    float2 *o_mv = a.out + plane_of(um, v) * plane + x * step_x;
+                    float2 *o_mm = a.out + plane_of(um, vm) * plane + x * step_x;
+                    float2 *o_um = a.out + plane_of(u, vm) * plane + x * step_x;
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int y = c + yb + j;
@@ -204,7 +214,7 @@ __global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
                             const float2 t = twv[nmod[slot0 + j]];
                             const float P = acc[j].x, Q = acc[j].y, P2 = acc[j].z, Q2 = acc[j].w;
                             const float2 Fa = make_float2(fmaf(t.x, P, t.y * Q), fmaf(t.y, P, -t.x * Q));
-                            const int64_t off = (int64_t)y * a.W;
+                            const int64_t off = (int64_t)y * step_y;
                             __stcs(o_uv + off, Fa);
                             if (fill) __stcs(o_mm + off, make_float2(Fa.x, -Fa.y));
                             if (paired) {
@@ -238,6 +248,29 @@ __global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
         const int c = ys + k * TH;
         col_pass(c, min(TH, ye - c));
     }
+}
+
+// dst[x][y] = src[y][x] for an H x W image (32 x 32 tiles through shared memory).
+__global__ void k_transpose(const float *__restrict__ src, int64_t pitch, int H, int W, float *__restrict__ dst)
+{
+    __shared__ float t[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int y = by + r, x = bx + threadIdx.x;
+        if (y < H && x < W) t[r][threadIdx.x] = src[(int64_t)y * pitch + x];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int x = bx + r, y = by + threadIdx.x;
+        if (x < W && y < H) dst[(int64_t)x * H + y] = t[threadIdx.x][r];
+    }
+}
+
+cudaError_t launch_transpose(const float *src, int64_t pitch, int H, int W, float *dst, cudaStream_t st)
+{
+    const dim3 grid((W + 31) / 32, (H + 31) / 32);
+    k_transpose<<<grid, dim3(32, 8), 0, st>>>(src, pitch, H, W, dst);
+    return cudaGetLastError();
 }
 
 cudaError_t sdft_fp32_prepare()

@@ -109,3 +109,22 @@ def test_sdft_tc_c3_sampled_and_vs_fp32(torch_cuda, precision):
     ref = oracle.sdft(img, 4.0, 16, points=(xs, ys))
     scale = float(np.max(np.abs(f32)))
     assert float(np.max(np.abs(got[:, :, ys, xs] - ref))) <= TC_TOL * scale
+
+
+@pytest.mark.parametrize("order", [0, 1, 2])
+@pytest.mark.parametrize("My,Mx", [(16, 4), (12, 6), (4, 16)])
+def test_filter_order_non_square_windows(order, My, Mx):
+    # Sec. III-B: either pass order gives the same F_{u,v}; the vertical-first order runs on the
+    # transposed image.  Both must match the direct windowed DFT.
+    import torch
+    from paper_1704_05231_gb300 import GaborBank
+    img = synth.pink_noise([31, My, Mx], 45, 70)
+    with GaborBank() as gbk:
+        gbk.set_option("sdft_order", order)
+        got = gbk.sdft(torch.from_numpy(img).cuda(), 3.0, (My, Mx)).cpu().numpy()
+        mirror = GaborBank(boundary="mirror")
+        mirror.set_option("sdft_order", order)
+        gm = mirror.sdft(torch.from_numpy(img).cuda(), 3.0, (My, Mx)).cpu().numpy()
+        mirror.close()
+    assert rel_err(got, oracle.sdft(img, 3.0, My, Mx)) <= FP32_TOL
+    assert rel_err(gm, oracle.sdft(img, 3.0, My, Mx, boundary="mirror")) <= FP32_TOL
