@@ -86,10 +86,11 @@ __device__ __forceinline__ void conv8_linear(const V *__restrict__ src, const fl
     }
 }
 
-// Ring source (column pass): row r of the window is ring[slot(r) * stride], slots advance
-// by 8 per chunk modulo RS.  slot0 and RS are multiples of 8, so a chunk never wraps.
-template <typename V>
-__device__ __forceinline__ void conv8_ring(const V *__restrict__ ring, int stride, int RS, int slot0,
+// Ring source (column pass): row r of the window is ring[slot(r) * STRIDE], slots advance
+// by 8 per chunk modulo RS.  slot0 and RS are multiples of 8, so a chunk never wraps.  STRIDE
+// is a compile-time constant so the 8 loads of a chunk use immediate offsets.
+template <typename V, int STRIDE>
+__device__ __forceinline__ void conv8_ring(const V *__restrict__ ring, int RS, int slot0,
                                            const float4 *__restrict__ taps4, int nchunks, V (&acc)[8])
 {
     V wa[8], wb[8];
@@ -98,27 +99,31 @@ __device__ __forceinline__ void conv8_ring(const V *__restrict__ ring, int strid
         s += 8;
         if (s >= RS) s -= RS;
     };
+    const V *p = ring + s * STRIDE;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) wa[i] = ring[(s + i) * stride];
+    for (int i = 0; i < 8; ++i) wa[i] = p[i * STRIDE];
     float4 t0 = taps4[0], t1 = taps4[1];
     int c = 0;
     for (; c + 2 <= nchunks; c += 2) {
         adv();
+        p = ring + s * STRIDE;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) wb[i] = ring[(s + i) * stride];
+        for (int i = 0; i < 8; ++i) wb[i] = p[i * STRIDE];
         const float4 u0 = taps4[2 * c + 2], u1 = taps4[2 * c + 3];
         conv_step(wa, wb, t0, t1, acc);
         adv();
+        p = ring + s * STRIDE;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) wa[i] = ring[(s + i) * stride];
+        for (int i = 0; i < 8; ++i) wa[i] = p[i * STRIDE];
         t0 = taps4[2 * c + 4];
         t1 = taps4[2 * c + 5];
         conv_step(wb, wa, u0, u1, acc);
     }
     if (c < nchunks) {
         adv();
+        p = ring + s * STRIDE;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) wb[i] = ring[(s + i) * stride];
+        for (int i = 0; i < 8; ++i) wb[i] = p[i * STRIDE];
         conv_step(wa, wb, t0, t1, acc);
     }
 }

@@ -31,8 +31,8 @@ namespace gb {
 namespace {
 
 struct Smem {
-    float4 *ring4;
-    float2 *ring2;
+    float2 *ring2;      // ring of column signals: [RS][33] float2 per plane; paired units keep
+                        // (P, Q) of theta_a in plane 0 and (P', Q') of pi - theta_a in plane 1
     float2 *stage;
     float *raw;      // two buffers of TH x RW floats
     float2 *phx;
@@ -42,9 +42,8 @@ struct Smem {
 __device__ __forceinline__ Smem carve(unsigned char *base, const FreqDev &f)
 {
     Smem s;
-    s.ring4 = reinterpret_cast<float4 *>(base);
     s.ring2 = reinterpret_cast<float2 *>(base);
-    s.stage = reinterpret_cast<float2 *>(s.ring4 + (size_t)f.RS * (kStripW + 1));
+    s.stage = s.ring2 + (size_t)2 * f.RS * (kStripW + 1);
     s.raw = reinterpret_cast<float *>(s.stage + (size_t)f.TH * f.SW);
     s.phx = reinterpret_cast<float2 *>(s.raw + (size_t)2 * f.TH * f.RW);
     s.taps = reinterpret_cast<float *>(s.phx + f.SW + 1);
@@ -114,7 +113,7 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
         const int gx = x0 - R + j;
         sm.phx[j] = (j < ncols && (ext || (gx >= 0 && gx < im.W))) ? u.phx[gx] : make_float2(0.f, 0.f);
     }
-    for (int i = tid; i < RS * stride; i += kBankThreads) sm.ring4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = tid; i < 2 * RS * stride; i += kBankThreads) sm.ring2[i] = make_float2(0.f, 0.f);
 
     // Row blocks: the prologue [ys - R, need_0) in pieces of TH rows, then one block per
     // later chunk k covering [need_{k-1}, need_k), need_k = min(ys + (k+1) TH, ye) + R.
@@ -211,10 +210,8 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
                 const float ji = fmaf(px.y, A, -px.x * B);
                 // Eq. 10: f_cr, f_sr, f_ci, f_si
                 const float fcr = jr * cy.x, fsr = jr * cy.y, fci = ji * cy.x, fsi = ji * cy.y;
-                if (paired)
-                    sm.ring4[base + j] = make_float4(fcr + fsi, fsr - fci, fcr - fsi, fsr + fci);
-                else
-                    sm.ring2[base + j] = make_float2(fcr + fsi, fsr - fci);
+                sm.ring2[base + j] = make_float2(fcr + fsi, fsr - fci);
+                if (paired) sm.ring2[(size_t)RS * stride + base + j] = make_float2(fcr - fsi, fsr + fci);
             }
         }
     };
@@ -231,7 +228,7 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
             float2 acc[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
-            conv8_ring<float2>(sm.ring2 + 2 * xl + sub, 2 * stride, RS, slot0, taps4, nchunks, acc);
+            conv8_ring<float2, kStripW + 1>(sm.ring2 + (size_t)sub * RS * stride + xl, RS, slot0, taps4, nchunks, acc);
             if (x < im.W) {
                 float2 *o = im.out + out_offset(a, sub ? u.plane_b : u.plane_a, plane, x);
 #pragma unroll
@@ -250,7 +247,7 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
             float2 acc[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
-            conv8_ring<float2>(sm.ring2 + xl, stride, RS, slot0, taps4, nchunks, acc);
+            conv8_ring<float2, kStripW + 1>(sm.ring2 + xl, RS, slot0, taps4, nchunks, acc);
             if (x < im.W) {
                 float2 *oa = im.out + out_offset(a, u.plane_a, plane, x);
 #pragma unroll

@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
                 float4 acc[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-                conv8_ring<float4>(sig + xl, stride, a.RS, slot0, ty4, a.TpadY / 8, acc);
+                conv8_ring<float4, kStripW + 1>(sig + xl, a.RS, slot0, ty4, a.TpadY / 8, acc);
                 if (x < a.W) {
                     const int um = (Mx - u) % Mx, vm = (My - v) % My;
                     const bool fill = !a.half && v > 0 && 2 * v < My;
