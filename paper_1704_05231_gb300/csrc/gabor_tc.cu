@@ -37,6 +37,7 @@ namespace {
 constexpr int kRowTileX = 128;   // row kernel: image columns per tile (MMA M)
 constexpr int kRowTileYMax = 64; // row kernel: image rows per tile (64, or 32 for large radii; MMA N = 2 x rows)
 constexpr int kColTileY = 64;    // column kernel: output rows per tile (MMA N)
+constexpr int kRowEpiWarps = 4;  // row kernel: epilogue warps (one per TMEM lane quarter); the rest produce
 
 // (lo, hi) rounded to FP16 in one 32-bit word, lo in the low half (one cvt.rn.f16x2.f32).
 __device__ __forceinline__ uint32_t h2pack(float lo, float hi)
@@ -188,9 +189,9 @@ __device__ __forceinline__ void image_centre(const TcBankArgs &a, float &c, int 
 // Items: (frequency s, tile y, tile x), sorted by frequency; each item runs every unit of s.
 // The image centre c and the scale 2^-e (|f - c| 2^-e < 1, FP16 range) come from k_minmax; the
 // is applied to the staged patch after the image centre c is subtracted (the column pass adds
-// c F[1] back).  Warps 8-15 stage operands (the
+// c F[1] back).  Warps kRowEpiWarps .. 15 stage operands (the
 // phases of the next unit arrive by cp.async while the current unit's operand is built);
-// warps 0-7 are the epilogue, two per TMEM lane quarter, each taking half of the rows.
+// warps 0 .. kRowEpiWarps-1 are the epilogue (one or two per TMEM lane quarter).
 __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant__ TcBankArgs a)
 {
     const int nitems = a.nf * a.row_cnt;
@@ -215,8 +216,8 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
     if (tid == 0) {
         mbar_init(&tmem_full[0], 1);
         mbar_init(&tmem_full[1], 1);
-        mbar_init(&tmem_empty[0], 8);
-        mbar_init(&tmem_empty[1], 8);
+        mbar_init(&tmem_empty[0], kRowEpiWarps);
+        mbar_init(&tmem_empty[1], kRowEpiWarps);
         mbar_init(dm_empty, 1);
         mbar_init(drain, 1);
         *abort_s = 0;
@@ -235,10 +236,10 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
     int e;
     image_centre(a, cen, e);
 
-    if (warp >= 8) {
+    if (warp >= kRowEpiWarps) {
         // -------------------------------------------------------------- producers
-        constexpr int NP = 256;                 // producer threads (warps 8-15)
-        const int ptid = tid - 256, pwarp = warp - 8;
+        constexpr int NP = 32 * (16 - kRowEpiWarps);   // producer threads
+        const int ptid = tid - 32 * kRowEpiWarps, pwarp = warp - kRowEpiWarps;
         const float sc = ldexpf(1.f, -e);
         int cur_s = -1, job = 0;
         // cp.async of unit u's phases cos(w^c x), sin(w^c x) for the tile's columns into
@@ -394,11 +395,11 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
     } else {
         // -------------------------------------------------------------- epilogue
         // Thread = image column x0 + x (TMEM lane x); accumulator columns 2r + {c, s}.  Warp
-        // w reads lane quarter w & 3 and rows [half TY/2, half TY/2 + TY/2), half = w >> 2.
+        // w reads lane quarter w & 3 and rows [rbase, rbase + rpw) of the tile.
         const int quarter = warp & 3, half = warp >> 2;
         const int x = 32 * quarter + lane;
         const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
-        const int rbase = half * (TY / 2);
+        const int rpw = TY / (kRowEpiWarps / 4), rbase = half * rpw;
         int job = 0;
         for (int it = blockIdx.x; it < nitems && !*abort_s; it += gridDim.x) {
             const RowItem w = row_item(a, D, it);
@@ -412,10 +413,13 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
             for (int q = 0; q < nu; ++q, ++job) {
                 const TcUnitDev u = D.units[u0 + q];
                 const int b = job & 1;
-                // row phases of the warp's rows: lane l holds row rbase + l (broadcast by shuffle)
-                const int yl = y0 + rbase + lane;
+                // row phases of the warp's rows: lane l holds rows rbase + l and rbase + 32 + l
+                // (broadcast by shuffle)
+                const int yl = y0 + rbase + lane, yl1 = yl + 32;
                 const bool yok = a.bmode != kBoundaryZero || yl < a.H;
-                const float2 pyl = (lane < TY / 2 && yok) ? __ldg(&u.phy[yl]) : make_float2(0.f, 0.f);
+                const bool yok1 = a.bmode != kBoundaryZero || yl1 < a.H;
+                const float2 pyl = (lane < rpw && yok) ? __ldg(&u.phy[yl]) : make_float2(0.f, 0.f);
+                const float2 pyl1 = (lane + 32 < rpw && yok1) ? __ldg(&u.phy[yl1]) : make_float2(0.f, 0.f);
                 const float2 px = xin ? __ldg(&u.phx[gx]) : make_float2(0.f, 0.f);
                 if (!mbar_wait(&tmem_full[b], (job >> 1) & 1, abort_s)) {
                     ok = false;
@@ -428,7 +432,7 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
                 uint16_t *dst0 = a.sig + u.sig_idx * sstride + (int64_t)((a.Lpad + y0) >> 3) * bstride +
                                  (int64_t)(xin ? gx : 0) * 8;
 #pragma unroll 1
-                for (int c0 = 2 * rbase; c0 < 2 * rbase + TY; c0 += 16) {
+                for (int c0 = 2 * rbase; c0 < 2 * (rbase + rpw); c0 += 16) {
                     float v[16];
                     tmem_ld16(tmem + lane_base + 128u * b + c0, v);
                     const int r0 = c0 >> 1;
@@ -440,8 +444,9 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
                         for (int t = 0; t < 2; ++t) {
                             const int j = 2 * jp + t;
                             const int rl = r0 + j - rbase;
-                            const float2 cy = make_float2(__shfl_sync(0xffffffffu, pyl.x, rl),
-                                                          __shfl_sync(0xffffffffu, pyl.y, rl));
+                            const float2 pr = rl < 32 ? pyl : pyl1;
+                            const float2 cy = make_float2(__shfl_sync(0xffffffffu, pr.x, rl & 31),
+                                                          __shfl_sync(0xffffffffu, pr.y, rl & 31));
                             const float A = v[2 * j] * unscale, B = v[2 * j + 1] * unscale;
                             // Eq. 5-6: Re J = cos A + sin B, Im J = sin A - cos B
                             const float jr = fmaf(px.x, A, px.y * B), ji = fmaf(px.y, A, -px.x * B);
