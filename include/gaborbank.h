@@ -164,7 +164,14 @@ typedef enum {
        stores across output rows, which costs more than it saves on this store-bound kernel.
        Full spectra only (half_spectrum = 1 always runs horizontal first).  Results agree to
        FP32 rounding. */
-    GB_OPT_SDFT_ORDER = 7
+    GB_OPT_SDFT_ORDER = 7,
+    /* FP32 bank kernel schedule: 0 automatic (= 1), 1 phased (all 16 warps of a CTA run a
+       chunk's row pass, then its column pass), 2 pipelined (8 warps run the row passes of
+       chunk k while the other 8 run the column pass of chunk k - 1; the ring buffer holds two
+       chunks of at most 32 rows, hand-over by mbarriers with bounded waits, which report
+       device status 35 and GB_ERR_TIMEOUT when they give up).  Results are identical: the
+       schedules compute every output with the same operations in the same order. */
+    GB_OPT_PIPELINE = 8
 } gb_option;
 
 /* 1-D Gaussian smoothers (GB_OPT_SMOOTHER). */

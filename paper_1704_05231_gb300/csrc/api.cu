@@ -215,13 +215,19 @@ gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
     GB_CU(cudaMemcpy(h->d_T, T.data(), nf * sizeof(int), cudaMemcpyHostToDevice));
     GB_CU(cudaMemcpy(h->d_unitdev, ud.data(), nu * sizeof(UnitDev), cudaMemcpyHostToDevice));
     h->freqdev.resize(nf);
-    h->max_smem = 0;
-    for (int s = 0; s < nf; ++s) {
-        const int tr = (s < (int)h->ftile_rows.size() && h->ftile_rows[s] > 0) ? h->ftile_rows[s] : h->tile_rows;
-        FreqDev fd = gabor_fp32_geometry(h->freqs[s].R, tr);
-        fd.taps = h->d_taps + (size_t)s * h->tpad_max;
-        h->freqdev[s] = fd;
-        h->max_smem = std::max(h->max_smem, gabor_fp32_smem_bytes(fd));
+    // the pipelined schedule where every frequency's geometry fits, else the phased one
+    h->fp32_pipelined = h->fp32_pipeline == 2;
+    for (int pass = 0; pass < 2; ++pass) {
+        h->max_smem = 0;
+        for (int s = 0; s < nf; ++s) {
+            const int tr = (s < (int)h->ftile_rows.size() && h->ftile_rows[s] > 0) ? h->ftile_rows[s] : h->tile_rows;
+            FreqDev fd = gabor_fp32_geometry(h->freqs[s].R, tr, h->fp32_pipelined);
+            fd.taps = h->d_taps + (size_t)s * h->tpad_max;
+            h->freqdev[s] = fd;
+            h->max_smem = std::max(h->max_smem, gabor_fp32_smem_bytes(fd));
+        }
+        if (!h->fp32_pipelined || h->max_smem <= (size_t)(kSmemLimit - kStaticSmemReserve)) break;
+        h->fp32_pipelined = false;
     }
     GB_CU(cudaMemcpy(h->d_freqdev, h->freqdev.data(), nf * sizeof(FreqDev), cudaMemcpyHostToDevice));
     GB_CU(launch_build_taps(h->d_sigma, h->d_lo, h->d_T, nf, h->tpad_max, h->d_taps, st));
@@ -683,6 +689,8 @@ gb_status filter_device(gabor_bank *h, const float *d_img, int H, int W, int64_t
     a.bmode = h->boundary;
     a.layout = h->layout;
     a.nplanes = (int)(h->omega.size() * h->theta.size());
+    a.status = h->d_status;
+    a.pipelined = h->fp32_pipelined ? 1 : 0;
     GB_CU(launch_gabor_fp32(a, n, h->max_smem, h->sm_count, st));
     return GB_OK;
 }
@@ -987,6 +995,8 @@ gb_status gabor_bank_filter_batch(gabor_bank_t h, int n, const float *const *d_i
     a.bmode = h->boundary;
     a.layout = h->layout;
     a.nplanes = (int)(h->omega.size() * h->theta.size());
+    a.status = h->d_status;
+    a.pipelined = h->fp32_pipelined ? 1 : 0;
     GB_CU(launch_gabor_fp32(a, nitems, h->max_smem, h->sm_count, st));
     return GB_OK;
 }
@@ -1013,6 +1023,15 @@ gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value)
             DeviceGuard g(h->device);
             cudaDeviceSynchronize();
             h->tile_rows = (int)value;
+            free_tables(h);
+        }
+        return GB_OK;
+    case GB_OPT_PIPELINE:
+        if (value < 0 || value > 2) return fail(GB_ERR_INVALID_ARG, "GB_OPT_PIPELINE takes 0, 1 or 2");
+        if (h->fp32_pipeline != (int)value) {
+            DeviceGuard g(h->device);
+            cudaDeviceSynchronize();
+            h->fp32_pipeline = (int)value;
             free_tables(h);
         }
         return GB_OK;

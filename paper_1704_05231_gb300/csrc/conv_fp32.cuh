@@ -13,18 +13,9 @@
 namespace gb {
 
 // Two independent round-to-nearest FMAs in one packed FP32x2 instruction (sm_100+): the same
-// results as two fmaf calls, half the issue slots.
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
-{
-    float2 d;
-    asm("{\n.reg .b64 ra, rb, rc, rd;\n"
-        "mov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\nmov.b64 rc, {%6, %7};\n"
-        "fma.rn.f32x2 rd, ra, rb, rc;\n"
-        "mov.b64 {%0, %1}, rd;\n}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return d;
-}
+// results as two fmaf calls, half the issue slots.  The compiler intrinsic lets register
+// allocation keep operand pairs in place (no packing moves).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 __device__ __forceinline__ float4 fmav(float4 w, float t, float4 a)
 {

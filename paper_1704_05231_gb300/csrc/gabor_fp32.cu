@@ -25,6 +25,7 @@
 
 #include "internal.h"
 #include "conv_fp32.cuh"
+#include "tc_common.cuh"
 
 namespace gb {
 
@@ -37,6 +38,7 @@ struct Smem {
     float *raw;      // two buffers of TH x RW floats
     float2 *phx;
     float *taps;
+    uint64_t *bars;  // pipelined variant: full[2], empty[2]; then the abort flag
 };
 
 __device__ __forceinline__ Smem carve(unsigned char *base, const FreqDev &f)
@@ -47,6 +49,7 @@ __device__ __forceinline__ Smem carve(unsigned char *base, const FreqDev &f)
     s.raw = reinterpret_cast<float *>(s.stage + (size_t)f.TH * f.SW);
     s.phx = reinterpret_cast<float2 *>(s.raw + (size_t)2 * f.TH * f.RW);
     s.taps = reinterpret_cast<float *>(s.phx + f.SW + 1);
+    s.bars = reinterpret_cast<uint64_t *>(((uintptr_t)(s.taps + f.Tpad + 8) + 7) & ~(uintptr_t)7);
     return s;
 }
 
@@ -56,10 +59,10 @@ size_t gabor_fp32_smem_bytes(const FreqDev &f)
 {
     return (size_t)f.RS * (kStripW + 1) * sizeof(float4) + (size_t)f.TH * f.SW * sizeof(float2) +
            (size_t)2 * f.TH * f.RW * sizeof(float) + (size_t)(f.SW + 1) * sizeof(float2) +
-           (size_t)(f.Tpad + 8) * sizeof(float);
+           (size_t)(f.Tpad + 8) * sizeof(float) + 8 + 4 * sizeof(uint64_t) + 16;
 }
 
-FreqDev gabor_fp32_geometry(int R, int tile_rows)
+FreqDev gabor_fp32_geometry(int R, int tile_rows, bool pipelined)
 {
     FreqDev f{};
     f.R = R;
@@ -67,10 +70,12 @@ FreqDev gabor_fp32_geometry(int R, int tile_rows)
     f.Tpad = round_up(f.T, 8);
     f.SW = stage_width(kStripW + f.Tpad);
     f.RW = round_up(kStripW + f.T - 1, 4);
-    int TH = tile_rows > 0 ? tile_rows : 64;
+    // the pipelined variant rows 32 per chunk at most, and its ring holds two chunks
+    int TH = tile_rows > 0 ? tile_rows : (pipelined ? 32 : 64);
+    if (pipelined) TH = std::min(TH, 32);
     for (;;) {
         f.TH = TH;
-        f.RS = round_up(TH + f.T - 1, 8);
+        f.RS = round_up((pipelined ? 2 * TH : TH) + f.T - 1, 8);
         if (gabor_fp32_smem_bytes(f) <= (size_t)(kSmemLimit - kStaticSmemReserve) || TH <= 8) break;
         TH /= 2;
     }
@@ -86,7 +91,12 @@ __device__ __forceinline__ int64_t out_offset(const BankArgs &a, int p, int64_t 
 
 constexpr int kBankThreads = 512;   // 16 warps per CTA (one CTA per SM)
 
-__device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkItem it, unsigned char *smem_raw)
+// PIPE = false: all 16 warps run the phases of a chunk in turn (row pass, then column pass).
+// PIPE = true: warps 0-7 run the row passes, warps 8-15 the column passes, one chunk apart;
+// the ring holds two chunks and mbarriers hand chunks over (bounded waits).  Returns false
+// when a wait gave up (the status word is set).
+template <bool PIPE>
+__device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkItem it, unsigned char *smem_raw)
 {
     const UnitDev u = a.units[it.unit];
     const FreqDev f = a.freqs[u.s];
@@ -104,7 +114,25 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
     const int64_t ystride = a.layout ? (int64_t)im.W * a.nplanes : (int64_t)im.W;   // between output rows
     const Smem sm = carve(smem_raw, f);
     const float4 *taps4 = reinterpret_cast<const float4 *>(sm.taps);
+    constexpr int kRowWarps = PIPE ? 8 : 16;   // warps that load rows and run the row pass
+    constexpr int kRB = PIPE ? 4 : 8;          // 8-row blocks of one row-pass sweep
+    auto sync_rows = [&]() {
+        if (PIPE)
+            named_barrier(1, kRowWarps * 32);
+        else
+            __syncthreads();
+    };
 
+    uint64_t *full = sm.bars, *empty = sm.bars + 2;   // pipelined hand-over, per ring half
+    volatile int *abort_s = reinterpret_cast<volatile int *>(sm.bars + 4);
+    if (PIPE && tid == 0) {
+        mbar_init(&full[0], kRowWarps * 32);
+        mbar_init(&full[1], kRowWarps * 32);
+        mbar_init(&empty[0], (kBankThreads / 32 - kRowWarps) * 32);
+        mbar_init(&empty[1], (kBankThreads / 32 - kRowWarps) * 32);
+        *abort_s = 0;
+        mbar_fence_init();
+    }
     for (int i = tid; i < f.Tpad + 8; i += kBankThreads) sm.taps[i] = i < f.Tpad ? f.taps[i] : 0.f;
     // Demodulation phases at the staged positions (beyond the image only for non-zero rules,
     // whose extended samples are demodulated at their own positions).
@@ -138,7 +166,7 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
         block_rows(b, start, n);
         float *dst = sm.raw + (size_t)(b & 1) * TH * RW;
         if (!ext) {
-            for (int r = warp; r < n; r += kBankThreads / 32) {
+            for (int r = warp; r < n; r += kRowWarps) {
                 const int y = start + r;
                 const bool yin = y >= 0 && y < im.H;
                 const float *src = im.img + (int64_t)(yin ? y : 0) * im.pitch;
@@ -150,7 +178,7 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
                 }
             }
         } else {
-            for (int r = warp; r < n; r += kBankThreads / 32) {
+            for (int r = warp; r < n; r += kRowWarps) {
                 const float *src = im.img + (int64_t)ext_coord(start + r, im.H, a.bmode) * im.pitch;
                 for (int j = lane; j < ncols; j += 32)
                     cp_async4(dst + (size_t)r * RW + j, src + ext_coord(x0 - R + j, im.W, a.bmode), 4);
@@ -164,25 +192,32 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
         int start, n;
         block_rows(b, start, n);
         const float *rawb = sm.raw + (size_t)(b & 1) * TH * RW;
-        // demodulation f_c, f_s of Eq. 5 into the float2 stage
-        for (int r = warp; r < n; r += kBankThreads / 32) {
-            float2 *dst = sm.stage + (size_t)r * SW;
-            const float *src = rawb + (size_t)r * RW;
-            for (int j = lane; j < SW; j += 32) {
-                const float v = j < ncols ? src[j] : 0.f;
-                const float2 ph = sm.phx[j];
-                dst[j] = make_float2(v * ph.x, v * ph.y);
+        // demodulation f_c, f_s of Eq. 5 into the float2 stage: a lane keeps the phase of its
+        // column and demodulates the warp's rows (at most 4), all loads issued first
+        constexpr int kRowsPerWarp = 4;   // TH <= 4 kRowWarps
+        for (int j = lane; j < SW; j += 32) {
+            const float2 ph = sm.phx[j];
+            float v[kRowsPerWarp];
+#pragma unroll
+            for (int i = 0; i < kRowsPerWarp; ++i) {
+                const int r = warp + i * kRowWarps;
+                v[i] = (r < n && j < ncols) ? rawb[(size_t)r * RW + j] : 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < kRowsPerWarp; ++i) {
+                const int r = warp + i * kRowWarps;
+                if (r < n) sm.stage[(size_t)r * SW + j] = make_float2(v[i] * ph.x, v[i] * ph.y);
             }
         }
-        __syncthreads();
-        // 16 (row, 8-column group) outputs per warp, 64 rows x 4 groups in all; the two half
-        // warps take the two halves of the tap chunks and add them with one shuffle.
+        sync_rows();
+        // 16 (row, 8-column group) outputs per warp, 8 kRB rows x 4 groups in all; the two
+        // half warps take the two halves of the tap chunks and add them with one shuffle.
         const int hl = lane & 15, half = lane >> 4;
-        const int r = (hl & 7) | ((warp & 7) << 3);
-        const int q = (hl >> 3) | ((warp >> 3) << 1);
+        const int r = (hl & 7) | ((warp % kRB) << 3);
+        const int q = (hl >> 3) | ((warp / kRB) << 1);
         // Warp-uniform: the warp's 8 rows start inside the block (rows < TH, so every stage read
         // is in bounds); rows r >= n are computed but not stored.
-        if (8 * (warp & 7) < n) {
+        if (8 * (warp % kRB) < n) {
             float2 acc[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
@@ -217,14 +252,18 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
     };
 
     // Vertical pass for output rows [c, c + nout).
-    // Paired units: warps 0-7 smooth (P, Q) of theta_a and warps 8-15 (P', Q') of pi - theta_a
-    // (the .xy / .zw halves of the ring's float4), 8 rows each; unpaired units use warps 0-7.
+    // Paired units: one half of the column warps smooths (P, Q) of theta_a, the other (P', Q')
+    // of pi - theta_a, 8 rows per warp at a time; unpaired units use all column warps on rows.
     auto col_pass = [&](int c, int nout) {
-        const int xl = lane, sub = warp >> 3, yb = 8 * (warp & 7);
+        const int cw = PIPE ? warp - 8 : warp;          // column-warp index
+        const int ncw = PIPE ? 8 : 16;
+        const int xl = lane;
+        const int sub = paired ? cw / (ncw / 2) : 0;
+        const int ybase = 8 * (paired ? cw % (ncw / 2) : cw);
+        const int ystep = 8 * (paired ? ncw / 2 : ncw);
         const int x = x0 + xl;
-        if (yb >= nout || (!paired && sub)) return;
-        const int slot0 = (c - ys + yb) % RS;
-        if (paired) {
+        for (int yb = ybase; yb < nout; yb += ystep) {
+            const int slot0 = (c - ys + yb) % RS;
             float2 acc[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
@@ -243,45 +282,73 @@ __device__ __forceinline__ void gabor_fp32_item(const BankArgs &a, const WorkIte
                     }
                 }
             }
-        } else {
-            float2 acc[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
-            conv8_ring<float2, kStripW + 1>(sm.ring2 + xl, RS, slot0, taps4, nchunks, acc);
-            if (x < im.W) {
-                float2 *oa = im.out + out_offset(a, u.plane_a, plane, x);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int y = c + yb + j;
-                    if (yb + j < nout) {
-                        const float2 cy = u.phy[y];
-                        const float P = acc[j].x, Q = acc[j].y;
-                        __stcs(oa + (int64_t)y * ystride,
-                               make_float2(fmaf(cy.x, P, cy.y * Q), fmaf(cy.y, P, -cy.x * Q)));
-                    }
-                }
-            }
         }
     };
 
-    issue(0);
-    int b = 0;
-    for (int k = 0; k < nch; ++k) {
-        const int last = (k == 0) ? npro : npro + k;   // blocks [b, last) feed chunk k
-        for (; b < last; ++b) {
-            if (b + 1 < nblocks) {
-                issue(b + 1);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
+    if (!PIPE) {
+        issue(0);
+        int b = 0;
+        for (int k = 0; k < nch; ++k) {
+            const int last = (k == 0) ? npro : npro + k;   // blocks [b, last) feed chunk k
+            for (; b < last; ++b) {
+                if (b + 1 < nblocks) {
+                    issue(b + 1);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                __syncthreads();   // raw block b visible; previous stage / ring readers done
+                row_pass(b);
             }
-            __syncthreads();   // raw block b visible; previous stage / ring readers done
-            row_pass(b);
+            __syncthreads();       // ring rows of chunk k complete
+            const int c = ys + k * TH;
+            col_pass(c, min(TH, ye - c));
         }
-        __syncthreads();       // ring rows of chunk k complete
-        const int c = ys + k * TH;
-        col_pass(c, min(TH, ye - c));
+        return true;
     }
+    // ---- pipelined: chunk k's rows (warps 0-7) overlap chunk k-1's column pass (warps 8-15)
+    __syncthreads();   // taps, phases, zeroed ring and barriers visible to both groups
+    bool ok = true;
+    if (warp < kRowWarps) {
+        issue(0);
+        int b = 0;
+        for (int k = 0; k < nch; ++k) {
+            // chunk k's rows reuse the ring slots of chunk k-2's window
+            const bool failed = k >= 2 && !mbar_wait(&empty[k & 1], ((k - 2) >> 1) & 1, abort_s);
+            if (named_barrier_or(1, kRowWarps * 32, failed)) {
+                ok = false;
+                break;
+            }
+            const int last = (k == 0) ? npro : npro + k;
+            for (; b < last; ++b) {
+                if (b + 1 < nblocks) {
+                    issue(b + 1);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                sync_rows();       // raw block b visible; the stage is free
+                row_pass(b);
+            }
+            mbar_arrive(&full[k & 1]);   // this thread's ring rows of chunk k are written
+        }
+        cp_async_wait<0>();
+    } else {
+        for (int k = 0; k < nch; ++k) {
+            if (!mbar_wait(&full[k & 1], (k >> 1) & 1, abort_s)) {
+                ok = false;
+                break;
+            }
+            const int c = ys + k * TH;
+            col_pass(c, min(TH, ye - c));
+            mbar_arrive(&empty[k & 1]);
+        }
+    }
+    if (!ok && lane == 0) {
+        *abort_s = 1;
+        if (a.status) atomicExch(a.status, 35);
+    }
+    return ok;
 }
 
 // Work item `item` of a single-image launch, decoded from the groups (uniform per CTA).
@@ -298,6 +365,8 @@ __device__ __forceinline__ WorkItem decode_item(const BankArgs &a, int item)
 
 // Persistent CTAs pull work items (cost-sorted, largest first) from a device counter that the
 // launcher zeroes before the launch.
+// A CTA stops taking items after a bounded wait gave up (pipelined schedule).
+template <bool PIPE>
 __global__ void __launch_bounds__(kBankThreads) k_gabor_fp32(const __grid_constant__ BankArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -307,15 +376,26 @@ __global__ void __launch_bounds__(kBankThreads) k_gabor_fp32(const __grid_consta
         __syncthreads();
         const int item = next_item;
         if (item >= a.nitems) break;
-        gabor_fp32_item(a, a.items ? a.items[item] : decode_item(a, item), smem_raw);
-        __syncthreads();   // shared memory is reused by the next item
+        const WorkItem it = a.items ? a.items[item] : decode_item(a, item);
+        const bool ok = gabor_fp32_item<PIPE>(a, it, smem_raw);
+        // shared memory is reused by the next item
+        const bool failed = __syncthreads_or(!ok);
+        if (PIPE && threadIdx.x == 0) {
+            const FreqDev &f = a.freqs[a.units[it.unit].s];
+            uint64_t *bars = carve(smem_raw, f).bars;
+            for (int i = 0; i < 4; ++i) mbar_inval(bars + i);
+        }
+        if (failed) break;
     }
 }
 
 cudaError_t gabor_fp32_prepare()
 {
     // the kernel's own static shared memory (the work-queue word) counts against the limit
-    return cudaFuncSetAttribute(k_gabor_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_gabor_fp32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemLimit - kStaticSmemReserve);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_gabor_fp32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kSmemLimit - kStaticSmemReserve);
 }
 
@@ -327,10 +407,14 @@ cudaError_t launch_gabor_fp32(const BankArgs &a0, int nitems, size_t smem, int s
     cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     int cps = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k_gabor_fp32, kBankThreads, smem);
+    e = a.pipelined ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k_gabor_fp32<true>, kBankThreads, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k_gabor_fp32<false>, kBankThreads, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(nitems, std::max(1, cps) * sm_count);
-    k_gabor_fp32<<<grid, kBankThreads, smem, st>>>(a);
+    if (a.pipelined)
+        k_gabor_fp32<true><<<grid, kBankThreads, smem, st>>>(a);
+    else
+        k_gabor_fp32<false><<<grid, kBankThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

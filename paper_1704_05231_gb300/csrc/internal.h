@@ -96,6 +96,8 @@ struct BankArgs {
     int bmode;                // BoundaryMode
     int layout;               // 0: out[plane][y][x], 1: out[y][x][plane]
     int nplanes;              // n_freq * n_theta
+    int *status;              // device status word (pipelined variant's bounded waits)
+    int pipelined;            // 1: warp-specialised row / column pipeline (host-side choice)
     ItemGroup groups[kMaxGroups];
 };
 
@@ -213,7 +215,7 @@ cudaError_t launch_build_taps(const double *d_sigma, const int *d_lo, const int 
                               int tpad_max, float *taps, cudaStream_t st);
 cudaError_t launch_build_twiddles(int M, float2 *tw, cudaStream_t st);
 // Tile geometry of the FP32 bank kernel for radius R (tile_rows = 0: automatic).
-FreqDev gabor_fp32_geometry(int R, int tile_rows);
+FreqDev gabor_fp32_geometry(int R, int tile_rows, bool pipelined);
 size_t gabor_fp32_smem_bytes(const FreqDev &f);
 cudaError_t launch_gabor_fp32(const BankArgs &a, int nitems, size_t smem, int sm_count, cudaStream_t st);
 cudaError_t gabor_fp32_prepare();
@@ -270,6 +272,8 @@ struct gabor_bank {
     int segments = 0;
     int boundary = 0;                         // gb::BoundaryMode
     int smoother = 0;                         // 0 truncated Gaussian (FIR), 1 recursive Gaussian (IIR)
+    int fp32_pipeline = 0;                    // GB_OPT_PIPELINE (0 automatic, 1 phased, 2 pipelined)
+    bool fp32_pipelined = false;              // schedule of the current tables
     int sdft_order = 0;                       // 0 automatic, 1 horizontal pass first, 2 vertical first
     float *d_transp = nullptr;                // transposed image for the vertical-first SDFT
     size_t transp_elems = 0;

@@ -212,3 +212,67 @@ def test_tc_bank_bf16_is_refused(torch_cuda):
         with pytest.raises(GBError) as ei:
             gbk.filter(torch.zeros((32, 32), dtype=torch.float32, device="cuda"))
         assert ei.value.status == -4
+
+
+def _schedules(torch, imgs, th, om, sg, opts=(), **kw):
+    """Outputs of the phased (GB_OPT_PIPELINE = 1) and pipelined (= 2) FP32 schedules."""
+    from paper_1704_05231_gb300 import GaborBank
+    res = []
+    for sched in (1, 2):
+        with GaborBank(th, om, sg, **kw) as gbk:
+            gbk.set_option("pipeline", sched)
+            for k, v in opts:
+                gbk.set_option(k, v)
+            outs = [gbk.filter(torch.from_numpy(i).cuda()).cpu().numpy() for i in imgs]
+            gbk.device_status()
+        res.append(outs)
+    return res
+
+
+@pytest.mark.parametrize("H,W", [(1, 50), (37, 75), (129, 33), (200, 161), (300, 96)])
+def test_pipelined_schedule_matches_phased_and_oracle(torch_cuda, H, W):
+    # Warp-specialised schedule: same operations per output, so the results are identical.
+    img = synth.pink_noise([17, H, W], H, W)
+    th = [0.0, 0.6, math.pi / 2, math.pi - 0.6, 2.0]
+    om = [math.pi / 3, 0.4, 0.2]
+    sg = [1.5, 5.0, 11.0]
+    (a,), (b,) = _schedules(torch_cuda, [img], th, om, sg)
+    assert np.array_equal(a, b)
+    assert rel_err(b, oracle.gabor_bank(img, th, om, sg)) <= FP32_TOL
+
+
+@pytest.mark.parametrize("tile_rows,segments", [(8, 0), (16, 3), (32, 1), (64, 2)])
+def test_pipelined_schedule_tilings(torch_cuda, tile_rows, segments):
+    img = synth.paper_like(4, 230, 170)
+    th, om, sg = c2_bank()
+    (a,), (b,) = _schedules(torch_cuda, [img], th, om, sg,
+                            opts=(("tile_rows", tile_rows), ("segments", segments)))
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("boundary", ["zero", "replicate", "mirror"])
+@pytest.mark.parametrize("layout", ["planes", "pixels"])
+def test_pipelined_schedule_boundary_and_layout(torch_cuda, boundary, layout):
+    img = synth.pink_noise(23, 90, 140)
+    th, om, sg = c1_bank()
+    (a,), (b,) = _schedules(torch_cuda, [img], th, om, sg, boundary=boundary, layout=layout)
+    assert np.array_equal(a, b)
+    if layout == "planes":
+        assert rel_err(b, oracle.gabor_bank(img, th, om, sg, boundary=boundary)) <= FP32_TOL
+
+
+def test_pipelined_schedule_batch_and_large_radius(torch_cuda):
+    from paper_1704_05231_gb300 import GaborBank
+    torch = torch_cuda
+    imgs = [synth.pink_noise([29, i], h, w) for i, (h, w) in enumerate([(40, 70), (128, 96), (333, 257)])]
+    th = [0.3, math.pi - 0.3, math.pi / 2]
+    om, sg = [0.05, 0.9], [53.0, 2.0]   # R = 159: the largest FP32 radius, pipelined tile of 8 rows
+    (sa, sb) = _schedules(torch, imgs, th, om, sg)
+    for x, y in zip(sa, sb):
+        assert np.array_equal(x, y)
+    with GaborBank(th, om, sg) as gbk:
+        gbk.set_option("pipeline", 2)
+        batch = [o.cpu().numpy() for o in gbk.filter_batch([torch.from_numpy(i).cuda() for i in imgs])]
+        gbk.device_status()
+    for x, y in zip(sb, batch):
+        assert np.array_equal(x, y)
