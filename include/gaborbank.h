@@ -171,7 +171,14 @@ typedef enum {
        chunks of at most 32 rows, hand-over by mbarriers with bounded waits, which report
        device status 35 and GB_ERR_TIMEOUT when they give up).  Results are identical: the
        schedules compute every output with the same operations in the same order. */
-    GB_OPT_PIPELINE = 8
+    GB_OPT_PIPELINE = 8,
+    /* Form of the FP32 bank's row pass (Eq. 5-6), J(x) = sum_d S(d) f(x + d) exp(-i omega^c d):
+       0 automatic (= 2), 1 demodulate by (cos, sin)(omega^c x), smooth with the real Gaussian,
+       remodulate (the three steps as the paper writes them), 2 one pass with the modulated
+       taps S(d) exp(-i omega^c d) (the same sum in one step; the same packed FMAs, no
+       demodulated copy of the rows).  The column pass is the same in both.  Results agree to
+       FP32 rounding (each within 1e-5 max|out| of the FP64 oracle). */
+    GB_OPT_ROW_PASS = 9
 } gb_option;
 
 /* 1-D Gaussian smoothers (GB_OPT_SMOOTHER). */

@@ -221,7 +221,7 @@ gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
         h->max_smem = 0;
         for (int s = 0; s < nf; ++s) {
             const int tr = (s < (int)h->ftile_rows.size() && h->ftile_rows[s] > 0) ? h->ftile_rows[s] : h->tile_rows;
-            FreqDev fd = gabor_fp32_geometry(h->freqs[s].R, tr, h->fp32_pipelined);
+            FreqDev fd = gabor_fp32_geometry(h->freqs[s].R, tr, h->fp32_pipelined, h->fp32_row_form != 1);
             fd.taps = h->d_taps + (size_t)s * h->tpad_max;
             h->freqdev[s] = fd;
             h->max_smem = std::max(h->max_smem, gabor_fp32_smem_bytes(fd));
@@ -691,6 +691,7 @@ gb_status filter_device(gabor_bank *h, const float *d_img, int H, int W, int64_t
     a.nplanes = (int)(h->omega.size() * h->theta.size());
     a.status = h->d_status;
     a.pipelined = h->fp32_pipelined ? 1 : 0;
+    a.mtaps = h->fp32_row_form != 1 ? 1 : 0;
     GB_CU(launch_gabor_fp32(a, n, h->max_smem, h->sm_count, st));
     return GB_OK;
 }
@@ -997,6 +998,7 @@ gb_status gabor_bank_filter_batch(gabor_bank_t h, int n, const float *const *d_i
     a.nplanes = (int)(h->omega.size() * h->theta.size());
     a.status = h->d_status;
     a.pipelined = h->fp32_pipelined ? 1 : 0;
+    a.mtaps = h->fp32_row_form != 1 ? 1 : 0;
     GB_CU(launch_gabor_fp32(a, nitems, h->max_smem, h->sm_count, st));
     return GB_OK;
 }
@@ -1032,6 +1034,15 @@ gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value)
             DeviceGuard g(h->device);
             cudaDeviceSynchronize();
             h->fp32_pipeline = (int)value;
+            free_tables(h);
+        }
+        return GB_OK;
+    case GB_OPT_ROW_PASS:
+        if (value < 0 || value > 2) return fail(GB_ERR_INVALID_ARG, "GB_OPT_ROW_PASS takes 0, 1 or 2");
+        if (h->fp32_row_form != (int)value) {
+            DeviceGuard g(h->device);
+            cudaDeviceSynchronize();
+            h->fp32_row_form = (int)value;
             free_tables(h);
         }
         return GB_OK;

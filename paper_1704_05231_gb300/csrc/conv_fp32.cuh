@@ -119,6 +119,59 @@ __device__ __forceinline__ void conv8_ring(const V *__restrict__ ring, int RS, i
     }
 }
 
+// Complex taps over a real window (the row pass in modulated-tap form): acc[j] += win[j + d] g[d]
+// for the 8 complex taps of one chunk, win = lo[0..7] ++ hi[0..7]; one packed FMA per product.
+__device__ __forceinline__ void conv_step_ct(const float (&lo)[8], const float (&hi)[8], const float2 (&g)[8],
+                                             float2 (&acc)[8])
+{
+#pragma unroll
+    for (int d = 0; d < 8; ++d)
+#pragma unroll
+        for (int j = 0; j < 8 - d; ++j) acc[j] = ffma2(g[d], make_float2(lo[j + d], lo[j + d]), acc[j]);
+#pragma unroll
+    for (int d = 1; d < 8; ++d)
+#pragma unroll
+        for (int j = 8 - d; j < 8; ++j) acc[j] = ffma2(g[d], make_float2(hi[j + d - 8], hi[j + d - 8]), acc[j]);
+}
+
+__device__ __forceinline__ void load_ctaps(float2 (&g)[8], const float4 *__restrict__ g4)
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 v = g4[i];
+        g[2 * i] = make_float2(v.x, v.y);
+        g[2 * i + 1] = make_float2(v.z, v.w);
+    }
+}
+
+// Contiguous real source, complex taps: out[j] = sum_t src[j + t] g[t], j < 8.  Reads
+// src[0 .. 8 * nchunks + 7] and g[0 .. 8 * nchunks + 7] (g4: two complex taps per float4).
+__device__ __forceinline__ void conv8_linear_ct(const float *__restrict__ src, const float4 *__restrict__ g4,
+                                                int nchunks, float2 (&acc)[8])
+{
+    float wa[8], wb[8];
+    float2 ga[8], gb[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) wa[i] = src[i];
+    load_ctaps(ga, g4);
+    int c = 0;
+    for (; c + 2 <= nchunks; c += 2) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) wb[i] = src[8 * (c + 1) + i];
+        load_ctaps(gb, g4 + 4 * (c + 1));
+        conv_step_ct(wa, wb, ga, acc);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) wa[i] = src[8 * (c + 2) + i];
+        load_ctaps(ga, g4 + 4 * (c + 2));
+        conv_step_ct(wb, wa, gb, acc);
+    }
+    if (c < nchunks) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) wb[i] = src[8 * (c + 1) + i];
+        conv_step_ct(wa, wb, ga, acc);
+    }
+}
+
 // 4-byte global -> shared async copy; src_bytes = 0 writes a zero without reading.
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem, int src_bytes)
 {

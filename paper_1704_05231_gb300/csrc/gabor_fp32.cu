@@ -7,11 +7,14 @@
 // segment in chunks of TH rows:
 //
 //   row pass  (Eq. 5-6)   rows of f (strip plus an R-wide halo) arrive by cp.async into a
-//                         double buffer, one row block ahead of use; they are demodulated
-//                         by (cos, sin)(omega^c k), smoothed with the real Gaussian S (8
-//                         outputs x 8 taps register blocks), remodulated into J_theta and
-//                         immediately demodulated by (cos, sin)(omega^s y) into the column
-//                         signals of Eq. 10:
+//                         double buffer, one row block ahead of use, and become
+//                             J_theta(x) = sum_d S(d) f(x + d) exp(-i omega^c d)
+//                         in one of two forms: demodulate by (cos, sin)(omega^c k), smooth
+//                         with the real Gaussian S, remodulate (Eq. 5-6 step by step), or one
+//                         pass with the modulated taps S(d) exp(-i omega^c d), the same sum
+//                         without the demodulated copy of the rows (default: half the
+//                         shared-memory traffic).  J is immediately demodulated by
+//                         (cos, sin)(omega^s y) into the column signals of Eq. 10:
 //                             f_cr + f_si, f_sr - f_ci            (theta_a,      Eq. 7-9)
 //                             f_cr - f_si, f_sr + f_ci            (pi - theta_a, Eq. 15-16)
 //                         which go into a ring buffer of rows in shared memory.  J never
@@ -32,23 +35,29 @@ namespace gb {
 namespace {
 
 struct Smem {
-    float2 *ring2;      // ring of column signals: [RS][33] float2 per plane; paired units keep
-                        // (P, Q) of theta_a in plane 0 and (P', Q') of pi - theta_a in plane 1
-    float2 *stage;
+    float2 *ring2;   // ring of column signals: [RS][33] float2 per plane; paired units keep
+                     // (P, Q) of theta_a in plane 0 and (P', Q') of pi - theta_a in plane 1
+    float2 *stage;   // demodulation form: TH x SW demodulated rows (f_c, f_s)
     float *raw;      // two buffers of TH x RW floats
-    float2 *phx;
-    float *taps;
-    uint64_t *bars;  // pipelined variant: full[2], empty[2]; then the abort flag
+    float2 *ctaps;   // modulated taps: Tpad + 8 complex taps S(t - R) exp(-i omega^c (t - R))
+    float2 *phx;     // demodulation form: SW + 1 row phases
+    float *taps;     // Tpad + 8 real taps (column pass)
+    uint64_t *bars;  // pipelined schedule: full[2], empty[2]; then the abort flag
 };
 
+__host__ __device__ __forceinline__ int ctap_count(const FreqDev &f) { return f.mtaps ? f.Tpad + 8 : 0; }
+__host__ __device__ __forceinline__ int phx_count(const FreqDev &f) { return f.mtaps ? 0 : f.SW + 1; }
+
+// Every region starts on a 16-byte boundary (RS, TH multiples of 8; SW odd; Tpad + 8 even).
 __device__ __forceinline__ Smem carve(unsigned char *base, const FreqDev &f)
 {
     Smem s;
     s.ring2 = reinterpret_cast<float2 *>(base);
     s.stage = s.ring2 + (size_t)2 * f.RS * (kStripW + 1);
     s.raw = reinterpret_cast<float *>(s.stage + (size_t)f.TH * f.SW);
-    s.phx = reinterpret_cast<float2 *>(s.raw + (size_t)2 * f.TH * f.RW);
-    s.taps = reinterpret_cast<float *>(s.phx + f.SW + 1);
+    s.ctaps = reinterpret_cast<float2 *>(s.raw + (size_t)2 * f.TH * f.RW);
+    s.phx = s.ctaps + ctap_count(f);
+    s.taps = reinterpret_cast<float *>(s.phx + phx_count(f));
     s.bars = reinterpret_cast<uint64_t *>(((uintptr_t)(s.taps + f.Tpad + 8) + 7) & ~(uintptr_t)7);
     return s;
 }
@@ -58,19 +67,28 @@ __device__ __forceinline__ Smem carve(unsigned char *base, const FreqDev &f)
 size_t gabor_fp32_smem_bytes(const FreqDev &f)
 {
     return (size_t)f.RS * (kStripW + 1) * sizeof(float4) + (size_t)f.TH * f.SW * sizeof(float2) +
-           (size_t)2 * f.TH * f.RW * sizeof(float) + (size_t)(f.SW + 1) * sizeof(float2) +
+           (size_t)2 * f.TH * f.RW * sizeof(float) + (size_t)(ctap_count(f) + phx_count(f)) * sizeof(float2) +
            (size_t)(f.Tpad + 8) * sizeof(float) + 8 + 4 * sizeof(uint64_t) + 16;
 }
 
-FreqDev gabor_fp32_geometry(int R, int tile_rows, bool pipelined)
+FreqDev gabor_fp32_geometry(int R, int tile_rows, bool pipelined, bool mtaps)
 {
     FreqDev f{};
     f.R = R;
     f.T = 2 * R + 1;
     f.Tpad = round_up(f.T, 8);
-    f.SW = stage_width(kStripW + f.Tpad);
-    f.RW = round_up(kStripW + f.T - 1, 4);
-    // the pipelined variant rows 32 per chunk at most, and its ring holds two chunks
+    f.mtaps = mtaps ? 1 : 0;
+    if (mtaps) {
+        // no demodulated copy; raw rows hold the whole tap window of every output (zeros past
+        // the halo) and are = 1 (mod 32) floats apart, so that 8 rows x 2 column groups x
+        // 2 tap halves of a warp fall on distinct banks
+        f.SW = 0;
+        f.RW = round_up(kStripW + f.Tpad - 1, 32) + 1;
+    } else {
+        f.SW = stage_width(kStripW + f.Tpad);
+        f.RW = round_up(kStripW + f.T - 1, 4);
+    }
+    // the pipelined schedule takes 32 rows per chunk at most, and its ring holds two chunks
     int TH = tile_rows > 0 ? tile_rows : (pipelined ? 32 : 64);
     if (pipelined) TH = std::min(TH, 32);
     for (;;) {
@@ -94,8 +112,8 @@ constexpr int kBankThreads = 512;   // 16 warps per CTA (one CTA per SM)
 // PIPE = false: all 16 warps run the phases of a chunk in turn (row pass, then column pass).
 // PIPE = true: warps 0-7 run the row passes, warps 8-15 the column passes, one chunk apart;
 // the ring holds two chunks and mbarriers hand chunks over (bounded waits).  Returns false
-// when a wait gave up (the status word is set).
-template <bool PIPE>
+// when a wait gave up (the status word is set).  MT: row pass with modulated taps.
+template <bool PIPE, bool MT>
 __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkItem it, unsigned char *smem_raw)
 {
     const UnitDev u = a.units[it.unit];
@@ -114,6 +132,7 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
     const int64_t ystride = a.layout ? (int64_t)im.W * a.nplanes : (int64_t)im.W;   // between output rows
     const Smem sm = carve(smem_raw, f);
     const float4 *taps4 = reinterpret_cast<const float4 *>(sm.taps);
+    const float4 *ctaps4 = reinterpret_cast<const float4 *>(sm.ctaps);
     constexpr int kRowWarps = PIPE ? 8 : 16;   // warps that load rows and run the row pass
     constexpr int kRB = PIPE ? 4 : 8;          // 8-row blocks of one row-pass sweep
     auto sync_rows = [&]() {
@@ -134,12 +153,24 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
         mbar_fence_init();
     }
     for (int i = tid; i < f.Tpad + 8; i += kBankThreads) sm.taps[i] = i < f.Tpad ? f.taps[i] : 0.f;
-    // Demodulation phases at the staged positions (beyond the image only for non-zero rules,
-    // whose extended samples are demodulated at their own positions).
     const bool ext = a.bmode != kBoundaryZero;
-    for (int j = tid; j <= SW; j += kBankThreads) {
-        const int gx = x0 - R + j;
-        sm.phx[j] = (j < ncols && (ext || (gx >= 0 && gx < im.W))) ? u.phx[gx] : make_float2(0.f, 0.f);
+    if (MT) {
+        // taps S(d) exp(-i omega^c d), d = t - R: (cos, -sin) from the unit's phase table
+        for (int t = tid; t < f.Tpad + 8; t += kBankThreads) {
+            const float2 ph = t < f.T ? u.phx[t - R] : make_float2(0.f, 0.f);
+            const float g = t < f.T ? f.taps[t] : 0.f;
+            sm.ctaps[t] = make_float2(g * ph.x, -(g * ph.y));
+        }
+        // raw columns past the halo are read (by zero taps) and never copied: zero them
+        const int tail = RW - ncols;
+        for (int i = tid; i < 2 * TH * tail; i += kBankThreads) sm.raw[(size_t)(i / tail) * RW + ncols + i % tail] = 0.f;
+    } else {
+        // Demodulation phases at the staged positions (beyond the image only for non-zero
+        // rules, whose extended samples are demodulated at their own positions).
+        for (int j = tid; j <= SW; j += kBankThreads) {
+            const int gx = x0 - R + j;
+            sm.phx[j] = (j < ncols && (ext || (gx >= 0 && gx < im.W))) ? u.phx[gx] : make_float2(0.f, 0.f);
+        }
     }
     for (int i = tid; i < 2 * RS * stride; i += kBankThreads) sm.ring2[i] = make_float2(0.f, 0.f);
 
@@ -192,38 +223,48 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
         int start, n;
         block_rows(b, start, n);
         const float *rawb = sm.raw + (size_t)(b & 1) * TH * RW;
-        // demodulation f_c, f_s of Eq. 5 into the float2 stage: a lane keeps the phase of its
-        // column and demodulates the warp's rows (at most 4), all loads issued first
-        constexpr int kRowsPerWarp = 4;   // TH <= 4 kRowWarps
-        for (int j = lane; j < SW; j += 32) {
-            const float2 ph = sm.phx[j];
-            float v[kRowsPerWarp];
+        if (!MT) {
+            // demodulation f_c, f_s of Eq. 5 into the float2 stage: a lane keeps the phase of
+            // its column and demodulates the warp's rows (at most 4), all loads issued first
+            constexpr int kRowsPerWarp = 4;   // TH <= 4 kRowWarps
+            for (int j = lane; j < SW; j += 32) {
+                const float2 ph = sm.phx[j];
+                float v[kRowsPerWarp];
 #pragma unroll
-            for (int i = 0; i < kRowsPerWarp; ++i) {
-                const int r = warp + i * kRowWarps;
-                v[i] = (r < n && j < ncols) ? rawb[(size_t)r * RW + j] : 0.f;
-            }
+                for (int i = 0; i < kRowsPerWarp; ++i) {
+                    const int r = warp + i * kRowWarps;
+                    v[i] = (r < n && j < ncols) ? rawb[(size_t)r * RW + j] : 0.f;
+                }
 #pragma unroll
-            for (int i = 0; i < kRowsPerWarp; ++i) {
-                const int r = warp + i * kRowWarps;
-                if (r < n) sm.stage[(size_t)r * SW + j] = make_float2(v[i] * ph.x, v[i] * ph.y);
+                for (int i = 0; i < kRowsPerWarp; ++i) {
+                    const int r = warp + i * kRowWarps;
+                    if (r < n) sm.stage[(size_t)r * SW + j] = make_float2(v[i] * ph.x, v[i] * ph.y);
+                }
             }
+            sync_rows();
         }
-        sync_rows();
         // 16 (row, 8-column group) outputs per warp, 8 kRB rows x 4 groups in all; the two
         // half warps take the two halves of the tap chunks and add them with one shuffle.
+        // Demodulation form: a half warp covers 8 rows x groups 2 q0, 2 q0 + 1 (distinct bank
+        // pairs of the float2 stage); modulated taps: groups q0, q0 + 2 and an odd tap split
+        // where one exists (distinct banks of the raw rows).
         const int hl = lane & 15, half = lane >> 4;
         const int r = (hl & 7) | ((warp % kRB) << 3);
-        const int q = (hl >> 3) | ((warp / kRB) << 1);
+        const int q0 = warp / kRB;
+        const int q = MT ? q0 + 2 * (hl >> 3) : (hl >> 3) | (q0 << 1);
         // Warp-uniform: the warp's 8 rows start inside the block (rows < TH, so every stage read
         // is in bounds); rows r >= n are computed but not stored.
         if (8 * (warp % kRB) < n) {
             float2 acc[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
-            const int nh = (nchunks + 1) >> 1, c0 = half ? nh : 0;
-            conv8_linear<float2>(sm.stage + (size_t)r * SW + 8 * q + 8 * c0, taps4 + 2 * c0,
-                                 half ? nchunks - nh : nh, acc);
+            int nh = (nchunks + 1) >> 1;
+            if (MT && (nchunks & 1) && !(nh & 1)) nh = nchunks >> 1;
+            const int c0 = half ? nh : 0, cnt = half ? nchunks - nh : nh;
+            if (MT)
+                conv8_linear_ct(rawb + (size_t)r * RW + 8 * q + 8 * c0, ctaps4 + 4 * c0, cnt, acc);
+            else
+                conv8_linear<float2>(sm.stage + (size_t)r * SW + 8 * q + 8 * c0, taps4 + 2 * c0, cnt, acc);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, 16);
@@ -238,11 +279,17 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
                 if (r >= n) break;
                 const int j = jj + 4 * half;   // each half warp finishes 4 of the 8 outputs
                 const float2 aj = half ? acc[jj + 4] : acc[jj];
-                const float2 px = sm.phx[R + 8 * q + j];
-                const float A = aj.x, B = aj.y;
-                // Eq. 5-6: Re J = cos A + sin B, Im J = sin A - cos B
-                const float jr = fmaf(px.x, A, px.y * B);
-                const float ji = fmaf(px.y, A, -px.x * B);
+                float jr, ji;
+                if (MT) {
+                    jr = aj.x;
+                    ji = aj.y;
+                } else {
+                    const float2 px = sm.phx[R + 8 * q + j];
+                    const float A = aj.x, B = aj.y;
+                    // Eq. 5-6: Re J = cos A + sin B, Im J = sin A - cos B
+                    jr = fmaf(px.x, A, px.y * B);
+                    ji = fmaf(px.y, A, -px.x * B);
+                }
                 // Eq. 10: f_cr, f_sr, f_ci, f_si
                 const float fcr = jr * cy.x, fsr = jr * cy.y, fci = ji * cy.x, fsi = ji * cy.y;
                 sm.ring2[base + j] = make_float2(fcr + fsi, fsr - fci);
@@ -285,21 +332,33 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
         }
     };
 
+    // Make row block b visible with block b + 1 in flight, then run the row pass of block b.
+    // The demodulation form reads the raw buffer before its own barrier, so block b + 1 can
+    // be issued before it; the modulated-tap form reads raw rows until the end of its pass, so
+    // block b + 1 (which refills the buffer of block b - 1) is issued after the barrier.
+    auto advance = [&](int b) {
+        if (MT) {
+            cp_async_wait<0>();
+            sync_rows();   // raw block b visible; the row pass of block b - 1 is done
+            if (b + 1 < nblocks) issue(b + 1);
+        } else {
+            if (b + 1 < nblocks) {
+                issue(b + 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            sync_rows();   // raw block b visible; previous stage / ring readers done
+        }
+        row_pass(b);
+    };
+
     if (!PIPE) {
         issue(0);
         int b = 0;
         for (int k = 0; k < nch; ++k) {
             const int last = (k == 0) ? npro : npro + k;   // blocks [b, last) feed chunk k
-            for (; b < last; ++b) {
-                if (b + 1 < nblocks) {
-                    issue(b + 1);
-                    cp_async_wait<1>();
-                } else {
-                    cp_async_wait<0>();
-                }
-                __syncthreads();   // raw block b visible; previous stage / ring readers done
-                row_pass(b);
-            }
+            for (; b < last; ++b) advance(b);
             __syncthreads();       // ring rows of chunk k complete
             const int c = ys + k * TH;
             col_pass(c, min(TH, ye - c));
@@ -320,16 +379,7 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
                 break;
             }
             const int last = (k == 0) ? npro : npro + k;
-            for (; b < last; ++b) {
-                if (b + 1 < nblocks) {
-                    issue(b + 1);
-                    cp_async_wait<1>();
-                } else {
-                    cp_async_wait<0>();
-                }
-                sync_rows();       // raw block b visible; the stage is free
-                row_pass(b);
-            }
+            for (; b < last; ++b) advance(b);
             mbar_arrive(&full[k & 1]);   // this thread's ring rows of chunk k are written
         }
         cp_async_wait<0>();
@@ -366,7 +416,7 @@ __device__ __forceinline__ WorkItem decode_item(const BankArgs &a, int item)
 // Persistent CTAs pull work items (cost-sorted, largest first) from a device counter that the
 // launcher zeroes before the launch.
 // A CTA stops taking items after a bounded wait gave up (pipelined schedule).
-template <bool PIPE>
+template <bool PIPE, bool MT>
 __global__ void __launch_bounds__(kBankThreads) k_gabor_fp32(const __grid_constant__ BankArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -377,7 +427,7 @@ __global__ void __launch_bounds__(kBankThreads) k_gabor_fp32(const __grid_consta
         const int item = next_item;
         if (item >= a.nitems) break;
         const WorkItem it = a.items ? a.items[item] : decode_item(a, item);
-        const bool ok = gabor_fp32_item<PIPE>(a, it, smem_raw);
+        const bool ok = gabor_fp32_item<PIPE, MT>(a, it, smem_raw);
         // shared memory is reused by the next item
         const bool failed = __syncthreads_or(!ok);
         if (PIPE && threadIdx.x == 0) {
@@ -389,14 +439,32 @@ __global__ void __launch_bounds__(kBankThreads) k_gabor_fp32(const __grid_consta
     }
 }
 
-cudaError_t gabor_fp32_prepare()
+template <bool PIPE, bool MT>
+cudaError_t prepare_one()
 {
     // the kernel's own static shared memory (the work-queue word) counts against the limit
-    cudaError_t e = cudaFuncSetAttribute(k_gabor_fp32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemLimit - kStaticSmemReserve);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_gabor_fp32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_gabor_fp32<PIPE, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kSmemLimit - kStaticSmemReserve);
+}
+
+cudaError_t gabor_fp32_prepare()
+{
+    cudaError_t e = prepare_one<false, false>();
+    if (e == cudaSuccess) e = prepare_one<false, true>();
+    if (e == cudaSuccess) e = prepare_one<true, false>();
+    if (e == cudaSuccess) e = prepare_one<true, true>();
+    return e;
+}
+
+template <bool PIPE, bool MT>
+cudaError_t launch_one(const BankArgs &a, int nitems, size_t smem, int sm_count, cudaStream_t st)
+{
+    int cps = 1;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k_gabor_fp32<PIPE, MT>, kBankThreads, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(nitems, std::max(1, cps) * sm_count);
+    k_gabor_fp32<PIPE, MT><<<grid, kBankThreads, smem, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gabor_fp32(const BankArgs &a0, int nitems, size_t smem, int sm_count, cudaStream_t st)
@@ -406,16 +474,11 @@ cudaError_t launch_gabor_fp32(const BankArgs &a0, int nitems, size_t smem, int s
     a.nitems = nitems;
     cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    int cps = 1;
-    e = a.pipelined ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k_gabor_fp32<true>, kBankThreads, smem)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k_gabor_fp32<false>, kBankThreads, smem);
-    if (e != cudaSuccess) return e;
-    const int grid = std::min(nitems, std::max(1, cps) * sm_count);
     if (a.pipelined)
-        k_gabor_fp32<true><<<grid, kBankThreads, smem, st>>>(a);
-    else
-        k_gabor_fp32<false><<<grid, kBankThreads, smem, st>>>(a);
-    return cudaGetLastError();
+        return a.mtaps ? launch_one<true, true>(a, nitems, smem, sm_count, st)
+                       : launch_one<true, false>(a, nitems, smem, sm_count, st);
+    return a.mtaps ? launch_one<false, true>(a, nitems, smem, sm_count, st)
+                   : launch_one<false, false>(a, nitems, smem, sm_count, st);
 }
 
 }  // namespace gb

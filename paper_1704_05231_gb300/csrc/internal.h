@@ -56,8 +56,9 @@ struct FreqDev {
     int TH;             // rows per streamed chunk (multiple of 8, <= 64)
     int RS;             // ring rows (multiple of 8, >= TH + T - 1)
     int SW;             // staging row width in float2 (>= kStripW + Tpad, = 1 mod 16)
-    int RW;             // raw staging row width in floats (>= kStripW + T - 1, multiple of 4)
-    int pad_;
+    int RW;             // raw staging row width in floats (demodulation form: >= kStripW + T - 1,
+                        // multiple of 4; modulated taps: >= kStripW + Tpad, = 1 mod 32)
+    int mtaps;          // row pass form: 1 modulated taps, 0 demodulate / smooth / remodulate
 };
 
 // One image of a launch.
@@ -98,6 +99,7 @@ struct BankArgs {
     int nplanes;              // n_freq * n_theta
     int *status;              // device status word (pipelined variant's bounded waits)
     int pipelined;            // 1: warp-specialised row / column pipeline (host-side choice)
+    int mtaps;                // 1: row pass with modulated taps (host-side choice)
     ItemGroup groups[kMaxGroups];
 };
 
@@ -215,7 +217,7 @@ cudaError_t launch_build_taps(const double *d_sigma, const int *d_lo, const int 
                               int tpad_max, float *taps, cudaStream_t st);
 cudaError_t launch_build_twiddles(int M, float2 *tw, cudaStream_t st);
 // Tile geometry of the FP32 bank kernel for radius R (tile_rows = 0: automatic).
-FreqDev gabor_fp32_geometry(int R, int tile_rows, bool pipelined);
+FreqDev gabor_fp32_geometry(int R, int tile_rows, bool pipelined, bool mtaps);
 size_t gabor_fp32_smem_bytes(const FreqDev &f);
 cudaError_t launch_gabor_fp32(const BankArgs &a, int nitems, size_t smem, int sm_count, cudaStream_t st);
 cudaError_t gabor_fp32_prepare();
@@ -274,6 +276,7 @@ struct gabor_bank {
     int smoother = 0;                         // 0 truncated Gaussian (FIR), 1 recursive Gaussian (IIR)
     int fp32_pipeline = 0;                    // GB_OPT_PIPELINE (0 automatic, 1 phased, 2 pipelined)
     bool fp32_pipelined = false;              // schedule of the current tables
+    int fp32_row_form = 0;                    // GB_OPT_ROW_PASS (0 automatic, 1 demodulation, 2 modulated taps)
     int sdft_order = 0;                       // 0 automatic, 1 horizontal pass first, 2 vertical first
     float *d_transp = nullptr;                // transposed image for the vertical-first SDFT
     size_t transp_elems = 0;

@@ -276,3 +276,45 @@ def test_pipelined_schedule_batch_and_large_radius(torch_cuda):
         gbk.device_status()
     for x, y in zip(sb, batch):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("row_pass", [1, 2])
+@pytest.mark.parametrize("boundary", ["zero", "mirror"])
+@pytest.mark.parametrize("H,W", [(1, 50), (37, 75), (200, 161)])
+def test_row_pass_forms_match_oracle(torch_cuda, row_pass, boundary, H, W):
+    # Eq. 5-6 as demodulate / smooth / remodulate (1) and as one modulated-tap pass (2);
+    # radii 1, 5, 33 (tap chunks 1, 2, 9: both tap-split parities of the modulated form)
+    from paper_1704_05231_gb300 import GaborBank
+    img = synth.pink_noise([31, H, W], H, W)
+    th = [0.0, 0.6, math.pi / 2, math.pi - 0.6, 2.0]
+    om, sg = [2.5, 0.4, 0.15], [0.3, 1.5, 11.0]
+    with GaborBank(th, om, sg, boundary=boundary) as gbk:
+        gbk.set_option("row_pass", row_pass)
+        got = gbk.filter(torch_cuda.from_numpy(img).cuda()).cpu().numpy()
+        gbk.device_status()
+    assert rel_err(got, oracle.gabor_bank(img, th, om, sg, boundary=boundary)) <= FP32_TOL
+
+
+@pytest.mark.parametrize("row_pass", [1, 2])
+def test_row_pass_forms_c2_and_large_radius_sampled(torch_cuda, row_pass):
+    from paper_1704_05231_gb300 import GaborBank
+    torch = torch_cuda
+    rng = np.random.default_rng(5)
+    for (H, W), (th, om, sg) in [((1024, 1024), c2_bank()),
+                                 ((333, 257), ([0.3, math.pi - 0.3, math.pi / 2], [0.05], [53.0]))]:
+        img = synth.paper_like(2, H, W)
+        with GaborBank(th, om, sg) as gbk:
+            gbk.set_option("row_pass", row_pass)
+            got = gbk.filter(torch.from_numpy(img).cuda()).cpu().numpy()
+        xs, ys = sample_points(rng, H, W, 300)
+        ref = oracle.gabor_bank(img, th, om, sg, points=(xs, ys))
+        scale = float(np.max(np.abs(got)))
+        assert float(np.max(np.abs(got[:, :, ys, xs] - ref))) <= FP32_TOL * scale
+
+
+def test_row_pass_forms_pipelined_bitwise(torch_cuda):
+    img = synth.paper_like(6, 230, 170)
+    th, om, sg = c2_bank()
+    for form in (1, 2):
+        (a,), (b,) = _schedules(torch_cuda, [img], th, om, sg, opts=(("row_pass", form),))
+        assert np.array_equal(a, b)
