@@ -168,6 +168,8 @@ void free_tables(gabor_bank *h)
 }
 
 // Device tables of the plan: taps per frequency, phase tables per unit (K0, FP64).
+int twin_of(const gabor_bank *h, int ui);
+
 gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
 {
     const int nu = (int)h->units.size();
@@ -200,6 +202,7 @@ gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
         ud[i].phy = h->d_phy + (size_t)i * (Hcap + 2 * mg) + mg;
         ud[i].s = h->units[i].s;
         ud[i].sig = sig;
+        ud[i].twin = twin_of(h, i);
         sig += h->units[i].k_b >= 0 ? 4 : 2;
         ud[i].plane_a = h->units[i].s * K + h->units[i].k_a;
         ud[i].plane_b = h->units[i].k_b >= 0 ? h->units[i].s * K + h->units[i].k_b : -1;
@@ -288,11 +291,47 @@ gb_status validate_image(const void *img, int H, int W, int64_t pitch, const voi
     return GB_OK;
 }
 
-// Cost of one work item in FMA lanes: `rows` output rows of a 32-column strip, plus the
-// 2R-row prologue of its horizontal pass.
-double item_cost(const FreqDev &f, bool paired, double rows)
+// FP32 bank items take two unpaired units of a frequency together ("twins") under the
+// modulated-tap row pass: two row passes, and column passes that fill both halves of a CTA.
+// Units of a frequency are ordered paired first; unpaired ones are twinned in order.
+bool twins_on(const gabor_bank *h) { return h->fp32_row_form != 1; }
+
+int paired_count(const gabor_bank *h, int s)
 {
-    return 32.0 * f.Tpad * (rows * (paired ? 4 : 2) + (rows + 2 * f.R) * 2);
+    int np = 0;
+    for (int u = h->freqs[s].u0; u < h->freqs[s].u1; ++u) np += h->units[u].k_b >= 0;
+    return np;
+}
+
+// The second unit of the twin item that unit ui leads, or -1.
+int twin_of(const gabor_bank *h, int ui)
+{
+    const Unit &u = h->units[ui];
+    if (!twins_on(h) || u.k_b >= 0) return -1;
+    const Freq &f = h->freqs[u.s];
+    const int k = ui - (f.u0 + paired_count(h, u.s));
+    return (k % 2 == 0 && ui + 1 < f.u1) ? ui + 1 : -1;
+}
+
+// Unit ui is the second unit of a twin item (it has no items of its own).
+bool twinned(const gabor_bank *h, int ui)
+{
+    const Unit &u = h->units[ui];
+    if (!twins_on(h) || u.k_b >= 0) return false;
+    return (ui - (h->freqs[u.s].u0 + paired_count(h, u.s))) % 2 == 1;
+}
+
+// Cost of one work item in FMA lanes: `rows` output rows of a 32-column strip, plus the
+// 2R-row prologue of its horizontal pass (`planes` column planes, `rowpasses` row passes).
+double item_cost(const FreqDev &f, int planes, int rowpasses, double rows)
+{
+    return 32.0 * f.Tpad * (rows * 2 * planes + (rows + 2 * f.R) * 2 * rowpasses);
+}
+double item_cost(const gabor_bank *h, int ui, double rows)
+{
+    const FreqDev &f = h->freqdev[h->units[ui].s];
+    if (h->units[ui].k_b >= 0) return item_cost(f, 2, 1, rows);
+    return twin_of(h, ui) >= 0 ? item_cost(f, 2, 2, rows) : item_cost(f, 1, 1, rows);
 }
 
 // Row segments per column strip of frequency s on an Hh-row image: the per-frequency
@@ -305,7 +344,7 @@ int segments_of(const gabor_bank *h, int s, int Hh, double cap)
     int nseg = fseg > 0 ? fseg : 1;
     if (fseg <= 0) {
         const int min_len = std::max(f.TH, 2 * f.R);
-        while (item_cost(f, true, (double)Hh / nseg) > cap && Hh / (nseg + 1) >= min_len) ++nseg;
+        while (item_cost(f, 2, 1, (double)Hh / nseg) > cap && Hh / (nseg + 1) >= min_len) ++nseg;
     }
     return std::max(1, std::min(nseg, Hh));
 }
@@ -316,7 +355,8 @@ double item_cap(const gabor_bank *h, const std::vector<int64_t> &shapes)
     double total = 0;
     for (size_t i = 0; i + 1 < shapes.size(); i += 2) {
         const int nstrips = (int)((shapes[i + 1] + kStripW - 1) / kStripW);
-        for (const Unit &u : h->units) total += nstrips * item_cost(h->freqdev[u.s], u.k_b >= 0, (double)shapes[i]);
+        for (int u = 0; u < (int)h->units.size(); ++u)
+            if (!twinned(h, u)) total += nstrips * item_cost(h, u, (double)shapes[i]);
     }
     return total / std::max(1, h->sm_count) / 3.0;
 }
@@ -334,16 +374,19 @@ bool single_image_groups(const gabor_bank *h, int H, int W, BankArgs &a, int *ni
         const int nseg = segments_of(h, s, H, cap);
         const int seg_len = (H + nseg - 1) / nseg;
         const int nseg_used = (H + seg_len - 1) / seg_len;
-        int np = 0;
-        for (int u = h->freqs[s].u0; u < h->freqs[s].u1; ++u) np += h->units[u].k_b >= 0;
+        const int np = paired_count(h, s);
         const int nu = h->freqs[s].u1 - h->freqs[s].u0;
-        for (int pass = 0; pass < 2; ++pass) {
-            const int cnt = pass == 0 ? np : nu - np;
-            if (cnt == 0) continue;
+        // paired units; twin items of unpaired units; an unpaired unit left over
+        const int nun = nu - np, ntw = twins_on(h) ? nun / 2 : 0;
+        const int u0 = h->freqs[s].u0;
+        const int cnt[3] = {np, ntw, nun - 2 * ntw};
+        const int first_unit[3] = {u0, u0 + np, u0 + np + 2 * ntw};
+        for (int pass = 0; pass < 3; ++pass) {
+            if (cnt[pass] == 0) continue;
             G g;
-            g.cost = item_cost(h->freqdev[s], pass == 0, seg_len);
-            g.g = ItemGroup{0, h->freqs[s].u0 + (pass == 0 ? 0 : np), nstrips, nseg_used, seg_len};
-            g.n = cnt * nstrips * nseg_used;
+            g.cost = item_cost(h, first_unit[pass], seg_len);
+            g.g = ItemGroup{0, first_unit[pass], nstrips, nseg_used, seg_len, pass == 1 ? 2 : 1};
+            g.n = cnt[pass] * nstrips * nseg_used;
             gs.push_back(g);
         }
     }
@@ -378,15 +421,14 @@ gb_status get_worklist(gabor_bank *h, const std::vector<int64_t> &shapes, WorkIt
         const int Hh = (int)shapes[2 * i], Ww = (int)shapes[2 * i + 1];
         const int nstrips = (Ww + kStripW - 1) / kStripW;
         for (int s = 0; s < (int)h->freqs.size(); ++s) {
-            const FreqDev &f = h->freqdev[s];
             const int seg_len = (Hh + segments_of(h, s, Hh, cap) - 1) / segments_of(h, s, Hh, cap);
             for (int ui = h->freqs[s].u0; ui < h->freqs[s].u1; ++ui) {
-                const bool paired = h->units[ui].k_b >= 0;
+                if (twinned(h, ui)) continue;   // covered by the items of its twin
                 for (int st = 0; st < nstrips; ++st)
                     for (int y0 = 0; y0 < Hh; y0 += seg_len) {
                         Cand c;
                         c.w = WorkItem{i, ui, st, y0, std::min(Hh, y0 + seg_len)};
-                        c.cost = item_cost(f, paired, c.w.y1 - c.w.y0);
+                        c.cost = item_cost(h, ui, c.w.y1 - c.w.y0);
                         cands.push_back(c);
                     }
             }

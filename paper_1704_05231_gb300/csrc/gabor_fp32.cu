@@ -39,13 +39,14 @@ struct Smem {
                      // (P, Q) of theta_a in plane 0 and (P', Q') of pi - theta_a in plane 1
     float2 *stage;   // demodulation form: TH x SW demodulated rows (f_c, f_s)
     float *raw;      // two buffers of TH x RW floats
-    float2 *ctaps;   // modulated taps: Tpad + 8 complex taps S(t - R) exp(-i omega^c (t - R))
+    float2 *ctaps;   // modulated taps: 2 x (Tpad + 8) complex taps S(t - R) exp(-i omega^c (t - R))
     float2 *phx;     // demodulation form: SW + 1 row phases
     float *taps;     // Tpad + 8 real taps (column pass)
     uint64_t *bars;  // pipelined schedule: full[2], empty[2]; then the abort flag
 };
 
-__host__ __device__ __forceinline__ int ctap_count(const FreqDev &f) { return f.mtaps ? f.Tpad + 8 : 0; }
+// modulated taps: one set per unit of a (twin) item
+__host__ __device__ __forceinline__ int ctap_count(const FreqDev &f) { return f.mtaps ? 2 * (f.Tpad + 8) : 0; }
 __host__ __device__ __forceinline__ int phx_count(const FreqDev &f) { return f.mtaps ? 0 : f.SW + 1; }
 
 // Every region starts on a 16-byte boundary (RS, TH multiples of 8; SW odd; Tpad + 8 even).
@@ -112,7 +113,9 @@ constexpr int kBankThreads = 512;   // 16 warps per CTA (one CTA per SM)
 // PIPE = false: all 16 warps run the phases of a chunk in turn (row pass, then column pass).
 // PIPE = true: warps 0-7 run the row passes, warps 8-15 the column passes, one chunk apart;
 // the ring holds two chunks and mbarriers hand chunks over (bounded waits).  Returns false
-// when a wait gave up (the status word is set).  MT: row pass with modulated taps.
+// when a wait gave up (the status word is set).  MT: row pass with modulated taps; an item
+// of this form may also carry two unpaired units of one frequency ("twins"): two row passes
+// into the two ring planes, whose column passes then fill both halves of the CTA.
 template <bool PIPE, bool MT>
 __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkItem it, unsigned char *smem_raw)
 {
@@ -120,6 +123,10 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
     const FreqDev f = a.freqs[u.s];
     const ImageDev im = a.imgs ? a.imgs[it.img] : a.img0;
     const bool paired = u.plane_b >= 0;
+    const int utw = MT ? u.twin : -1;
+    const bool twin = utw >= 0;
+    const UnitDev u2 = a.units[twin ? utw : it.unit];   // the second unit of a twin item
+    const bool two = paired || twin;                     // two ring planes
     const int x0 = it.strip * kStripW;
     const int ys = it.y0, ye = it.y1;
     const int tid = threadIdx.x;
@@ -156,10 +163,12 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
     const bool ext = a.bmode != kBoundaryZero;
     if (MT) {
         // taps S(d) exp(-i omega^c d), d = t - R: (cos, -sin) from the unit's phase table
-        for (int t = tid; t < f.Tpad + 8; t += kBankThreads) {
-            const float2 ph = t < f.T ? u.phx[t - R] : make_float2(0.f, 0.f);
+        // (a twin item: both units' taps, one set after the other)
+        for (int i = tid; i < (twin ? 2 : 1) * (f.Tpad + 8); i += kBankThreads) {
+            const int t = i % (f.Tpad + 8);
+            const float2 ph = t < f.T ? (i < f.Tpad + 8 ? u.phx : u2.phx)[t - R] : make_float2(0.f, 0.f);
             const float g = t < f.T ? f.taps[t] : 0.f;
-            sm.ctaps[t] = make_float2(g * ph.x, -(g * ph.y));
+            sm.ctaps[i] = make_float2(g * ph.x, -(g * ph.y));
         }
         // raw columns past the halo are read (by zero taps) and never copied: zero them
         const int tail = RW - ncols;
@@ -255,60 +264,68 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
         // Warp-uniform: the warp's 8 rows start inside the block (rows < TH, so every stage read
         // is in bounds); rows r >= n are computed but not stored.
         if (8 * (warp % kRB) < n) {
-            float2 acc[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
             int nh = (nchunks + 1) >> 1;
             if (MT && (nchunks & 1) && !(nh & 1)) nh = nchunks >> 1;
             const int c0 = half ? nh : 0, cnt = half ? nchunks - nh : nh;
-            if (MT)
-                conv8_linear_ct(rawb + (size_t)r * RW + 8 * q + 8 * c0, ctaps4 + 4 * c0, cnt, acc);
-            else
-                conv8_linear<float2>(sm.stage + (size_t)r * SW + 8 * q + 8 * c0, taps4 + 2 * c0, cnt, acc);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, 16);
-                acc[j].y += __shfl_xor_sync(0xffffffffu, acc[j].y, 16);
-            }
             const int y = start + r;
             const int base = ((y - ring_origin) % RS) * stride + 8 * q;
             const bool yin = ext || (y >= 0 && y < im.H);
-            const float2 cy = yin ? u.phy[y] : make_float2(0.f, 0.f);
+#pragma unroll 1
+            for (int v = 0; v < (twin ? 2 : 1); ++v) {   // the unit, then its twin
+                float2 acc[8];
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                if (r >= n) break;
-                const int j = jj + 4 * half;   // each half warp finishes 4 of the 8 outputs
-                const float2 aj = half ? acc[jj + 4] : acc[jj];
-                float jr, ji;
-                if (MT) {
-                    jr = aj.x;
-                    ji = aj.y;
-                } else {
-                    const float2 px = sm.phx[R + 8 * q + j];
-                    const float A = aj.x, B = aj.y;
-                    // Eq. 5-6: Re J = cos A + sin B, Im J = sin A - cos B
-                    jr = fmaf(px.x, A, px.y * B);
-                    ji = fmaf(px.y, A, -px.x * B);
+                for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
+                if (MT)
+                    conv8_linear_ct(rawb + (size_t)r * RW + 8 * q + 8 * c0,
+                                    ctaps4 + v * ((f.Tpad + 8) / 2) + 4 * c0, cnt, acc);
+                else
+                    conv8_linear<float2>(sm.stage + (size_t)r * SW + 8 * q + 8 * c0, taps4 + 2 * c0, cnt, acc);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, 16);
+                    acc[j].y += __shfl_xor_sync(0xffffffffu, acc[j].y, 16);
                 }
-                // Eq. 10: f_cr, f_sr, f_ci, f_si
-                const float fcr = jr * cy.x, fsr = jr * cy.y, fci = ji * cy.x, fsi = ji * cy.y;
-                sm.ring2[base + j] = make_float2(fcr + fsi, fsr - fci);
-                if (paired) sm.ring2[(size_t)RS * stride + base + j] = make_float2(fcr - fsi, fsr + fci);
+                const float2 cy = yin ? (v ? u2.phy : u.phy)[y] : make_float2(0.f, 0.f);
+                float2 *ring = sm.ring2 + (size_t)v * RS * stride + base;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    if (r >= n) break;
+                    const int j = jj + 4 * half;   // each half warp finishes 4 of the 8 outputs
+                    const float2 aj = half ? acc[jj + 4] : acc[jj];
+                    float jr, ji;
+                    if (MT) {
+                        jr = aj.x;
+                        ji = aj.y;
+                    } else {
+                        const float2 px = sm.phx[R + 8 * q + j];
+                        const float A = aj.x, B = aj.y;
+                        // Eq. 5-6: Re J = cos A + sin B, Im J = sin A - cos B
+                        jr = fmaf(px.x, A, px.y * B);
+                        ji = fmaf(px.y, A, -px.x * B);
+                    }
+                    // Eq. 10: f_cr, f_sr, f_ci, f_si
+                    const float fcr = jr * cy.x, fsr = jr * cy.y, fci = ji * cy.x, fsi = ji * cy.y;
+                    ring[j] = make_float2(fcr + fsi, fsr - fci);
+                    if (paired) sm.ring2[(size_t)RS * stride + base + j] = make_float2(fcr - fsi, fsr + fci);
+                }
             }
         }
     };
 
     // Vertical pass for output rows [c, c + nout).
-    // Paired units: one half of the column warps smooths (P, Q) of theta_a, the other (P', Q')
-    // of pi - theta_a, 8 rows per warp at a time; unpaired units use all column warps on rows.
+    // Two planes: one half of the column warps smooths plane 0 ((P, Q) of theta_a), the other
+    // plane 1 ((P', Q') of pi - theta_a, or the twin's (P, Q)), 8 rows per warp at a time; a
+    // single unpaired unit uses all column warps on rows.
     auto col_pass = [&](int c, int nout) {
         const int cw = PIPE ? warp - 8 : warp;          // column-warp index
         const int ncw = PIPE ? 8 : 16;
         const int xl = lane;
-        const int sub = paired ? cw / (ncw / 2) : 0;
-        const int ybase = 8 * (paired ? cw % (ncw / 2) : cw);
-        const int ystep = 8 * (paired ? ncw / 2 : ncw);
+        const int sub = two ? cw / (ncw / 2) : 0;
+        const int ybase = 8 * (two ? cw % (ncw / 2) : cw);
+        const int ystep = 8 * (two ? ncw / 2 : ncw);
         const int x = x0 + xl;
+        const float2 *phy = (sub && twin) ? u2.phy : u.phy;
+        const int oplane = sub ? (twin ? u2.plane_a : u.plane_b) : u.plane_a;
         for (int yb = ybase; yb < nout; yb += ystep) {
             const int slot0 = (c - ys + yb) % RS;
             float2 acc[8];
@@ -316,12 +333,12 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
             for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
             conv8_ring<float2, kStripW + 1>(sm.ring2 + (size_t)sub * RS * stride + xl, RS, slot0, taps4, nchunks, acc);
             if (x < im.W) {
-                float2 *o = im.out + out_offset(a, sub ? u.plane_b : u.plane_a, plane, x);
+                float2 *o = im.out + out_offset(a, oplane, plane, x);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int y = c + yb + j;
                     if (yb + j < nout) {
-                        const float2 cy = u.phy[y];
+                        const float2 cy = phy[y];
                         const float P = acc[j].x, Q = acc[j].y;
                         // Eq. 7-8 (theta_a) or Eq. 15-16 (pi - theta_a)
                         __stcs(o + (int64_t)y * ystride,
@@ -410,7 +427,7 @@ __device__ __forceinline__ WorkItem decode_item(const BankArgs &a, int item)
     const int local = item - G.first;
     const int seg = local % G.nseg, rest = local / G.nseg;
     const int y0 = seg * G.seg_len;
-    return WorkItem{0, G.u0 + rest / G.nstrips, rest % G.nstrips, y0, min(a.img0.H, y0 + G.seg_len)};
+    return WorkItem{0, G.u0 + G.ustride * (rest / G.nstrips), rest % G.nstrips, y0, min(a.img0.H, y0 + G.seg_len)};
 }
 
 // Persistent CTAs pull work items (cost-sorted, largest first) from a device counter that the

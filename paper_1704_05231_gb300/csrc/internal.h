@@ -47,6 +47,9 @@ struct UnitDev {
     int plane_a;        // output plane of theta_a  (s * n_theta + k)
     int plane_b;        // output plane of pi - theta_a, or -1 when unpaired
     int sig;            // first column signal of the unit in the recursive path's buffers
+    int twin;           // FP32 bank, modulated-tap row pass: the unpaired unit that shares this
+                        // unit's work items, or -1
+    int pad_;
 };
 
 // Device view of one frequency: Gaussian taps and the FP32 kernel's tile geometry.
@@ -79,6 +82,7 @@ struct WorkItem {
 // first + ((q * nstrips) + strip) * nseg + seg is unit u0 + q, that strip and segment.
 struct ItemGroup {
     int first, u0, nstrips, nseg, seg_len;
+    int ustride;        // units between consecutive items' units (2: twin items)
 };
 constexpr int kMaxGroups = 64;
 
