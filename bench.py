@@ -30,7 +30,7 @@ if ROOT not in sys.path:
 METRIC = "Gabor bank pixel·filter outputs/s, plain vs TC at ≤2e-3 rel err; serve p99 ms"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_gabor_fp32 launch on this
 # workload from an ncu capture of the current kernel; None once the kernel changes.
-K_GABOR_FP32_TRAFFIC = 144747520   # 4502272 read + 140245248 written (autotuned tiling)
+K_GABOR_FP32_TRAFFIC = 143746816   # 4373760 read + 139373056 written (autotuned tiling)
 UNIT = "outputs/s"
 H = W = 1024
 
