@@ -30,7 +30,7 @@ if ROOT not in sys.path:
 METRIC = "Gabor bank pixel·filter outputs/s, plain vs TC at ≤2e-3 rel err; serve p99 ms"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_gabor_fp32 launch on this
 # workload from an ncu capture of the current kernel; None once the kernel changes.
-K_GABOR_FP32_TRAFFIC = 143746816   # 4373760 read + 139373056 written (autotuned tiling)
+K_GABOR_FP32_TRAFFIC = None
 UNIT = "outputs/s"
 H = W = 1024
 
@@ -448,7 +448,7 @@ def batch_leg(torch, steps, warmup, flush, stream):
         ent = {}
         if prec == "fp32":
             t = autotune(gbk, imgs, steps=1, tile_rows=(0,), segments=(0, 1, 2, 4))
-            ent["tiling"] = t["tiling"]
+            ent["tiling"], ent["ctas_per_sm"] = t["tiling"], t["ctas"]
         graph = capture_graph(lambda: gbk.filter_batch(imgs, outs))
         ms = statistics.mean(time_device(torch, graph.replay, steps, warmup, flush, stream))
         gbk.device_status()
@@ -530,10 +530,11 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
-    tiling = None
+    tiling, ctas = None, 1
     if not args.no_tune:
         from paper_1704_05231_gb300.tune import autotune
-        tiling = autotune(gbk, d_img, steps=3)["tiling"]
+        tuned = autotune(gbk, d_img, steps=3)
+        tiling, ctas = tuned["tiling"], tuned["ctas"]
     for _ in range(max(3, args.warmup)):
         gbk.filter(d_img, out)
     torch.cuda.synchronize()
@@ -581,7 +582,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config({"path": "FP32 CUDA-core fused bank kernel", "parallelism": f"replicas x{world}",
-                                       "tiling": tiling}),
+                                       "tiling": tiling, "ctas_per_sm": ctas}),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": K_GABOR_FP32_TRAFFIC,
                          "kernel": "k_gabor_fp32 (one persistent launch per step)",

@@ -178,7 +178,12 @@ typedef enum {
        taps S(d) exp(-i omega^c d) (the same sum in one step; the same packed FMAs, no
        demodulated copy of the rows).  The column pass is the same in both.  Results agree to
        FP32 rounding (each within 1e-5 max|out| of the FP64 oracle). */
-    GB_OPT_ROW_PASS = 9
+    GB_OPT_ROW_PASS = 9,
+    /* FP32 bank CTAs per SM: 0 automatic (= 1), 1 one CTA of 16 warps, 2 two CTAs of 8 warps
+       (each with half of the SM's shared memory, so smaller row tiles for large radii; falls
+       back to 1 where a frequency does not fit, and under GB_OPT_PIPELINE = 2).  Results are
+       identical. */
+    GB_OPT_BANK_CTAS = 10
 } gb_option;
 
 /* 1-D Gaussian smoothers (GB_OPT_SMOOTHER). */

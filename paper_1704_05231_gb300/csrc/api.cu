@@ -218,19 +218,24 @@ gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
     GB_CU(cudaMemcpy(h->d_T, T.data(), nf * sizeof(int), cudaMemcpyHostToDevice));
     GB_CU(cudaMemcpy(h->d_unitdev, ud.data(), nu * sizeof(UnitDev), cudaMemcpyHostToDevice));
     h->freqdev.resize(nf);
-    // the pipelined schedule where every frequency's geometry fits, else the phased one
+    // the pipelined schedule where every frequency's geometry fits, else the phased one; two
+    // CTAs per SM where every frequency's geometry fits in half of the SM's shared memory
     h->fp32_pipelined = h->fp32_pipeline == 2;
-    for (int pass = 0; pass < 2; ++pass) {
+    h->fp32_ctas = (!h->fp32_pipelined && h->fp32_ctas_opt == 2) ? 2 : 1;
+    for (int pass = 0; pass < 3; ++pass) {
         h->max_smem = 0;
         for (int s = 0; s < nf; ++s) {
             const int tr = (s < (int)h->ftile_rows.size() && h->ftile_rows[s] > 0) ? h->ftile_rows[s] : h->tile_rows;
-            FreqDev fd = gabor_fp32_geometry(h->freqs[s].R, tr, h->fp32_pipelined, h->fp32_row_form != 1);
+            FreqDev fd = gabor_fp32_geometry(h->freqs[s].R, tr, h->fp32_pipelined, h->fp32_row_form != 1, h->fp32_ctas);
             fd.taps = h->d_taps + (size_t)s * h->tpad_max;
             h->freqdev[s] = fd;
             h->max_smem = std::max(h->max_smem, gabor_fp32_smem_bytes(fd));
         }
-        if (!h->fp32_pipelined || h->max_smem <= (size_t)(kSmemLimit - kStaticSmemReserve)) break;
-        h->fp32_pipelined = false;
+        if (h->max_smem <= gabor_fp32_smem_budget(h->fp32_ctas)) break;
+        if (h->fp32_pipelined)
+            h->fp32_pipelined = false;
+        else
+            h->fp32_ctas = 1;
     }
     GB_CU(cudaMemcpy(h->d_freqdev, h->freqdev.data(), nf * sizeof(FreqDev), cudaMemcpyHostToDevice));
     GB_CU(launch_build_taps(h->d_sigma, h->d_lo, h->d_T, nf, h->tpad_max, h->d_taps, st));
@@ -349,7 +354,7 @@ int segments_of(const gabor_bank *h, int s, int Hh, double cap)
     return std::max(1, std::min(nseg, Hh));
 }
 
-// Item-size cap of a launch over `shapes`: a third of one SM's share of the whole launch.
+// Item-size cap of a launch over `shapes`: a third of one resident CTA's share of the launch.
 double item_cap(const gabor_bank *h, const std::vector<int64_t> &shapes)
 {
     double total = 0;
@@ -358,7 +363,7 @@ double item_cap(const gabor_bank *h, const std::vector<int64_t> &shapes)
         for (int u = 0; u < (int)h->units.size(); ++u)
             if (!twinned(h, u)) total += nstrips * item_cost(h, u, (double)shapes[i]);
     }
-    return total / std::max(1, h->sm_count) / 3.0;
+    return total / std::max(1, h->sm_count * h->fp32_ctas) / 3.0;
 }
 
 // Work items of a single-image launch as groups decoded by the kernel (no device list):
@@ -734,6 +739,7 @@ gb_status filter_device(gabor_bank *h, const float *d_img, int H, int W, int64_t
     a.status = h->d_status;
     a.pipelined = h->fp32_pipelined ? 1 : 0;
     a.mtaps = h->fp32_row_form != 1 ? 1 : 0;
+    a.ctas = h->fp32_ctas;
     GB_CU(launch_gabor_fp32(a, n, h->max_smem, h->sm_count, st));
     return GB_OK;
 }
@@ -1041,6 +1047,7 @@ gb_status gabor_bank_filter_batch(gabor_bank_t h, int n, const float *const *d_i
     a.status = h->d_status;
     a.pipelined = h->fp32_pipelined ? 1 : 0;
     a.mtaps = h->fp32_row_form != 1 ? 1 : 0;
+    a.ctas = h->fp32_ctas;
     GB_CU(launch_gabor_fp32(a, nitems, h->max_smem, h->sm_count, st));
     return GB_OK;
 }
@@ -1085,6 +1092,15 @@ gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value)
             DeviceGuard g(h->device);
             cudaDeviceSynchronize();
             h->fp32_row_form = (int)value;
+            free_tables(h);
+        }
+        return GB_OK;
+    case GB_OPT_BANK_CTAS:
+        if (value < 0 || value > 2) return fail(GB_ERR_INVALID_ARG, "GB_OPT_BANK_CTAS takes 0, 1 or 2");
+        if (h->fp32_ctas_opt != (int)value) {
+            DeviceGuard g(h->device);
+            cudaDeviceSynchronize();
+            h->fp32_ctas_opt = (int)value;
             free_tables(h);
         }
         return GB_OK;

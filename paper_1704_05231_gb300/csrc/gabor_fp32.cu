@@ -72,7 +72,14 @@ size_t gabor_fp32_smem_bytes(const FreqDev &f)
            (size_t)(f.Tpad + 8) * sizeof(float) + 8 + 4 * sizeof(uint64_t) + 16;
 }
 
-FreqDev gabor_fp32_geometry(int R, int tile_rows, bool pipelined, bool mtaps)
+// Dynamic shared memory one CTA may take when `ctas` CTAs share an SM (228 KB per SM, 1 KB
+// of it reserved per CTA, and the kernel's own static word).
+size_t gabor_fp32_smem_budget(int ctas)
+{
+    return (size_t)(kSmemPerSm - ctas * kSmemCtaReserve) / ctas - kStaticSmemReserve;
+}
+
+FreqDev gabor_fp32_geometry(int R, int tile_rows, bool pipelined, bool mtaps, int ctas)
 {
     FreqDev f{};
     f.R = R;
@@ -95,7 +102,7 @@ FreqDev gabor_fp32_geometry(int R, int tile_rows, bool pipelined, bool mtaps)
     for (;;) {
         f.TH = TH;
         f.RS = round_up((pipelined ? 2 * TH : TH) + f.T - 1, 8);
-        if (gabor_fp32_smem_bytes(f) <= (size_t)(kSmemLimit - kStaticSmemReserve) || TH <= 8) break;
+        if (gabor_fp32_smem_bytes(f) <= gabor_fp32_smem_budget(ctas) || TH <= 8) break;
         TH /= 2;
     }
     return f;
@@ -108,15 +115,17 @@ __device__ __forceinline__ int64_t out_offset(const BankArgs &a, int p, int64_t 
     return a.layout ? (int64_t)x * a.nplanes + p : (int64_t)p * plane + x;
 }
 
-constexpr int kBankThreads = 512;   // 16 warps per CTA (one CTA per SM)
+// NW = 16: one CTA of 16 warps per SM; NW = 8: two CTAs of 8 warps per SM, whose phases
+// (row pass, barrier, column pass, epilogues) interleave on the SM.
 
 // PIPE = false: all 16 warps run the phases of a chunk in turn (row pass, then column pass).
 // PIPE = true: warps 0-7 run the row passes, warps 8-15 the column passes, one chunk apart;
 // the ring holds two chunks and mbarriers hand chunks over (bounded waits).  Returns false
-// when a wait gave up (the status word is set).  MT: row pass with modulated taps; an item
+// when a wait gave up (the status word is set).  NW warps per CTA (PIPE: 16).  MT: row pass
+// with modulated taps; an item
 // of this form may also carry two unpaired units of one frequency ("twins"): two row passes
 // into the two ring planes, whose column passes then fill both halves of the CTA.
-template <bool PIPE, bool MT>
+template <bool PIPE, bool MT, int NW>
 __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkItem it, unsigned char *smem_raw)
 {
     const UnitDev u = a.units[it.unit];
@@ -140,8 +149,10 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
     const Smem sm = carve(smem_raw, f);
     const float4 *taps4 = reinterpret_cast<const float4 *>(sm.taps);
     const float4 *ctaps4 = reinterpret_cast<const float4 *>(sm.ctaps);
-    constexpr int kRowWarps = PIPE ? 8 : 16;   // warps that load rows and run the row pass
-    constexpr int kRB = PIPE ? 4 : 8;          // 8-row blocks of one row-pass sweep
+    static_assert(NW == 16 || (NW == 8 && !PIPE), "16 warps, or 8 without the pipelined schedule");
+    constexpr int kThreadsCta = 32 * NW;
+    constexpr int kRowWarps = PIPE ? 8 : NW;   // warps that load rows and run the row pass
+    constexpr int kRB = kRowWarps / 2;         // 8-row blocks of one row-pass sweep
     auto sync_rows = [&]() {
         if (PIPE)
             named_barrier(1, kRowWarps * 32);
@@ -154,17 +165,17 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
     if (PIPE && tid == 0) {
         mbar_init(&full[0], kRowWarps * 32);
         mbar_init(&full[1], kRowWarps * 32);
-        mbar_init(&empty[0], (kBankThreads / 32 - kRowWarps) * 32);
-        mbar_init(&empty[1], (kBankThreads / 32 - kRowWarps) * 32);
+        mbar_init(&empty[0], (NW - kRowWarps) * 32);
+        mbar_init(&empty[1], (NW - kRowWarps) * 32);
         *abort_s = 0;
         mbar_fence_init();
     }
-    for (int i = tid; i < f.Tpad + 8; i += kBankThreads) sm.taps[i] = i < f.Tpad ? f.taps[i] : 0.f;
+    for (int i = tid; i < f.Tpad + 8; i += kThreadsCta) sm.taps[i] = i < f.Tpad ? f.taps[i] : 0.f;
     const bool ext = a.bmode != kBoundaryZero;
     if (MT) {
         // taps S(d) exp(-i omega^c d), d = t - R: (cos, -sin) from the unit's phase table
         // (a twin item: both units' taps, one set after the other)
-        for (int i = tid; i < (twin ? 2 : 1) * (f.Tpad + 8); i += kBankThreads) {
+        for (int i = tid; i < (twin ? 2 : 1) * (f.Tpad + 8); i += kThreadsCta) {
             const int t = i % (f.Tpad + 8);
             const float2 ph = t < f.T ? (i < f.Tpad + 8 ? u.phx : u2.phx)[t - R] : make_float2(0.f, 0.f);
             const float g = t < f.T ? f.taps[t] : 0.f;
@@ -172,16 +183,16 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
         }
         // raw columns past the halo are read (by zero taps) and never copied: zero them
         const int tail = RW - ncols;
-        for (int i = tid; i < 2 * TH * tail; i += kBankThreads) sm.raw[(size_t)(i / tail) * RW + ncols + i % tail] = 0.f;
+        for (int i = tid; i < 2 * TH * tail; i += kThreadsCta) sm.raw[(size_t)(i / tail) * RW + ncols + i % tail] = 0.f;
     } else {
         // Demodulation phases at the staged positions (beyond the image only for non-zero
         // rules, whose extended samples are demodulated at their own positions).
-        for (int j = tid; j <= SW; j += kBankThreads) {
+        for (int j = tid; j <= SW; j += kThreadsCta) {
             const int gx = x0 - R + j;
             sm.phx[j] = (j < ncols && (ext || (gx >= 0 && gx < im.W))) ? u.phx[gx] : make_float2(0.f, 0.f);
         }
     }
-    for (int i = tid; i < 2 * RS * stride; i += kBankThreads) sm.ring2[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < 2 * RS * stride; i += kThreadsCta) sm.ring2[i] = make_float2(0.f, 0.f);
 
     // Row blocks: the prologue [ys - R, need_0) in pieces of TH rows, then one block per
     // later chunk k covering [need_{k-1}, need_k), need_k = min(ys + (k+1) TH, ye) + R.
@@ -235,7 +246,7 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
         if (!MT) {
             // demodulation f_c, f_s of Eq. 5 into the float2 stage: a lane keeps the phase of
             // its column and demodulates the warp's rows (at most 4), all loads issued first
-            constexpr int kRowsPerWarp = 4;   // TH <= 4 kRowWarps
+            constexpr int kRowsPerWarp = 64 / kRowWarps;   // TH <= 64
             for (int j = lane; j < SW; j += 32) {
                 const float2 ph = sm.phx[j];
                 float v[kRowsPerWarp];
@@ -252,18 +263,19 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
             }
             sync_rows();
         }
-        // 16 (row, 8-column group) outputs per warp, 8 kRB rows x 4 groups in all; the two
+        // 16 (row, 8-column group) outputs per warp, sweeps of 8 kRB rows x 4 groups; the two
         // half warps take the two halves of the tap chunks and add them with one shuffle.
         // Demodulation form: a half warp covers 8 rows x groups 2 q0, 2 q0 + 1 (distinct bank
         // pairs of the float2 stage); modulated taps: groups q0, q0 + 2 and an odd tap split
         // where one exists (distinct banks of the raw rows).
         const int hl = lane & 15, half = lane >> 4;
-        const int r = (hl & 7) | ((warp % kRB) << 3);
         const int q0 = warp / kRB;
         const int q = MT ? q0 + 2 * (hl >> 3) : (hl >> 3) | (q0 << 1);
+        for (int r0 = 0; r0 < n; r0 += 8 * kRB) {
+        const int r = r0 + ((hl & 7) | ((warp % kRB) << 3));
         // Warp-uniform: the warp's 8 rows start inside the block (rows < TH, so every stage read
         // is in bounds); rows r >= n are computed but not stored.
-        if (8 * (warp % kRB) < n) {
+        if (r0 + 8 * (warp % kRB) < n) {
             int nh = (nchunks + 1) >> 1;
             if (MT && (nchunks & 1) && !(nh & 1)) nh = nchunks >> 1;
             const int c0 = half ? nh : 0, cnt = half ? nchunks - nh : nh;
@@ -310,6 +322,7 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
                 }
             }
         }
+        }
     };
 
     // Vertical pass for output rows [c, c + nout).
@@ -318,7 +331,7 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
     // single unpaired unit uses all column warps on rows.
     auto col_pass = [&](int c, int nout) {
         const int cw = PIPE ? warp - 8 : warp;          // column-warp index
-        const int ncw = PIPE ? 8 : 16;
+        const int ncw = PIPE ? 8 : NW;
         const int xl = lane;
         const int sub = two ? cw / (ncw / 2) : 0;
         const int ybase = 8 * (two ? cw % (ncw / 2) : cw);
@@ -433,8 +446,8 @@ __device__ __forceinline__ WorkItem decode_item(const BankArgs &a, int item)
 // Persistent CTAs pull work items (cost-sorted, largest first) from a device counter that the
 // launcher zeroes before the launch.
 // A CTA stops taking items after a bounded wait gave up (pipelined schedule).
-template <bool PIPE, bool MT>
-__global__ void __launch_bounds__(kBankThreads) k_gabor_fp32(const __grid_constant__ BankArgs a)
+template <bool PIPE, bool MT, int NW>
+__global__ void __launch_bounds__(32 * NW, 16 / NW) k_gabor_fp32(const __grid_constant__ BankArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int next_item;
@@ -444,7 +457,7 @@ __global__ void __launch_bounds__(kBankThreads) k_gabor_fp32(const __grid_consta
         const int item = next_item;
         if (item >= a.nitems) break;
         const WorkItem it = a.items ? a.items[item] : decode_item(a, item);
-        const bool ok = gabor_fp32_item<PIPE, MT>(a, it, smem_raw);
+        const bool ok = gabor_fp32_item<PIPE, MT, NW>(a, it, smem_raw);
         // shared memory is reused by the next item
         const bool failed = __syncthreads_or(!ok);
         if (PIPE && threadIdx.x == 0) {
@@ -456,31 +469,33 @@ __global__ void __launch_bounds__(kBankThreads) k_gabor_fp32(const __grid_consta
     }
 }
 
-template <bool PIPE, bool MT>
+template <bool PIPE, bool MT, int NW>
 cudaError_t prepare_one()
 {
     // the kernel's own static shared memory (the work-queue word) counts against the limit
-    return cudaFuncSetAttribute(k_gabor_fp32<PIPE, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_gabor_fp32<PIPE, MT, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kSmemLimit - kStaticSmemReserve);
 }
 
 cudaError_t gabor_fp32_prepare()
 {
-    cudaError_t e = prepare_one<false, false>();
-    if (e == cudaSuccess) e = prepare_one<false, true>();
-    if (e == cudaSuccess) e = prepare_one<true, false>();
-    if (e == cudaSuccess) e = prepare_one<true, true>();
+    cudaError_t e = prepare_one<false, false, 16>();
+    if (e == cudaSuccess) e = prepare_one<false, true, 16>();
+    if (e == cudaSuccess) e = prepare_one<true, false, 16>();
+    if (e == cudaSuccess) e = prepare_one<true, true, 16>();
+    if (e == cudaSuccess) e = prepare_one<false, false, 8>();
+    if (e == cudaSuccess) e = prepare_one<false, true, 8>();
     return e;
 }
 
-template <bool PIPE, bool MT>
+template <bool PIPE, bool MT, int NW>
 cudaError_t launch_one(const BankArgs &a, int nitems, size_t smem, int sm_count, cudaStream_t st)
 {
     int cps = 1;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k_gabor_fp32<PIPE, MT>, kBankThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k_gabor_fp32<PIPE, MT, NW>, 32 * NW, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(nitems, std::max(1, cps) * sm_count);
-    k_gabor_fp32<PIPE, MT><<<grid, kBankThreads, smem, st>>>(a);
+    k_gabor_fp32<PIPE, MT, NW><<<grid, 32 * NW, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -492,10 +507,13 @@ cudaError_t launch_gabor_fp32(const BankArgs &a0, int nitems, size_t smem, int s
     cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     if (a.pipelined)
-        return a.mtaps ? launch_one<true, true>(a, nitems, smem, sm_count, st)
-                       : launch_one<true, false>(a, nitems, smem, sm_count, st);
-    return a.mtaps ? launch_one<false, true>(a, nitems, smem, sm_count, st)
-                   : launch_one<false, false>(a, nitems, smem, sm_count, st);
+        return a.mtaps ? launch_one<true, true, 16>(a, nitems, smem, sm_count, st)
+                       : launch_one<true, false, 16>(a, nitems, smem, sm_count, st);
+    if (a.ctas == 2)
+        return a.mtaps ? launch_one<false, true, 8>(a, nitems, smem, sm_count, st)
+                       : launch_one<false, false, 8>(a, nitems, smem, sm_count, st);
+    return a.mtaps ? launch_one<false, true, 16>(a, nitems, smem, sm_count, st)
+                   : launch_one<false, false, 16>(a, nitems, smem, sm_count, st);
 }
 
 }  // namespace gb

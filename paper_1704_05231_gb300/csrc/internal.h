@@ -18,6 +18,8 @@ constexpr int kMaxRadius = 160;    // largest Gaussian radius of the fused FP32 
 constexpr int kMaxSdftM = 64;      // largest SDFT window side
 constexpr int kSmemLimit = 227 * 1024;
 constexpr int kStaticSmemReserve = 256;   // static shared memory kept free next to the dynamic part
+constexpr int kSmemPerSm = 228 * 1024;    // shared memory of one SM
+constexpr int kSmemCtaReserve = 1024;     // taken by the system from every resident CTA
 
 // Boundary rules for the image beyond its edges.
 enum BoundaryMode { kBoundaryZero = 0, kBoundaryReplicate = 1, kBoundaryMirror = 2 };
@@ -104,6 +106,7 @@ struct BankArgs {
     int *status;              // device status word (pipelined variant's bounded waits)
     int pipelined;            // 1: warp-specialised row / column pipeline (host-side choice)
     int mtaps;                // 1: row pass with modulated taps (host-side choice)
+    int ctas;                 // CTAs per SM: 1 (16 warps each) or 2 (8 warps each)
     ItemGroup groups[kMaxGroups];
 };
 
@@ -221,7 +224,8 @@ cudaError_t launch_build_taps(const double *d_sigma, const int *d_lo, const int 
                               int tpad_max, float *taps, cudaStream_t st);
 cudaError_t launch_build_twiddles(int M, float2 *tw, cudaStream_t st);
 // Tile geometry of the FP32 bank kernel for radius R (tile_rows = 0: automatic).
-FreqDev gabor_fp32_geometry(int R, int tile_rows, bool pipelined, bool mtaps);
+FreqDev gabor_fp32_geometry(int R, int tile_rows, bool pipelined, bool mtaps, int ctas);
+size_t gabor_fp32_smem_budget(int ctas);
 size_t gabor_fp32_smem_bytes(const FreqDev &f);
 cudaError_t launch_gabor_fp32(const BankArgs &a, int nitems, size_t smem, int sm_count, cudaStream_t st);
 cudaError_t gabor_fp32_prepare();
@@ -281,6 +285,8 @@ struct gabor_bank {
     int fp32_pipeline = 0;                    // GB_OPT_PIPELINE (0 automatic, 1 phased, 2 pipelined)
     bool fp32_pipelined = false;              // schedule of the current tables
     int fp32_row_form = 0;                    // GB_OPT_ROW_PASS (0 automatic, 1 demodulation, 2 modulated taps)
+    int fp32_ctas_opt = 0;                    // GB_OPT_BANK_CTAS (0 automatic, 1, 2)
+    int fp32_ctas = 1;                        // CTAs per SM of the current tables
     int sdft_order = 0;                       // 0 automatic, 1 horizontal pass first, 2 vertical first
     float *d_transp = nullptr;                // transposed image for the vertical-first SDFT
     size_t transp_elems = 0;

@@ -1,10 +1,11 @@
 """Autotuner for the tile geometry of the FP32 filter-bank kernel.
 
 For every frequency of a plan it picks the rows per streamed chunk (TH) and the number of row
-segments per column strip by timing the whole bank on the caller's images (coordinate
-descent over the frequencies, CUDA events, L2 flushed between timings).  The choice trades
-the 2R-row vertical halo recomputed per segment against load balance across the SMs; it does
-not change any result (every output's arithmetic is the same).  Choices are cached in a JSON
+segments per column strip, and for the whole plan the CTAs per SM (one of 16 warps or two of
+8), by timing the whole bank on the caller's images (coordinate descent over the
+frequencies for each CTA setting, CUDA events, L2 flushed between timings).  The choice
+trades the 2R-row vertical halo recomputed per segment against load balance across the SMs;
+it does not change any result (every output's arithmetic is the same).  Choices are cached in a JSON
 file keyed by GPU name, image-size classes, radii, orientation count and precision.
 """
 from __future__ import annotations
@@ -16,6 +17,7 @@ import statistics
 
 TILE_ROWS = (0, 32, 64)
 SEGMENTS = (0, 1, 2, 4, 8)
+CTAS = (1, 2)
 
 
 def default_cache_path():
@@ -49,12 +51,14 @@ def _save(path, data):
     os.replace(tmp, path)
 
 
-def autotune(gbk, imgs, cache_path=None, steps=3, use_cache=True, tile_rows=TILE_ROWS, segments=SEGMENTS):
-    """Choose (tile_rows, segments) per frequency for `imgs` (a CUDA tensor or a list of them).
+def autotune(gbk, imgs, cache_path=None, steps=3, use_cache=True, tile_rows=TILE_ROWS, segments=SEGMENTS,
+             ctas=CTAS):
+    """Choose (tile_rows, segments) per frequency and the CTAs per SM for `imgs` (a CUDA tensor
+    or a list of them).
 
     Applies the choice to `gbk` and returns {"key", "tiling": [[tile_rows, segments], ...],
-    "ms"}.  `tile_rows` and `segments` are the candidate values searched.  Only the FP32 path
-    has a tunable geometry; other precisions return the defaults.
+    "ctas", "ms"}.  `tile_rows`, `segments` and `ctas` are the candidate values searched.  Only
+    the FP32 path has a tunable geometry; other precisions return the defaults.
     """
     import torch
     batch = isinstance(imgs, (list, tuple))
@@ -62,11 +66,13 @@ def autotune(gbk, imgs, cache_path=None, steps=3, use_cache=True, tile_rows=TILE
     shapes = [tuple(t.shape) for t in ims]
     nf = len(gbk.omegas)
     if gbk.precision != "fp32" or nf == 0:
-        return {"key": None, "tiling": [[0, 0]] * nf, "ms": None}
+        return {"key": None, "tiling": [[0, 0]] * nf, "ctas": None, "ms": None}
     path = cache_path or default_cache_path()
-    key = cache_key(gbk, shapes, torch.cuda.get_device_name()) + f"|{list(tile_rows)}|{list(segments)}"
+    key = (cache_key(gbk, shapes, torch.cuda.get_device_name()) +
+           f"|{list(tile_rows)}|{list(segments)}|{list(ctas)}")
     cache = _load(path) if use_cache else {}
     if key in cache:
+        gbk.set_option("bank_ctas", cache[key]["ctas"])
         for s, (tr, sg) in enumerate(cache[key]["tiling"]):
             gbk.set_tiling(s, tr, sg)
         return dict(cache[key], key=key, cached=True)
@@ -95,20 +101,36 @@ def autotune(gbk, imgs, cache_path=None, steps=3, use_cache=True, tile_rows=TILE
             ts.append(a.elapsed_time(b))
         return statistics.median(ts)
 
-    tiling = [[0, 0] for _ in range(nf)]
-    best_ms = timed()
-    for s in sorted(range(nf), key=lambda i: -gbk.sigmas[i]):
-        for tr in tile_rows:
-            for sg in segments:
-                if [tr, sg] == tiling[s]:
-                    continue
-                gbk.set_tiling(s, tr, sg)
-                ms = timed()
-                if ms < best_ms:
-                    best_ms = ms
-                    tiling[s] = [tr, sg]
-        gbk.set_tiling(s, *tiling[s])
-    entry = {"tiling": tiling, "ms": best_ms}
+    best = None
+    for c in ctas:
+        gbk.set_option("bank_ctas", c)
+        # start from the best uniform segment count, then descend frequency by frequency
+        start, best_ms = None, None
+        for sg in segments:
+            gbk.set_tiling(-1, 0, sg)
+            ms = timed()
+            if best_ms is None or ms < best_ms:
+                start, best_ms = sg, ms
+        tiling = [[0, start] for _ in range(nf)]
+        gbk.set_tiling(-1, 0, start)
+        for s in sorted(range(nf), key=lambda i: -gbk.sigmas[i]):
+            for tr in tile_rows:
+                for sg in segments:
+                    if [tr, sg] == tiling[s]:
+                        continue
+                    gbk.set_tiling(s, tr, sg)
+                    ms = timed()
+                    if ms < best_ms:
+                        best_ms = ms
+                        tiling[s] = [tr, sg]
+            gbk.set_tiling(s, *tiling[s])
+        if best is None or best_ms < best[2]:
+            best = (c, tiling, best_ms)
+    c, tiling, best_ms = best
+    gbk.set_option("bank_ctas", c)
+    for s, (tr, sg) in enumerate(tiling):
+        gbk.set_tiling(s, tr, sg)
+    entry = {"tiling": tiling, "ctas": c, "ms": best_ms}
     if use_cache:
         cache = _load(path)
         cache[key] = entry

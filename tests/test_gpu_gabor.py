@@ -318,3 +318,28 @@ def test_row_pass_forms_pipelined_bitwise(torch_cuda):
     for form in (1, 2):
         (a,), (b,) = _schedules(torch_cuda, [img], th, om, sg, opts=(("row_pass", form),))
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("row_pass", [1, 2])
+@pytest.mark.parametrize("boundary", ["zero", "replicate"])
+def test_two_ctas_per_sm_bitwise(torch_cuda, row_pass, boundary):
+    # GB_OPT_BANK_CTAS = 2: two CTAs of 8 warps per SM (two row-pass sweeps per block, smaller
+    # tiles for large radii); every output takes the same operations as with one CTA of 16.
+    from paper_1704_05231_gb300 import GaborBank
+    torch = torch_cuda
+    imgs = [synth.pink_noise([37, i], h, w) for i, (h, w) in enumerate([(37, 75), (300, 161), (1, 40)])]
+    th = [0.0, 0.6, math.pi / 2, math.pi - 0.6, 2.0]
+    om, sg = [2.5, 0.4, 0.15, 0.05], [0.3, 1.5, 11.0, 40.0]   # R up to 120
+    res = []
+    for ctas in (1, 2):
+        with GaborBank(th, om, sg, boundary=boundary) as gbk:
+            gbk.set_option("row_pass", row_pass)
+            gbk.set_option("bank_ctas", ctas)
+            ts = [torch.from_numpy(i).cuda() for i in imgs]
+            res.append([gbk.filter(t).cpu().numpy() for t in ts] +
+                       [o.cpu().numpy() for o in gbk.filter_batch(ts)])
+            gbk.device_status()
+    for x, y in zip(*res):
+        assert np.array_equal(x, y)
+    ref = oracle.gabor_bank(imgs[0], th, om, sg, boundary=boundary)
+    assert rel_err(res[1][0], ref) <= FP32_TOL
