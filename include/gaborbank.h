@@ -183,7 +183,13 @@ typedef enum {
        (each with half of the SM's shared memory, so smaller row tiles for large radii; falls
        back to 1 where a frequency does not fit, and under GB_OPT_PIPELINE = 2).  Results are
        identical. */
-    GB_OPT_BANK_CTAS = 10
+    GB_OPT_BANK_CTAS = 10,
+    /* Form of the FP32 SDFT passes (Eq. 19-24): 0 automatic (= 2), 1 demodulate, smooth with
+       the real Gaussian, remodulate, in both passes (the steps as the paper writes them), 2 one
+       convolution with the modulated taps S(a - Mx/2) exp(-i w0 u a) per pass: J_u is read
+       straight from its ring for every v, and F_{Mx-u,v} comes from the same four real sums
+       over J*_u.  Results agree to FP32 rounding.  The tensor-core SDFT is unaffected. */
+    GB_OPT_SDFT_FORM = 11
 } gb_option;
 
 /* 1-D Gaussian smoothers (GB_OPT_SMOOTHER). */

@@ -922,6 +922,7 @@ gb_status gabor_bank_sdft(gabor_bank_t h, const float *d_img, int H, int W, int6
     a.taps_y = h->d_sdft_taps + (kMaxSdftM + 8);
     a.tw_x = h->d_sdft_tw;
     a.tw_y = h->d_sdft_tw + kMaxSdftM;
+    a.demod_form = h->sdft_form == 1 ? 1 : 0;
     if (h->prec == GB_FP32) {
         // Filter order (Sec. III-B).  Vertical first (a transposed problem) saves FMAs when
         // My > Mx (the first FIR pass along the longer side), but its stores run across the
@@ -1103,6 +1104,10 @@ gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value)
             h->fp32_ctas_opt = (int)value;
             free_tables(h);
         }
+        return GB_OK;
+    case GB_OPT_SDFT_FORM:
+        if (value < 0 || value > 2) return fail(GB_ERR_INVALID_ARG, "GB_OPT_SDFT_FORM takes 0, 1 or 2");
+        h->sdft_form = (int)value;
         return GB_OK;
     case GB_OPT_BOUNDARY:
         if (value < GB_BOUNDARY_ZERO || value > GB_BOUNDARY_MIRROR)

@@ -172,6 +172,64 @@ __device__ __forceinline__ void conv8_linear_ct(const float *__restrict__ src, c
     }
 }
 
+// Complex taps over a ring of complex rows J (the SDFT column pass in modulated-tap form), for
+// 8 consecutive outputs: with taps g = (Gr, Gi, Gi, Gr),
+//   ac[j] += (Gr Jr, Gi Jr),  bd[j] += (Gi Ji, Gr Ji)
+// so that sum g J = (ac.x - bd.x, ac.y + bd.y) and sum g conj(J) = (ac.x + bd.x, ac.y - bd.y).
+__device__ __forceinline__ void conv_step_cc(const float2 (&lo)[8], const float2 (&hi)[8],
+                                             const float4 *__restrict__ g4, float2 (&ac)[8], float2 (&bd)[8])
+{
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const float4 g = g4[d];
+        const float2 gri = make_float2(g.x, g.y), gir = make_float2(g.z, g.w);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float2 w = j + d < 8 ? lo[j + d] : hi[j + d - 8];
+            ac[j] = ffma2(gri, make_float2(w.x, w.x), ac[j]);
+            bd[j] = ffma2(gir, make_float2(w.y, w.y), bd[j]);
+        }
+    }
+}
+
+// Ring source of complex rows (see conv8_ring): out = the four real sums of conv_step_cc over
+// 8 * nchunks taps; reads g4[0 .. 8 * nchunks - 1].
+template <int STRIDE>
+__device__ __forceinline__ void conv8_ring_cc(const float2 *__restrict__ ring, int RS, int slot0,
+                                              const float4 *__restrict__ g4, int nchunks, float2 (&ac)[8],
+                                              float2 (&bd)[8])
+{
+    float2 wa[8], wb[8];
+    int s = slot0;
+    auto adv = [&]() {
+        s += 8;
+        if (s >= RS) s -= RS;
+    };
+    const float2 *p = ring + s * STRIDE;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) wa[i] = p[i * STRIDE];
+    int c = 0;
+    for (; c + 2 <= nchunks; c += 2) {
+        adv();
+        p = ring + s * STRIDE;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) wb[i] = p[i * STRIDE];
+        conv_step_cc(wa, wb, g4 + 8 * c, ac, bd);
+        adv();
+        p = ring + s * STRIDE;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) wa[i] = p[i * STRIDE];
+        conv_step_cc(wb, wa, g4 + 8 * (c + 1), ac, bd);
+    }
+    if (c < nchunks) {
+        adv();
+        p = ring + s * STRIDE;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) wb[i] = p[i * STRIDE];
+        conv_step_cc(wa, wb, g4 + 8 * c, ac, bd);
+    }
+}
+
 // 4-byte global -> shared async copy; src_bytes = 0 writes a zero without reading.
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem, int src_bytes)
 {

@@ -200,6 +200,7 @@ struct SdftArgs {
     int TH, seg_len, RS, SW, RW;
     int bmode;           // BoundaryMode
     int trans;           // 1: a transposed problem (vertical pass first); outputs are written back transposed
+    int demod_form;      // 1: demodulate / smooth / remodulate step by step; 0: modulated taps
 };
 
 // One frequency of the plan.
@@ -287,6 +288,7 @@ struct gabor_bank {
     int fp32_row_form = 0;                    // GB_OPT_ROW_PASS (0 automatic, 1 demodulation, 2 modulated taps)
     int fp32_ctas_opt = 0;                    // GB_OPT_BANK_CTAS (0 automatic, 1, 2)
     int fp32_ctas = 1;                        // CTAs per SM of the current tables
+    int sdft_form = 0;                        // GB_OPT_SDFT_FORM (0 automatic, 1 step by step, 2 modulated taps)
     int sdft_order = 0;                       // 0 automatic, 1 horizontal pass first, 2 vertical first
     float *d_transp = nullptr;                // transposed image for the vertical-first SDFT
     size_t transp_elems = 0;

@@ -14,6 +14,13 @@
 //     conjugate fill          F_{(Mx-u)%Mx, My-v} = F*_{u,v} and F_{u, My-v} = F*_{Mx-u,v}
 //                             for 0 < v < My/2 (Algorithm 2, last loop).
 //
+// With the FIR passes used here each demodulate / smooth / remodulate triple is one
+// convolution with modulated taps: J_u(x) = sum_a S(a - Mx/2) e^{-i w0 u a} f(xhat + a) and
+// F_{u,v}(y) = sum_b S(b - My/2) e^{-i w0 v b} J_u(yhat + b), F_{Mx-u,v} the same sum over
+// J*_u (twiddles from the exact integers (u a) mod Mx, (v b) mod My).  That form (the
+// default) reads J_u straight from its ring for every v, with no demodulated copy of the
+// window and no barrier between the v passes; the step-by-step form is kept as an option.
+//
 // Filter order (Sec. III-B): the pass over the first axis runs for M/2 + 1 frequencies, the
 // second for all M of the first times M/2 + 1 of its own.  With the FIR passes used here the
 // first pass needs fewer FMAs along the longer window side; on request (vertical first) the
@@ -39,11 +46,19 @@ size_t sdft_smem_bytes(int TH, int RS, int SW, int RW, int TpadX, int TpadY, int
            (size_t)(My / 2 + 1) * My * sizeof(float2) + (size_t)round_up(RS, 4) * sizeof(int);
 }
 
+// Modulated-tap form: J ring, raw rows, row taps (complex), column taps per v as
+// (Gr, Gi, Gi, Gr).  Every region starts on a 16-byte boundary.
+size_t sdft_mt_smem_bytes(int TH, int RS, int RW, int TpadX, int TpadY, int My)
+{
+    return (size_t)RS * (kStripW + 1) * sizeof(float2) + (size_t)2 * TH * RW * sizeof(float) +
+           (size_t)(TpadX + 8) * sizeof(float2) + (size_t)(My / 2 + 1) * (TpadY + 8) * sizeof(float4);
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
+// Step-by-step form: demodulate, smooth with the real Gaussian, remodulate, in both passes.
+__device__ __forceinline__ void sdft_demod_form(const SdftArgs &a, unsigned char *smem_raw)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int u = blockIdx.z;                 // 0 .. Mx/2
     const int Mx = a.Mx, My = a.My;
     const bool paired = u > 0 && 2 * u < Mx;  // J_0 and J_{Mx/2} are real
@@ -250,6 +265,187 @@ __global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
     }
 }
 
+// Modulated-tap form (see the head of this file).
+__device__ __forceinline__ void sdft_mt_form(const SdftArgs &a, unsigned char *smem_raw)
+{
+    const int u = blockIdx.z;                 // 0 .. Mx/2
+    const int Mx = a.Mx, My = a.My;
+    const bool paired = u > 0 && 2 * u < Mx;  // J_0 and J_{Mx/2} are real
+    const int x0 = blockIdx.x * kStripW;
+    const int ys = blockIdx.y * a.seg_len;
+    if (ys >= a.H) return;
+    const int ye = min(a.H, ys + a.seg_len);
+    const int tid = threadIdx.x;
+    const int stride = kStripW + 1;
+    const int TH = a.TH, RS = a.RS, RW = a.RW;
+    const int nv = My / 2 + 1;
+
+    float2 *jring = reinterpret_cast<float2 *>(smem_raw);
+    float *raw = reinterpret_cast<float *>(jring + (size_t)RS * stride);
+    float2 *gx = reinterpret_cast<float2 *>(raw + (size_t)2 * TH * RW);      // TpadX + 8 row taps
+    float4 *gy = reinterpret_cast<float4 *>(gx + a.TpadX + 8);              // [nv][TpadY + 8]
+    const float4 *gx4 = reinterpret_cast<const float4 *>(gx);
+
+    // G_u(a) = S(a - Mx/2) e^{-i w0 u a};  G_v(b) = S(b - My/2) e^{-i w0 v b}
+    for (int i = tid; i < a.TpadX + 8; i += kThreads) {
+        const float t = i < a.TpadX ? a.taps_x[i] : 0.f;
+        const float2 w = i < Mx ? a.tw_x[(u * i) % Mx] : make_float2(0.f, 0.f);
+        gx[i] = make_float2(t * w.x, -(t * w.y));
+    }
+    for (int i = tid; i < nv * (a.TpadY + 8); i += kThreads) {
+        const int v = i / (a.TpadY + 8), b = i % (a.TpadY + 8);
+        const float t = b < a.TpadY ? a.taps_y[b] : 0.f;
+        const float2 w = b < My ? a.tw_y[(v * b) % My] : make_float2(0.f, 0.f);
+        const float gr = t * w.x, gi = -(t * w.y);
+        gy[i] = make_float4(gr, gi, gi, gr);
+    }
+    for (int i = tid; i < RS * stride; i += kThreads) jring[i] = make_float2(0.f, 0.f);
+    const int ncols = kStripW + Mx - 1;
+    // raw columns past the window are read (by zero taps) and never copied: zero them
+    const int tail = RW - ncols;
+    for (int i = tid; i < 2 * TH * tail; i += kThreads) raw[(size_t)(i / tail) * RW + ncols + i % tail] = 0.f;
+
+    const int ring_origin = ys - My / 2;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int need0 = min(ys + TH, ye) + My / 2 - 1;
+    const int npro = (need0 - ring_origin + TH - 1) / TH;
+    const int nch = (ye - ys + TH - 1) / TH;
+    const int nblocks = npro + nch - 1;
+    // Row blocks: the prologue [ys - My/2, need_0), then [need_{k-1}, need_k) per chunk k,
+    // need_k = min(ys + (k+1) TH, ye) + My/2 - 1 (rows y - My/2 .. y + My/2 - 1).
+    auto block_rows = [&](int b, int &start, int &n) {
+        if (b < npro) {
+            start = ring_origin + b * TH;
+            n = min(TH, need0 - start);
+        } else {
+            const int k = b - npro + 1;
+            start = min(ys + k * TH, ye) + My / 2 - 1;
+            n = min(ys + (k + 1) * TH, ye) + My / 2 - 1 - start;
+        }
+    };
+    auto issue = [&](int b) {
+        int start, n;
+        block_rows(b, start, n);
+        float *dst = raw + (size_t)(b & 1) * TH * RW;
+        if (a.bmode == kBoundaryZero) {
+            for (int r = warp; r < n; r += kThreads / 32) {
+                const int y = start + r;
+                const bool yin = y >= 0 && y < a.H;
+                const float *src = a.img + (int64_t)(yin ? y : 0) * a.pitch;
+                for (int j = lane; j < ncols; j += 32) {
+                    const int gxx = x0 - Mx / 2 + j;
+                    const bool ok = yin && gxx >= 0 && gxx < a.W;
+                    cp_async4(dst + (size_t)r * RW + j, ok ? (const void *)(src + gxx) : (const void *)a.img,
+                              ok ? 4 : 0);
+                }
+            }
+        } else {
+            for (int r = warp; r < n; r += kThreads / 32) {
+                const float *src = a.img + (int64_t)ext_coord(start + r, a.H, a.bmode) * a.pitch;
+                for (int j = lane; j < ncols; j += 32)
+                    cp_async4(dst + (size_t)r * RW + j, src + ext_coord(x0 - Mx / 2 + j, a.W, a.bmode), 4);
+            }
+        }
+        cp_async_commit();
+    };
+    // Row pass of block b (Eq. 19, 21-22 as one complex-tap convolution of the raw rows):
+    // thread = (row r, 8-column group q); a warp covers 8 rows x 4 groups (RW = 1 mod 32:
+    // distinct banks).
+    auto row_pass = [&](int b) {
+        int start, n;
+        block_rows(b, start, n);
+        const float *rawb = raw + (size_t)(b & 1) * TH * RW;
+        const int r = (tid & 7) | ((tid >> 5) << 3);
+        const int q = (tid >> 3) & 3;
+        if (r < n) {
+            float2 acc[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
+            conv8_linear_ct(rawb + (size_t)r * RW + 8 * q, gx4, a.TpadX / 8, acc);
+            const int y = start + r;
+            const int slot = (y - ring_origin) % RS;
+            const bool yin = a.bmode != kBoundaryZero || (y >= 0 && y < a.H);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) jring[slot * stride + 8 * q + j] = yin ? acc[j] : make_float2(0.f, 0.f);
+        }
+    };
+
+    const int64_t plane = a.plane;
+    const int64_t step_y = a.trans ? 1 : a.W, step_x = a.trans ? a.H : 1;
+    auto plane_of = [&](int uu, int vv) -> int64_t { return a.trans ? (int64_t)uu * My + vv : (int64_t)vv * Mx + uu; };
+    // Column pass for output rows [c, c + nout): every v reads the same J ring.
+    auto col_pass = [&](int c, int nout) {
+        const int xl = tid & 31, yg = tid >> 5;
+        const int x = x0 + xl;
+        const int um = (Mx - u) % Mx;
+        for (int v = 0; v < nv; ++v) {
+            const float4 *gv = gy + v * (a.TpadY + 8);
+            const int vm = (My - v) % My;
+            const bool fill = !a.half && v > 0 && 2 * v < My;
+            for (int yb = 8 * yg; yb < nout; yb += 8 * (kThreads / 32)) {
+                const int slot0 = (c - ys + yb) % RS;
+                float2 ac[8], bd[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    ac[j] = make_float2(0.f, 0.f);
+                    bd[j] = make_float2(0.f, 0.f);
+                }
+                conv8_ring_cc<kStripW + 1>(jring + xl, RS, slot0, gv, a.TpadY / 8, ac, bd);
+                if (x < a.W) {
+                    float2 *o_uv = a.out + plane_of(u, v) * plane + x * step_x;
+                    float2 *o_mv = a.out + plane_of(um, v) * plane + x * step_x;
+                    float2 *o_mm = a.out + plane_of(um, vm) * plane + x * step_x;
+                    float2 *o_um = a.out + plane_of(u, vm) * plane + x * step_x;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int y = c + yb + j;
+                        if (y < c + nout) {
+                            // F_{u,v} = sum G_v J_u,  F_{Mx-u,v} = sum G_v J*_u (Eq. 25-26)
+                            const float2 Fa = make_float2(ac[j].x - bd[j].x, ac[j].y + bd[j].y);
+                            const int64_t off = (int64_t)y * step_y;
+                            __stcs(o_uv + off, Fa);
+                            if (fill) __stcs(o_mm + off, make_float2(Fa.x, -Fa.y));
+                            if (paired) {
+                                const float2 Fb = make_float2(ac[j].x + bd[j].x, ac[j].y - bd[j].y);
+                                __stcs(o_mv + off, Fb);
+                                if (fill) __stcs(o_um + off, make_float2(Fb.x, -Fb.y));
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    };
+
+    // The row pass reads raw rows to its end, so block b + 1 (which refills the buffer of
+    // block b - 1) is issued after the barrier that ends the row pass of block b - 1.
+    issue(0);
+    int b = 0;
+    for (int k = 0; k < nch; ++k) {
+        const int last = (k == 0) ? npro : npro + k;
+        for (; b < last; ++b) {
+            cp_async_wait<0>();
+            __syncthreads();   // raw block b visible; the row pass of block b - 1 and the column
+                               // pass of the previous chunk are done
+            if (b + 1 < nblocks) issue(b + 1);
+            row_pass(b);
+        }
+        __syncthreads();       // ring rows of chunk k complete
+        const int c = ys + k * TH;
+        col_pass(c, min(TH, ye - c));
+    }
+}
+
+template <bool MT>
+__global__ void __launch_bounds__(kThreads) k_sdft_fp32(const SdftArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if constexpr (MT)
+        sdft_mt_form(a, smem_raw);
+    else
+        sdft_demod_form(a, smem_raw);
+}
+
 // dst[x][y] = src[y][x] for an H x W image (32 x 32 tiles through shared memory).
 __global__ void k_transpose(const float *__restrict__ src, int64_t pitch, int H, int W, float *__restrict__ dst)
 {
@@ -275,22 +471,26 @@ cudaError_t launch_transpose(const float *src, int64_t pitch, int H, int W, floa
 
 cudaError_t sdft_fp32_prepare()
 {
-    return cudaFuncSetAttribute(k_sdft_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kSmemLimit);
+    cudaError_t e = cudaFuncSetAttribute(k_sdft_fp32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_sdft_fp32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
 }
 
 cudaError_t launch_sdft_fp32(SdftArgs a, int sm_count, cudaStream_t st)
 {
+    const bool mt = !a.demod_form;
     a.TpadX = round_up(a.Mx, 8);
     a.TpadY = round_up(a.My, 8);
-    a.SW = stage_width(kStripW + a.TpadX);
-    a.RW = round_up(kStripW + a.Mx - 1, 4);
+    a.SW = mt ? 0 : stage_width(kStripW + a.TpadX);
+    // modulated taps: raw rows hold every tap window of the strip (zero tail), 1 mod 32 floats apart
+    a.RW = mt ? round_up(kStripW + a.TpadX - 1, 32) + 1 : round_up(kStripW + a.Mx - 1, 4);
     int TH = 64;
     size_t smem;
     for (;;) {
         a.TH = TH;
         a.RS = round_up(TH + a.My - 1, 8);
-        smem = sdft_smem_bytes(TH, a.RS, a.SW, a.RW, a.TpadX, a.TpadY, a.My);
+        smem = mt ? sdft_mt_smem_bytes(TH, a.RS, a.RW, a.TpadX, a.TpadY, a.My)
+                  : sdft_smem_bytes(TH, a.RS, a.SW, a.RW, a.TpadX, a.TpadY, a.My);
         if (smem <= (size_t)kSmemLimit || TH <= 8) break;
         TH /= 2;
     }
@@ -305,7 +505,10 @@ cudaError_t launch_sdft_fp32(SdftArgs a, int sm_count, cudaStream_t st)
     a.seg_len = (a.H + nseg - 1) / nseg;
     nseg = (a.H + a.seg_len - 1) / a.seg_len;
     const dim3 grid(nstrips, nseg, nu);
-    k_sdft_fp32<<<grid, kThreads, smem, st>>>(a);
+    if (mt)
+        k_sdft_fp32<true><<<grid, kThreads, smem, st>>>(a);
+    else
+        k_sdft_fp32<false><<<grid, kThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

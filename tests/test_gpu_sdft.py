@@ -128,3 +128,41 @@ def test_filter_order_non_square_windows(order, My, Mx):
         mirror.close()
     assert rel_err(got, oracle.sdft(img, 3.0, My, Mx)) <= FP32_TOL
     assert rel_err(gm, oracle.sdft(img, 3.0, My, Mx, boundary="mirror")) <= FP32_TOL
+
+
+@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("boundary", ["zero", "replicate"])
+@pytest.mark.parametrize("H,W,M,sigma", [(64, 80, 16, 4.0), (5, 70, 16, 4.0), (100, 3, 4, 0.8),
+                                         (33, 129, 12, 2.0), (40, 50, (8, 16), 2.0), (90, 40, 32, 6.0)])
+def test_sdft_forms_match_oracle(torch_cuda, form, boundary, H, W, M, sigma):
+    # GB_OPT_SDFT_FORM: 1 the passes step by step (demodulate, smooth, remodulate), 2 one
+    # modulated-tap convolution per pass with J_{Mx-u} = J*_u folded into the column sums.
+    from paper_1704_05231_gb300 import GaborBank
+    img = synth.pink_noise([41, H, W], H, W)
+    My, Mx = (M, M) if isinstance(M, int) else M
+    with GaborBank(boundary=boundary) as gbk:
+        gbk.set_option("sdft_form", form)
+        got = gbk.sdft(torch_cuda.from_numpy(img).cuda(), sigma, M).cpu().numpy()
+        half = gbk.sdft(torch_cuda.from_numpy(img).cuda(), sigma, M, half_spectrum=True).cpu().numpy()
+    ref = oracle.sdft(img, sigma, My, Mx, boundary=boundary)
+    assert rel_err(got, ref) <= FP32_TOL
+    assert np.array_equal(half, got[:My // 2 + 1])
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_sdft_forms_c3_sampled_and_order(torch_cuda, order):
+    from paper_1704_05231_gb300 import GaborBank
+    img = synth.pink_noise(0, 512, 512)
+    res = {}
+    for form in (1, 2):
+        with GaborBank() as gbk:
+            gbk.set_option("sdft_form", form)
+            gbk.set_option("sdft_order", order)
+            res[form] = gbk.sdft(torch_cuda.from_numpy(img).cuda(), 4.0, 16).cpu().numpy()
+    rng = np.random.default_rng(3)
+    xs, ys = sample_points(rng, 512, 512, 200)
+    ref = oracle.sdft(img, 4.0, 16, points=(xs, ys))
+    for form in (1, 2):
+        scale = float(np.max(np.abs(res[form])))
+        assert float(np.max(np.abs(res[form][:, :, ys, xs] - ref))) <= FP32_TOL * scale
+    assert rel_err(res[2], res[1]) <= FP32_TOL
