@@ -437,9 +437,10 @@ __device__ __forceinline__ void sdft_mt_form(const SdftArgs &a, unsigned char *s
 }
 
 // The modulated-tap form is bounded to 80 registers so that three CTAs share an SM (its
-// shared memory allows it; measured 10% faster than two at 16 x 16, a few bytes spilled).
+// shared memory allows it; measured 10% faster than two at 16 x 16, a few bytes spilled);
+// the step-by-step form to 128, so that two do.
 template <bool MT>
-__global__ void __launch_bounds__(kThreads, MT ? 3 : 1) k_sdft_fp32(const SdftArgs a)
+__global__ void __launch_bounds__(kThreads, MT ? 3 : 2) k_sdft_fp32(const SdftArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if constexpr (MT)
