@@ -3,6 +3,9 @@
 // for the contract of every entry point.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+
+#include <cudaTypedefs.h>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -561,6 +564,43 @@ gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
     return GB_OK;
 }
 
+// The driver's tensor-map encoder, fetched once through the runtime (no link against the
+// driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// TMA maps of the blocked intermediate [signal][Hp / 8][W][8] for the column pass, as a 4-D
+// tensor (8 rows of a block, W columns, signals, Hp / 8 blocks; FP16): boxes of 8 x 32 x 4 x 8
+// and 8 x 64 x 2 x 8, no swizzle (they land as the MMA's K-major core matrices), zeros beyond
+// the image width.
+gb_status encode_tc_maps(TcBankArgs &a, int nsig)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return fail(GB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[4] = {8, (cuuint64_t)a.W, (cuuint64_t)nsig, (cuuint64_t)(a.Hp / 8)};
+    const cuuint64_t strides[3] = {16, (cuuint64_t)a.Hp * a.W * 2, (cuuint64_t)a.W * 16};
+    const cuuint32_t elem[4] = {1, 1, 1, 1};
+    const cuuint32_t boxes[2][4] = {{8, 32, 4, 8}, {8, 64, 2, 8}};
+    for (int k = 0; k < 2; ++k) {
+        const CUresult r = enc(&a.tmA[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, a.sig, dims, strides, boxes[k], elem,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(GB_ERR_CUDA, "cuTensorMapEncodeTiled failed for the intermediate");
+    }
+    return GB_OK;
+}
+
 gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int64_t pitch, void *d_out,
                            cudaStream_t st)
 {
@@ -659,6 +699,7 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.layout = h->layout;
     a.nplanes = (int)(h->omega.size() * h->theta.size());
     a.row_y0 = -ypad;
+    GB_TRY(encode_tc_maps(a, h->tc_nsig));
     GB_CU(launch_gabor_tc(a, h->sm_count, st));
     return GB_OK;
 }

@@ -90,15 +90,16 @@ __host__ __device__ inline ColSmem col_smem(int K, int nst)
     L.xch_off = L.a_off + (uint32_t)nst * 128 * K * 2;
     L.desc_off = L.xch_off + 4u * kColTileY * 32 * 4;
     L.bar_off = L.desc_off + kDescBytes;
-    L.misc_off = L.bar_off + 16 * 8;
+    L.misc_off = L.bar_off + 24 * 8;
     L.total = L.misc_off + 64;
     return L;
 }
 
-// A buffers of the column kernel for K: 3 when shared memory allows, else 2 (0: does not fit).
+// A buffers of the column kernel for K: up to kColMaxStages as shared memory allows, at least
+// 2 (0: does not fit).
 __host__ __device__ inline int col_stages(int K)
 {
-    for (int n = 3; n >= 2; --n)
+    for (int n = kColMaxStages; n >= 2; --n)
         if (1024 + col_smem(K, n).total <= (uint32_t)kSmemLimit) return n;
     return 0;
 }
@@ -488,11 +489,20 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
 
 // --------------------------------------------------------------------------- column pass
 // Items: (unit, x0, y0), sorted by frequency; paired units take 32 columns x 4 signals,
-// unpaired ones 64 columns x 2 signals (always 128 A rows).  The producers keep NST - 1 jobs
-// of operand loads in flight ahead of the MMA (NST A buffers).  Epilogue: every warp moves
+// unpaired ones 64 columns x 2 signals (always 128 A rows).  One producer warp keeps NST - 1
+// jobs of A-operand TMA loads in flight ahead of the MMA (NST A buffers).  A box of 8 rows of
+// a block x 32 (64) columns x 4 (2) signals x 8 row blocks of the blocked intermediate lands
+// as 8 x 8-element core matrices: operand row n = 32 s + x (64 s + x), element (n, k) at
+// (k / 8) * 2048 + n * 16 + (k % 8) * 2 bytes, the MMA's K-major layout without swizzle (core
+// matrices 128 bytes apart along n, 2048 along k).  Epilogue: every warp moves its TMEM lane
+// quarter (one signal for 32 columns) to shared memory and releases the accumulator; then
+// each warp remodulates 8 of the 64 rows for every column of the tile.  Epilogue: every warp moves
 // its TMEM lane quarter (one signal for 32 columns) to shared memory and releases the
 // accumulator; then each warp remodulates 16 of the 64 rows for every column of the tile.
-__global__ void __launch_bounds__(512, 1) k_gabor_tc_cols(const __grid_constant__ TcBankArgs a)
+constexpr int kColEpiWarps = 8;                           // warps 0-7; warp 8 produces
+constexpr int kColThreads = 32 * (kColEpiWarps + 1);
+
+__global__ void __launch_bounds__(kColThreads, 1) k_gabor_tc_cols(const __grid_constant__ TcBankArgs a)
 {
     const int nitems = a.nf * a.col_cnt;
     extern __shared__ unsigned char smem_dyn[];
@@ -508,6 +518,7 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_cols(const __grid_constant_
     uint64_t *tmem_empty = bars + kColAcc;       // [kColAcc] 8 epilogue warps
     uint64_t *a_empty = bars + 2 * kColAcc;      // [kColMaxStages] commit
     uint64_t *drain = bars + 2 * kColAcc + kColMaxStages;
+    uint64_t *a_full = bars + 2 * kColAcc + kColMaxStages + 1;   // [kColMaxStages] TMA bytes
     uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
     const uint32_t abuf = 128u * a.col_kmax * 2;
@@ -519,9 +530,12 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_cols(const __grid_constant_
     if (tid == 0) {
         for (int i = 0; i < kColAcc; ++i) {
             mbar_init(&tmem_full[i], 1);
-            mbar_init(&tmem_empty[i], 8);
+            mbar_init(&tmem_empty[i], kColEpiWarps);
         }
-        for (int i = 0; i < kColMaxStages; ++i) mbar_init(&a_empty[i], 1);
+        for (int i = 0; i < kColMaxStages; ++i) {
+            mbar_init(&a_empty[i], 1);
+            mbar_init(&a_full[i], 1);
+        }
         mbar_init(drain, 1);
         *abort_s = 0;
         mbar_fence_init();
@@ -537,106 +551,101 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_cols(const __grid_constant_
     const uint32_t idesc = idesc_f16(0, 128, kColTileY);
     const int njobs = nitems > (int)blockIdx.x ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
-    if (warp >= 8) {
-        // -------------------------------------------------------------- producers
-        constexpr int NP = 256;   // producer threads (warps 8-15)
-        const int ptid = tid - 256;
+    if (warp == kColEpiWarps) {
+        // -------------------------------------------------------------- producer warp
+        // The warp copies G when the frequency changes; lane 0 keeps NST - 1 jobs of A-operand
+        // TMA loads in flight ahead of the MMA and issues the MMAs.
         auto item = [&](int j) { return col_item(a, D, blockIdx.x + j * gridDim.x); };
         auto load_g = [&](int s) {
             const TcFreqDev f = D.freqs[s];
             const uint4 *src = reinterpret_cast<const uint4 *>(f.Bcol);
             uint4 *dst = reinterpret_cast<uint4 *>(sG);
-            for (int i = ptid; i < kColTileY * f.Kcol * 2 / 16; i += NP) dst[i] = src[i];
+            for (int i = lane; i < kColTileY * f.Kcol * 2 / 16; i += 32) dst[i] = src[i];
         };
-        // cp.async of job j's A operand into buffer j % NST (zero rows beyond the image).
-        // Thread ptid owns A row n = ptid % 128 (signal n / xw, column x0 + n % xw) and copies
-        // every second of its K / 8 16-byte chunks; a warp reads 32 consecutive columns of one
-        // 8-row block.
+        // Job j's A operand into buffer j % NST: one box per 64 rows of the window (rows n of
+        // the operand = signal n / xw, column x0 + n % xw; zeros beyond the image width).
         auto issue = [&](int j) {
             const ColItem w = item(j);
             const TcUnitDev u = D.units[w.unit];
             const TcFreqDev f = D.freqs[u.s];
-            const int xw = u.plane_b >= 0 ? 32 : 64;
-            const int n = ptid & 127, sgi = n / xw, x = w.x0 + n - sgi * xw;
-            const bool ok = x < a.W;
-            const int64_t bstride = (int64_t)a.W * 8;   // between 8-row blocks
-            const int64_t yb0 = ((int64_t)a.Lpad + w.y0 - f.R8) >> 3;   // first 8-row block of the window
-            const int kc0 = ptid >> 7;
-            const uint16_t *src = a.sig + (u.sig_idx + sgi) * ((int64_t)a.W * a.Hp) + (yb0 + kc0) * bstride +
-                                  (int64_t)(ok ? x : 0) * 8;
-            const unsigned sbase = smem_u32(sA + (j % NST) * abuf);
-            const int kch = f.Kcol / 8;
-            for (int kc = kc0; kc < kch; kc += 2, src += 2 * bstride) {
-                const unsigned sdst = sbase + sw128_offset(128, n, 8 * kc);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sdst), "l"(src), "r"(ok ? 16 : 0)
-                             : "memory");
-            }
-            cp_async_commit();
+            const int st = j % NST;
+            const void *tm = u.plane_b >= 0 ? (const void *)&a.tmA[0] : (const void *)&a.tmA[1];
+            mbar_arrive_expect_tx(&a_full[st], 128u * f.Kcol * 2);
+            const int yb0 = (a.Lpad + w.y0 - f.R8) >> 3;   // first 8-row block of the window
+            const uint32_t dst = smem_u32(sA + st * abuf);
+            for (int kb = 0; kb < f.Kcol / 64; ++kb)
+                tma_load_4d(dst + kb * 16384u, tm, 0, w.x0, (int)u.sig_idx, yb0 + 8 * kb, &a_full[st]);
         };
-        // every group count below is uniform: jobs past the end commit empty groups
-        for (int p = 0; p < NST - 1; ++p) {
-            if (p < njobs) issue(p);
-            else cp_async_commit();
-        }
+        int issued = 0, landed = 0;   // jobs whose loads were issued / waited for (lane 0)
+        if (lane == 0)
+            for (; issued < NST - 1 && issued < njobs; ++issued) issue(issued);
         int cur_s = -1;
-        for (int j = 0; j < njobs; ++j) {
-            if (named_barrier_or(1, NP, *abort_s != 0)) break;
+        bool ok = true;
+        for (int j = 0; j < njobs && ok; ++j) {
+            if (__shfl_sync(0xffffffffu, (int)*abort_s, 0)) break;
             // G of job j's frequency: every earlier MMA must be done with the previous G
             const int sj = D.units[item(j).unit].s;
-            bool failed = false;
             if (sj != cur_s) {
-                failed = j >= 1 && !mbar_wait(&a_empty[(j - 1) % NST], ((j - 1) / NST) & 1, abort_s);
-                if (named_barrier_or(1, NP, failed)) {
-                    if (ptid == 0) fail_status(a.status, abort_s, 34);
+                bool failed = false;
+                if (lane == 0) failed = j >= 1 && !mbar_wait(&a_empty[(j - 1) % NST], ((j - 1) / NST) & 1, abort_s);
+                if (__shfl_sync(0xffffffffu, failed, 0)) {
+                    if (lane == 0) fail_status(a.status, abort_s, 34);
                     break;
                 }
                 load_g(sj);
+                fence_proxy_async_smem();
+                __syncwarp();
                 cur_s = sj;
             }
-            // job j's operand has landed (NST - 2 younger groups may still be in flight)
-            if (NST >= 3)
-                cp_async_wait<1>();
-            else
-                cp_async_wait<0>();
-            fence_proxy_async_smem();
-            named_barrier(1, NP);
-            if (ptid == 0) {
-                const int b = j % kColAcc;
+            if (lane == 0) {
+                const int b = j % kColAcc, st = j % NST;
                 const TcFreqDev f = D.freqs[sj];
-                if (j >= kColAcc && !mbar_wait(&tmem_empty[b], ((j - kColAcc) / kColAcc) & 1, abort_s)) {
+                const bool got = mbar_wait(&a_full[st], (j / NST) & 1, abort_s);
+                if (got) landed = j + 1;
+                if (!got) {
+                    fail_status(a.status, abort_s, 35);
+                    ok = false;
+                } else if (j >= kColAcc && !mbar_wait(&tmem_empty[b], ((j - kColAcc) / kColAcc) & 1, abort_s)) {
                     fail_status(a.status, abort_s, 32);
+                    ok = false;
                 } else {
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(sA + (j % NST) * abuf), g0 = smem_u32(sG);
+                    const uint32_t a0 = smem_u32(sA + st * abuf), g0 = smem_u32(sG);
                     for (int kb = 0; kb < f.Kcol / 64; ++kb)
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)
-                            tc_mma_f16(tmem + 64u * b, smem_desc_sw128(a0 + kb * 128 * 128) + 2 * kk,
+                            tc_mma_f16(tmem + 64u * b, smem_desc_kmajor(a0 + kb * 16384 + kk * 4096, 2048, 128),
                                        smem_desc_sw128(g0 + kb * kColTileY * 128) + 2 * kk, idesc, (kb | kk) != 0);
                     tc_commit(&tmem_full[b]);
-                    tc_commit(&a_empty[j % NST]);
+                    tc_commit(&a_empty[st]);
+                    // refill: job j + NST - 1 goes into the buffer that job j - 1's MMA read
+                    const int jn = j + NST - 1;
+                    if (jn < njobs) {
+                        if (j >= 1 && !mbar_wait(&a_empty[(j - 1) % NST], ((j - 1) / NST) & 1, abort_s)) {
+                            fail_status(a.status, abort_s, 31);
+                            ok = false;
+                        } else {
+                            issue(jn);
+                            issued = jn + 1;
+                        }
+                    }
                 }
             }
-            // refill: job j + NST - 1 goes into the buffer that job j - 1's MMA read (that MMA
-            // runs while job j's is queued behind it)
-            const int jn = j + NST - 1;
-            if (jn < njobs) {
-                failed = j >= 1 && !mbar_wait(&a_empty[(j - 1) % NST], ((j - 1) / NST) & 1, abort_s);
-                if (named_barrier_or(1, NP, failed)) {
-                    if (ptid == 0) fail_status(a.status, abort_s, 31);
-                    break;
-                }
-                issue(jn);
-            } else {
-                cp_async_commit();
-            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
         }
-        cp_async_wait<0>();
-        if (ptid == 0) {
+        if (lane == 0) {
+            // drain: every MMA is complete, and every TMA load issued has landed, before TMEM
+            // and shared memory are released
             tc_commit(drain);
             if (!mbar_wait(drain, 0, abort_s)) {
                 volatile int dummy = 0;
                 mbar_wait(drain, 0, &dummy);
+            }
+            // loads issued but not waited for (after an abort) land before shared memory is
+            // released
+            for (int jj = landed; jj < issued; ++jj) {
+                volatile int dummy = 0;
+                mbar_wait(&a_full[jj % NST], (jj / NST) & 1, &dummy);
             }
         }
     } else {
@@ -915,7 +924,7 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
         if (e != cudaSuccess) return e;
     }
     if (n_col_items > 0) {
-        k_gabor_tc_cols<<<std::min(n_col_items, sm_count), 512, smem_c, st>>>(a);
+        k_gabor_tc_cols<<<std::min(n_col_items, sm_count), kColThreads, smem_c, st>>>(a);
         return cudaGetLastError();
     }
     return cudaSuccess;

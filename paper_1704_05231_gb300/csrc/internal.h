@@ -1,6 +1,7 @@
 // Internal declarations of the gaborbank library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
@@ -156,6 +157,10 @@ struct TcBankArgs {
     int nplanes;           // n_freq * n_theta
     int row_y0;            // first image row of the row pass (< 0: halo rows for non-zero rules)
     int pad2_;
+    // TMA maps of the intermediate (dimensions 8 rows of a block x W x signals x Hp / 8 blocks,
+    // FP16, no swizzle) for the column pass's A operand: boxes of 8 x 32 columns x 4 signals x
+    // 8 blocks (paired units) and 8 x 64 x 2 x 8 (unpaired units)
+    CUtensorMap tmA[2];
 };
 struct TcGeometry {
     int R, R8, Krow, Kcol, PW;

@@ -29,6 +29,25 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
+// Arrive once and expect `bytes` of asynchronous (TMA) transfers on the barrier's phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// 4-D tiled TMA load of the box at element coordinates (c0, c1, c2, c3) of `tmap` (a kernel
+// parameter) into shared memory at `dst`; completes its bytes on `bar`.  c0 * element size
+// must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void *tmap, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void mbar_inval(uint64_t *bar)
 {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -178,6 +197,19 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
     d |= (uint64_t)1 << 46;                         // descriptor version
     d |= (uint64_t)2 << 61;                         // SWIZZLE_128B
     return d;
+}
+
+// Shared-memory matrix descriptor of a K-major operand without swizzle: 8 x 8-element core
+// matrices of 128 contiguous bytes, `lbo` bytes apart along K and `sbo` bytes apart along the
+// M/N rows.
+__device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);         // start address
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;     // leading byte offset: next core matrix along K
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;     // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    return d;                                        // swizzle mode 0: none
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulator, both operands K-major.
