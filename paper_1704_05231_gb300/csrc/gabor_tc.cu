@@ -519,6 +519,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_gabor_tc_cols(const __grid_c
     uint64_t *a_empty = bars + 2 * kColAcc;      // [kColMaxStages] commit
     uint64_t *drain = bars + 2 * kColAcc + kColMaxStages;
     uint64_t *a_full = bars + 2 * kColAcc + kColMaxStages + 1;   // [kColMaxStages] TMA bytes
+    uint64_t *g_full = bars + 2 * kColAcc + 2 * kColMaxStages + 1;   // G of a frequency landed
     uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
     const uint32_t abuf = 128u * a.col_kmax * 2;
@@ -536,6 +537,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_gabor_tc_cols(const __grid_c
             mbar_init(&a_empty[i], 1);
             mbar_init(&a_full[i], 1);
         }
+        mbar_init(g_full, 1);
         mbar_init(drain, 1);
         *abort_s = 0;
         mbar_fence_init();
@@ -553,15 +555,10 @@ __global__ void __launch_bounds__(kColThreads, 1) k_gabor_tc_cols(const __grid_c
 
     if (warp == kColEpiWarps) {
         // -------------------------------------------------------------- producer warp
-        // The warp copies G when the frequency changes; lane 0 keeps NST - 1 jobs of A-operand
-        // TMA loads in flight ahead of the MMA and issues the MMAs.
+        // Lane 0 loads G (one bulk copy) when the frequency changes, keeps NST - 1 jobs of
+        // A-operand TMA loads in flight ahead of the MMA, and issues the MMAs.
         auto item = [&](int j) { return col_item(a, D, blockIdx.x + j * gridDim.x); };
-        auto load_g = [&](int s) {
-            const TcFreqDev f = D.freqs[s];
-            const uint4 *src = reinterpret_cast<const uint4 *>(f.Bcol);
-            uint4 *dst = reinterpret_cast<uint4 *>(sG);
-            for (int i = lane; i < kColTileY * f.Kcol * 2 / 16; i += 32) dst[i] = src[i];
-        };
+        int g_loads = 0, g_landed = 0;   // G copies issued / waited for (lane 0)
         // Job j's A operand into buffer j % NST: one box per 64 rows of the window (rows n of
         // the operand = signal n / xw, column x0 + n % xw; zeros beyond the image width).
         auto issue = [&](int j) {
@@ -587,14 +584,21 @@ __global__ void __launch_bounds__(kColThreads, 1) k_gabor_tc_cols(const __grid_c
             const int sj = D.units[item(j).unit].s;
             if (sj != cur_s) {
                 bool failed = false;
-                if (lane == 0) failed = j >= 1 && !mbar_wait(&a_empty[(j - 1) % NST], ((j - 1) / NST) & 1, abort_s);
+                if (lane == 0) {
+                    failed = j >= 1 && !mbar_wait(&a_empty[(j - 1) % NST], ((j - 1) / NST) & 1, abort_s);
+                    if (!failed) {
+                        const uint32_t gbytes = kColTileY * D.freqs[sj].Kcol * 2;
+                        mbar_arrive_expect_tx(g_full, gbytes);
+                        bulk_load(smem_u32(sG), D.freqs[sj].Bcol, gbytes, g_full);
+                        ++g_loads;
+                        failed = !mbar_wait(g_full, (g_loads - 1) & 1, abort_s);
+                        if (!failed) g_landed = g_loads;
+                    }
+                }
                 if (__shfl_sync(0xffffffffu, failed, 0)) {
                     if (lane == 0) fail_status(a.status, abort_s, 34);
                     break;
                 }
-                load_g(sj);
-                fence_proxy_async_smem();
-                __syncwarp();
                 cur_s = sj;
             }
             if (lane == 0) {
@@ -646,6 +650,10 @@ __global__ void __launch_bounds__(kColThreads, 1) k_gabor_tc_cols(const __grid_c
             for (int jj = landed; jj < issued; ++jj) {
                 volatile int dummy = 0;
                 mbar_wait(&a_full[jj % NST], (jj / NST) & 1, &dummy);
+            }
+            if (g_landed < g_loads) {
+                volatile int dummy = 0;
+                mbar_wait(g_full, (g_loads - 1) & 1, &dummy);
             }
         }
     } else {
