@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
     uint64_t *tmem_empty = bars + 2;   // [2] 8 epilogue warps
     uint64_t *dm_empty = bars + 4;     // [1] commit: the MMA reading Dm is done
     uint64_t *drain = bars + 5;
+    uint64_t *t_full = bars + 6;       // [1] T of a frequency landed (bulk copy)
     uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
     const TcDesc D = load_desc(a, sm + L.desc_off);
@@ -221,6 +222,7 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
         mbar_init(&tmem_empty[1], kRowEpiWarps);
         mbar_init(dm_empty, 1);
         mbar_init(drain, 1);
+        mbar_init(t_full, 1);
         *abort_s = 0;
         mbar_fence_init();
     }
@@ -243,6 +245,7 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
         const int ptid = tid - 32 * kRowEpiWarps, pwarp = warp - kRowEpiWarps;
         const float sc = ldexpf(1.f, -e);
         int cur_s = -1, job = 0;
+        int t_loads = 0, t_landed = 0;   // T copies issued / waited for (uniform; ptid 0 waits)
         // cp.async of unit u's phases cos(w^c x), sin(w^c x) for the tile's columns into
         // phbuf[slot][0][.] and phbuf[slot][1][.]
         auto issue_phases = [&](const TcUnitDev &u, int x0, int R, int PW, int ncols, int slot) {
@@ -273,9 +276,12 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
                 break;
             }
             if (s != cur_s) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(f.Brow);
-                uint4 *dst = reinterpret_cast<uint4 *>(sT);
-                for (int i = ptid; i < kRowTileX * K * 2 / 16; i += NP) dst[i] = src[i];
+                // one bulk copy; the first MMA of the item waits for it
+                if (ptid == 0) {
+                    mbar_arrive_expect_tx(t_full, kRowTileX * K * 2);
+                    bulk_load(smem_u32(sT), f.Brow, kRowTileX * K * 2, t_full);
+                }
+                ++t_loads;
                 cur_s = s;
             }
             // patch rows y0 .. y0 + TY - 1, columns x0 - R .. x0 + 127 + R (zero outside the image)
@@ -367,7 +373,11 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
                 fence_proxy_async_smem();
                 named_barrier(1, NP);
                 if (ptid == 0) {
-                    if (job >= 2 && !mbar_wait(&tmem_empty[b], ((job - 2) >> 1) & 1, abort_s)) {
+                    const bool t_ok = t_landed == t_loads || mbar_wait(t_full, (t_loads - 1) & 1, abort_s);
+                    if (t_ok) t_landed = t_loads;
+                    if (!t_ok) {
+                        fail_status(a.status, abort_s, 25);
+                    } else if (job >= 2 && !mbar_wait(&tmem_empty[b], ((job - 2) >> 1) & 1, abort_s)) {
                         fail_status(a.status, abort_s, 23);
                     } else {
                         tc_fence_after();
@@ -391,6 +401,10 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
             if (!mbar_wait(drain, 0, abort_s)) {
                 volatile int dummy = 0;
                 mbar_wait(drain, 0, &dummy);
+            }
+            if (t_landed < t_loads) {   // a copy still in flight after an abort lands first
+                volatile int dummy = 0;
+                mbar_wait(t_full, (t_loads - 1) & 1, &dummy);
             }
         }
     } else {
