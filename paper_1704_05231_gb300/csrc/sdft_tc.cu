@@ -47,7 +47,7 @@ __host__ __device__ inline TcLayout tc_layout(int Kp, int NP, int My, int PW)
     L.patch_off = L.a_off + (uint32_t)(Kp / 64) * kTileP * 128;
     L.koff_off = L.patch_off + (uint32_t)My * PW * 4;
     L.bar_off = (L.koff_off + (uint32_t)Kp * 4 + 15) & ~15u;
-    L.misc_off = L.bar_off + 8 * 8;
+    L.misc_off = L.bar_off + 16 * 8;
     L.total = L.misc_off + 64;
     return L;
 }
@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(384, 1) k_sdft_tc(const SdftTcArgs a)
     uint64_t *a_empty = bars + 4;      // [1]  all MMAs of a tile done  (commit, count 1)
     uint64_t *scale_full = bars + 5;   // [2]  tile scale published     (count 1)
     uint64_t *final_bar = bars + 7;    // [1]  drain                    (commit, count 1)
+    uint64_t *b_full = bars + 8;       // [1]  B landed                 (bulk copy)
     uint32_t *tmem_base_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
     int *escale = reinterpret_cast<int *>(sm + L.misc_off + 8);        // [2]
@@ -101,11 +102,6 @@ __global__ void __launch_bounds__(384, 1) k_sdft_tc(const SdftTcArgs a)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // B: resident for the whole CTA.
-    {
-        uint4 *dst = reinterpret_cast<uint4 *>(sB);
-        for (int i = tid; i < a.b_bytes / 16; i += 384) dst[i] = a.Bglob[i];
-    }
     for (int k = tid; k < a.Kp; k += 384) {
         const int b = k / a.Mx, aa = k % a.Mx;
         koff[k] = k < a.K ? b * a.PW + aa : -1;
@@ -119,8 +115,12 @@ __global__ void __launch_bounds__(384, 1) k_sdft_tc(const SdftTcArgs a)
         mbar_init(&scale_full[0], 1);
         mbar_init(&scale_full[1], 1);
         mbar_init(final_bar, 1);
+        mbar_init(b_full, 1);
         *abort_s = 0;
         mbar_fence_init();
+        // B: resident for the whole CTA, one bulk copy that the first MMA waits for
+        mbar_arrive_expect_tx(b_full, (uint32_t)a.b_bytes);
+        bulk_load(smem_u32(sB), a.Bglob, (uint32_t)a.b_bytes, b_full);
     }
     if (warp == 0) {
         tmem_alloc(tmem_base_s, 512);
@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(384, 1) k_sdft_tc(const SdftTcArgs a)
     if (warp >= 8) {
         // ------------------------------------------------------------ producers
         const int ptid = tid - 256;
+        bool b_landed = false;   // ptid 0: B's bulk copy waited for
         // The next tile's patch is prefetched into registers (kPre per thread) while the
         // current tile is converted, so its global-load latency is hidden.
         constexpr int kPre = 24;
@@ -247,7 +248,15 @@ __global__ void __launch_bounds__(384, 1) k_sdft_tc(const SdftTcArgs a)
             if (ptid == 0) {
                 mbar_arrive(&scale_full[i & 1]);
                 bool ok = true;
-                for (int h = 0; h < 2; ++h) {
+                if (!b_landed) {
+                    b_landed = mbar_wait(b_full, 0, abort_s);
+                    if (!b_landed) {
+                        *abort_s = 1;
+                        atomicExch(a.status, 4);
+                        ok = false;
+                    }
+                }
+                for (int h = 0; ok && h < 2; ++h) {
                     if (i > 0 && !mbar_wait(&tmem_empty[h], (i - 1) & 1, abort_s)) {
                         *abort_s = 1;
                         atomicExch(a.status, 3);
@@ -276,6 +285,10 @@ __global__ void __launch_bounds__(384, 1) k_sdft_tc(const SdftTcArgs a)
                 // an abort was raised elsewhere or the MMAs never completed: wait once more
                 volatile int dummy = 0;
                 mbar_wait(final_bar, 0, &dummy);
+            }
+            if (!b_landed) {   // B's copy lands before shared memory is released
+                volatile int dummy = 0;
+                mbar_wait(b_full, 0, &dummy);
             }
         }
     } else {
