@@ -49,10 +49,11 @@ __device__ __forceinline__ void conv_step(const V (&lo)[8], const V (&hi)[8], co
 
 // Contiguous source (row pass): out[j] = sum_t src[j + t] * taps[t], j < 8.
 // Reads src[0 .. 8 * nchunks + 7].  Window and taps of the next chunk are loaded one chunk
-// ahead; two register banks alternate (no copies).
+// ahead; two register banks alternate (no copies).  tail: one more tap, taps[8 nchunks]
+// (filters of 8 k + 1 taps), applied to the window bank already loaded.
 template <typename V>
 __device__ __forceinline__ void conv8_linear(const V *__restrict__ src, const float4 *__restrict__ taps4,
-                                             int nchunks, V (&acc)[8])
+                                             int nchunks, V (&acc)[8], bool tail = false)
 {
     V wa[8], wb[8];
 #pragma unroll
@@ -75,14 +76,21 @@ __device__ __forceinline__ void conv8_linear(const V *__restrict__ src, const fl
         for (int i = 0; i < 8; ++i) wb[i] = src[8 * (c + 1) + i];
         conv_step(wa, wb, t0, t1, acc);
     }
+    if (tail) {
+        const float t = reinterpret_cast<const float *>(taps4)[8 * nchunks];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] = fmav((nchunks & 1) ? wb[j] : wa[j], t, acc[j]);
+    }
 }
 
 // Ring source (column pass): row r of the window is ring[slot(r) * STRIDE], slots advance
 // by 8 per chunk modulo RS.  slot0 and RS are multiples of 8, so a chunk never wraps.  STRIDE
-// is a compile-time constant so the 8 loads of a chunk use immediate offsets.
+// is a compile-time constant so the 8 loads of a chunk use immediate offsets.  tail: as in
+// conv8_linear.
 template <typename V, int STRIDE>
 __device__ __forceinline__ void conv8_ring(const V *__restrict__ ring, int RS, int slot0,
-                                           const float4 *__restrict__ taps4, int nchunks, V (&acc)[8])
+                                           const float4 *__restrict__ taps4, int nchunks, V (&acc)[8],
+                                           bool tail = false)
 {
     V wa[8], wb[8];
     int s = slot0;
@@ -117,6 +125,11 @@ __device__ __forceinline__ void conv8_ring(const V *__restrict__ ring, int RS, i
         for (int i = 0; i < 8; ++i) wb[i] = p[i * STRIDE];
         conv_step(wa, wb, t0, t1, acc);
     }
+    if (tail) {
+        const float t = reinterpret_cast<const float *>(taps4)[8 * nchunks];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] = fmav((nchunks & 1) ? wb[j] : wa[j], t, acc[j]);
+    }
 }
 
 // Complex taps over a real window (the row pass in modulated-tap form): acc[j] += win[j + d] g[d]
@@ -146,8 +159,9 @@ __device__ __forceinline__ void load_ctaps(float2 (&g)[8], const float4 *__restr
 
 // Contiguous real source, complex taps: out[j] = sum_t src[j + t] g[t], j < 8.  Reads
 // src[0 .. 8 * nchunks + 7] and g[0 .. 8 * nchunks + 7] (g4: two complex taps per float4).
+// tail: as in conv8_linear.
 __device__ __forceinline__ void conv8_linear_ct(const float *__restrict__ src, const float4 *__restrict__ g4,
-                                                int nchunks, float2 (&acc)[8])
+                                                int nchunks, float2 (&acc)[8], bool tail = false)
 {
     float wa[8], wb[8];
     float2 ga[8], gb[8];
@@ -169,6 +183,14 @@ __device__ __forceinline__ void conv8_linear_ct(const float *__restrict__ src, c
 #pragma unroll
         for (int i = 0; i < 8; ++i) wb[i] = src[8 * (c + 1) + i];
         conv_step_ct(wa, wb, ga, acc);
+    }
+    if (tail) {   // one more tap, g[8 nchunks] (filters of 8 k + 1 taps), on the loaded bank
+        const float2 g = reinterpret_cast<const float2 *>(g4)[8 * nchunks];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float w = (nchunks & 1) ? wb[j] : wa[j];
+            acc[j] = ffma2(g, make_float2(w, w), acc[j]);
+        }
     }
 }
 

@@ -143,7 +143,10 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
     const int stride = kStripW + 1;
     const int R = f.R, TH = f.TH, RS = f.RS, SW = f.SW, RW = f.RW;
     const int ncols = kStripW + f.T - 1;        // input columns x0 - R .. x0 + 31 + R
-    const int nchunks = f.Tpad / 8;
+    // full 8-tap chunks, and one tail tap for filters of 8 k + 1 taps (R = 0 mod 4) instead of
+    // a chunk of 7 zero taps
+    const bool tail1 = (f.T & 7) == 1;
+    const int nchunks = tail1 ? f.T / 8 : f.Tpad / 8;
     const int64_t plane = (int64_t)im.H * im.W;
     const int64_t ystride = a.layout ? (int64_t)im.W * a.nplanes : (int64_t)im.W;   // between output rows
     const Smem sm = carve(smem_raw, f);
@@ -266,18 +269,20 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
         // 16 (row, 8-column group) outputs per warp, sweeps of 8 kRB rows x 4 groups; the two
         // half warps take the two halves of the tap chunks and add them with one shuffle.
         // Demodulation form: a half warp covers 8 rows x groups 2 q0, 2 q0 + 1 (distinct bank
-        // pairs of the float2 stage); modulated taps: groups q0, q0 + 2 and an odd tap split
-        // where one exists (distinct banks of the raw rows).
+        // pairs of the float2 stage).  Modulated taps (raw rows 1 mod 32 floats apart): the
+        // half warps' tap splits nh are 8 nh floats apart, so groups q0, q0 + 2 (16 banks
+        // apart) for odd nh and 2 q0, 2 q0 + 1 (8 apart) for nh = 2 mod 4 keep all 32 window
+        // loads of a warp on distinct banks (nh = 0 mod 4: two-way conflicts).
         const int hl = lane & 15, half = lane >> 4;
         const int q0 = warp / kRB;
-        const int q = MT ? q0 + 2 * (hl >> 3) : (hl >> 3) | (q0 << 1);
+        int nh = (nchunks + 1) >> 1;
+        if (MT && (nh & 3) == 0 && (nchunks & 1)) --nh;   // same longest half, odd split
+        const int q = MT ? ((nh & 3) == 2 ? 2 * q0 + (hl >> 3) : q0 + 2 * (hl >> 3)) : (hl >> 3) | (q0 << 1);
         for (int r0 = 0; r0 < n; r0 += 8 * kRB) {
         const int r = r0 + ((hl & 7) | ((warp % kRB) << 3));
         // Warp-uniform: the warp's 8 rows start inside the block (rows < TH, so every stage read
         // is in bounds); rows r >= n are computed but not stored.
         if (r0 + 8 * (warp % kRB) < n) {
-            int nh = (nchunks + 1) >> 1;
-            if (MT && (nchunks & 1) && !(nh & 1)) nh = nchunks >> 1;
             const int c0 = half ? nh : 0, cnt = half ? nchunks - nh : nh;
             const int y = start + r;
             const int base = ((y - ring_origin) % RS) * stride + 8 * q;
@@ -287,11 +292,13 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
                 float2 acc[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
+                // the tail tap goes to the half warp that ends at the last chunk
                 if (MT)
                     conv8_linear_ct(rawb + (size_t)r * RW + 8 * q + 8 * c0,
-                                    ctaps4 + v * ((f.Tpad + 8) / 2) + 4 * c0, cnt, acc);
+                                    ctaps4 + v * ((f.Tpad + 8) / 2) + 4 * c0, cnt, acc, tail1 && half);
                 else
-                    conv8_linear<float2>(sm.stage + (size_t)r * SW + 8 * q + 8 * c0, taps4 + 2 * c0, cnt, acc);
+                    conv8_linear<float2>(sm.stage + (size_t)r * SW + 8 * q + 8 * c0, taps4 + 2 * c0, cnt, acc,
+                                         tail1 && half);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, 16);
@@ -344,7 +351,8 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
             float2 acc[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
-            conv8_ring<float2, kStripW + 1>(sm.ring2 + (size_t)sub * RS * stride + xl, RS, slot0, taps4, nchunks, acc);
+            conv8_ring<float2, kStripW + 1>(sm.ring2 + (size_t)sub * RS * stride + xl, RS, slot0, taps4, nchunks, acc,
+                                            tail1);
             if (x < im.W) {
                 float2 *o = im.out + out_offset(a, oplane, plane, x);
 #pragma unroll
