@@ -343,3 +343,20 @@ def test_two_ctas_per_sm_bitwise(torch_cuda, row_pass, boundary):
         assert np.array_equal(x, y)
     ref = oracle.gabor_bank(imgs[0], th, om, sg, boundary=boundary)
     assert rel_err(res[1][0], ref) <= FP32_TOL
+
+
+def test_c2_full_size_tuned_geometry_bitwise(torch_cuda):
+    # The geometry the benchmark's autotuner picks (two CTAs of 8 warps per SM, per-frequency
+    # tiles and segments) gives the same bits as the default geometry on the full-size bank.
+    from paper_1704_05231_gb300 import GaborBank
+    torch = torch_cuda
+    img = torch.from_numpy(synth.paper_like(0, 1024, 1024)).cuda()
+    th, om, sg = c2_bank()
+    with GaborBank(th, om, sg) as gbk:
+        ref = gbk.filter(img).cpu().numpy()
+        gbk.set_option("bank_ctas", 2)
+        for s, (tr, seg) in enumerate([(0, 2), (0, 2), (0, 0), (32, 2)]):
+            gbk.set_tiling(s, tr, seg)
+        got = gbk.filter(img).cpu().numpy()
+        gbk.device_status()
+    assert np.array_equal(got, ref)
