@@ -8,9 +8,10 @@
 //                  while every lane runs its row's recursion: forward over f_c, f_s (Eq. 5)
 //                  into a scratch buffer, then backward, remodulation into J (Eq. 5-6) and the
 //                  column signals of Eq. 10 for theta and pi - theta (Eq. 15-16).
-//   column kernel  one thread per (unit, image column): forward recursion of the unit's 2 or
-//                  4 column signals down the column into scratch, backward recursion upward,
-//                  remodulation by (cos, sin)(w^s y) (Eq. 7-8, 15-16) and the output stores.
+//   column kernel  one thread per (unit, image column, column signal): forward recursion of
+//                  the signal down the column into scratch, backward recursion upward; the
+//                  two signals of an orientation meet by shuffle for the remodulation by
+//                  (cos, sin)(w^s y) (Eq. 7-8, 15-16) and the output stores.
 //
 // Every signal is extended by P_s = ceil(12 sigma_s) + 32 samples on each side (zeros under
 // the zero rule, whose forward passes can start at the first image sample), and each
@@ -139,81 +140,70 @@ __global__ void __launch_bounds__(32 * kIirWarps) k_iir_rows(const IirArgs a)
 // Rows per block of the column recursion: the block's loads are issued together, ahead of its
 // recursion steps, so one memory latency covers kIirRows steps.
 constexpr int kIirRows = 16;
+constexpr int kIirColThreads = 128;   // 64 columns x 2 signals of one pair per CTA
 
-__global__ void __launch_bounds__(128) k_iir_cols(const IirArgs a)
+// Thread = (column, one column signal of a pair): lane = 2 (column) + s, s = 0 for the P signal
+// and 1 for Q; blockIdx.z picks the pair (0: theta_a, 1: pi - theta_a of a paired unit).  The
+// two signals of an output meet by one shuffle.  (One thread per signal rather than per unit
+// column: the recursion is sequential along the column, so parallelism comes from lanes.)
+__global__ void __launch_bounds__(kIirColThreads) k_iir_cols(const IirArgs a)
 {
-    const int u = blockIdx.y;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= a.W) return;
+    const int u = blockIdx.y, pair = blockIdx.z;
     const UnitDev un = a.units[u];
-    const IirFreq fq = a.freqs[un.s];
     const bool paired = un.plane_b >= 0;
+    if (pair == 1 && !paired) return;
+    const int sgn = threadIdx.x & 1;
+    const int x = blockIdx.x * (kIirColThreads / 2) + (threadIdx.x >> 1);
+    const bool xin = x < a.W;
+    const IirFreq fq = a.freqs[un.s];
     const bool ext = a.bmode != kBoundaryZero;
     const int Pyl = ext ? fq.P : 0;                // extension above y = 0
     const int Hc = Pyl + a.H + fq.P;
     const float c0 = fq.c[0], c1 = fq.c[1], c2 = fq.c[2], c3 = fq.c[3];
     const int64_t plane = (int64_t)a.Hr * a.W;
-    const float *sig0 = a.sig + un.sig * plane;
-    float *tmp0 = reinterpret_cast<float *>(a.tmp) + un.sig * ((int64_t)a.Hcmax * a.W);
+    const int k = 2 * pair + sgn;                  // the unit's column signal of this thread
+    const float *sig = a.sig + (un.sig + k) * plane;
     const int64_t tplane = (int64_t)a.Hcmax * a.W;
-    const int nsig = paired ? 4 : 2;
+    float *tmp = reinterpret_cast<float *>(a.tmp) + (un.sig + k) * tplane;
+    const int xc = xin ? x : 0;
 
-    float w1[4] = {0.f, 0.f, 0.f, 0.f}, w2[4] = {0.f, 0.f, 0.f, 0.f}, w3[4] = {0.f, 0.f, 0.f, 0.f};
+    float w1 = 0.f, w2 = 0.f, w3 = 0.f;
     for (int j0 = 0; j0 < Hc; j0 += kIirRows) {
-        float v[4][kIirRows];
+        float v[kIirRows];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-            for (int t = 0; t < kIirRows; ++t) {
-                const int rr = j0 + t - Pyl + a.Py;   // row of the signal buffer
-                v[k][t] = (k < nsig && j0 + t < Hc && rr >= 0 && rr < a.Hr) ? sig0[k * plane + (int64_t)rr * a.W + x] : 0.f;
-            }
+        for (int t = 0; t < kIirRows; ++t) {
+            const int rr = j0 + t - Pyl + a.Py;   // row of the signal buffer
+            v[t] = (xin && j0 + t < Hc && rr >= 0 && rr < a.Hr) ? sig[(int64_t)rr * a.W + xc] : 0.f;
+        }
 #pragma unroll
         for (int t = 0; t < kIirRows; ++t) {
             if (j0 + t >= Hc) break;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (k < nsig) {
-                    const float w = fmaf(c0, v[k][t], fmaf(c1, w1[k], fmaf(c2, w2[k], c3 * w3[k])));
-                    w3[k] = w2[k]; w2[k] = w1[k]; w1[k] = w;
-                    tmp0[k * tplane + (int64_t)(j0 + t) * a.W + x] = w;
-                }
-            }
+            const float w = fmaf(c0, v[t], fmaf(c1, w1, fmaf(c2, w2, c3 * w3)));
+            w3 = w2; w2 = w1; w1 = w;
+            if (xin) tmp[(int64_t)(j0 + t) * a.W + x] = w;
         }
     }
-    float s1[4] = {0.f, 0.f, 0.f, 0.f}, s2[4] = {0.f, 0.f, 0.f, 0.f}, s3[4] = {0.f, 0.f, 0.f, 0.f};
+    float s1 = 0.f, s2 = 0.f, s3 = 0.f;
     const int64_t oplane = (int64_t)a.H * a.W;
+    const int oplane_idx = pair ? un.plane_b : un.plane_a;
     for (int j1 = Hc - 1; j1 >= 0; j1 -= kIirRows) {
-        float v[4][kIirRows];
+        float v[kIirRows];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-            for (int t = 0; t < kIirRows; ++t)
-                v[k][t] = (k < nsig && j1 - t >= 0) ? tmp0[k * tplane + (int64_t)(j1 - t) * a.W + x] : 0.f;
+        for (int t = 0; t < kIirRows; ++t) v[t] = (xin && j1 - t >= 0) ? tmp[(int64_t)(j1 - t) * a.W + x] : 0.f;
 #pragma unroll
         for (int t = 0; t < kIirRows; ++t) {
             const int j = j1 - t;
-            if (j < 0) break;
-            float sv[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                sv[k] = 0.f;
-                if (k < nsig) {
-                    sv[k] = fmaf(c0, v[k][t], fmaf(c1, s1[k], fmaf(c2, s2[k], c3 * s3[k])));
-                    s3[k] = s2[k]; s2[k] = s1[k]; s1[k] = sv[k];
-                }
-            }
+            if (j < 0) break;   // uniform across the warp
+            const float sv = fmaf(c0, v[t], fmaf(c1, s1, fmaf(c2, s2, c3 * s3)));
+            s3 = s2; s2 = s1; s1 = sv;
+            const float q = __shfl_xor_sync(0xffffffffu, sv, 1);   // the pair's other signal
             const int y = j - Pyl;
-            if (y >= 0 && y < a.H) {
+            if (sgn == 0 && xin && y >= 0 && y < a.H) {
                 const float2 cy = un.phy[y];
-                // Eq. 7-8 (theta) and Eq. 15-16 (pi - theta)
+                // Eq. 7-8 (theta) or Eq. 15-16 (pi - theta)
                 const int64_t pix = (int64_t)y * a.W + x;
-                const int64_t oa = a.layout ? pix * a.nplanes + un.plane_a : (int64_t)un.plane_a * oplane + pix;
-                __stcs(a.out + oa, make_float2(fmaf(cy.x, sv[0], cy.y * sv[1]), fmaf(cy.y, sv[0], -cy.x * sv[1])));
-                if (paired) {
-                    const int64_t ob = a.layout ? pix * a.nplanes + un.plane_b : (int64_t)un.plane_b * oplane + pix;
-                    __stcs(a.out + ob, make_float2(fmaf(cy.x, sv[2], cy.y * sv[3]), fmaf(cy.y, sv[2], -cy.x * sv[3])));
-                }
+                const int64_t o = a.layout ? pix * a.nplanes + oplane_idx : (int64_t)oplane_idx * oplane + pix;
+                __stcs(a.out + o, make_float2(fmaf(cy.x, sv, cy.y * q), fmaf(cy.y, sv, -cy.x * q)));
             }
         }
     }
@@ -232,8 +222,8 @@ cudaError_t launch_gabor_iir(const IirArgs &a, int nunits, cudaStream_t st)
     k_iir_rows<<<gr, 32 * kIirWarps, kIirWarps * sizeof(IirRowSmem), st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const dim3 gc((a.W + 127) / 128, nunits);
-    k_iir_cols<<<gc, 128, 0, st>>>(a);
+    const dim3 gc((a.W + kIirColThreads / 2 - 1) / (kIirColThreads / 2), nunits, 2);
+    k_iir_cols<<<gc, kIirColThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
