@@ -18,9 +18,13 @@
 //                  -> P, Q, P', Q' (Eq. 9).  Epilogue: F = remodulation by (cos, sin)(w^s y)
 //                  (Eq. 7-8, 15-16), complex64 stores with coalesced rows.
 //
-// Both kernels are persistent (one CTA per SM) and warp-specialised: warps 4-7 stage operands
-// in the 128-byte-swizzled K-major layout and thread 128 issues tcgen05.mma into one of two TMEM
-// buffers; warps 0-3 read the accumulators with tcgen05.ld.  Every mbarrier wait is bounded.
+// Both kernels are persistent (one CTA per SM) and warp-specialised.  Row kernel: 12 producer
+// warps stage the patch and build Dm in the 128-byte-swizzled K-major layout, one producer
+// thread issues tcgen05.mma into one of two TMEM buffers, 4 epilogue warps read the
+// accumulators with tcgen05.ld.  Column kernel: one producer warp brings the A operands by TMA
+// (cp.async.bulk.tensor) into up to four buffers and issues the MMAs into four TMEM
+// accumulators; 8 epilogue warps.  The frequency's Toeplitz operand (T, G) arrives by one bulk
+// copy (cp.async.bulk) on an mbarrier.  Every mbarrier wait is bounded.
 #include <algorithm>
 #include <type_traits>
 

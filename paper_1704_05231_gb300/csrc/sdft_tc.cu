@@ -17,7 +17,8 @@
 //
 // Roles (384 threads): warps 0-7 epilogue (TMEM lanes 0-127 = the tile's pixels, two warps
 // per lane quadrant splitting the columns); warps 8-11 producers (patch load, per-tile scale,
-// im2col); thread 256 issues the MMAs.
+// im2col); thread 256 issues the MMAs.  B arrives once per CTA by one bulk copy (cp.async.bulk)
+// that the first MMA waits for.
 // Every mbarrier wait is bounded; on timeout the CTA records a code in the status word and
 // stops.
 #include <algorithm>
