@@ -459,6 +459,7 @@ gb_status get_worklist(gabor_bank *h, const std::vector<int64_t> &shapes, WorkIt
 void free_tc(gabor_bank *h)
 {
     dfree(h->d_tcB);
+    dfree(h->d_tcAm);
     dfree(h->d_tcfreq);
     dfree(h->d_tcunit);
     dfree(h->d_tcsig);
@@ -533,11 +534,28 @@ gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
         float unscale = 1.f;
         GB_CU(build_gabor_tc_b(h->d_tcB + off_r[s], h->d_tcB + off_c[s], g.R, h->freqs[s].sigma, bf16, &unscale, st));
         fd[s] = TcFreqDev{h->d_tcB + off_r[s], h->d_tcB + off_c[s], g.R, g.R8, g.Krow, g.Kcol, unscale, unscale,
-                          h->freqs[s].u0, 0};
+                          h->freqs[s].u0, gabor_tc_mt_k(g.R)};
     }
     std::vector<int> order(nf);
     for (int s = 0; s < nf; ++s) order[s] = s;
     std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return h->freqs[p].R > h->freqs[q].R; });
+    // modulated-tap row operands: one [128][Kmt] block per unit
+    std::vector<size_t> off_am(nu);
+    size_t am_total = 0;
+    h->tc_mt_kmax = h->tc_mt_pwmax = 0;
+    for (int i = 0; i < nu; ++i) {
+        const int R = h->freqs[h->units[i].s].R;
+        off_am[i] = am_total;
+        am_total += (size_t)128 * gabor_tc_mt_k(R);
+        h->tc_mt_kmax = std::max(h->tc_mt_kmax, gabor_tc_mt_k(R));
+        h->tc_mt_pwmax = std::max(h->tc_mt_pwmax, gabor_tc_mt_pw(R));
+    }
+    h->tc_mt_ty = gabor_tc_mt_tile_y(h->tc_mt_kmax, h->tc_mt_pwmax);
+    GB_TRY(dalloc(&h->d_tcAm, std::max<size_t>(am_total, 1)));
+    for (int i = 0; i < nu; ++i) {
+        const Freq &fq = h->freqs[h->units[i].s];
+        GB_CU(build_gabor_tc_am(h->d_tcAm + off_am[i], fq.R, fq.sigma, h->units[i].wc, st));
+    }
     std::vector<TcUnitDev> ud(nu);
     const int K = (int)h->theta.size();
     int64_t sig = 0;
@@ -551,6 +569,7 @@ gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
         ud[i].plane_b = paired ? un.s * K + un.k_b : -1;
         ud[i].pad_ = 0;
         ud[i].sig_idx = sig;
+        ud[i].Am = h->d_tcAm + off_am[i];
         sig += paired ? 4 : 2;
     }
     GB_CU(cudaMemcpy(h->d_tcfreq, fd.data(), nf * sizeof(TcFreqDev), cudaMemcpyHostToDevice));
@@ -618,13 +637,16 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     GB_TRY(ensure_tables(h, H, W, st));
     if (tables_move) free_tc(h);
     GB_TRY(ensure_tc(h, st));
-    const int ty = h->tc_row_ty;
+    // row pass: modulated taps (64-column tiles) unless GB_OPT_ROW_PASS asks for the steps
+    const bool row_mt = h->fp32_row_form != 1;
+    const int ty = row_mt ? h->tc_mt_ty : h->tc_row_ty;
+    const int tile_x = row_mt ? gabor_tc_mt_tile_x() : gabor_tc_row_tile_x();
     // Non-zero boundary rules: the row pass also produces the halo rows [-R, 0) and
     // [H, H + R) of the column signals, from the extended image.
     int rmax = 0;
     for (const Freq &f : h->freqs) rmax = std::max(rmax, f.R);
     const int ypad = h->boundary == kBoundaryZero ? 0 : (rmax + ty - 1) / ty * ty;
-    const int64_t row_cnt = (int64_t)((H + 2 * ypad + ty - 1) / ty) * ((W + 127) / 128);
+    const int64_t row_cnt = (int64_t)((H + 2 * ypad + ty - 1) / ty) * ((W + tile_x - 1) / tile_x);
     const int64_t col_cnt = ny64 * (h->tc_np_f * nx32 + (h->tc_nu_f - h->tc_np_f) * nx64);
     if ((int64_t)nf * std::max(row_cnt, col_cnt) > (int64_t)1 << 30)
         return fail(GB_ERR_UNSUPPORTED, "image too large for the tensor-core bank");
@@ -676,8 +698,9 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.freqs = h->d_tcfreq;
     a.units = h->d_tcunit;
     a.status = h->d_status;
-    a.row_kmax = h->tc_row_kmax;
-    a.row_pwmax = h->tc_row_pwmax;
+    a.row_kmax = row_mt ? h->tc_mt_kmax : h->tc_row_kmax;
+    a.row_pwmax = row_mt ? h->tc_mt_pwmax : h->tc_row_pwmax;
+    a.row_mt = row_mt ? 1 : 0;
     a.col_kmax = h->tc_col_kmax;
     a.minmax = h->d_tcminmax;
     a.onesA = onesA;
@@ -689,7 +712,7 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.nf = nf;
     a.nu_f = h->tc_nu_f;
     a.np_f = h->tc_np_f;
-    a.row_nx = (W + 127) / 128;
+    a.row_nx = (W + tile_x - 1) / tile_x;
     a.row_cnt = (int)row_cnt;
     a.col_ny = (int)ny64;
     a.col_nx32 = (int)nx32;

@@ -505,6 +505,315 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
     if (warp == 0) tmem_dealloc(tmem, 256);
 }
 
+// ------------------------------------------------------------ row pass, modulated taps
+// GB_OPT_ROW_PASS = 2 (default): Eq. 5-6 as one product with a per-unit operand of modulated
+// taps, no per-unit demodulated copy of the patch:
+//
+//   D[(x, re|im)][r] = sum_k Am[(x, re|im)][k] P[r][k],
+//   Am[(x, re)][k] = S(d) cos(w^c d),  Am[(x, im)][k] = -S(d) sin(w^c d),  d = k - x - R,
+//   P[r][k] = (f(y0 + r, x0 - R + k) - c) 2^-e
+//
+// -> Re J, Im J of 64 columns x TY rows of one unit.  Operand row n = 2 x + (0 | 1), so the
+// two parts of a column sit in adjacent TMEM lanes and meet by shuffle.  Per item (frequency,
+// tile): producers (warps 8-15) stage the patch once and convert it to the FP16 operand P; the
+// MMA thread (256) brings each unit's Am (built once per plan) by one bulk copy into one of two
+// buffers and issues the MMA; 8 epilogue warps (two per lane quarter) form the column signals
+// of Eq. 10 and store them to the intermediate like the step-by-step kernel.
+constexpr int kMtTileX = 64;     // output columns per item (MMA M = 2 x 64)
+constexpr int kMtEpiWarps = 8;
+
+struct MtSmem {
+    uint32_t a_off, p_off, patch_off, desc_off, bar_off, misc_off, total;
+};
+
+__host__ __device__ inline MtSmem mt_smem(int K, int PW, int TY)
+{
+    MtSmem L;
+    L.a_off = 0;                                              // [2] x 128 x K FP16 (SW128)
+    L.p_off = L.a_off + 2u * 128 * K * 2;                     // TY x K FP16 (SW128)
+    L.patch_off = L.p_off + (uint32_t)TY * K * 2;             // TY x PWs FP32
+    L.desc_off = (L.patch_off + (uint32_t)TY * (round_up(PW, 8) + 4) * 4 + 127) & ~127u;
+    L.bar_off = L.desc_off + kDescBytes;
+    L.misc_off = L.bar_off + 16 * 8;
+    L.total = L.misc_off + 64;
+    return L;
+}
+
+__device__ __forceinline__ RowItem row_item_mt(const TcBankArgs &a, const TcDesc &d, int it)
+{
+    const int g = it / a.row_cnt, local = it - g * a.row_cnt;
+    return RowItem{d.forder[g], a.row_y0 + (local / a.row_nx) * a.row_ty, (local % a.row_nx) * kMtTileX};
+}
+
+__global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_constant__ TcBankArgs a)
+{
+    const int nitems = a.nf * a.row_cnt;
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int TY = a.row_ty;
+    const MtSmem L = mt_smem(a.row_kmax, a.row_pwmax, TY);
+    unsigned char *sA = sm + L.a_off;
+    unsigned char *sP = sm + L.p_off;
+    float *patch = reinterpret_cast<float *>(sm + L.patch_off);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.bar_off);
+    uint64_t *tmem_full = bars;        // [2] commit
+    uint64_t *tmem_empty = bars + 2;   // [2] epilogue warps
+    uint64_t *a_full = bars + 4;       // [2] Am landed (bulk copy)
+    uint64_t *a_empty = bars + 6;      // [2] commit: the MMA reading the buffer is done
+    uint64_t *p_empty = bars + 8;      // [1] commit: the item's MMAs (reading P) are done
+    uint64_t *drain = bars + 9;
+    uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
+    volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
+    const TcDesc D = load_desc(a, sm + L.desc_off);
+    const uint32_t abuf = 128u * a.row_kmax * 2;
+
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&tmem_full[i], 1);
+            mbar_init(&tmem_empty[i], kMtEpiWarps);
+            mbar_init(&a_full[i], 1);
+            mbar_init(&a_empty[i], 1);
+        }
+        mbar_init(p_empty, 1);
+        mbar_init(drain, 1);
+        *abort_s = 0;
+        mbar_fence_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_s, 128);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_s;
+    const uint32_t idesc = idesc_f16(0, 128, TY);
+    float cen;
+    int e;
+    image_centre(a, cen, e);
+
+    if (warp >= kMtEpiWarps) {
+        // -------------------------------------------------------------- producers
+        constexpr int NP = 32 * (16 - kMtEpiWarps);
+        const int ptid = tid - 32 * kMtEpiWarps, pwarp = warp - kMtEpiWarps;
+        const float sc = ldexpf(1.f, -e);
+        int job = 0, nitem = 0;
+        int a_issued = 0, a_landed = 0;   // ptid 0: Am copies issued / waited for
+        bool ok = true;
+        for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++nitem) {
+            if (named_barrier_or(1, NP, *abort_s != 0)) break;
+            const RowItem w = row_item_mt(a, D, it);
+            const int s = w.s, y0 = w.y0, x0 = w.x0;
+            const TcFreqDev f = D.freqs[s];
+            const int R = f.R, K = f.Kmt;
+            const int ncols = kMtTileX + 2 * R, PW = round_up(ncols, 4);
+            const int PWs = round_up(PW, 8) + 4;
+            const int u0 = f.u0, nu = a.nu_f;
+            // P (and the staged patch) are free once the previous item's MMAs are done
+            bool failed = nitem > 0 && !mbar_wait(p_empty, (nitem - 1) & 1, abort_s);
+            if (named_barrier_or(1, NP, failed)) {
+                if (ptid == 0) fail_status(a.status, abort_s, 26);
+                break;
+            }
+            // patch rows y0 .. y0 + TY - 1, columns x0 - R .. x0 + 63 + R
+            if (a.bmode == kBoundaryZero) {
+                for (int r = pwarp; r < TY; r += NP / 32) {
+                    const int y = y0 + r;
+                    const bool yin = y >= 0 && y < a.H;
+                    const float *src = a.img + (int64_t)(yin ? y : 0) * a.pitch;
+                    for (int c = lane; c < PW; c += 32) {
+                        const int gx = x0 - R + c;
+                        const bool in = yin && c < ncols && gx >= 0 && gx < a.W;
+                        cp_async4(patch + r * PWs + c, in ? (const void *)(src + gx) : (const void *)a.img, in ? 4 : 0);
+                    }
+                }
+            } else {
+                for (int r = pwarp; r < TY; r += NP / 32) {
+                    const float *src = a.img + (int64_t)ext_coord(y0 + r, a.H, a.bmode) * a.pitch;
+                    for (int c = lane; c < PW; c += 32) {
+                        const bool in = c < ncols;
+                        cp_async4(patch + r * PWs + c,
+                                  in ? (const void *)(src + ext_coord(x0 - R + c, a.W, a.bmode)) : (const void *)a.img,
+                                  in ? 4 : 0);
+                    }
+                }
+            }
+            cp_async_commit();
+            cp_async_wait<0>();
+            named_barrier(1, NP);
+            // P[r][k] = (f - c) 2^-e in FP16 (zero outside the image under the zero rule and
+            // beyond the window), 8 k per 16-byte chunk of the swizzled K-major layout
+            for (int idx = ptid; idx < TY * (K / 8); idx += NP) {
+                const int r = idx % TY, k0 = 8 * (idx / TY);
+                const int y = y0 + r;
+                const bool yok = a.bmode != kBoundaryZero || (y >= 0 && y < a.H);
+                float v[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int k = k0 + t, gx = x0 - R + k;
+                    const bool in = yok && k < ncols && (a.bmode != kBoundaryZero || (gx >= 0 && gx < a.W));
+                    v[t] = in ? (patch[r * PWs + k] - cen) * sc : 0.f;
+                }
+                *reinterpret_cast<uint4 *>(sP + sw128_offset(TY, r, k0)) =
+                    make_uint4(h2pack(v[0], v[1]), h2pack(v[2], v[3]), h2pack(v[4], v[5]), h2pack(v[6], v[7]));
+            }
+            fence_proxy_async_smem();
+            named_barrier(1, NP);
+            if (ptid == 0) {
+                const uint32_t abytes = 128u * K * 2;
+                // Am of unit q into buffer (job + q) & 1 once the MMA that last read it is done
+                auto issue_a = [&](int q) {
+                    const int jq = job + q, buf = jq & 1;
+                    if (jq >= 2 && !mbar_wait(&a_empty[buf], ((jq - 2) >> 1) & 1, abort_s)) return false;
+                    mbar_arrive_expect_tx(&a_full[buf], abytes);
+                    bulk_load(smem_u32(sA + buf * abuf), D.units[u0 + q].Am, abytes, &a_full[buf]);
+                    ++a_issued;
+                    return true;
+                };
+                for (int q = 0; q < nu && q < 2 && ok; ++q) ok = issue_a(q);
+                for (int q = 0; q < nu && ok; ++q) {
+                    const int jq = job + q, b = jq & 1;
+                    ok = mbar_wait(&a_full[b], (jq >> 1) & 1, abort_s);
+                    if (ok) a_landed = jq + 1;   // copy jq (copies go in job order)
+                    if (ok && jq >= 2) ok = mbar_wait(&tmem_empty[b], ((jq - 2) >> 1) & 1, abort_s);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + b * abuf), p0 = smem_u32(sP);
+                    for (int kb = 0; kb < K / 64; ++kb)
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            tc_mma_f16(tmem + (uint32_t)TY * b, smem_desc_sw128(a0 + kb * 128 * 128) + 2 * kk,
+                                       smem_desc_sw128(p0 + kb * TY * 128) + 2 * kk, idesc, (kb | kk) != 0);
+                    tc_commit(&tmem_full[b]);
+                    tc_commit(&a_empty[b]);
+                    if (q + 2 < nu) ok = issue_a(q + 2);
+                }
+                tc_commit(p_empty);
+                if (!ok) fail_status(a.status, abort_s, 27);
+            }
+            job += nu;
+        }
+        if (ptid == 0) {
+            tc_commit(drain);
+            if (!mbar_wait(drain, 0, abort_s)) {
+                volatile int dummy = 0;
+                mbar_wait(drain, 0, &dummy);
+            }
+            // bulk copies issued but not waited for (after an abort) land before shared memory
+            // is released; copy i went to buffer i & 1 as its (i >> 1)-th use
+            for (int i = a_landed; i < a_issued; ++i) {
+                volatile int dummy = 0;
+                mbar_wait(&a_full[i & 1], (i >> 1) & 1, &dummy);
+            }
+        }
+    } else {
+        // -------------------------------------------------------------- epilogue
+        // TMEM lane n = 2 x + part: warp w reads quarter w & 3 (columns 16 (w & 3) .. + 15) and
+        // rows [rbase, rbase + TY / 2); lanes with part 0 store the theta signals of Eq. 10,
+        // lanes with part 1 those of pi - theta (Eq. 15-16).
+        const int quarter = warp & 3, half = warp >> 2;
+        const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+        const int rpw = TY / 2, rbase = half * rpw;
+        const int part = lane & 1, xl = 16 * quarter + (lane >> 1);
+        int job = 0;
+        for (int it = blockIdx.x; it < nitems && !*abort_s; it += gridDim.x) {
+            const RowItem w = row_item_mt(a, D, it);
+            const int y0 = w.y0;
+            const TcFreqDev f = D.freqs[w.s];
+            const float unscale = ldexpf(f.unscale_row, e);
+            const int gx = w.x0 + xl;
+            const bool xin = gx < a.W;
+            const int u0 = f.u0, nu = a.nu_f;
+            bool ok = true;
+            for (int q = 0; q < nu; ++q, ++job) {
+                const TcUnitDev u = D.units[u0 + q];
+                const int b = job & 1;
+                // row phases: lane l < rpw holds row rbase + l (broadcast by shuffle)
+                const int yl = y0 + rbase + lane;
+                const bool yok = a.bmode != kBoundaryZero || yl < a.H;
+                const float2 pyl = (lane < rpw && yok) ? __ldg(&u.phy[yl]) : make_float2(0.f, 0.f);
+                if (!mbar_wait(&tmem_full[b], (job >> 1) & 1, abort_s)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const bool paired = u.plane_b >= 0;
+                const int64_t sstride = (int64_t)a.W * a.Hp;   // between signals of the unit
+                const int64_t bstride = (int64_t)a.W * 8;      // between 8-row blocks
+                uint16_t *dst0 = a.sig + (u.sig_idx + 2 * part) * sstride + (int64_t)((a.Lpad + y0) >> 3) * bstride +
+                                 (int64_t)(xin ? gx : 0) * 8;
+                const bool store = xin && (part == 0 || paired);
+#pragma unroll 1
+                for (int c0 = rbase; c0 < rbase + rpw; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + lane_base + (uint32_t)TY * b + c0, v);
+                    uint32_t pk[2][2][4];   // [signal of the pair][8-row block][row pair]
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float own = v[j] * unscale;
+                        const float other = __shfl_xor_sync(0xffffffffu, own, 1);
+                        const float jr = part ? other : own, ji = part ? own : other;
+                        const int rl = c0 + j - rbase;
+                        const float2 cy = make_float2(__shfl_sync(0xffffffffu, pyl.x, rl),
+                                                      __shfl_sync(0xffffffffu, pyl.y, rl));
+                        // Eq. 10 (theta) or Eq. 15-16 (pi - theta)
+                        const float fcr = jr * cy.x, fsr = jr * cy.y, fci = ji * cy.x, fsi = ji * cy.y;
+                        const float sa = part ? fcr - fsi : fcr + fsi;
+                        const float sb = part ? fsr + fci : fsr - fci;
+                        // pack rows j (low half) and j + 1 (high half) of each signal
+                        if (j & 1) {
+                            pk[0][j >> 3][(j & 7) >> 1] |= (uint32_t)__half_as_ushort(__float2half_rn(sa)) << 16;
+                            pk[1][j >> 3][(j & 7) >> 1] |= (uint32_t)__half_as_ushort(__float2half_rn(sb)) << 16;
+                        } else {
+                            pk[0][j >> 3][(j & 7) >> 1] = __half_as_ushort(__float2half_rn(sa));
+                            pk[1][j >> 3][(j & 7) >> 1] = __half_as_ushort(__float2half_rn(sb));
+                        }
+                    }
+                    if (store) {
+#pragma unroll
+                        for (int blk = 0; blk < 2; ++blk) {
+                            uint16_t *d = dst0 + (int64_t)((c0 + 8 * blk) >> 3) * bstride;
+                            *reinterpret_cast<uint4 *>(d) = make_uint4(pk[0][blk][0], pk[0][blk][1], pk[0][blk][2], pk[0][blk][3]);
+                            *reinterpret_cast<uint4 *>(d + sstride) =
+                                make_uint4(pk[1][blk][0], pk[1][blk][1], pk[1][blk][2], pk[1][blk][3]);
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tmem_empty[b]);
+            }
+            if (!ok) {
+                if (lane == 0) fail_status(a.status, abort_s, 28);
+                break;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+// Am of one unit: rows n = 2 x + (0 | 1), x < 64, Am[n][k] = S(d) (cos, -sin)(w^c d) 2^sB,
+// d = k - x - R, zero outside |d| <= R; FP64, rounded to FP16, K-major SW128.
+__global__ void k_build_mtoeplitz(uint16_t *__restrict__ A, int K, int R, double sigma, double wc, int sB)
+{
+    const int n = 128 * K;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int row = i / K, k = i % K;
+        const int x = row >> 1, part = row & 1;
+        const int d = k - x - R;
+        double v = 0.0;
+        if (d >= -R && d <= R) {
+            const double g = exp(-(double)d * d / (2.0 * sigma * sigma)) / (2.5066282746310002 * sigma);
+            v = ldexp(part ? -g * sin(wc * d) : g * cos(wc * d), sB);
+        }
+        A[sw128_offset(128, row, k) / 2] = __half_as_ushort(__float2half_rn((float)v));
+    }
+}
+
 // --------------------------------------------------------------------------- column pass
 // Items: (unit, x0, y0), sorted by frequency; paired units take 32 columns x 4 signals,
 // unpaired ones 64 columns x 2 signals (always 128 A rows).  One producer warp keeps NST - 1
@@ -889,6 +1198,25 @@ int gabor_tc_row_tile_y(int Rmax)
 }
 int gabor_tc_col_tile_y() { return kColTileY; }
 
+int gabor_tc_mt_tile_x() { return kMtTileX; }
+int gabor_tc_mt_k(int R) { return round_up(kMtTileX + 2 * R, 64); }
+int gabor_tc_mt_pw(int R) { return round_up(kMtTileX + 2 * R, 4); }
+size_t gabor_tc_smem_rows_mt(int Kmax, int PWmax, int TY) { return 1024 + mt_smem(Kmax, PWmax, TY).total; }
+int gabor_tc_mt_tile_y(int Kmax, int PWmax)
+{
+    return gabor_tc_smem_rows_mt(Kmax, PWmax, 64) <= (size_t)kSmemLimit ? 64 : 32;
+}
+
+cudaError_t build_gabor_tc_am(uint16_t *Am, int R, double sigma, double wc, cudaStream_t st)
+{
+    // the scale of the frequency's Toeplitz operands: |S(d) cos|, |S(d) sin| <= S(0)
+    int e = 0;
+    frexp(1.0 / (2.5066282746310002 * sigma), &e);
+    const int K = gabor_tc_mt_k(R);
+    k_build_mtoeplitz<<<(128 * K + 255) / 256, 256, 0, st>>>(Am, K, R, sigma, wc, -e);
+    return cudaGetLastError();
+}
+
 cudaError_t build_gabor_tc_b(uint16_t *Brow, uint16_t *Bcol, int R, double sigma, int bf16, float *unscale,
                              cudaStream_t st)
 {
@@ -917,6 +1245,7 @@ cudaError_t build_gabor_tc_prefix(const double *unit_w, const TcUnitDev *units, 
 cudaError_t gabor_tc_prepare()
 {
     cudaError_t e = cudaFuncSetAttribute(k_gabor_tc_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gabor_tc_rows_mt, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gabor_tc_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     return e;
 }
@@ -927,7 +1256,8 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
     a.col_nst = col_stages(a.col_kmax);
     if (a.col_nst < 2) return cudaErrorInvalidValue;
     const int n_row_items = a.nf * a.row_cnt, n_col_items = a.nf * a.col_cnt;
-    const size_t smem_r = gabor_tc_smem_rows(a.row_kmax, a.row_pwmax, a.row_ty);
+    const size_t smem_r = a.row_mt ? gabor_tc_smem_rows_mt(a.row_kmax, a.row_pwmax, a.row_ty)
+                                   : gabor_tc_smem_rows(a.row_kmax, a.row_pwmax, a.row_ty);
     const size_t smem_c = gabor_tc_smem_cols(a.col_kmax);
     cudaError_t e0 = cudaMemsetAsync(a.minmax, 0, 2 * sizeof(unsigned), st);
     if (e0 != cudaSuccess) return e0;
@@ -945,7 +1275,10 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
         if (e0 != cudaSuccess) return e0;
     }
     if (n_row_items > 0) {
-        k_gabor_tc_rows<<<std::min(n_row_items, sm_count), 512, smem_r, st>>>(a);
+        if (a.row_mt)
+            k_gabor_tc_rows_mt<<<std::min(n_row_items, sm_count), 512, smem_r, st>>>(a);
+        else
+            k_gabor_tc_rows<<<std::min(n_row_items, sm_count), 512, smem_r, st>>>(a);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

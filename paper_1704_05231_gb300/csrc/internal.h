@@ -117,12 +117,14 @@ struct TcFreqDev {
     const uint16_t *Bcol;  // [64][Kcol] Toeplitz S(l - y - R8)
     int R, R8, Krow, Kcol;
     float unscale_row, unscale_col;   // 2^-sB of the B operands
-    int u0, pad_;          // first unit of the frequency
+    int u0;                // first unit of the frequency
+    int Kmt;               // K of the modulated-tap row pass: 64 + 2R rounded to 64
 };
 struct TcUnitDev {
     const float2 *phx, *phy;
     int s, plane_a, plane_b, pad_;
     int64_t sig_idx;       // first signal of the unit; its block starts at sig_idx * W * Hp
+    const uint16_t *Am;    // modulated-tap row operand [128][Kmt] (FP16, K-major SW128)
 };
 struct TcBankArgs {
     const float *img;
@@ -156,7 +158,7 @@ struct TcBankArgs {
     int layout;            // 0: out[plane][y][x], 1: out[y][x][plane]
     int nplanes;           // n_freq * n_theta
     int row_y0;            // first image row of the row pass (< 0: halo rows for non-zero rules)
-    int pad2_;
+    int row_mt;            // 1: the modulated-tap row kernel (64-column tiles)
     // TMA maps of the intermediate (dimensions 8 rows of a block x W x signals x Hp / 8 blocks,
     // FP16, no swizzle) for the column pass's A operand: boxes of 8 x 32 columns x 4 signals x
     // 8 blocks (paired units) and 8 x 64 x 2 x 8 (unpaired units)
@@ -242,6 +244,13 @@ cudaError_t launch_transpose(const float *src, int64_t pitch, int H, int W, floa
 // Tensor-core bank.
 TcGeometry gabor_tc_geometry(int R);
 bool gabor_tc_supported(int R);
+// Modulated-tap row pass: tile geometry and the per-unit operand builder.
+int gabor_tc_mt_tile_x();
+int gabor_tc_mt_k(int R);
+int gabor_tc_mt_pw(int R);
+int gabor_tc_mt_tile_y(int Kmax, int PWmax);
+size_t gabor_tc_smem_rows_mt(int Kmax, int PWmax, int TY);
+cudaError_t build_gabor_tc_am(uint16_t *Am, int R, double sigma, double wc, cudaStream_t st);
 cudaError_t build_gabor_tc_b(uint16_t *Brow, uint16_t *Bcol, int R, double sigma, int bf16, float *unscale,
                              cudaStream_t st);
 cudaError_t gabor_tc_prepare();
@@ -330,6 +339,7 @@ struct gabor_bank {
     int sdftB_Mx = 0, sdftB_My = 0;
     // tensor-core bank: B operands per frequency, unit descriptors, intermediate signals
     uint16_t *d_tcB = nullptr;
+    uint16_t *d_tcAm = nullptr;               // modulated-tap row operands, one per unit
     gb::TcFreqDev *d_tcfreq = nullptr;
     gb::TcUnitDev *d_tcunit = nullptr;
     uint16_t *d_tcsig = nullptr;    // library-owned intermediate (when no workspace is attached)
@@ -344,6 +354,7 @@ struct gabor_bank {
     double2 *d_tcpre = nullptr;       // prefix sums of the kernel taps per unit (F[1] tables)
     int tc_pre_stride = 0;
     int tc_row_ty = 64;
+    int tc_mt_kmax = 0, tc_mt_pwmax = 0, tc_mt_ty = 64;   // modulated-tap row pass geometry
     int tc_H = 0, tc_W = 0, tc_Lpad = 0;
     int64_t tc_Hp = 0;
     bool tc_ready = false;

@@ -360,3 +360,22 @@ def test_c2_full_size_tuned_geometry_bitwise(torch_cuda):
         got = gbk.filter(img).cpu().numpy()
         gbk.device_status()
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("row_pass", [1, 2])
+@pytest.mark.parametrize("boundary", ["zero", "mirror"])
+@pytest.mark.parametrize("H,W", [(37, 75), (160, 200), (129, 33)])
+def test_tc_bank_row_pass_forms(torch_cuda, row_pass, boundary, H, W):
+    # Tensor-core bank: row pass as demodulated operand x Toeplitz (1) or modulated-tap operand
+    # x patch (2); both within the tensor-core bound of the FP64 oracle.
+    from paper_1704_05231_gb300 import GaborBank
+    from tests.helpers import TC_TOL
+    img = synth.paper_like([43, H, W], H, W)
+    th, om, sg = c2_bank()
+    with GaborBank(th, om, sg, precision="fp16_tc", boundary=boundary) as gbk:
+        gbk.set_option("row_pass", row_pass)
+        got = gbk.filter(torch_cuda.from_numpy(img).cuda()).cpu().numpy()
+        gbk.device_status()
+    e = rel_err(got, oracle.gabor_bank(img, th, om, sg, boundary=boundary))
+    print("TC row pass", row_pass, boundary, H, W, "rel err", e)
+    assert e <= TC_TOL
