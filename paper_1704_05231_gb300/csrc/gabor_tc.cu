@@ -601,22 +601,11 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
         int job = 0, nitem = 0;
         int a_issued = 0, a_landed = 0;   // ptid 0: Am copies issued / waited for
         bool ok = true;
-        for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++nitem) {
-            if (named_barrier_or(1, NP, *abort_s != 0)) break;
+        // cp.async of item it's patch: rows y0 .. y0 + TY - 1, columns x0 - R .. x0 + 63 + R
+        auto stage = [&](int it) {
             const RowItem w = row_item_mt(a, D, it);
-            const int s = w.s, y0 = w.y0, x0 = w.x0;
-            const TcFreqDev f = D.freqs[s];
-            const int R = f.R, K = f.Kmt;
-            const int ncols = kMtTileX + 2 * R, PW = round_up(ncols, 4);
-            const int PWs = round_up(PW, 8) + 4;
-            const int u0 = f.u0, nu = a.nu_f;
-            // P (and the staged patch) are free once the previous item's MMAs are done
-            bool failed = nitem > 0 && !mbar_wait(p_empty, (nitem - 1) & 1, abort_s);
-            if (named_barrier_or(1, NP, failed)) {
-                if (ptid == 0) fail_status(a.status, abort_s, 26);
-                break;
-            }
-            // patch rows y0 .. y0 + TY - 1, columns x0 - R .. x0 + 63 + R
+            const int R = D.freqs[w.s].R, y0 = w.y0, x0 = w.x0;
+            const int ncols = kMtTileX + 2 * R, PW = round_up(ncols, 4), PWs = round_up(PW, 8) + 4;
             if (a.bmode == kBoundaryZero) {
                 for (int r = pwarp; r < TY; r += NP / 32) {
                     const int y = y0 + r;
@@ -640,7 +629,24 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
                 }
             }
             cp_async_commit();
-            cp_async_wait<0>();
+        };
+        if ((int)blockIdx.x < nitems) stage(blockIdx.x);
+        for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++nitem) {
+            if (named_barrier_or(1, NP, *abort_s != 0)) break;
+            const RowItem w = row_item_mt(a, D, it);
+            const int s = w.s, y0 = w.y0, x0 = w.x0;
+            const TcFreqDev f = D.freqs[s];
+            const int R = f.R, K = f.Kmt;
+            const int ncols = kMtTileX + 2 * R, PW = round_up(ncols, 4);
+            const int PWs = round_up(PW, 8) + 4;
+            const int u0 = f.u0, nu = a.nu_f;
+            // P is free once the previous item's MMAs are done
+            bool failed = nitem > 0 && !mbar_wait(p_empty, (nitem - 1) & 1, abort_s);
+            if (named_barrier_or(1, NP, failed)) {
+                if (ptid == 0) fail_status(a.status, abort_s, 26);
+                break;
+            }
+            cp_async_wait<0>();   // this item's patch (staged during the previous item)
             named_barrier(1, NP);
             // P[r][k] = (f - c) 2^-e in FP16 (zero outside the image under the zero rule and
             // beyond the window), 8 k per 16-byte chunk of the swizzled K-major layout
@@ -659,7 +665,8 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
                     make_uint4(h2pack(v[0], v[1]), h2pack(v[2], v[3]), h2pack(v[4], v[5]), h2pack(v[6], v[7]));
             }
             fence_proxy_async_smem();
-            named_barrier(1, NP);
+            named_barrier(1, NP);   // the FP32 patch is free: stage the next item's
+            if (it + (int)gridDim.x < nitems) stage(it + gridDim.x);
             if (ptid == 0) {
                 const uint32_t abytes = 128u * K * 2;
                 // Am of unit q into buffer (job + q) & 1 once the MMA that last read it is done
@@ -694,6 +701,7 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
             }
             job += nu;
         }
+        cp_async_wait<0>();   // a patch staged before a stop lands before shared memory is released
         if (ptid == 0) {
             tc_commit(drain);
             if (!mbar_wait(drain, 0, abort_s)) {
@@ -750,25 +758,24 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
                     tmem_ld16(tmem + lane_base + (uint32_t)TY * b + c0, v);
                     uint32_t pk[2][2][4];   // [signal of the pair][8-row block][row pair]
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float own = v[j] * unscale;
-                        const float other = __shfl_xor_sync(0xffffffffu, own, 1);
-                        const float jr = part ? other : own, ji = part ? own : other;
-                        const int rl = c0 + j - rbase;
-                        const float2 cy = make_float2(__shfl_sync(0xffffffffu, pyl.x, rl),
-                                                      __shfl_sync(0xffffffffu, pyl.y, rl));
-                        // Eq. 10 (theta) or Eq. 15-16 (pi - theta)
-                        const float fcr = jr * cy.x, fsr = jr * cy.y, fci = ji * cy.x, fsi = ji * cy.y;
-                        const float sa = part ? fcr - fsi : fcr + fsi;
-                        const float sb = part ? fsr + fci : fsr - fci;
-                        // pack rows j (low half) and j + 1 (high half) of each signal
-                        if (j & 1) {
-                            pk[0][j >> 3][(j & 7) >> 1] |= (uint32_t)__half_as_ushort(__float2half_rn(sa)) << 16;
-                            pk[1][j >> 3][(j & 7) >> 1] |= (uint32_t)__half_as_ushort(__float2half_rn(sb)) << 16;
-                        } else {
-                            pk[0][j >> 3][(j & 7) >> 1] = __half_as_ushort(__float2half_rn(sa));
-                            pk[1][j >> 3][(j & 7) >> 1] = __half_as_ushort(__float2half_rn(sb));
+                    for (int j = 0; j < 16; j += 2) {
+                        float sa[2], sb[2];
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) {
+                            const float own = v[j + t] * unscale;
+                            const float other = __shfl_xor_sync(0xffffffffu, own, 1);
+                            const float jr = part ? other : own, ji = part ? own : other;
+                            const int rl = c0 + j + t - rbase;
+                            const float2 cy = make_float2(__shfl_sync(0xffffffffu, pyl.x, rl),
+                                                          __shfl_sync(0xffffffffu, pyl.y, rl));
+                            // Eq. 10 (theta) or Eq. 15-16 (pi - theta)
+                            const float fcr = jr * cy.x, fsr = jr * cy.y, fci = ji * cy.x, fsi = ji * cy.y;
+                            sa[t] = part ? fcr - fsi : fcr + fsi;
+                            sb[t] = part ? fsr + fci : fsr - fci;
                         }
+                        // rows j (low half) and j + 1 (high half) of each signal
+                        pk[0][j >> 3][(j & 7) >> 1] = h2pack(sa[0], sa[1]);
+                        pk[1][j >> 3][(j & 7) >> 1] = h2pack(sb[0], sb[1]);
                     }
                     if (store) {
 #pragma unroll
