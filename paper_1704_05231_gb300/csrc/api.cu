@@ -460,6 +460,7 @@ void free_tc(gabor_bank *h)
 {
     dfree(h->d_tcB);
     dfree(h->d_tcAm);
+    dfree(h->d_tcGm);
     dfree(h->d_tcfreq);
     dfree(h->d_tcunit);
     dfree(h->d_tcsig);
@@ -551,10 +552,19 @@ gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
         h->tc_mt_pwmax = std::max(h->tc_mt_pwmax, gabor_tc_mt_pw(R));
     }
     h->tc_mt_ty = gabor_tc_mt_tile_y(h->tc_mt_kmax, h->tc_mt_pwmax);
+    h->tc_mt_ok = gabor_tc_mt_fits(h->tc_mt_kmax, h->tc_mt_pwmax, h->tc_col_kmax);
     GB_TRY(dalloc(&h->d_tcAm, std::max<size_t>(am_total, 1)));
+    std::vector<size_t> off_gm(nu);
+    size_t gm_total = 0;
+    for (int i = 0; i < nu; ++i) {
+        off_gm[i] = gm_total;
+        gm_total += (size_t)128 * gabor_tc_geometry(h->freqs[h->units[i].s].R).Kcol;
+    }
+    GB_TRY(dalloc(&h->d_tcGm, std::max<size_t>(gm_total, 1)));
     for (int i = 0; i < nu; ++i) {
         const Freq &fq = h->freqs[h->units[i].s];
         GB_CU(build_gabor_tc_am(h->d_tcAm + off_am[i], fq.R, fq.sigma, h->units[i].wc, st));
+        GB_CU(build_gabor_tc_gm(h->d_tcGm + off_gm[i], fq.R, fq.sigma, h->units[i].ws, st));
     }
     std::vector<TcUnitDev> ud(nu);
     const int K = (int)h->theta.size();
@@ -570,6 +580,7 @@ gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
         ud[i].pad_ = 0;
         ud[i].sig_idx = sig;
         ud[i].Am = h->d_tcAm + off_am[i];
+        ud[i].Gm = h->d_tcGm + off_gm[i];
         sig += paired ? 4 : 2;
     }
     GB_CU(cudaMemcpy(h->d_tcfreq, fd.data(), nf * sizeof(TcFreqDev), cudaMemcpyHostToDevice));
@@ -603,7 +614,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 // tensor (8 rows of a block, W columns, signals, Hp / 8 blocks; FP16): boxes of 8 x 32 x 4 x 8
 // and 8 x 64 x 2 x 8, no swizzle (they land as the MMA's K-major core matrices), zeros beyond
 // the image width.
-gb_status encode_tc_maps(TcBankArgs &a, int nsig)
+gb_status encode_tc_maps(TcBankArgs &a, int nsig, bool mt)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return fail(GB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
@@ -611,6 +622,18 @@ gb_status encode_tc_maps(TcBankArgs &a, int nsig)
     const cuuint64_t strides[3] = {16, (cuuint64_t)a.Hp * a.W * 2, (cuuint64_t)a.W * 16};
     const cuuint32_t elem[4] = {1, 1, 1, 1};
     const cuuint32_t boxes[2][4] = {{8, 32, 4, 8}, {8, 64, 2, 8}};
+    if (mt) {
+        // modulated taps: Re J, Im J of a unit are signals 2 u, 2 u + 1; a box of 8 rows x the
+        // two parts x 64 columns x 8 blocks lands with operand row n = 2 x + part
+        const cuuint64_t mdims[4] = {8, (cuuint64_t)nsig, (cuuint64_t)a.W, (cuuint64_t)(a.Hp / 8)};
+        const cuuint64_t mstrides[3] = {(cuuint64_t)a.Hp * a.W * 2, 16, (cuuint64_t)a.W * 16};
+        const cuuint32_t mbox[4] = {8, 2, 64, 8};
+        const CUresult r = enc(&a.tmA[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, a.sig, mdims, mstrides, mbox, elem,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(GB_ERR_CUDA, "cuTensorMapEncodeTiled failed for the intermediate");
+        return GB_OK;
+    }
     for (int k = 0; k < 2; ++k) {
         const CUresult r = enc(&a.tmA[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, a.sig, dims, strides, boxes[k], elem,
                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -637,8 +660,9 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     GB_TRY(ensure_tables(h, H, W, st));
     if (tables_move) free_tc(h);
     GB_TRY(ensure_tc(h, st));
-    // row pass: modulated taps (64-column tiles) unless GB_OPT_ROW_PASS asks for the steps
-    const bool row_mt = h->fp32_row_form != 1;
+    // both passes with modulated taps (64-column row tiles, J as the intermediate) unless
+    // GB_OPT_ROW_PASS asks for the steps or a radius does not fit the kernels
+    const bool row_mt = h->fp32_row_form != 1 && h->tc_mt_ok;
     const int ty = row_mt ? h->tc_mt_ty : h->tc_row_ty;
     const int tile_x = row_mt ? gabor_tc_mt_tile_x() : gabor_tc_row_tile_x();
     // Non-zero boundary rules: the row pass also produces the halo rows [-R, 0) and
@@ -647,7 +671,8 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     for (const Freq &f : h->freqs) rmax = std::max(rmax, f.R);
     const int ypad = h->boundary == kBoundaryZero ? 0 : (rmax + ty - 1) / ty * ty;
     const int64_t row_cnt = (int64_t)((H + 2 * ypad + ty - 1) / ty) * ((W + tile_x - 1) / tile_x);
-    const int64_t col_cnt = ny64 * (h->tc_np_f * nx32 + (h->tc_nu_f - h->tc_np_f) * nx64);
+    const int64_t col_cnt = row_mt ? ny64 * h->tc_nu_f * nx64
+                                   : ny64 * (h->tc_np_f * nx32 + (h->tc_nu_f - h->tc_np_f) * nx64);
     if ((int64_t)nf * std::max(row_cnt, col_cnt) > (int64_t)1 << 30)
         return fail(GB_ERR_UNSUPPORTED, "image too large for the tensor-core bank");
     const int Lpad = tc_lpad(h);
@@ -722,7 +747,7 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.layout = h->layout;
     a.nplanes = (int)(h->omega.size() * h->theta.size());
     a.row_y0 = -ypad;
-    GB_TRY(encode_tc_maps(a, h->tc_nsig));
+    GB_TRY(encode_tc_maps(a, h->tc_nsig, row_mt));
     GB_CU(launch_gabor_tc(a, h->sm_count, st));
     return GB_OK;
 }

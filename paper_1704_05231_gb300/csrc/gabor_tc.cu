@@ -513,12 +513,11 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
 //   Am[(x, re)][k] = S(d) cos(w^c d),  Am[(x, im)][k] = -S(d) sin(w^c d),  d = k - x - R,
 //   P[r][k] = (f(y0 + r, x0 - R + k) - c) 2^-e
 //
-// -> Re J, Im J of 64 columns x TY rows of one unit.  Operand row n = 2 x + (0 | 1), so the
-// two parts of a column sit in adjacent TMEM lanes and meet by shuffle.  Per item (frequency,
-// tile): producers (warps 8-15) stage the patch once and convert it to the FP16 operand P; the
-// MMA thread (256) brings each unit's Am (built once per plan) by one bulk copy into one of two
-// buffers and issues the MMA; 8 epilogue warps (two per lane quarter) form the column signals
-// of Eq. 10 and store them to the intermediate like the step-by-step kernel.
+// -> Re J, Im J of 64 columns x TY rows of one unit (operand row n = 2 x + re|im).  Per item
+// (frequency, tile): producers (warps 8-15) stage the patch once and convert it to the FP16
+// operand P; the MMA thread (256) brings each unit's Am (built once per plan) by one bulk copy
+// into one of two buffers and issues the MMA; 8 epilogue warps (two per lane quarter) store J
+// itself, two signals per unit, for the modulated-tap column pass.
 constexpr int kMtTileX = 64;     // output columns per item (MMA M = 2 x 64)
 constexpr int kMtEpiWarps = 8;
 
@@ -718,8 +717,8 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
     } else {
         // -------------------------------------------------------------- epilogue
         // TMEM lane n = 2 x + part: warp w reads quarter w & 3 (columns 16 (w & 3) .. + 15) and
-        // rows [rbase, rbase + TY / 2); lanes with part 0 store the theta signals of Eq. 10,
-        // lanes with part 1 those of pi - theta (Eq. 15-16).
+        // rows [rbase, rbase + TY / 2), and stores its part of J (signal 2 unit + part of the
+        // intermediate; the column pass demodulates nothing, its taps are modulated too).
         const int quarter = warp & 3, half = warp >> 2;
         const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
         const int rpw = TY / 2, rbase = half * rpw;
@@ -735,56 +734,28 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
             const int u0 = f.u0, nu = a.nu_f;
             bool ok = true;
             for (int q = 0; q < nu; ++q, ++job) {
-                const TcUnitDev u = D.units[u0 + q];
                 const int b = job & 1;
-                // row phases: lane l < rpw holds row rbase + l (broadcast by shuffle)
-                const int yl = y0 + rbase + lane;
-                const bool yok = a.bmode != kBoundaryZero || yl < a.H;
-                const float2 pyl = (lane < rpw && yok) ? __ldg(&u.phy[yl]) : make_float2(0.f, 0.f);
                 if (!mbar_wait(&tmem_full[b], (job >> 1) & 1, abort_s)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const bool paired = u.plane_b >= 0;
-                const int64_t sstride = (int64_t)a.W * a.Hp;   // between signals of the unit
+                const int64_t sstride = (int64_t)a.W * a.Hp;   // between signals
                 const int64_t bstride = (int64_t)a.W * 8;      // between 8-row blocks
-                uint16_t *dst0 = a.sig + (u.sig_idx + 2 * part) * sstride + (int64_t)((a.Lpad + y0) >> 3) * bstride +
-                                 (int64_t)(xin ? gx : 0) * 8;
-                const bool store = xin && (part == 0 || paired);
+                uint16_t *dst0 = a.sig + (int64_t)(2 * (u0 + q) + part) * sstride +
+                                 (int64_t)((a.Lpad + y0) >> 3) * bstride + (int64_t)(xin ? gx : 0) * 8;
 #pragma unroll 1
                 for (int c0 = rbase; c0 < rbase + rpw; c0 += 16) {
                     float v[16];
                     tmem_ld16(tmem + lane_base + (uint32_t)TY * b + c0, v);
-                    uint32_t pk[2][2][4];   // [signal of the pair][8-row block][row pair]
+                    uint32_t pk[2][4];   // [8-row block][row pair]
 #pragma unroll
-                    for (int j = 0; j < 16; j += 2) {
-                        float sa[2], sb[2];
+                    for (int j = 0; j < 16; j += 2) pk[j >> 3][(j & 7) >> 1] = h2pack(v[j] * unscale, v[j + 1] * unscale);
+                    if (xin) {
 #pragma unroll
-                        for (int t = 0; t < 2; ++t) {
-                            const float own = v[j + t] * unscale;
-                            const float other = __shfl_xor_sync(0xffffffffu, own, 1);
-                            const float jr = part ? other : own, ji = part ? own : other;
-                            const int rl = c0 + j + t - rbase;
-                            const float2 cy = make_float2(__shfl_sync(0xffffffffu, pyl.x, rl),
-                                                          __shfl_sync(0xffffffffu, pyl.y, rl));
-                            // Eq. 10 (theta) or Eq. 15-16 (pi - theta)
-                            const float fcr = jr * cy.x, fsr = jr * cy.y, fci = ji * cy.x, fsi = ji * cy.y;
-                            sa[t] = part ? fcr - fsi : fcr + fsi;
-                            sb[t] = part ? fsr + fci : fsr - fci;
-                        }
-                        // rows j (low half) and j + 1 (high half) of each signal
-                        pk[0][j >> 3][(j & 7) >> 1] = h2pack(sa[0], sa[1]);
-                        pk[1][j >> 3][(j & 7) >> 1] = h2pack(sb[0], sb[1]);
-                    }
-                    if (store) {
-#pragma unroll
-                        for (int blk = 0; blk < 2; ++blk) {
-                            uint16_t *d = dst0 + (int64_t)((c0 + 8 * blk) >> 3) * bstride;
-                            *reinterpret_cast<uint4 *>(d) = make_uint4(pk[0][blk][0], pk[0][blk][1], pk[0][blk][2], pk[0][blk][3]);
-                            *reinterpret_cast<uint4 *>(d + sstride) =
-                                make_uint4(pk[1][blk][0], pk[1][blk][1], pk[1][blk][2], pk[1][blk][3]);
-                        }
+                        for (int blk = 0; blk < 2; ++blk)
+                            *reinterpret_cast<uint4 *>(dst0 + (int64_t)((c0 + 8 * blk) >> 3) * bstride) =
+                                make_uint4(pk[blk][0], pk[blk][1], pk[blk][2], pk[blk][3]);
                     }
                 }
                 tc_fence_before();
@@ -818,6 +789,244 @@ __global__ void k_build_mtoeplitz(uint16_t *__restrict__ A, int K, int R, double
             v = ldexp(part ? -g * sin(wc * d) : g * cos(wc * d), sB);
         }
         A[sw128_offset(128, row, k) / 2] = __half_as_ushort(__float2half_rn((float)v));
+    }
+}
+
+// --------------------------------------------------------- column pass, modulated taps
+// With the modulated-tap row pass the intermediate holds J itself (Re J, Im J per unit) and
+// the column pass of Eq. 7-9 is one product with a per-unit operand of modulated taps,
+//   D[(x, re|im of J)][(y, re|im of G)] = sum_l J[(x, .)][l] Gm[(y, .)][l],
+//   Gm[(y, re)][l] = S(d) cos(w^s d),  Gm[(y, im)][l] = -S(d) sin(w^s d),  d = l - y - R8,
+// whose four real sums per (x, y) give F_theta = sum G J and F_{pi-theta} = sum G J*
+// (Eq. 13-16) with two additions each: no row phases at all.  Operand rows n = 2 x + part,
+// columns m = 2 y + part, so the sums of a column meet by one shuffle.  Items: (unit,
+// 64-column tile, 64-row tile).  One producer warp (lane 0) loads each job's J boxes by TMA and
+// its unit's Gm by one bulk copy, two jobs deep, and issues the MMAs into two TMEM
+// accumulators; 8 epilogue warps add the c A(x) B(y) correction and store complex64.
+constexpr int kMtColAcc = 2;       // TMEM accumulators (128 columns each)
+constexpr int kMtColThreads = 32 * (8 + 1);
+
+struct MtColSmem {
+    uint32_t a_off, b_off, desc_off, bar_off, misc_off, total;
+};
+
+__host__ __device__ inline MtColSmem mt_col_smem(int K)
+{
+    MtColSmem L;
+    L.a_off = 0;                                   // [2] x 128 x K (no swizzle, core matrices)
+    L.b_off = L.a_off + 2u * 128 * K * 2;          // [2] x 128 x K (SW128)
+    L.desc_off = L.b_off + 2u * 128 * K * 2;
+    L.bar_off = L.desc_off + kDescBytes;
+    L.misc_off = L.bar_off + 16 * 8;
+    L.total = L.misc_off + 64;
+    return L;
+}
+
+struct MtColItem {
+    int unit, x0, y0;
+};
+__device__ __forceinline__ MtColItem col_item_mt(const TcBankArgs &a, const TcDesc &d, int it)
+{
+    const int g = it / a.col_cnt, local = it - g * a.col_cnt;
+    const int per_unit = a.col_ny * a.col_nx64;
+    const int q = local / per_unit, rest = local - q * per_unit;
+    const TcFreqDev f = d.freqs[d.forder[g]];
+    return MtColItem{f.u0 + q, (rest % a.col_nx64) * 64, (rest / a.col_nx64) * kColTileY};
+}
+
+__global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __grid_constant__ TcBankArgs a)
+{
+    const int nitems = a.nf * a.col_cnt;
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const MtColSmem L = mt_col_smem(a.col_kmax);
+    unsigned char *sA = sm + L.a_off;
+    unsigned char *sB = sm + L.b_off;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.bar_off);
+    uint64_t *tmem_full = bars;            // [2] commit
+    uint64_t *tmem_empty = bars + 2;       // [2] 8 epilogue warps
+    uint64_t *ab_full = bars + 4;          // [2] TMA + bulk-copy bytes of a job's operands
+    uint64_t *ab_empty = bars + 6;         // [2] commit: the MMA reading the buffers is done
+    uint64_t *drain = bars + 8;
+    uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
+    volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
+    const uint32_t obuf = 128u * a.col_kmax * 2;
+    const TcDesc D = load_desc(a, sm + L.desc_off);
+    float cen;
+    int e_unused;
+    image_centre(a, cen, e_unused);
+
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&tmem_full[i], 1);
+            mbar_init(&tmem_empty[i], 8);
+            mbar_init(&ab_full[i], 1);
+            mbar_init(&ab_empty[i], 1);
+        }
+        mbar_init(drain, 1);
+        *abort_s = 0;
+        mbar_fence_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_s, 128 * kMtColAcc);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_s;
+    const uint32_t idesc = idesc_f16(0, 128, 128);
+    const int njobs = nitems > (int)blockIdx.x ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+    if (warp == 8) {
+        // -------------------------------------------------------------- producer (lane 0)
+        if (lane == 0) {
+            auto item = [&](int j) { return col_item_mt(a, D, blockIdx.x + j * gridDim.x); };
+            // job j's operands into buffers j & 1: J boxes (8 rows of a block x 2 parts x 64
+            // columns x 8 blocks, landing as K-major core matrices with operand row
+            // n = 2 x + part) and the unit's Gm (one bulk copy)
+            auto issue = [&](int j) {
+                const MtColItem w = item(j);
+                const TcUnitDev u = D.units[w.unit];
+                const TcFreqDev f = D.freqs[u.s];
+                const int st = j & 1;
+                const uint32_t bytes = 128u * f.Kcol * 2;
+                mbar_arrive_expect_tx(&ab_full[st], 2 * bytes);
+                const int yb0 = (a.Lpad + w.y0 - f.R8) >> 3;
+                const uint32_t dst = smem_u32(sA + st * obuf);
+                for (int kb = 0; kb < f.Kcol / 64; ++kb)
+                    tma_load_4d(dst + kb * 16384u, &a.tmA[0], 0, 2 * w.unit, w.x0, yb0 + 8 * kb, &ab_full[st]);
+                bulk_load(smem_u32(sB + st * obuf), u.Gm, bytes, &ab_full[st]);
+            };
+            int issued = 0, landed = 0;
+            for (; issued < 2 && issued < njobs; ++issued) issue(issued);
+            for (int j = 0; j < njobs; ++j) {
+                if (*abort_s) break;
+                const int st = j & 1, acc = j & 1;
+                const TcFreqDev f = D.freqs[D.units[item(j).unit].s];
+                if (!mbar_wait(&ab_full[st], (j >> 1) & 1, abort_s)) {
+                    fail_status(a.status, abort_s, 36);
+                    break;
+                }
+                landed = j + 1;
+                if (j >= kMtColAcc && !mbar_wait(&tmem_empty[acc], ((j - kMtColAcc) >> 1) & 1, abort_s)) {
+                    fail_status(a.status, abort_s, 37);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(sA + st * obuf), b0 = smem_u32(sB + st * obuf);
+                for (int kb = 0; kb < f.Kcol / 64; ++kb)
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        tc_mma_f16(tmem + 128u * acc, smem_desc_kmajor(a0 + kb * 16384 + kk * 4096, 2048, 128),
+                                   smem_desc_sw128(b0 + kb * 128 * 128) + 2 * kk, idesc, (kb | kk) != 0);
+                tc_commit(&tmem_full[acc]);
+                tc_commit(&ab_empty[st]);
+                // job j + 2 goes into these buffers once this MMA is done with them
+                if (j + 2 < njobs) {
+                    if (!mbar_wait(&ab_empty[st], (j >> 1) & 1, abort_s)) {
+                        fail_status(a.status, abort_s, 38);
+                        break;
+                    }
+                    issue(j + 2);
+                    issued = j + 3;
+                }
+            }
+            tc_commit(drain);
+            if (!mbar_wait(drain, 0, abort_s)) {
+                volatile int dummy = 0;
+                mbar_wait(drain, 0, &dummy);
+            }
+            // operands issued but not waited for (after a stop) land before shared memory is
+            // released
+            for (int jj = landed; jj < issued; ++jj) {
+                volatile int dummy = 0;
+                mbar_wait(&ab_full[jj & 1], (jj >> 1) & 1, &dummy);
+            }
+        }
+    } else {
+        // -------------------------------------------------------------- epilogue
+        // TMEM lane n = 2 x + part (part 0: Re J, 1: Im J), column m = 2 y + g (g 0: Re G,
+        // 1: Im G).  Warp w reads quarter w & 3 (columns x 16 (w & 3) .. + 15) and rows y
+        // 32 (w >> 2) .. + 31.  The part-0 lane of a column stores F_theta, the part-1 lane
+        // F_{pi - theta} (paired units).
+        const int quarter = warp & 3, half = warp >> 2;
+        const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+        const int part = lane & 1, xl = 16 * quarter + (lane >> 1);
+        for (int j = 0; j < njobs; ++j) {
+            const MtColItem w = col_item_mt(a, D, blockIdx.x + j * gridDim.x);
+            const TcUnitDev u = D.units[w.unit];
+            const TcFreqDev f = D.freqs[u.s];
+            const int acc = j & 1;
+            const bool paired = u.plane_b >= 0;
+            const int x = w.x0 + xl, ybase = w.y0 + 32 * half;
+            const bool xok = x < a.W;
+            // c B(y) of the warp's rows (lane l holds row ybase + l); A(x) of the lane's column
+            const int yl = ybase + lane;
+            const float2 byl = yl < a.H ? __ldg(&a.onesB[(int64_t)w.unit * a.H + yl]) : make_float2(0.f, 0.f);
+            const float2 ax = xok ? __ldg(&a.onesA[(int64_t)w.unit * a.W + x]) : make_float2(0.f, 0.f);
+            if (!mbar_wait(&tmem_full[acc], (j >> 1) & 1, abort_s)) {
+                if (lane == 0) fail_status(a.status, abort_s, 39);
+                break;
+            }
+            tc_fence_after();
+            const float unscale = f.unscale_col;
+            const bool store = xok && (part == 0 || paired);
+            const int plane = part ? u.plane_b : u.plane_a;
+            // correction c A(x) B(y) for theta, c conj(A(x)) B(y) for pi - theta
+            const float axi = part ? -ax.y : ax.y;
+#pragma unroll 1
+            for (int c0 = 0; c0 < 64; c0 += 16) {   // accumulator columns 64 half + c0 .. + 15
+                uint32_t r[16];
+                tmem_ld16_async(tmem + lane_base + 128u * acc + 64 * half + c0, r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const float gr = __uint_as_float(r[2 * t]) * unscale;       // sum Re G x (this part of J)
+                    const float gi = __uint_as_float(r[2 * t + 1]) * unscale;   // sum Im G x (this part of J)
+                    const float or_ = __shfl_xor_sync(0xffffffffu, gr, 1);
+                    const float oi = __shfl_xor_sync(0xffffffffu, gi, 1);
+                    // A = sum Re G Re J, B = sum Im G Im J, C = sum Im G Re J, D = sum Re G Im J
+                    const float A = part ? or_ : gr, C = part ? oi : gi;
+                    const float Dd = part ? gr : or_, B = part ? gi : oi;
+                    const int yr = (c0 >> 1) + t;                // row within the warp's 32
+                    const float cbr = cen * __shfl_sync(0xffffffffu, byl.x, yr);   // c B(y)
+                    const float cbi = cen * __shfl_sync(0xffffffffu, byl.y, yr);
+                    const int y = ybase + yr;
+                    // F_theta = sum G J = (A - B, C + D); F_{pi-theta} = sum G J* = (A + B, C - D)
+                    const float fr = part ? A + B : A - B, fi = part ? C - Dd : C + Dd;
+                    if (store && y < a.H)
+                        __stcs(a.out + tc_out_offset(a, plane, y, x),
+                               make_float2(fr + (ax.x * cbr - axi * cbi), fi + (ax.x * cbi + axi * cbr)));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tmem_empty[acc]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 128 * kMtColAcc);
+}
+
+// Gm of one unit: rows m = 2 y + (0 | 1), y < 64, Gm[m][l] = S(d) (cos, -sin)(w^s d) 2^sB,
+// d = l - y - R8, zero outside |d| <= R; FP64, rounded to FP16, K-major SW128.
+__global__ void k_build_mtoeplitz_col(uint16_t *__restrict__ G, int K, int R8, int R, double sigma, double ws, int sB)
+{
+    const int n = 128 * K;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int row = i / K, l = i % K;
+        const int y = row >> 1, part = row & 1;
+        const int d = l - y - R8;
+        double v = 0.0;
+        if (d >= -R && d <= R) {
+            const double g = exp(-(double)d * d / (2.0 * sigma * sigma)) / (2.5066282746310002 * sigma);
+            v = ldexp(part ? -g * sin(ws * d) : g * cos(ws * d), sB);
+        }
+        G[sw128_offset(128, row, l) / 2] = __half_as_ushort(__float2half_rn((float)v));
     }
 }
 
@@ -1214,6 +1423,21 @@ int gabor_tc_mt_tile_y(int Kmax, int PWmax)
     return gabor_tc_smem_rows_mt(Kmax, PWmax, 64) <= (size_t)kSmemLimit ? 64 : 32;
 }
 
+cudaError_t build_gabor_tc_gm(uint16_t *Gm, int R, double sigma, double ws, cudaStream_t st)
+{
+    int e = 0;
+    frexp(1.0 / (2.5066282746310002 * sigma), &e);
+    const TcGeometry g = gabor_tc_geometry(R);
+    k_build_mtoeplitz_col<<<(128 * g.Kcol + 255) / 256, 256, 0, st>>>(Gm, g.Kcol, g.R8, R, sigma, ws, -e);
+    return cudaGetLastError();
+}
+
+bool gabor_tc_mt_fits(int row_kmax, int row_pwmax, int col_kmax)
+{
+    return gabor_tc_smem_rows_mt(row_kmax, row_pwmax, 32) <= (size_t)kSmemLimit &&
+           1024 + mt_col_smem(col_kmax).total <= (uint32_t)kSmemLimit;
+}
+
 cudaError_t build_gabor_tc_am(uint16_t *Am, int R, double sigma, double wc, cudaStream_t st)
 {
     // the scale of the frequency's Toeplitz operands: |S(d) cos|, |S(d) sin| <= S(0)
@@ -1253,6 +1477,7 @@ cudaError_t gabor_tc_prepare()
 {
     cudaError_t e = cudaFuncSetAttribute(k_gabor_tc_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gabor_tc_rows_mt, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gabor_tc_cols_mt, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gabor_tc_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     return e;
 }
@@ -1262,10 +1487,11 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
     TcBankArgs a = a0;
     a.col_nst = col_stages(a.col_kmax);
     if (a.col_nst < 2) return cudaErrorInvalidValue;
+    if (a.row_mt && !gabor_tc_mt_fits(a.row_kmax, a.row_pwmax, a.col_kmax)) return cudaErrorInvalidValue;
     const int n_row_items = a.nf * a.row_cnt, n_col_items = a.nf * a.col_cnt;
     const size_t smem_r = a.row_mt ? gabor_tc_smem_rows_mt(a.row_kmax, a.row_pwmax, a.row_ty)
                                    : gabor_tc_smem_rows(a.row_kmax, a.row_pwmax, a.row_ty);
-    const size_t smem_c = gabor_tc_smem_cols(a.col_kmax);
+    const size_t smem_c = a.row_mt ? 1024 + mt_col_smem(a.col_kmax).total : gabor_tc_smem_cols(a.col_kmax);
     cudaError_t e0 = cudaMemsetAsync(a.minmax, 0, 2 * sizeof(unsigned), st);
     if (e0 != cudaSuccess) return e0;
     const dim3 ag(std::max(1, std::min(4, (a.W + 255) / 256)), std::max(1, std::min(a.H, 2 * sm_count)));
@@ -1290,7 +1516,10 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
         if (e != cudaSuccess) return e;
     }
     if (n_col_items > 0) {
-        k_gabor_tc_cols<<<std::min(n_col_items, sm_count), kColThreads, smem_c, st>>>(a);
+        if (a.row_mt)
+            k_gabor_tc_cols_mt<<<std::min(n_col_items, sm_count), kMtColThreads, smem_c, st>>>(a);
+        else
+            k_gabor_tc_cols<<<std::min(n_col_items, sm_count), kColThreads, smem_c, st>>>(a);
         return cudaGetLastError();
     }
     return cudaSuccess;

@@ -125,6 +125,7 @@ struct TcUnitDev {
     int s, plane_a, plane_b, pad_;
     int64_t sig_idx;       // first signal of the unit; its block starts at sig_idx * W * Hp
     const uint16_t *Am;    // modulated-tap row operand [128][Kmt] (FP16, K-major SW128)
+    const uint16_t *Gm;    // modulated-tap column operand [128][Kcol] (FP16, K-major SW128)
 };
 struct TcBankArgs {
     const float *img;
@@ -158,7 +159,7 @@ struct TcBankArgs {
     int layout;            // 0: out[plane][y][x], 1: out[y][x][plane]
     int nplanes;           // n_freq * n_theta
     int row_y0;            // first image row of the row pass (< 0: halo rows for non-zero rules)
-    int row_mt;            // 1: the modulated-tap row kernel (64-column tiles)
+    int row_mt;            // 1: the modulated-tap kernels (intermediate = Re J, Im J per unit)
     // TMA maps of the intermediate (dimensions 8 rows of a block x W x signals x Hp / 8 blocks,
     // FP16, no swizzle) for the column pass's A operand: boxes of 8 x 32 columns x 4 signals x
     // 8 blocks (paired units) and 8 x 64 x 2 x 8 (unpaired units)
@@ -251,6 +252,8 @@ int gabor_tc_mt_pw(int R);
 int gabor_tc_mt_tile_y(int Kmax, int PWmax);
 size_t gabor_tc_smem_rows_mt(int Kmax, int PWmax, int TY);
 cudaError_t build_gabor_tc_am(uint16_t *Am, int R, double sigma, double wc, cudaStream_t st);
+cudaError_t build_gabor_tc_gm(uint16_t *Gm, int R, double sigma, double ws, cudaStream_t st);
+bool gabor_tc_mt_fits(int row_kmax, int row_pwmax, int col_kmax);
 cudaError_t build_gabor_tc_b(uint16_t *Brow, uint16_t *Bcol, int R, double sigma, int bf16, float *unscale,
                              cudaStream_t st);
 cudaError_t gabor_tc_prepare();
@@ -355,6 +358,8 @@ struct gabor_bank {
     int tc_pre_stride = 0;
     int tc_row_ty = 64;
     int tc_mt_kmax = 0, tc_mt_pwmax = 0, tc_mt_ty = 64;   // modulated-tap row pass geometry
+    bool tc_mt_ok = false;                    // the modulated-tap kernels fit every frequency
+    uint16_t *d_tcGm = nullptr;               // modulated-tap column operands, one per unit
     int tc_H = 0, tc_W = 0, tc_Lpad = 0;
     int64_t tc_Hp = 0;
     bool tc_ready = false;
