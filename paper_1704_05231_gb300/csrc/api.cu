@@ -671,7 +671,9 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     for (const Freq &f : h->freqs) rmax = std::max(rmax, f.R);
     const int ypad = h->boundary == kBoundaryZero ? 0 : (rmax + ty - 1) / ty * ty;
     const int64_t row_cnt = (int64_t)((H + 2 * ypad + ty - 1) / ty) * ((W + tile_x - 1) / tile_x);
-    const int64_t col_cnt = row_mt ? ny64 * h->tc_nu_f * nx64
+    const int col_ty = gabor_tc_mt_col_ty(h->tc_col_kmax);   // modulated-tap column rows per job
+    const int64_t ny_mt = (H + col_ty - 1) / col_ty;
+    const int64_t col_cnt = row_mt ? ny_mt * h->tc_nu_f * nx64
                                    : ny64 * (h->tc_np_f * nx32 + (h->tc_nu_f - h->tc_np_f) * nx64);
     if ((int64_t)nf * std::max(row_cnt, col_cnt) > (int64_t)1 << 30)
         return fail(GB_ERR_UNSUPPORTED, "image too large for the tensor-core bank");
@@ -739,7 +741,8 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.np_f = h->tc_np_f;
     a.row_nx = (W + tile_x - 1) / tile_x;
     a.row_cnt = (int)row_cnt;
-    a.col_ny = (int)ny64;
+    a.col_ny = (int)(row_mt ? ny_mt : ny64);
+    a.col_mt_ty = col_ty;
     a.col_nx32 = (int)nx32;
     a.col_nx64 = (int)nx64;
     a.col_cnt = (int)col_cnt;

@@ -800,8 +800,9 @@ __global__ void k_build_mtoeplitz(uint16_t *__restrict__ A, int K, int R, double
 // whose four real sums per (x, y) give F_theta = sum G J and F_{pi-theta} = sum G J*
 // (Eq. 13-16) with two additions each: no row phases at all.  Operand rows n = 2 x + part,
 // columns m = 2 y + part, so the sums of a column meet by one shuffle.  Items: (unit,
-// 64-column tile, 64-row tile).  One producer warp (lane 0) loads each job's J boxes by TMA and
-// its unit's Gm by one bulk copy, two jobs deep, and issues the MMAs into two TMEM
+// 64-column tile, 64-row tile; 32-row tiles, MMA N = 64, when the two-deep operands of 64 rows
+// exceed shared memory, as for radius 96).  One producer warp (lane 0) loads each job's J boxes
+// by TMA and its unit's Gm by bulk copies, two jobs deep, and issues the MMAs into two TMEM
 // accumulators; 8 epilogue warps add the c A(x) B(y) correction and store complex64.
 constexpr int kMtColAcc = 2;       // TMEM accumulators (128 columns each)
 constexpr int kMtColThreads = 32 * (8 + 1);
@@ -810,12 +811,14 @@ struct MtColSmem {
     uint32_t a_off, b_off, desc_off, bar_off, misc_off, total;
 };
 
-__host__ __device__ inline MtColSmem mt_col_smem(int K)
+// TYC: output rows per job (64; 32 when the operands of 64 do not fit): the B operand holds
+// the first 2 TYC rows of each 128-row K-block of Gm.
+__host__ __device__ inline MtColSmem mt_col_smem(int K, int TYC)
 {
     MtColSmem L;
     L.a_off = 0;                                   // [2] x 128 x K (no swizzle, core matrices)
-    L.b_off = L.a_off + 2u * 128 * K * 2;          // [2] x 128 x K (SW128)
-    L.desc_off = L.b_off + 2u * 128 * K * 2;
+    L.b_off = L.a_off + 2u * 128 * K * 2;          // [2] x 2 TYC x K (SW128)
+    L.desc_off = L.b_off + 2u * (2 * TYC) * K * 2;
     L.bar_off = L.desc_off + kDescBytes;
     L.misc_off = L.bar_off + 16 * 8;
     L.total = L.misc_off + 64;
@@ -831,7 +834,7 @@ __device__ __forceinline__ MtColItem col_item_mt(const TcBankArgs &a, const TcDe
     const int per_unit = a.col_ny * a.col_nx64;
     const int q = local / per_unit, rest = local - q * per_unit;
     const TcFreqDev f = d.freqs[d.forder[g]];
-    return MtColItem{f.u0 + q, (rest % a.col_nx64) * 64, (rest / a.col_nx64) * kColTileY};
+    return MtColItem{f.u0 + q, (rest % a.col_nx64) * 64, (rest / a.col_nx64) * a.col_mt_ty};
 }
 
 __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __grid_constant__ TcBankArgs a)
@@ -840,7 +843,8 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const MtColSmem L = mt_col_smem(a.col_kmax);
+    const int TYC = a.col_mt_ty;
+    const MtColSmem L = mt_col_smem(a.col_kmax, TYC);
     unsigned char *sA = sm + L.a_off;
     unsigned char *sB = sm + L.b_off;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.bar_off);
@@ -851,7 +855,9 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     uint64_t *drain = bars + 8;
     uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
-    const uint32_t obuf = 128u * a.col_kmax * 2;
+    const uint32_t obuf = 128u * a.col_kmax * 2;            // an A buffer
+    const uint32_t gbuf = 2u * TYC * a.col_kmax * 2;         // a B buffer
+    const uint32_t gblk = 2u * TYC * 128;                    // one K-block of B
     const TcDesc D = load_desc(a, sm + L.desc_off);
     float cen;
     int e_unused;
@@ -876,7 +882,7 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_s;
-    const uint32_t idesc = idesc_f16(0, 128, 128);
+    const uint32_t idesc = idesc_f16(0, 128, 2 * TYC);
     const int njobs = nitems > (int)blockIdx.x ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
     if (warp == 8) {
@@ -890,14 +896,18 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
                 const MtColItem w = item(j);
                 const TcUnitDev u = D.units[w.unit];
                 const TcFreqDev f = D.freqs[u.s];
-                const int st = j & 1;
-                const uint32_t bytes = 128u * f.Kcol * 2;
-                mbar_arrive_expect_tx(&ab_full[st], 2 * bytes);
+                const int st = j & 1, nkb = f.Kcol / 64;
+                mbar_arrive_expect_tx(&ab_full[st], nkb * (16384u + gblk));
                 const int yb0 = (a.Lpad + w.y0 - f.R8) >> 3;
                 const uint32_t dst = smem_u32(sA + st * obuf);
-                for (int kb = 0; kb < f.Kcol / 64; ++kb)
+                for (int kb = 0; kb < nkb; ++kb)
                     tma_load_4d(dst + kb * 16384u, &a.tmA[0], 0, 2 * w.unit, w.x0, yb0 + 8 * kb, &ab_full[st]);
-                bulk_load(smem_u32(sB + st * obuf), u.Gm, bytes, &ab_full[st]);
+                if (TYC == 64) {
+                    bulk_load(smem_u32(sB + st * gbuf), u.Gm, nkb * gblk, &ab_full[st]);
+                } else {   // the first 2 TYC rows of each K-block
+                    for (int kb = 0; kb < nkb; ++kb)
+                        bulk_load(smem_u32(sB + st * gbuf) + kb * gblk, u.Gm + (size_t)kb * 128 * 64, gblk, &ab_full[st]);
+                }
             };
             int issued = 0, landed = 0;
             for (; issued < 2 && issued < njobs; ++issued) issue(issued);
@@ -915,12 +925,12 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a0 = smem_u32(sA + st * obuf), b0 = smem_u32(sB + st * obuf);
+                const uint32_t a0 = smem_u32(sA + st * obuf), b0 = smem_u32(sB + st * gbuf);
                 for (int kb = 0; kb < f.Kcol / 64; ++kb)
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
                         tc_mma_f16(tmem + 128u * acc, smem_desc_kmajor(a0 + kb * 16384 + kk * 4096, 2048, 128),
-                                   smem_desc_sw128(b0 + kb * 128 * 128) + 2 * kk, idesc, (kb | kk) != 0);
+                                   smem_desc_sw128(b0 + kb * gblk) + 2 * kk, idesc, (kb | kk) != 0);
                 tc_commit(&tmem_full[acc]);
                 tc_commit(&ab_empty[st]);
                 // job j + 2 goes into these buffers once this MMA is done with them
@@ -949,8 +959,8 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
         // -------------------------------------------------------------- epilogue
         // TMEM lane n = 2 x + part (part 0: Re J, 1: Im J), column m = 2 y + g (g 0: Re G,
         // 1: Im G).  Warp w reads quarter w & 3 (columns x 16 (w & 3) .. + 15) and rows y
-        // 32 (w >> 2) .. + 31.  The part-0 lane of a column stores F_theta, the part-1 lane
-        // F_{pi - theta} (paired units).
+        // (TYC / 2) (w >> 2) .. + TYC / 2 - 1.  The part-0 lane of a column stores F_theta, the
+        // part-1 lane F_{pi - theta} (paired units).
         const int quarter = warp & 3, half = warp >> 2;
         const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
         const int part = lane & 1, xl = 16 * quarter + (lane >> 1);
@@ -960,11 +970,12 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
             const TcFreqDev f = D.freqs[u.s];
             const int acc = j & 1;
             const bool paired = u.plane_b >= 0;
-            const int x = w.x0 + xl, ybase = w.y0 + 32 * half;
+            const int x = w.x0 + xl, ybase = w.y0 + (TYC / 2) * half;
             const bool xok = x < a.W;
-            // c B(y) of the warp's rows (lane l holds row ybase + l); A(x) of the lane's column
+            // c B(y) of the warp's rows (lane l < TYC / 2 holds row ybase + l); A(x) of the lane's column
             const int yl = ybase + lane;
-            const float2 byl = yl < a.H ? __ldg(&a.onesB[(int64_t)w.unit * a.H + yl]) : make_float2(0.f, 0.f);
+            const float2 byl = (lane < TYC / 2 && yl < a.H) ? __ldg(&a.onesB[(int64_t)w.unit * a.H + yl])
+                                                            : make_float2(0.f, 0.f);
             const float2 ax = xok ? __ldg(&a.onesA[(int64_t)w.unit * a.W + x]) : make_float2(0.f, 0.f);
             if (!mbar_wait(&tmem_full[acc], (j >> 1) & 1, abort_s)) {
                 if (lane == 0) fail_status(a.status, abort_s, 39);
@@ -977,9 +988,9 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
             // correction c A(x) B(y) for theta, c conj(A(x)) B(y) for pi - theta
             const float axi = part ? -ax.y : ax.y;
 #pragma unroll 1
-            for (int c0 = 0; c0 < 64; c0 += 16) {   // accumulator columns 64 half + c0 .. + 15
+            for (int c0 = 0; c0 < TYC; c0 += 16) {   // accumulator columns TYC half + c0 .. + 15
                 uint32_t r[16];
-                tmem_ld16_async(tmem + lane_base + 128u * acc + 64 * half + c0, r);
+                tmem_ld16_async(tmem + lane_base + 128u * acc + TYC * half + c0, r);
                 tmem_wait_ld();
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
@@ -990,7 +1001,7 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
                     // A = sum Re G Re J, B = sum Im G Im J, C = sum Im G Re J, D = sum Re G Im J
                     const float A = part ? or_ : gr, C = part ? oi : gi;
                     const float Dd = part ? gr : or_, B = part ? gi : oi;
-                    const int yr = (c0 >> 1) + t;                // row within the warp's 32
+                    const int yr = (c0 >> 1) + t;                // row within the warp's TYC / 2
                     const float cbr = cen * __shfl_sync(0xffffffffu, byl.x, yr);   // c B(y)
                     const float cbi = cen * __shfl_sync(0xffffffffu, byl.y, yr);
                     const int y = ybase + yr;
@@ -1435,7 +1446,12 @@ cudaError_t build_gabor_tc_gm(uint16_t *Gm, int R, double sigma, double ws, cuda
 bool gabor_tc_mt_fits(int row_kmax, int row_pwmax, int col_kmax)
 {
     return gabor_tc_smem_rows_mt(row_kmax, row_pwmax, 32) <= (size_t)kSmemLimit &&
-           1024 + mt_col_smem(col_kmax).total <= (uint32_t)kSmemLimit;
+           1024 + mt_col_smem(col_kmax, 32).total <= (uint32_t)kSmemLimit;
+}
+
+int gabor_tc_mt_col_ty(int col_kmax)
+{
+    return 1024 + mt_col_smem(col_kmax, 64).total <= (uint32_t)kSmemLimit ? 64 : 32;
 }
 
 cudaError_t build_gabor_tc_am(uint16_t *Am, int R, double sigma, double wc, cudaStream_t st)
@@ -1491,7 +1507,7 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
     const int n_row_items = a.nf * a.row_cnt, n_col_items = a.nf * a.col_cnt;
     const size_t smem_r = a.row_mt ? gabor_tc_smem_rows_mt(a.row_kmax, a.row_pwmax, a.row_ty)
                                    : gabor_tc_smem_rows(a.row_kmax, a.row_pwmax, a.row_ty);
-    const size_t smem_c = a.row_mt ? 1024 + mt_col_smem(a.col_kmax).total : gabor_tc_smem_cols(a.col_kmax);
+    const size_t smem_c = a.row_mt ? 1024 + mt_col_smem(a.col_kmax, a.col_mt_ty).total : gabor_tc_smem_cols(a.col_kmax);
     cudaError_t e0 = cudaMemsetAsync(a.minmax, 0, 2 * sizeof(unsigned), st);
     if (e0 != cudaSuccess) return e0;
     const dim3 ag(std::max(1, std::min(4, (a.W + 255) / 256)), std::max(1, std::min(a.H, 2 * sm_count)));

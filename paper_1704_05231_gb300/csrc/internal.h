@@ -147,7 +147,7 @@ struct TcBankArgs {
     const float2 *onesB;   // [unit][H]
     const double2 *ones_pre;   // [unit][2][2 Rmax + 2] prefix sums of S(d) exp(i w^{c|s} d)
     int ones_stride;           // 2 Rmax + 2
-    int pad3_;
+    int col_mt_ty;             // modulated-tap column pass: output rows per job (64, or 32 for large K)
     // Work items, decoded from the image shape: frequencies in the order forder[] (largest
     // radius first); every frequency has nu_f units, the first np_f of them paired.
     const int *forder;
@@ -254,6 +254,7 @@ size_t gabor_tc_smem_rows_mt(int Kmax, int PWmax, int TY);
 cudaError_t build_gabor_tc_am(uint16_t *Am, int R, double sigma, double wc, cudaStream_t st);
 cudaError_t build_gabor_tc_gm(uint16_t *Gm, int R, double sigma, double ws, cudaStream_t st);
 bool gabor_tc_mt_fits(int row_kmax, int row_pwmax, int col_kmax);
+int gabor_tc_mt_col_ty(int col_kmax);
 cudaError_t build_gabor_tc_b(uint16_t *Brow, uint16_t *Bcol, int R, double sigma, int bf16, float *unscale,
                              cudaStream_t st);
 cudaError_t gabor_tc_prepare();

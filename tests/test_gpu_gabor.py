@@ -379,3 +379,33 @@ def test_tc_bank_row_pass_forms(torch_cuda, row_pass, boundary, H, W):
     e = rel_err(got, oracle.gabor_bank(img, th, om, sg, boundary=boundary))
     print("TC row pass", row_pass, boundary, H, W, "rel err", e)
     assert e <= TC_TOL
+
+
+@pytest.mark.parametrize("row_pass", [1, 2])
+@pytest.mark.parametrize("boundary", ["zero", "mirror"])
+def test_tc_bank_large_radius_sampled(torch_cuda, row_pass, boundary):
+    # Batched-bank frequencies pi/2 .. pi/32 (sigma = pi / omega, radii 6 .. 96): with radius
+    # 96 the modulated-tap column pass takes 32-row jobs (the 64-row operands exceed shared
+    # memory); ragged sizes put partial jobs at both image edges.
+    from paper_1704_05231_gb300 import GaborBank
+    from tests.helpers import TC_TOL
+    torch = torch_cuda
+    rng = np.random.default_rng(23)
+    th = [k * math.pi / 8 for k in range(8)]
+    om = [math.pi / 2 ** k for k in range(1, 6)]
+    sg = [math.pi / w for w in om]
+    for H, W in [(333, 257), (97, 530)]:
+        img = synth.paper_like([47, H, W], H, W)
+        with GaborBank(th, om, sg, precision="fp16_tc", boundary=boundary) as gbk:
+            gbk.set_option("row_pass", row_pass)
+            got = gbk.filter(torch.from_numpy(img).cuda()).cpu().numpy()
+            gbk.device_status()
+        with GaborBank(th, om, sg, boundary=boundary) as gbk:
+            f32 = gbk.filter(torch.from_numpy(img).cuda()).cpu().numpy()
+        e = rel_err(got, f32)
+        print("TC large radius", row_pass, boundary, H, W, "rel err vs FP32", e)
+        assert e <= TC_TOL
+        xs, ys = sample_points(rng, H, W, 200)
+        ref = oracle.gabor_bank(img, th, om, sg, points=(xs, ys), boundary=boundary)
+        scale = float(np.max(np.abs(f32)))
+        assert float(np.max(np.abs(got[:, :, ys, xs] - ref))) <= TC_TOL * scale
