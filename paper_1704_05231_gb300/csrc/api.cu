@@ -594,21 +594,6 @@ gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
     return GB_OK;
 }
 
-// The driver's tensor-map encoder, fetched once through the runtime (no link against the
-// driver library).
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
-}
 
 // TMA maps of the blocked intermediate [signal][Hp / 8][W][8] for the column pass, as a 4-D
 // tensor (8 rows of a block, W columns, signals, Hp / 8 blocks; FP16): boxes of 8 x 32 x 4 x 8
@@ -841,6 +826,22 @@ gb_status filter_device(gabor_bank *h, const float *d_img, int H, int W, int64_t
 namespace gb {
 // Records the message returned by gabor_bank_last_error() on this host thread.
 void set_last_error(const char *msg) { g_err = msg; }
+
+// The driver's tensor-map encoder, fetched once through the runtime (no link against the
+// driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
 }  // namespace gb
 
 extern "C" {
@@ -927,6 +928,8 @@ gb_status gabor_bank_destroy(gabor_bank_t h)
     free_tc(h);
     if (h->d_sdft_B) cudaFree(h->d_sdft_B);
     h->d_sdft_B = nullptr;
+    if (h->d_sdft_ws) cudaFree(h->d_sdft_ws);
+    h->d_sdft_ws = nullptr;
     if (h->d_stage_out) cudaFree(h->d_stage_out);
     h->d_stage_out = nullptr;
     delete h;
@@ -1069,8 +1072,20 @@ gb_status gabor_bank_sdft(gabor_bank_t h, const float *d_img, int H, int W, int6
         h->sdftB_Mx = Mx;
         h->sdftB_My = My;
     }
+    const size_t ws_bytes = (size_t)sdft_tc_ws_bytes(H, W, Mx, My);
+    if (ws_bytes > h->sdft_ws_bytes) {
+        GB_CU(cudaStreamSynchronize(st));   // earlier work of this handle may still read it
+        if (h->d_sdft_ws) cudaFree(h->d_sdft_ws);
+        h->d_sdft_ws = nullptr;
+        h->sdft_ws_bytes = 0;
+        uint4 *p = nullptr;
+        GB_TRY(dalloc(&p, (ws_bytes + 15) / 16));
+        h->d_sdft_ws = p;
+        h->sdft_ws_bytes = ws_bytes;
+    }
     GB_CU(launch_sdft_tc(d_img, pitch, H, W, reinterpret_cast<float2 *>(d_out), Mx, My, half_spectrum,
-                         h->d_sdft_B, h->sdft_B_unscale, bf16, h->boundary, h->d_status, h->sm_count, st));
+                         h->d_sdft_B, h->sdft_B_unscale, bf16, h->boundary, h->d_status, h->sm_count,
+                         ws_bytes ? h->d_sdft_ws : nullptr, st));
     return GB_OK;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
@@ -279,9 +280,16 @@ bool sdft_tc_supported(int Mx, int My);
 int sdft_tc_b_bytes(int Mx, int My);
 cudaError_t build_sdft_tc_b(void *Bdev, double sigma, int Mx, int My, int bf16, float *b_unscale, cudaStream_t st);
 cudaError_t sdft_tc_prepare();
+// TMA-fed kernel (Mx in {8, 16, 32, 64}, Mx * My a multiple of 64): its workspace holds the
+// row-unfolded image; other windows build A in shared memory from a staged patch.
+bool sdft_tc_tma_ok(int Mx, int My);
+int64_t sdft_tc_ws_bytes(int H, int W, int Mx, int My);
+// ws: sdft_tc_ws_bytes() bytes (16-byte aligned) when sdft_tc_tma_ok(), else unused (may be NULL).
 cudaError_t launch_sdft_tc(const float *img, int64_t pitch, int H, int W, float2 *out, int Mx, int My, int half,
                            const void *Bdev, float b_unscale, int bf16, int bmode, int *status, int sm_count,
-                           cudaStream_t st);
+                           void *ws, cudaStream_t st);
+// The driver's tensor-map encoder (fetched once through the runtime).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
 }  // namespace gb
 
@@ -339,6 +347,8 @@ struct gabor_bank {
     void *d_sdft_B = nullptr;
     size_t sdft_B_bytes = 0;
     float sdft_B_unscale = 1.f;
+    void *d_sdft_ws = nullptr;      // tensor-core SDFT workspace (max |f|, unfolded image)
+    size_t sdft_ws_bytes = 0;
     double sdftB_sigma = -1.0;
     int sdftB_Mx = 0, sdftB_My = 0;
     // tensor-core bank: B operands per frequency, unit descriptors, intermediate signals
