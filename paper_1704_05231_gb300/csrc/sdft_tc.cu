@@ -508,6 +508,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_sdft_tc_tma(const __grid_con
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // Launched as a programmatic dependent of k_unfold: everything above (barriers, TMEM, the
+    // copy of B) overlaps its tail; U and the scale are read only after it has completed.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const uint32_t tmem = *tmem_base_s;
     const int ntiles_cta = a.ntiles > (int)blockIdx.x ? (a.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
@@ -601,29 +604,39 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_sdft_tc_tma(const __grid_con
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
-// max |f| over the image, as float bits (non-negative floats order as unsigned integers)
+// max |f| over the image, as float bits (non-negative floats order as unsigned integers); one
+// atomic per block (256 threads)
 __global__ void k_absmax(const float *__restrict__ img, int64_t pitch, int H, int W, unsigned *maxbits)
 {
+    __shared__ float wmax[8];
     float m = 0.f;
     for (int y = blockIdx.y; y < H; y += gridDim.y)
         for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < W; x += gridDim.x * blockDim.x)
             m = fmaxf(m, fabsf(__ldg(img + (int64_t)y * pitch + x)));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(maxbits, __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, wmax[w]);
+        if (m > 0.f) atomicMax(maxbits, __float_as_uint(m));
+    }
 }
 
 // U[x][r][a] = s f(x - Mx/2 + a, r - My/2) for x in [0, W), r in [0, H + My), a in [0, Mx),
-// the image extended by the boundary rule; one thread per (x, r) (r fastest, so a warp's
-// stores are contiguous), Mx / 8 16-byte stores.
+// the image extended by the boundary rule; one thread per (x, r), x fastest (a warp's loads of
+// one image row are contiguous), Mx / 8 16-byte stores of its own 2 Mx bytes.
 template <typename T>
 __global__ void k_unfold(const float *__restrict__ img, int64_t pitch, int H, int W, int Mx, int My, int bmode,
                          const unsigned *maxbits, uint4 *__restrict__ U)
 {
+    // the SDFT kernel that reads U may start its prologue now (it waits for this grid's end)
+    asm volatile("griddepcontrol.launch_dependents;");
     const float sc = ldexpf(1.f, -scale_exponent(__ldg(maxbits)));
     const int64_t n = (int64_t)(H + My) * W;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i / (H + My)), r = (int)(i - (int64_t)x * (H + My));
+        const int r = (int)(i / W), x = (int)(i - (int64_t)r * W);
+        const int64_t o = ((int64_t)x * (H + My) + r) * Mx;   // U[x][r][0]
         const int gy = r - My / 2;
         const bool yin = gy >= 0 && gy < H;
         const float *row = img + (int64_t)(bmode == kBoundaryZero ? (yin ? gy : 0) : ext_coord(gy, H, bmode)) * pitch;
@@ -643,7 +656,7 @@ __global__ void k_unfold(const float *__restrict__ img, int64_t pitch, int H, in
                 }
                 w[q] = (uint32_t)to_bits<T>(v[0] * sc) | ((uint32_t)to_bits<T>(v[1] * sc) << 16);
             }
-            U[(i * Mx + a0) / 8] = make_uint4(w[0], w[1], w[2], w[3]);
+            U[(o + a0) / 8] = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
@@ -678,6 +691,7 @@ __global__ void k_build_sdft_b(uint16_t *__restrict__ B, int Mx, int My, int K, 
 
 bool sdft_tc_supported(int Mx, int My)
 {
+    if (sdft_tc_tma_ok(Mx, My)) return true;
     const int K = Mx * My;
     if (K > 256) return false;
     const int Kp = round_up_i(K, 64);
@@ -802,12 +816,18 @@ cudaError_t launch_sdft_tc(const float *img, int64_t pitch, int H, int W, float2
         a.maxbits = maxbits;
         const TcLayout LT = tc_layout_tma(a.Kp, a.NP);
         const size_t smem = std::max<size_t>(LT.total + 1024, 120 * 1024);
-        const int grid = std::min(a.ntiles, sm_count);
-        if (bf16)
-            k_sdft_tc_tma<__nv_bfloat16><<<grid, kTmaThreads, smem, st>>>(a);
-        else
-            k_sdft_tc_tma<__half><<<grid, kTmaThreads, smem, st>>>(a);
-        return cudaGetLastError();
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(std::min(a.ntiles, sm_count));
+        cfg.blockDim = dim3(kTmaThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return bf16 ? cudaLaunchKernelEx(&cfg, k_sdft_tc_tma<__nv_bfloat16>, a)
+                    : cudaLaunchKernelEx(&cfg, k_sdft_tc_tma<__half>, a);
     }
     const TcLayout L = tc_layout(a.Kp, a.NP, My, a.PW);
     // at least ~half the SM's shared memory, so one CTA (and one 512-column TMEM block) per SM

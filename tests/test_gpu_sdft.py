@@ -72,8 +72,10 @@ def test_sdft_c3_full_size_sampled(torch_cuda):
 
 @pytest.mark.parametrize("precision", ["fp16_tc", "bf16_tc"])
 @pytest.mark.parametrize("H,W,M,sigma", [(40, 300, 16, 4.0), (7, 129, 8, 1.5), (64, 64, (8, 16), 2.0),
-                                         (20, 140, 12, 2.0)])
+                                         (20, 140, 12, 2.0), (33, 150, (8, 32), 2.5), (45, 131, (32, 8), 2.5)])
 def test_sdft_tc_parity(torch_cuda, precision, H, W, M, sigma):
+    # 16 x 16, 8 x 8, 8 x 16, 8 x 32 and 32 x 8 run the TMA-fed kernel (the last two only
+    # there: their operands exceed shared memory with a staged patch); 12 x 12 the im2col one.
     from tests.helpers import TC_TOL
     img = synth.pink_noise([8, H, W], H, W)
     got = run_sdft(torch_cuda, img, sigma, M, precision=precision)
