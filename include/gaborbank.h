@@ -122,7 +122,12 @@ gb_status gabor_bank_filter_host(gabor_bank_t h, const float *h_img, int H, int 
  *                   of v; the rest follow from F_{u,v} = F*_{(Mx-u)%Mx,(My-v)%My}.
  * d_out          device complex64, 8-byte aligned.
  * The handle's precision selects the FP32 separable path (Algorithm 2) or the tensor-core
- * windowed-DFT contraction.  Asynchronous.  Errors as gabor_bank_filter.
+ * windowed-DFT contraction (Mx * My <= 256).  For Mx in {8, 16, 32, 64} with Mx * My a
+ * multiple of 64 the tensor-core path first writes a row-unfolded FP16/BF16 copy of the image,
+ * (H + My) * W * Mx * 2 bytes, into a handle-owned buffer that grows when an image needs more
+ * (the call then synchronizes the stream once); other windows need no per-image buffer.
+ * Asynchronous.  Errors as gabor_bank_filter; GB_ERR_UNSUPPORTED when a tensor-core window's
+ * operands do not fit in shared memory.
  */
 gb_status gabor_bank_sdft(gabor_bank_t h, const float *d_img, int H, int W, int64_t pitch,
                           double sigma, int My, int Mx, int half_spectrum, void *d_out,

@@ -8,17 +8,20 @@
 //                                      B[n][k] = {Re, Im} exp(-i 2 pi (u a / Mx + v b / My))
 //                                                S(a - Mx/2) S(b - My/2) * 2^sB
 //
-// A (FP16 or BF16, per-tile power-of-two scale sA) is built in shared memory by im2col from a
-// staged FP32 patch; B (built once per plan in FP64 on the GPU, stored pre-swizzled) stays
-// resident in shared memory for the whole persistent CTA.  D accumulates in FP32 in tensor
-// memory, in two passes of NP columns each (double-buffered, 2 x 256 TMEM columns), and is
-// read back by the epilogue warps, rescaled exactly by 2^-(sA+sB), and stored as complex64;
-// bins with v > My/2 are filled from F_{u,v} = F*_{Mx-u, My-v} (Algorithm 2, last loop).
+// B (built once per plan in FP64 on the GPU, stored pre-swizzled) arrives by one bulk copy
+// (cp.async.bulk) and stays resident in shared memory for the whole persistent CTA.  D
+// accumulates in FP32 in tensor memory, in two passes of NP columns each (2 x 256 TMEM
+// columns), and is read back by the epilogue warps, rescaled exactly by 2^-(sA+sB), and stored
+// as complex64; bins with v > My/2 are filled from F_{u,v} = F*_{Mx-u, My-v} (Algorithm 2,
+// last loop).  A (FP16 or BF16) comes one of two ways:
 //
-// Roles (384 threads): warps 0-7 epilogue (TMEM lanes 0-127 = the tile's pixels, two warps
-// per lane quadrant splitting the columns); warps 8-11 producers (patch load, per-tile scale,
-// im2col); thread 256 issues the MMAs.  B arrives once per CTA by one bulk copy (cp.async.bulk)
-// that the first MMA waits for.
+//   k_sdft_tc_tma  (Mx in {8, 16, 32, 64}, Mx * My a multiple of 64): by TMA boxes of the
+//                  pixel-major row-unfolded image U that k_unfold writes (sA from the image's
+//                  max |f|, k_absmax); 16 epilogue warps, one MMA thread, one TMA thread.
+//   k_sdft_tc      (other windows): by im2col in shared memory from a staged FP32 patch (sA
+//                  per tile); 8 epilogue warps (TMEM lanes 0-127 = the tile's pixels, two per
+//                  lane quadrant), 4 producer warps, one MMA thread.
+//
 // Every mbarrier wait is bounded; on timeout the CTA records a code in the status word and
 // stops.
 #include <algorithm>
