@@ -86,17 +86,41 @@ def test_sdft_tc_parity(torch_cuda, precision, H, W, M, sigma):
     assert e <= TC_TOL
 
 
-def test_sdft_tc_scaled_input_and_status(torch_cuda):
-    # Per-tile power-of-two scaling: a 1e4-scaled image stays within FP16 range.
+@pytest.mark.parametrize("M", [16, 12])
+@pytest.mark.parametrize("gain", [1.0e6, 1.0e4, 1.0e-6])
+def test_sdft_tc_scaled_input_and_status(torch_cuda, M, gain):
+    # The power-of-two operand scale (per image on the TMA-fed path, M = 16; per tile on the
+    # im2col path, M = 12): images far above the FP16 range (1e6) or deep in its subnormals
+    # (1e-6) keep the tensor-core bound.
     from paper_1704_05231_gb300 import GaborBank
     from tests.helpers import TC_TOL
     torch = torch_cuda
-    img = (synth.pink_noise(12, 33, 200) * 1.0e4).astype(np.float32)
+    img = (synth.pink_noise(12, 33, 200) * gain).astype(np.float32)
     with GaborBank(precision="fp16_tc") as gbk:
-        got = gbk.sdft(torch.from_numpy(img).cuda(), 4.0, 16).cpu().numpy()
+        got = gbk.sdft(torch.from_numpy(img).cuda(), 4.0, M).cpu().numpy()
         gbk.device_status()
-    ref = oracle.sdft(img, 4.0, 16)
+    ref = oracle.sdft(img, 4.0, M)
     assert rel_err(got, ref) <= TC_TOL
+
+
+def test_sdft_tc_workspace_growth_and_pitch(torch_cuda):
+    # The TMA-fed path's unfolded-image workspace grows with the image and is reused for a
+    # smaller one; strided views (pitch 260 > W) read the same pixels as contiguous copies.
+    # Every result equals a fresh handle's on the contiguous copy, bitwise, and the half
+    # spectrum is the first My/2 + 1 planes of the full one.
+    from paper_1704_05231_gb300 import GaborBank
+    torch = torch_cuda
+    t = torch.from_numpy(synth.pink_noise([51], 150, 260)).cuda()
+    shapes = [(40, 70), (150, 260), (33, 129)]
+    with GaborBank(precision="fp16_tc") as gbk:
+        outs = [gbk.sdft(t[:h, :w], 4.0, 16).cpu().numpy() for h, w in shapes]
+        half = gbk.sdft(t[:33, :129], 4.0, 16, half_spectrum=True).cpu().numpy()
+        gbk.device_status()
+    for (h, w), got in zip(shapes, outs):
+        with GaborBank(precision="fp16_tc") as fresh:
+            ref = fresh.sdft(t[:h, :w].contiguous(), 4.0, 16).cpu().numpy()
+        assert np.array_equal(got, ref)
+    assert np.array_equal(half, outs[2][:9])
 
 
 @pytest.mark.parametrize("precision", ["fp16_tc", "bf16_tc"])
