@@ -586,6 +586,10 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // programmatic dependent of k_ones (which waits for k_minmax): the set-up above overlaps
+    // them; the centre and scale are read after they completed
+    pdl_launch_dependents();
+    pdl_wait();
     const uint32_t tmem = *tmem_s;
     const uint32_t idesc = idesc_f16(0, 128, TY);
     float cen;
@@ -859,9 +863,6 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     const uint32_t gbuf = 2u * TYC * a.col_kmax * 2;         // a B buffer
     const uint32_t gblk = 2u * TYC * 128;                    // one K-block of B
     const TcDesc D = load_desc(a, sm + L.desc_off);
-    float cen;
-    int e_unused;
-    image_centre(a, cen, e_unused);
 
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
@@ -881,6 +882,12 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // programmatic dependent of the row pass: the set-up above overlaps its tail; J, the F[1]
+    // tables and the centre are read after it completed
+    pdl_wait();
+    float cen;
+    int e_unused;
+    image_centre(a, cen, e_unused);
     const uint32_t tmem = *tmem_s;
     const uint32_t idesc = idesc_f16(0, 128, 2 * TYC);
     const int njobs = nitems > (int)blockIdx.x ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -1304,6 +1311,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_gabor_tc_cols(const __grid_c
 // (both words start at zero; one atomicMax pair per block).
 __global__ void k_minmax(const float *__restrict__ img, int64_t pitch, int H, int W, unsigned *__restrict__ out)
 {
+    pdl_launch_dependents();   // k_ones may run alongside (it waits for this grid before it ends)
     unsigned lo = 0xffffffffu, hi = 0u;
     for (int y = blockIdx.y; y < H; y += gridDim.y)
         for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < W; x += gridDim.x * blockDim.x) {
@@ -1362,6 +1370,9 @@ __global__ void k_build_prefix(const double *__restrict__ unit_w, const TcUnitDe
 __global__ void k_ones(const TcBankArgs a, const TcUnitDev *__restrict__ units, const TcFreqDev *__restrict__ freqs,
                        int nunits, float2 *__restrict__ A, float2 *__restrict__ B)
 {
+    // a programmatic dependent of k_minmax that does not read its result: it runs alongside,
+    // and completes only after k_minmax has (so the kernels after it see both)
+    pdl_launch_dependents();
     const int64_t n = (int64_t)nunits * (a.W + a.H);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int u = (int)(i / (a.W + a.H)), p = (int)(i % (a.W + a.H));
@@ -1381,6 +1392,7 @@ __global__ void k_ones(const TcBankArgs a, const TcUnitDev *__restrict__ units, 
         else
             B[(int64_t)u * a.H + pos] = f;
     }
+    pdl_wait();
 }
 
 __global__ void k_build_toeplitz(uint16_t *__restrict__ B, int rows, int K, int off, int R, double sigma, int sB)
@@ -1518,22 +1530,24 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
         const int nu = a.nf * a.nu_f;
         const int64_t n = (int64_t)nu * (a.W + a.H);
         const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4 * sm_count));
-        k_ones<<<blocks, 256, 0, st>>>(a, a.units, a.freqs, nu, const_cast<float2 *>(a.onesA),
-                                       const_cast<float2 *>(a.onesB));
-        e0 = cudaGetLastError();
+        e0 = launch_pdl(k_ones, dim3(blocks), dim3(256), 0, st, a, a.units, a.freqs, nu,
+                        const_cast<float2 *>(a.onesA), const_cast<float2 *>(a.onesB));
         if (e0 != cudaSuccess) return e0;
     }
     if (n_row_items > 0) {
-        if (a.row_mt)
-            k_gabor_tc_rows_mt<<<std::min(n_row_items, sm_count), 512, smem_r, st>>>(a);
-        else
+        cudaError_t e;
+        if (a.row_mt) {
+            e = launch_pdl(k_gabor_tc_rows_mt, dim3(std::min(n_row_items, sm_count)), dim3(512), smem_r, st, a);
+        } else {
             k_gabor_tc_rows<<<std::min(n_row_items, sm_count), 512, smem_r, st>>>(a);
-        cudaError_t e = cudaGetLastError();
+            e = cudaGetLastError();
+        }
         if (e != cudaSuccess) return e;
     }
     if (n_col_items > 0) {
         if (a.row_mt)
-            k_gabor_tc_cols_mt<<<std::min(n_col_items, sm_count), kMtColThreads, smem_c, st>>>(a);
+            return launch_pdl(k_gabor_tc_cols_mt, dim3(std::min(n_col_items, sm_count)), dim3(kMtColThreads), smem_c,
+                              st, a);
         else
             k_gabor_tc_cols<<<std::min(n_col_items, sm_count), kColThreads, smem_c, st>>>(a);
         return cudaGetLastError();

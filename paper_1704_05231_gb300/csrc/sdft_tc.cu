@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_sdft_tc_tma(const __grid_con
     tc_fence_after();
     // Launched as a programmatic dependent of k_unfold: everything above (barriers, TMEM, the
     // copy of B) overlaps its tail; U and the scale are read only after it has completed.
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    pdl_wait();
     const uint32_t tmem = *tmem_base_s;
     const int ntiles_cta = a.ntiles > (int)blockIdx.x ? (a.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
@@ -634,7 +634,7 @@ __global__ void k_unfold(const float *__restrict__ img, int64_t pitch, int H, in
                          const unsigned *maxbits, uint4 *__restrict__ U)
 {
     // the SDFT kernel that reads U may start its prologue now (it waits for this grid's end)
-    asm volatile("griddepcontrol.launch_dependents;");
+    pdl_launch_dependents();
     const float sc = ldexpf(1.f, -scale_exponent(__ldg(maxbits)));
     const int64_t n = (int64_t)(H + My) * W;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -819,18 +819,9 @@ cudaError_t launch_sdft_tc(const float *img, int64_t pitch, int H, int W, float2
         a.maxbits = maxbits;
         const TcLayout LT = tc_layout_tma(a.Kp, a.NP);
         const size_t smem = std::max<size_t>(LT.total + 1024, 120 * 1024);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(std::min(a.ntiles, sm_count));
-        cfg.blockDim = dim3(kTmaThreads);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        return bf16 ? cudaLaunchKernelEx(&cfg, k_sdft_tc_tma<__nv_bfloat16>, a)
-                    : cudaLaunchKernelEx(&cfg, k_sdft_tc_tma<__half>, a);
+        const dim3 grid(std::min(a.ntiles, sm_count)), block(kTmaThreads);
+        return bf16 ? launch_pdl(k_sdft_tc_tma<__nv_bfloat16>, grid, block, smem, st, a)
+                    : launch_pdl(k_sdft_tc_tma<__half>, grid, block, smem, st, a);
     }
     const TcLayout L = tc_layout(a.Kp, a.NP, My, a.PW);
     // at least ~half the SM's shared memory, so one CTA (and one 512-column TMEM block) per SM
