@@ -611,6 +611,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_sdft_tc_tma(const __grid_con
 // atomic per block (256 threads)
 __global__ void k_absmax(const float *__restrict__ img, int64_t pitch, int H, int W, unsigned *maxbits)
 {
+    pdl_launch_dependents();   // k_unfold may launch now (it waits for this grid before reading the max)
     __shared__ float wmax[8];
     float m = 0.f;
     for (int y = blockIdx.y; y < H; y += gridDim.y)
@@ -633,8 +634,10 @@ template <typename T>
 __global__ void k_unfold(const float *__restrict__ img, int64_t pitch, int H, int W, int Mx, int My, int bmode,
                          const unsigned *maxbits, uint4 *__restrict__ U)
 {
-    // the SDFT kernel that reads U may start its prologue now (it waits for this grid's end)
+    // the SDFT kernel that reads U may start its prologue now (it waits for this grid's end);
+    // this grid is itself a programmatic dependent of k_absmax
     pdl_launch_dependents();
+    pdl_wait();
     const float sc = ldexpf(1.f, -scale_exponent(__ldg(maxbits)));
     const int64_t n = (int64_t)(H + My) * W;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -798,11 +801,10 @@ cudaError_t launch_sdft_tc(const float *img, int64_t pitch, int H, int W, float2
         k_absmax<<<ag, 256, 0, st>>>(img, pitch, H, W, maxbits);
         const int64_t n = (int64_t)(H + My) * W;
         const int ub = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 16 * sm_count));
-        if (bf16)
-            k_unfold<__nv_bfloat16><<<ub, 256, 0, st>>>(img, pitch, H, W, Mx, My, bmode, maxbits, U);
-        else
-            k_unfold<__half><<<ub, 256, 0, st>>>(img, pitch, H, W, Mx, My, bmode, maxbits, U);
-        e = cudaGetLastError();
+        e = bf16 ? launch_pdl(k_unfold<__nv_bfloat16>, dim3(ub), dim3(256), 0, st, img, pitch, H, W, Mx, My, bmode,
+                              static_cast<const unsigned *>(maxbits), U)
+                 : launch_pdl(k_unfold<__half>, dim3(ub), dim3(256), 0, st, img, pitch, H, W, Mx, My, bmode,
+                              static_cast<const unsigned *>(maxbits), U);
         if (e != cudaSuccess) return e;
         // U as a 2-D tensor ((H + My) Mx values of a pixel, W pixels): boxes of 64 x 128 (one
         // K-block of A: 128 pixel rows of 128 bytes), 128-byte swizzle
