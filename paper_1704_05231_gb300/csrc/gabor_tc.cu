@@ -1313,12 +1313,23 @@ __global__ void k_minmax(const float *__restrict__ img, int64_t pitch, int H, in
 {
     pdl_launch_dependents();   // k_ones may run alongside (it waits for this grid before it ends)
     unsigned lo = 0xffffffffu, hi = 0u;
-    for (int y = blockIdx.y; y < H; y += gridDim.y)
-        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < W; x += gridDim.x * blockDim.x) {
+    const int64_t ystep = (int64_t)gridDim.y * pitch;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < W; x += gridDim.x * blockDim.x) {
+        int y = blockIdx.y;
+        // four rows' loads in flight per thread
+        for (; y + 3 * (int)gridDim.y < H; y += 4 * (int)gridDim.y) {
+            const float *p = img + (int64_t)y * pitch + x;
+            const unsigned k0 = fkey(__ldg(p)), k1 = fkey(__ldg(p + ystep)), k2 = fkey(__ldg(p + 2 * ystep)),
+                           k3 = fkey(__ldg(p + 3 * ystep));
+            lo = min(lo, min(min(k0, k1), min(k2, k3)));
+            hi = max(hi, max(max(k0, k1), max(k2, k3)));
+        }
+        for (; y < H; y += gridDim.y) {
             const unsigned k = fkey(__ldg(img + (int64_t)y * pitch + x));
             lo = min(lo, k);
             hi = max(hi, k);
         }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));

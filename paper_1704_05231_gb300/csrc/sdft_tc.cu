@@ -614,9 +614,17 @@ __global__ void k_absmax(const float *__restrict__ img, int64_t pitch, int H, in
     pdl_launch_dependents();   // k_unfold may launch now (it waits for this grid before reading the max)
     __shared__ float wmax[8];
     float m = 0.f;
-    for (int y = blockIdx.y; y < H; y += gridDim.y)
-        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < W; x += gridDim.x * blockDim.x)
-            m = fmaxf(m, fabsf(__ldg(img + (int64_t)y * pitch + x)));
+    const int64_t ystep = (int64_t)gridDim.y * pitch;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < W; x += gridDim.x * blockDim.x) {
+        int y = blockIdx.y;
+        // four rows' loads in flight per thread
+        for (; y + 3 * (int)gridDim.y < H; y += 4 * (int)gridDim.y) {
+            const float *p = img + (int64_t)y * pitch + x;
+            const float v0 = __ldg(p), v1 = __ldg(p + ystep), v2 = __ldg(p + 2 * ystep), v3 = __ldg(p + 3 * ystep);
+            m = fmaxf(m, fmaxf(fmaxf(fabsf(v0), fabsf(v1)), fmaxf(fabsf(v2), fabsf(v3))));
+        }
+        for (; y < H; y += gridDim.y) m = fmaxf(m, fabsf(__ldg(img + (int64_t)y * pitch + x)));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
