@@ -297,7 +297,7 @@ int oracle_sdft_direct(const double *f_re, const double *f_im, int H, int W,
 /*
  * ---------------------------------------------------------------------------------------
  * Recursive (IIR) Gaussian variant of Algorithm 1 (Sec. II adopts the recursive Gaussian of
- * Young and van Vliet; approximate, judged by SER against the FIR result, Sec. IV-C).
+ * Young and van Vliet; approximate, assessed by SER against the FIR result, Sec. IV-C).
  *
  * The smoother is the third-order forward / backward recursion of Young and van Vliet,
  * "Recursive implementation of the Gaussian filter", Signal Processing 44 (1995): with

@@ -1,7 +1,7 @@
 // Recursive-Gaussian variant of the FP32 bank (GB_SMOOTHER_IIR): Algorithm 1 with both 1-D
 // Gaussian passes replaced by the third-order forward / backward recursion of Young and van
 // Vliet (Signal Processing, 1995), the smoother Sec. II adopts.  Its cost per output does not
-// depend on sigma; it approximates S_sigma (Sec. IV-C judges it by SER against the FIR bank).
+// depend on sigma; it approximates S_sigma (Sec. IV-C assesses it by SER against the FIR bank).
 //
 //   row kernel     one lane per (unit, image row), 32 rows per warp.  Rows are staged through
 //                  32 x 32 shared-memory tiles so that global loads and stores stay coalesced
