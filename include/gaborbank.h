@@ -263,28 +263,33 @@ gb_status gabor_bank_selftest_wait(gabor_bank_t h, int signal, double limit_ms, 
 
 /*
  * gabor_sdft_noalloc - the FP32 localized sliding DFT of gabor_bank_sdft (same arguments and
- * output layout, FP32 CUDA-core path) for callers that cannot allocate device memory: code
- * inside a custom allocator or memory pool that forbids cudaMalloc, or an application whose
- * device-memory budget is fixed before it starts.  No handle is needed and the call allocates
- * nothing.  The paper has no counterpart; this is a deployment convenience.
+ * output layout, FP32 CUDA-core path, zero boundary rule) for callers that cannot allocate
+ * device memory: code inside a custom allocator or memory pool that forbids cudaMalloc, or an
+ * application whose device-memory budget is fixed before it starts.  No handle is needed and
+ * the call allocates nothing.  The paper has no counterpart; this is a deployment convenience.
  *
- * Its tables (Gaussian taps and twiddles) live in one fixed 2 KiB __device__ array of the
- * library, which every GPU that loads the library holds until the process exits.  Limits:
- * My, Mx even, 2 .. 64 (GB_ERR_UNSUPPORTED beyond).  The first call on a device does a
- * one-time set-up on that device (symbol address, kernel attributes); make that first call
- * before any CUDA stream capture.  Every call rewrites the shared table, so calls that
- * overlap on the GPU (for example on two streams) race; serialise them on one stream.
- * Asynchronous like gabor_bank_sdft; errors as gabor_bank_sdft.
+ * Its tables (Gaussian taps and twiddles of both window axes) live in one fixed 2 KiB
+ * __device__ array of the library, which every GPU that loads the library holds until the
+ * process exits.  Limits: My, Mx even, 2 .. 64 (GB_ERR_UNSUPPORTED beyond).  The first call on
+ * a device does a one-time set-up on that device (the array's device address, kernel
+ * attributes) under a process-wide mutex; make that first call before any CUDA stream
+ * capture.  Every call then enqueues two kernels on `stream`: one that rewrites the whole
+ * table (1600 bytes, from by-value parameters; no host-to-device copy) and the SDFT kernel.
+ * Because every call rewrites the shared table, calls that overlap on the GPU (for example on
+ * two streams) race; serialise them on one stream.  Asynchronous like gabor_bank_sdft; argument
+ * checks and errors as gabor_bank_sdft.
  */
 gb_status gabor_sdft_noalloc(const float *d_img, int H, int W, int64_t pitch, double sigma,
                              int My, int Mx, int half_spectrum, void *d_out, void *stream);
 
 /*
  * gabor_bank_workspace_bytes - device bytes of intermediate a GB_FP16_TC / GB_BF16_TC handle
- * needs to filter an H x W image: the FP16 column signals of Eq. 10 between the row and the
- * column pass (4 signals per paired orientation, 2 per unpaired one, each image column
- * padded by zero rows above and below).  0 for FP32 handles (their intermediates stay on
- * chip) and for invalid arguments.  Host-only; no device work.
+ * needs to filter an H x W image: the FP16 signals between the row and the column pass (by
+ * default Re J and Im J of every horizontal pass, Eq. 5-6; under GB_OPT_ROW_PASS = 1 the
+ * column signals of Eq. 10), each image column padded by zero rows above and below, followed
+ * by the bank's response to a constant image, one row and one column table per horizontal
+ * pass.  Sized for the larger of the two forms.  0 for FP32 handles (their intermediates stay
+ * on chip) and for invalid arguments.  Host-only; no device work.
  */
 int64_t gabor_bank_workspace_bytes(gabor_bank_t h, int H, int W);
 

@@ -278,27 +278,6 @@ gb_status ensure_sdft_tables(gabor_bank *h, double sigma, int My, int Mx, cudaSt
     return GB_OK;
 }
 
-gb_status check_sticky()
-{
-    cudaError_t e = cudaPeekAtLastError();
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(GB_ERR_CUDA, std::string("earlier CUDA error: ") + cudaGetErrorString(e));
-    }
-    return GB_OK;
-}
-
-gb_status validate_image(const void *img, int H, int W, int64_t pitch, const void *out)
-{
-    if (!img || !out) return fail(GB_ERR_INVALID_ARG, "NULL image or output pointer");
-    if (H <= 0 || W <= 0) return fail(GB_ERR_INVALID_ARG, "H and W must be positive");
-    if (pitch < W) return fail(GB_ERR_INVALID_ARG, "pitch must be >= W");
-    if ((int64_t)H * pitch > (int64_t)1 << 40) return fail(GB_ERR_INVALID_ARG, "image too large");
-    if (reinterpret_cast<uintptr_t>(img) % 4) return fail(GB_ERR_INVALID_ARG, "image not 4-byte aligned");
-    if (reinterpret_cast<uintptr_t>(out) % 8) return fail(GB_ERR_INVALID_ARG, "output not 8-byte aligned");
-    return GB_OK;
-}
-
 // FP32 bank items take two unpaired units of a frequency together ("twins") under the
 // modulated-tap row pass: two row passes, and column passes that fill both halves of a CTA.
 // Units of a frequency are ordered paired first; unpaired ones are twinned in order.
@@ -826,6 +805,27 @@ gb_status filter_device(gabor_bank *h, const float *d_img, int H, int W, int64_t
 namespace gb {
 // Records the message returned by gabor_bank_last_error() on this host thread.
 void set_last_error(const char *msg) { g_err = msg; }
+
+gb_status check_sticky()
+{
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GB_ERR_CUDA, std::string("earlier CUDA error: ") + cudaGetErrorString(e));
+    }
+    return GB_OK;
+}
+
+gb_status validate_image(const void *img, int H, int W, int64_t pitch, const void *out)
+{
+    if (!img || !out) return fail(GB_ERR_INVALID_ARG, "NULL image or output pointer");
+    if (H <= 0 || W <= 0) return fail(GB_ERR_INVALID_ARG, "H and W must be positive");
+    if (pitch < W) return fail(GB_ERR_INVALID_ARG, "pitch must be >= W");
+    if ((int64_t)H * pitch > (int64_t)1 << 40) return fail(GB_ERR_INVALID_ARG, "image too large");
+    if (reinterpret_cast<uintptr_t>(img) % 4) return fail(GB_ERR_INVALID_ARG, "image not 4-byte aligned");
+    if (reinterpret_cast<uintptr_t>(out) % 8) return fail(GB_ERR_INVALID_ARG, "output not 8-byte aligned");
+    return GB_OK;
+}
 
 // The driver's tensor-map encoder, fetched once through the runtime (no link against the
 // driver library).

@@ -233,6 +233,10 @@ cudaError_t launch_build_gabor_tables(const double *d_unit_w, int nunits, int Wc
 cudaError_t launch_build_taps(const double *d_sigma, const int *d_lo, const int *d_T, int nfreq,
                               int tpad_max, float *taps, cudaStream_t st);
 cudaError_t launch_build_twiddles(int M, float2 *tw, cudaStream_t st);
+// Taps and twiddles of both SDFT window axes from by-value parameters: taps[2][tap_stride]
+// (S(t - M/2), zero from t = M on), tw[2][tw_stride] ((cos, sin)(2 pi j / M), j < M).
+cudaError_t launch_build_sdft_tables(double sigma, int Mx, int My, int tap_stride, int tw_stride, float *taps,
+                                     float2 *tw, cudaStream_t st);
 // Tile geometry of the FP32 bank kernel for radius R (tile_rows = 0: automatic).
 FreqDev gabor_fp32_geometry(int R, int tile_rows, bool pipelined, bool mtaps, int ctas);
 size_t gabor_fp32_smem_budget(int ctas);
@@ -275,6 +279,11 @@ cudaError_t launch_fma_peak(float *out, int blocks, int iters, int packed, cudaS
 cudaError_t launch_wait_selftest(int *status, int signal, unsigned long long limit_ns, cudaStream_t st);
 // Sets the message returned by gabor_bank_last_error() on the calling host thread.
 void set_last_error(const char *msg);
+// Argument checks shared by the entry points that take one image and one output (GB_OK or
+// GB_ERR_INVALID_ARG with the message set), and the check for a CUDA error left by earlier
+// work (GB_ERR_CUDA, cleared).
+gb_status validate_image(const void *img, int H, int W, int64_t pitch, const void *out);
+gb_status check_sticky();
 // Tensor-core SDFT (windowed-DFT contraction on tcgen05).
 bool sdft_tc_supported(int Mx, int My);
 int sdft_tc_b_bytes(int Mx, int My);

@@ -6,8 +6,10 @@
 // Here they live in one file-scope __device__ array, g_noalloc_scratch, instead of in memory
 // owned by a gabor_bank handle, and the entry point needs no handle.  The array is kNoallocBytes
 // (2 KiB) on every GPU that loads the library, for the life of the process.  Each call
-// rewrites the whole table before its kernel runs; calls that overlap on the GPU (for example
-// on two streams) race on it.
+// rewrites the whole table with one small kernel before the SDFT kernel runs (two launches per
+// call, no host-to-device copy); calls that overlap on the GPU (for example on two streams)
+// race on it.
+#include <atomic>
 #include <cmath>
 #include <mutex>
 
@@ -21,45 +23,47 @@ constexpr int kNoallocMaxDevices = 64;
 constexpr int kNoallocTap = kMaxSdftM + 8;   // taps per axis (zero-padded)
 constexpr size_t kNoallocBytes = 2048;
 
-// Layout: taps_x, taps_y (kNoallocTap floats each), twiddles x, y (kMaxSdftM float2 each),
-// sigma x, y (double), lo x, y and T x, y (int).
+// Layout: taps_x, taps_y (kNoallocTap floats each), then the twiddles of x and y (kMaxSdftM
+// float2 each).  Every call writes all of it from by-value parameters.
 constexpr size_t kOffTaps = 0;
 constexpr size_t kOffTw = kOffTaps + 2 * kNoallocTap * sizeof(float);        // 576
-constexpr size_t kOffSigma = kOffTw + 2 * kMaxSdftM * sizeof(float2);        // 1600
-constexpr size_t kOffInts = kOffSigma + 2 * sizeof(double);                  // 1616
-static_assert(kOffInts + 4 * sizeof(int) <= kNoallocBytes, "scratch too small");
+static_assert(kOffTw + 2 * kMaxSdftM * sizeof(float2) <= kNoallocBytes, "scratch too small");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 struct DeviceSetup {
     unsigned char *scratch = nullptr;   // device address of g_noalloc_scratch
     int sm_count = 0;
-    bool ready = false;
 };
 
 DeviceSetup g_setup[kNoallocMaxDevices];
+std::atomic<bool> g_ready[kNoallocMaxDevices];
 std::mutex g_setup_mutex;
 
 // Once per device, with that device current: the device address of the scratch array (the
-// host-side name is only a stand-in) and the kernel attributes.
+// host-side name is only a stand-in) and the kernel attributes.  The first call on a device
+// takes a process-wide mutex; later calls read the recorded set-up without locking.
 gb_status setup_device(int dev, DeviceSetup *out)
 {
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    DeviceSetup &d = g_setup[dev];
-    if (!d.ready) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = sdft_fp32_prepare();
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            set_last_error((std::string("gabor_sdft_noalloc set-up: ") + cudaGetErrorString(e)).c_str());
-            return GB_ERR_CUDA;
+    if (!g_ready[dev].load(std::memory_order_acquire)) {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        if (!g_ready[dev].load(std::memory_order_relaxed)) {
+            DeviceSetup d;
+            void *ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess) e = sdft_fp32_prepare();
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                set_last_error((std::string("gabor_sdft_noalloc set-up: ") + cudaGetErrorString(e)).c_str());
+                return GB_ERR_CUDA;
+            }
+            d.scratch = static_cast<unsigned char *>(ptr);
+            g_setup[dev] = d;
+            g_ready[dev].store(true, std::memory_order_release);
         }
-        d.scratch = static_cast<unsigned char *>(ptr);
-        d.ready = true;
     }
-    *out = d;
+    *out = g_setup[dev];
     return GB_OK;
 }
 
@@ -78,11 +82,9 @@ using namespace gb;
 extern "C" gb_status gabor_sdft_noalloc(const float *d_img, int H, int W, int64_t pitch, double sigma,
                                          int My, int Mx, int half_spectrum, void *d_out, void *stream)
 {
-    if (!d_img || !d_out) return fail_arg(GB_ERR_INVALID_ARG, "NULL image or output pointer");
-    if (H <= 0 || W <= 0) return fail_arg(GB_ERR_INVALID_ARG, "H and W must be positive");
-    if (pitch < W) return fail_arg(GB_ERR_INVALID_ARG, "pitch must be >= W");
-    if (reinterpret_cast<uintptr_t>(d_img) % 4) return fail_arg(GB_ERR_INVALID_ARG, "image not 4-byte aligned");
-    if (reinterpret_cast<uintptr_t>(d_out) % 8) return fail_arg(GB_ERR_INVALID_ARG, "output not 8-byte aligned");
+    // the same argument checks, in the same order and with the same messages, as gabor_bank_sdft
+    gb_status s = validate_image(d_img, H, W, pitch, d_out);
+    if (s != GB_OK) return s;
     if (!std::isfinite(sigma) || sigma <= 0.0) return fail_arg(GB_ERR_INVALID_ARG, "sigma must be positive");
     if (My < 2 || Mx < 2) return fail_arg(GB_ERR_INVALID_ARG, "window sides must be >= 2");
     if ((My & 1) || (Mx & 1)) return fail_arg(GB_ERR_UNSUPPORTED, "odd window sizes are not supported");
@@ -95,23 +97,17 @@ extern "C" gb_status gabor_sdft_noalloc(const float *d_img, int H, int W, int64_
         cudaGetLastError();
         return fail_arg(GB_ERR_CUDA, "gabor_sdft_noalloc: no usable current device");
     }
+    s = check_sticky();
+    if (s != GB_OK) return s;
     DeviceSetup d;
-    gb_status s = setup_device(dev, &d);
+    s = setup_device(dev, &d);
     if (s != GB_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     float *taps = reinterpret_cast<float *>(d.scratch + kOffTaps);
     float2 *tw = reinterpret_cast<float2 *>(d.scratch + kOffTw);
-    double *d_sigma = reinterpret_cast<double *>(d.scratch + kOffSigma);
-    int *d_ints = reinterpret_cast<int *>(d.scratch + kOffInts);
-    // Parameters of this call (pageable source: staged before the call returns).
-    const double sg[2] = {sigma, sigma};
-    const int ints[4] = {Mx / 2, My / 2, Mx, My};   // lo x, lo y, T x, T y
-    e = cudaMemcpyAsync(d_sigma, sg, sizeof(sg), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ints, ints, sizeof(ints), cudaMemcpyHostToDevice, st);
-    // Every table entry is rewritten: taps beyond T are written as zeros.
-    if (e == cudaSuccess) e = launch_build_taps(d_sigma, d_ints, d_ints + 2, 2, kNoallocTap, taps, st);
-    if (e == cudaSuccess) e = launch_build_twiddles(Mx, tw, st);
-    if (e == cudaSuccess) e = launch_build_twiddles(My, tw + kMaxSdftM, st);
+    // One small kernel rewrites the whole table (1600 bytes) from by-value parameters: no host
+    // copy, nothing left over from an earlier call with another window.
+    e = launch_build_sdft_tables(sigma, Mx, My, kNoallocTap, kMaxSdftM, taps, tw, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail_arg(GB_ERR_CUDA, "gabor_sdft_noalloc: table build failed");

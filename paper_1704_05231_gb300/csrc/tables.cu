@@ -36,6 +36,12 @@ __global__ void k_build_gabor_tables(const double *__restrict__ unit_w, int nuni
     }
 }
 
+// S(d) = exp(-d^2 / (2 sigma^2)) / (sqrt(2 pi) sigma) in FP64, rounded to FP32 (Sec. II).
+__device__ __forceinline__ float gauss_tap(double d, double sg)
+{
+    return (float)(exp(-(d * d) / (2.0 * sg * sg)) / (2.5066282746310002 * sg));
+}
+
 // taps[s][t] = S_sigma_s(t - lo_s) for t < T_s, zero for T_s <= t < tpad_max.
 __global__ void k_build_taps(const double *__restrict__ sigma, const int *__restrict__ lo,
                              const int *__restrict__ T, int nfreq, int tpad_max,
@@ -44,14 +50,7 @@ __global__ void k_build_taps(const double *__restrict__ sigma, const int *__rest
     const int n = nfreq * tpad_max;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int s = i / tpad_max, t = i % tpad_max;
-        float v = 0.f;
-        if (t < T[s]) {
-            const double d = (double)(t - lo[s]);
-            const double sg = sigma[s];
-            // S(d) = exp(-d^2 / (2 sigma^2)) / (sqrt(2 pi) sigma)
-            v = (float)(exp(-(d * d) / (2.0 * sg * sg)) / (2.5066282746310002 * sg));
-        }
-        taps[i] = v;
+        taps[i] = t < T[s] ? gauss_tap((double)(t - lo[s]), sigma[s]) : 0.f;
     }
 }
 
@@ -63,6 +62,38 @@ __global__ void k_build_twiddles(int M, float2 *__restrict__ tw)
         sincospi(2.0 * (double)j / (double)M, &s, &c);
         tw[j] = make_float2((float)c, (float)s);
     }
+}
+
+// Every table of the FP32 SDFT from parameters passed by value (no device inputs): taps of
+// both window axes, taps[a][t] = S_sigma(t - M_a / 2) for t < M_a and 0 up to tap_stride, and
+// the twiddles tw[a][j] = (cos, sin)(2 pi j / M_a) for j < M_a and (1, 0) up to tw_stride
+// (a = 0: x, M_0 = Mx; a = 1: y, M_1 = My).  The same values as k_build_taps and
+// k_build_twiddles, entry for entry.
+__global__ void k_build_sdft_tables(double sigma, int Mx, int My, int tap_stride, int tw_stride,
+                                    float *__restrict__ taps, float2 *__restrict__ tw)
+{
+    const int ntap = 2 * tap_stride, n = ntap + 2 * tw_stride;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (i < ntap) {
+            const int ax = i / tap_stride, t = i % tap_stride;
+            const int M = ax ? My : Mx;
+            taps[i] = t < M ? gauss_tap((double)(t - M / 2), sigma) : 0.f;
+        } else {
+            const int k = i - ntap, ax = k / tw_stride, j = k % tw_stride;
+            const int M = ax ? My : Mx;
+            double sn = 0.0, c = 1.0;
+            if (j < M) sincospi(2.0 * (double)j / (double)M, &sn, &c);
+            tw[k] = make_float2((float)c, (float)sn);
+        }
+    }
+}
+
+cudaError_t launch_build_sdft_tables(double sigma, int Mx, int My, int tap_stride, int tw_stride, float *taps,
+                                     float2 *tw, cudaStream_t st)
+{
+    const int n = 2 * (tap_stride + tw_stride);
+    k_build_sdft_tables<<<(n + 255) / 256, 256, 0, st>>>(sigma, Mx, My, tap_stride, tw_stride, taps, tw);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_build_gabor_tables(const double *d_unit_w, int nunits, int Wcap, int Hcap, int mg,
