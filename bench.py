@@ -89,8 +89,8 @@ def fp32_peak_tflops(torch):
         from paper_1704_05231_gb300.bank import fp32_fma_peak
         m = fp32_fma_peak()
         nom, sms, mhz = fp32_nominal_tflops(torch)
-        _FP32_PEAK = (m["peak"], f"measured by the FMA probe (scalar {m['scalar']:.1f}, packed FP32x2 {m['packed']:.1f} "
-                                 f"TFLOP/s); nominal {sms} SMs x 128 lanes x 2 x {mhz:.0f} MHz = {nom:.1f}")
+        _FP32_PEAK = (m["peak"], f"FMA probe: scalar {m['scalar']:.1f}, packed {m['packed']:.1f} TFLOP/s; "
+                                 f"nominal {nom:.1f} ({sms} SMs, {mhz:.0f} MHz)")
     return _FP32_PEAK
 
 
@@ -229,7 +229,7 @@ def cpu_baseline(img, thetas, omegas, sigmas, seconds):
     return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_px} random pixels x {len(thetas) * len(omegas)} filters of the 1024x1024 "
                       f"bank (direct FP64 sums), {el:.1f} s",
-            "one_core": {"value": v1, "sample": f"{n1} random pixels, {el1:.1f} s, 1 thread"}}
+            "one_core": {"value": v1, "sample": f"{n1} px, {el1:.1f} s"}}
 
 
 def run_reference(args):
@@ -284,12 +284,40 @@ def time_device(torch, fn, steps, warmup, flush, stream):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     for k in range(steps):
-        flush.zero_()
+        if flush is not None:
+            flush.zero_()
         starts[k].record(stream)
         fn()
         ends[k].record(stream)
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def c1_leg(torch, steps, warmup, stream):
+    """The smallest bank (256 x 256 uniform image, seed 0; 4 orientations x 2 frequencies,
+    sigma 4, radius 12): latency-bound, working set inside L2, so no flush between steps.
+    Timed per call and as a replayed one-call CUDA graph (no host launch cost)."""
+    from paper_1704_05231_gb300 import GaborBank, synth
+    from paper_1704_05231_gb300.bank import capture_graph
+    Hc = Wc = 256
+    img = torch.from_numpy(synth.uniform01(0, Hc, Wc)).cuda()
+    th = [0.0, math.pi / 4, math.pi / 2, 3 * math.pi / 4]
+    om = [math.pi / 4, math.pi / 8]
+    n_out = len(th) * len(om) * Hc * Wc
+    res = {"workload": "256x256 uniform [0,1) (seed 0), 4 orientations x 2 frequencies, sigma 4, radius 12; "
+                       "L2-resident, latency-bound", "outputs_per_step": n_out}
+    for prec in ("fp32", "fp16_tc"):
+        gbk = GaborBank(th, om, [4.0, 4.0], precision=prec, max_shape=(Hc, Wc))
+        out = torch.empty(gbk.out_shape(Hc, Wc), dtype=torch.complex64, device="cuda")
+        ms = statistics.median(time_device(torch, lambda: gbk.filter(img, out), max(steps, 50), warmup, None,
+                                           stream))
+        graph = capture_graph(lambda: gbk.filter(img, out))
+        gms = statistics.median(time_device(torch, graph.replay, max(steps, 50), warmup, None, stream))
+        gbk.device_status()
+        res[prec] = {"us": ms * 1e3, "graph_us": gms * 1e3, "value": n_out / (gms * 1e-3), "unit": UNIT}
+        del graph
+        gbk.close()
+    return res
 
 
 def bank_tc_leg(torch, d_img, thetas, omegas, sigmas, ref_out, n_out, steps, warmup, flush, stream):
@@ -491,6 +519,96 @@ def serve_leg(args):
     return res
 
 
+LEG_KEYS = ("c1", "tc", "sdft", "ablation", "batch", "iir", "serve")
+
+
+def _r(x, nd=4):
+    """x rounded to nd significant digits (None and non-numbers unchanged)."""
+    if isinstance(x, bool) or not isinstance(x, (int, float)) or x == 0 or x != x:
+        return x
+    return float(f"{x:.{nd}g}")
+
+
+def _g(x):
+    """outputs/s in units of 1e9."""
+    return _r(x / 1e9) if isinstance(x, (int, float)) else x
+
+
+def _get(d, *path):
+    for p in path:
+        if not isinstance(d, dict) or p not in d:
+            return None
+        d = d[p]
+    return d
+
+
+def leg_summary(line):
+    """One short entry per leg: times in ms (us where named), rates in 1e9 outputs/s (gout_s),
+    fractions of the stated roof."""
+    out = {}
+    c1 = line.get("c1")
+    if c1:
+        for p in ("fp32", "fp16_tc"):
+            if p in c1:
+                out[f"c1_256_{p}"] = {"us": _r(c1[p]["us"]), "graph_us": _r(c1[p]["graph_us"]),
+                                      "gout_s": _g(c1[p]["value"])}
+    tc = line.get("tc")
+    if tc:
+        for p, e in tc.items():
+            if "error" in e:
+                out[f"bank_{p}"] = {"error": e["error"][:80]}
+            else:
+                out[f"bank_{p}"] = {"ms": _r(e["ms_per_step"]), "gout_s": _g(e["value"]),
+                                    "hbm_frac": _r(e["roofline"]["frac"], 3), "err_vs_fp32": _r(e["rel_err_vs_fp32"], 3)}
+    sd = line.get("sdft")
+    if sd:
+        for p in ("fp32", "fp16_tc", "bf16_tc"):
+            if p in sd:
+                e = sd[p]
+                out[f"sdft512_m16_{p}"] = {"ms": _r(e["ms_per_step"]), "gout_s": _g(e["value"]),
+                                           "hbm_frac": _r(e["roofline"]["frac"], 3)}
+        if "reuse" in sd:
+            out["sdft_reuse_speedup"] = _r(sd["reuse"]["speedup_from_reuse"], 3)
+        if "fill_same_bytes" in sd:
+            out["sdft_fill_gbs"] = _r(sd["fill_same_bytes"]["GB/s"])
+    ab = line.get("ablation")
+    if ab:
+        out["bank_reuse_speedup"] = {p: _r(e["speedup_from_reuse"], 3) for p, e in ab.items()}
+    bt = line.get("batch")
+    if bt:
+        for p in ("fp32", "fp16_tc", "bf16_tc"):
+            e = bt.get(p)
+            if e:
+                out[f"batch64_{p}"] = {"ms": _r(e["ms_per_step"]), "gout_s": _g(e["value"]),
+                                       "launches": e.get("launches_per_step"),
+                                       "frac": _r(_get(e, "roofline", "frac"), 3),
+                                       "bound": _get(e, "roofline", "bound")}
+    ir = line.get("iir")
+    if ir:
+        out["iir"] = {"bank_ms": _r(_get(ir, "paper_bank", "ms_per_step")),
+                      "batch64_ms": _r(_get(ir, "batch_64", "ms_per_step"))}
+    sv = line.get("serve")
+    if sv:
+        for p in ("fp32", "fp16_tc"):
+            e = sv.get(p)
+            if e:
+                out[f"serve_{p}"] = {"p50_ms": _r(e["p50_ms"]), "p99_ms": _r(e["p99_ms"]),
+                                     "gout_s": _g(e["outputs_per_s"]), "sat_req_s": _r(e["saturation_req_s"]),
+                                     "p99_ms_0.9x": _r(_get(e, "0.9x", "p99_ms"))}
+    return out
+
+
+def compact_line(line):
+    """The stdout JSON line: every contract key, legs replaced by their summary."""
+    c = {k: v for k, v in line.items() if k not in LEG_KEYS}
+    if "roofline" in c:
+        c["roofline"] = {k: (_r(v) if isinstance(v, float) else v) for k, v in c["roofline"].items()}
+    legs = leg_summary(line)
+    if legs:
+        c["legs"] = legs
+    return c
+
+
 def max_over_ranks(ms, dist, device):
     """The slowest rank's step time (ms): every replica runs the same work, so the job's
     step ends when the last one does."""
@@ -595,6 +713,8 @@ def run_ours(args):
             "clocks": clocks,
             "wall_s": wall}
     legs = set() if args.no_extra else set(args.legs.split(","))
+    if "c1" in legs:
+        line["c1"] = c1_leg(torch, args.steps, args.warmup, stream)
     if "tc" in legs:
         line["tc"] = bank_tc_leg(torch, d_img, thetas, omegas, sigmas, out, n_out, args.steps, args.warmup, flush,
                                  stream)
@@ -611,7 +731,12 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(img, thetas, omegas, sigmas, args.cpu_seconds)
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        # every leg in full on stderr; the stdout line keeps the headline and one compact
+        # summary per leg, short enough to survive a log tail of a few kilobytes
+        for k in LEG_KEYS:
+            if k in line:
+                print("leg " + json.dumps({k: line[k]}), file=sys.stderr, flush=True)
+        print(json.dumps(compact_line(line)), flush=True)
     gbk.close()
     if dist:
         dist.destroy_process_group()
@@ -629,8 +754,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-tune", action="store_true", help="default tile geometry instead of the autotuner's")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream leg")
-    ap.add_argument("--legs", default="tc,sdft,ablation,batch,iir,serve",
-                    help="comma list of extra legs: tc, sdft, ablation, batch, iir, serve")
+    ap.add_argument("--legs", default="c1,tc,sdft,ablation,batch,iir,serve",
+                    help="comma list of extra legs: c1, tc, sdft, ablation, batch, iir, serve")
     ap.add_argument("--serve-n", type=int, default=2000, help="measured requests of the served stream")
     ap.add_argument("--serve-warm", type=int, default=200)
     args = ap.parse_args()

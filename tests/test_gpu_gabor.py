@@ -78,18 +78,24 @@ def test_c2_bank_reduced_size_full_parity(torch_cuda):
     assert e <= FP32_TOL
 
 
-def test_c2_full_size_sampled(torch_cuda):
+@pytest.fixture(scope="module")
+def c2_full():
+    """The paper-size bank's image (1024 x 1024, seed 0) and its FP64 oracle result in full:
+    the direct 2-D sum of Eq. 1 at all 25.2 M outputs (all host cores)."""
     img = synth.paper_like(0, 1024, 1024)
     th, om, sg = c2_bank()
+    return img, oracle.gabor_bank(img, th, om, sg)
+
+
+def test_c2_full_size_full_oracle(torch_cuda, c2_full):
+    # The benchmark's workload, every output against the oracle; scale = max|oracle|.
+    img, ref = c2_full
+    th, om, sg = c2_bank()
     got = run_bank(torch_cuda, img, th, om, sg)
-    rng = np.random.default_rng(11)
-    xs, ys = sample_points(rng, 1024, 1024, 1500)
-    ref = oracle.gabor_bank(img, th, om, sg, points=(xs, ys))
-    sub = got[:, :, ys, xs]
-    # scale: max|out| of the whole GPU result (the result tensor), checked against the oracle's
-    scale = float(np.max(np.abs(got)))
-    assert float(np.max(np.abs(ref))) <= scale * (1 + 1e-4)
-    assert float(np.max(np.abs(sub - ref))) <= FP32_TOL * scale
+    assert np.all(np.isfinite(got))
+    e = rel_err(got, ref)
+    print("C2 1024^2 FP32 rel err (full oracle)", e, "worst plane", max(plane_rel_errs(got, ref)))
+    assert e <= FP32_TOL
 
 
 def test_orientation_order_and_reuse_ablation(torch_cuda):
@@ -172,18 +178,15 @@ def test_tc_bank_ragged_and_c2_bank(torch_cuda, precision, H, W):
 
 
 @pytest.mark.parametrize("precision", ["fp16_tc"])
-def test_tc_bank_c2_full_size_vs_fp32_and_oracle(torch_cuda, precision):
+def test_tc_bank_c2_full_size_full_oracle(torch_cuda, c2_full, precision):
     from tests.helpers import TC_TOL
-    img = synth.paper_like(0, 1024, 1024)
+    img, ref = c2_full
     th, om, sg = c2_bank()
     got = run_bank(torch_cuda, img, th, om, sg, precision=precision)
-    f32 = run_bank(torch_cuda, img, th, om, sg)
-    assert rel_err(got, f32) <= TC_TOL
-    rng = np.random.default_rng(13)
-    xs, ys = sample_points(rng, 1024, 1024, 800)
-    ref = oracle.gabor_bank(img, th, om, sg, points=(xs, ys))
-    scale = float(np.max(np.abs(f32)))
-    assert float(np.max(np.abs(got[:, :, ys, xs] - ref))) <= TC_TOL * scale
+    assert np.all(np.isfinite(got))
+    e = rel_err(got, ref)
+    print("C2 1024^2", precision, "rel err (full oracle)", e, "worst plane", max(plane_rel_errs(got, ref)))
+    assert e <= TC_TOL
 
 
 def test_tc_bank_unpaired_orientations_and_reuse_off(torch_cuda):
@@ -296,20 +299,25 @@ def test_row_pass_forms_match_oracle(torch_cuda, row_pass, boundary, H, W):
 
 
 @pytest.mark.parametrize("row_pass", [1, 2])
-def test_row_pass_forms_c2_and_large_radius_sampled(torch_cuda, row_pass):
+def test_row_pass_forms_c2_full_and_large_radius_sampled(torch_cuda, c2_full, row_pass):
     from paper_1704_05231_gb300 import GaborBank
     torch = torch_cuda
+    img, ref = c2_full
+    with GaborBank(*c2_bank()) as gbk:
+        gbk.set_option("row_pass", row_pass)
+        got = gbk.filter(torch.from_numpy(img).cuda()).cpu().numpy()
+    assert rel_err(got, ref) <= FP32_TOL
+    # R = 159 (the largest FP32 radius) on sampled pixels; scale = max|oracle| over the samples
     rng = np.random.default_rng(5)
-    for (H, W), (th, om, sg) in [((1024, 1024), c2_bank()),
-                                 ((333, 257), ([0.3, math.pi - 0.3, math.pi / 2], [0.05], [53.0]))]:
-        img = synth.paper_like(2, H, W)
-        with GaborBank(th, om, sg) as gbk:
-            gbk.set_option("row_pass", row_pass)
-            got = gbk.filter(torch.from_numpy(img).cuda()).cpu().numpy()
-        xs, ys = sample_points(rng, H, W, 300)
-        ref = oracle.gabor_bank(img, th, om, sg, points=(xs, ys))
-        scale = float(np.max(np.abs(got)))
-        assert float(np.max(np.abs(got[:, :, ys, xs] - ref))) <= FP32_TOL * scale
+    th, om, sg = [0.3, math.pi - 0.3, math.pi / 2], [0.05], [53.0]
+    img = synth.paper_like(2, 333, 257)
+    with GaborBank(th, om, sg) as gbk:
+        gbk.set_option("row_pass", row_pass)
+        got = gbk.filter(torch.from_numpy(img).cuda()).cpu().numpy()
+    xs, ys = sample_points(rng, 333, 257, 300)
+    ref = oracle.gabor_bank(img, th, om, sg, points=(xs, ys))
+    assert np.all(np.isfinite(got))
+    assert rel_err(got[:, :, ys, xs], ref) <= FP32_TOL
 
 
 def test_row_pass_forms_pipelined_bitwise(torch_cuda):
@@ -407,5 +415,6 @@ def test_tc_bank_large_radius_sampled(torch_cuda, row_pass, boundary):
         assert e <= TC_TOL
         xs, ys = sample_points(rng, H, W, 200)
         ref = oracle.gabor_bank(img, th, om, sg, points=(xs, ys), boundary=boundary)
-        scale = float(np.max(np.abs(f32)))
-        assert float(np.max(np.abs(got[:, :, ys, xs] - ref))) <= TC_TOL * scale
+        # scale = max|oracle| over the samples (at most the result's max: a stricter bound)
+        assert rel_err(got[:, :, ys, xs], ref) <= TC_TOL
+        assert rel_err(f32[:, :, ys, xs], ref) <= FP32_TOL

@@ -99,3 +99,96 @@ def test_served_results_match_oracle(pool, precision, tol):
     assert rel_err(got[0], ref0) <= tol
     ref1 = oracle.sdft(np.ascontiguousarray(imgs[1]), 4.0, 16)
     assert rel_err(got[1], ref1) <= tol
+
+
+# ------------------------------------------------ the served-stream workload's own sizes
+
+@pytest.fixture(scope="module")
+def pool4096():
+    """The benchmark's source images: four device-resident 4096 x 4096 1/f-noise images."""
+    from paper_1704_05231_gb300.serve import ImagePool
+    return ImagePool(n=4, side=4096, seed=3)
+
+
+def _paper_stream(n_use):
+    """The first n_use requests of the benchmark's served stream (seed 2: sides log-uniform
+    on [256, 4096], banks of 4-8 orientations x 2-5 octaves, 10% 16 x 16 SDFT requests)."""
+    from paper_1704_05231_gb300.serve import served_stream
+    reqs = served_stream(seed=2, n=2200)[:n_use]
+    for i, r in enumerate(reqs):
+        r["rid"] = i
+    return reqs
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", FP32_TOL), ("fp16_tc", TC_TOL)])
+def test_served_stream_seeded_sample_matches_oracle(pool4096, precision, tol):
+    # 400 requests of the served stream run as a mix (arrivals at 3000 req/s, four slots);
+    # a seeded 2% sample of them (at least two SDFT requests) is checked against the FP64
+    # oracle on 256 seeded pixels per request, all planes; scale = max|oracle| over the samples.
+    import torch
+    from paper_1704_05231_gb300.serve import Server, with_rate
+    from tests.helpers import sample_points
+    reqs = _paper_stream(400)
+    rng = np.random.default_rng(12)
+    banks = [i for i, r in enumerate(reqs) if r["kind"] == "bank"]
+    sdfts = [i for i, r in enumerate(reqs) if r["kind"] == "sdft"]
+    pick = sorted(set(rng.choice(banks, 6, replace=False).tolist()) | set(rng.choice(sdfts, 2, replace=False).tolist()))
+    pts = {i: sample_points(rng, reqs[i]["H"], reqs[i]["W"], 256) for i in pick}
+    got = {}
+
+    def on_done(req, out):
+        i = req["rid"]
+        if i in pts:
+            xs, ys = pts[i]
+            ix = torch.from_numpy(ys.astype(np.int64) * req["W"] + xs).to(out.device)
+            got[i] = out.reshape(out.shape[0], out.shape[1], -1)[:, :, ix].cpu().numpy()
+            assert bool(torch.isfinite(torch.view_as_real(out)).all()), i
+
+    srv = Server(precision=precision, slots=4, budget_bytes=64 << 30, max_side=4096, pool=pool4096)
+    try:
+        srv.prepare(reqs)
+        recs = srv.run(with_rate(reqs, 3000.0), on_done=on_done)
+    finally:
+        srv.close()
+    assert all(r is not None and not r.get("rejected") for r in recs)
+    assert sorted(got) == pick
+    for i in pick:
+        r = reqs[i]
+        img = np.ascontiguousarray(pool4096.crop(r).cpu().numpy())
+        if r["kind"] == "bank":
+            ref = oracle.gabor_bank(img, r["thetas"], r["omegas"], r["sigmas"], points=pts[i])
+        else:
+            ref = oracle.sdft(img, r["sigma"], r["M"], points=pts[i])
+        e = rel_err(got[i], ref)
+        print(precision, "request", i, r["kind"], r["H"], r["W"], "rel err", e)
+        assert e <= tol, (i, r["kind"], r["H"], r["W"], e)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16_tc"])
+def test_alone_equals_mix_bitwise_stream_sizes(pool4096, precision):
+    # The first 24 requests of the served stream (256-4096 px sides), alone and in a mix of
+    # four slots: each result is bitwise the same.
+    import torch
+    from paper_1704_05231_gb300.serve import Server, request_outputs, with_rate
+    reqs = [r for r in _paper_stream(40) if request_outputs(r) * 8 <= (3 << 30)][:24]
+    alone, same = {}, {}
+
+    def keep(req, out):
+        alone[req["rid"]] = out.clone()
+
+    def check(req, out):
+        same[req["rid"]] = bool(torch.equal(alone[req["rid"]], out))
+
+    srv = Server(precision=precision, slots=4, budget_bytes=32 << 30, max_side=4096, pool=pool4096)
+    try:
+        srv.prepare(reqs)
+        for r in reqs:
+            srv.run([dict(r, t=0.0)], on_done=keep)
+        recs = srv.run(with_rate(reqs, 5000.0), on_done=check)
+    finally:
+        srv.close()
+    assert len(same) == len(reqs) and all(same.values()), [k for k, v in same.items() if not v]
+    overlap = sum(1 for a in recs for b in recs
+                  if a["rid"] < b["rid"] and b["t_admit"] < a["t_done"] and a["t_admit"] < b["t_done"])
+    print(precision, "stream-size requests", len(reqs), "overlapping pairs", overlap)
+    assert overlap > 0
