@@ -378,6 +378,19 @@ def sdft_leg(torch, steps, warmup, flush, stream):
         res[prec] = ent
         gbk.close()
         del out
+    # Reuse of Sec. III-B (J_u once per u for every v, F_{Mx-u,v} from J*_u) on and off: the
+    # GPU analogue of the paper's SDFT reuse gain (Table III), FP32 path
+    ent = {}
+    for reuse in (1, 0):
+        gbk = GaborBank(precision="fp32")
+        gbk.set_option("sdft_reuse", reuse)
+        out = torch.empty((16, 16, Hs, Ws), dtype=torch.complex64, device="cuda")
+        ms = statistics.mean(time_device(torch, lambda: gbk.sdft(img, 4.0, 16, out=out), steps, warmup, flush, stream))
+        ent["reuse" if reuse else "no_reuse"] = {"ms_per_step": ms, "value": n_out / (ms * 1e-3)}
+        gbk.close()
+        del out
+    ent["speedup_from_reuse"] = ent["no_reuse"]["ms_per_step"] / ent["reuse"]["ms_per_step"]
+    res["reuse"] = ent
     # Non-square windows (My x Mx, same 256 bins): the FP32 kernel always runs the horizontal
     # pass first; its FMA count differs by window orientation, its output bytes do not.
     from paper_1704_05231_gb300 import GBError
@@ -692,6 +705,20 @@ def run_ours(args):
         for _ in range(e2e_steps):
             gbk.filter_host_ptr(h_img.data_ptr(), H, W, W, h_out.data_ptr())
         e2e_s = (time.perf_counter() - t1) / e2e_steps
+        # the copy ceiling: the same host<->device bytes as plain pinned copies, no compute
+        d_out_c = torch.empty_like(out)
+        copy_stream = torch.cuda.current_stream()
+        for _ in range(2):
+            d_img.copy_(h_img, non_blocking=True)
+            h_out.copy_(d_out_c, non_blocking=True)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        for _ in range(e2e_steps):
+            d_img.copy_(h_img, non_blocking=True)
+            h_out.copy_(d_out_c, non_blocking=True)
+            copy_stream.synchronize()
+        copy_s = (time.perf_counter() - t2) / e2e_steps
+        del d_out_c
 
     flops = algorithmic_flops(thetas, omegas, sigmas)
     peak, peak_note = fp32_peak_tflops(torch)
@@ -708,7 +735,12 @@ def run_ours(args):
                          "algorithmic": "(3N+1)(2R+1) FMA per pixel per frequency"},
             "e2e": None if args.no_e2e else {
                 "value": n_out / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H * W * 4,
-                "d2h_bytes_per_step": n_out * 8, "path": "gabor_bank_filter_host, pinned buffers"},
+                "d2h_bytes_per_step": n_out * 8, "ms": e2e_s * 1e3,
+                "path": "gabor_bank_filter_host, pinned buffers (per-frequency launches, D2H overlapped)",
+                "copy_ceiling": {"ms": copy_s * 1e3, "value": n_out / copy_s,
+                                 "d2h_gb_s": n_out * 8 / copy_s / 1e9,
+                                 "note": "the same H2D + D2H bytes as plain pinned copies, no compute"},
+                "frac_of_copy_ceiling": copy_s / e2e_s},
             "gpu_launches": args.steps,
             "clocks": clocks,
             "wall_s": wall}

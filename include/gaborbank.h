@@ -102,7 +102,11 @@ gb_status gabor_bank_filter(gabor_bank_t h, const float *d_img, int H, int W, in
  * device, filters, copies the result back and synchronises `stream`.  h_out holds
  * n_freq * n_theta * H * W complex64.  Pinned (page-locked) host buffers give full copy
  * bandwidth; pageable ones work too.  Device staging buffers are owned by the handle and
- * grow on demand.  Synchronous.  Errors as gabor_bank_filter, plus GB_ERR_OUT_OF_MEMORY.
+ * grow on demand.  On FP32 handles with the plane-major layout and several frequencies the
+ * bank runs as one launch per frequency (cheapest first) and the planes of each finished
+ * frequency are copied back on a second, handle-owned stream while the next ones compute;
+ * results are bitwise those of one launch.  Synchronous.  Errors as gabor_bank_filter, plus
+ * GB_ERR_OUT_OF_MEMORY.
  */
 gb_status gabor_bank_filter_host(gabor_bank_t h, const float *h_img, int H, int W,
                                  int64_t pitch, void *h_out, void *stream);
@@ -194,7 +198,14 @@ typedef enum {
        convolution with the modulated taps S(a - Mx/2) exp(-i w0 u a) per pass: J_u is read
        straight from its ring for every v, and F_{Mx-u,v} comes from the same four real sums
        over J*_u.  Results agree to FP32 rounding.  The tensor-core SDFT is unaffected. */
-    GB_OPT_SDFT_FORM = 11
+    GB_OPT_SDFT_FORM = 11,
+    /* Reuse in the FP32 SDFT (Sec. III-B, Algorithm 2): 1 (default) computes the row pass J_u
+       once per u <= Mx/2 and reuses it for every v <= My/2, with F_{Mx-u,v} from J*_u
+       (Eq. 25-26); 0 is the paper's "no reuse" comparison: J_u is recomputed for every
+       (u, v) with u in [0, Mx), v in [0, My/2], nothing is derived from J*_u, and only the
+       conjugate fill F_{u,v} = F*_{Mx-u,My-v} stays.  Results agree to FP32 rounding.  The
+       tensor-core SDFT is unaffected. */
+    GB_OPT_SDFT_REUSE = 12
 } gb_option;
 
 /* 1-D Gaussian smoothers (GB_OPT_SMOOTHER). */

@@ -336,28 +336,31 @@ int segments_of(const gabor_bank *h, int s, int Hh, double cap)
     return std::max(1, std::min(nseg, Hh));
 }
 
-// Item-size cap of a launch over `shapes`: a third of one resident CTA's share of the launch.
-double item_cap(const gabor_bank *h, const std::vector<int64_t> &shapes)
+// Item-size cap of a launch over `shapes` (of frequency only_s, or of all when -1): a third of
+// one resident CTA's share of the launch.
+double item_cap(const gabor_bank *h, const std::vector<int64_t> &shapes, int only_s = -1)
 {
     double total = 0;
     for (size_t i = 0; i + 1 < shapes.size(); i += 2) {
         const int nstrips = (int)((shapes[i + 1] + kStripW - 1) / kStripW);
         for (int u = 0; u < (int)h->units.size(); ++u)
-            if (!twinned(h, u)) total += nstrips * item_cost(h, u, (double)shapes[i]);
+            if (!twinned(h, u) && (only_s < 0 || h->units[u].s == only_s))
+                total += nstrips * item_cost(h, u, (double)shapes[i]);
     }
     return total / std::max(1, h->sm_count * h->fp32_ctas) / 3.0;
 }
 
 // Work items of a single-image launch as groups decoded by the kernel (no device list):
-// one group per (frequency, pairing), largest item first.  Returns false when the plan has
-// more groups than the kernel arguments hold.
-bool single_image_groups(const gabor_bank *h, int H, int W, BankArgs &a, int *nitems)
+// one group per (frequency, pairing), largest item first; only frequency only_s when >= 0.
+// Returns false when the plan has more groups than the kernel arguments hold.
+bool single_image_groups(const gabor_bank *h, int H, int W, BankArgs &a, int *nitems, int only_s = -1)
 {
-    const double cap = item_cap(h, {H, W});
+    const double cap = item_cap(h, {H, W}, only_s);
     const int nstrips = (W + kStripW - 1) / kStripW;
     struct G { double cost; ItemGroup g; int n; };
     std::vector<G> gs;
     for (int s = 0; s < (int)h->freqs.size(); ++s) {
+        if (only_s >= 0 && s != only_s) continue;
         const int nseg = segments_of(h, s, H, cap);
         const int seg_len = (H + nseg - 1) / nseg;
         const int nseg_used = (H + seg_len - 1) / seg_len;
@@ -772,15 +775,18 @@ gb_status filter_device_iir(gabor_bank *h, const float *d_img, int H, int W, int
     return GB_OK;
 }
 
+// The bank on one device image; only_s >= 0 (FP32 FIR path, plane-major layout, a plan with
+// few enough groups) limits the launch to frequency only_s, whose planes it writes in place.
 gb_status filter_device(gabor_bank *h, const float *d_img, int H, int W, int64_t pitch,
-                        void *d_out, cudaStream_t st)
+                        void *d_out, cudaStream_t st, int only_s = -1)
 {
     if (h->smoother == GB_SMOOTHER_IIR) return filter_device_iir(h, d_img, H, W, pitch, d_out, st);
     if (h->prec != GB_FP32) return filter_device_tc(h, d_img, H, W, pitch, d_out, st);
     GB_TRY(ensure_tables(h, H, W, st));
     BankArgs a{};
     int n = 0;
-    if (!single_image_groups(h, H, W, a, &n)) {
+    if (!single_image_groups(h, H, W, a, &n, only_s)) {
+        if (only_s >= 0) return fail(GB_ERR_UNSUPPORTED, "per-frequency launch needs the decoded work groups");
         a.ngroups = 0;
         GB_TRY(get_worklist(h, {H, W}, const_cast<WorkItem **>(&a.items), &n));
     }
@@ -932,6 +938,8 @@ gb_status gabor_bank_destroy(gabor_bank_t h)
     h->d_sdft_ws = nullptr;
     if (h->d_stage_out) cudaFree(h->d_stage_out);
     h->d_stage_out = nullptr;
+    for (cudaEvent_t ev : h->freq_done) cudaEventDestroy(ev);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     delete h;
     return GB_OK;
 }
@@ -980,8 +988,46 @@ gb_status gabor_bank_filter_host(gabor_bank_t h, const float *h_img, int H, int 
     GB_CU(cudaMemcpy2DAsync(h->d_stage_img, (size_t)W * sizeof(float), h_img,
                             (size_t)pitch * sizeof(float), (size_t)W * sizeof(float), H,
                             cudaMemcpyHostToDevice, st));
-    GB_TRY(filter_device(h, h->d_stage_img, H, W, W, h->d_stage_out, st));
-    GB_CU(cudaMemcpyAsync(h_out, h->d_stage_out, out_bytes, cudaMemcpyDeviceToHost, st));
+    const int nf = (int)h->freqs.size();
+    BankArgs probe{};
+    int nprobe = 0;
+    const bool chunked = nf > 1 && h->prec == GB_FP32 && h->smoother == GB_SMOOTHER_FIR &&
+                         h->layout == GB_LAYOUT_PLANES && single_image_groups(h, H, W, probe, &nprobe);
+    if (!chunked) {
+        GB_TRY(filter_device(h, h->d_stage_img, H, W, W, h->d_stage_out, st));
+        GB_CU(cudaMemcpyAsync(h_out, h->d_stage_out, out_bytes, cudaMemcpyDeviceToHost, st));
+        GB_CU(cudaStreamSynchronize(st));
+        return GB_OK;
+    }
+    // One launch per frequency, cheapest first; the planes of a finished frequency go back
+    // to the host on a second stream (one copy per frequency) while the next ones compute.
+    GB_TRY(ensure_tables(h, H, W, st));
+    if (!h->copy_stream) GB_CU(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    while ((int)h->freq_done.size() < nf + 1) {
+        cudaEvent_t ev = nullptr;
+        GB_CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        h->freq_done.push_back(ev);
+    }
+    std::vector<int> order(nf);
+    for (int s = 0; s < nf; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return h->freqs[p].T < h->freqs[q].T; });
+    const size_t freq_bytes = (size_t)h->theta.size() * H * W * sizeof(float2);
+    // the copy stream must not overtake earlier work on `st` that reads or writes h_out
+    GB_CU(cudaEventRecord(h->freq_done[nf], st));
+    GB_CU(cudaStreamWaitEvent(h->copy_stream, h->freq_done[nf], 0));
+    // every launch is queued before the first copy: a copy to pageable memory returns only
+    // when it is done, and must not hold back the launches behind it
+    for (int s : order) {
+        GB_TRY(filter_device(h, h->d_stage_img, H, W, W, h->d_stage_out, st, s));
+        GB_CU(cudaEventRecord(h->freq_done[s], st));
+    }
+    for (int s : order) {
+        GB_CU(cudaStreamWaitEvent(h->copy_stream, h->freq_done[s], 0));
+        GB_CU(cudaMemcpyAsync(static_cast<char *>(h_out) + s * freq_bytes,
+                              reinterpret_cast<char *>(h->d_stage_out) + s * freq_bytes, freq_bytes,
+                              cudaMemcpyDeviceToHost, h->copy_stream));
+    }
+    GB_CU(cudaStreamSynchronize(h->copy_stream));
     GB_CU(cudaStreamSynchronize(st));
     return GB_OK;
 }
@@ -1018,6 +1064,7 @@ gb_status gabor_bank_sdft(gabor_bank_t h, const float *d_img, int H, int W, int6
     a.tw_x = h->d_sdft_tw;
     a.tw_y = h->d_sdft_tw + kMaxSdftM;
     a.demod_form = h->sdft_form == 1 ? 1 : 0;
+    a.noreuse = h->sdft_reuse ? 0 : 1;
     if (h->prec == GB_FP32) {
         // Filter order (Sec. III-B).  Vertical first (a transposed problem) saves FMAs when
         // My > Mx (the first FIR pass along the longer side), but its stores run across the
@@ -1215,6 +1262,10 @@ gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value)
     case GB_OPT_SDFT_FORM:
         if (value < 0 || value > 2) return fail(GB_ERR_INVALID_ARG, "GB_OPT_SDFT_FORM takes 0, 1 or 2");
         h->sdft_form = (int)value;
+        return GB_OK;
+    case GB_OPT_SDFT_REUSE:
+        if (value != 0 && value != 1) return fail(GB_ERR_INVALID_ARG, "GB_OPT_SDFT_REUSE takes 0 or 1");
+        h->sdft_reuse = (int)value;
         return GB_OK;
     case GB_OPT_BOUNDARY:
         if (value < GB_BOUNDARY_ZERO || value > GB_BOUNDARY_MIRROR)

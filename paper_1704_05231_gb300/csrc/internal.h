@@ -210,6 +210,8 @@ struct SdftArgs {
     int bmode;           // BoundaryMode
     int trans;           // 1: a transposed problem (vertical pass first); outputs are written back transposed
     int demod_form;      // 1: demodulate / smooth / remodulate step by step; 0: modulated taps
+    int noreuse;         // 1: the no-reuse ablation, one CTA per (u in [0, Mx), v in [0, My/2]) that
+                         // recomputes J_u for its single v (no J_{Mx-u} = J*_u)
 };
 
 // One frequency of the plan.
@@ -324,6 +326,7 @@ struct gabor_bank {
     int fp32_ctas_opt = 0;                    // GB_OPT_BANK_CTAS (0 automatic, 1, 2)
     int fp32_ctas = 1;                        // CTAs per SM of the current tables
     int sdft_form = 0;                        // GB_OPT_SDFT_FORM (0 automatic, 1 step by step, 2 modulated taps)
+    int sdft_reuse = 1;                       // GB_OPT_SDFT_REUSE (1 reuse J_u, 0 the no-reuse ablation)
     int sdft_order = 0;                       // 0 automatic, 1 horizontal pass first, 2 vertical first
     float *d_transp = nullptr;                // transposed image for the vertical-first SDFT
     size_t transp_elems = 0;
@@ -398,4 +401,6 @@ struct gabor_bank {
     size_t stage_img_bytes = 0;
     void *d_stage_out = nullptr;
     size_t stage_out_bytes = 0;
+    cudaStream_t copy_stream = nullptr;       // device-to-host copies of finished frequencies
+    std::vector<cudaEvent_t> freq_done;       // one per frequency, plus one for the call's start
 };

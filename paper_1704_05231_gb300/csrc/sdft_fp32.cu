@@ -21,6 +21,11 @@
 // default) reads J_u straight from its ring for every v, with no demodulated copy of the
 // window and no barrier between the v passes; the step-by-step form is kept as an option.
 //
+// No-reuse ablation (GB_OPT_SDFT_REUSE = 0): the reuse of Sec. III-B switched off.  Every
+// (u, v) with u in [0, Mx) and v in [0, My/2] gets its own CTAs, which compute the row pass
+// J_u for that v alone and derive nothing from J*_u; the conjugate fill of the v > My/2 half
+// (F_{u,v} = F*_{Mx-u,My-v}) stays, as in the paper's own comparison (Table III).
+//
 // Filter order (Sec. III-B): the pass over the first axis runs for M/2 + 1 frequencies, the
 // second for all M of the first times M/2 + 1 of its own.  With the FIR passes used here the
 // first pass needs fewer FMAs along the longer window side; on request (vertical first) the
@@ -59,9 +64,13 @@ size_t sdft_mt_smem_bytes(int TH, int RS, int RW, int TpadX, int TpadY, int My)
 // Step-by-step form: demodulate, smooth with the real Gaussian, remodulate, in both passes.
 __device__ __forceinline__ void sdft_demod_form(const SdftArgs &a, unsigned char *smem_raw)
 {
-    const int u = blockIdx.z;                 // 0 .. Mx/2
     const int Mx = a.Mx, My = a.My;
-    const bool paired = u > 0 && 2 * u < Mx;  // J_0 and J_{Mx/2} are real
+    const int nvz = My / 2 + 1;
+    // u in 0 .. Mx/2 (reuse), or the (u, v) of this CTA in the no-reuse ablation
+    const int u = a.noreuse ? (int)blockIdx.z / nvz : (int)blockIdx.z;
+    const int v_lo = a.noreuse ? (int)blockIdx.z % nvz : 0, v_hi = a.noreuse ? v_lo + 1 : nvz;
+    // J_0 and J_{Mx/2} are real; without reuse F_{Mx-u,v} has CTAs of its own
+    const bool paired = !a.noreuse && u > 0 && 2 * u < Mx;
     const int x0 = blockIdx.x * kStripW;
     const int ys = blockIdx.y * a.seg_len;
     if (ys >= a.H) return;
@@ -196,7 +205,7 @@ __device__ __forceinline__ void sdft_demod_form(const SdftArgs &a, unsigned char
         const int base_off = pmod(base_row - ring_origin, a.RS);
         for (int s = tid; s < a.RS; s += kThreads) nmod[s] = pmod(base_row + pmod(s - base_off, a.RS), My);
         __syncthreads();
-        for (int v = 0; v < nv; ++v) {
+        for (int v = v_lo; v < v_hi; ++v) {
             const float2 *twv = tw2 + v * My;
             // Demodulate every ring slot by (cos, sin)(w0 v n) (Eq. 23-24 / 10).
             for (int i = tid; i < a.RS * kStripW; i += kThreads) {
@@ -268,9 +277,13 @@ __device__ __forceinline__ void sdft_demod_form(const SdftArgs &a, unsigned char
 // Modulated-tap form (see the head of this file).
 __device__ __forceinline__ void sdft_mt_form(const SdftArgs &a, unsigned char *smem_raw)
 {
-    const int u = blockIdx.z;                 // 0 .. Mx/2
     const int Mx = a.Mx, My = a.My;
-    const bool paired = u > 0 && 2 * u < Mx;  // J_0 and J_{Mx/2} are real
+    const int nvz = My / 2 + 1;
+    // u in 0 .. Mx/2 (reuse), or the (u, v) of this CTA in the no-reuse ablation
+    const int u = a.noreuse ? (int)blockIdx.z / nvz : (int)blockIdx.z;
+    const int v_lo = a.noreuse ? (int)blockIdx.z % nvz : 0, v_hi = a.noreuse ? v_lo + 1 : nvz;
+    // J_0 and J_{Mx/2} are real; without reuse F_{Mx-u,v} has CTAs of its own
+    const bool paired = !a.noreuse && u > 0 && 2 * u < Mx;
     const int x0 = blockIdx.x * kStripW;
     const int ys = blockIdx.y * a.seg_len;
     if (ys >= a.H) return;
@@ -378,7 +391,7 @@ __device__ __forceinline__ void sdft_mt_form(const SdftArgs &a, unsigned char *s
         const int xl = tid & 31, yg = tid >> 5;
         const int x = x0 + xl;
         const int um = (Mx - u) % Mx;
-        for (int v = 0; v < nv; ++v) {
+        for (int v = v_lo; v < v_hi; ++v) {
             const float4 *gv = gy + v * (a.TpadY + 8);
             const int vm = (My - v) % My;
             const bool fill = !a.half && v > 0 && 2 * v < My;
@@ -499,7 +512,7 @@ cudaError_t launch_sdft_fp32(SdftArgs a, int sm_count, cudaStream_t st)
     }
     const int cps = std::max(1, std::min(8, (int)(kSmemLimit / (smem + 1024))));
     const int nstrips = (a.W + kStripW - 1) / kStripW;
-    const int nu = a.Mx / 2 + 1;
+    const int nu = a.noreuse ? a.Mx * (a.My / 2 + 1) : a.Mx / 2 + 1;
     const int64_t base = (int64_t)nstrips * nu;
     int nseg = 1;
     const int64_t target = 2LL * sm_count * cps;

@@ -418,3 +418,22 @@ def test_tc_bank_large_radius_sampled(torch_cuda, row_pass, boundary):
         # scale = max|oracle| over the samples (at most the result's max: a stricter bound)
         assert rel_err(got[:, :, ys, xs], ref) <= TC_TOL
         assert rel_err(f32[:, :, ys, xs], ref) <= FP32_TOL
+
+
+@pytest.mark.parametrize("layout", ["planes", "pixels"])
+def test_host_path_per_frequency_copies_bitwise(torch_cuda, layout):
+    # gabor_bank_filter_host on pinned buffers: per-frequency launches whose planes are copied
+    # back while the next frequency computes (plane-major layout), or one launch (pixel-major);
+    # bitwise the device call's result either way, and repeated calls give the same bits.
+    from paper_1704_05231_gb300 import GaborBank
+    torch = torch_cuda
+    img = synth.paper_like(3, 300, 410)
+    th, om, sg = c2_bank()
+    with GaborBank(th, om, sg, layout=layout) as gbk:
+        dev = gbk.filter(torch.from_numpy(img).cuda()).cpu().numpy()
+        h_img = torch.from_numpy(img).pin_memory()
+        h_out = torch.full(gbk.out_shape(300, 410), float("nan"), dtype=torch.complex64).pin_memory()
+        for _ in range(2):
+            gbk.filter_host_ptr(h_img.data_ptr(), 300, 410, 410, h_out.data_ptr())
+            assert np.array_equal(h_out.numpy(), dev)
+            h_out.fill_(float("nan"))

@@ -194,3 +194,34 @@ def test_sdft_forms_c3_full_oracle_and_order(torch_cuda, c3_full, order):
     for form in (1, 2):
         assert rel_err(res[form], ref) <= FP32_TOL
     assert rel_err(res[2], res[1]) <= FP32_TOL
+
+
+@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("H,W,M,sigma,half,boundary", [(64, 80, 16, 4.0, False, "zero"),
+                                                        (37, 45, (8, 12), 1.5, False, "mirror"),
+                                                        (50, 33, (12, 6), 2.0, True, "replicate"),
+                                                        (5, 70, 16, 4.0, False, "zero")])
+def test_sdft_no_reuse_ablation_matches_oracle(torch_cuda, form, H, W, M, sigma, half, boundary):
+    # GB_OPT_SDFT_REUSE = 0: J_u recomputed for every (u, v), F_{Mx-u,v} not taken from J*_u
+    # (the paper's comparison without the reuse of Sec. III-B); the same result as the oracle.
+    from paper_1704_05231_gb300 import GaborBank
+    My, Mx = (M, M) if isinstance(M, int) else M
+    img = synth.pink_noise([9, H, W], H, W)
+    with GaborBank(boundary=boundary) as gbk:
+        gbk.set_option("sdft_form", form)
+        gbk.set_option("sdft_reuse", 0)
+        got = gbk.sdft(torch_cuda.from_numpy(img).cuda(), sigma, (My, Mx), half_spectrum=half).cpu().numpy()
+        gbk.set_option("sdft_reuse", 1)
+        again = gbk.sdft(torch_cuda.from_numpy(img).cuda(), sigma, (My, Mx), half_spectrum=half).cpu().numpy()
+    ref = oracle.sdft(img, sigma, My, Mx, boundary=boundary)[:got.shape[0]]
+    assert rel_err(got, ref) <= FP32_TOL
+    assert rel_err(again, ref) <= FP32_TOL
+
+
+def test_sdft_no_reuse_c3_full_oracle(torch_cuda, c3_full):
+    from paper_1704_05231_gb300 import GaborBank
+    img, ref = c3_full
+    with GaborBank() as gbk:
+        gbk.set_option("sdft_reuse", 0)
+        got = gbk.sdft(torch_cuda.from_numpy(img).cuda(), 4.0, 16).cpu().numpy()
+    assert rel_err(got, ref) <= FP32_TOL
