@@ -46,7 +46,7 @@ struct Smem {
 };
 
 // modulated taps: one set per unit of a (twin) item
-__host__ __device__ __forceinline__ int ctap_count(const FreqDev &f) { return f.mtaps ? 2 * (f.Tpad + 8) : 0; }
+__host__ __device__ __forceinline__ int ctap_count(const FreqDev &f) { return f.mtaps ? 2 * (f.Tpr + 8) : 0; }
 __host__ __device__ __forceinline__ int phx_count(const FreqDev &f) { return f.mtaps ? 0 : f.SW + 1; }
 
 // Every region starts on a 16-byte boundary (RS, TH multiples of 8; SW odd; Tpad + 8 even).
@@ -86,12 +86,15 @@ FreqDev gabor_fp32_geometry(int R, int tile_rows, bool pipelined, bool mtaps, in
     f.T = 2 * R + 1;
     f.Tpad = round_up(f.T, 8);
     f.mtaps = mtaps ? 1 : 0;
+    f.Rw = mtaps ? round_up(R, 4) : R;
+    f.Tr = f.Rw + R + 1;
+    f.Tpr = round_up(f.Tr, 8);
     if (mtaps) {
         // no demodulated copy; raw rows hold the whole tap window of every output (zeros past
-        // the halo) and are = 1 (mod 32) floats apart, so that 8 rows x 2 column groups x
-        // 2 tap halves of a warp fall on distinct banks
+        // the halo) and are = 4 (mod 32) floats apart, so that the 16-byte window loads of the
+        // 8 lanes (8 rows) of a quarter warp fall on distinct banks
         f.SW = 0;
-        f.RW = round_up(kStripW + f.Tpad - 1, 32) + 1;
+        f.RW = round_up(kStripW + f.Tpr - 1, 32) + 4;
     } else {
         f.SW = stage_width(kStripW + f.Tpad);
         f.RW = round_up(kStripW + f.T - 1, 4);
@@ -142,11 +145,14 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
     const int warp = tid >> 5, lane = tid & 31;
     const int stride = kStripW + 1;
     const int R = f.R, TH = f.TH, RS = f.RS, SW = f.SW, RW = f.RW;
-    const int ncols = kStripW + f.T - 1;        // input columns x0 - R .. x0 + 31 + R
+    const int Rw = f.Rw;
+    const int ncols = kStripW + f.Tr - 1;       // input columns x0 - Rw .. x0 + 31 + R
     // full 8-tap chunks, and one tail tap for filters of 8 k + 1 taps (R = 0 mod 4) instead of
-    // a chunk of 7 zero taps
+    // a chunk of 7 zero taps; the row pass runs over its Tr taps, the column pass over T
     const bool tail1 = (f.T & 7) == 1;
     const int nchunks = tail1 ? f.T / 8 : f.Tpad / 8;
+    const bool tail1r = (f.Tr & 7) == 1;
+    const int nchunks_r = tail1r ? f.Tr / 8 : f.Tpr / 8;
     const int64_t plane = (int64_t)im.H * im.W;
     const int64_t ystride = a.layout ? (int64_t)im.W * a.nplanes : (int64_t)im.W;   // between output rows
     const Smem sm = carve(smem_raw, f);
@@ -176,12 +182,13 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
     for (int i = tid; i < f.Tpad + 8; i += kThreadsCta) sm.taps[i] = i < f.Tpad ? f.taps[i] : 0.f;
     const bool ext = a.bmode != kBoundaryZero;
     if (MT) {
-        // taps S(d) exp(-i omega^c d), d = t - R: (cos, -sin) from the unit's phase table
-        // (a twin item: both units' taps, one set after the other)
-        for (int i = tid; i < (twin ? 2 : 1) * (f.Tpad + 8); i += kThreadsCta) {
-            const int t = i % (f.Tpad + 8);
-            const float2 ph = t < f.T ? (i < f.Tpad + 8 ? u.phx : u2.phx)[t - R] : make_float2(0.f, 0.f);
-            const float g = t < f.T ? f.taps[t] : 0.f;
+        // taps S(d) exp(-i omega^c d), d = t - Rw: (cos, -sin) from the unit's phase table,
+        // zero for |d| > R (a twin item: both units' taps, one set after the other)
+        for (int i = tid; i < (twin ? 2 : 1) * (f.Tpr + 8); i += kThreadsCta) {
+            const int t = i % (f.Tpr + 8) - (Rw - R);   // index into the T taps S(t - R)
+            const bool in = t >= 0 && t < f.T;
+            const float2 ph = in ? (i < f.Tpr + 8 ? u.phx : u2.phx)[t - R] : make_float2(0.f, 0.f);
+            const float g = in ? f.taps[t] : 0.f;
             sm.ctaps[i] = make_float2(g * ph.x, -(g * ph.y));
         }
         // raw columns past the halo are read (by zero taps) and never copied: zero them
@@ -220,22 +227,33 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
         block_rows(b, start, n);
         float *dst = sm.raw + (size_t)(b & 1) * TH * RW;
         if (!ext) {
+            // strips whose window lies inside the image: 16-byte copies for rows that start on
+            // a 16-byte boundary (raw rows do: RW and x0 - Rw are multiples of 4 under
+            // modulated taps), the last ncols mod 4 columns by 4-byte copies
+            const bool xin = MT && x0 - Rw >= 0 && x0 - Rw + ncols <= im.W;
+            const int n16 = ncols >> 2;
             for (int r = warp; r < n; r += kRowWarps) {
                 const int y = start + r;
                 const bool yin = y >= 0 && y < im.H;
+                float *d = dst + (size_t)r * RW;
                 const float *src = im.img + (int64_t)(yin ? y : 0) * im.pitch;
-                for (int j = lane; j < ncols; j += 32) {
-                    const int gx = x0 - R + j;
-                    const bool ok = yin && gx >= 0 && gx < im.W;
-                    cp_async4(dst + (size_t)r * RW + j, ok ? (const void *)(src + gx) : (const void *)im.img,
-                              ok ? 4 : 0);
+                if (yin && xin && (reinterpret_cast<uintptr_t>(src + (x0 - Rw)) & 15) == 0) {
+                    const float *s0 = src + (x0 - Rw);
+                    for (int j = lane; j < n16; j += 32) cp_async16(d + 4 * j, s0 + 4 * j);
+                    for (int j = 4 * n16 + lane; j < ncols; j += 32) cp_async4(d + j, s0 + j, 4);
+                } else {
+                    for (int j = lane; j < ncols; j += 32) {
+                        const int gx = x0 - Rw + j;
+                        const bool ok = yin && gx >= 0 && gx < im.W;
+                        cp_async4(d + j, ok ? (const void *)(src + gx) : (const void *)im.img, ok ? 4 : 0);
+                    }
                 }
             }
         } else {
             for (int r = warp; r < n; r += kRowWarps) {
                 const float *src = im.img + (int64_t)ext_coord(start + r, im.H, a.bmode) * im.pitch;
                 for (int j = lane; j < ncols; j += 32)
-                    cp_async4(dst + (size_t)r * RW + j, src + ext_coord(x0 - R + j, im.W, a.bmode), 4);
+                    cp_async4(dst + (size_t)r * RW + j, src + ext_coord(x0 - Rw + j, im.W, a.bmode), 4);
             }
         }
         cp_async_commit();
@@ -269,21 +287,20 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
         // 16 (row, 8-column group) outputs per warp, sweeps of 8 kRB rows x 4 groups; the two
         // half warps take the two halves of the tap chunks and add them with one shuffle.
         // Demodulation form: a half warp covers 8 rows x groups 2 q0, 2 q0 + 1 (distinct bank
-        // pairs of the float2 stage).  Modulated taps (raw rows 1 mod 32 floats apart): the
-        // half warps' tap splits nh are 8 nh floats apart, so groups q0, q0 + 2 (16 banks
-        // apart) for odd nh and 2 q0, 2 q0 + 1 (8 apart) for nh = 2 mod 4 keep all 32 window
-        // loads of a warp on distinct banks (nh = 0 mod 4: two-way conflicts).
+        // pairs of the float2 stage).  Modulated taps (raw rows 4 mod 32 floats apart, window
+        // loads of 16 bytes): each quarter warp reads 8 different rows, which fall on distinct
+        // banks whatever the group and tap half.
         const int hl = lane & 15, half = lane >> 4;
         const int q0 = warp / kRB;
-        int nh = (nchunks + 1) >> 1;
-        if (MT && (nh & 3) == 0 && (nchunks & 1)) --nh;   // same longest half, odd split
+        int nh = (nchunks_r + 1) >> 1;
+        if (MT && (nh & 3) == 0 && (nchunks_r & 1)) --nh;   // same longest half, odd split
         const int q = MT ? ((nh & 3) == 2 ? 2 * q0 + (hl >> 3) : q0 + 2 * (hl >> 3)) : (hl >> 3) | (q0 << 1);
         for (int r0 = 0; r0 < n; r0 += 8 * kRB) {
         const int r = r0 + ((hl & 7) | ((warp % kRB) << 3));
         // Warp-uniform: the warp's 8 rows start inside the block (rows < TH, so every stage read
         // is in bounds); rows r >= n are computed but not stored.
         if (r0 + 8 * (warp % kRB) < n) {
-            const int c0 = half ? nh : 0, cnt = half ? nchunks - nh : nh;
+            const int c0 = half ? nh : 0, cnt = half ? nchunks_r - nh : nh;
             const int y = start + r;
             const int base = ((y - ring_origin) % RS) * stride + 8 * q;
             const bool yin = ext || (y >= 0 && y < im.H);
@@ -294,11 +311,11 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
                 for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
                 // the tail tap goes to the half warp that ends at the last chunk
                 if (MT)
-                    conv8_linear_ct(rawb + (size_t)r * RW + 8 * q + 8 * c0,
-                                    ctaps4 + v * ((f.Tpad + 8) / 2) + 4 * c0, cnt, acc, tail1 && half);
+                    conv8_linear_ct4(rawb + (size_t)r * RW + 8 * q + 8 * c0,
+                                     ctaps4 + v * ((f.Tpr + 8) / 2) + 4 * c0, cnt, acc, tail1r && half);
                 else
                     conv8_linear<float2>(sm.stage + (size_t)r * SW + 8 * q + 8 * c0, taps4 + 2 * c0, cnt, acc,
-                                         tail1 && half);
+                                         tail1r && half);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, 16);
@@ -354,17 +371,20 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
             conv8_ring<float2, kStripW + 1>(sm.ring2 + (size_t)sub * RS * stride + xl, RS, slot0, taps4, nchunks, acc,
                                             tail1);
             if (x < im.W) {
-                float2 *o = im.out + out_offset(a, oplane, plane, x);
+                // output row c + yb + j: one pointer stepped by the row stride, phases at
+                // immediate offsets
+                float2 *o = im.out + out_offset(a, oplane, plane, x) + (int64_t)(c + yb) * ystride;
+                const float2 *py = phy + (c + yb);
+                const int jn = nout - yb;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const int y = c + yb + j;
-                    if (yb + j < nout) {
-                        const float2 cy = phy[y];
+                    if (j < jn) {
+                        const float2 cy = py[j];
                         const float P = acc[j].x, Q = acc[j].y;
                         // Eq. 7-8 (theta_a) or Eq. 15-16 (pi - theta_a)
-                        __stcs(o + (int64_t)y * ystride,
-                               make_float2(fmaf(cy.x, P, cy.y * Q), fmaf(cy.y, P, -cy.x * Q)));
+                        __stcs(o, make_float2(fmaf(cy.x, P, cy.y * Q), fmaf(cy.y, P, -cy.x * Q)));
                     }
+                    o += ystride;
                 }
             }
         }

@@ -64,8 +64,13 @@ struct FreqDev {
     int RS;             // ring rows (multiple of 8, >= TH + T - 1)
     int SW;             // staging row width in float2 (>= kStripW + Tpad, = 1 mod 16)
     int RW;             // raw staging row width in floats (demodulation form: >= kStripW + T - 1,
-                        // multiple of 4; modulated taps: >= kStripW + Tpad, = 1 mod 32)
+                        // multiple of 4; modulated taps: >= kStripW + Tpr, = 4 mod 32)
     int mtaps;          // row pass form: 1 modulated taps, 0 demodulate / smooth / remodulate
+    // row pass window: input columns x0 - Rw .. x0 + 31 + R of a strip, Tr = Rw + R + 1 taps
+    // (Tpr padded to 8), the first Rw - R of them zero.  Modulated taps: Rw = R rounded up to 4,
+    // so that the window starts on a 16-byte boundary; demodulation form: Rw = R.
+    int Rw, Tr, Tpr;
+    int pad_;
 };
 
 // One image of a launch.

@@ -362,8 +362,8 @@ __device__ __forceinline__ void sdft_mt_form(const SdftArgs &a, unsigned char *s
         cp_async_commit();
     };
     // Row pass of block b (Eq. 19, 21-22 as one complex-tap convolution of the raw rows):
-    // thread = (row r, 8-column group q); a warp covers 8 rows x 4 groups (RW = 1 mod 32:
-    // distinct banks).
+    // thread = (row r, 8-column group q); a warp covers 8 rows x 4 groups (RW = 4 mod 32:
+    // the 16-byte window loads of a quarter warp hit distinct banks).
     auto row_pass = [&](int b) {
         int start, n;
         block_rows(b, start, n);
@@ -374,7 +374,7 @@ __device__ __forceinline__ void sdft_mt_form(const SdftArgs &a, unsigned char *s
             float2 acc[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
-            conv8_linear_ct(rawb + (size_t)r * RW + 8 * q, gx4, a.TpadX / 8, acc);
+            conv8_linear_ct4(rawb + (size_t)r * RW + 8 * q, gx4, a.TpadX / 8, acc);
             const int y = start + r;
             const int slot = (y - ring_origin) % RS;
             const bool yin = a.bmode != kBoundaryZero || (y >= 0 && y < a.H);
@@ -498,8 +498,9 @@ cudaError_t launch_sdft_fp32(SdftArgs a, int sm_count, cudaStream_t st)
     a.TpadX = round_up(a.Mx, 8);
     a.TpadY = round_up(a.My, 8);
     a.SW = mt ? 0 : stage_width(kStripW + a.TpadX);
-    // modulated taps: raw rows hold every tap window of the strip (zero tail), 1 mod 32 floats apart
-    a.RW = mt ? round_up(kStripW + a.TpadX - 1, 32) + 1 : round_up(kStripW + a.Mx - 1, 4);
+    // modulated taps: raw rows hold every tap window of the strip (zero tail), 4 mod 32 floats
+    // apart (16-byte window loads, conflict-free over the 8 rows of a quarter warp)
+    a.RW = mt ? round_up(kStripW + a.TpadX - 1, 32) + 4 : round_up(kStripW + a.Mx - 1, 4);
     int TH = 64;
     size_t smem;
     for (;;) {
