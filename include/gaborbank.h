@@ -145,7 +145,13 @@ gb_status gabor_bank_sdft(gabor_bank_t h, const float *d_img, int H, int W, int6
  * Asynchronous.  Results are bitwise identical to n separate gabor_bank_filter calls with the
  * same handle.  A call whose pointers and shapes equal the previous call's (and whose tables
  * already exist) enqueues only a memset and the kernel, so it can be captured in a CUDA graph.
- * FP32 handles: one launch; tensor-core handles: one bank pass per image.
+ * FP32 handles: one launch.  GB_FP16_TC handles: four launches for the whole batch (image
+ * min / max, the constant-image tables, the row pass and the column pass over every image's
+ * tiles), with intermediates in a handle-owned batch workspace (about 4 bytes per pixel and
+ * horizontal pass, plus halo rows), allocated on the first call with a new set of pointers and
+ * shapes; plans that need the step-by-step kernels (GB_OPT_ROW_PASS = 1, radii above 96 px)
+ * run one bank pass per image.  A batch call on a set of pointers and shapes other than the
+ * previous one synchronises the stream once.
  */
 gb_status gabor_bank_filter_batch(gabor_bank_t h, int n, const float *const *d_imgs,
                                   const int *H, const int *W, const int64_t *pitch,

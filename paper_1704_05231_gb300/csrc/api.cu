@@ -438,8 +438,22 @@ gb_status get_worklist(gabor_bank *h, const std::vector<int64_t> &shapes, WorkIt
 
 // Tensor-core bank state: B operands, frequency and unit descriptors (once per plan; unit
 // descriptors again when the phase tables move) and the library-owned intermediate.
+void free_tc_batch(gabor_bank *h)
+{
+    dfree(h->d_tcb_ws);
+    h->tcb_ws_bytes = 0;
+    dfree(h->d_tcb_imgs);
+    dfree(h->d_tcb_maps);
+    h->tcb_cap = 0;
+    dfree(h->d_tcb_rows);
+    dfree(h->d_tcb_cols);
+    h->tcb_rows_cap = h->tcb_cols_cap = 0;
+    h->tcb_key.clear();
+}
+
 void free_tc(gabor_bank *h)
 {
+    free_tc_batch(h);
     dfree(h->d_tcB);
     dfree(h->d_tcAm);
     dfree(h->d_tcGm);
@@ -719,6 +733,193 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.row_y0 = -ypad;
     GB_TRY(encode_tc_maps(a, h->tc_nsig, row_mt));
     GB_CU(launch_gabor_tc(a, h->sm_count, st));
+    return GB_OK;
+}
+
+// A batch on a tensor-core handle with the modulated-tap kernels: every image's row and column
+// items in one launch each (after one k_minmax and one k_ones launch).  *done = false when the
+// plan needs the step-by-step kernels (the caller then runs one bank pass per image).
+gb_status filter_batch_tc(gabor_bank *h, int n, const float *const *d_imgs, const int *H, const int *W,
+                          const int64_t *pitch, void *const *d_outs, cudaStream_t st, bool *done)
+{
+    *done = false;
+    if (h->prec == GB_BF16_TC)
+        return fail(GB_ERR_UNSUPPORTED,
+                    "the filter bank on tensor cores runs with FP16 operands (GB_FP16_TC); BF16 operands "
+                    "exceed 2e-3 * max|out| on the bank");
+    for (const Freq &f : h->freqs)
+        if (!gabor_tc_supported(f.R)) return fail(GB_ERR_UNSUPPORTED, "tensor-core bank supports radii up to 96 px");
+    int Hm = 0, Wm = 0;
+    for (int i = 0; i < n; ++i) {
+        Hm = std::max(Hm, H[i]);
+        Wm = std::max(Wm, W[i]);
+    }
+    const bool tables_move = !(h->tables_ready && Wm <= h->Wcap && Hm <= h->Hcap);
+    GB_TRY(ensure_tables(h, Hm, Wm, st));
+    if (tables_move) free_tc(h);
+    GB_TRY(ensure_tc(h, st));
+    if (h->fp32_row_form == 1 || !h->tc_mt_ok) return GB_OK;
+    const int nf = (int)h->freqs.size(), nu = (int)h->units.size();
+    const int ty = h->tc_mt_ty, tile_x = gabor_tc_mt_tile_x();
+    const int col_ty = gabor_tc_mt_col_ty(h->tc_col_kmax);
+    int rmax = 0;
+    for (const Freq &f : h->freqs) rmax = std::max(rmax, f.R);
+    const int ypad = h->boundary == kBoundaryZero ? 0 : (rmax + ty - 1) / ty * ty;
+    const int Lpad = tc_lpad(h);
+    const int nsig = 2 * nu;   // Re J, Im J of every unit
+    // workspace: intermediates, F[1] tables, partial keys, centres (each 256-byte aligned)
+    auto al = [](int64_t b) { return (b + 255) / 256 * 256; };
+    std::vector<int64_t> off_sig(n), off_ones(n), Hp(n);
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        Hp[i] = (int64_t)(H[i] + 63) / 64 * 64 + 2 * Lpad;
+        off_sig[i] = total;
+        total += al((int64_t)nsig * W[i] * Hp[i] * 2);
+    }
+    for (int i = 0; i < n; ++i) {
+        off_ones[i] = total;
+        total += al((int64_t)nu * ((int64_t)W[i] + H[i]) * (int64_t)sizeof(float2));
+    }
+    const int64_t off_parts = total;
+    total += al((int64_t)n * kMmParts * 2 * sizeof(unsigned));
+    const int64_t off_ce = total;
+    total += al((int64_t)n * sizeof(float2));
+    // the batch key: every pointer and shape, and the options the layout depends on
+    std::vector<int64_t> key;
+    key.reserve(5 * (size_t)n + 3);
+    key.push_back(h->boundary);
+    key.push_back(h->layout);
+    key.push_back(total);
+    for (int i = 0; i < n; ++i) {
+        key.push_back((int64_t)reinterpret_cast<uintptr_t>(d_imgs[i]));
+        key.push_back(pitch[i]);
+        key.push_back(H[i]);
+        key.push_back(W[i]);
+        key.push_back((int64_t)reinterpret_cast<uintptr_t>(d_outs[i]));
+    }
+    if (key != h->tcb_key) {
+        GB_CU(cudaStreamSynchronize(st));   // earlier batches of this handle may still use the buffers
+        h->tcb_key.clear();
+        if ((size_t)total > h->tcb_ws_bytes) {
+            dfree(h->d_tcb_ws);
+            h->tcb_ws_bytes = 0;
+            GB_TRY(dalloc(&h->d_tcb_ws, (size_t)total));
+            h->tcb_ws_bytes = (size_t)total;
+        }
+        if (n > h->tcb_cap) {
+            dfree(h->d_tcb_imgs);
+            dfree(h->d_tcb_maps);
+            h->tcb_cap = 0;
+            GB_TRY(dalloc(&h->d_tcb_imgs, (size_t)n));
+            GB_TRY(dalloc(&h->d_tcb_maps, (size_t)n));
+            h->tcb_cap = n;
+        }
+        unsigned char *ws = h->d_tcb_ws;
+        std::vector<TcImgDev> imgs(n);
+        std::vector<CUtensorMap> maps(n);
+        PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+        if (!enc) return fail(GB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+        for (int i = 0; i < n; ++i) {
+            TcImgDev &d = imgs[i];
+            d.img = d_imgs[i];
+            d.pitch = pitch[i];
+            d.H = H[i];
+            d.W = W[i];
+            d.out = reinterpret_cast<float2 *>(d_outs[i]);
+            d.plane = (int64_t)H[i] * W[i];
+            d.sig = reinterpret_cast<uint16_t *>(ws + off_sig[i]);
+            d.Hp = Hp[i];
+            d.onesA = reinterpret_cast<const float2 *>(ws + off_ones[i]);
+            d.onesB = d.onesA + (int64_t)nu * W[i];
+            // the intermediate as 8 rows of a block x signals x W x Hp / 8 blocks (FP16); boxes of
+            // 8 rows x the two parts x 64 columns x 8 blocks, as in the single-image call
+            const cuuint64_t dims[4] = {8, (cuuint64_t)nsig, (cuuint64_t)W[i], (cuuint64_t)(Hp[i] / 8)};
+            const cuuint64_t strides[3] = {(cuuint64_t)Hp[i] * W[i] * 2, 16, (cuuint64_t)W[i] * 16};
+            const cuuint32_t box[4] = {8, 2, 64, 8}, elem[4] = {1, 1, 1, 1};
+            const CUresult r = enc(&maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, d.sig, dims, strides, box, elem,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return fail(GB_ERR_CUDA, "cuTensorMapEncodeTiled failed for a batch intermediate");
+        }
+        // items: frequencies largest radius first (the row pass of frequency s covers every
+        // unit of s), then images, then tiles
+        std::vector<int> order(nf);
+        for (int s2 = 0; s2 < nf; ++s2) order[s2] = s2;
+        std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return h->freqs[p].R > h->freqs[q].R; });
+        std::vector<int4> rows, cols;
+        for (int s2 : order)
+            for (int i = 0; i < n; ++i) {
+                const int nty = (H[i] + 2 * ypad + ty - 1) / ty, ntx = (W[i] + tile_x - 1) / tile_x;
+                for (int r = 0; r < nty; ++r)
+                    for (int c = 0; c < ntx; ++c) rows.push_back(make_int4(i, s2, -ypad + r * ty, c * tile_x));
+            }
+        for (int s2 : order)
+            for (int i = 0; i < n; ++i) {
+                const int ny = (H[i] + col_ty - 1) / col_ty, nx = (W[i] + 63) / 64;
+                for (int u = h->freqs[s2].u0; u < h->freqs[s2].u1; ++u)
+                    for (int r = 0; r < ny; ++r)
+                        for (int c = 0; c < nx; ++c) cols.push_back(make_int4(i, u, c * 64, r * col_ty));
+            }
+        if (rows.size() > ((size_t)1 << 30) || cols.size() > ((size_t)1 << 30))
+            return fail(GB_ERR_UNSUPPORTED, "batch too large for the tensor-core bank");
+        if (rows.size() > h->tcb_rows_cap) {
+            dfree(h->d_tcb_rows);
+            h->tcb_rows_cap = 0;
+            GB_TRY(dalloc(&h->d_tcb_rows, rows.size()));
+            h->tcb_rows_cap = rows.size();
+        }
+        if (cols.size() > h->tcb_cols_cap) {
+            dfree(h->d_tcb_cols);
+            h->tcb_cols_cap = 0;
+            GB_TRY(dalloc(&h->d_tcb_cols, cols.size()));
+            h->tcb_cols_cap = cols.size();
+        }
+        GB_CU(cudaMemcpy(h->d_tcb_imgs, imgs.data(), n * sizeof(TcImgDev), cudaMemcpyHostToDevice));
+        GB_CU(cudaMemcpy(h->d_tcb_maps, maps.data(), n * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+        if (!rows.empty())
+            GB_CU(cudaMemcpy(h->d_tcb_rows, rows.data(), rows.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        if (!cols.empty())
+            GB_CU(cudaMemcpy(h->d_tcb_cols, cols.data(), cols.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        // the intermediates' halo rows (above the image and below its last row tile) are read as
+        // zeros and never written: clear the intermediates once per batch layout
+        GB_CU(cudaMemsetAsync(h->d_tcb_ws, 0, (size_t)off_ones[0], st));
+        GB_CU(cudaStreamSynchronize(st));
+        h->tcb_nrow = (int)rows.size();
+        h->tcb_ncol = (int)cols.size();
+        h->tcb_key = key;
+    }
+    TcBankArgs a{};
+    a.freqs = h->d_tcfreq;
+    a.units = h->d_tcunit;
+    a.status = h->d_status;
+    a.row_kmax = h->tc_mt_kmax;
+    a.row_pwmax = h->tc_mt_pwmax;
+    a.row_mt = 1;
+    a.col_kmax = h->tc_col_kmax;
+    a.ones_pre = h->d_tcpre;
+    a.ones_stride = h->tc_pre_stride;
+    a.row_ty = ty;
+    a.forder = h->d_tcforder;
+    a.nf = nf;
+    a.nu_f = h->tc_nu_f;
+    a.np_f = h->tc_np_f;
+    a.col_mt_ty = col_ty;
+    a.bmode = h->boundary;
+    a.layout = h->layout;
+    a.nplanes = (int)(h->omega.size() * h->theta.size());
+    a.row_y0 = -ypad;
+    a.Lpad = Lpad;
+    a.imgs = h->d_tcb_imgs;
+    a.tmaps = h->d_tcb_maps;
+    a.mm_part = reinterpret_cast<unsigned *>(h->d_tcb_ws + off_parts);
+    a.img_ce = reinterpret_cast<float2 *>(h->d_tcb_ws + off_ce);
+    a.row_list = h->d_tcb_rows;
+    a.col_list = h->d_tcb_cols;
+    a.n_row = h->tcb_nrow;
+    a.n_col = h->tcb_ncol;
+    a.nimg = n;
+    GB_CU(launch_gabor_tc_batch(a, h->sm_count, st));
+    *done = true;
     return GB_OK;
 }
 
@@ -1150,8 +1351,16 @@ gb_status gabor_bank_filter_batch(gabor_bank_t h, int n, const float *const *d_i
     GB_TRY(check_sticky());
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (n == 0) return GB_OK;
+    if (h->prec != GB_FP32 && h->smoother == GB_SMOOTHER_FIR) {
+        // tensor-core handles: the whole batch in four launches (modulated-tap kernels), else
+        // one bank pass per image
+        bool done = false;
+        GB_TRY(filter_batch_tc(h, n, d_imgs, H, W, pitch, d_outs, st, &done));
+        if (done) return GB_OK;
+    }
     if (h->prec != GB_FP32 || h->smoother == GB_SMOOTHER_IIR) {
-        // tensor-core handles and the recursive smoother: one bank pass per image
+        // the recursive smoother, and tensor-core plans that need the step-by-step kernels: one
+        // bank pass per image
         for (int i = 0; i < n; ++i) GB_TRY(filter_device(h, d_imgs[i], H[i], W[i], pitch[i], d_outs[i], st));
         return GB_OK;
     }

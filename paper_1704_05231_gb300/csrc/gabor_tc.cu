@@ -116,6 +116,7 @@ __host__ __device__ inline int col_stages(int K)
 // 64 rows x 32 columns (paired units, listed first) or x 64 columns (unpaired units).
 struct RowItem {
     int s, y0, x0;
+    int img;     // image of a batch (0 for one image)
 };
 struct ColItem {
     int unit, x0, y0;
@@ -168,6 +169,32 @@ __device__ __forceinline__ int64_t tc_out_offset(const TcBankArgs &a, int p, int
     return a.layout ? pix * a.nplanes + p : (int64_t)p * a.plane + pix;
 }
 
+// The image an item works on: the call's image, or image i of a batch (with its TMA map).
+struct TcImgView {
+    const float *img;
+    int64_t pitch;
+    int H, W;
+    float2 *out;
+    int64_t plane;
+    uint16_t *sig;
+    int64_t Hp;
+    const float2 *onesA, *onesB;
+    const CUtensorMap *tm;
+};
+__device__ __forceinline__ TcImgView tc_img(const TcBankArgs &a, int i)
+{
+    if (a.imgs) {
+        const TcImgDev d = a.imgs[i];
+        return TcImgView{d.img, d.pitch, d.H, d.W, d.out, d.plane, d.sig, d.Hp, d.onesA, d.onesB, a.tmaps + i};
+    }
+    return TcImgView{a.img, a.pitch, a.H, a.W, a.out, a.plane, a.sig, a.Hp, a.onesA, a.onesB, &a.tmA[0]};
+}
+__device__ __forceinline__ int64_t tc_out_offset(const TcBankArgs &a, const TcImgView &im, int p, int y, int x)
+{
+    const int64_t pix = (int64_t)y * im.W + x;
+    return a.layout ? pix * a.nplanes + p : (int64_t)p * im.plane + pix;
+}
+
 // Order-preserving unsigned keys of floats (for atomic min / max over signed values).
 __device__ __forceinline__ unsigned fkey(float f)
 {
@@ -180,14 +207,30 @@ __device__ __forceinline__ float fkey_value(unsigned k)
 }
 
 // The centre c = (min + max) / 2 the passes subtract from the image, and e with
-// max|f - c| = m 2^e, m in [0.5, 1) (FP16 operands get the exact scale 2^-e).
-__device__ __forceinline__ void image_centre(const TcBankArgs &a, float &c, int &e)
+// max|f - c| = m 2^e, m in [0.5, 1) (FP16 operands get the exact scale 2^-e), from the
+// order-preserving keys ~min, max.
+__device__ __forceinline__ void centre_of(unsigned nlo, unsigned hik, float &c, int &e)
 {
-    const float lo = fkey_value(~a.minmax[0]), hi = fkey_value(a.minmax[1]);
+    const float lo = fkey_value(~nlo), hi = fkey_value(hik);
     c = hi >= lo ? 0.5f * (lo + hi) : 0.f;
     const float m = hi >= lo ? fmaxf(hi - c, c - lo) : 0.f;
     e = 0;
     if (m > 0.f) frexpf(m, &e);
+}
+__device__ __forceinline__ void image_centre(const TcBankArgs &a, float &c, int &e)
+{
+    centre_of(a.minmax[0], a.minmax[1], c, e);
+}
+// ... of image i: the call's image, or the per-image values k_ones wrote for a batch
+__device__ __forceinline__ void tc_centre(const TcBankArgs &a, int i, float &c, int &e)
+{
+    if (a.img_ce) {
+        const float2 v = a.img_ce[i];
+        c = v.x;
+        e = (int)v.y;
+        return;
+    }
+    image_centre(a, c, e);
 }
 
 // ------------------------------------------------------------------------------ row pass
@@ -540,13 +583,17 @@ __host__ __device__ inline MtSmem mt_smem(int K, int PW, int TY)
 
 __device__ __forceinline__ RowItem row_item_mt(const TcBankArgs &a, const TcDesc &d, int it)
 {
+    if (a.row_list) {
+        const int4 v = a.row_list[it];
+        return RowItem{v.y, v.z, v.w, v.x};
+    }
     const int g = it / a.row_cnt, local = it - g * a.row_cnt;
-    return RowItem{d.forder[g], a.row_y0 + (local / a.row_nx) * a.row_ty, (local % a.row_nx) * kMtTileX};
+    return RowItem{d.forder[g], a.row_y0 + (local / a.row_nx) * a.row_ty, (local % a.row_nx) * kMtTileX, 0};
 }
 
 __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_constant__ TcBankArgs a)
 {
-    const int nitems = a.nf * a.row_cnt;
+    const int nitems = a.row_list ? a.n_row : a.nf * a.row_cnt;
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -592,41 +639,38 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
     pdl_wait();
     const uint32_t tmem = *tmem_s;
     const uint32_t idesc = idesc_f16(0, 128, TY);
-    float cen;
-    int e;
-    image_centre(a, cen, e);
 
     if (warp >= kMtEpiWarps) {
         // -------------------------------------------------------------- producers
         constexpr int NP = 32 * (16 - kMtEpiWarps);
         const int ptid = tid - 32 * kMtEpiWarps, pwarp = warp - kMtEpiWarps;
-        const float sc = ldexpf(1.f, -e);
         int job = 0, nitem = 0;
         int a_issued = 0, a_landed = 0;   // ptid 0: Am copies issued / waited for
         bool ok = true;
         // cp.async of item it's patch: rows y0 .. y0 + TY - 1, columns x0 - R .. x0 + 63 + R
         auto stage = [&](int it) {
             const RowItem w = row_item_mt(a, D, it);
+            const TcImgView im = tc_img(a, w.img);
             const int R = D.freqs[w.s].R, y0 = w.y0, x0 = w.x0;
             const int ncols = kMtTileX + 2 * R, PW = round_up(ncols, 4), PWs = round_up(PW, 8) + 4;
             if (a.bmode == kBoundaryZero) {
                 for (int r = pwarp; r < TY; r += NP / 32) {
                     const int y = y0 + r;
-                    const bool yin = y >= 0 && y < a.H;
-                    const float *src = a.img + (int64_t)(yin ? y : 0) * a.pitch;
+                    const bool yin = y >= 0 && y < im.H;
+                    const float *src = im.img + (int64_t)(yin ? y : 0) * im.pitch;
                     for (int c = lane; c < PW; c += 32) {
                         const int gx = x0 - R + c;
-                        const bool in = yin && c < ncols && gx >= 0 && gx < a.W;
-                        cp_async4(patch + r * PWs + c, in ? (const void *)(src + gx) : (const void *)a.img, in ? 4 : 0);
+                        const bool in = yin && c < ncols && gx >= 0 && gx < im.W;
+                        cp_async4(patch + r * PWs + c, in ? (const void *)(src + gx) : (const void *)im.img, in ? 4 : 0);
                     }
                 }
             } else {
                 for (int r = pwarp; r < TY; r += NP / 32) {
-                    const float *src = a.img + (int64_t)ext_coord(y0 + r, a.H, a.bmode) * a.pitch;
+                    const float *src = im.img + (int64_t)ext_coord(y0 + r, im.H, a.bmode) * im.pitch;
                     for (int c = lane; c < PW; c += 32) {
                         const bool in = c < ncols;
                         cp_async4(patch + r * PWs + c,
-                                  in ? (const void *)(src + ext_coord(x0 - R + c, a.W, a.bmode)) : (const void *)a.img,
+                                  in ? (const void *)(src + ext_coord(x0 - R + c, im.W, a.bmode)) : (const void *)im.img,
                                   in ? 4 : 0);
                     }
                 }
@@ -638,6 +682,11 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
             if (named_barrier_or(1, NP, *abort_s != 0)) break;
             const RowItem w = row_item_mt(a, D, it);
             const int s = w.s, y0 = w.y0, x0 = w.x0;
+            const TcImgView im = tc_img(a, w.img);
+            float cen;
+            int e;
+            tc_centre(a, w.img, cen, e);
+            const float sc = ldexpf(1.f, -e);
             const TcFreqDev f = D.freqs[s];
             const int R = f.R, K = f.Kmt;
             const int ncols = kMtTileX + 2 * R, PW = round_up(ncols, 4);
@@ -656,12 +705,12 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
             for (int idx = ptid; idx < TY * (K / 8); idx += NP) {
                 const int r = idx % TY, k0 = 8 * (idx / TY);
                 const int y = y0 + r;
-                const bool yok = a.bmode != kBoundaryZero || (y >= 0 && y < a.H);
+                const bool yok = a.bmode != kBoundaryZero || (y >= 0 && y < im.H);
                 float v[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
                     const int k = k0 + t, gx = x0 - R + k;
-                    const bool in = yok && k < ncols && (a.bmode != kBoundaryZero || (gx >= 0 && gx < a.W));
+                    const bool in = yok && k < ncols && (a.bmode != kBoundaryZero || (gx >= 0 && gx < im.W));
                     v[t] = in ? (patch[r * PWs + k] - cen) * sc : 0.f;
                 }
                 *reinterpret_cast<uint4 *>(sP + sw128_offset(TY, r, k0)) =
@@ -731,10 +780,14 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
         for (int it = blockIdx.x; it < nitems && !*abort_s; it += gridDim.x) {
             const RowItem w = row_item_mt(a, D, it);
             const int y0 = w.y0;
+            const TcImgView im = tc_img(a, w.img);
+            float cen_unused;
+            int e;
+            tc_centre(a, w.img, cen_unused, e);
             const TcFreqDev f = D.freqs[w.s];
             const float unscale = ldexpf(f.unscale_row, e);
             const int gx = w.x0 + xl;
-            const bool xin = gx < a.W;
+            const bool xin = gx < im.W;
             const int u0 = f.u0, nu = a.nu_f;
             bool ok = true;
             for (int q = 0; q < nu; ++q, ++job) {
@@ -744,9 +797,9 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
                     break;
                 }
                 tc_fence_after();
-                const int64_t sstride = (int64_t)a.W * a.Hp;   // between signals
-                const int64_t bstride = (int64_t)a.W * 8;      // between 8-row blocks
-                uint16_t *dst0 = a.sig + (int64_t)(2 * (u0 + q) + part) * sstride +
+                const int64_t sstride = (int64_t)im.W * im.Hp;   // between signals
+                const int64_t bstride = (int64_t)im.W * 8;       // between 8-row blocks
+                uint16_t *dst0 = im.sig + (int64_t)(2 * (u0 + q) + part) * sstride +
                                  (int64_t)((a.Lpad + y0) >> 3) * bstride + (int64_t)(xin ? gx : 0) * 8;
 #pragma unroll 1
                 for (int c0 = rbase; c0 < rbase + rpw; c0 += 16) {
@@ -831,19 +884,24 @@ __host__ __device__ inline MtColSmem mt_col_smem(int K, int TYC)
 
 struct MtColItem {
     int unit, x0, y0;
+    int img;     // image of a batch (0 for one image)
 };
 __device__ __forceinline__ MtColItem col_item_mt(const TcBankArgs &a, const TcDesc &d, int it)
 {
+    if (a.col_list) {
+        const int4 v = a.col_list[it];
+        return MtColItem{v.y, v.z, v.w, v.x};
+    }
     const int g = it / a.col_cnt, local = it - g * a.col_cnt;
     const int per_unit = a.col_ny * a.col_nx64;
     const int q = local / per_unit, rest = local - q * per_unit;
     const TcFreqDev f = d.freqs[d.forder[g]];
-    return MtColItem{f.u0 + q, (rest % a.col_nx64) * 64, (rest / a.col_nx64) * a.col_mt_ty};
+    return MtColItem{f.u0 + q, (rest % a.col_nx64) * 64, (rest / a.col_nx64) * a.col_mt_ty, 0};
 }
 
 __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __grid_constant__ TcBankArgs a)
 {
-    const int nitems = a.nf * a.col_cnt;
+    const int nitems = a.col_list ? a.n_col : a.nf * a.col_cnt;
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -885,9 +943,6 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     // programmatic dependent of the row pass: the set-up above overlaps its tail; J, the F[1]
     // tables and the centre are read after it completed
     pdl_wait();
-    float cen;
-    int e_unused;
-    image_centre(a, cen, e_unused);
     const uint32_t tmem = *tmem_s;
     const uint32_t idesc = idesc_f16(0, 128, 2 * TYC);
     const int njobs = nitems > (int)blockIdx.x ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -908,7 +963,7 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
                 const int yb0 = (a.Lpad + w.y0 - f.R8) >> 3;
                 const uint32_t dst = smem_u32(sA + st * obuf);
                 for (int kb = 0; kb < nkb; ++kb)
-                    tma_load_4d(dst + kb * 16384u, &a.tmA[0], 0, 2 * w.unit, w.x0, yb0 + 8 * kb, &ab_full[st]);
+                    tma_load_4d(dst + kb * 16384u, tc_img(a, w.img).tm, 0, 2 * w.unit, w.x0, yb0 + 8 * kb, &ab_full[st]);
                 if (TYC == 64) {
                     bulk_load(smem_u32(sB + st * gbuf), u.Gm, nkb * gblk, &ab_full[st]);
                 } else {   // the first 2 TYC rows of each K-block
@@ -973,17 +1028,21 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
         const int part = lane & 1, xl = 16 * quarter + (lane >> 1);
         for (int j = 0; j < njobs; ++j) {
             const MtColItem w = col_item_mt(a, D, blockIdx.x + j * gridDim.x);
+            const TcImgView im = tc_img(a, w.img);
+            float cen;
+            int e_unused;
+            tc_centre(a, w.img, cen, e_unused);
             const TcUnitDev u = D.units[w.unit];
             const TcFreqDev f = D.freqs[u.s];
             const int acc = j & 1;
             const bool paired = u.plane_b >= 0;
             const int x = w.x0 + xl, ybase = w.y0 + (TYC / 2) * half;
-            const bool xok = x < a.W;
+            const bool xok = x < im.W;
             // c B(y) of the warp's rows (lane l < TYC / 2 holds row ybase + l); A(x) of the lane's column
             const int yl = ybase + lane;
-            const float2 byl = (lane < TYC / 2 && yl < a.H) ? __ldg(&a.onesB[(int64_t)w.unit * a.H + yl])
-                                                            : make_float2(0.f, 0.f);
-            const float2 ax = xok ? __ldg(&a.onesA[(int64_t)w.unit * a.W + x]) : make_float2(0.f, 0.f);
+            const float2 byl = (lane < TYC / 2 && yl < im.H) ? __ldg(&im.onesB[(int64_t)w.unit * im.H + yl])
+                                                             : make_float2(0.f, 0.f);
+            const float2 ax = xok ? __ldg(&im.onesA[(int64_t)w.unit * im.W + x]) : make_float2(0.f, 0.f);
             if (!mbar_wait(&tmem_full[acc], (j >> 1) & 1, abort_s)) {
                 if (lane == 0) fail_status(a.status, abort_s, 39);
                 break;
@@ -1014,8 +1073,8 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
                     const int y = ybase + yr;
                     // F_theta = sum G J = (A - B, C + D); F_{pi-theta} = sum G J* = (A + B, C - D)
                     const float fr = part ? A + B : A - B, fi = part ? C - Dd : C + Dd;
-                    if (store && y < a.H)
-                        __stcs(a.out + tc_out_offset(a, plane, y, x),
+                    if (store && y < im.H)
+                        __stcs(im.out + tc_out_offset(a, im, plane, y, x),
                                make_float2(fr + (ax.x * cbr - axi * cbi), fi + (ax.x * cbi + axi * cbr)));
                 }
             }
@@ -1351,6 +1410,44 @@ __global__ void k_minmax(const float *__restrict__ img, int64_t pitch, int H, in
     }
 }
 
+// Batch form of k_minmax: grid (8, 8, images); block (bx, by) of image z writes the (~min, max)
+// keys of its share of the image to partial bx + 8 by (kMmParts per image, no atomics and no
+// zeroing; k_ones reduces them).
+__global__ void k_minmax_batch(const TcBankArgs a)
+{
+    pdl_launch_dependents();
+    const TcImgDev im = a.imgs[blockIdx.z];
+    unsigned lo = 0xffffffffu, hi = 0u;
+    for (int y = blockIdx.y; y < im.H; y += gridDim.y) {
+        const float *row = im.img + (int64_t)y * im.pitch;
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < im.W; x += gridDim.x * blockDim.x) {
+            const unsigned k = fkey(__ldg(row + x));
+            lo = min(lo, k);
+            hi = max(hi, k);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    __shared__ unsigned wlo[32], whi[32];
+    if ((threadIdx.x & 31) == 0) {
+        wlo[threadIdx.x >> 5] = lo;
+        whi[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+            lo = min(lo, wlo[i]);
+            hi = max(hi, whi[i]);
+        }
+        unsigned *p = a.mm_part + ((int64_t)blockIdx.z * kMmParts + blockIdx.y * gridDim.x + blockIdx.x) * 2;
+        p[0] = ~lo;
+        p[1] = hi;
+    }
+}
+
 // pre[u][0][j] = sum_{d=-R}^{-R+j-1} S(d) exp(i w^c d), pre[u][1][j] the same with w^s,
 // j = 0 .. 2R+1 (FP64, phases reduced exactly: w d = pi (w / pi) d mod 2 pi).  One thread per
 // (unit, direction).
@@ -1404,6 +1501,53 @@ __global__ void k_ones(const TcBankArgs a, const TcUnitDev *__restrict__ units, 
             B[(int64_t)u * a.H + pos] = f;
     }
     pdl_wait();
+}
+
+// Batch form of k_ones: grid (blocks, images), the tables of image blockIdx.y; then, once
+// k_minmax_batch has completed, block 0 of every image reduces its partial keys into the
+// image's (centre, exponent).
+__global__ void k_ones_batch(const TcBankArgs a, const TcUnitDev *__restrict__ units,
+                             const TcFreqDev *__restrict__ freqs, int nunits)
+{
+    pdl_launch_dependents();
+    const TcImgDev im = a.imgs[blockIdx.y];
+    const int64_t n = (int64_t)nunits * (im.W + im.H);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int u = (int)(i / (im.W + im.H)), p = (int)(i % (im.W + im.H));
+        const bool is_x = p < im.W;
+        const int pos = is_x ? p : p - im.W, n1 = is_x ? im.W : im.H;
+        const int R = freqs[units[u].s].R;
+        const double2 *pr = a.ones_pre + ((int64_t)u * 2 + (is_x ? 0 : 1)) * a.ones_stride;
+        int lo = -R, hi = R;
+        if (a.bmode == kBoundaryZero) {
+            lo = max(-R, pos - (n1 - 1));
+            hi = min(R, pos);
+        }
+        const double2 v = make_double2(pr[hi + R + 1].x - pr[lo + R].x, pr[hi + R + 1].y - pr[lo + R].y);
+        const float2 f = make_float2((float)v.x, (float)v.y);
+        float2 *dst = const_cast<float2 *>(is_x ? im.onesA + (int64_t)u * im.W + pos : im.onesB + (int64_t)u * im.H + pos);
+        *dst = f;
+    }
+    pdl_wait();
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        const unsigned *p = a.mm_part + (int64_t)blockIdx.y * kMmParts * 2;
+        unsigned nlo = 0u, hik = 0u;
+        for (int i = threadIdx.x; i < kMmParts; i += 32) {
+            nlo = max(nlo, p[2 * i]);
+            hik = max(hik, p[2 * i + 1]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            nlo = max(nlo, __shfl_xor_sync(0xffffffffu, nlo, o));
+            hik = max(hik, __shfl_xor_sync(0xffffffffu, hik, o));
+        }
+        if (threadIdx.x == 0) {
+            float c;
+            int e;
+            centre_of(nlo, hik, c, e);
+            a.img_ce[blockIdx.y] = make_float2(c, (float)e);
+        }
+    }
 }
 
 __global__ void k_build_toeplitz(uint16_t *__restrict__ B, int rows, int K, int off, int R, double sigma, int sB)
@@ -1564,6 +1708,28 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
         return cudaGetLastError();
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_gabor_tc_batch(const TcBankArgs &a0, int sm_count, cudaStream_t st)
+{
+    TcBankArgs a = a0;
+    if (!a.imgs || !a.row_mt || !gabor_tc_mt_fits(a.row_kmax, a.row_pwmax, a.col_kmax)) return cudaErrorInvalidValue;
+    a.col_nst = col_stages(a.col_kmax);
+    const size_t smem_r = gabor_tc_smem_rows_mt(a.row_kmax, a.row_pwmax, a.row_ty);
+    const size_t smem_c = 1024 + mt_col_smem(a.col_kmax, a.col_mt_ty).total;
+    static_assert(kMmParts == 64, "k_minmax_batch runs 8 x 8 blocks per image");
+    k_minmax_batch<<<dim3(8, 8, a.nimg), 256, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(k_ones_batch, dim3(16, a.nimg), dim3(256), 0, st, a, a.units, a.freqs, a.nf * a.nu_f);
+    if (e != cudaSuccess) return e;
+    if (a.n_row > 0) {
+        e = launch_pdl(k_gabor_tc_rows_mt, dim3(std::min(a.n_row, sm_count)), dim3(512), smem_r, st, a);
+        if (e != cudaSuccess) return e;
+    }
+    if (a.n_col > 0)
+        e = launch_pdl(k_gabor_tc_cols_mt, dim3(std::min(a.n_col, sm_count)), dim3(kMtColThreads), smem_c, st, a);
+    return e;
 }
 
 }  // namespace gb

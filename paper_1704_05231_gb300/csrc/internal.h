@@ -133,6 +133,20 @@ struct TcUnitDev {
     const uint16_t *Am;    // modulated-tap row operand [128][Kmt] (FP16, K-major SW128)
     const uint16_t *Gm;    // modulated-tap column operand [128][Kcol] (FP16, K-major SW128)
 };
+// One image of a tensor-core batch (gabor_bank_filter_batch): its input, output, intermediate
+// ([signal][Hp / 8][W][8], image row y at Lpad + y) and F[1] tables.
+struct TcImgDev {
+    const float *img;
+    int64_t pitch;
+    int H, W;
+    float2 *out;
+    int64_t plane;         // H * W
+    uint16_t *sig;
+    int64_t Hp;
+    const float2 *onesA;   // [unit][W]
+    const float2 *onesB;   // [unit][H]
+};
+constexpr int kMmParts = 64;   // partial min / max words per image of a batch (k_minmax)
 struct TcBankArgs {
     const float *img;
     int64_t pitch;
@@ -170,6 +184,16 @@ struct TcBankArgs {
     // FP16, no swizzle) for the column pass's A operand: boxes of 8 x 32 columns x 4 signals x
     // 8 blocks (paired units) and 8 x 64 x 2 x 8 (unpaired units)
     CUtensorMap tmA[2];
+    // Batches (modulated-tap kernels only): per-image views and TMA maps of their intermediates
+    // in device memory, (centre, exponent) per image written by k_ones, kMmParts partial
+    // (~min, max) key pairs per image, and explicit item lists; all nullptr for one image.
+    const TcImgDev *imgs;
+    const CUtensorMap *tmaps;
+    float2 *img_ce;
+    unsigned *mm_part;
+    const int4 *row_list;  // {image, frequency, y0, x0}
+    const int4 *col_list;  // {image, unit, x0, y0}
+    int n_row, n_col, nimg, pad2_;
 };
 struct TcGeometry {
     int R, R8, Krow, Kcol, PW;
@@ -271,6 +295,9 @@ cudaError_t build_gabor_tc_b(uint16_t *Brow, uint16_t *Bcol, int R, double sigma
                              cudaStream_t st);
 cudaError_t gabor_tc_prepare();
 cudaError_t launch_gabor_tc(const TcBankArgs &a, int sm_count, cudaStream_t st);
+// The modulated-tap bank over a batch (a.imgs != nullptr): k_minmax, k_ones, the row and the
+// column kernel, four launches for every image of the batch.
+cudaError_t launch_gabor_tc_batch(const TcBankArgs &a, int sm_count, cudaStream_t st);
 // Prefix sums of S(d) exp(i w^c d) and S(d) exp(i w^s d), d = -R .. R, per unit (FP64).
 cudaError_t build_gabor_tc_prefix(const double *unit_w, const TcUnitDev *units, const TcFreqDev *freqs,
                                   const double *sigma, int nunits, int stride, double2 *pre, cudaStream_t st);
@@ -406,6 +433,18 @@ struct gabor_bank {
     size_t stage_img_bytes = 0;
     void *d_stage_out = nullptr;
     size_t stage_out_bytes = 0;
+    // tensor-core batches (modulated-tap kernels): workspace (intermediates, F[1] tables,
+    // partial min / max keys, per-image centres), device image views, TMA maps and item lists,
+    // with the key of the batch they were built for
+    unsigned char *d_tcb_ws = nullptr;
+    size_t tcb_ws_bytes = 0;
+    gb::TcImgDev *d_tcb_imgs = nullptr;
+    CUtensorMap *d_tcb_maps = nullptr;
+    int tcb_cap = 0;
+    int4 *d_tcb_rows = nullptr, *d_tcb_cols = nullptr;
+    size_t tcb_rows_cap = 0, tcb_cols_cap = 0;
+    int tcb_nrow = 0, tcb_ncol = 0;
+    std::vector<int64_t> tcb_key;
     cudaStream_t copy_stream = nullptr;       // device-to-host copies of finished frequencies
     std::vector<cudaEvent_t> freq_done;       // one per frequency, plus one for the call's start
 };

@@ -145,3 +145,34 @@ def test_tc_batch_matches_fp32_on_small_images():
         b = g16.filter_batch(ts)
         for x, y in zip(a, b):
             assert rel_err(y.cpu().numpy(), x.cpu().numpy()) <= TC_TOL
+
+
+@pytest.mark.parametrize("boundary,layout", [("zero", "planes"), ("mirror", "planes"), ("zero", "pixels")])
+def test_tc_batch_one_launch_set_bitwise_equals_single_calls(boundary, layout):
+    # Tensor-core batch: one k_minmax, one k_ones, one row and one column launch for all images;
+    # every output takes the same MMAs as in a single-image call, so the results are bitwise
+    # those of one call per image, also when replayed from a captured CUDA graph.
+    import torch
+    from paper_1704_05231_gb300 import GaborBank
+    from paper_1704_05231_gb300.bank import capture_graph
+    shapes = [(40, 70), (128, 96), (333, 257), (7, 300), (190, 41)]
+    imgs = [torch.from_numpy(synth.pink_noise([61, i], h, w)).cuda() for i, (h, w) in enumerate(shapes)]
+    th, om, sg = c4_bank()
+    with GaborBank(th, om, sg, precision="fp16_tc", boundary=boundary, layout=layout) as gbk:
+        singles = [gbk.filter(t).clone() for t in imgs]
+        outs = [torch.full_like(s, float("nan")) for s in singles]
+        gbk.filter_batch(imgs, outs)
+        gbk.device_status()
+        for a, b in zip(singles, outs):
+            assert torch.equal(a, b)
+        g = capture_graph(lambda: gbk.filter_batch(imgs, outs))
+        for o in outs:
+            o.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        gbk.device_status()
+        for a, b in zip(singles, outs):
+            assert torch.equal(a, b)
+    if layout == "planes":
+        ref = oracle.gabor_bank(imgs[0].cpu().numpy(), th, om, sg, boundary=boundary)
+        assert rel_err(singles[0].cpu().numpy(), ref) <= TC_TOL
