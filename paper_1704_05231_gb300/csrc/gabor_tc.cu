@@ -860,9 +860,12 @@ __global__ void k_build_mtoeplitz(uint16_t *__restrict__ A, int K, int R, double
 // 64-column tile, 64-row tile; 32-row tiles, MMA N = 64, when the two-deep operands of 64 rows
 // exceed shared memory, as for radius 96).  One producer warp (lane 0) loads each job's J boxes
 // by TMA and its unit's Gm by bulk copies, two jobs deep, and issues the MMAs into two TMEM
-// accumulators; 8 epilogue warps add the c A(x) B(y) correction and store complex64.
+// accumulators; 16 epilogue warps (one row quarter x one TMEM lane quarter each) read their
+// accumulator columns with one wait, release the accumulator, add the c A(x) B(y) correction
+// and store complex64.
 constexpr int kMtColAcc = 2;       // TMEM accumulators (128 columns each)
-constexpr int kMtColThreads = 32 * (8 + 1);
+constexpr int kMtColEpiWarps = 16;
+constexpr int kMtColThreads = 32 * (kMtColEpiWarps + 1);
 
 struct MtColSmem {
     uint32_t a_off, b_off, desc_off, bar_off, misc_off, total;
@@ -925,7 +928,7 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(&tmem_full[i], 1);
-            mbar_init(&tmem_empty[i], 8);
+            mbar_init(&tmem_empty[i], kMtColEpiWarps);
             mbar_init(&ab_full[i], 1);
             mbar_init(&ab_empty[i], 1);
         }
@@ -947,7 +950,7 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     const uint32_t idesc = idesc_f16(0, 128, 2 * TYC);
     const int njobs = nitems > (int)blockIdx.x ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
-    if (warp == 8) {
+    if (warp == kMtColEpiWarps) {
         // -------------------------------------------------------------- producer (lane 0)
         if (lane == 0) {
             auto item = [&](int j) { return col_item_mt(a, D, blockIdx.x + j * gridDim.x); };
@@ -1020,12 +1023,15 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     } else {
         // -------------------------------------------------------------- epilogue
         // TMEM lane n = 2 x + part (part 0: Re J, 1: Im J), column m = 2 y + g (g 0: Re G,
-        // 1: Im G).  Warp w reads quarter w & 3 (columns x 16 (w & 3) .. + 15) and rows y
-        // (TYC / 2) (w >> 2) .. + TYC / 2 - 1.  The part-0 lane of a column stores F_theta, the
-        // part-1 lane F_{pi - theta} (paired units).
-        const int quarter = warp & 3, half = warp >> 2;
+        // 1: Im G).  Warp w reads lane quarter w & 3 (columns x 16 (w & 3) .. + 15) and the
+        // TYC / 4 rows y from (TYC / 4) (w >> 2) on, with one or two 16-column loads waited for
+        // once.  The part-0 lane of a column stores F_theta, the part-1 lane F_{pi - theta}
+        // (paired units).
+        const int quarter = warp & 3, rq = warp >> 2;
+        const int rpw = TYC / 4;                       // rows per warp: 16 or 8
         const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
         const int part = lane & 1, xl = 16 * quarter + (lane >> 1);
+        const float sgn = part ? -1.f : 1.f;
         for (int j = 0; j < njobs; ++j) {
             const MtColItem w = col_item_mt(a, D, blockIdx.x + j * gridDim.x);
             const TcImgView im = tc_img(a, w.img);
@@ -1036,51 +1042,50 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
             const TcFreqDev f = D.freqs[u.s];
             const int acc = j & 1;
             const bool paired = u.plane_b >= 0;
-            const int x = w.x0 + xl, ybase = w.y0 + (TYC / 2) * half;
+            const int x = w.x0 + xl, ybase = w.y0 + rpw * rq;
             const bool xok = x < im.W;
-            // c B(y) of the warp's rows (lane l < TYC / 2 holds row ybase + l); A(x) of the lane's column
+            // c B(y) of the warp's rows (lane l < rpw holds row ybase + l); A(x) of the lane's column
             const int yl = ybase + lane;
-            const float2 byl = (lane < TYC / 2 && yl < im.H) ? __ldg(&im.onesB[(int64_t)w.unit * im.H + yl])
-                                                             : make_float2(0.f, 0.f);
+            float2 byl = (lane < rpw && yl < im.H) ? __ldg(&im.onesB[(int64_t)w.unit * im.H + yl]) : make_float2(0.f, 0.f);
+            byl.x *= cen;
+            byl.y *= cen;
             const float2 ax = xok ? __ldg(&im.onesA[(int64_t)w.unit * im.W + x]) : make_float2(0.f, 0.f);
+            // correction c A(x) B(y) for theta, c conj(A(x)) B(y) for pi - theta
+            const float axr = ax.x, axi = sgn * ax.y;
+            const int plane = part ? u.plane_b : u.plane_a;
+            const bool store = xok && (part == 0 || paired);
+            const int nrows = min(rpw, im.H - ybase);
+            const int64_t ostep = a.layout ? (int64_t)im.W * a.nplanes : (int64_t)im.W;
+            float2 *o = im.out + tc_out_offset(a, im, store ? plane : 0, max(ybase, 0), xok ? x : 0);
             if (!mbar_wait(&tmem_full[acc], (j >> 1) & 1, abort_s)) {
                 if (lane == 0) fail_status(a.status, abort_s, 39);
                 break;
             }
             tc_fence_after();
-            const float unscale = f.unscale_col;
-            const bool store = xok && (part == 0 || paired);
-            const int plane = part ? u.plane_b : u.plane_a;
-            // correction c A(x) B(y) for theta, c conj(A(x)) B(y) for pi - theta
-            const float axi = part ? -ax.y : ax.y;
-#pragma unroll 1
-            for (int c0 = 0; c0 < TYC; c0 += 16) {   // accumulator columns TYC half + c0 .. + 15
-                uint32_t r[16];
-                tmem_ld16_async(tmem + lane_base + 128u * acc + TYC * half + c0, r);
-                tmem_wait_ld();
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const float gr = __uint_as_float(r[2 * t]) * unscale;       // sum Re G x (this part of J)
-                    const float gi = __uint_as_float(r[2 * t + 1]) * unscale;   // sum Im G x (this part of J)
-                    const float or_ = __shfl_xor_sync(0xffffffffu, gr, 1);
-                    const float oi = __shfl_xor_sync(0xffffffffu, gi, 1);
-                    // A = sum Re G Re J, B = sum Im G Im J, C = sum Im G Re J, D = sum Re G Im J
-                    const float A = part ? or_ : gr, C = part ? oi : gi;
-                    const float Dd = part ? gr : or_, B = part ? gi : oi;
-                    const int yr = (c0 >> 1) + t;                // row within the warp's TYC / 2
-                    const float cbr = cen * __shfl_sync(0xffffffffu, byl.x, yr);   // c B(y)
-                    const float cbi = cen * __shfl_sync(0xffffffffu, byl.y, yr);
-                    const int y = ybase + yr;
-                    // F_theta = sum G J = (A - B, C + D); F_{pi-theta} = sum G J* = (A + B, C - D)
-                    const float fr = part ? A + B : A - B, fi = part ? C - Dd : C + Dd;
-                    if (store && y < im.H)
-                        __stcs(im.out + tc_out_offset(a, im, plane, y, x),
-                               make_float2(fr + (ax.x * cbr - axi * cbi), fi + (ax.x * cbi + axi * cbr)));
-                }
-            }
+            uint32_t r[32];
+            const uint32_t ta = tmem + lane_base + 128u * acc + 2 * rpw * rq;
+            tmem_ld16_async(ta, *reinterpret_cast<uint32_t(*)[16]>(&r[0]));
+            if (rpw == 16) tmem_ld16_async(ta + 16, *reinterpret_cast<uint32_t(*)[16]>(&r[16]));
+            tmem_wait_ld();
+            // the accumulator is free for the next job's MMA once the values are in registers
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tmem_empty[acc]);
+            const float unscale = f.unscale_col;
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                if (t >= rpw) break;
+                // this lane: (sum Re G, sum Im G) x (its part of J); the partner lane the other part
+                const float gr = __uint_as_float(r[2 * t]) * unscale, gi = __uint_as_float(r[2 * t + 1]) * unscale;
+                const float or_ = __shfl_xor_sync(0xffffffffu, gr, 1), oi = __shfl_xor_sync(0xffffffffu, gi, 1);
+                const float cbr = __shfl_sync(0xffffffffu, byl.x, t), cbi = __shfl_sync(0xffffffffu, byl.y, t);
+                // part 0 (A = gr, C = gi, D = or_, B = oi): F_theta = (A - B, C + D);
+                // part 1 (D = gr, B = gi, A = or_, C = oi): F_{pi-theta} = (A + B, C - D)
+                const float fr = part ? or_ + gi : gr - oi;
+                const float fi = part ? oi - gr : gi + or_;
+                if (store && t < nrows) __stcs(o, make_float2(fr + (axr * cbr - axi * cbi), fi + (axr * cbi + axi * cbr)));
+                o += ostep;
+            }
         }
     }
     tc_fence_before();
