@@ -543,7 +543,7 @@ gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
     for (int i = 0; i < nu; ++i) {
         const int R = h->freqs[h->units[i].s].R;
         off_am[i] = am_total;
-        am_total += (size_t)128 * gabor_tc_mt_k(R);
+        am_total += ((size_t)gabor_tc_mt_am_elems(R) + 127) / 128 * 128;   // 256-byte aligned strips
         h->tc_mt_kmax = std::max(h->tc_mt_kmax, gabor_tc_mt_k(R));
         h->tc_mt_pwmax = std::max(h->tc_mt_pwmax, gabor_tc_mt_pw(R));
     }
@@ -552,15 +552,16 @@ gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
     GB_TRY(dalloc(&h->d_tcAm, std::max<size_t>(am_total, 1)));
     std::vector<size_t> off_gm(nu);
     size_t gm_total = 0;
+    const int col_ty = gabor_tc_mt_col_ty(h->tc_col_kmax);
     for (int i = 0; i < nu; ++i) {
         off_gm[i] = gm_total;
-        gm_total += (size_t)128 * gabor_tc_geometry(h->freqs[h->units[i].s].R).Kcol;
+        gm_total += ((size_t)gabor_tc_mt_gm_elems(h->freqs[h->units[i].s].R, col_ty) + 127) / 128 * 128;
     }
     GB_TRY(dalloc(&h->d_tcGm, std::max<size_t>(gm_total, 1)));
     for (int i = 0; i < nu; ++i) {
         const Freq &fq = h->freqs[h->units[i].s];
         GB_CU(build_gabor_tc_am(h->d_tcAm + off_am[i], fq.R, fq.sigma, h->units[i].wc, st));
-        GB_CU(build_gabor_tc_gm(h->d_tcGm + off_gm[i], fq.R, fq.sigma, h->units[i].ws, st));
+        GB_CU(build_gabor_tc_gm(h->d_tcGm + off_gm[i], fq.R, fq.sigma, h->units[i].ws, col_ty, st));
     }
     std::vector<TcUnitDev> ud(nu);
     const int K = (int)h->theta.size();

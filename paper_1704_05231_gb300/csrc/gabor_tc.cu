@@ -564,6 +564,18 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
 constexpr int kMtTileX = 64;     // output columns per item (MMA M = 2 x 64)
 constexpr int kMtEpiWarps = 8;
 
+// The modulated-tap operands are banded Toeplitz matrices with interleaved (re, im) rows:
+// row n = 2 x + part, column k, value t_part(k - x - off).  With x counted backwards from the
+// tile's last row, the no-swizzle K-major core matrix of 8-row group g and K-group kc holds
+// t(4 (2 kc + g) + c + r / 2 - off') at (row r, element c): it depends on j = 2 kc + g only.
+// So the operand is a strip of core matrices Q_j, 128 bytes each, read by one descriptor with
+// 256 bytes between K-groups and 128 bytes between row groups; `rows` rows and K columns take
+// 2 K / 8 + rows / 8 cores (instead of rows x K elements).
+__host__ __device__ constexpr int tstrip_cores(int K, int rows) { return 2 * (K / 8) + rows / 8; }
+__host__ __device__ constexpr uint32_t tstrip_bytes(int K, int rows) { return (uint32_t)tstrip_cores(K, rows) * 128u; }
+// Descriptor of K step ks (16 columns) of a strip at shared address s0.
+__device__ __forceinline__ uint64_t tstrip_desc(uint32_t s0, int ks) { return smem_desc_kmajor(s0 + 512u * ks, 256, 128); }
+
 struct MtSmem {
     uint32_t a_off, p_off, patch_off, desc_off, bar_off, misc_off, total;
 };
@@ -571,8 +583,8 @@ struct MtSmem {
 __host__ __device__ inline MtSmem mt_smem(int K, int PW, int TY)
 {
     MtSmem L;
-    L.a_off = 0;                                              // [2] x 128 x K FP16 (SW128)
-    L.p_off = L.a_off + 2u * 128 * K * 2;                     // TY x K FP16 (SW128)
+    L.a_off = 0;                                              // [2] strips of 128 rows x K
+    L.p_off = (L.a_off + 2u * tstrip_bytes(K, 128) + 1023) & ~1023u;   // TY x K FP16 (SW128)
     L.patch_off = L.p_off + (uint32_t)TY * K * 2;             // TY x PWs FP32
     L.desc_off = (L.patch_off + (uint32_t)TY * (round_up(PW, 8) + 4) * 4 + 127) & ~127u;
     L.bar_off = L.desc_off + kDescBytes;
@@ -609,10 +621,11 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
     uint64_t *a_empty = bars + 6;      // [2] commit: the MMA reading the buffer is done
     uint64_t *p_empty = bars + 8;      // [1] commit: the item's MMAs (reading P) are done
     uint64_t *drain = bars + 9;
+    uint64_t *p_full = bars + 10;      // [1] the producers built the item's P
     uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
     const TcDesc D = load_desc(a, sm + L.desc_off);
-    const uint32_t abuf = 128u * a.row_kmax * 2;
+    const uint32_t abuf = tstrip_bytes(a.row_kmax, 128);
 
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
@@ -623,6 +636,7 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
         }
         mbar_init(p_empty, 1);
         mbar_init(drain, 1);
+        mbar_init(p_full, 1);
         *abort_s = 0;
         mbar_fence_init();
     }
@@ -640,28 +654,95 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
     const uint32_t tmem = *tmem_s;
     const uint32_t idesc = idesc_f16(0, 128, TY);
 
-    if (warp >= kMtEpiWarps) {
-        // -------------------------------------------------------------- producers
-        constexpr int NP = 32 * (16 - kMtEpiWarps);
+    if (warp == 15) {
+        // -------------------------------------------------------------- MMA warp (lane 0)
+        // Runs ahead of the producers: the Am copy of job jq (unit q of the CTA's item jq / nu)
+        // goes into buffer jq & 1 as soon as the MMA of job jq - 2 has released it, across
+        // item boundaries; the MMAs of an item wait for its P (p_full) and release it (p_empty).
+        if (lane == 0) {
+            const int nu = a.nu_f;
+            const int my_items = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+            const int njobs = my_items * nu;
+            int issued = 0, landed = 0;
+            bool ok = true;
+            auto issue_a = [&]() {   // the Am copy of job `issued`
+                const int jq = issued, buf = jq & 1;
+                if (jq >= 2 && !mbar_wait(&a_empty[buf], ((jq - 2) >> 1) & 1, abort_s)) return false;
+                const RowItem w = row_item_mt(a, D, blockIdx.x + (jq / nu) * gridDim.x);
+                const TcFreqDev f = D.freqs[w.s];
+                const uint32_t abytes = tstrip_bytes(f.Kmt, 128);
+                mbar_arrive_expect_tx(&a_full[buf], abytes);
+                bulk_load(smem_u32(sA + buf * abuf), D.units[f.u0 + jq % nu].Am, abytes, &a_full[buf]);
+                ++issued;
+                return true;
+            };
+            for (int nitem = 0; nitem < my_items && ok; ++nitem) {
+                const RowItem w = row_item_mt(a, D, blockIdx.x + nitem * gridDim.x);
+                const int K = D.freqs[w.s].Kmt;
+                while (ok && issued < njobs && issued < nitem * nu + 2) ok = issue_a();
+                if (ok) ok = mbar_wait(p_full, nitem & 1, abort_s);   // this item's P
+                for (int q = 0; q < nu && ok; ++q) {
+                    const int jq = nitem * nu + q, b = jq & 1;
+                    ok = mbar_wait(&a_full[b], (jq >> 1) & 1, abort_s);
+                    if (ok) landed = jq + 1;   // copy jq (copies go in job order)
+                    if (ok && jq >= 2) ok = mbar_wait(&tmem_empty[b], ((jq - 2) >> 1) & 1, abort_s);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + b * abuf), p0 = smem_u32(sP);
+                    for (int kb = 0; kb < K / 64; ++kb)
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            tc_mma_f16(tmem + (uint32_t)TY * b, tstrip_desc(a0, 4 * kb + kk),
+                                       smem_desc_sw128(p0 + kb * TY * 128) + 2 * kk, idesc, (kb | kk) != 0);
+                    tc_commit(&tmem_full[b]);
+                    tc_commit(&a_empty[b]);
+                    // the next copies (this item's later units, or the next item's first ones)
+                    while (ok && issued < njobs && issued < jq + 3) ok = issue_a();
+                }
+                if (ok) tc_commit(p_empty);
+            }
+            if (!ok) fail_status(a.status, abort_s, 27);
+            tc_commit(drain);
+            if (!mbar_wait(drain, 0, abort_s)) {
+                volatile int dummy = 0;
+                mbar_wait(drain, 0, &dummy);
+            }
+            // bulk copies issued but not waited for (after a stop) land before shared memory is
+            // released; copy i went to buffer i & 1 as its (i >> 1)-th use
+            for (int i = landed; i < issued; ++i) {
+                volatile int dummy = 0;
+                mbar_wait(&a_full[i & 1], (i >> 1) & 1, &dummy);
+            }
+        }
+    } else if (warp >= kMtEpiWarps) {
+        // -------------------------------------------------------------- producers (warps 8-14)
+        constexpr int NP = 32 * (15 - kMtEpiWarps);
         const int ptid = tid - 32 * kMtEpiWarps, pwarp = warp - kMtEpiWarps;
-        int job = 0, nitem = 0;
-        int a_issued = 0, a_landed = 0;   // ptid 0: Am copies issued / waited for
-        bool ok = true;
-        // cp.async of item it's patch: rows y0 .. y0 + TY - 1, columns x0 - R .. x0 + 63 + R
+        int nitem = 0;
+        // cp.async of item it's patch: rows y0 .. y0 + TY - 1, columns x0 - R .. x0 + 63 + R;
+        // interior rows that start on a 16-byte boundary by 16-byte copies
         auto stage = [&](int it) {
             const RowItem w = row_item_mt(a, D, it);
             const TcImgView im = tc_img(a, w.img);
             const int R = D.freqs[w.s].R, y0 = w.y0, x0 = w.x0;
             const int ncols = kMtTileX + 2 * R, PW = round_up(ncols, 4), PWs = round_up(PW, 8) + 4;
             if (a.bmode == kBoundaryZero) {
+                const bool xin = x0 - R >= 0 && x0 - R + ncols <= im.W;
+                const int n16 = ncols >> 2;
                 for (int r = pwarp; r < TY; r += NP / 32) {
                     const int y = y0 + r;
                     const bool yin = y >= 0 && y < im.H;
                     const float *src = im.img + (int64_t)(yin ? y : 0) * im.pitch;
-                    for (int c = lane; c < PW; c += 32) {
-                        const int gx = x0 - R + c;
-                        const bool in = yin && c < ncols && gx >= 0 && gx < im.W;
-                        cp_async4(patch + r * PWs + c, in ? (const void *)(src + gx) : (const void *)im.img, in ? 4 : 0);
+                    if (yin && xin && (reinterpret_cast<uintptr_t>(src + (x0 - R)) & 15) == 0) {
+                        const float *s0 = src + (x0 - R);
+                        for (int c = lane; c < n16; c += 32) cp_async16(patch + r * PWs + 4 * c, s0 + 4 * c);
+                        for (int c = 4 * n16 + lane; c < ncols; c += 32) cp_async4(patch + r * PWs + c, s0 + c, 4);
+                    } else {
+                        for (int c = lane; c < PW; c += 32) {
+                            const int gx = x0 - R + c;
+                            const bool in = yin && c < ncols && gx >= 0 && gx < im.W;
+                            cp_async4(patch + r * PWs + c, in ? (const void *)(src + gx) : (const void *)im.img, in ? 4 : 0);
+                        }
                     }
                 }
             } else {
@@ -681,17 +762,16 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
         for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++nitem) {
             if (named_barrier_or(1, NP, *abort_s != 0)) break;
             const RowItem w = row_item_mt(a, D, it);
-            const int s = w.s, y0 = w.y0, x0 = w.x0;
+            const int y0 = w.y0, x0 = w.x0;
             const TcImgView im = tc_img(a, w.img);
             float cen;
             int e;
             tc_centre(a, w.img, cen, e);
             const float sc = ldexpf(1.f, -e);
-            const TcFreqDev f = D.freqs[s];
+            const TcFreqDev f = D.freqs[w.s];
             const int R = f.R, K = f.Kmt;
             const int ncols = kMtTileX + 2 * R, PW = round_up(ncols, 4);
             const int PWs = round_up(PW, 8) + 4;
-            const int u0 = f.u0, nu = a.nu_f;
             // P is free once the previous item's MMAs are done
             bool failed = nitem > 0 && !mbar_wait(p_empty, (nitem - 1) & 1, abort_s);
             if (named_barrier_or(1, NP, failed)) {
@@ -709,73 +789,29 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
                 float v[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
-                    const int k = k0 + t, gx = x0 - R + k;
-                    const bool in = yok && k < ncols && (a.bmode != kBoundaryZero || (gx >= 0 && gx < im.W));
-                    v[t] = in ? (patch[r * PWs + k] - cen) * sc : 0.f;
+                    const int kk = k0 + t, gx = x0 - R + kk;
+                    const bool in = yok && kk < ncols && (a.bmode != kBoundaryZero || (gx >= 0 && gx < im.W));
+                    v[t] = in ? (patch[r * PWs + kk] - cen) * sc : 0.f;
                 }
                 *reinterpret_cast<uint4 *>(sP + sw128_offset(TY, r, k0)) =
                     make_uint4(h2pack(v[0], v[1]), h2pack(v[2], v[3]), h2pack(v[4], v[5]), h2pack(v[6], v[7]));
             }
             fence_proxy_async_smem();
-            named_barrier(1, NP);   // the FP32 patch is free: stage the next item's
+            named_barrier(1, NP);   // P built; the FP32 patch is free: stage the next item's
+            if (ptid == 0) mbar_arrive(p_full);
             if (it + (int)gridDim.x < nitems) stage(it + gridDim.x);
-            if (ptid == 0) {
-                const uint32_t abytes = 128u * K * 2;
-                // Am of unit q into buffer (job + q) & 1 once the MMA that last read it is done
-                auto issue_a = [&](int q) {
-                    const int jq = job + q, buf = jq & 1;
-                    if (jq >= 2 && !mbar_wait(&a_empty[buf], ((jq - 2) >> 1) & 1, abort_s)) return false;
-                    mbar_arrive_expect_tx(&a_full[buf], abytes);
-                    bulk_load(smem_u32(sA + buf * abuf), D.units[u0 + q].Am, abytes, &a_full[buf]);
-                    ++a_issued;
-                    return true;
-                };
-                for (int q = 0; q < nu && q < 2 && ok; ++q) ok = issue_a(q);
-                for (int q = 0; q < nu && ok; ++q) {
-                    const int jq = job + q, b = jq & 1;
-                    ok = mbar_wait(&a_full[b], (jq >> 1) & 1, abort_s);
-                    if (ok) a_landed = jq + 1;   // copy jq (copies go in job order)
-                    if (ok && jq >= 2) ok = mbar_wait(&tmem_empty[b], ((jq - 2) >> 1) & 1, abort_s);
-                    if (!ok) break;
-                    tc_fence_after();
-                    const uint32_t a0 = smem_u32(sA + b * abuf), p0 = smem_u32(sP);
-                    for (int kb = 0; kb < K / 64; ++kb)
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            tc_mma_f16(tmem + (uint32_t)TY * b, smem_desc_sw128(a0 + kb * 128 * 128) + 2 * kk,
-                                       smem_desc_sw128(p0 + kb * TY * 128) + 2 * kk, idesc, (kb | kk) != 0);
-                    tc_commit(&tmem_full[b]);
-                    tc_commit(&a_empty[b]);
-                    if (q + 2 < nu) ok = issue_a(q + 2);
-                }
-                tc_commit(p_empty);
-                if (!ok) fail_status(a.status, abort_s, 27);
-            }
-            job += nu;
         }
         cp_async_wait<0>();   // a patch staged before a stop lands before shared memory is released
-        if (ptid == 0) {
-            tc_commit(drain);
-            if (!mbar_wait(drain, 0, abort_s)) {
-                volatile int dummy = 0;
-                mbar_wait(drain, 0, &dummy);
-            }
-            // bulk copies issued but not waited for (after an abort) land before shared memory
-            // is released; copy i went to buffer i & 1 as its (i >> 1)-th use
-            for (int i = a_landed; i < a_issued; ++i) {
-                volatile int dummy = 0;
-                mbar_wait(&a_full[i & 1], (i >> 1) & 1, &dummy);
-            }
-        }
     } else {
         // -------------------------------------------------------------- epilogue
-        // TMEM lane n = 2 x + part: warp w reads quarter w & 3 (columns 16 (w & 3) .. + 15) and
-        // rows [rbase, rbase + TY / 2), and stores its part of J (signal 2 unit + part of the
-        // intermediate; the column pass demodulates nothing, its taps are modulated too).
+        // TMEM lane n = 2 x' + part, x' = 63 - x (the operand strip runs backwards in x): warp w
+        // reads quarter w & 3 (x' 16 (w & 3) .. + 15) and rows [rbase, rbase + TY / 2), and
+        // stores its part of J (signal 2 unit + part of the intermediate; the column pass
+        // demodulates nothing, its taps are modulated too).
         const int quarter = warp & 3, half = warp >> 2;
         const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
         const int rpw = TY / 2, rbase = half * rpw;
-        const int part = lane & 1, xl = 16 * quarter + (lane >> 1);
+        const int part = lane & 1, xl = kMtTileX - 1 - (16 * quarter + (lane >> 1));
         int job = 0;
         for (int it = blockIdx.x; it < nitems && !*abort_s; it += gridDim.x) {
             const RowItem w = row_item_mt(a, D, it);
@@ -831,21 +867,23 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
     if (warp == 0) tmem_dealloc(tmem, 128);
 }
 
-// Am of one unit: rows n = 2 x + (0 | 1), x < 64, Am[n][k] = S(d) (cos, -sin)(w^c d) 2^sB,
-// d = k - x - R, zero outside |d| <= R; FP64, rounded to FP16, K-major SW128.
-__global__ void k_build_mtoeplitz(uint16_t *__restrict__ A, int K, int R, double sigma, double wc, int sB)
+// Strip of a modulated Toeplitz operand (see tstrip_cores): core j, row r, element c holds
+// S(d) (cos, -sin)(w d) 2^sB for row part r & 1, d = 4 j + c + r / 2 - off, zero outside
+// |d| <= R; FP64, rounded to FP16.  Row pass (Am): off = 63 + R, w = w^c (rows x of the 64-
+// column tile backwards, k the input column from x0 - R on).  Column pass (Gm): off =
+// TYC - 1 + R8, w = w^s (rows y of the job backwards, l the window row from y0 - R8 on).
+__global__ void k_build_tstrip(uint16_t *__restrict__ Q, int ncores, int off, int R, double sigma, double w, int sB)
 {
-    const int n = 128 * K;
+    const int n = 64 * ncores;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int row = i / K, k = i % K;
-        const int x = row >> 1, part = row & 1;
-        const int d = k - x - R;
+        const int j = i >> 6, r = (i >> 3) & 7, c = i & 7;
+        const int d = 4 * j + c + (r >> 1) - off;
         double v = 0.0;
         if (d >= -R && d <= R) {
             const double g = exp(-(double)d * d / (2.0 * sigma * sigma)) / (2.5066282746310002 * sigma);
-            v = ldexp(part ? -g * sin(wc * d) : g * cos(wc * d), sB);
+            v = ldexp((r & 1) ? -g * sin(w * d) : g * cos(w * d), sB);
         }
-        A[sw128_offset(128, row, k) / 2] = __half_as_ushort(__float2half_rn((float)v));
+        Q[i] = __half_as_ushort(__float2half_rn((float)v));
     }
 }
 
@@ -871,14 +909,14 @@ struct MtColSmem {
     uint32_t a_off, b_off, desc_off, bar_off, misc_off, total;
 };
 
-// TYC: output rows per job (64; 32 when the operands of 64 do not fit): the B operand holds
-// the first 2 TYC rows of each 128-row K-block of Gm.
+// TYC: output rows per job (64; 32 when the operands of 64 do not fit); the B operand is the
+// unit's strip of 2 TYC rows x K.
 __host__ __device__ inline MtColSmem mt_col_smem(int K, int TYC)
 {
     MtColSmem L;
     L.a_off = 0;                                   // [2] x 128 x K (no swizzle, core matrices)
-    L.b_off = L.a_off + 2u * 128 * K * 2;          // [2] x 2 TYC x K (SW128)
-    L.desc_off = L.b_off + 2u * (2 * TYC) * K * 2;
+    L.b_off = L.a_off + 2u * 128 * K * 2;          // [2] strips of 2 TYC rows x K
+    L.desc_off = (L.b_off + 2u * tstrip_bytes(K, 2 * TYC) + 127) & ~127u;
     L.bar_off = L.desc_off + kDescBytes;
     L.misc_off = L.bar_off + 16 * 8;
     L.total = L.misc_off + 64;
@@ -921,8 +959,7 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
     const uint32_t obuf = 128u * a.col_kmax * 2;            // an A buffer
-    const uint32_t gbuf = 2u * TYC * a.col_kmax * 2;         // a B buffer
-    const uint32_t gblk = 2u * TYC * 128;                    // one K-block of B
+    const uint32_t gbuf = tstrip_bytes(a.col_kmax, 2 * TYC);   // a B buffer
     const TcDesc D = load_desc(a, sm + L.desc_off);
 
     if (tid == 0) {
@@ -962,17 +999,13 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
                 const TcUnitDev u = D.units[w.unit];
                 const TcFreqDev f = D.freqs[u.s];
                 const int st = j & 1, nkb = f.Kcol / 64;
-                mbar_arrive_expect_tx(&ab_full[st], nkb * (16384u + gblk));
+                const uint32_t bbytes = tstrip_bytes(f.Kcol, 2 * TYC);
+                mbar_arrive_expect_tx(&ab_full[st], nkb * 16384u + bbytes);
                 const int yb0 = (a.Lpad + w.y0 - f.R8) >> 3;
                 const uint32_t dst = smem_u32(sA + st * obuf);
                 for (int kb = 0; kb < nkb; ++kb)
                     tma_load_4d(dst + kb * 16384u, tc_img(a, w.img).tm, 0, 2 * w.unit, w.x0, yb0 + 8 * kb, &ab_full[st]);
-                if (TYC == 64) {
-                    bulk_load(smem_u32(sB + st * gbuf), u.Gm, nkb * gblk, &ab_full[st]);
-                } else {   // the first 2 TYC rows of each K-block
-                    for (int kb = 0; kb < nkb; ++kb)
-                        bulk_load(smem_u32(sB + st * gbuf) + kb * gblk, u.Gm + (size_t)kb * 128 * 64, gblk, &ab_full[st]);
-                }
+                bulk_load(smem_u32(sB + st * gbuf), u.Gm, bbytes, &ab_full[st]);
             };
             int issued = 0, landed = 0;
             for (; issued < 2 && issued < njobs; ++issued) issue(issued);
@@ -995,7 +1028,7 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
                         tc_mma_f16(tmem + 128u * acc, smem_desc_kmajor(a0 + kb * 16384 + kk * 4096, 2048, 128),
-                                   smem_desc_sw128(b0 + kb * gblk) + 2 * kk, idesc, (kb | kk) != 0);
+                                   tstrip_desc(b0, 4 * kb + kk), idesc, (kb | kk) != 0);
                 tc_commit(&tmem_full[acc]);
                 tc_commit(&ab_empty[st]);
                 // job j + 2 goes into these buffers once this MMA is done with them
@@ -1022,10 +1055,11 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
         }
     } else {
         // -------------------------------------------------------------- epilogue
-        // TMEM lane n = 2 x + part (part 0: Re J, 1: Im J), column m = 2 y + g (g 0: Re G,
-        // 1: Im G).  Warp w reads lane quarter w & 3 (columns x 16 (w & 3) .. + 15) and the
-        // TYC / 4 rows y from (TYC / 4) (w >> 2) on, with one or two 16-column loads waited for
-        // once.  The part-0 lane of a column stores F_theta, the part-1 lane F_{pi - theta}
+        // TMEM lane n = 2 x + part (part 0: Re J, 1: Im J), column m = 2 y' + g (g 0: Re G,
+        // 1: Im G), y' = TYC - 1 - y (the Gm strip runs backwards in y).  Warp w reads lane
+        // quarter w & 3 (columns x 16 (w & 3) .. + 15) and the TYC / 4 rows y from (TYC / 4) (w >> 2)
+        // on, one block of 2 TYC / 4 accumulator columns, with one or two 16-column loads waited
+        // for once.  The part-0 lane of a column stores F_theta, the part-1 lane F_{pi - theta}
         // (paired units).
         const int quarter = warp & 3, rq = warp >> 2;
         const int rpw = TYC / 4;                       // rows per warp: 16 or 8
@@ -1063,7 +1097,7 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
             }
             tc_fence_after();
             uint32_t r[32];
-            const uint32_t ta = tmem + lane_base + 128u * acc + 2 * rpw * rq;
+            const uint32_t ta = tmem + lane_base + 128u * acc + 2 * (TYC - rpw * (rq + 1));
             tmem_ld16_async(ta, *reinterpret_cast<uint32_t(*)[16]>(&r[0]));
             if (rpw == 16) tmem_ld16_async(ta + 16, *reinterpret_cast<uint32_t(*)[16]>(&r[16]));
             tmem_wait_ld();
@@ -1072,11 +1106,15 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
             __syncwarp();
             if (lane == 0) mbar_arrive(&tmem_empty[acc]);
             const float unscale = f.unscale_col;
+            // loaded value pair tt belongs to row t = rpw - 1 - tt (the strip runs backwards in
+            // y): walk the rows from the last one up, keeping the register index static
+            o += (int64_t)(rpw - 1) * ostep;
 #pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                if (t >= rpw) break;
+            for (int tt = 0; tt < 16; ++tt) {
+                if (tt >= rpw) break;
+                const int t = rpw - 1 - tt;
                 // this lane: (sum Re G, sum Im G) x (its part of J); the partner lane the other part
-                const float gr = __uint_as_float(r[2 * t]) * unscale, gi = __uint_as_float(r[2 * t + 1]) * unscale;
+                const float gr = __uint_as_float(r[2 * tt]) * unscale, gi = __uint_as_float(r[2 * tt + 1]) * unscale;
                 const float or_ = __shfl_xor_sync(0xffffffffu, gr, 1), oi = __shfl_xor_sync(0xffffffffu, gi, 1);
                 const float cbr = __shfl_sync(0xffffffffu, byl.x, t), cbi = __shfl_sync(0xffffffffu, byl.y, t);
                 // part 0 (A = gr, C = gi, D = or_, B = oi): F_theta = (A - B, C + D);
@@ -1084,7 +1122,7 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
                 const float fr = part ? or_ + gi : gr - oi;
                 const float fi = part ? oi - gr : gi + or_;
                 if (store && t < nrows) __stcs(o, make_float2(fr + (axr * cbr - axi * cbi), fi + (axr * cbi + axi * cbr)));
-                o += ostep;
+                o -= ostep;
             }
         }
     }
@@ -1092,24 +1130,6 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     __syncthreads();
     tc_fence_after();
     if (warp == 0) tmem_dealloc(tmem, 128 * kMtColAcc);
-}
-
-// Gm of one unit: rows m = 2 y + (0 | 1), y < 64, Gm[m][l] = S(d) (cos, -sin)(w^s d) 2^sB,
-// d = l - y - R8, zero outside |d| <= R; FP64, rounded to FP16, K-major SW128.
-__global__ void k_build_mtoeplitz_col(uint16_t *__restrict__ G, int K, int R8, int R, double sigma, double ws, int sB)
-{
-    const int n = 128 * K;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int row = i / K, l = i % K;
-        const int y = row >> 1, part = row & 1;
-        const int d = l - y - R8;
-        double v = 0.0;
-        if (d >= -R && d <= R) {
-            const double g = exp(-(double)d * d / (2.0 * sigma * sigma)) / (2.5066282746310002 * sigma);
-            v = ldexp(part ? -g * sin(ws * d) : g * cos(ws * d), sB);
-        }
-        G[sw128_offset(128, row, l) / 2] = __half_as_ushort(__float2half_rn((float)v));
-    }
 }
 
 // --------------------------------------------------------------------------- column pass
@@ -1606,12 +1626,16 @@ int gabor_tc_mt_tile_y(int Kmax, int PWmax)
     return gabor_tc_smem_rows_mt(Kmax, PWmax, 64) <= (size_t)kSmemLimit ? 64 : 32;
 }
 
-cudaError_t build_gabor_tc_gm(uint16_t *Gm, int R, double sigma, double ws, cudaStream_t st)
+int gabor_tc_mt_am_elems(int R) { return (int)(tstrip_bytes(gabor_tc_mt_k(R), 128) / 2); }
+int gabor_tc_mt_gm_elems(int R, int col_ty) { return (int)(tstrip_bytes(gabor_tc_geometry(R).Kcol, 2 * col_ty) / 2); }
+
+cudaError_t build_gabor_tc_gm(uint16_t *Gm, int R, double sigma, double ws, int col_ty, cudaStream_t st)
 {
     int e = 0;
     frexp(1.0 / (2.5066282746310002 * sigma), &e);
     const TcGeometry g = gabor_tc_geometry(R);
-    k_build_mtoeplitz_col<<<(128 * g.Kcol + 255) / 256, 256, 0, st>>>(Gm, g.Kcol, g.R8, R, sigma, ws, -e);
+    const int nc = tstrip_cores(g.Kcol, 2 * col_ty);
+    k_build_tstrip<<<(64 * nc + 255) / 256, 256, 0, st>>>(Gm, nc, col_ty - 1 + g.R8, R, sigma, ws, -e);
     return cudaGetLastError();
 }
 
@@ -1631,8 +1655,8 @@ cudaError_t build_gabor_tc_am(uint16_t *Am, int R, double sigma, double wc, cuda
     // the scale of the frequency's Toeplitz operands: |S(d) cos|, |S(d) sin| <= S(0)
     int e = 0;
     frexp(1.0 / (2.5066282746310002 * sigma), &e);
-    const int K = gabor_tc_mt_k(R);
-    k_build_mtoeplitz<<<(128 * K + 255) / 256, 256, 0, st>>>(Am, K, R, sigma, wc, -e);
+    const int nc = tstrip_cores(gabor_tc_mt_k(R), 128);
+    k_build_tstrip<<<(64 * nc + 255) / 256, 256, 0, st>>>(Am, nc, kMtTileX - 1 + R, R, sigma, wc, -e);
     return cudaGetLastError();
 }
 

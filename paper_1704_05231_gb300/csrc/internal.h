@@ -130,8 +130,8 @@ struct TcUnitDev {
     const float2 *phx, *phy;
     int s, plane_a, plane_b, pad_;
     int64_t sig_idx;       // first signal of the unit; its block starts at sig_idx * W * Hp
-    const uint16_t *Am;    // modulated-tap row operand [128][Kmt] (FP16, K-major SW128)
-    const uint16_t *Gm;    // modulated-tap column operand [128][Kcol] (FP16, K-major SW128)
+    const uint16_t *Am;    // modulated-tap row operand: strip of 128 rows x Kmt (FP16 core matrices)
+    const uint16_t *Gm;    // modulated-tap column operand: strip of 2 col_mt_ty rows x Kcol
 };
 // One image of a tensor-core batch (gabor_bank_filter_batch): its input, output, intermediate
 // ([signal][Hp / 8][W][8], image row y at Lpad + y) and F[1] tables.
@@ -288,7 +288,10 @@ int gabor_tc_mt_pw(int R);
 int gabor_tc_mt_tile_y(int Kmax, int PWmax);
 size_t gabor_tc_smem_rows_mt(int Kmax, int PWmax, int TY);
 cudaError_t build_gabor_tc_am(uint16_t *Am, int R, double sigma, double wc, cudaStream_t st);
-cudaError_t build_gabor_tc_gm(uint16_t *Gm, int R, double sigma, double ws, cudaStream_t st);
+cudaError_t build_gabor_tc_gm(uint16_t *Gm, int R, double sigma, double ws, int col_ty, cudaStream_t st);
+// FP16 elements of one unit's modulated-tap operand strips (row pass; column pass of col_ty rows).
+int gabor_tc_mt_am_elems(int R);
+int gabor_tc_mt_gm_elems(int R, int col_ty);
 bool gabor_tc_mt_fits(int row_kmax, int row_pwmax, int col_kmax);
 int gabor_tc_mt_col_ty(int col_kmax);
 cudaError_t build_gabor_tc_b(uint16_t *Brow, uint16_t *Bcol, int R, double sigma, int bf16, float *unscale,
