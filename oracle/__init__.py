@@ -72,6 +72,8 @@ def _load():
             lib.oracle_iir_gabor.restype = ctypes.c_int
             lib.oracle_iir_gabor.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_int, _dp, ctypes.c_int]
+            lib.oracle_iir_coeffs.restype = None
+            lib.oracle_iir_coeffs.argtypes = [ctypes.c_double, _dp]
             lib.oracle_iir_pad.restype = ctypes.c_int
             lib.oracle_iir_pad.argtypes = [ctypes.c_double]
             lib.oracle_gabor_direct_b.restype = ctypes.c_int
@@ -230,6 +232,13 @@ def iir_smooth(x, sigma, boundary="zero"):
     return out
 
 
+def iir_coeffs(sigma):
+    """(B, b1/b0, b2/b0, b3/b0) of the recursion w[n] = B x[n] + sum_i (b_i / b0) w[n - i]."""
+    out = np.empty(4, dtype=np.float64)
+    _load().oracle_iir_coeffs(float(sigma), _ptr(out))
+    return tuple(float(v) for v in out)
+
+
 def iir_pad(sigma):
     """Samples the recursive passes extend each signal by on both sides."""
     return _load().oracle_iir_pad(float(sigma))
@@ -268,4 +277,5 @@ def ser_db(fast, exact):
 
 
 __all__ = ["build", "gauss", "radius", "gabor_filter", "gabor_bank", "gabor_rows",
-           "gabor_cols", "sdft", "iir_smooth", "iir_pad", "iir_gabor_filter", "iir_gabor_bank", "ser_db"]
+           "gabor_cols", "sdft", "iir_smooth", "iir_coeffs", "iir_pad", "iir_gabor_filter", "iir_gabor_bank",
+           "ser_db"]

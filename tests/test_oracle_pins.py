@@ -400,3 +400,52 @@ def test_iir_gabor_symmetries_and_approach_to_fir():
     sers = [oracle.ser_db(oracle.iir_gabor_filter(img, math.pi / (2 * s), 0.5, s),
                           oracle.gabor_filter(img, math.pi / (2 * s), 0.5, s))[1] for s in (2.0, 4.0, 8.0)]
     assert sers[0] > 12 and sers[0] < sers[1] < sers[2]
+
+
+# Young and van Vliet (1995) give their third-order recursive Gaussian in two forms: the decimal
+# polynomials in q of b0 .. b3 that the oracle evaluates, and the poles m0, m1 +- i m2 of the
+# continuous filter it was derived from, b0 ~ (m0 + q)(m1^2 + m2^2 + 2 m1 q + q^2),
+# b1 ~ q (2 m0 m1 + m1^2 + m2^2 + (2 m0 + 4 m1) q + 3 q^2), b2 ~ -q^2 (m0 + 2 m1 + 3 q),
+# b3 ~ q^3 (one common factor).  The recursion's ratios b_i / b0 must agree in both forms to the
+# precision of the printed decimals (about 5e-6): a slipped or dropped digit in any of the
+# oracle's eight polynomial constants moves them by 1e-4 or more.
+_YVV_POLES = (1.16680, 1.10783, 1.40586)
+
+
+def _yvv_pole_ratios(q):
+    m0, m1, m2 = _YVV_POLES
+    b0 = (m0 + q) * (m1 ** 2 + m2 ** 2 + 2 * m1 * q + q * q)
+    b1 = q * (2 * m0 * m1 + m1 ** 2 + m2 ** 2 + (2 * m0 + 4 * m1) * q + 3 * q * q)
+    b2 = -q * q * (m0 + 2 * m1 + 3 * q)
+    return b1 / b0, b2 / b0, q ** 3 / b0
+
+
+@pytest.mark.parametrize("sigma", [0.5, 0.7, 1.0, 2.0, 2.49, 2.5, 4.0, 16.0, 64.0, 150.0])
+def test_iir_coefficients_match_the_pole_form(sigma):
+    from scipy.optimize import brentq
+    B, c1, c2, c3 = oracle.iir_coeffs(sigma)
+    # the q at which the pole form has the oracle's b3 / b0 (monotonic in q)
+    q = brentq(lambda t: _yvv_pole_ratios(t)[2] - c3, 1e-6, 1e4, xtol=1e-15)
+    p1, p2, p3 = _yvv_pole_ratios(q)
+    assert abs(c1 / p1 - 1) <= 2e-5 and abs(c2 / p2 - 1) <= 2e-5
+    assert abs(B - (1 - p1 - p2 - p3)) <= 2e-5 * (abs(p1) + abs(p2) + p3)
+
+
+@pytest.mark.parametrize("sigma", [1.0, 1.5, 2.0, 3.0, 5.0, 10.0, 20.0, 40.0])
+def test_iir_smoother_width_fits_sigma(sigma):
+    # q(sigma) (two fitted branches) is chosen so that the forward / backward pair approximates
+    # the Gaussian of width sigma: the sampled Gaussian closest to the recursion's impulse
+    # response (least squares) has a width within 4% of sigma (measured: -1% .. +3.5%), so a
+    # slip in the branch constants that changes the width by more than that fails here.
+    from scipy.optimize import minimize_scalar
+    n = int(30 * sigma) + 200
+    x = np.zeros(2 * n + 1)
+    x[n] = 1.0
+    h = oracle.iir_smooth(x, sigma)
+    d = np.arange(-n, n + 1)
+
+    def misfit(s):
+        return float(np.sum((h - np.exp(-d * d / (2 * s * s)) / (math.sqrt(2 * math.pi) * s)) ** 2))
+
+    best = minimize_scalar(misfit, bounds=(0.3 * sigma, 2 * sigma), method="bounded", options={"xatol": 1e-8}).x
+    assert abs(best / sigma - 1) <= 0.04
