@@ -321,13 +321,14 @@ def c1_leg(torch, steps, warmup, stream):
 
 
 def bank_tc_leg(torch, d_img, thetas, omegas, sigmas, ref_out, n_out, steps, warmup, flush, stream):
-    """The same bank on tensor cores (FP16 / BF16 operands, FP32 accumulation): outputs/s,
-    rel. error against the FP32 path on this image, HBM roofline of the whole step."""
+    """The same bank on tensor cores (FP16 operands, and BF16 operands as hi + lo pairs; FP32
+    accumulation): outputs/s, rel. error against the FP32 path on this image, HBM roofline of
+    the whole step."""
     from paper_1704_05231_gb300 import GaborBank
     peak, kind = hbm_peak_gbs()
     res = {}
     ref = ref_out.clone()
-    for prec in ("fp16_tc",):
+    for prec in ("fp16_tc", "bf16_tc"):
         try:
             gbk = GaborBank(thetas, omegas, sigmas, precision=prec, max_shape=(H, W))
             out = torch.empty_like(ref)
@@ -484,7 +485,7 @@ def batch_leg(torch, steps, warmup, flush, stream):
            "outputs_per_step": n_out, "pixels": sum(h * w for h, w in shapes)}
     peak_hbm, kind = hbm_peak_gbs()
     peak_alu, _ = fp32_peak_tflops(torch)
-    for prec in ("fp32", "fp16_tc"):
+    for prec in ("fp32", "fp16_tc", "bf16_tc"):
         gbk = GaborBank(th, om, sg, precision=prec, max_shape=(2048, 2048))
         outs = [torch.empty(gbk.out_shape(h, w), dtype=torch.complex64, device="cuda") for h, w in shapes]
         ent = {}

@@ -48,7 +48,9 @@ typedef enum {
 typedef enum {
     GB_FP32 = 0,    /* FP32 CUDA-core path: |err| <= 1e-5 * max|out| against FP64 */
     GB_FP16_TC = 1, /* tcgen05 tensor cores, FP16 operands, FP32 accumulation */
-    GB_BF16_TC = 2  /* tcgen05 tensor cores, BF16 operands, FP32 accumulation */
+    GB_BF16_TC = 2  /* tcgen05 tensor cores, BF16 operands, FP32 accumulation; the filter bank
+                       splits every operand into BF16 hi + lo parts (three products per step,
+                       lo x lo dropped), which makes it more accurate than GB_FP16_TC */
 } gb_precision;
 
 /*
@@ -91,8 +93,9 @@ gb_status gabor_bank_destroy(gabor_bank_t h);
  * GB_FP16_TC handle without a workspace (gabor_bank_set_workspace) grows its own
  * intermediate buffer when an image needs more than it holds.
  * Asynchronous.  Errors: GB_ERR_INVALID_ARG (NULL, H/W <= 0, pitch < W, misaligned),
- * GB_ERR_UNSUPPORTED (BF16 bank, or a radius above 96 px on tensor cores), GB_ERR_BUDGET
- * (attached workspace too small), GB_ERR_CUDA.  gabor_bank_create refuses radii above 160 px.
+ * GB_ERR_UNSUPPORTED (a radius above 96 px on tensor cores; a GB_BF16_TC bank under
+ * GB_OPT_ROW_PASS = 1), GB_ERR_BUDGET (attached workspace too small), GB_ERR_CUDA.
+ * gabor_bank_create refuses radii above 160 px.
  */
 gb_status gabor_bank_filter(gabor_bank_t h, const float *d_img, int H, int W, int64_t pitch,
                             void *d_out, void *stream);
@@ -145,7 +148,7 @@ gb_status gabor_bank_sdft(gabor_bank_t h, const float *d_img, int H, int W, int6
  * Asynchronous.  Results are bitwise identical to n separate gabor_bank_filter calls with the
  * same handle.  A call whose pointers and shapes equal the previous call's (and whose tables
  * already exist) enqueues only a memset and the kernel, so it can be captured in a CUDA graph.
- * FP32 handles: one launch.  GB_FP16_TC handles: four launches for the whole batch (image
+ * FP32 handles: one launch.  Tensor-core handles: four launches for the whole batch (image
  * min / max, the constant-image tables, the row pass and the column pass over every image's
  * tiles), with intermediates in a handle-owned batch workspace (about 4 bytes per pixel and
  * horizontal pass, plus halo rows), allocated on the first call with a new set of pointers and

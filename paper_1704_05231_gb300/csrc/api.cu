@@ -483,6 +483,8 @@ int64_t tc_sig_elems(const gabor_bank *h, int H, int W)
     const int64_t Hp = (int64_t)(H + 63) / 64 * 64 + 2 * tc_lpad(h);
     int64_t nsig = 0;
     for (const Unit &u : h->units) nsig += u.k_b >= 0 ? 4 : 2;
+    // modulated taps: Re J, Im J per unit, as hi and lo under BF16
+    nsig = std::max<int64_t>(nsig, (int64_t)(h->prec == GB_BF16_TC ? 4 : 2) * (int64_t)h->units.size());
     return nsig * W * Hp;
 }
 
@@ -497,6 +499,7 @@ gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
 {
     const int nf = (int)h->freqs.size(), nu = (int)h->units.size();
     const int bf16 = h->prec == GB_BF16_TC;
+    const int split = bf16;   // BF16: the modulated-tap operands as hi + lo pairs
     if (h->tc_ready) return GB_OK;
     size_t total = 0;
     std::vector<size_t> off_r(nf), off_c(nf);
@@ -543,25 +546,25 @@ gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
     for (int i = 0; i < nu; ++i) {
         const int R = h->freqs[h->units[i].s].R;
         off_am[i] = am_total;
-        am_total += ((size_t)gabor_tc_mt_am_elems(R) + 127) / 128 * 128;   // 256-byte aligned strips
+        am_total += ((size_t)gabor_tc_mt_am_elems(R, split) + 127) / 128 * 128;   // 256-byte aligned strips
         h->tc_mt_kmax = std::max(h->tc_mt_kmax, gabor_tc_mt_k(R));
         h->tc_mt_pwmax = std::max(h->tc_mt_pwmax, gabor_tc_mt_pw(R));
     }
-    h->tc_mt_ty = gabor_tc_mt_tile_y(h->tc_mt_kmax, h->tc_mt_pwmax);
-    h->tc_mt_ok = gabor_tc_mt_fits(h->tc_mt_kmax, h->tc_mt_pwmax, h->tc_col_kmax);
+    h->tc_mt_ty = gabor_tc_mt_tile_y(h->tc_mt_kmax, h->tc_mt_pwmax, split);
+    h->tc_mt_ok = gabor_tc_mt_fits(h->tc_mt_kmax, h->tc_mt_pwmax, h->tc_col_kmax, split);
     GB_TRY(dalloc(&h->d_tcAm, std::max<size_t>(am_total, 1)));
     std::vector<size_t> off_gm(nu);
     size_t gm_total = 0;
-    const int col_ty = gabor_tc_mt_col_ty(h->tc_col_kmax);
+    const int col_ty = gabor_tc_mt_col_ty(h->tc_col_kmax, split);
     for (int i = 0; i < nu; ++i) {
         off_gm[i] = gm_total;
-        gm_total += ((size_t)gabor_tc_mt_gm_elems(h->freqs[h->units[i].s].R, col_ty) + 127) / 128 * 128;
+        gm_total += ((size_t)gabor_tc_mt_gm_elems(h->freqs[h->units[i].s].R, col_ty, split) + 127) / 128 * 128;
     }
     GB_TRY(dalloc(&h->d_tcGm, std::max<size_t>(gm_total, 1)));
     for (int i = 0; i < nu; ++i) {
         const Freq &fq = h->freqs[h->units[i].s];
-        GB_CU(build_gabor_tc_am(h->d_tcAm + off_am[i], fq.R, fq.sigma, h->units[i].wc, st));
-        GB_CU(build_gabor_tc_gm(h->d_tcGm + off_gm[i], fq.R, fq.sigma, h->units[i].ws, col_ty, st));
+        GB_CU(build_gabor_tc_am(h->d_tcAm + off_am[i], fq.R, fq.sigma, h->units[i].wc, split, st));
+        GB_CU(build_gabor_tc_gm(h->d_tcGm + off_gm[i], fq.R, fq.sigma, h->units[i].ws, col_ty, split, st));
     }
     std::vector<TcUnitDev> ud(nu);
     const int K = (int)h->theta.size();
@@ -628,14 +631,11 @@ gb_status encode_tc_maps(TcBankArgs &a, int nsig, bool mt)
 gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int64_t pitch, void *d_out,
                            cudaStream_t st)
 {
-    if (h->prec == GB_BF16_TC)
-        return fail(GB_ERR_UNSUPPORTED,
-                    "the filter bank on tensor cores runs with FP16 operands (GB_FP16_TC); BF16 operands "
-                    "exceed 2e-3 * max|out| on the bank");
     for (const Freq &f : h->freqs)
         if (!gabor_tc_supported(f.R))
             return fail(GB_ERR_UNSUPPORTED, "tensor-core bank supports radii up to 96 px");
     const int nf = (int)h->freqs.size();
+    const int split = h->prec == GB_BF16_TC;
     const int64_t ny64 = (H + 63) / 64, nx32 = (W + 31) / 32, nx64 = (W + 63) / 64;
     // the unit descriptors point into the phase tables: (re)build them with the tables
     const bool tables_move = !(h->tables_ready && W <= h->Wcap && H <= h->Hcap);
@@ -645,6 +645,10 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     // both passes with modulated taps (64-column row tiles, J as the intermediate) unless
     // GB_OPT_ROW_PASS asks for the steps or a radius does not fit the kernels
     const bool row_mt = h->fp32_row_form != 1 && h->tc_mt_ok;
+    if (split && !row_mt)
+        return fail(GB_ERR_UNSUPPORTED,
+                    "the BF16 bank (hi + lo operand pairs) runs with the modulated-tap kernels only: not under "
+                    "GB_OPT_ROW_PASS = 1, nor when a radius does not fit them");
     const int ty = row_mt ? h->tc_mt_ty : h->tc_row_ty;
     const int tile_x = row_mt ? gabor_tc_mt_tile_x() : gabor_tc_row_tile_x();
     // Non-zero boundary rules: the row pass also produces the halo rows [-R, 0) and
@@ -653,7 +657,7 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     for (const Freq &f : h->freqs) rmax = std::max(rmax, f.R);
     const int ypad = h->boundary == kBoundaryZero ? 0 : (rmax + ty - 1) / ty * ty;
     const int64_t row_cnt = (int64_t)((H + 2 * ypad + ty - 1) / ty) * ((W + tile_x - 1) / tile_x);
-    const int col_ty = gabor_tc_mt_col_ty(h->tc_col_kmax);   // modulated-tap column rows per job
+    const int col_ty = gabor_tc_mt_col_ty(h->tc_col_kmax, split);   // modulated-tap column rows per job
     const int64_t ny_mt = (H + col_ty - 1) / col_ty;
     const int64_t col_cnt = row_mt ? ny_mt * h->tc_nu_f * nx64
                                    : ny64 * (h->tc_np_f * nx32 + (h->tc_nu_f - h->tc_np_f) * nx64);
@@ -686,11 +690,13 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
         // Layout [signal][Hp / 8][W][8].  The row pass writes rows [Lpad, Lpad + round_up(H, TY))
         // of every signal (zeros below row H); the column pass reads up to R8 rows beyond, so
         // the blocks of rows [0, Lpad) and [Lpad + round_up(H, 8), Hp) must be zero.
+        // every signal either form uses (the modulated-tap form: 2 per unit, 4 as BF16 hi + lo)
         const size_t sig_bytes = (size_t)Hp * W * 2, blk = (size_t)W * 16;
         const int64_t back = (Lpad + ((int64_t)H + 7) / 8 * 8) / 8;
-        GB_CU(cudaMemset2DAsync(sig, sig_bytes, 0, (size_t)(Lpad / 8) * blk, (size_t)h->tc_nsig, st));
+        const size_t nsig_z = (size_t)std::max(h->tc_nsig, (split ? 4 : 2) * (int)h->units.size());
+        GB_CU(cudaMemset2DAsync(sig, sig_bytes, 0, (size_t)(Lpad / 8) * blk, nsig_z, st));
         GB_CU(cudaMemset2DAsync(reinterpret_cast<char *>(sig) + back * blk, sig_bytes, 0,
-                                (size_t)(Hp / 8 - back) * blk, (size_t)h->tc_nsig, st));
+                                (size_t)(Hp / 8 - back) * blk, nsig_z, st));
     }
     h->tc_H = h->ws_ptr ? 0 : H;
     h->tc_W = h->ws_ptr ? 0 : W;
@@ -732,7 +738,8 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.layout = h->layout;
     a.nplanes = (int)(h->omega.size() * h->theta.size());
     a.row_y0 = -ypad;
-    GB_TRY(encode_tc_maps(a, h->tc_nsig, row_mt));
+    a.split = split;
+    GB_TRY(encode_tc_maps(a, split ? 4 * (int)h->units.size() : h->tc_nsig, row_mt));
     GB_CU(launch_gabor_tc(a, h->sm_count, st));
     return GB_OK;
 }
@@ -744,10 +751,7 @@ gb_status filter_batch_tc(gabor_bank *h, int n, const float *const *d_imgs, cons
                           const int64_t *pitch, void *const *d_outs, cudaStream_t st, bool *done)
 {
     *done = false;
-    if (h->prec == GB_BF16_TC)
-        return fail(GB_ERR_UNSUPPORTED,
-                    "the filter bank on tensor cores runs with FP16 operands (GB_FP16_TC); BF16 operands "
-                    "exceed 2e-3 * max|out| on the bank");
+    const int split = h->prec == GB_BF16_TC;
     for (const Freq &f : h->freqs)
         if (!gabor_tc_supported(f.R)) return fail(GB_ERR_UNSUPPORTED, "tensor-core bank supports radii up to 96 px");
     int Hm = 0, Wm = 0;
@@ -762,12 +766,12 @@ gb_status filter_batch_tc(gabor_bank *h, int n, const float *const *d_imgs, cons
     if (h->fp32_row_form == 1 || !h->tc_mt_ok) return GB_OK;
     const int nf = (int)h->freqs.size(), nu = (int)h->units.size();
     const int ty = h->tc_mt_ty, tile_x = gabor_tc_mt_tile_x();
-    const int col_ty = gabor_tc_mt_col_ty(h->tc_col_kmax);
+    const int col_ty = gabor_tc_mt_col_ty(h->tc_col_kmax, split);
     int rmax = 0;
     for (const Freq &f : h->freqs) rmax = std::max(rmax, f.R);
     const int ypad = h->boundary == kBoundaryZero ? 0 : (rmax + ty - 1) / ty * ty;
     const int Lpad = tc_lpad(h);
-    const int nsig = 2 * nu;   // Re J, Im J of every unit
+    const int nsig = (split ? 4 : 2) * nu;   // Re J, Im J of every unit (hi and lo under BF16)
     // workspace: intermediates, F[1] tables, partial keys, centres (each 256-byte aligned)
     auto al = [](int64_t b) { return (b + 255) / 256 * 256; };
     std::vector<int64_t> off_sig(n), off_ones(n), Hp(n);
@@ -919,6 +923,7 @@ gb_status filter_batch_tc(gabor_bank *h, int n, const float *const *d_imgs, cons
     a.n_row = h->tcb_nrow;
     a.n_col = h->tcb_ncol;
     a.nimg = n;
+    a.split = split;
     GB_CU(launch_gabor_tc_batch(a, h->sm_count, st));
     *done = true;
     return GB_OK;

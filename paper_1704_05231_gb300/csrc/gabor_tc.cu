@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "internal.h"
@@ -48,6 +49,16 @@ __device__ __forceinline__ uint32_t h2pack(float lo, float hi)
 {
     const __half2 h = __floats2half2_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// BF16 hi + lo split of (a, b): hi words bf16(a), bf16(b) and lo words bf16(a - hi), bf16(b - hi).
+__device__ __forceinline__ void b2split(float a, float b, uint32_t &hi, uint32_t &lo)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
 __device__ __forceinline__ void fail_status(int *status, volatile int *flag, int code)
@@ -580,12 +591,14 @@ struct MtSmem {
     uint32_t a_off, p_off, patch_off, desc_off, bar_off, misc_off, total;
 };
 
-__host__ __device__ inline MtSmem mt_smem(int K, int PW, int TY)
+// split = 1 (BF16 operands as hi + lo pairs): two strips per A buffer and P as hi and lo.
+__host__ __device__ inline MtSmem mt_smem(int K, int PW, int TY, int split = 0)
 {
     MtSmem L;
-    L.a_off = 0;                                              // [2] strips of 128 rows x K
-    L.p_off = (L.a_off + 2u * tstrip_bytes(K, 128) + 1023) & ~1023u;   // TY x K FP16 (SW128)
-    L.patch_off = L.p_off + (uint32_t)TY * K * 2;             // TY x PWs FP32
+    const uint32_t np = split ? 2u : 1u;
+    L.a_off = 0;                                              // [2] buffers of np strips of 128 rows x K
+    L.p_off = (L.a_off + 2u * np * tstrip_bytes(K, 128) + 1023) & ~1023u;   // np x TY x K (SW128)
+    L.patch_off = L.p_off + np * (uint32_t)TY * K * 2;        // TY x PWs FP32
     L.desc_off = (L.patch_off + (uint32_t)TY * (round_up(PW, 8) + 4) * 4 + 127) & ~127u;
     L.bar_off = L.desc_off + kDescBytes;
     L.misc_off = L.bar_off + 16 * 8;
@@ -603,6 +616,8 @@ __device__ __forceinline__ RowItem row_item_mt(const TcBankArgs &a, const TcDesc
     return RowItem{d.forder[g], a.row_y0 + (local / a.row_nx) * a.row_ty, (local % a.row_nx) * kMtTileX, 0};
 }
 
+// SPLIT: BF16 operands as hi + lo pairs (a.split); FP16 operands otherwise.
+template <bool SPLIT>
 __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_constant__ TcBankArgs a)
 {
     const int nitems = a.row_list ? a.n_row : a.nf * a.row_cnt;
@@ -610,7 +625,7 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
     unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int TY = a.row_ty;
-    const MtSmem L = mt_smem(a.row_kmax, a.row_pwmax, TY);
+    const MtSmem L = mt_smem(a.row_kmax, a.row_pwmax, TY, SPLIT ? 1 : 0);
     unsigned char *sA = sm + L.a_off;
     unsigned char *sP = sm + L.p_off;
     float *patch = reinterpret_cast<float *>(sm + L.patch_off);
@@ -625,7 +640,9 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
     uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
     const TcDesc D = load_desc(a, sm + L.desc_off);
-    const uint32_t abuf = tstrip_bytes(a.row_kmax, 128);
+    constexpr uint32_t np = SPLIT ? 2u : 1u;
+    const uint32_t abuf = np * tstrip_bytes(a.row_kmax, 128);   // an A buffer (hi, lo strips)
+    const uint32_t plo = (uint32_t)TY * a.row_kmax * 2;         // P lo after P hi (split)
 
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
@@ -652,7 +669,7 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
     pdl_launch_dependents();
     pdl_wait();
     const uint32_t tmem = *tmem_s;
-    const uint32_t idesc = idesc_f16(0, 128, TY);
+    const uint32_t idesc = idesc_f16(SPLIT ? 1 : 0, 128, TY);
 
     if (warp == 15) {
         // -------------------------------------------------------------- MMA warp (lane 0)
@@ -670,7 +687,7 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
                 if (jq >= 2 && !mbar_wait(&a_empty[buf], ((jq - 2) >> 1) & 1, abort_s)) return false;
                 const RowItem w = row_item_mt(a, D, blockIdx.x + (jq / nu) * gridDim.x);
                 const TcFreqDev f = D.freqs[w.s];
-                const uint32_t abytes = tstrip_bytes(f.Kmt, 128);
+                const uint32_t abytes = np * tstrip_bytes(f.Kmt, 128);
                 mbar_arrive_expect_tx(&a_full[buf], abytes);
                 bulk_load(smem_u32(sA + buf * abuf), D.units[f.u0 + jq % nu].Am, abytes, &a_full[buf]);
                 ++issued;
@@ -689,11 +706,18 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(sA + b * abuf), p0 = smem_u32(sP);
+                    const uint32_t a0l = a0 + tstrip_bytes(K, 128);
                     for (int kb = 0; kb < K / 64; ++kb)
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            tc_mma_f16(tmem + (uint32_t)TY * b, tstrip_desc(a0, 4 * kb + kk),
-                                       smem_desc_sw128(p0 + kb * TY * 128) + 2 * kk, idesc, (kb | kk) != 0);
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t pd = smem_desc_sw128(p0 + kb * TY * 128) + 2 * kk;
+                            tc_mma_f16(tmem + (uint32_t)TY * b, tstrip_desc(a0, 4 * kb + kk), pd, idesc, (kb | kk) != 0);
+                            if constexpr (SPLIT) {   // Am_hi P_lo + Am_lo P_hi (the lo x lo product is dropped)
+                                tc_mma_f16(tmem + (uint32_t)TY * b, tstrip_desc(a0, 4 * kb + kk),
+                                           smem_desc_sw128(p0 + plo + kb * TY * 128) + 2 * kk, idesc, 1);
+                                tc_mma_f16(tmem + (uint32_t)TY * b, tstrip_desc(a0l, 4 * kb + kk), pd, idesc, 1);
+                            }
+                        }
                     tc_commit(&tmem_full[b]);
                     tc_commit(&a_empty[b]);
                     // the next copies (this item's later units, or the next item's first ones)
@@ -793,8 +817,16 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
                     const bool in = yok && kk < ncols && (a.bmode != kBoundaryZero || (gx >= 0 && gx < im.W));
                     v[t] = in ? (patch[r * PWs + kk] - cen) * sc : 0.f;
                 }
-                *reinterpret_cast<uint4 *>(sP + sw128_offset(TY, r, k0)) =
-                    make_uint4(h2pack(v[0], v[1]), h2pack(v[2], v[3]), h2pack(v[4], v[5]), h2pack(v[6], v[7]));
+                if constexpr (SPLIT) {   // BF16 hi + lo
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) b2split(v[2 * t], v[2 * t + 1], hw[t], lw[t]);
+                    *reinterpret_cast<uint4 *>(sP + sw128_offset(TY, r, k0)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4 *>(sP + plo + sw128_offset(TY, r, k0)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                } else {
+                    *reinterpret_cast<uint4 *>(sP + sw128_offset(TY, r, k0)) =
+                        make_uint4(h2pack(v[0], v[1]), h2pack(v[2], v[3]), h2pack(v[4], v[5]), h2pack(v[6], v[7]));
+                }
             }
             fence_proxy_async_smem();
             named_barrier(1, NP);   // P built; the FP32 patch is free: stage the next item's
@@ -835,20 +867,32 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
                 tc_fence_after();
                 const int64_t sstride = (int64_t)im.W * im.Hp;   // between signals
                 const int64_t bstride = (int64_t)im.W * 8;       // between 8-row blocks
-                uint16_t *dst0 = im.sig + (int64_t)(2 * (u0 + q) + part) * sstride +
-                                 (int64_t)((a.Lpad + y0) >> 3) * bstride + (int64_t)(xin ? gx : 0) * 8;
+                // signals of the unit: (Re J, Im J), or under split (Re hi, Im hi, Re lo, Im lo)
+                const int64_t sig0 = (int64_t)(2 * np) * (u0 + q) + part;
+                uint16_t *dst0 = im.sig + sig0 * sstride + (int64_t)((a.Lpad + y0) >> 3) * bstride +
+                                 (int64_t)(xin ? gx : 0) * 8;
 #pragma unroll 1
                 for (int c0 = rbase; c0 < rbase + rpw; c0 += 16) {
                     float v[16];
                     tmem_ld16(tmem + lane_base + (uint32_t)TY * b + c0, v);
-                    uint32_t pk[2][4];   // [8-row block][row pair]
+                    uint32_t pk[2][4], pl[2][4];   // [8-row block][row pair]
+                    if constexpr (SPLIT) {
 #pragma unroll
-                    for (int j = 0; j < 16; j += 2) pk[j >> 3][(j & 7) >> 1] = h2pack(v[j] * unscale, v[j + 1] * unscale);
+                        for (int j = 0; j < 16; j += 2)
+                            b2split(v[j] * unscale, v[j + 1] * unscale, pk[j >> 3][(j & 7) >> 1], pl[j >> 3][(j & 7) >> 1]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; j += 2) pk[j >> 3][(j & 7) >> 1] = h2pack(v[j] * unscale, v[j + 1] * unscale);
+                    }
                     if (xin) {
 #pragma unroll
-                        for (int blk = 0; blk < 2; ++blk)
-                            *reinterpret_cast<uint4 *>(dst0 + (int64_t)((c0 + 8 * blk) >> 3) * bstride) =
-                                make_uint4(pk[blk][0], pk[blk][1], pk[blk][2], pk[blk][3]);
+                        for (int blk = 0; blk < 2; ++blk) {
+                            const int64_t o = (int64_t)((c0 + 8 * blk) >> 3) * bstride;
+                            *reinterpret_cast<uint4 *>(dst0 + o) = make_uint4(pk[blk][0], pk[blk][1], pk[blk][2], pk[blk][3]);
+                            if constexpr (SPLIT)
+                                *reinterpret_cast<uint4 *>(dst0 + 2 * sstride + o) =
+                                    make_uint4(pl[blk][0], pl[blk][1], pl[blk][2], pl[blk][3]);
+                        }
                     }
                 }
                 tc_fence_before();
@@ -872,7 +916,9 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_consta
 // |d| <= R; FP64, rounded to FP16.  Row pass (Am): off = 63 + R, w = w^c (rows x of the 64-
 // column tile backwards, k the input column from x0 - R on).  Column pass (Gm): off =
 // TYC - 1 + R8, w = w^s (rows y of the job backwards, l the window row from y0 - R8 on).
-__global__ void k_build_tstrip(uint16_t *__restrict__ Q, int ncores, int off, int R, double sigma, double w, int sB)
+// split = 1: BF16 instead, hi = bf16(v) in Q[0 .. n) and lo = bf16(v - hi) in Q[n .. 2 n).
+__global__ void k_build_tstrip(uint16_t *__restrict__ Q, int ncores, int off, int R, double sigma, double w, int sB,
+                               int split)
 {
     const int n = 64 * ncores;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -883,7 +929,13 @@ __global__ void k_build_tstrip(uint16_t *__restrict__ Q, int ncores, int off, in
             const double g = exp(-(double)d * d / (2.0 * sigma * sigma)) / (2.5066282746310002 * sigma);
             v = ldexp((r & 1) ? -g * sin(w * d) : g * cos(w * d), sB);
         }
-        Q[i] = __half_as_ushort(__float2half_rn((float)v));
+        if (split) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn((float)v);
+            Q[i] = __bfloat16_as_ushort(hi);
+            Q[n + i] = __bfloat16_as_ushort(__float2bfloat16_rn((float)(v - (double)__bfloat162float(hi))));
+        } else {
+            Q[i] = __half_as_ushort(__float2half_rn((float)v));
+        }
     }
 }
 
@@ -910,13 +962,14 @@ struct MtColSmem {
 };
 
 // TYC: output rows per job (64; 32 when the operands of 64 do not fit); the B operand is the
-// unit's strip of 2 TYC rows x K.
-__host__ __device__ inline MtColSmem mt_col_smem(int K, int TYC)
+// unit's strip of 2 TYC rows x K.  nst operand stages; split = 1: hi and lo of both operands.
+__host__ __device__ inline MtColSmem mt_col_smem(int K, int TYC, int split = 0, int nst = 2)
 {
     MtColSmem L;
-    L.a_off = 0;                                   // [2] x 128 x K (no swizzle, core matrices)
-    L.b_off = L.a_off + 2u * 128 * K * 2;          // [2] strips of 2 TYC rows x K
-    L.desc_off = (L.b_off + 2u * tstrip_bytes(K, 2 * TYC) + 127) & ~127u;
+    const uint32_t np = split ? 2u : 1u;
+    L.a_off = 0;                                        // [nst][np] x 128 x K (no swizzle, core matrices)
+    L.b_off = L.a_off + nst * np * 128u * K * 2;        // [nst][np] strips of 2 TYC rows x K
+    L.desc_off = (L.b_off + nst * np * tstrip_bytes(K, 2 * TYC) + 127) & ~127u;
     L.bar_off = L.desc_off + kDescBytes;
     L.misc_off = L.bar_off + 16 * 8;
     L.total = L.misc_off + 64;
@@ -940,6 +993,8 @@ __device__ __forceinline__ MtColItem col_item_mt(const TcBankArgs &a, const TcDe
     return MtColItem{f.u0 + q, (rest % a.col_nx64) * 64, (rest / a.col_nx64) * a.col_mt_ty, 0};
 }
 
+// SPLIT: BF16 operands as hi + lo pairs (a.split, a.col_mt_nst stages); FP16 operands in two stages otherwise.
+template <bool SPLIT>
 __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __grid_constant__ TcBankArgs a)
 {
     const int nitems = a.col_list ? a.n_col : a.nf * a.col_cnt;
@@ -947,7 +1002,9 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int TYC = a.col_mt_ty;
-    const MtColSmem L = mt_col_smem(a.col_kmax, TYC);
+    const int NST = SPLIT ? a.col_mt_nst : 2;
+    constexpr int np = SPLIT ? 2 : 1;
+    const MtColSmem L = mt_col_smem(a.col_kmax, TYC, SPLIT ? 1 : 0, NST);
     unsigned char *sA = sm + L.a_off;
     unsigned char *sB = sm + L.b_off;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.bar_off);
@@ -958,8 +1015,9 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     uint64_t *drain = bars + 8;
     uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
-    const uint32_t obuf = 128u * a.col_kmax * 2;            // an A buffer
-    const uint32_t gbuf = tstrip_bytes(a.col_kmax, 2 * TYC);   // a B buffer
+    const uint32_t ahalf = 128u * a.col_kmax * 2;                 // one A operand (hi, or lo under split)
+    const uint32_t obuf = np * ahalf;                             // the A operands of a stage
+    const uint32_t gbuf = np * tstrip_bytes(a.col_kmax, 2 * TYC); // the B strips of a stage
     const TcDesc D = load_desc(a, sm + L.desc_off);
 
     if (tid == 0) {
@@ -984,36 +1042,40 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     // tables and the centre are read after it completed
     pdl_wait();
     const uint32_t tmem = *tmem_s;
-    const uint32_t idesc = idesc_f16(0, 128, 2 * TYC);
+    const uint32_t idesc = idesc_f16(SPLIT ? 1 : 0, 128, 2 * TYC);
     const int njobs = nitems > (int)blockIdx.x ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
     if (warp == kMtColEpiWarps) {
         // -------------------------------------------------------------- producer (lane 0)
         if (lane == 0) {
             auto item = [&](int j) { return col_item_mt(a, D, blockIdx.x + j * gridDim.x); };
-            // job j's operands into buffers j & 1: J boxes (8 rows of a block x 2 parts x 64
+            // job j's operands into stage j % NST: J boxes (8 rows of a block x 2 parts x 64
             // columns x 8 blocks, landing as K-major core matrices with operand row
-            // n = 2 x + part) and the unit's Gm (one bulk copy)
+            // n = 2 x + part; under split the hi pair of signals, then the lo pair) and the
+            // unit's Gm strips (one bulk copy: hi, then lo under split)
             auto issue = [&](int j) {
                 const MtColItem w = item(j);
                 const TcUnitDev u = D.units[w.unit];
                 const TcFreqDev f = D.freqs[u.s];
-                const int st = j & 1, nkb = f.Kcol / 64;
+                const int st = j % NST, nkb = f.Kcol / 64;
                 const uint32_t bbytes = tstrip_bytes(f.Kcol, 2 * TYC);
-                mbar_arrive_expect_tx(&ab_full[st], nkb * 16384u + bbytes);
+                mbar_arrive_expect_tx(&ab_full[st], np * (nkb * 16384u + bbytes));
                 const int yb0 = (a.Lpad + w.y0 - f.R8) >> 3;
                 const uint32_t dst = smem_u32(sA + st * obuf);
-                for (int kb = 0; kb < nkb; ++kb)
-                    tma_load_4d(dst + kb * 16384u, tc_img(a, w.img).tm, 0, 2 * w.unit, w.x0, yb0 + 8 * kb, &ab_full[st]);
-                bulk_load(smem_u32(sB + st * gbuf), u.Gm, bbytes, &ab_full[st]);
+                const void *tm = tc_img(a, w.img).tm;
+                for (int h = 0; h < np; ++h)
+                    for (int kb = 0; kb < nkb; ++kb)
+                        tma_load_4d(dst + h * ahalf + kb * 16384u, tm, 0, 2 * np * w.unit + 2 * h, w.x0, yb0 + 8 * kb,
+                                    &ab_full[st]);
+                bulk_load(smem_u32(sB + st * gbuf), u.Gm, np * bbytes, &ab_full[st]);
             };
             int issued = 0, landed = 0;
-            for (; issued < 2 && issued < njobs; ++issued) issue(issued);
+            for (; issued < NST && issued < njobs; ++issued) issue(issued);
             for (int j = 0; j < njobs; ++j) {
                 if (*abort_s) break;
-                const int st = j & 1, acc = j & 1;
+                const int st = j % NST, acc = j & 1;
                 const TcFreqDev f = D.freqs[D.units[item(j).unit].s];
-                if (!mbar_wait(&ab_full[st], (j >> 1) & 1, abort_s)) {
+                if (!mbar_wait(&ab_full[st], (j / NST) & 1, abort_s)) {
                     fail_status(a.status, abort_s, 36);
                     break;
                 }
@@ -1024,21 +1086,30 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
                 }
                 tc_fence_after();
                 const uint32_t a0 = smem_u32(sA + st * obuf), b0 = smem_u32(sB + st * gbuf);
+                const uint32_t a0l = a0 + ahalf, b0l = b0 + tstrip_bytes(f.Kcol, 2 * TYC);
                 for (int kb = 0; kb < f.Kcol / 64; ++kb)
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        tc_mma_f16(tmem + 128u * acc, smem_desc_kmajor(a0 + kb * 16384 + kk * 4096, 2048, 128),
-                                   tstrip_desc(b0, 4 * kb + kk), idesc, (kb | kk) != 0);
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t ao = kb * 16384 + kk * 4096;
+                        tc_mma_f16(tmem + 128u * acc, smem_desc_kmajor(a0 + ao, 2048, 128), tstrip_desc(b0, 4 * kb + kk),
+                                   idesc, (kb | kk) != 0);
+                        if constexpr (SPLIT) {   // J_hi G_lo + J_lo G_hi (the lo x lo product is dropped)
+                            tc_mma_f16(tmem + 128u * acc, smem_desc_kmajor(a0 + ao, 2048, 128),
+                                       tstrip_desc(b0l, 4 * kb + kk), idesc, 1);
+                            tc_mma_f16(tmem + 128u * acc, smem_desc_kmajor(a0l + ao, 2048, 128),
+                                       tstrip_desc(b0, 4 * kb + kk), idesc, 1);
+                        }
+                    }
                 tc_commit(&tmem_full[acc]);
                 tc_commit(&ab_empty[st]);
-                // job j + 2 goes into these buffers once this MMA is done with them
-                if (j + 2 < njobs) {
-                    if (!mbar_wait(&ab_empty[st], (j >> 1) & 1, abort_s)) {
+                // job j + NST goes into these buffers once this MMA is done with them
+                if (j + NST < njobs) {
+                    if (!mbar_wait(&ab_empty[st], (j / NST) & 1, abort_s)) {
                         fail_status(a.status, abort_s, 38);
                         break;
                     }
-                    issue(j + 2);
-                    issued = j + 3;
+                    issue(j + NST);
+                    issued = j + NST + 1;
                 }
             }
             tc_commit(drain);
@@ -1050,7 +1121,7 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
             // released
             for (int jj = landed; jj < issued; ++jj) {
                 volatile int dummy = 0;
-                mbar_wait(&ab_full[jj & 1], (jj >> 1) & 1, &dummy);
+                mbar_wait(&ab_full[jj % NST], (jj / NST) & 1, &dummy);
             }
         }
     } else {
@@ -1620,43 +1691,55 @@ int gabor_tc_col_tile_y() { return kColTileY; }
 int gabor_tc_mt_tile_x() { return kMtTileX; }
 int gabor_tc_mt_k(int R) { return round_up(kMtTileX + 2 * R, 64); }
 int gabor_tc_mt_pw(int R) { return round_up(kMtTileX + 2 * R, 4); }
-size_t gabor_tc_smem_rows_mt(int Kmax, int PWmax, int TY) { return 1024 + mt_smem(Kmax, PWmax, TY).total; }
-int gabor_tc_mt_tile_y(int Kmax, int PWmax)
+size_t gabor_tc_smem_rows_mt(int Kmax, int PWmax, int TY, int split)
 {
-    return gabor_tc_smem_rows_mt(Kmax, PWmax, 64) <= (size_t)kSmemLimit ? 64 : 32;
+    return 1024 + mt_smem(Kmax, PWmax, TY, split).total;
+}
+int gabor_tc_mt_tile_y(int Kmax, int PWmax, int split)
+{
+    return gabor_tc_smem_rows_mt(Kmax, PWmax, 64, split) <= (size_t)kSmemLimit ? 64 : 32;
 }
 
-int gabor_tc_mt_am_elems(int R) { return (int)(tstrip_bytes(gabor_tc_mt_k(R), 128) / 2); }
-int gabor_tc_mt_gm_elems(int R, int col_ty) { return (int)(tstrip_bytes(gabor_tc_geometry(R).Kcol, 2 * col_ty) / 2); }
+int gabor_tc_mt_am_elems(int R, int split) { return (int)((split ? 2 : 1) * tstrip_bytes(gabor_tc_mt_k(R), 128) / 2); }
+int gabor_tc_mt_gm_elems(int R, int col_ty, int split)
+{
+    return (int)((split ? 2 : 1) * tstrip_bytes(gabor_tc_geometry(R).Kcol, 2 * col_ty) / 2);
+}
 
-cudaError_t build_gabor_tc_gm(uint16_t *Gm, int R, double sigma, double ws, int col_ty, cudaStream_t st)
+cudaError_t build_gabor_tc_gm(uint16_t *Gm, int R, double sigma, double ws, int col_ty, int split, cudaStream_t st)
 {
     int e = 0;
     frexp(1.0 / (2.5066282746310002 * sigma), &e);
     const TcGeometry g = gabor_tc_geometry(R);
     const int nc = tstrip_cores(g.Kcol, 2 * col_ty);
-    k_build_tstrip<<<(64 * nc + 255) / 256, 256, 0, st>>>(Gm, nc, col_ty - 1 + g.R8, R, sigma, ws, -e);
+    k_build_tstrip<<<(64 * nc + 255) / 256, 256, 0, st>>>(Gm, nc, col_ty - 1 + g.R8, R, sigma, ws, -e, split);
     return cudaGetLastError();
 }
 
-bool gabor_tc_mt_fits(int row_kmax, int row_pwmax, int col_kmax)
+bool gabor_tc_mt_fits(int row_kmax, int row_pwmax, int col_kmax, int split)
 {
-    return gabor_tc_smem_rows_mt(row_kmax, row_pwmax, 32) <= (size_t)kSmemLimit &&
-           1024 + mt_col_smem(col_kmax, 32).total <= (uint32_t)kSmemLimit;
+    return gabor_tc_smem_rows_mt(row_kmax, row_pwmax, 32, split) <= (size_t)kSmemLimit &&
+           1024 + mt_col_smem(col_kmax, 32, split, 1).total <= (uint32_t)kSmemLimit;
 }
 
-int gabor_tc_mt_col_ty(int col_kmax)
+int gabor_tc_mt_col_ty(int col_kmax, int split)
 {
-    return 1024 + mt_col_smem(col_kmax, 64).total <= (uint32_t)kSmemLimit ? 64 : 32;
+    return 1024 + mt_col_smem(col_kmax, 64, split, 1).total <= (uint32_t)kSmemLimit ? 64 : 32;
 }
 
-cudaError_t build_gabor_tc_am(uint16_t *Am, int R, double sigma, double wc, cudaStream_t st)
+// Operand stages of the modulated-tap column kernel: two where they fit, else one.
+int gabor_tc_mt_col_stages(int col_kmax, int col_ty, int split)
+{
+    return 1024 + mt_col_smem(col_kmax, col_ty, split, 2).total <= (uint32_t)kSmemLimit ? 2 : 1;
+}
+
+cudaError_t build_gabor_tc_am(uint16_t *Am, int R, double sigma, double wc, int split, cudaStream_t st)
 {
     // the scale of the frequency's Toeplitz operands: |S(d) cos|, |S(d) sin| <= S(0)
     int e = 0;
     frexp(1.0 / (2.5066282746310002 * sigma), &e);
     const int nc = tstrip_cores(gabor_tc_mt_k(R), 128);
-    k_build_tstrip<<<(64 * nc + 255) / 256, 256, 0, st>>>(Am, nc, kMtTileX - 1 + R, R, sigma, wc, -e);
+    k_build_tstrip<<<(64 * nc + 255) / 256, 256, 0, st>>>(Am, nc, kMtTileX - 1 + R, R, sigma, wc, -e, split);
     return cudaGetLastError();
 }
 
@@ -1688,8 +1771,10 @@ cudaError_t build_gabor_tc_prefix(const double *unit_w, const TcUnitDev *units, 
 cudaError_t gabor_tc_prepare()
 {
     cudaError_t e = cudaFuncSetAttribute(k_gabor_tc_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gabor_tc_rows_mt, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gabor_tc_cols_mt, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gabor_tc_rows_mt<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gabor_tc_rows_mt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gabor_tc_cols_mt<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gabor_tc_cols_mt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gabor_tc_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     return e;
 }
@@ -1699,11 +1784,14 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
     TcBankArgs a = a0;
     a.col_nst = col_stages(a.col_kmax);
     if (a.col_nst < 2) return cudaErrorInvalidValue;
-    if (a.row_mt && !gabor_tc_mt_fits(a.row_kmax, a.row_pwmax, a.col_kmax)) return cudaErrorInvalidValue;
+    if (a.row_mt && !gabor_tc_mt_fits(a.row_kmax, a.row_pwmax, a.col_kmax, a.split)) return cudaErrorInvalidValue;
+    if (a.split && !a.row_mt) return cudaErrorInvalidValue;   // hi + lo operands: modulated-tap kernels only
+    a.col_mt_nst = gabor_tc_mt_col_stages(a.col_kmax, a.col_mt_ty, a.split);
     const int n_row_items = a.nf * a.row_cnt, n_col_items = a.nf * a.col_cnt;
-    const size_t smem_r = a.row_mt ? gabor_tc_smem_rows_mt(a.row_kmax, a.row_pwmax, a.row_ty)
+    const size_t smem_r = a.row_mt ? gabor_tc_smem_rows_mt(a.row_kmax, a.row_pwmax, a.row_ty, a.split)
                                    : gabor_tc_smem_rows(a.row_kmax, a.row_pwmax, a.row_ty);
-    const size_t smem_c = a.row_mt ? 1024 + mt_col_smem(a.col_kmax, a.col_mt_ty).total : gabor_tc_smem_cols(a.col_kmax);
+    const size_t smem_c = a.row_mt ? 1024 + mt_col_smem(a.col_kmax, a.col_mt_ty, a.split, a.col_mt_nst).total
+                                   : gabor_tc_smem_cols(a.col_kmax);
     cudaError_t e0 = cudaMemsetAsync(a.minmax, 0, 2 * sizeof(unsigned), st);
     if (e0 != cudaSuccess) return e0;
     const dim3 ag(std::max(1, std::min(4, (a.W + 255) / 256)), std::max(1, std::min(a.H, 2 * sm_count)));
@@ -1721,7 +1809,8 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
     if (n_row_items > 0) {
         cudaError_t e;
         if (a.row_mt) {
-            e = launch_pdl(k_gabor_tc_rows_mt, dim3(std::min(n_row_items, sm_count)), dim3(512), smem_r, st, a);
+            e = launch_pdl(a.split ? k_gabor_tc_rows_mt<true> : k_gabor_tc_rows_mt<false>,
+                           dim3(std::min(n_row_items, sm_count)), dim3(512), smem_r, st, a);
         } else {
             k_gabor_tc_rows<<<std::min(n_row_items, sm_count), 512, smem_r, st>>>(a);
             e = cudaGetLastError();
@@ -1730,8 +1819,8 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
     }
     if (n_col_items > 0) {
         if (a.row_mt)
-            return launch_pdl(k_gabor_tc_cols_mt, dim3(std::min(n_col_items, sm_count)), dim3(kMtColThreads), smem_c,
-                              st, a);
+            return launch_pdl(a.split ? k_gabor_tc_cols_mt<true> : k_gabor_tc_cols_mt<false>,
+                              dim3(std::min(n_col_items, sm_count)), dim3(kMtColThreads), smem_c, st, a);
         else
             k_gabor_tc_cols<<<std::min(n_col_items, sm_count), kColThreads, smem_c, st>>>(a);
         return cudaGetLastError();
@@ -1742,10 +1831,12 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
 cudaError_t launch_gabor_tc_batch(const TcBankArgs &a0, int sm_count, cudaStream_t st)
 {
     TcBankArgs a = a0;
-    if (!a.imgs || !a.row_mt || !gabor_tc_mt_fits(a.row_kmax, a.row_pwmax, a.col_kmax)) return cudaErrorInvalidValue;
+    if (!a.imgs || !a.row_mt || !gabor_tc_mt_fits(a.row_kmax, a.row_pwmax, a.col_kmax, a.split))
+        return cudaErrorInvalidValue;
     a.col_nst = col_stages(a.col_kmax);
-    const size_t smem_r = gabor_tc_smem_rows_mt(a.row_kmax, a.row_pwmax, a.row_ty);
-    const size_t smem_c = 1024 + mt_col_smem(a.col_kmax, a.col_mt_ty).total;
+    a.col_mt_nst = gabor_tc_mt_col_stages(a.col_kmax, a.col_mt_ty, a.split);
+    const size_t smem_r = gabor_tc_smem_rows_mt(a.row_kmax, a.row_pwmax, a.row_ty, a.split);
+    const size_t smem_c = 1024 + mt_col_smem(a.col_kmax, a.col_mt_ty, a.split, a.col_mt_nst).total;
     static_assert(kMmParts == 64, "k_minmax_batch runs 8 x 8 blocks per image");
     k_minmax_batch<<<dim3(8, 8, a.nimg), 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
@@ -1753,11 +1844,13 @@ cudaError_t launch_gabor_tc_batch(const TcBankArgs &a0, int sm_count, cudaStream
     e = launch_pdl(k_ones_batch, dim3(16, a.nimg), dim3(256), 0, st, a, a.units, a.freqs, a.nf * a.nu_f);
     if (e != cudaSuccess) return e;
     if (a.n_row > 0) {
-        e = launch_pdl(k_gabor_tc_rows_mt, dim3(std::min(a.n_row, sm_count)), dim3(512), smem_r, st, a);
+        e = launch_pdl(a.split ? k_gabor_tc_rows_mt<true> : k_gabor_tc_rows_mt<false>, dim3(std::min(a.n_row, sm_count)),
+                       dim3(512), smem_r, st, a);
         if (e != cudaSuccess) return e;
     }
     if (a.n_col > 0)
-        e = launch_pdl(k_gabor_tc_cols_mt, dim3(std::min(a.n_col, sm_count)), dim3(kMtColThreads), smem_c, st, a);
+        e = launch_pdl(a.split ? k_gabor_tc_cols_mt<true> : k_gabor_tc_cols_mt<false>, dim3(std::min(a.n_col, sm_count)),
+                       dim3(kMtColThreads), smem_c, st, a);
     return e;
 }
 

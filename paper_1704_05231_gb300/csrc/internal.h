@@ -193,7 +193,10 @@ struct TcBankArgs {
     unsigned *mm_part;
     const int4 *row_list;  // {image, frequency, y0, x0}
     const int4 *col_list;  // {image, unit, x0, y0}
-    int n_row, n_col, nimg, pad2_;
+    int n_row, n_col, nimg;
+    int split;             // 1: BF16 operands as hi + lo pairs (modulated-tap kernels)
+    int col_mt_nst;        // operand stages of the modulated-tap column kernel (1 or 2)
+    int pad3_;
 };
 struct TcGeometry {
     int R, R8, Krow, Kcol, PW;
@@ -285,15 +288,18 @@ bool gabor_tc_supported(int R);
 int gabor_tc_mt_tile_x();
 int gabor_tc_mt_k(int R);
 int gabor_tc_mt_pw(int R);
-int gabor_tc_mt_tile_y(int Kmax, int PWmax);
-size_t gabor_tc_smem_rows_mt(int Kmax, int PWmax, int TY);
-cudaError_t build_gabor_tc_am(uint16_t *Am, int R, double sigma, double wc, cudaStream_t st);
-cudaError_t build_gabor_tc_gm(uint16_t *Gm, int R, double sigma, double ws, int col_ty, cudaStream_t st);
-// FP16 elements of one unit's modulated-tap operand strips (row pass; column pass of col_ty rows).
-int gabor_tc_mt_am_elems(int R);
-int gabor_tc_mt_gm_elems(int R, int col_ty);
-bool gabor_tc_mt_fits(int row_kmax, int row_pwmax, int col_kmax);
-int gabor_tc_mt_col_ty(int col_kmax);
+// split = 1: BF16 operands as hi + lo pairs (three products per K step).
+int gabor_tc_mt_tile_y(int Kmax, int PWmax, int split);
+size_t gabor_tc_smem_rows_mt(int Kmax, int PWmax, int TY, int split);
+cudaError_t build_gabor_tc_am(uint16_t *Am, int R, double sigma, double wc, int split, cudaStream_t st);
+cudaError_t build_gabor_tc_gm(uint16_t *Gm, int R, double sigma, double ws, int col_ty, int split, cudaStream_t st);
+// 16-bit elements of one unit's modulated-tap operand strips (row pass; column pass of col_ty
+// rows), both hi and lo under split.
+int gabor_tc_mt_am_elems(int R, int split);
+int gabor_tc_mt_gm_elems(int R, int col_ty, int split);
+int gabor_tc_mt_col_stages(int col_kmax, int col_ty, int split);
+bool gabor_tc_mt_fits(int row_kmax, int row_pwmax, int col_kmax, int split);
+int gabor_tc_mt_col_ty(int col_kmax, int split);
 cudaError_t build_gabor_tc_b(uint16_t *Brow, uint16_t *Bcol, int R, double sigma, int bf16, float *unscale,
                              cudaStream_t st);
 cudaError_t gabor_tc_prepare();

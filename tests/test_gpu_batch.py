@@ -147,8 +147,9 @@ def test_tc_batch_matches_fp32_on_small_images():
             assert rel_err(y.cpu().numpy(), x.cpu().numpy()) <= TC_TOL
 
 
+@pytest.mark.parametrize("precision", ["fp16_tc", "bf16_tc"])
 @pytest.mark.parametrize("boundary,layout", [("zero", "planes"), ("mirror", "planes"), ("zero", "pixels")])
-def test_tc_batch_one_launch_set_bitwise_equals_single_calls(boundary, layout):
+def test_tc_batch_one_launch_set_bitwise_equals_single_calls(boundary, layout, precision):
     # Tensor-core batch: one k_minmax, one k_ones, one row and one column launch for all images;
     # every output takes the same MMAs as in a single-image call, so the results are bitwise
     # those of one call per image, also when replayed from a captured CUDA graph.
@@ -158,7 +159,7 @@ def test_tc_batch_one_launch_set_bitwise_equals_single_calls(boundary, layout):
     shapes = [(40, 70), (128, 96), (333, 257), (7, 300), (190, 41)]
     imgs = [torch.from_numpy(synth.pink_noise([61, i], h, w)).cuda() for i, (h, w) in enumerate(shapes)]
     th, om, sg = c4_bank()
-    with GaborBank(th, om, sg, precision="fp16_tc", boundary=boundary, layout=layout) as gbk:
+    with GaborBank(th, om, sg, precision=precision, boundary=boundary, layout=layout) as gbk:
         singles = [gbk.filter(t).clone() for t in imgs]
         outs = [torch.full_like(s, float("nan")) for s in singles]
         gbk.filter_batch(imgs, outs)

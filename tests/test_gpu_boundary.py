@@ -25,7 +25,7 @@ def _bank(precision, boundary, layout="planes"):
     return GaborBank(th, om, sg, precision=precision, boundary=boundary, layout=layout), th, om, sg
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", FP32_TOL), ("fp16_tc", TC_TOL)])
+@pytest.mark.parametrize("precision,tol", [("fp32", FP32_TOL), ("fp16_tc", TC_TOL), ("bf16_tc", TC_TOL)])
 @pytest.mark.parametrize("boundary", ["replicate", "mirror"])
 @pytest.mark.parametrize("H,W", SHAPES)
 def test_bank_boundary_matches_oracle(precision, tol, boundary, H, W):
@@ -40,7 +40,7 @@ def test_bank_boundary_matches_oracle(precision, tol, boundary, H, W):
     assert e <= tol
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", FP32_TOL), ("fp16_tc", TC_TOL)])
+@pytest.mark.parametrize("precision,tol", [("fp32", FP32_TOL), ("fp16_tc", TC_TOL), ("bf16_tc", TC_TOL)])
 @pytest.mark.parametrize("boundary", ["replicate", "mirror"])
 def test_paper_bank_boundary_160x200(precision, tol, boundary):
     import torch

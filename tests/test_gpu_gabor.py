@@ -152,7 +152,7 @@ def test_impulse_response_on_gpu(torch_cuda):
 
 # ---------------------------------------------------------------- tensor-core bank
 
-@pytest.mark.parametrize("precision", ["fp16_tc"])
+@pytest.mark.parametrize("precision", ["fp16_tc", "bf16_tc"])
 def test_tc_bank_c1_full_parity(torch_cuda, precision):
     from tests.helpers import TC_TOL
     img = synth.uniform01(0, 256, 256)
@@ -164,7 +164,7 @@ def test_tc_bank_c1_full_parity(torch_cuda, precision):
     assert e <= TC_TOL
 
 
-@pytest.mark.parametrize("precision", ["fp16_tc"])
+@pytest.mark.parametrize("precision", ["fp16_tc", "bf16_tc"])
 @pytest.mark.parametrize("H,W", [(37, 75), (160, 200), (1, 50), (129, 33)])
 def test_tc_bank_ragged_and_c2_bank(torch_cuda, precision, H, W):
     from tests.helpers import TC_TOL
@@ -177,7 +177,7 @@ def test_tc_bank_ragged_and_c2_bank(torch_cuda, precision, H, W):
     assert e <= TC_TOL
 
 
-@pytest.mark.parametrize("precision", ["fp16_tc"])
+@pytest.mark.parametrize("precision", ["fp16_tc", "bf16_tc"])
 def test_tc_bank_c2_full_size_full_oracle(torch_cuda, c2_full, precision):
     from tests.helpers import TC_TOL
     img, ref = c2_full
@@ -207,14 +207,29 @@ def test_tc_bank_unpaired_orientations_and_reuse_off(torch_cuda):
     assert rel_err(b, ref) <= TC_TOL
 
 
-def test_tc_bank_bf16_is_refused(torch_cuda):
+def test_tc_bank_bf16_hi_lo_and_its_limits(torch_cuda):
+    # BF16 operands as hi + lo pairs (three products per K step): far inside the tensor-core
+    # bound (well below the FP16 error), equal to the FP32 path to about 1e-5; the
+    # step-by-step kernels take FP16 operands only, so that form refuses BF16.
     from paper_1704_05231_gb300 import GaborBank, GBError
+    from tests.helpers import TC_TOL
     torch = torch_cuda
-    th, om, sg = c1_bank()
+    img = synth.paper_like(9, 96, 130)
+    th, om, sg = c2_bank()
+    t = torch.from_numpy(img).cuda()
+    ref = oracle.gabor_bank(img, th, om, sg)
     with GaborBank(th, om, sg, precision="bf16_tc") as gbk:
+        b = gbk.filter(t).cpu().numpy()
+        gbk.device_status()
+        gbk.set_option("row_pass", 1)
         with pytest.raises(GBError) as ei:
-            gbk.filter(torch.zeros((32, 32), dtype=torch.float32, device="cuda"))
+            gbk.filter(t)
         assert ei.value.status == -4
+    with GaborBank(th, om, sg, precision="fp16_tc") as gbk:
+        h = gbk.filter(t).cpu().numpy()
+    eb, eh = rel_err(b, ref), rel_err(h, ref)
+    print("BF16 hi+lo rel err", eb, "FP16", eh)
+    assert eb <= TC_TOL and eb <= 0.1 * eh
 
 
 def _schedules(torch, imgs, th, om, sg, opts=(), **kw):
@@ -389,9 +404,9 @@ def test_tc_bank_row_pass_forms(torch_cuda, row_pass, boundary, H, W):
     assert e <= TC_TOL
 
 
-@pytest.mark.parametrize("row_pass", [1, 2])
+@pytest.mark.parametrize("row_pass,precision", [(1, "fp16_tc"), (2, "fp16_tc"), (2, "bf16_tc")])
 @pytest.mark.parametrize("boundary", ["zero", "mirror"])
-def test_tc_bank_large_radius_sampled(torch_cuda, row_pass, boundary):
+def test_tc_bank_large_radius_sampled(torch_cuda, row_pass, precision, boundary):
     # Batched-bank frequencies pi/2 .. pi/32 (sigma = pi / omega, radii 6 .. 96): with radius
     # 96 the modulated-tap column pass takes 32-row jobs (the 64-row operands exceed shared
     # memory); ragged sizes put partial jobs at both image edges.
@@ -404,14 +419,14 @@ def test_tc_bank_large_radius_sampled(torch_cuda, row_pass, boundary):
     sg = [math.pi / w for w in om]
     for H, W in [(333, 257), (97, 530)]:
         img = synth.paper_like([47, H, W], H, W)
-        with GaborBank(th, om, sg, precision="fp16_tc", boundary=boundary) as gbk:
+        with GaborBank(th, om, sg, precision=precision, boundary=boundary) as gbk:
             gbk.set_option("row_pass", row_pass)
             got = gbk.filter(torch.from_numpy(img).cuda()).cpu().numpy()
             gbk.device_status()
         with GaborBank(th, om, sg, boundary=boundary) as gbk:
             f32 = gbk.filter(torch.from_numpy(img).cuda()).cpu().numpy()
         e = rel_err(got, f32)
-        print("TC large radius", row_pass, boundary, H, W, "rel err vs FP32", e)
+        print("TC large radius", row_pass, precision, boundary, H, W, "rel err vs FP32", e)
         assert e <= TC_TOL
         xs, ys = sample_points(rng, H, W, 200)
         ref = oracle.gabor_bank(img, th, om, sg, points=(xs, ys), boundary=boundary)
