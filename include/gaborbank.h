@@ -214,7 +214,13 @@ typedef enum {
        (u, v) with u in [0, Mx), v in [0, My/2], nothing is derived from J*_u, and only the
        conjugate fill F_{u,v} = F*_{Mx-u,My-v} stays.  Results agree to FP32 rounding.  The
        tensor-core SDFT is unaffected. */
-    GB_OPT_SDFT_REUSE = 12
+    GB_OPT_SDFT_REUSE = 12,
+    /* Tile shapes of the tensor-core bank's modulated-tap kernels: value = row + 256 * column,
+       row = image rows per row-pass item, column = output rows per column-pass job, each 0
+       (automatic: 64 where the operands fit in shared memory, else 32) or 32 or 64 (taken when
+       it fits, else the automatic value).  Results do not change (every output takes the same
+       products).  Used by the autotuner.  Synchronises the device. */
+    GB_OPT_TC_TILES = 13
 } gb_option;
 
 /* 1-D Gaussian smoothers (GB_OPT_SMOOTHER). */

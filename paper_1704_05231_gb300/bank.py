@@ -20,7 +20,7 @@ STATUS = {0: "GB_OK", -1: "GB_ERR_INVALID_ARG", -2: "GB_ERR_OUT_OF_MEMORY", -3: 
           -4: "GB_ERR_UNSUPPORTED", -5: "GB_ERR_BUDGET", -6: "GB_ERR_TIMEOUT"}
 STATUS_CODE = {v: k for k, v in STATUS.items()}
 PRECISION = {"fp32": 0, "fp16_tc": 1, "bf16_tc": 2}
-OPTION = {"reuse": 1, "tile_rows": 2, "segments": 3, "boundary": 4, "layout": 5, "smoother": 6, "sdft_order": 7, "pipeline": 8, "row_pass": 9, "bank_ctas": 10, "sdft_form": 11, "sdft_reuse": 12}
+OPTION = {"reuse": 1, "tile_rows": 2, "segments": 3, "boundary": 4, "layout": 5, "smoother": 6, "sdft_order": 7, "pipeline": 8, "row_pass": 9, "bank_ctas": 10, "sdft_form": 11, "sdft_reuse": 12, "tc_tiles": 13}
 SMOOTHER = {"fir": 0, "iir": 1}
 BOUNDARY = {"zero": 0, "replicate": 1, "mirror": 2}
 LAYOUT = {"planes": 0, "pixels": 1}

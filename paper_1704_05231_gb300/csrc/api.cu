@@ -476,6 +476,15 @@ int tc_lpad(const gabor_bank *h)
     return ((rmax + 64) + 63) / 64 * 64;
 }
 
+// Output rows per column job of the modulated-tap column kernel: the GB_OPT_TC_TILES choice
+// where it fits, else the largest that fits.
+int tc_col_ty(const gabor_bank *h)
+{
+    const int split = h->prec == GB_BF16_TC;
+    const int auto_ty = gabor_tc_mt_col_ty(h->tc_col_kmax, split);
+    return (h->tc_col_ty_opt == 32 || (h->tc_col_ty_opt == 64 && auto_ty == 64)) ? h->tc_col_ty_opt : auto_ty;
+}
+
 // Elements of the intermediate for an H x W image: every column signal of every unit, one
 // column of Hp = round64(H) + 2 Lpad rows per image column.
 int64_t tc_sig_elems(const gabor_bank *h, int H, int W)
@@ -551,11 +560,12 @@ gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
         h->tc_mt_pwmax = std::max(h->tc_mt_pwmax, gabor_tc_mt_pw(R));
     }
     h->tc_mt_ty = gabor_tc_mt_tile_y(h->tc_mt_kmax, h->tc_mt_pwmax, split);
+    if (h->tc_row_ty_opt == 32) h->tc_mt_ty = 32;   // 64 only where it fits
     h->tc_mt_ok = gabor_tc_mt_fits(h->tc_mt_kmax, h->tc_mt_pwmax, h->tc_col_kmax, split);
     GB_TRY(dalloc(&h->d_tcAm, std::max<size_t>(am_total, 1)));
     std::vector<size_t> off_gm(nu);
     size_t gm_total = 0;
-    const int col_ty = gabor_tc_mt_col_ty(h->tc_col_kmax, split);
+    const int col_ty = tc_col_ty(h);
     for (int i = 0; i < nu; ++i) {
         off_gm[i] = gm_total;
         gm_total += ((size_t)gabor_tc_mt_gm_elems(h->freqs[h->units[i].s].R, col_ty, split) + 127) / 128 * 128;
@@ -657,7 +667,7 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     for (const Freq &f : h->freqs) rmax = std::max(rmax, f.R);
     const int ypad = h->boundary == kBoundaryZero ? 0 : (rmax + ty - 1) / ty * ty;
     const int64_t row_cnt = (int64_t)((H + 2 * ypad + ty - 1) / ty) * ((W + tile_x - 1) / tile_x);
-    const int col_ty = gabor_tc_mt_col_ty(h->tc_col_kmax, split);   // modulated-tap column rows per job
+    const int col_ty = tc_col_ty(h);   // modulated-tap column rows per job
     const int64_t ny_mt = (H + col_ty - 1) / col_ty;
     const int64_t col_cnt = row_mt ? ny_mt * h->tc_nu_f * nx64
                                    : ny64 * (h->tc_np_f * nx32 + (h->tc_nu_f - h->tc_np_f) * nx64);
@@ -766,7 +776,7 @@ gb_status filter_batch_tc(gabor_bank *h, int n, const float *const *d_imgs, cons
     if (h->fp32_row_form == 1 || !h->tc_mt_ok) return GB_OK;
     const int nf = (int)h->freqs.size(), nu = (int)h->units.size();
     const int ty = h->tc_mt_ty, tile_x = gabor_tc_mt_tile_x();
-    const int col_ty = gabor_tc_mt_col_ty(h->tc_col_kmax, split);
+    const int col_ty = tc_col_ty(h);
     int rmax = 0;
     for (const Freq &f : h->freqs) rmax = std::max(rmax, f.R);
     const int ypad = h->boundary == kBoundaryZero ? 0 : (rmax + ty - 1) / ty * ty;
@@ -1478,6 +1488,19 @@ gb_status gabor_bank_set_option(gabor_bank_t h, int key, int64_t value)
         if (value < 0 || value > 2) return fail(GB_ERR_INVALID_ARG, "GB_OPT_SDFT_FORM takes 0, 1 or 2");
         h->sdft_form = (int)value;
         return GB_OK;
+    case GB_OPT_TC_TILES: {
+        const int r = (int)(value & 255), c = (int)(value >> 8);
+        if (value < 0 || (r != 0 && r != 32 && r != 64) || (c != 0 && c != 32 && c != 64))
+            return fail(GB_ERR_INVALID_ARG, "GB_OPT_TC_TILES takes row + 256 * column, each 0, 32 or 64");
+        if (r != h->tc_row_ty_opt || c != h->tc_col_ty_opt) {
+            DeviceGuard g(h->device);
+            cudaDeviceSynchronize();
+            h->tc_row_ty_opt = r;
+            h->tc_col_ty_opt = c;
+            free_tc(h);   // the column operand strips depend on the job rows
+        }
+        return GB_OK;
+    }
     case GB_OPT_SDFT_REUSE:
         if (value != 0 && value != 1) return fail(GB_ERR_INVALID_ARG, "GB_OPT_SDFT_REUSE takes 0 or 1");
         h->sdft_reuse = (int)value;

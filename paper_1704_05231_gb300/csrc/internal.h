@@ -423,6 +423,7 @@ struct gabor_bank {
     int tc_row_ty = 64;
     int tc_mt_kmax = 0, tc_mt_pwmax = 0, tc_mt_ty = 64;   // modulated-tap row pass geometry
     bool tc_mt_ok = false;                    // the modulated-tap kernels fit every frequency
+    int tc_row_ty_opt = 0, tc_col_ty_opt = 0; // GB_OPT_TC_TILES (0 automatic, 32, 64)
     uint16_t *d_tcGm = nullptr;               // modulated-tap column operands, one per unit
     int tc_H = 0, tc_W = 0, tc_Lpad = 0;
     int64_t tc_Hp = 0;

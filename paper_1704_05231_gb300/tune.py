@@ -1,12 +1,14 @@
-"""Autotuner for the tile geometry of the FP32 filter-bank kernel.
+"""Autotuner for the tile geometry of the filter-bank kernels.
 
-For every frequency of a plan it picks the rows per streamed chunk (TH) and the number of row
-segments per column strip, and for the whole plan the CTAs per SM (one of 16 warps or two of
-8), by timing the whole bank on the caller's images (coordinate descent over the
-frequencies for each CTA setting, CUDA events, L2 flushed between timings).  The choice
-trades the 2R-row vertical halo recomputed per segment against load balance across the SMs;
-it does not change any result (every output's arithmetic is the same).  Choices are cached in a JSON
-file keyed by GPU name, image-size classes, radii, orientation count and precision.
+FP32 handles: for every frequency of a plan it picks the rows per streamed chunk (TH) and the
+number of row segments per column strip, and for the whole plan the CTAs per SM (one of 16
+warps or two of 8), by timing the whole bank on the caller's images (coordinate descent over
+the frequencies for each CTA setting, CUDA events, L2 flushed between timings).  The choice
+trades the 2R-row vertical halo recomputed per segment against load balance across the SMs.
+Tensor-core handles: the rows per row-pass item and per column-pass job of the modulated-tap
+kernels (32 or 64 each, GB_OPT_TC_TILES), timed the same way.  No choice changes any result
+(every output's arithmetic is the same).  Choices are cached in a JSON file keyed by GPU name,
+image-size classes, radii, orientation count and precision.
 """
 from __future__ import annotations
 
@@ -18,6 +20,7 @@ import statistics
 TILE_ROWS = (0, 32, 64)
 SEGMENTS = (0, 1, 2, 4, 8)
 CTAS = (1, 2)
+TC_TILES = ((64, 64), (32, 64), (64, 32), (32, 32))   # (row-pass rows, column-pass rows)
 
 
 def default_cache_path():
@@ -53,28 +56,33 @@ def _save(path, data):
 
 def autotune(gbk, imgs, cache_path=None, steps=3, use_cache=True, tile_rows=TILE_ROWS, segments=SEGMENTS,
              ctas=CTAS):
-    """Choose (tile_rows, segments) per frequency and the CTAs per SM for `imgs` (a CUDA tensor
-    or a list of them).
+    """Choose the tile geometry for `imgs` (a CUDA tensor or a list of them).
 
-    Applies the choice to `gbk` and returns {"key", "tiling": [[tile_rows, segments], ...],
-    "ctas", "ms"}.  `tile_rows`, `segments` and `ctas` are the candidate values searched.  Only
-    the FP32 path has a tunable geometry; other precisions return the defaults.
+    FP32 handles: (tile_rows, segments) per frequency and the CTAs per SM; returns {"key",
+    "tiling": [[tile_rows, segments], ...], "ctas", "ms"} (`tile_rows`, `segments` and `ctas`
+    are the candidate values searched).  Tensor-core handles: the modulated-tap tile rows;
+    returns {"key", "tc_tiles": [row, column], "ms"}.  The choice is applied to `gbk`.
     """
     import torch
     batch = isinstance(imgs, (list, tuple))
     ims = list(imgs) if batch else [imgs]
     shapes = [tuple(t.shape) for t in ims]
     nf = len(gbk.omegas)
-    if gbk.precision != "fp32" or nf == 0:
-        return {"key": None, "tiling": [[0, 0]] * nf, "ctas": None, "ms": None}
+    if nf == 0:
+        return {"key": None, "tiling": [], "ctas": None, "ms": None}
+    tc = gbk.precision != "fp32"
     path = cache_path or default_cache_path()
-    key = (cache_key(gbk, shapes, torch.cuda.get_device_name()) +
-           f"|{list(tile_rows)}|{list(segments)}|{list(ctas)}")
+    key = cache_key(gbk, shapes, torch.cuda.get_device_name()) + (
+        f"|tc{list(TC_TILES)}" if tc else f"|{list(tile_rows)}|{list(segments)}|{list(ctas)}")
     cache = _load(path) if use_cache else {}
     if key in cache:
-        gbk.set_option("bank_ctas", cache[key]["ctas"])
-        for s, (tr, sg) in enumerate(cache[key]["tiling"]):
-            gbk.set_tiling(s, tr, sg)
+        if tc:
+            r, c = cache[key]["tc_tiles"]
+            gbk.set_option("tc_tiles", r + 256 * c)
+        else:
+            gbk.set_option("bank_ctas", cache[key]["ctas"])
+            for s, (tr, sg) in enumerate(cache[key]["tiling"]):
+                gbk.set_tiling(s, tr, sg)
         return dict(cache[key], key=key, cached=True)
 
     outs = [torch.empty(gbk.out_shape(*sh), dtype=torch.complex64, device=t.device) for t, sh in zip(ims, shapes)]
@@ -100,6 +108,21 @@ def autotune(gbk, imgs, cache_path=None, steps=3, use_cache=True, tile_rows=TILE
             torch.cuda.synchronize()
             ts.append(a.elapsed_time(b))
         return statistics.median(ts)
+
+    if tc:
+        best = None
+        for r, c in TC_TILES:
+            gbk.set_option("tc_tiles", r + 256 * c)
+            ms = timed()
+            if best is None or ms < best[2]:
+                best = (r, c, ms)
+        gbk.set_option("tc_tiles", best[0] + 256 * best[1])
+        entry = {"tc_tiles": [best[0], best[1]], "ms": best[2]}
+        if use_cache:
+            cache = _load(path)
+            cache[key] = entry
+            _save(path, cache)
+        return dict(entry, key=key, cached=False)
 
     best = None
     for c in ctas:

@@ -177,3 +177,26 @@ def test_tc_batch_one_launch_set_bitwise_equals_single_calls(boundary, layout, p
     if layout == "planes":
         ref = oracle.gabor_bank(imgs[0].cpu().numpy(), th, om, sg, boundary=boundary)
         assert rel_err(singles[0].cpu().numpy(), ref) <= TC_TOL
+
+
+@pytest.mark.parametrize("precision", ["fp16_tc", "bf16_tc"])
+def test_tc_tile_choices_and_autotune_bitwise(precision):
+    # GB_OPT_TC_TILES (rows per row item / column job: 32 or 64) changes no result; the
+    # autotuner's tensor-core branch times the choices and applies one.
+    import torch
+    from paper_1704_05231_gb300 import GaborBank, tune
+    th, om, sg = c4_bank()
+    imgs = [torch.from_numpy(synth.pink_noise([71, i], h, w)).cuda() for i, (h, w) in enumerate([(150, 230), (97, 64)])]
+    res = []
+    with GaborBank(th, om, sg, precision=precision) as gbk:
+        for r, c in ((64, 64), (32, 64), (64, 32), (32, 32)):
+            gbk.set_option("tc_tiles", r + 256 * c)
+            res.append([gbk.filter(t).clone() for t in imgs] + [o.clone() for o in gbk.filter_batch(imgs)])
+            gbk.device_status()
+        t = tune.autotune(gbk, imgs, use_cache=False, steps=1)
+        assert t["tc_tiles"][0] in (32, 64) and t["tc_tiles"][1] in (32, 64)
+        res.append([gbk.filter(t_).clone() for t_ in imgs])
+        gbk.device_status()
+    for other in res[1:]:
+        for a, b in zip(res[0], other):
+            assert torch.equal(a, b)
