@@ -228,10 +228,13 @@ typedef enum {
     GB_SMOOTHER_FIR = 0,       /* S_sigma truncated at R: exact against Eq. 1 (all precisions) */
     GB_SMOOTHER_IIR = 1        /* Young-van Vliet third-order forward / backward recursion (the
                                   smoother of Sec. II): approximate, cost independent of sigma; FP32
-                                  handles, sigma >= 0.5.  Each signal is extended by ceil(12 sigma) + 32
-                                  samples per side under the boundary rule; the recursions start from
-                                  zero state.  Uses a library-owned workspace of about
-                                  (n_signals + 2 n_units) * (H + P) * (W + P) * 4 bytes. */
+                                  handles, sigma >= 0.5.  Each signal is extended by P = ceil(12 sigma)
+                                  + 32 samples per side under the boundary rule; the recursions start
+                                  from zero state.  Evaluated in difference form, chunk-parallel along
+                                  every line.  Uses a library-owned workspace of about
+                                  8 * n_units * (H + 2 P) * W bytes (J of every horizontal pass) plus
+                                  1.5 bytes per column-pass sample; extended rows (W + 2 P) longer than
+                                  about 20000 samples return GB_ERR_UNSUPPORTED. */
 } gb_smoother;
 
 /* Image extension rules (GB_OPT_BOUNDARY).  The paper leaves the border unstated. */

@@ -81,8 +81,10 @@ int radius_of(double sigma, double rf) { return (int)std::ceil(rf * sigma - 1e-9
 int iir_pad(double sigma) { return (int)std::ceil(12.0 * sigma) + 32; }
 
 // Young and van Vliet's recursive Gaussian (Signal Processing 44, 1995): q from sigma (two
-// fitted branches), the third-order coefficients b0..b3 and the gain B; c = {B, b1/b0, b2/b0,
-// b3/b0} for w[n] = B x[n] + (b1 w[n-1] + b2 w[n-2] + b3 w[n-3]) / b0.
+// fitted branches), the third-order coefficients b0..b3 and the gain B, for
+// w[n] = B x[n] + (b1 w[n-1] + b2 w[n-2] + b3 w[n-3]) / b0; stored for the difference form
+// (c0 = B, e1 = (b2 + b3) / b0, c3 = b3 / b0, kept as ce = c0 + e1) with the powers
+// A^(16 * 2^i) of its zero-input state matrix, all in FP64 before rounding.
 IirFreq iir_coefficients(double sigma)
 {
     const double q = sigma >= 2.5 ? 0.98711 * sigma - 0.96330 : 3.97156 - 4.14554 * std::sqrt(1.0 - 0.26891 * sigma);
@@ -91,12 +93,27 @@ IirFreq iir_coefficients(double sigma)
     const double b1 = 2.44413 * q + 2.85619 * q2 + 1.26661 * q3;
     const double b2 = -(1.4281 * q2 + 1.26661 * q3);
     const double b3 = 0.422205 * q3;
+    const double c0 = 1.0 - (b1 + b2 + b3) / b0, e1 = (b2 + b3) / b0, c3 = b3 / b0;
     IirFreq f{};
-    f.c[0] = (float)(1.0 - (b1 + b2 + b3) / b0);
-    f.c[1] = (float)(b1 / b0);
-    f.c[2] = (float)(b2 / b0);
-    f.c[3] = (float)(b3 / b0);
+    f.c0 = (float)c0;
+    f.ce = (float)(c0 + e1);
+    f.c3 = (float)c3;
     f.P = iir_pad(sigma);
+    // state (w1, d1, d2); one zero-input step: D = -c0 w1 - e1 d1 - c3 d2, (w1 + D, D, d1)
+    double A[9] = {1.0 - c0, -e1, -c3, -c0, -e1, -c3, 0.0, 1.0, 0.0};
+    auto mul = [](const double *x, const double *y, double *z) {
+        double t[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                t[3 * i + j] = x[3 * i] * y[j] + x[3 * i + 1] * y[3 + j] + x[3 * i + 2] * y[6 + j];
+        std::copy(t, t + 9, z);
+    };
+    double M[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    for (int k = 0; k < kIirChunk; ++k) mul(M, A, M);
+    for (int l = 0; l < kIirLevels; ++l) {
+        for (int i = 0; i < 9; ++i) f.m[l][i] = (float)M[i];
+        mul(M, M, M);
+    }
     return f;
 }
 
@@ -196,7 +213,6 @@ gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
     std::vector<double> w(2 * nu), sg(nf);
     std::vector<int> lo(nf), T(nf);
     std::vector<UnitDev> ud(nu);
-    int sig = 0;
     for (int i = 0; i < nu; ++i) {
         w[2 * i] = h->units[i].wc / M_PI;
         w[2 * i + 1] = h->units[i].ws / M_PI;
@@ -204,9 +220,7 @@ gb_status ensure_tables(gabor_bank *h, int H, int W, cudaStream_t st)
         ud[i].phx = h->d_phx + (size_t)i * (Wcap + 2 * mg) + mg;
         ud[i].phy = h->d_phy + (size_t)i * (Hcap + 2 * mg) + mg;
         ud[i].s = h->units[i].s;
-        ud[i].sig = sig;
         ud[i].twin = twin_of(h, i);
-        sig += h->units[i].k_b >= 0 ? 4 : 2;
         ud[i].plane_a = h->units[i].s * K + h->units[i].k_a;
         ud[i].plane_b = h->units[i].k_b >= 0 ? h->units[i].s * K + h->units[i].k_b : -1;
     }
@@ -939,8 +953,8 @@ gb_status filter_batch_tc(gabor_bank *h, int n, const float *const *d_imgs, cons
     return GB_OK;
 }
 
-// The bank with the recursive Gaussian (GB_SMOOTHER_IIR): row and column recursions through a
-// library-owned workspace.
+// The bank with the recursive Gaussian (GB_SMOOTHER_IIR): the row recursions write J into a
+// library-owned workspace, the column recursions read it and write the bank.
 gb_status filter_device_iir(gabor_bank *h, const float *d_img, int H, int W, int64_t pitch, void *d_out,
                             cudaStream_t st)
 {
@@ -956,10 +970,14 @@ gb_status filter_device_iir(gabor_bank *h, const float *d_img, int H, int W, int
         GB_TRY(dalloc(&h->d_iirfreq, (size_t)nf));
         GB_CU(cudaMemcpy(h->d_iirfreq, fq.data(), nf * sizeof(IirFreq), cudaMemcpyHostToDevice));
     }
-    int pmax = 0, nsig = 0;
-    for (const Freq &f : h->freqs) pmax = std::max(pmax, iir_pad(f.sigma));
-    for (const Unit &u : h->units) nsig += u.k_b >= 0 ? 4 : 2;
     const bool ext = h->boundary != kBoundaryZero;
+    int pmax = 0, wxmax = 0, hcmax = 0;
+    for (const Freq &f : h->freqs) {
+        const int P = iir_pad(f.sigma);
+        pmax = std::max(pmax, P);
+        wxmax = std::max(wxmax, (ext ? P : 0) + W + P);
+        hcmax = std::max(hcmax, (ext ? P : 0) + H + P);
+    }
     IirArgs a{};
     a.img = d_img;
     a.pitch = pitch;
@@ -969,16 +987,18 @@ gb_status filter_device_iir(gabor_bank *h, const float *d_img, int H, int W, int
     a.layout = h->layout;
     a.nplanes = (int)(h->omega.size() * h->theta.size());
     a.bmode = h->boundary;
+    a.nunits = (int)h->units.size();
     a.units = h->d_unitdev;
     a.freqs = h->d_iirfreq;
     a.Py = ext ? pmax : 0;
     a.Hr = H + 2 * a.Py;
-    a.Wxmax = (ext ? pmax : 0) + W + pmax;
-    a.Hcmax = (ext ? pmax : 0) + H + pmax;
-    const size_t row_tmp = (size_t)h->units.size() * a.Hr * a.Wxmax * sizeof(float2);
-    const size_t col_tmp = (size_t)nsig * a.Hcmax * W * sizeof(float);
-    const size_t tmp_bytes = (std::max(row_tmp, col_tmp) + 255) / 256 * 256;
-    const size_t need = tmp_bytes + (size_t)nsig * a.Hr * W * sizeof(float);
+    a.row_nsc = (wxmax + 511) / 512;
+    a.col_nsc = (hcmax + 127) / 128;
+    if (!gabor_iir_fits(a.row_nsc, a.col_nsc))
+        return fail(GB_ERR_UNSUPPORTED, "the recursive Gaussian's extended rows or columns exceed its shared-memory plan");
+    const size_t j_bytes = ((size_t)h->units.size() * a.Hr * W * sizeof(float2) + 255) / 256 * 256;
+    const size_t need = j_bytes + (size_t)gabor_iir_col_ctas(W, (int)h->units.size()) *
+                                      gabor_iir_col_scratch_floats(a.col_nsc) * sizeof(float);
     if (need > h->iirws_bytes) {
         GB_CU(cudaStreamSynchronize(st));   // earlier work of this handle may still use it
         dfree(h->d_iirws);
@@ -986,9 +1006,9 @@ gb_status filter_device_iir(gabor_bank *h, const float *d_img, int H, int W, int
         GB_TRY(dalloc(&h->d_iirws, need));
         h->iirws_bytes = need;
     }
-    a.tmp = reinterpret_cast<float2 *>(h->d_iirws);
-    a.sig = reinterpret_cast<float *>(h->d_iirws + tmp_bytes);
-    GB_CU(launch_gabor_iir(a, (int)h->units.size(), st));
+    a.J = reinterpret_cast<float2 *>(h->d_iirws);
+    a.col_scratch = reinterpret_cast<float *>(h->d_iirws + j_bytes);
+    GB_CU(launch_gabor_iir(a, st));
     return GB_OK;
 }
 

@@ -50,10 +50,9 @@ struct UnitDev {
     int s;              // frequency index
     int plane_a;        // output plane of theta_a  (s * n_theta + k)
     int plane_b;        // output plane of pi - theta_a, or -1 when unpaired
-    int sig;            // first column signal of the unit in the recursive path's buffers
     int twin;           // FP32 bank, modulated-tap row pass: the unpaired unit that shares this
                         // unit's work items, or -1
-    int pad_;
+    int pad_[2];
 };
 
 // Device view of one frequency: Gaussian taps and the FP32 kernel's tile geometry.
@@ -204,26 +203,36 @@ struct TcGeometry {
 };
 
 // ---- recursive-Gaussian bank (gabor_iir.cu) ----
-// Young-van Vliet coefficients of one frequency: w[n] = c0 x[n] + c1 w[n-1] + c2 w[n-2] +
-// c3 w[n-3] (and the same backward), and the extension P on each side of a signal.
+// Young-van Vliet recursion of one frequency, w[n] = c0 x[n] + c1 w[n-1] + c2 w[n-2] +
+// c3 w[n-3] (and the same backward), evaluated in difference form: with the state
+// (w1, d1, d2) = (w[n-1], w[n-1] - w[n-2], w[n-2] - w[n-3]) one step is
+//   D = c0 (x[n] - w1) - e1 d1 - c3 d2,  w[n] = w1 + D,  (w1, d1, d2) <- (w[n], D, d1),
+// e1 = c2 + c3 (the same recursion, since c1 + c2 + c3 = 1 - c0); the kernels use
+// ce = c0 + e1.  m[i] is the 3 x 3 state matrix of kIirChunk << i zero-input steps
+// (row-major), for the chunk-parallel scans.  P is the extension on each side of a signal.
+constexpr int kIirChunk = 16;   // samples per thread chunk of the chunk-parallel recursions
+constexpr int kIirLevels = 5;   // m[i] = A^(16 * 2^i), i < 5
 struct IirFreq {
-    float c[4];
+    float c0, ce, c3;
     int P;
-    int pad_[3];
+    float m[kIirLevels][9];
+    float pad_[3];
 };
 struct IirArgs {
     const float *img;
     int64_t pitch;
     int H, W;
     float2 *out;
-    int layout, nplanes, bmode, pad_;
+    int layout, nplanes, bmode, nunits;
     const UnitDev *units;
     const IirFreq *freqs;
-    float2 *tmp;           // scratch: row forward outputs [unit][Hr][Wxmax], then column ones [signal][Hcmax][W]
-    float *sig;            // column signals [signal][Hr][W], row r at y = r - Py
-    int Hr, Py, Wxmax, Hcmax;
+    float2 *J;             // row-pass outputs J [unit][Hr][W], row r at y = r - Py
+    int Hr, Py;
+    int row_nsc;           // super-chunks of the longest extended row (512 samples each)
+    int col_nsc;           // super-chunks of the longest extended column (128 rows each)
+    float *col_scratch;    // the column kernel's forward start states, gabor_iir_col_scratch_floats
+                           // (col_nsc) floats per column CTA
 };
-
 // Arguments of the FP32 localized-SDFT kernel (Algorithm 2).
 struct SdftArgs {
     const float *img;
@@ -315,7 +324,10 @@ int gabor_tc_row_tile_y(int Rmax);
 int gabor_tc_col_tile_y();
 // Recursive-Gaussian bank (gabor_iir.cu).
 cudaError_t gabor_iir_prepare();
-cudaError_t launch_gabor_iir(const IirArgs &a, int nunits, cudaStream_t st);
+bool gabor_iir_fits(int row_nsc, int col_nsc);   // the kernels' shared memory fits
+size_t gabor_iir_col_scratch_floats(int col_nsc);
+int gabor_iir_col_ctas(int W, int nunits);
+cudaError_t launch_gabor_iir(const IirArgs &a, cudaStream_t st);
 // FP32 FMA throughput probe (peak.cu).
 cudaError_t launch_fma_peak(float *out, int blocks, int iters, int packed, cudaStream_t st);
 // Bounded-wait self-test (selftest.cu).
