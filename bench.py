@@ -359,11 +359,20 @@ def sdft_leg(torch, steps, warmup, flush, stream):
     peak, kind = hbm_peak_gbs()
     res = {"workload": "512x512 1/f noise (seed 0), 16x16 window, sigma 4, 256 bins, complex64 out",
            "outputs_per_step": n_out}
-    # plain write bandwidth of the same output volume (torch fill kernel), for context
+    # write bandwidth of the same output volume, for context: a zero fill (torch; faster than
+    # the memory's raw rate through zero compression) and the library's store probe (the
+    # tensor-core SDFT's own store pattern and CTA shape, non-zero values, no arithmetic): the
+    # ceiling of that pattern
+    from paper_1704_05231_gb300.bank import store_probe
     fill = torch.empty((16, 16, Hs, Ws), dtype=torch.complex64, device="cuda")
     fms = statistics.mean(time_device(torch, lambda: fill.zero_(), steps, warmup, flush, stream))
-    res["fill_same_bytes"] = {"ms": fms, "GB/s": n_out * 8 / (fms * 1e-3) / 1e9}
-    del fill
+    res["fill_same_bytes"] = {"ms": fms, "GB/s": n_out * 8 / (fms * 1e-3) / 1e9, "values": "zeros"}
+    pv = fill.view(256, Hs, Ws)
+    pms = statistics.mean(time_device(torch, lambda: store_probe(pv), steps, warmup, flush, stream))
+    res["store_pattern"] = {"ms": pms, "GB/s": n_out * 8 / (pms * 1e-3) / 1e9,
+                            "frac_of_peak": n_out * 8 / (pms * 1e-3) / 1e9 / peak,
+                            "note": "the TC SDFT's output stream alone: 16 storing warps, one CTA per SM, non-zero values"}
+    del fill, pv
     ref = None
     for prec in ("fp32", "fp16_tc", "bf16_tc"):
         gbk = GaborBank(precision=prec)
@@ -378,6 +387,7 @@ def sdft_leg(torch, steps, warmup, flush, stream):
             ref = out.clone()
         else:
             ent["rel_err_vs_fp32"] = float((out - ref).abs().max() / ref.abs().max())
+            ent["frac_of_store_pattern"] = pms / ms
         res[prec] = ent
         gbk.close()
         del out
@@ -589,7 +599,11 @@ def leg_summary(line):
         if "reuse" in sd:
             out["sdft_reuse_speedup"] = _r(sd["reuse"]["speedup_from_reuse"], 3)
         if "fill_same_bytes" in sd:
-            out["sdft_fill_gbs"] = _r(sd["fill_same_bytes"]["GB/s"])
+            out["sdft_zero_fill_gbs"] = _r(sd["fill_same_bytes"]["GB/s"])
+        if "store_pattern" in sd:
+            out["sdft_store_pattern_gbs"] = _r(sd["store_pattern"]["GB/s"])
+            if "fp16_tc" in sd:
+                out["sdft512_m16_fp16_tc"]["frac_of_store_pattern"] = _r(sd["fp16_tc"]["frac_of_store_pattern"], 3)
     ab = line.get("ablation")
     if ab:
         out["bank_reuse_speedup"] = {p: _r(e["speedup_from_reuse"], 3) for p, e in ab.items()}

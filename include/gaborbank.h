@@ -280,6 +280,18 @@ gb_status gabor_bank_device_status(gabor_bank_t h, void *stream);
 gb_status gabor_fp32_fma_probe(void *d_out, int blocks, int iters, int packed, void *stream);
 
 /*
+ * gabor_store_probe - store-bandwidth probe for the tensor-core SDFT's output pattern (the
+ * paper has no counterpart).  Writes nplanes x H x W complex64 values to d_out (plane-major,
+ * the SDFT's output layout, caller-owned device memory of 8 * nplanes * H * W bytes) the way
+ * that kernel's epilogue does, without its arithmetic: `ctas` CTAs of 16 warps, tiles of 128
+ * pixels of one row, a warp storing 32 consecutive pixels of one plane per instruction.  The
+ * values are non-zero (a zero fill runs faster through the memory's zero compression).  Time
+ * it with CUDA events.  Asynchronous.  GB_ERR_INVALID_ARG on NULL or non-positive arguments or
+ * W not a multiple of 128.
+ */
+gb_status gabor_store_probe(void *d_out, int64_t nplanes, int H, int W, int ctas, void *stream);
+
+/*
  * gabor_bank_selftest_wait - failure-detection self-test of the bounded device waits.  Enqueues
  * a one-warp kernel whose thread 0 waits on a shared-memory mbarrier with the same bounded
  * wait the tensor-core kernels use.  signal = 1: the barrier is signalled first and the wait

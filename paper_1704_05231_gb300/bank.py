@@ -48,6 +48,7 @@ SIGNATURES = {
     "gabor_sdft_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_i64, _c_dbl, _c_int, _c_int, _c_int, _vp, _vp]),
     "gabor_bank_selftest_wait": (_c_int, [_vp, _c_int, _c_dbl, _vp]),
     "gabor_fp32_fma_probe": (_c_int, [_vp, _c_int, _c_int, _c_int, _vp]),
+    "gabor_store_probe": (_c_int, [_vp, ctypes.c_int64, _c_int, _c_int, _c_int, _vp]),
     "gabor_bank_workspace_bytes": (_c_i64, [_vp, _c_int, _c_int]),
     "gabor_bank_set_workspace": (_c_int, [_vp, _vp, _c_i64]),
     "gabor_arena_create": (_c_int, [ctypes.POINTER(_vp), _c_i64]),
@@ -321,6 +322,18 @@ class Arena:
             self.close()
         except Exception:
             pass
+
+
+def store_probe(out, ctas=None, stream=None):
+    """Enqueue the library's store-pattern probe on `out` (a contiguous complex64 CUDA tensor of
+    shape (nplanes, H, W), W a multiple of 128): the tensor-core SDFT's output stream without
+    its arithmetic, `ctas` CTAs of 16 warps (default: one per SM)."""
+    import torch
+    lib = load_library()
+    nplanes, H, W = out.shape
+    if ctas is None:
+        ctas = torch.cuda.get_device_properties(out.device).multi_processor_count
+    _check(lib.gabor_store_probe(ctypes.c_void_p(out.data_ptr()), nplanes, H, W, ctas, _stream_handle(stream)))
 
 
 def fp32_fma_peak(iters=4096, waves=8, steps=5):

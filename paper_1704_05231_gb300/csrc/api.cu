@@ -1602,6 +1602,17 @@ gb_status gabor_fp32_fma_probe(void *d_out, int blocks, int iters, int packed, v
     return GB_OK;
 }
 
+gb_status gabor_store_probe(void *d_out, int64_t nplanes, int H, int W, int ctas, void *stream)
+{
+    if (!d_out || nplanes <= 0 || H <= 0 || W <= 0 || W % 128 != 0 || ctas <= 0)
+        return fail(GB_ERR_INVALID_ARG, "bad probe arguments (W must be a positive multiple of 128)");
+    if ((int64_t)H * W > (int64_t)1 << 40 || nplanes > ((int64_t)1 << 40) / ((int64_t)H * W))
+        return fail(GB_ERR_INVALID_ARG, "probe output too large");
+    GB_TRY(check_sticky());
+    GB_CU(launch_store_pattern(static_cast<float2 *>(d_out), nplanes, H, W, ctas, static_cast<cudaStream_t>(stream)));
+    return GB_OK;
+}
+
 gb_status gabor_bank_selftest_wait(gabor_bank_t h, int signal, double limit_ms, void *stream)
 {
     if (!h) return fail(GB_ERR_INVALID_ARG, "NULL handle");

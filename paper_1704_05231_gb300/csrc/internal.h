@@ -330,6 +330,7 @@ int gabor_iir_col_ctas(int W, int nunits);
 cudaError_t launch_gabor_iir(const IirArgs &a, cudaStream_t st);
 // FP32 FMA throughput probe (peak.cu).
 cudaError_t launch_fma_peak(float *out, int blocks, int iters, int packed, cudaStream_t st);
+cudaError_t launch_store_pattern(float2 *out, int64_t nplanes, int H, int W, int ctas, cudaStream_t st);
 // Bounded-wait self-test (selftest.cu).
 cudaError_t launch_wait_selftest(int *status, int signal, unsigned long long limit_ns, cudaStream_t st);
 // Sets the message returned by gabor_bank_last_error() on the calling host thread.

@@ -225,3 +225,21 @@ def test_sdft_no_reuse_c3_full_oracle(torch_cuda, c3_full):
         gbk.set_option("sdft_reuse", 0)
         got = gbk.sdft(torch_cuda.from_numpy(img).cuda(), 4.0, 16).cpu().numpy()
     assert rel_err(got, ref) <= FP32_TOL
+
+
+def test_store_probe_writes_every_output(torch_cuda):
+    # The store-pattern probe (the tensor-core SDFT's output stream without arithmetic) writes
+    # every element of its plane-major output exactly: out[p][y][x] = (p + 1, x + 1).
+    import torch
+    from paper_1704_05231_gb300 import GBError
+    from paper_1704_05231_gb300.bank import store_probe
+    nplanes, H, W = 19, 37, 256
+    out = torch.full((nplanes, H, W), float("nan"), dtype=torch.complex64, device="cuda")
+    store_probe(out, ctas=5)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    want = (np.arange(1, nplanes + 1, dtype=np.float32)[:, None, None]
+            + 1j * np.arange(1, W + 1, dtype=np.float32)[None, None, :]) * np.ones((1, H, 1), np.float32)
+    assert np.array_equal(got, want.astype(np.complex64))
+    with pytest.raises(GBError):
+        store_probe(torch.empty((2, 4, 100), dtype=torch.complex64, device="cuda"))
