@@ -372,6 +372,9 @@ def sdft_leg(torch, steps, warmup, flush, stream):
     res["store_pattern"] = {"ms": pms, "GB/s": n_out * 8 / (pms * 1e-3) / 1e9,
                             "frac_of_peak": n_out * 8 / (pms * 1e-3) / 1e9 / peak,
                             "note": "the TC SDFT's output stream alone: 16 storing warps, one CTA per SM, non-zero values"}
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    p2 = statistics.mean(time_device(torch, lambda: store_probe(pv, ctas=2 * nsm), steps, warmup, flush, stream))
+    res["store_pattern"]["two_ctas_per_sm_GB/s"] = n_out * 8 / (p2 * 1e-3) / 1e9
     del fill, pv
     ref = None
     for prec in ("fp32", "fp16_tc", "bf16_tc"):
