@@ -618,7 +618,7 @@ __device__ __forceinline__ RowItem row_item_mt(const TcBankArgs &a, const TcDesc
 
 // SPLIT: BF16 operands as hi + lo pairs (a.split); FP16 operands otherwise.
 template <bool SPLIT>
-__global__ void __launch_bounds__(512, 1) k_gabor_tc_rows_mt(const __grid_constant__ TcBankArgs a)
+__global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_constant__ TcBankArgs a)
 {
     const int nitems = a.row_list ? a.n_row : a.nf * a.row_cnt;
     extern __shared__ unsigned char smem_dyn[];
@@ -1779,6 +1779,11 @@ cudaError_t gabor_tc_prepare()
     return e;
 }
 
+// Modulated-tap row-pass CTAs per SM: two when their shared memory fits (64 registers per
+// thread, 128 TMEM columns each), so that one CTA's patch staging overlaps the other's MMAs and
+// epilogue.
+static int mt_rows_per_sm(size_t smem) { return 2 * (smem + 1024) <= (size_t)228 * 1024 ? 2 : 1; }
+
 cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
 {
     TcBankArgs a = a0;
@@ -1810,7 +1815,7 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
         cudaError_t e;
         if (a.row_mt) {
             e = launch_pdl(a.split ? k_gabor_tc_rows_mt<true> : k_gabor_tc_rows_mt<false>,
-                           dim3(std::min(n_row_items, sm_count)), dim3(512), smem_r, st, a);
+                           dim3(std::min(n_row_items, sm_count * mt_rows_per_sm(smem_r))), dim3(512), smem_r, st, a);
         } else {
             k_gabor_tc_rows<<<std::min(n_row_items, sm_count), 512, smem_r, st>>>(a);
             e = cudaGetLastError();
@@ -1844,8 +1849,8 @@ cudaError_t launch_gabor_tc_batch(const TcBankArgs &a0, int sm_count, cudaStream
     e = launch_pdl(k_ones_batch, dim3(16, a.nimg), dim3(256), 0, st, a, a.units, a.freqs, a.nf * a.nu_f);
     if (e != cudaSuccess) return e;
     if (a.n_row > 0) {
-        e = launch_pdl(a.split ? k_gabor_tc_rows_mt<true> : k_gabor_tc_rows_mt<false>, dim3(std::min(a.n_row, sm_count)),
-                       dim3(512), smem_r, st, a);
+        e = launch_pdl(a.split ? k_gabor_tc_rows_mt<true> : k_gabor_tc_rows_mt<false>,
+                       dim3(std::min(a.n_row, sm_count * mt_rows_per_sm(smem_r))), dim3(512), smem_r, st, a);
         if (e != cudaSuccess) return e;
     }
     if (a.n_col > 0)
