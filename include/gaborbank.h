@@ -264,8 +264,10 @@ gb_status gabor_bank_set_tiling(gabor_bank_t h, int s, int tile_rows, int segmen
 
 /*
  * gabor_bank_device_status - wait for `stream`, then read and clear the handle's device
- * error word: GB_OK, or GB_ERR_TIMEOUT if a bounded device wait (tensor-core pipeline
- * barriers) gave up since the last read.  Synchronous.
+ * error word: GB_OK; GB_ERR_TIMEOUT if a bounded device wait (tensor-core pipeline barriers)
+ * gave up since the last read; GB_ERR_UNSUPPORTED if a GB_FP16_TC bank met an image whose
+ * centre level c = (min + max) / 2 is beyond its FP16 operands' range (|c| above about 2^24;
+ * GB_BF16_TC has no such limit), whose results are then wrong.  Synchronous.
  */
 gb_status gabor_bank_device_status(gabor_bank_t h, void *stream);
 
@@ -329,8 +331,10 @@ gb_status gabor_sdft_noalloc(const float *d_img, int H, int W, int64_t pitch, do
  * default Re J and Im J of every horizontal pass, Eq. 5-6; under GB_OPT_ROW_PASS = 1 the
  * column signals of Eq. 10), each image column padded by zero rows above and below, followed
  * by the bank's response to a constant image, one row and one column table per horizontal
- * pass.  Sized for the larger of the two forms.  0 for FP32 handles (their intermediates stay
- * on chip) and for invalid arguments.  Host-only; no device work.
+ * pass, and the operands that add it back in the column pass's matrix products (4 KB per 64
+ * image columns and per 32 image rows of every horizontal pass).  Sized for the larger of the
+ * two forms.  0 for FP32 handles (their intermediates stay on chip) and for invalid
+ * arguments.  Host-only; no device work.
  */
 int64_t gabor_bank_workspace_bytes(gabor_bank_t h, int H, int W);
 

@@ -501,21 +501,33 @@ int tc_col_ty(const gabor_bank *h)
 
 // Elements of the intermediate for an H x W image: every column signal of every unit, one
 // column of Hp = round64(H) + 2 Lpad rows per image column.
+int tc_wq(int W) { return (W + 15) / 16 * 16; }
 int64_t tc_sig_elems(const gabor_bank *h, int H, int W)
 {
     const int64_t Hp = (int64_t)(H + 63) / 64 * 64 + 2 * tc_lpad(h);
     int64_t nsig = 0;
     for (const Unit &u : h->units) nsig += u.k_b >= 0 ? 4 : 2;
-    // modulated taps: Re J, Im J per unit, as hi and lo under BF16
-    nsig = std::max<int64_t>(nsig, (int64_t)(h->prec == GB_BF16_TC ? 4 : 2) * (int64_t)h->units.size());
-    return nsig * W * Hp;
+    // modulated taps: a plane of Re J, Im J per unit (two, hi and lo, under BF16), Wq columns
+    const int64_t mt = (int64_t)(h->prec == GB_BF16_TC ? 2 : 1) * (int64_t)h->units.size() * 2 * tc_wq(W) * Hp;
+    return std::max(nsig * W * Hp, mt);
 }
 
 // Workspace bytes of a tensor-core call: the intermediate signals, then the F[1] tables A, B.
 int64_t tc_sig_bytes(const gabor_bank *h, int H, int W) { return (tc_sig_elems(h, H, W) * 2 + 255) / 256 * 256; }
+// F[1] tables: A(x), B(y) of every unit (float2), 256-byte aligned
+int64_t tc_ones_bytes(const gabor_bank *h, int H, int W)
+{
+    return ((int64_t)h->units.size() * ((int64_t)W + H) * (int64_t)sizeof(float2) + 255) / 256 * 256;
+}
+// the column pass's correction operands: per unit one block per 64 columns and per 32 rows
+// (enough for either column-job height)
+int64_t tc_corr_bytes(const gabor_bank *h, int H, int W)
+{
+    return (int64_t)h->units.size() * (((int64_t)W + 63) / 64 + ((int64_t)H + 31) / 32) * kCorrBlockHalfs * 2;
+}
 int64_t tc_ws_bytes(const gabor_bank *h, int H, int W)
 {
-    return tc_sig_bytes(h, H, W) + (int64_t)h->units.size() * ((int64_t)W + H) * (int64_t)sizeof(float2);
+    return tc_sig_bytes(h, H, W) + tc_ones_bytes(h, H, W) + tc_corr_bytes(h, H, W);
 }
 
 gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
@@ -632,12 +644,13 @@ gb_status encode_tc_maps(TcBankArgs &a, int nsig, bool mt)
     const cuuint32_t elem[4] = {1, 1, 1, 1};
     const cuuint32_t boxes[2][4] = {{8, 32, 4, 8}, {8, 64, 2, 8}};
     if (mt) {
-        // modulated taps: Re J, Im J of a unit are signals 2 u, 2 u + 1; a box of 8 rows x the
-        // two parts x 64 columns x 8 blocks lands with operand row n = 2 x + part
-        const cuuint64_t mdims[4] = {8, (cuuint64_t)nsig, (cuuint64_t)a.W, (cuuint64_t)(a.Hp / 8)};
-        const cuuint64_t mstrides[3] = {(cuuint64_t)a.Hp * a.W * 2, 16, (cuuint64_t)a.W * 16};
-        const cuuint32_t mbox[4] = {8, 2, 64, 8};
-        const CUresult r = enc(&a.tmA[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, a.sig, mdims, mstrides, mbox, elem,
+        // modulated taps: nsig planes of [Hp / 8][Wq][part][8]; a box of 256 elements (16
+        // columns x both parts x 8 rows, 512 contiguous bytes) x 4 column groups x 8 blocks lands
+        // with operand row n = 2 x + part, K-group b 2048 bytes apart
+        const cuuint64_t mdims[3] = {256, (cuuint64_t)(a.Wq / 16), (cuuint64_t)(a.Hp / 8) * nsig};
+        const cuuint64_t mstrides[2] = {512, (cuuint64_t)a.Wq * 32};
+        const cuuint32_t mbox[3] = {256, 4, 8};
+        const CUresult r = enc(&a.tmA[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, a.sig, mdims, mstrides, mbox, elem,
                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(GB_ERR_CUDA, "cuTensorMapEncodeTiled failed for the intermediate");
@@ -704,24 +717,29 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
             h->tcsig_elems = (size_t)need;
         }
         sig = h->d_tcsig;
-        zero_halo = h->tc_H != H || h->tc_W != W;
+        zero_halo = h->tc_H != H || h->tc_W != W || h->tc_zero_mt != (row_mt ? 1 : 0);
     } else if ((size_t)need_bytes > h->ws_bytes) {
         return fail(GB_ERR_BUDGET, "workspace too small: this image needs " + std::to_string(need_bytes) + " bytes");
     }
     float2 *onesA = reinterpret_cast<float2 *>(reinterpret_cast<char *>(sig) + tc_sig_bytes(h, H, W));
     float2 *onesB = onesA + (int64_t)h->units.size() * W;
+    uint16_t *corrA = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(onesA) + tc_ones_bytes(h, H, W));
+    uint16_t *corrB = corrA + (int64_t)h->units.size() * ((W + 63) / 64) * kCorrBlockHalfs;
     if (zero_halo && need > 0) {
         // Layout [signal][Hp / 8][W][8].  The row pass writes rows [Lpad, Lpad + round_up(H, TY))
         // of every signal (zeros below row H); the column pass reads up to R8 rows beyond, so
         // the blocks of rows [0, Lpad) and [Lpad + round_up(H, 8), Hp) must be zero.
         // every signal either form uses (the modulated-tap form: 2 per unit, 4 as BF16 hi + lo)
-        const size_t sig_bytes = (size_t)Hp * W * 2, blk = (size_t)W * 16;
+        // (modulated taps: planes of Wq columns x both parts per 8-row block)
         const int64_t back = (Lpad + ((int64_t)H + 7) / 8 * 8) / 8;
-        const size_t nsig_z = (size_t)std::max(h->tc_nsig, (split ? 4 : 2) * (int)h->units.size());
+        const size_t sig_bytes = row_mt ? (size_t)Hp * tc_wq(W) * 4 : (size_t)Hp * W * 2;
+        const size_t blk = row_mt ? (size_t)tc_wq(W) * 32 : (size_t)W * 16;
+        const size_t nsig_z = row_mt ? (size_t)(split ? 2 : 1) * h->units.size() : (size_t)h->tc_nsig;
         GB_CU(cudaMemset2DAsync(sig, sig_bytes, 0, (size_t)(Lpad / 8) * blk, nsig_z, st));
         GB_CU(cudaMemset2DAsync(reinterpret_cast<char *>(sig) + back * blk, sig_bytes, 0,
                                 (size_t)(Hp / 8 - back) * blk, nsig_z, st));
     }
+    h->tc_zero_mt = row_mt ? 1 : 0;
     h->tc_H = h->ws_ptr ? 0 : H;
     h->tc_W = h->ws_ptr ? 0 : W;
     TcBankArgs a{};
@@ -734,6 +752,7 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.sig = sig;
     a.Hp = Hp;
     a.Lpad = Lpad;
+    a.Wq = tc_wq(W);
     a.freqs = h->d_tcfreq;
     a.units = h->d_tcunit;
     a.status = h->d_status;
@@ -744,6 +763,8 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.minmax = h->d_tcminmax;
     a.onesA = onesA;
     a.onesB = onesB;
+    a.corrA = corrA;
+    a.corrB = corrB;
     a.ones_pre = h->d_tcpre;
     a.ones_stride = h->tc_pre_stride;
     a.row_ty = ty;
@@ -763,7 +784,7 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.nplanes = (int)(h->omega.size() * h->theta.size());
     a.row_y0 = -ypad;
     a.split = split;
-    GB_TRY(encode_tc_maps(a, split ? 4 * (int)h->units.size() : h->tc_nsig, row_mt));
+    GB_TRY(encode_tc_maps(a, row_mt ? (split ? 2 : 1) * (int)h->units.size() : h->tc_nsig, row_mt));
     GB_CU(launch_gabor_tc(a, h->sm_count, st));
     return GB_OK;
 }
@@ -795,19 +816,23 @@ gb_status filter_batch_tc(gabor_bank *h, int n, const float *const *d_imgs, cons
     for (const Freq &f : h->freqs) rmax = std::max(rmax, f.R);
     const int ypad = h->boundary == kBoundaryZero ? 0 : (rmax + ty - 1) / ty * ty;
     const int Lpad = tc_lpad(h);
-    const int nsig = (split ? 4 : 2) * nu;   // Re J, Im J of every unit (hi and lo under BF16)
+    const int nplane = (split ? 2 : 1) * nu;   // a plane of Re J, Im J per unit (hi and lo under BF16)
     // workspace: intermediates, F[1] tables, partial keys, centres (each 256-byte aligned)
     auto al = [](int64_t b) { return (b + 255) / 256 * 256; };
-    std::vector<int64_t> off_sig(n), off_ones(n), Hp(n);
+    std::vector<int64_t> off_sig(n), off_ones(n), off_corr(n), Hp(n);
     int64_t total = 0;
     for (int i = 0; i < n; ++i) {
         Hp[i] = (int64_t)(H[i] + 63) / 64 * 64 + 2 * Lpad;
         off_sig[i] = total;
-        total += al((int64_t)nsig * W[i] * Hp[i] * 2);
+        total += al((int64_t)nplane * tc_wq(W[i]) * Hp[i] * 4);
     }
     for (int i = 0; i < n; ++i) {
         off_ones[i] = total;
         total += al((int64_t)nu * ((int64_t)W[i] + H[i]) * (int64_t)sizeof(float2));
+    }
+    for (int i = 0; i < n; ++i) {
+        off_corr[i] = total;
+        total += al((int64_t)nu * (((int64_t)W[i] + 63) / 64 + ((int64_t)H[i] + 31) / 32) * kCorrBlockHalfs * 2);
     }
     const int64_t off_parts = total;
     total += al((int64_t)n * kMmParts * 2 * sizeof(unsigned));
@@ -860,12 +885,15 @@ gb_status filter_batch_tc(gabor_bank *h, int n, const float *const *d_imgs, cons
             d.Hp = Hp[i];
             d.onesA = reinterpret_cast<const float2 *>(ws + off_ones[i]);
             d.onesB = d.onesA + (int64_t)nu * W[i];
-            // the intermediate as 8 rows of a block x signals x W x Hp / 8 blocks (FP16); boxes of
-            // 8 rows x the two parts x 64 columns x 8 blocks, as in the single-image call
-            const cuuint64_t dims[4] = {8, (cuuint64_t)nsig, (cuuint64_t)W[i], (cuuint64_t)(Hp[i] / 8)};
-            const cuuint64_t strides[3] = {(cuuint64_t)Hp[i] * W[i] * 2, 16, (cuuint64_t)W[i] * 16};
-            const cuuint32_t box[4] = {8, 2, 64, 8}, elem[4] = {1, 1, 1, 1};
-            const CUresult r = enc(&maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, d.sig, dims, strides, box, elem,
+            d.corrA = reinterpret_cast<uint16_t *>(ws + off_corr[i]);
+            d.corrB = d.corrA + (int64_t)nu * ((W[i] + 63) / 64) * kCorrBlockHalfs;
+            // the intermediate's planes as in the single-image call: boxes of 256 elements (16
+            // columns x both parts x 8 rows) x 4 column groups x 8 blocks
+            d.Wq = tc_wq(W[i]);
+            const cuuint64_t dims[3] = {256, (cuuint64_t)(d.Wq / 16), (cuuint64_t)(Hp[i] / 8) * nplane};
+            const cuuint64_t strides[2] = {512, (cuuint64_t)d.Wq * 32};
+            const cuuint32_t box[3] = {256, 4, 8}, elem[3] = {1, 1, 1};
+            const CUresult r = enc(&maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, d.sig, dims, strides, box, elem,
                                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) return fail(GB_ERR_CUDA, "cuTensorMapEncodeTiled failed for a batch intermediate");
@@ -1589,6 +1617,9 @@ gb_status gabor_bank_device_status(gabor_bank_t h, void *stream)
     int v = 0;
     GB_CU(cudaMemcpy(&v, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     GB_CU(cudaMemset(h->d_status, 0, sizeof(int)));
+    if (v == 60)
+        return fail(GB_ERR_UNSUPPORTED, "an image's centre level |c| exceeds the FP16 tensor-core bank's range "
+                                        "(|c| 2^sB >= 2^29, sB the column operand's scale exponent); use GB_BF16_TC");
     if (v != 0) return fail(GB_ERR_TIMEOUT, "a bounded device wait gave up (code " + std::to_string(v) + ")");
     return GB_OK;
 }

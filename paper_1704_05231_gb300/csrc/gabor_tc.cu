@@ -190,15 +190,19 @@ struct TcImgView {
     uint16_t *sig;
     int64_t Hp;
     const float2 *onesA, *onesB;
+    const uint16_t *corrA, *corrB;
     const CUtensorMap *tm;
+    int Wq;
 };
 __device__ __forceinline__ TcImgView tc_img(const TcBankArgs &a, int i)
 {
     if (a.imgs) {
         const TcImgDev d = a.imgs[i];
-        return TcImgView{d.img, d.pitch, d.H, d.W, d.out, d.plane, d.sig, d.Hp, d.onesA, d.onesB, a.tmaps + i};
+        return TcImgView{d.img, d.pitch, d.H, d.W, d.out, d.plane, d.sig, d.Hp, d.onesA, d.onesB, d.corrA, d.corrB,
+                         a.tmaps + i, d.Wq};
     }
-    return TcImgView{a.img, a.pitch, a.H, a.W, a.out, a.plane, a.sig, a.Hp, a.onesA, a.onesB, &a.tmA[0]};
+    return TcImgView{a.img, a.pitch, a.H, a.W, a.out, a.plane, a.sig, a.Hp, a.onesA, a.onesB, a.corrA, a.corrB,
+                     &a.tmA[0], a.Wq};
 }
 __device__ __forceinline__ int64_t tc_out_offset(const TcBankArgs &a, const TcImgView &im, int p, int y, int x)
 {
@@ -590,14 +594,15 @@ __device__ __forceinline__ uint64_t tstrip_desc(uint32_t s0, int ks) { return sm
 struct MtSmem {
     uint32_t a_off, p_off, patch_off, desc_off, bar_off, misc_off, total;
 };
+constexpr int kAmBufs = 2;   // Am strip buffers of the modulated-tap row kernel
 
 // split = 1 (BF16 operands as hi + lo pairs): two strips per A buffer and P as hi and lo.
 __host__ __device__ inline MtSmem mt_smem(int K, int PW, int TY, int split = 0)
 {
     MtSmem L;
     const uint32_t np = split ? 2u : 1u;
-    L.a_off = 0;                                              // [2] buffers of np strips of 128 rows x K
-    L.p_off = (L.a_off + 2u * np * tstrip_bytes(K, 128) + 1023) & ~1023u;   // np x TY x K (SW128)
+    L.a_off = 0;                                              // [kAmBufs] buffers of np strips of 128 rows x K
+    L.p_off = (L.a_off + kAmBufs * np * tstrip_bytes(K, 128) + 1023) & ~1023u;   // np x TY x K (SW128)
     L.patch_off = L.p_off + np * (uint32_t)TY * K * 2;        // TY x PWs FP32
     L.desc_off = (L.patch_off + (uint32_t)TY * (round_up(PW, 8) + 4) * 4 + 127) & ~127u;
     L.bar_off = L.desc_off + kDescBytes;
@@ -632,11 +637,11 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.bar_off);
     uint64_t *tmem_full = bars;        // [2] commit
     uint64_t *tmem_empty = bars + 2;   // [2] epilogue warps
-    uint64_t *a_full = bars + 4;       // [2] Am landed (bulk copy)
-    uint64_t *a_empty = bars + 6;      // [2] commit: the MMA reading the buffer is done
-    uint64_t *p_empty = bars + 8;      // [1] commit: the item's MMAs (reading P) are done
-    uint64_t *drain = bars + 9;
-    uint64_t *p_full = bars + 10;      // [1] the producers built the item's P
+    uint64_t *a_full = bars + 4;       // [kAmBufs] Am landed (bulk copy)
+    uint64_t *a_empty = bars + 4 + kAmBufs;   // [kAmBufs] commit: the MMA reading the buffer is done
+    uint64_t *p_empty = bars + 4 + 2 * kAmBufs;   // [1] commit: the item's MMAs (reading P) are done
+    uint64_t *drain = bars + 5 + 2 * kAmBufs;
+    uint64_t *p_full = bars + 6 + 2 * kAmBufs;    // [1] the producers built the item's P
     uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
     const TcDesc D = load_desc(a, sm + L.desc_off);
@@ -648,6 +653,8 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
         for (int i = 0; i < 2; ++i) {
             mbar_init(&tmem_full[i], 1);
             mbar_init(&tmem_empty[i], kMtEpiWarps);
+        }
+        for (int i = 0; i < kAmBufs; ++i) {
             mbar_init(&a_full[i], 1);
             mbar_init(&a_empty[i], 1);
         }
@@ -674,8 +681,9 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
     if (warp == 15) {
         // -------------------------------------------------------------- MMA warp (lane 0)
         // Runs ahead of the producers: the Am copy of job jq (unit q of the CTA's item jq / nu)
-        // goes into buffer jq & 1 as soon as the MMA of job jq - 2 has released it, across
-        // item boundaries; the MMAs of an item wait for its P (p_full) and release it (p_empty).
+        // goes into buffer jq % kAmBufs as soon as the MMA of job jq - kAmBufs has released it,
+        // across item boundaries; the MMAs of an item wait for its P (p_full) and release it
+        // (p_empty).
         if (lane == 0) {
             const int nu = a.nu_f;
             const int my_items = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -683,8 +691,8 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
             int issued = 0, landed = 0;
             bool ok = true;
             auto issue_a = [&]() {   // the Am copy of job `issued`
-                const int jq = issued, buf = jq & 1;
-                if (jq >= 2 && !mbar_wait(&a_empty[buf], ((jq - 2) >> 1) & 1, abort_s)) return false;
+                const int jq = issued, buf = jq % kAmBufs;
+                if (jq >= kAmBufs && !mbar_wait(&a_empty[buf], ((jq - kAmBufs) / kAmBufs) & 1, abort_s)) return false;
                 const RowItem w = row_item_mt(a, D, blockIdx.x + (jq / nu) * gridDim.x);
                 const TcFreqDev f = D.freqs[w.s];
                 const uint32_t abytes = np * tstrip_bytes(f.Kmt, 128);
@@ -699,13 +707,13 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
                 while (ok && issued < njobs && issued < nitem * nu + 2) ok = issue_a();
                 if (ok) ok = mbar_wait(p_full, nitem & 1, abort_s);   // this item's P
                 for (int q = 0; q < nu && ok; ++q) {
-                    const int jq = nitem * nu + q, b = jq & 1;
-                    ok = mbar_wait(&a_full[b], (jq >> 1) & 1, abort_s);
+                    const int jq = nitem * nu + q, b = jq & 1, ab = jq % kAmBufs;
+                    ok = mbar_wait(&a_full[ab], (jq / kAmBufs) & 1, abort_s);
                     if (ok) landed = jq + 1;   // copy jq (copies go in job order)
                     if (ok && jq >= 2) ok = mbar_wait(&tmem_empty[b], ((jq - 2) >> 1) & 1, abort_s);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(sA + b * abuf), p0 = smem_u32(sP);
+                    const uint32_t a0 = smem_u32(sA + ab * abuf), p0 = smem_u32(sP);
                     const uint32_t a0l = a0 + tstrip_bytes(K, 128);
                     for (int kb = 0; kb < K / 64; ++kb)
 #pragma unroll
@@ -719,7 +727,7 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
                             }
                         }
                     tc_commit(&tmem_full[b]);
-                    tc_commit(&a_empty[b]);
+                    tc_commit(&a_empty[ab]);
                     // the next copies (this item's later units, or the next item's first ones)
                     while (ok && issued < njobs && issued < jq + 3) ok = issue_a();
                 }
@@ -732,10 +740,10 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
                 mbar_wait(drain, 0, &dummy);
             }
             // bulk copies issued but not waited for (after a stop) land before shared memory is
-            // released; copy i went to buffer i & 1 as its (i >> 1)-th use
+            // released; copy i went to buffer i % kAmBufs as its (i / kAmBufs)-th use
             for (int i = landed; i < issued; ++i) {
                 volatile int dummy = 0;
-                mbar_wait(&a_full[i & 1], (i >> 1) & 1, &dummy);
+                mbar_wait(&a_full[i % kAmBufs], (i / kAmBufs) & 1, &dummy);
             }
         }
     } else if (warp >= kMtEpiWarps) {
@@ -865,12 +873,11 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
                     break;
                 }
                 tc_fence_after();
-                const int64_t sstride = (int64_t)im.W * im.Hp;   // between signals
-                const int64_t bstride = (int64_t)im.W * 8;       // between 8-row blocks
-                // signals of the unit: (Re J, Im J), or under split (Re hi, Im hi, Re lo, Im lo)
-                const int64_t sig0 = (int64_t)(2 * np) * (u0 + q) + part;
-                uint16_t *dst0 = im.sig + sig0 * sstride + (int64_t)((a.Lpad + y0) >> 3) * bstride +
-                                 (int64_t)(xin ? gx : 0) * 8;
+                const int64_t pstride = (int64_t)im.Wq * 2 * im.Hp;   // between planes
+                const int64_t bstride = (int64_t)im.Wq * 16;          // between 8-row blocks
+                // the unit's plane (and the next one, lo, under split); Re J, Im J interleaved
+                uint16_t *dst0 = im.sig + (int64_t)np * (u0 + q) * pstride + (int64_t)((a.Lpad + y0) >> 3) * bstride +
+                                 (int64_t)(xin ? gx : 0) * 16 + part * 8;
 #pragma unroll 1
                 for (int c0 = rbase; c0 < rbase + rpw; c0 += 16) {
                     float v[16];
@@ -890,7 +897,7 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
                             const int64_t o = (int64_t)((c0 + 8 * blk) >> 3) * bstride;
                             *reinterpret_cast<uint4 *>(dst0 + o) = make_uint4(pk[blk][0], pk[blk][1], pk[blk][2], pk[blk][3]);
                             if constexpr (SPLIT)
-                                *reinterpret_cast<uint4 *>(dst0 + 2 * sstride + o) =
+                                *reinterpret_cast<uint4 *>(dst0 + pstride + o) =
                                     make_uint4(pl[blk][0], pl[blk][1], pl[blk][2], pl[blk][3]);
                         }
                     }
@@ -955,10 +962,11 @@ __global__ void k_build_tstrip(uint16_t *__restrict__ Q, int ncores, int off, in
 // and store complex64.
 constexpr int kMtColAcc = 2;       // TMEM accumulators (128 columns each)
 constexpr int kMtColEpiWarps = 16;
+constexpr int kMtColMaxStages = 2;   // operand stages of the modulated-tap column kernel
 constexpr int kMtColThreads = 32 * (kMtColEpiWarps + 1);
 
 struct MtColSmem {
-    uint32_t a_off, b_off, desc_off, bar_off, misc_off, total;
+    uint32_t a_off, b_off, c_off, desc_off, bar_off, misc_off, total;
 };
 
 // TYC: output rows per job (64; 32 when the operands of 64 do not fit); the B operand is the
@@ -969,7 +977,8 @@ __host__ __device__ inline MtColSmem mt_col_smem(int K, int TYC, int split = 0, 
     const uint32_t np = split ? 2u : 1u;
     L.a_off = 0;                                        // [nst][np] x 128 x K (no swizzle, core matrices)
     L.b_off = L.a_off + nst * np * 128u * K * 2;        // [nst][np] strips of 2 TYC rows x K
-    L.desc_off = (L.b_off + nst * np * tstrip_bytes(K, 2 * TYC) + 127) & ~127u;
+    L.c_off = L.b_off + nst * np * tstrip_bytes(K, 2 * TYC);   // [nst] correction operands A, B
+    L.desc_off = (L.c_off + nst * 2u * kCorrBlockHalfs * 2 + 127) & ~127u;
     L.bar_off = L.desc_off + kDescBytes;
     L.misc_off = L.bar_off + 16 * 8;
     L.total = L.misc_off + 64;
@@ -993,7 +1002,7 @@ __device__ __forceinline__ MtColItem col_item_mt(const TcBankArgs &a, const TcDe
     return MtColItem{f.u0 + q, (rest % a.col_nx64) * 64, (rest / a.col_nx64) * a.col_mt_ty, 0};
 }
 
-// SPLIT: BF16 operands as hi + lo pairs (a.split, a.col_mt_nst stages); FP16 operands in two stages otherwise.
+// SPLIT: BF16 operands as hi + lo pairs (a.split); a.col_mt_nst operand stages.
 template <bool SPLIT>
 __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __grid_constant__ TcBankArgs a)
 {
@@ -1002,17 +1011,18 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int TYC = a.col_mt_ty;
-    const int NST = SPLIT ? a.col_mt_nst : 2;
+    const int NST = a.col_mt_nst;
     constexpr int np = SPLIT ? 2 : 1;
     const MtColSmem L = mt_col_smem(a.col_kmax, TYC, SPLIT ? 1 : 0, NST);
     unsigned char *sA = sm + L.a_off;
     unsigned char *sB = sm + L.b_off;
+    unsigned char *sC = sm + L.c_off;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.bar_off);
     uint64_t *tmem_full = bars;            // [2] commit
-    uint64_t *tmem_empty = bars + 2;       // [2] 8 epilogue warps
-    uint64_t *ab_full = bars + 4;          // [2] TMA + bulk-copy bytes of a job's operands
-    uint64_t *ab_empty = bars + 6;         // [2] commit: the MMA reading the buffers is done
-    uint64_t *drain = bars + 8;
+    uint64_t *tmem_empty = bars + 2;       // [2] epilogue warps
+    uint64_t *ab_full = bars + 4;          // [kMtColMaxStages] TMA + bulk-copy bytes of a job's operands
+    uint64_t *ab_empty = bars + 4 + kMtColMaxStages;   // [kMtColMaxStages] commit: the MMA reading them is done
+    uint64_t *drain = bars + 4 + 2 * kMtColMaxStages;
     uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
     const uint32_t ahalf = 128u * a.col_kmax * 2;                 // one A operand (hi, or lo under split)
@@ -1024,6 +1034,8 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
         for (int i = 0; i < 2; ++i) {
             mbar_init(&tmem_full[i], 1);
             mbar_init(&tmem_empty[i], kMtColEpiWarps);
+        }
+        for (int i = 0; i < kMtColMaxStages; ++i) {
             mbar_init(&ab_full[i], 1);
             mbar_init(&ab_empty[i], 1);
         }
@@ -1049,25 +1061,35 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
         // -------------------------------------------------------------- producer (lane 0)
         if (lane == 0) {
             auto item = [&](int j) { return col_item_mt(a, D, blockIdx.x + j * gridDim.x); };
-            // job j's operands into stage j % NST: J boxes (8 rows of a block x 2 parts x 64
-            // columns x 8 blocks, landing as K-major core matrices with operand row
-            // n = 2 x + part; under split the hi pair of signals, then the lo pair) and the
-            // unit's Gm strips (one bulk copy: hi, then lo under split)
+            // job j's operands into stage j % NST: J boxes (64 columns x both parts x 8 rows of
+            // a block x 8 blocks of the unit's plane, landing as K-major core matrices with
+            // operand row n = 2 x + part; under split the hi plane, then the lo plane), the
+            // unit's Gm strips (one bulk copy: hi, then lo under split) and the correction
+            // operands
             auto issue = [&](int j) {
                 const MtColItem w = item(j);
                 const TcUnitDev u = D.units[w.unit];
                 const TcFreqDev f = D.freqs[u.s];
                 const int st = j % NST, nkb = f.Kcol / 64;
                 const uint32_t bbytes = tstrip_bytes(f.Kcol, 2 * TYC);
-                mbar_arrive_expect_tx(&ab_full[st], np * (nkb * 16384u + bbytes));
+                mbar_arrive_expect_tx(&ab_full[st], np * (nkb * 16384u + bbytes) + 4u * kCorrBlockHalfs);
                 const int yb0 = (a.Lpad + w.y0 - f.R8) >> 3;
                 const uint32_t dst = smem_u32(sA + st * obuf);
-                const void *tm = tc_img(a, w.img).tm;
+                const TcImgView im = tc_img(a, w.img);
+                // boxes of 16 columns x both parts x 8 rows (512 contiguous bytes) x 4 x 8 blocks
+                const int pb = (int)(im.Hp >> 3);
                 for (int h = 0; h < np; ++h)
                     for (int kb = 0; kb < nkb; ++kb)
-                        tma_load_4d(dst + h * ahalf + kb * 16384u, tm, 0, 2 * np * w.unit + 2 * h, w.x0, yb0 + 8 * kb,
-                                    &ab_full[st]);
+                        tma_load_3d(dst + h * ahalf + kb * 16384u, im.tm, 0, w.x0 / 16,
+                                    (np * w.unit + h) * pb + yb0 + 8 * kb, &ab_full[st]);
                 bulk_load(smem_u32(sB + st * gbuf), u.Gm, np * bbytes, &ab_full[st]);
+                // the correction operands of (unit, x0) and (unit, y0)
+                const int nxb = (im.W + 63) / 64, nyb = (im.H + TYC - 1) / TYC;
+                const uint32_t cdst = smem_u32(sC + st * 4u * kCorrBlockHalfs);
+                bulk_load(cdst, im.corrA + ((int64_t)w.unit * nxb + w.x0 / 64) * kCorrBlockHalfs, 2u * kCorrBlockHalfs,
+                          &ab_full[st]);
+                bulk_load(cdst + 2u * kCorrBlockHalfs, im.corrB + ((int64_t)w.unit * nyb + w.y0 / TYC) * kCorrBlockHalfs,
+                          2u * kCorrBlockHalfs, &ab_full[st]);
             };
             int issued = 0, landed = 0;
             for (; issued < NST && issued < njobs; ++issued) issue(issued);
@@ -1100,6 +1122,12 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
                                        tstrip_desc(b0, 4 * kb + kk), idesc, 1);
                         }
                     }
+                // + c A(x) B(y), the bank's response to the constant image c: one K = 16 product
+                {
+                    const uint32_t c0 = smem_u32(sC + st * 4u * kCorrBlockHalfs);
+                    tc_mma_f16(tmem + 128u * acc, smem_desc_kmajor(c0, 2048, 128),
+                               smem_desc_kmajor(c0 + 2u * kCorrBlockHalfs, 2048, 128), idesc, 1);
+                }
                 tc_commit(&tmem_full[acc]);
                 tc_commit(&ab_empty[st]);
                 // job j + NST goes into these buffers once this MMA is done with them
@@ -1136,27 +1164,15 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
         const int rpw = TYC / 4;                       // rows per warp: 16 or 8
         const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
         const int part = lane & 1, xl = 16 * quarter + (lane >> 1);
-        const float sgn = part ? -1.f : 1.f;
         for (int j = 0; j < njobs; ++j) {
             const MtColItem w = col_item_mt(a, D, blockIdx.x + j * gridDim.x);
             const TcImgView im = tc_img(a, w.img);
-            float cen;
-            int e_unused;
-            tc_centre(a, w.img, cen, e_unused);
             const TcUnitDev u = D.units[w.unit];
             const TcFreqDev f = D.freqs[u.s];
             const int acc = j & 1;
             const bool paired = u.plane_b >= 0;
             const int x = w.x0 + xl, ybase = w.y0 + rpw * rq;
             const bool xok = x < im.W;
-            // c B(y) of the warp's rows (lane l < rpw holds row ybase + l); A(x) of the lane's column
-            const int yl = ybase + lane;
-            float2 byl = (lane < rpw && yl < im.H) ? __ldg(&im.onesB[(int64_t)w.unit * im.H + yl]) : make_float2(0.f, 0.f);
-            byl.x *= cen;
-            byl.y *= cen;
-            const float2 ax = xok ? __ldg(&im.onesA[(int64_t)w.unit * im.W + x]) : make_float2(0.f, 0.f);
-            // correction c A(x) B(y) for theta, c conj(A(x)) B(y) for pi - theta
-            const float axr = ax.x, axi = sgn * ax.y;
             const int plane = part ? u.plane_b : u.plane_a;
             const bool store = xok && (part == 0 || paired);
             const int nrows = min(rpw, im.H - ybase);
@@ -1187,12 +1203,12 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
                 // this lane: (sum Re G, sum Im G) x (its part of J); the partner lane the other part
                 const float gr = __uint_as_float(r[2 * tt]) * unscale, gi = __uint_as_float(r[2 * tt + 1]) * unscale;
                 const float or_ = __shfl_xor_sync(0xffffffffu, gr, 1), oi = __shfl_xor_sync(0xffffffffu, gi, 1);
-                const float cbr = __shfl_sync(0xffffffffu, byl.x, t), cbi = __shfl_sync(0xffffffffu, byl.y, t);
                 // part 0 (A = gr, C = gi, D = or_, B = oi): F_theta = (A - B, C + D);
                 // part 1 (D = gr, B = gi, A = or_, C = oi): F_{pi-theta} = (A + B, C - D)
+                // (the correction c A(x) B(y), c conj(A(x)) B(y) for pi - theta, is in the sums)
                 const float fr = part ? or_ + gi : gr - oi;
                 const float fi = part ? oi - gr : gi + or_;
-                if (store && t < nrows) __stcs(o, make_float2(fr + (axr * cbr - axi * cbi), fi + (axr * cbi + axi * cbr)));
+                if (store && t < nrows) __stcs(o, make_float2(fr, fi));
                 o -= ostep;
             }
         }
@@ -1571,6 +1587,91 @@ __global__ void k_build_prefix(const double *__restrict__ unit_w, const TcUnitDe
 
 // A[u][x] = sum over the in-image (zero rule) or all (other rules) taps d of S(d) exp(i w^c d),
 // B[u][y] likewise along y: F[1](x, y) = A(x) B(y) for the unit's orientation.
+// One entry of F[1] = A(x) B(y) (is_x: A at x = pos, else B at y = pos), from the unit's FP64
+// prefix sums: the taps d with pos - d inside the image under the zero rule, all of them else.
+__device__ __forceinline__ double2 ones_entry(const TcBankArgs &a, int R, int u, bool is_x, int pos, int n1)
+{
+    const double2 *pr = a.ones_pre + ((int64_t)u * 2 + (is_x ? 0 : 1)) * a.ones_stride;
+    int lo = -R, hi = R;
+    if (a.bmode == kBoundaryZero) {
+        lo = max(-R, pos - (n1 - 1));
+        hi = min(R, pos);
+    }
+    return make_double2(pr[hi + R + 1].x - pr[lo + R].x, pr[hi + R + 1].y - pr[lo + R].y);
+}
+
+// The correction operands of one image (layout in TcBankArgs): rows of 16 K elements, one per
+// thread of the grid-stride loop.  A row of c A(x) 2^(sB - t) (Re or Im) and a row of B(y) 2^t
+// hold parts whose products the MMA sums to a b within about 2^-22 |a b|: FP16 (a0, a0, a1)
+// against (b0, b1, b0) with a = a0 + a1; BF16 (a0, a0, a1, a0, a1, a2) against
+// (b0, b1, b0, b2, b1, b0) with a = a0 + a1 + a2.  2^t keeps |a| below 2^14 (|A|, |B| <= 1), so
+// FP16 parts stay in range for |c| 2^sB < 2^29 (status code 60 beyond).
+__device__ void corr_rows(const TcBankArgs &a, const TcUnitDev *__restrict__ units, const TcFreqDev *__restrict__ freqs,
+                          int nunits, int W, int H, float c, uint16_t *cA, uint16_t *cB, int64_t gtid, int64_t gstride)
+{
+    const int TYC = a.col_mt_ty, nxb = (W + 63) / 64, nyb = (H + TYC - 1) / TYC;
+    const int64_t nA = (int64_t)nunits * nxb * 128, n = nA + (int64_t)nunits * nyb * 128;
+    for (int64_t i = gtid; i < n; i += gstride) {
+        const bool isA = i < nA;
+        const int64_t jj = isA ? i : i - nA;
+        const int nb = isA ? nxb : nyb;
+        const int u = (int)(jj / ((int64_t)nb * 128)), blk = (int)(jj / 128 % nb), row = (int)(jj % 128);
+        const TcFreqDev f = freqs[units[u].s];
+        const float inv = 1.f / f.unscale_col;   // 2^sB, exact
+        const float amax = fabsf(c) * inv;        // bound of |c A(x)| 2^sB
+        int t = 0;
+        if (amax > 16384.f) frexpf(amax * (1.f / 16384.f), &t);
+        if (t > 15) {
+            if (!a.split && row == 0 && blk == 0) atomicExch(a.status, 60);
+            t = 15;
+        }
+        float v = 0.f;
+        if (isA) {
+            const int x = 64 * blk + row / 2;
+            if (x < W) {
+                const double2 e = ones_entry(a, f.R, u, true, x, W);
+                v = (float)(row & 1 ? e.y : e.x) * (c * inv) * ldexpf(1.f, -t);
+            }
+        } else {
+            const int yp = row / 2, y = blk * TYC + TYC - 1 - yp;
+            if (yp < TYC && y < H) {
+                const double2 e = ones_entry(a, f.R, u, false, y, H);
+                v = (float)(row & 1 ? e.y : e.x) * ldexpf(1.f, t);
+            }
+        }
+        // parts: the residuals are exact in FP32
+        uint16_t k[16] = {};
+        if (a.split) {
+            const __nv_bfloat16 p0 = __float2bfloat16_rn(v);
+            const float r1 = v - __bfloat162float(p0);
+            const __nv_bfloat16 p1 = __float2bfloat16_rn(r1);
+            const __nv_bfloat16 p2 = __float2bfloat16_rn(r1 - __bfloat162float(p1));
+            const __nv_bfloat16 sa[6] = {p0, p0, p1, p0, p1, p2}, sb[6] = {p0, p1, p0, p2, p1, p0};
+            const __nv_bfloat16 *sl = isA ? sa : sb;
+            for (int q = 0; q < 6; ++q) k[q] = *reinterpret_cast<const uint16_t *>(&sl[q]);
+        } else {
+            const __half p0 = __float2half_rn(v);
+            const __half p1 = __float2half_rn(v - __half2float(p0));
+            const __half sa[3] = {p0, p0, p1}, sb[3] = {p0, p1, p0};
+            const __half *sl = isA ? sa : sb;
+            for (int q = 0; q < 3; ++q) k[q] = *reinterpret_cast<const uint16_t *>(&sl[q]);
+        }
+        // element (row, k) at (k / 8) * 1024 + (row / 8) * 64 + (row % 8) * 8 + k % 8 halves
+        uint16_t *base = (isA ? cA : cB) + ((int64_t)u * nb + blk) * kCorrBlockHalfs + (row / 8) * 64 + (row % 8) * 8;
+        uint4 w0, w1;
+        w0.x = k[0] | (uint32_t)k[1] << 16;
+        w0.y = k[2] | (uint32_t)k[3] << 16;
+        w0.z = k[4] | (uint32_t)k[5] << 16;
+        w0.w = k[6] | (uint32_t)k[7] << 16;
+        w1.x = k[8] | (uint32_t)k[9] << 16;
+        w1.y = k[10] | (uint32_t)k[11] << 16;
+        w1.z = k[12] | (uint32_t)k[13] << 16;
+        w1.w = k[14] | (uint32_t)k[15] << 16;
+        *reinterpret_cast<uint4 *>(base) = w0;
+        *reinterpret_cast<uint4 *>(base + 1024) = w1;
+    }
+}
+
 __global__ void k_ones(const TcBankArgs a, const TcUnitDev *__restrict__ units, const TcFreqDev *__restrict__ freqs,
                        int nunits, float2 *__restrict__ A, float2 *__restrict__ B)
 {
@@ -1578,18 +1679,12 @@ __global__ void k_ones(const TcBankArgs a, const TcUnitDev *__restrict__ units, 
     // and completes only after k_minmax has (so the kernels after it see both)
     pdl_launch_dependents();
     const int64_t n = (int64_t)nunits * (a.W + a.H);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gstride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = gtid; i < n; i += gstride) {
         const int u = (int)(i / (a.W + a.H)), p = (int)(i % (a.W + a.H));
         const bool is_x = p < a.W;
-        const int pos = is_x ? p : p - a.W, n1 = is_x ? a.W : a.H;
-        const int R = freqs[units[u].s].R;
-        const double2 *pr = a.ones_pre + ((int64_t)u * 2 + (is_x ? 0 : 1)) * a.ones_stride;
-        int lo = -R, hi = R;
-        if (a.bmode == kBoundaryZero) {   // taps d with 0 <= pos - d < n1
-            lo = max(-R, pos - (n1 - 1));
-            hi = min(R, pos);
-        }
-        const double2 v = make_double2(pr[hi + R + 1].x - pr[lo + R].x, pr[hi + R + 1].y - pr[lo + R].y);
+        const int pos = is_x ? p : p - a.W;
+        const double2 v = ones_entry(a, freqs[units[u].s].R, u, is_x, pos, is_x ? a.W : a.H);
         const float2 f = make_float2((float)v.x, (float)v.y);
         if (is_x)
             A[(int64_t)u * a.W + pos] = f;
@@ -1597,6 +1692,12 @@ __global__ void k_ones(const TcBankArgs a, const TcUnitDev *__restrict__ units, 
             B[(int64_t)u * a.H + pos] = f;
     }
     pdl_wait();
+    if (a.row_mt && a.corrA) {   // the centre is known now
+        float c;
+        int e;
+        image_centre(a, c, e);
+        corr_rows(a, units, freqs, nunits, a.W, a.H, c, a.corrA, a.corrB, gtid, gstride);
+    }
 }
 
 // Batch form of k_ones: grid (blocks, images), the tables of image blockIdx.y; then, once
@@ -1608,24 +1709,20 @@ __global__ void k_ones_batch(const TcBankArgs a, const TcUnitDev *__restrict__ u
     pdl_launch_dependents();
     const TcImgDev im = a.imgs[blockIdx.y];
     const int64_t n = (int64_t)nunits * (im.W + im.H);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gstride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = gtid; i < n; i += gstride) {
         const int u = (int)(i / (im.W + im.H)), p = (int)(i % (im.W + im.H));
         const bool is_x = p < im.W;
-        const int pos = is_x ? p : p - im.W, n1 = is_x ? im.W : im.H;
-        const int R = freqs[units[u].s].R;
-        const double2 *pr = a.ones_pre + ((int64_t)u * 2 + (is_x ? 0 : 1)) * a.ones_stride;
-        int lo = -R, hi = R;
-        if (a.bmode == kBoundaryZero) {
-            lo = max(-R, pos - (n1 - 1));
-            hi = min(R, pos);
-        }
-        const double2 v = make_double2(pr[hi + R + 1].x - pr[lo + R].x, pr[hi + R + 1].y - pr[lo + R].y);
+        const int pos = is_x ? p : p - im.W;
+        const double2 v = ones_entry(a, freqs[units[u].s].R, u, is_x, pos, is_x ? im.W : im.H);
         const float2 f = make_float2((float)v.x, (float)v.y);
         float2 *dst = const_cast<float2 *>(is_x ? im.onesA + (int64_t)u * im.W + pos : im.onesB + (int64_t)u * im.H + pos);
         *dst = f;
     }
     pdl_wait();
-    if (blockIdx.x == 0 && threadIdx.x < 32) {
+    // every block reduces the image's partial keys into its centre; block 0 records it
+    __shared__ float cen_s;
+    if (threadIdx.x < 32) {
         const unsigned *p = a.mm_part + (int64_t)blockIdx.y * kMmParts * 2;
         unsigned nlo = 0u, hik = 0u;
         for (int i = threadIdx.x; i < kMmParts; i += 32) {
@@ -1641,9 +1738,12 @@ __global__ void k_ones_batch(const TcBankArgs a, const TcUnitDev *__restrict__ u
             float c;
             int e;
             centre_of(nlo, hik, c, e);
-            a.img_ce[blockIdx.y] = make_float2(c, (float)e);
+            cen_s = c;
+            if (blockIdx.x == 0) a.img_ce[blockIdx.y] = make_float2(c, (float)e);
         }
     }
+    __syncthreads();
+    corr_rows(a, units, freqs, nunits, im.W, im.H, cen_s, im.corrA, im.corrB, gtid, gstride);
 }
 
 __global__ void k_build_toeplitz(uint16_t *__restrict__ B, int rows, int K, int off, int R, double sigma, int sB)
@@ -1727,10 +1827,12 @@ int gabor_tc_mt_col_ty(int col_kmax, int split)
     return 1024 + mt_col_smem(col_kmax, 64, split, 1).total <= (uint32_t)kSmemLimit ? 64 : 32;
 }
 
-// Operand stages of the modulated-tap column kernel: two where they fit, else one.
+// Operand stages of the modulated-tap column kernel: as many as fit, up to kMtColMaxStages.
 int gabor_tc_mt_col_stages(int col_kmax, int col_ty, int split)
 {
-    return 1024 + mt_col_smem(col_kmax, col_ty, split, 2).total <= (uint32_t)kSmemLimit ? 2 : 1;
+    int n = kMtColMaxStages;
+    while (n > 1 && 1024 + mt_col_smem(col_kmax, col_ty, split, n).total > (uint32_t)kSmemLimit) --n;
+    return n;
 }
 
 cudaError_t build_gabor_tc_am(uint16_t *Am, int R, double sigma, double wc, int split, cudaStream_t st)

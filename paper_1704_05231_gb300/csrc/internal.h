@@ -138,23 +138,31 @@ struct TcImgDev {
     const float *img;
     int64_t pitch;
     int H, W;
+    int Wq, pad_q;         // modulated-tap intermediate: columns per 8-row block (W rounded up to 16)
     float2 *out;
     int64_t plane;         // H * W
     uint16_t *sig;
     int64_t Hp;
     const float2 *onesA;   // [unit][W]
     const float2 *onesB;   // [unit][H]
+    uint16_t *corrA;       // [unit][(W + 63) / 64] and [unit][(H + TYC - 1) / TYC] blocks of
+    uint16_t *corrB;       // kCorrBlockHalfs: the correction operands (TcBankArgs)
 };
 constexpr int kMmParts = 64;   // partial min / max words per image of a batch (k_minmax)
+constexpr int kCorrBlockHalfs = 2048;   // one correction operand block: 128 rows x 16 K, 4 KB
 struct TcBankArgs {
     const float *img;
     int64_t pitch;
     int H, W;
     float2 *out;
     int64_t plane;
-    uint16_t *sig;         // intermediate: [signal][Hp / 8][W][8], image row y at Lpad + y
+    // intermediate, image row y at Lpad + y: [signal][Hp / 8][W][8] (step-by-step form) or
+    // [plane][Hp / 8][Wq][part][8] (modulated taps: plane = unit, or 2 unit + {hi, lo} under
+    // BF16; part = Re J, Im J interleaved, so 16 columns x both parts x 8 rows are 512
+    // contiguous bytes)
+    uint16_t *sig;
     int64_t Hp;
-    int Lpad, pad_;
+    int Lpad, Wq;
     const TcFreqDev *freqs;
     const TcUnitDev *units;
     int *status;
@@ -166,6 +174,13 @@ struct TcBankArgs {
     const float2 *onesB;   // [unit][H]
     const double2 *ones_pre;   // [unit][2][2 Rmax + 2] prefix sums of S(d) exp(i w^{c|s} d)
     int ones_stride;           // 2 Rmax + 2
+    // The modulated-tap column pass adds c A(x) B(y) by one extra K = 16 MMA per job; its
+    // operands (written by k_ones once the centre c is known) in the shared-memory image the
+    // MMA reads: per unit, one block of 128 rows x 16 K (FP16 or BF16, no-swizzle K-major core
+    // matrices, kCorrBlockHalfs elements) per 64 image columns (rows 2 x + {Re, Im} of
+    // c A(x) 2^(sB - t)) and per TYC image rows (rows 2 (TYC - 1 - y) + {Re, Im} of B(y) 2^t).
+    uint16_t *corrA;
+    uint16_t *corrB;
     int col_mt_ty;             // modulated-tap column pass: output rows per job (64, or 32 for large K)
     // Work items, decoded from the image shape: frequencies in the order forder[] (largest
     // radius first); every frequency has nu_f units, the first np_f of them paired.
@@ -439,6 +454,7 @@ struct gabor_bank {
     int tc_row_ty_opt = 0, tc_col_ty_opt = 0; // GB_OPT_TC_TILES (0 automatic, 32, 64)
     uint16_t *d_tcGm = nullptr;               // modulated-tap column operands, one per unit
     int tc_H = 0, tc_W = 0, tc_Lpad = 0;
+    int tc_zero_mt = -1;   // the intermediate layout whose halo was last zeroed (1: modulated taps)
     int64_t tc_Hp = 0;
     bool tc_ready = false;
     size_t tc_smem_rows = 0, tc_smem_cols = 0;
