@@ -963,7 +963,7 @@ __global__ void k_build_tstrip(uint16_t *__restrict__ Q, int ncores, int off, in
 constexpr int kMtColAcc = 2;       // TMEM accumulators (128 columns each)
 constexpr int kMtColEpiWarps = 16;
 constexpr int kMtColMaxStages = 2;   // operand stages of the modulated-tap column kernel
-constexpr int kMtColThreads = 32 * (kMtColEpiWarps + 1);
+constexpr int kMtColThreads = 32 * (kMtColEpiWarps + 2);   // + the MMA warp and the copy warp
 
 struct MtColSmem {
     uint32_t a_off, b_off, c_off, desc_off, bar_off, misc_off, total;
@@ -1025,6 +1025,8 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     uint64_t *drain = bars + 4 + 2 * kMtColMaxStages;
     uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
+    volatile int *issued_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 8);   // jobs whose copies were issued
+    volatile int *landed_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 12);  // jobs whose copies were waited for
     const uint32_t ahalf = 128u * a.col_kmax * 2;                 // one A operand (hi, or lo under split)
     const uint32_t obuf = np * ahalf;                             // the A operands of a stage
     const uint32_t gbuf = np * tstrip_bytes(a.col_kmax, 2 * TYC); // the B strips of a stage
@@ -1041,6 +1043,8 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
         }
         mbar_init(drain, 1);
         *abort_s = 0;
+        *issued_s = 0;
+        *landed_s = 0;
         mbar_fence_init();
     }
     if (warp == 0) {
@@ -1057,20 +1061,28 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     const uint32_t idesc = idesc_f16(SPLIT ? 1 : 0, 128, 2 * TYC);
     const int njobs = nitems > (int)blockIdx.x ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
-    if (warp == kMtColEpiWarps) {
-        // -------------------------------------------------------------- producer (lane 0)
+    auto item = [&](int j) { return col_item_mt(a, D, blockIdx.x + j * gridDim.x); };
+    if (warp == kMtColEpiWarps + 1) {
+        // -------------------------------------------------------------- copies (lane 0)
+        // job j's operands into stage j % NST once the MMAs of job j - NST are done with it: J
+        // boxes (64 columns x both parts x 8 rows of a block x 8 blocks of the unit's plane,
+        // landing as K-major core matrices with operand row n = 2 x + part; under split the hi
+        // plane, then the lo plane), the unit's Gm strips (one bulk copy: hi, then lo under
+        // split) and the correction operands.  A warp of its own, so that issuing the copies
+        // overlaps the MMA warp's issue of the previous job's products.
         if (lane == 0) {
-            auto item = [&](int j) { return col_item_mt(a, D, blockIdx.x + j * gridDim.x); };
-            // job j's operands into stage j % NST: J boxes (64 columns x both parts x 8 rows of
-            // a block x 8 blocks of the unit's plane, landing as K-major core matrices with
-            // operand row n = 2 x + part; under split the hi plane, then the lo plane), the
-            // unit's Gm strips (one bulk copy: hi, then lo under split) and the correction
-            // operands
-            auto issue = [&](int j) {
+            int j = 0;
+            for (; j < njobs; ++j) {
+                if (*abort_s) break;
+                const int st = j % NST;
+                if (j >= NST && !mbar_wait(&ab_empty[st], ((j - NST) / NST) & 1, abort_s)) {
+                    fail_status(a.status, abort_s, 38);
+                    break;
+                }
                 const MtColItem w = item(j);
                 const TcUnitDev u = D.units[w.unit];
                 const TcFreqDev f = D.freqs[u.s];
-                const int st = j % NST, nkb = f.Kcol / 64;
+                const int nkb = f.Kcol / 64;
                 const uint32_t bbytes = tstrip_bytes(f.Kcol, 2 * TYC);
                 mbar_arrive_expect_tx(&ab_full[st], np * (nkb * 16384u + bbytes) + 4u * kCorrBlockHalfs);
                 const int yb0 = (a.Lpad + w.y0 - f.R8) >> 3;
@@ -1090,9 +1102,13 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
                           &ab_full[st]);
                 bulk_load(cdst + 2u * kCorrBlockHalfs, im.corrB + ((int64_t)w.unit * nyb + w.y0 / TYC) * kCorrBlockHalfs,
                           2u * kCorrBlockHalfs, &ab_full[st]);
-            };
-            int issued = 0, landed = 0;
-            for (; issued < NST && issued < njobs; ++issued) issue(issued);
+            }
+            *issued_s = j;
+        }
+    } else if (warp == kMtColEpiWarps) {
+        // -------------------------------------------------------------- MMAs (lane 0)
+        if (lane == 0) {
+            int landed = 0;
             for (int j = 0; j < njobs; ++j) {
                 if (*abort_s) break;
                 const int st = j % NST, acc = j & 1;
@@ -1130,26 +1146,12 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
                 }
                 tc_commit(&tmem_full[acc]);
                 tc_commit(&ab_empty[st]);
-                // job j + NST goes into these buffers once this MMA is done with them
-                if (j + NST < njobs) {
-                    if (!mbar_wait(&ab_empty[st], (j / NST) & 1, abort_s)) {
-                        fail_status(a.status, abort_s, 38);
-                        break;
-                    }
-                    issue(j + NST);
-                    issued = j + NST + 1;
-                }
             }
+            *landed_s = landed;
             tc_commit(drain);
             if (!mbar_wait(drain, 0, abort_s)) {
                 volatile int dummy = 0;
                 mbar_wait(drain, 0, &dummy);
-            }
-            // operands issued but not waited for (after a stop) land before shared memory is
-            // released
-            for (int jj = landed; jj < issued; ++jj) {
-                volatile int dummy = 0;
-                mbar_wait(&ab_full[jj % NST], (jj / NST) & 1, &dummy);
             }
         }
     } else {
@@ -1216,6 +1218,14 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (warp == kMtColEpiWarps && lane == 0) {
+        // copies issued but not waited for (after a stop) land before shared memory is released;
+        // at most one per stage is outstanding
+        for (int jj = *landed_s; jj < *issued_s; ++jj) {
+            volatile int dummy = 0;
+            mbar_wait(&ab_full[jj % NST], (jj / NST) & 1, &dummy);
+        }
+    }
     if (warp == 0) tmem_dealloc(tmem, 128 * kMtColAcc);
 }
 
