@@ -594,17 +594,18 @@ __device__ __forceinline__ uint64_t tstrip_desc(uint32_t s0, int ks) { return sm
 struct MtSmem {
     uint32_t a_off, p_off, patch_off, desc_off, bar_off, misc_off, total;
 };
-constexpr int kAmBufs = 2;   // Am strip buffers of the modulated-tap row kernel
+constexpr int kAmBufs = 3;   // Am strip buffers of the modulated-tap row kernel
 
 // split = 1 (BF16 operands as hi + lo pairs): two strips per A buffer and P as hi and lo.
 __host__ __device__ inline MtSmem mt_smem(int K, int PW, int TY, int split = 0)
 {
     MtSmem L;
     const uint32_t np = split ? 2u : 1u;
+    (void)PW;
     L.a_off = 0;                                              // [kAmBufs] buffers of np strips of 128 rows x K
-    L.p_off = (L.a_off + kAmBufs * np * tstrip_bytes(K, 128) + 1023) & ~1023u;   // np x TY x K (SW128)
-    L.patch_off = L.p_off + np * (uint32_t)TY * K * 2;        // TY x PWs FP32
-    L.desc_off = (L.patch_off + (uint32_t)TY * (round_up(PW, 8) + 4) * 4 + 127) & ~127u;
+    L.p_off = (L.a_off + kAmBufs * np * tstrip_bytes(K, 128) + 1023) & ~1023u;   // [2] x np x TY x K (SW128)
+    L.patch_off = L.p_off + 2 * np * (uint32_t)TY * K * 2;
+    L.desc_off = (L.patch_off + 127) & ~127u;
     L.bar_off = L.desc_off + kDescBytes;
     L.misc_off = L.bar_off + 16 * 8;
     L.total = L.misc_off + 64;
@@ -632,35 +633,37 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
     const int TY = a.row_ty;
     const MtSmem L = mt_smem(a.row_kmax, a.row_pwmax, TY, SPLIT ? 1 : 0);
     unsigned char *sA = sm + L.a_off;
-    unsigned char *sP = sm + L.p_off;
-    float *patch = reinterpret_cast<float *>(sm + L.patch_off);
+    unsigned char *sP = sm + L.p_off;   // two P buffers (items alternate)
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.bar_off);
     uint64_t *tmem_full = bars;        // [2] commit
     uint64_t *tmem_empty = bars + 2;   // [2] epilogue warps
     uint64_t *a_full = bars + 4;       // [kAmBufs] Am landed (bulk copy)
-    uint64_t *a_empty = bars + 4 + kAmBufs;   // [kAmBufs] commit: the MMA reading the buffer is done
-    uint64_t *p_empty = bars + 4 + 2 * kAmBufs;   // [1] commit: the item's MMAs (reading P) are done
-    uint64_t *drain = bars + 5 + 2 * kAmBufs;
-    uint64_t *p_full = bars + 6 + 2 * kAmBufs;    // [1] the producers built the item's P
+    uint64_t *p_empty = bars + 4 + kAmBufs;   // [2] commit: the item's MMAs (reading P) are done
+    uint64_t *drain = bars + 6 + kAmBufs;
+    uint64_t *p_full = bars + 7 + kAmBufs;    // [2] the producers built the item's P
     uint32_t *tmem_s = reinterpret_cast<uint32_t *>(sm + L.misc_off);
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
+    volatile int *issued_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 8);   // Am copies issued
+    volatile int *landed_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 12);  // Am copies waited for
     const TcDesc D = load_desc(a, sm + L.desc_off);
     constexpr uint32_t np = SPLIT ? 2u : 1u;
     const uint32_t abuf = np * tstrip_bytes(a.row_kmax, 128);   // an A buffer (hi, lo strips)
     const uint32_t plo = (uint32_t)TY * a.row_kmax * 2;         // P lo after P hi (split)
+    const uint32_t pbuf = np * plo;                              // one P buffer (hi, lo)
 
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(&tmem_full[i], 1);
             mbar_init(&tmem_empty[i], kMtEpiWarps);
         }
-        for (int i = 0; i < kAmBufs; ++i) {
-            mbar_init(&a_full[i], 1);
-            mbar_init(&a_empty[i], 1);
+        for (int i = 0; i < kAmBufs; ++i) mbar_init(&a_full[i], 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&p_empty[i], 1);
+            mbar_init(&p_full[i], 1);
         }
-        mbar_init(p_empty, 1);
         mbar_init(drain, 1);
-        mbar_init(p_full, 1);
+        *issued_s = 0;
+        *landed_s = 0;
         *abort_s = 0;
         mbar_fence_init();
     }
@@ -677,35 +680,33 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
     pdl_wait();
     const uint32_t tmem = *tmem_s;
     const uint32_t idesc = idesc_f16(SPLIT ? 1 : 0, 128, TY);
+    const int my_items = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int njobs_row = my_items * a.nu_f;
+    auto issue_am = [&](int jq) {   // the Am copy of job jq into buffer jq % kAmBufs
+        const int buf = jq % kAmBufs;
+        const RowItem w = row_item_mt(a, D, blockIdx.x + (jq / a.nu_f) * gridDim.x);
+        const TcFreqDev f = D.freqs[w.s];
+        const uint32_t abytes = np * tstrip_bytes(f.Kmt, 128);
+        mbar_arrive_expect_tx(&a_full[buf], abytes);
+        bulk_load(smem_u32(sA + buf * abuf), D.units[f.u0 + jq % a.nu_f].Am, abytes, &a_full[buf]);
+    };
 
     if (warp == 15) {
         // -------------------------------------------------------------- MMA warp (lane 0)
-        // Runs ahead of the producers: the Am copy of job jq (unit q of the CTA's item jq / nu)
-        // goes into buffer jq % kAmBufs as soon as the MMA of job jq - kAmBufs has released it,
-        // across item boundaries; the MMAs of an item wait for its P (p_full) and release it
-        // (p_empty).
+        // The Am copy of job jq (unit jq % nu of the CTA's item jq / nu) goes into buffer
+        // jq % kAmBufs: this warp issues the first kAmBufs; the others are issued by the epilogue
+        // (warp 0) as soon as the MMAs of job jq - kAmBufs are complete.  The MMAs of an item wait
+        // for its P (p_full) and release it (p_empty).
         if (lane == 0) {
             const int nu = a.nu_f;
-            const int my_items = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-            const int njobs = my_items * nu;
-            int issued = 0, landed = 0;
+            int landed = 0;
             bool ok = true;
-            auto issue_a = [&]() {   // the Am copy of job `issued`
-                const int jq = issued, buf = jq % kAmBufs;
-                if (jq >= kAmBufs && !mbar_wait(&a_empty[buf], ((jq - kAmBufs) / kAmBufs) & 1, abort_s)) return false;
-                const RowItem w = row_item_mt(a, D, blockIdx.x + (jq / nu) * gridDim.x);
-                const TcFreqDev f = D.freqs[w.s];
-                const uint32_t abytes = np * tstrip_bytes(f.Kmt, 128);
-                mbar_arrive_expect_tx(&a_full[buf], abytes);
-                bulk_load(smem_u32(sA + buf * abuf), D.units[f.u0 + jq % nu].Am, abytes, &a_full[buf]);
-                ++issued;
-                return true;
-            };
+            for (int jq = 0; jq < kAmBufs && jq < njobs_row; ++jq) issue_am(jq);
             for (int nitem = 0; nitem < my_items && ok; ++nitem) {
                 const RowItem w = row_item_mt(a, D, blockIdx.x + nitem * gridDim.x);
                 const int K = D.freqs[w.s].Kmt;
-                while (ok && issued < njobs && issued < nitem * nu + 2) ok = issue_a();
-                if (ok) ok = mbar_wait(p_full, nitem & 1, abort_s);   // this item's P
+                const int pb = nitem & 1;
+                if (ok) ok = mbar_wait(&p_full[pb], (nitem >> 1) & 1, abort_s);   // this item's P
                 for (int q = 0; q < nu && ok; ++q) {
                     const int jq = nitem * nu + q, b = jq & 1, ab = jq % kAmBufs;
                     ok = mbar_wait(&a_full[ab], (jq / kAmBufs) & 1, abort_s);
@@ -713,7 +714,7 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
                     if (ok && jq >= 2) ok = mbar_wait(&tmem_empty[b], ((jq - 2) >> 1) & 1, abort_s);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(sA + ab * abuf), p0 = smem_u32(sP);
+                    const uint32_t a0 = smem_u32(sA + ab * abuf), p0 = smem_u32(sP + pb * pbuf);
                     const uint32_t a0l = a0 + tstrip_bytes(K, 128);
                     for (int kb = 0; kb < K / 64; ++kb)
 #pragma unroll
@@ -727,11 +728,8 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
                             }
                         }
                     tc_commit(&tmem_full[b]);
-                    tc_commit(&a_empty[ab]);
-                    // the next copies (this item's later units, or the next item's first ones)
-                    while (ok && issued < njobs && issued < jq + 3) ok = issue_a();
                 }
-                if (ok) tc_commit(p_empty);
+                if (ok) tc_commit(&p_empty[pb]);
             }
             if (!ok) fail_status(a.status, abort_s, 27);
             tc_commit(drain);
@@ -739,58 +737,18 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
                 volatile int dummy = 0;
                 mbar_wait(drain, 0, &dummy);
             }
-            // bulk copies issued but not waited for (after a stop) land before shared memory is
-            // released; copy i went to buffer i % kAmBufs as its (i / kAmBufs)-th use
-            for (int i = landed; i < issued; ++i) {
-                volatile int dummy = 0;
-                mbar_wait(&a_full[i % kAmBufs], (i / kAmBufs) & 1, &dummy);
-            }
+            *landed_s = landed;
         }
     } else if (warp >= kMtEpiWarps) {
         // -------------------------------------------------------------- producers (warps 8-14)
+        // P of item it into buffer it's parity, straight from the image: P[r][k] =
+        // (f(x0 - R + k, y0 + r) - c) 2^-e in FP16 (zero beyond the window, and outside the image
+        // under the zero rule), 8 k per 16-byte chunk of the swizzled K-major layout; a thread
+        // takes chunks k8 = idx % (K / 8) of row r = idx / (K / 8), so a warp reads consecutive
+        // 32-byte runs of image rows.  The buffer is free once the MMAs of item it - 2 are done.
         constexpr int NP = 32 * (15 - kMtEpiWarps);
-        const int ptid = tid - 32 * kMtEpiWarps, pwarp = warp - kMtEpiWarps;
+        const int ptid = tid - 32 * kMtEpiWarps;
         int nitem = 0;
-        // cp.async of item it's patch: rows y0 .. y0 + TY - 1, columns x0 - R .. x0 + 63 + R;
-        // interior rows that start on a 16-byte boundary by 16-byte copies
-        auto stage = [&](int it) {
-            const RowItem w = row_item_mt(a, D, it);
-            const TcImgView im = tc_img(a, w.img);
-            const int R = D.freqs[w.s].R, y0 = w.y0, x0 = w.x0;
-            const int ncols = kMtTileX + 2 * R, PW = round_up(ncols, 4), PWs = round_up(PW, 8) + 4;
-            if (a.bmode == kBoundaryZero) {
-                const bool xin = x0 - R >= 0 && x0 - R + ncols <= im.W;
-                const int n16 = ncols >> 2;
-                for (int r = pwarp; r < TY; r += NP / 32) {
-                    const int y = y0 + r;
-                    const bool yin = y >= 0 && y < im.H;
-                    const float *src = im.img + (int64_t)(yin ? y : 0) * im.pitch;
-                    if (yin && xin && (reinterpret_cast<uintptr_t>(src + (x0 - R)) & 15) == 0) {
-                        const float *s0 = src + (x0 - R);
-                        for (int c = lane; c < n16; c += 32) cp_async16(patch + r * PWs + 4 * c, s0 + 4 * c);
-                        for (int c = 4 * n16 + lane; c < ncols; c += 32) cp_async4(patch + r * PWs + c, s0 + c, 4);
-                    } else {
-                        for (int c = lane; c < PW; c += 32) {
-                            const int gx = x0 - R + c;
-                            const bool in = yin && c < ncols && gx >= 0 && gx < im.W;
-                            cp_async4(patch + r * PWs + c, in ? (const void *)(src + gx) : (const void *)im.img, in ? 4 : 0);
-                        }
-                    }
-                }
-            } else {
-                for (int r = pwarp; r < TY; r += NP / 32) {
-                    const float *src = im.img + (int64_t)ext_coord(y0 + r, im.H, a.bmode) * im.pitch;
-                    for (int c = lane; c < PW; c += 32) {
-                        const bool in = c < ncols;
-                        cp_async4(patch + r * PWs + c,
-                                  in ? (const void *)(src + ext_coord(x0 - R + c, im.W, a.bmode)) : (const void *)im.img,
-                                  in ? 4 : 0);
-                    }
-                }
-            }
-            cp_async_commit();
-        };
-        if ((int)blockIdx.x < nitems) stage(blockIdx.x);
         for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++nitem) {
             if (named_barrier_or(1, NP, *abort_s != 0)) break;
             const RowItem w = row_item_mt(a, D, it);
@@ -801,47 +759,69 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
             tc_centre(a, w.img, cen, e);
             const float sc = ldexpf(1.f, -e);
             const TcFreqDev f = D.freqs[w.s];
-            const int R = f.R, K = f.Kmt;
-            const int ncols = kMtTileX + 2 * R, PW = round_up(ncols, 4);
-            const int PWs = round_up(PW, 8) + 4;
-            // P is free once the previous item's MMAs are done
-            bool failed = nitem > 0 && !mbar_wait(p_empty, (nitem - 1) & 1, abort_s);
+            const int R = f.R, K = f.Kmt, nk8 = K / 8;
+            const int ncols = kMtTileX + 2 * R;
+            const int pb = nitem & 1;
+            bool failed = nitem >= 2 && !mbar_wait(&p_empty[pb], ((nitem - 2) >> 1) & 1, abort_s);
             if (named_barrier_or(1, NP, failed)) {
                 if (ptid == 0) fail_status(a.status, abort_s, 26);
                 break;
             }
-            cp_async_wait<0>();   // this item's patch (staged during the previous item)
-            named_barrier(1, NP);
-            // P[r][k] = (f - c) 2^-e in FP16 (zero outside the image under the zero rule and
-            // beyond the window), 8 k per 16-byte chunk of the swizzled K-major layout
-            for (int idx = ptid; idx < TY * (K / 8); idx += NP) {
-                const int r = idx % TY, k0 = 8 * (idx / TY);
-                const int y = y0 + r;
-                const bool yok = a.bmode != kBoundaryZero || (y >= 0 && y < im.H);
-                float v[8];
+            unsigned char *dP = sP + pb * pbuf;
+            const bool zero = a.bmode == kBoundaryZero;
+            const int nchunks = TY * nk8;
+            // the loads of kU chunks are issued before any of them is converted
+            constexpr int kU = 2;
+            for (int base = ptid; base < nchunks; base += kU * NP) {
+                float v[kU][8];
 #pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const int kk = k0 + t, gx = x0 - R + kk;
-                    const bool in = yok && kk < ncols && (a.bmode != kBoundaryZero || (gx >= 0 && gx < im.W));
-                    v[t] = in ? (patch[r * PWs + kk] - cen) * sc : 0.f;
+                for (int uu = 0; uu < kU; ++uu) {
+                    const int idx = base + uu * NP;
+                    const int r = idx / nk8, k0 = 8 * (idx - r * nk8);
+                    const int y = y0 + r, gx0 = x0 - R + k0;
+                    const int yy = zero ? y : ext_coord(y, im.H, a.bmode);
+                    const bool yok = idx < nchunks && (!zero || (y >= 0 && y < im.H));
+                    const float *src = im.img + (int64_t)(yok ? yy : 0) * im.pitch;
+                    if (zero && yok && k0 + 8 <= ncols && gx0 >= 0 && gx0 + 8 <= im.W &&
+                        (reinterpret_cast<uintptr_t>(src + gx0) & 15) == 0) {
+                        const float4 p = __ldg(reinterpret_cast<const float4 *>(src + gx0));
+                        const float4 q = __ldg(reinterpret_cast<const float4 *>(src + gx0 + 4));
+                        v[uu][0] = p.x; v[uu][1] = p.y; v[uu][2] = p.z; v[uu][3] = p.w;
+                        v[uu][4] = q.x; v[uu][5] = q.y; v[uu][6] = q.z; v[uu][7] = q.w;
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) {
+                            const int k = k0 + t, gx = gx0 + t;
+                            const int xx = zero ? ((gx >= 0 && gx < im.W) ? gx : -1) : ext_coord(gx, im.W, a.bmode);
+                            v[uu][t] = (yok && k < ncols && xx >= 0) ? __ldg(src + xx) : cen;   // cen: 0 after - cen
+                        }
+                    }
                 }
-                if constexpr (SPLIT) {   // BF16 hi + lo
-                    uint32_t hw[4], lw[4];
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) b2split(v[2 * t], v[2 * t + 1], hw[t], lw[t]);
-                    *reinterpret_cast<uint4 *>(sP + sw128_offset(TY, r, k0)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                    *reinterpret_cast<uint4 *>(sP + plo + sw128_offset(TY, r, k0)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-                } else {
-                    *reinterpret_cast<uint4 *>(sP + sw128_offset(TY, r, k0)) =
-                        make_uint4(h2pack(v[0], v[1]), h2pack(v[2], v[3]), h2pack(v[4], v[5]), h2pack(v[6], v[7]));
+                for (int uu = 0; uu < kU; ++uu) {
+                    const int idx = base + uu * NP;
+                    if (idx >= nchunks) break;
+                    const int r = idx / nk8, k0 = 8 * (idx - r * nk8);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) v[uu][t] = (v[uu][t] - cen) * sc;
+                    if constexpr (SPLIT) {   // BF16 hi + lo
+                        uint32_t hw[4], lw[4];
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) b2split(v[uu][2 * t], v[uu][2 * t + 1], hw[t], lw[t]);
+                        *reinterpret_cast<uint4 *>(dP + sw128_offset(TY, r, k0)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4 *>(dP + plo + sw128_offset(TY, r, k0)) =
+                            make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    } else {
+                        *reinterpret_cast<uint4 *>(dP + sw128_offset(TY, r, k0)) =
+                            make_uint4(h2pack(v[uu][0], v[uu][1]), h2pack(v[uu][2], v[uu][3]),
+                                       h2pack(v[uu][4], v[uu][5]), h2pack(v[uu][6], v[uu][7]));
+                    }
                 }
             }
             fence_proxy_async_smem();
-            named_barrier(1, NP);   // P built; the FP32 patch is free: stage the next item's
-            if (ptid == 0) mbar_arrive(p_full);
-            if (it + (int)gridDim.x < nitems) stage(it + gridDim.x);
+            named_barrier(1, NP);   // P built
+            if (ptid == 0) mbar_arrive(&p_full[pb]);
         }
-        cp_async_wait<0>();   // a patch staged before a stop lands before shared memory is released
     } else {
         // -------------------------------------------------------------- epilogue
         // TMEM lane n = 2 x' + part, x' = 63 - x (the operand strip runs backwards in x): warp w
@@ -872,6 +852,12 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
                     ok = false;
                     break;
                 }
+                // job's MMAs are complete: its Am buffer takes the copy of job + kAmBufs
+                if (warp == 0 && lane == 0 && job + kAmBufs < njobs_row) {
+                    issue_am(job + kAmBufs);
+                    *issued_s = job + kAmBufs + 1;
+                }
+                __syncwarp();
                 tc_fence_after();
                 const int64_t pstride = (int64_t)im.Wq * 2 * im.Hp;   // between planes
                 const int64_t bstride = (int64_t)im.Wq * 16;          // between 8-row blocks
@@ -915,6 +901,15 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (warp == 15 && lane == 0) {
+        // Am copies issued but not waited for (after a stop) land before shared memory is
+        // released; copy i went to buffer i % kAmBufs as its (i / kAmBufs)-th use
+        const int issued = max(*issued_s, min(kAmBufs, njobs_row));
+        for (int i = *landed_s; i < issued; ++i) {
+            volatile int dummy = 0;
+            mbar_wait(&a_full[i % kAmBufs], (i / kAmBufs) & 1, &dummy);
+        }
+    }
     if (warp == 0) tmem_dealloc(tmem, 128);
 }
 
