@@ -957,7 +957,7 @@ __global__ void k_build_tstrip(uint16_t *__restrict__ Q, int ncores, int off, in
 // and store complex64.
 constexpr int kMtColAcc = 2;       // TMEM accumulators (128 columns each)
 constexpr int kMtColEpiWarps = 16;
-constexpr int kMtColMaxStages = 2;   // operand stages of the modulated-tap column kernel
+constexpr int kMtColMaxStages = 3;   // operand stages of the modulated-tap column kernel
 constexpr int kMtColThreads = 32 * (kMtColEpiWarps + 2);   // + the MMA warp and the copy warp
 
 struct MtColSmem {
@@ -1022,6 +1022,7 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
     volatile int *issued_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 8);   // jobs whose copies were issued
     volatile int *landed_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 12);  // jobs whose copies were waited for
+    volatile int *stage_k = reinterpret_cast<volatile int *>(sm + L.misc_off + 16);   // [kMtColMaxStages] K of the staged job
     const uint32_t ahalf = 128u * a.col_kmax * 2;                 // one A operand (hi, or lo under split)
     const uint32_t obuf = np * ahalf;                             // the A operands of a stage
     const uint32_t gbuf = np * tstrip_bytes(a.col_kmax, 2 * TYC); // the B strips of a stage
@@ -1066,6 +1067,7 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
         // split) and the correction operands.  A warp of its own, so that issuing the copies
         // overlaps the MMA warp's issue of the previous job's products.
         if (lane == 0) {
+            if (a.imgs == nullptr) prefetch_tmap(&a.tmA[0]);
             int j = 0;
             for (; j < njobs; ++j) {
                 if (*abort_s) break;
@@ -1079,6 +1081,7 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
                 const TcFreqDev f = D.freqs[u.s];
                 const int nkb = f.Kcol / 64;
                 const uint32_t bbytes = tstrip_bytes(f.Kcol, 2 * TYC);
+                stage_k[st] = f.Kcol;   // read by the MMA thread after the stage's barrier completes
                 mbar_arrive_expect_tx(&ab_full[st], np * (nkb * 16384u + bbytes) + 4u * kCorrBlockHalfs);
                 const int yb0 = (a.Lpad + w.y0 - f.R8) >> 3;
                 const uint32_t dst = smem_u32(sA + st * obuf);
@@ -1107,11 +1110,11 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
             for (int j = 0; j < njobs; ++j) {
                 if (*abort_s) break;
                 const int st = j % NST, acc = j & 1;
-                const TcFreqDev f = D.freqs[D.units[item(j).unit].s];
                 if (!mbar_wait(&ab_full[st], (j / NST) & 1, abort_s)) {
                     fail_status(a.status, abort_s, 36);
                     break;
                 }
+                const int Kcol = stage_k[st];
                 landed = j + 1;
                 if (j >= kMtColAcc && !mbar_wait(&tmem_empty[acc], ((j - kMtColAcc) >> 1) & 1, abort_s)) {
                     fail_status(a.status, abort_s, 37);
@@ -1119,8 +1122,8 @@ __global__ void __launch_bounds__(kMtColThreads, 1) k_gabor_tc_cols_mt(const __g
                 }
                 tc_fence_after();
                 const uint32_t a0 = smem_u32(sA + st * obuf), b0 = smem_u32(sB + st * gbuf);
-                const uint32_t a0l = a0 + ahalf, b0l = b0 + tstrip_bytes(f.Kcol, 2 * TYC);
-                for (int kb = 0; kb < f.Kcol / 64; ++kb)
+                const uint32_t a0l = a0 + ahalf, b0l = b0 + tstrip_bytes(Kcol, 2 * TYC);
+                for (int kb = 0; kb < Kcol / 64; ++kb)
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
                         const uint32_t ao = kb * 16384 + kk * 4096;
