@@ -30,7 +30,7 @@ if ROOT not in sys.path:
 METRIC = "Gabor bank pixel·filter outputs/s, plain vs TC at ≤2e-3 rel err; serve p99 ms"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_gabor_fp32 launch on this
 # workload from an ncu capture of the current kernel; None once the kernel changes.
-K_GABOR_FP32_TRAFFIC = 143906304   # 4382208 read + 139524096 written (autotuned: k_gabor_fp32<0, 1, 8>)
+K_GABOR_FP32_TRAFFIC = 143840768   # 4390912 read + 139449856 written (autotuned k_gabor_fp32<0, 1, 8>, one ncu pass)
 UNIT = "outputs/s"
 H = W = 1024
 
@@ -276,20 +276,44 @@ def hbm_peak_gbs():
         return 6800.0, "fallback"
 
 
-def time_device(torch, fn, steps, warmup, flush, stream):
+class nvtx_range:
+    """An NVTX push/pop range around a leg's warm-up and timed steps, so that a profiler can
+    select the launches of one leg (`ncu --nvtx --nvtx-include "<name>/"`); a no-op where
+    torch has no NVTX."""
+
+    def __init__(self, torch, name):
+        self.nvtx = getattr(torch.cuda, "nvtx", None) if name else None
+        self.name = name
+
+    def __enter__(self):
+        if self.nvtx is not None:
+            try:
+                self.nvtx.range_push(self.name)
+            except Exception:
+                self.nvtx = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.nvtx is not None:
+            self.nvtx.range_pop()
+        return False
+
+
+def time_device(torch, fn, steps, warmup, flush, stream, name=None):
     """CUDA-event time of fn() per step (ms), L2 flushed before each step, after warm-up."""
-    for _ in range(max(3, warmup)):
-        fn()
-    torch.cuda.synchronize()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    for k in range(steps):
-        if flush is not None:
-            flush.zero_()
-        starts[k].record(stream)
-        fn()
-        ends[k].record(stream)
-    torch.cuda.synchronize()
+    with nvtx_range(torch, name):
+        for _ in range(max(3, warmup)):
+            fn()
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for k in range(steps):
+            if flush is not None:
+                flush.zero_()
+            starts[k].record(stream)
+            fn()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in zip(starts, ends)]
 
 
@@ -334,7 +358,8 @@ def bank_tc_leg(torch, d_img, thetas, omegas, sigmas, ref_out, n_out, steps, war
             from paper_1704_05231_gb300.tune import autotune
             tiles = autotune(gbk, d_img, steps=3)["tc_tiles"]
             out = torch.empty_like(ref)
-            ms = statistics.mean(time_device(torch, lambda: gbk.filter(d_img, out), steps, warmup, flush, stream))
+            ms = statistics.mean(time_device(torch, lambda: gbk.filter(d_img, out), steps, warmup, flush, stream,
+                                             name=prec))
             gbk.device_status()
             bytes_ = n_out * 8 + H * W * 4
             res[prec] = {"value": n_out / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "tc_tiles": tiles,
@@ -380,7 +405,8 @@ def sdft_leg(torch, steps, warmup, flush, stream):
     for prec in ("fp32", "fp16_tc", "bf16_tc"):
         gbk = GaborBank(precision=prec)
         out = torch.empty((16, 16, Hs, Ws), dtype=torch.complex64, device="cuda")
-        ms = statistics.mean(time_device(torch, lambda: gbk.sdft(img, 4.0, 16, out=out), steps, warmup, flush, stream))
+        ms = statistics.mean(time_device(torch, lambda: gbk.sdft(img, 4.0, 16, out=out), steps, warmup, flush, stream,
+                                         name="sdft_" + prec))
         gbk.device_status()
         ent = {"value": n_out / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
                "roofline": {"bound": "hbm", "achieved": bytes_ / (ms * 1e-3) / 1e9, "peak": peak,
@@ -456,7 +482,8 @@ def iir_leg(torch, d_img, thetas, omegas, sigmas, fir_out, steps, warmup, flush,
     res = {}
     gbk = GaborBank(thetas, omegas, sigmas, smoother="iir", max_shape=(H, W))
     out = torch.empty(gbk.out_shape(H, W), dtype=torch.complex64, device="cuda")
-    ms = statistics.mean(time_device(torch, lambda: gbk.filter(d_img, out), steps, warmup, flush, stream))
+    ms = statistics.mean(time_device(torch, lambda: gbk.filter(d_img, out), steps, warmup, flush, stream,
+                                     name="iir_bank"))
     n_out = len(thetas) * len(omegas) * H * W
     ser = []
     for s in range(len(omegas)):
@@ -472,7 +499,8 @@ def iir_leg(torch, d_img, thetas, omegas, sigmas, fir_out, steps, warmup, flush,
     th, om, sg = synth.octave_bank(8, 5)
     gbk = GaborBank(th, om, sg, smoother="iir", max_shape=(2048, 2048))
     outs = [torch.empty(gbk.out_shape(h, w), dtype=torch.complex64, device="cuda") for h, w in shapes]
-    ms = statistics.mean(time_device(torch, lambda: gbk.filter_batch(imgs, outs), min(steps, 3), 3, flush, stream))
+    ms = statistics.mean(time_device(torch, lambda: gbk.filter_batch(imgs, outs), min(steps, 3), 3, flush, stream,
+                                     name="iir_batch"))
     n_out = sum(len(th) * len(om) * h * w for h, w in shapes)
     res["batch_64"] = {"ms_per_step": ms, "value": n_out / (ms * 1e-3), "unit": UNIT, "launches_per_step": 2 * len(shapes)}
     gbk.close()
@@ -689,6 +717,7 @@ def run_ours(args):
         from paper_1704_05231_gb300.tune import autotune
         tuned = autotune(gbk, d_img, steps=3)
         tiling, ctas = tuned["tiling"], tuned["ctas"]
+    headline = nvtx_range(torch, "fp32_bank").__enter__()
     for _ in range(max(3, args.warmup)):
         gbk.filter(d_img, out)
     torch.cuda.synchronize()
@@ -710,6 +739,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     wall = time.perf_counter() - t0
+    headline.__exit__()
     clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = statistics.mean(step_ms)
