@@ -525,9 +525,16 @@ int64_t tc_corr_bytes(const gabor_bank *h, int H, int W)
 {
     return (int64_t)h->units.size() * (((int64_t)W + 63) / 64 + ((int64_t)H + 31) / 32) * kCorrBlockHalfs * 2;
 }
+// the row pass's operand image (modulated taps under the zero rule): H rows of W rounded up
+// to 8 FP16 elements, twice (hi, lo) under BF16
+int64_t tc_pimg_pitch(int W) { return (W + 7) / 8 * 8; }
+int64_t tc_pimg_bytes(const gabor_bank *h, int H, int W)
+{
+    return ((int64_t)(h->prec == GB_BF16_TC ? 2 : 1) * H * tc_pimg_pitch(W) * 2 + 255) / 256 * 256;
+}
 int64_t tc_ws_bytes(const gabor_bank *h, int H, int W)
 {
-    return tc_sig_bytes(h, H, W) + tc_ones_bytes(h, H, W) + tc_corr_bytes(h, H, W);
+    return tc_sig_bytes(h, H, W) + tc_ones_bytes(h, H, W) + tc_corr_bytes(h, H, W) + tc_pimg_bytes(h, H, W);
 }
 
 gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
@@ -631,6 +638,24 @@ gb_status ensure_tc(gabor_bank *h, cudaStream_t st)
 }
 
 
+// TMA map of the row pass's operand image (p_tma): W x H x (1, or 2 for hi and lo) 16-bit
+// elements, boxes of 64 columns (128 bytes) x TY rows x 1 with the 128-byte swizzle (they land
+// as the SW128 K-major P blocks the MMA reads), zeros outside the image.
+gb_status encode_pimg_map(CUtensorMap *m, const uint16_t *pimg, int H, int W, int64_t pq, int split, int ty)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return fail(GB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(split ? 2 : 1)};
+    const cuuint64_t strides[2] = {(cuuint64_t)pq * 2, (cuuint64_t)pq * 2 * H};
+    const cuuint32_t box[3] = {64, (cuuint32_t)ty, 1}, elem[3] = {1, 1, 1};
+    const CUresult r = enc(m, split ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+                           const_cast<uint16_t *>(pimg), dims, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(GB_ERR_CUDA, "cuTensorMapEncodeTiled failed for the row operand image");
+    return GB_OK;
+}
+
 // TMA maps of the blocked intermediate [signal][Hp / 8][W][8] for the column pass, as a 4-D
 // tensor (8 rows of a block, W columns, signals, Hp / 8 blocks; FP16): boxes of 8 x 32 x 4 x 8
 // and 8 x 64 x 2 x 8, no swizzle (they land as the MMA's K-major core matrices), zeros beyond
@@ -654,6 +679,7 @@ gb_status encode_tc_maps(TcBankArgs &a, int nsig, bool mt)
                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(GB_ERR_CUDA, "cuTensorMapEncodeTiled failed for the intermediate");
+        if (a.p_tma) return encode_pimg_map(&a.tmA[1], a.pimg, a.H, a.W, a.pq, a.split, a.row_ty);
         return GB_OK;
     }
     for (int k = 0; k < 2; ++k) {
@@ -725,6 +751,7 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     float2 *onesB = onesA + (int64_t)h->units.size() * W;
     uint16_t *corrA = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(onesA) + tc_ones_bytes(h, H, W));
     uint16_t *corrB = corrA + (int64_t)h->units.size() * ((W + 63) / 64) * kCorrBlockHalfs;
+    uint16_t *pimg = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(corrA) + tc_corr_bytes(h, H, W));
     if (zero_halo && need > 0) {
         // Layout [signal][Hp / 8][W][8].  The row pass writes rows [Lpad, Lpad + round_up(H, TY))
         // of every signal (zeros below row H); the column pass reads up to R8 rows beyond, so
@@ -784,6 +811,9 @@ gb_status filter_device_tc(gabor_bank *h, const float *d_img, int H, int W, int6
     a.nplanes = (int)(h->omega.size() * h->theta.size());
     a.row_y0 = -ypad;
     a.split = split;
+    a.p_tma = row_mt && h->boundary == kBoundaryZero ? 1 : 0;
+    a.pimg = pimg;
+    a.pq = tc_pimg_pitch(W);
     GB_TRY(encode_tc_maps(a, row_mt ? (split ? 2 : 1) * (int)h->units.size() : h->tc_nsig, row_mt));
     GB_CU(launch_gabor_tc(a, h->sm_count, st));
     return GB_OK;
@@ -819,7 +849,7 @@ gb_status filter_batch_tc(gabor_bank *h, int n, const float *const *d_imgs, cons
     const int nplane = (split ? 2 : 1) * nu;   // a plane of Re J, Im J per unit (hi and lo under BF16)
     // workspace: intermediates, F[1] tables, partial keys, centres (each 256-byte aligned)
     auto al = [](int64_t b) { return (b + 255) / 256 * 256; };
-    std::vector<int64_t> off_sig(n), off_ones(n), off_corr(n), Hp(n);
+    std::vector<int64_t> off_sig(n), off_ones(n), off_corr(n), off_pimg(n), Hp(n);
     int64_t total = 0;
     for (int i = 0; i < n; ++i) {
         Hp[i] = (int64_t)(H[i] + 63) / 64 * 64 + 2 * Lpad;
@@ -833,6 +863,11 @@ gb_status filter_batch_tc(gabor_bank *h, int n, const float *const *d_imgs, cons
     for (int i = 0; i < n; ++i) {
         off_corr[i] = total;
         total += al((int64_t)nu * (((int64_t)W[i] + 63) / 64 + ((int64_t)H[i] + 31) / 32) * kCorrBlockHalfs * 2);
+    }
+    const bool p_tma = h->boundary == kBoundaryZero;
+    for (int i = 0; i < n; ++i) {
+        off_pimg[i] = total;
+        if (p_tma) total += tc_pimg_bytes(h, H[i], W[i]);
     }
     const int64_t off_parts = total;
     total += al((int64_t)n * kMmParts * 2 * sizeof(unsigned));
@@ -865,12 +900,12 @@ gb_status filter_batch_tc(gabor_bank *h, int n, const float *const *d_imgs, cons
             dfree(h->d_tcb_maps);
             h->tcb_cap = 0;
             GB_TRY(dalloc(&h->d_tcb_imgs, (size_t)n));
-            GB_TRY(dalloc(&h->d_tcb_maps, (size_t)n));
+            GB_TRY(dalloc(&h->d_tcb_maps, (size_t)2 * n));   // intermediates, then operand images
             h->tcb_cap = n;
         }
         unsigned char *ws = h->d_tcb_ws;
         std::vector<TcImgDev> imgs(n);
-        std::vector<CUtensorMap> maps(n);
+        std::vector<CUtensorMap> maps(2 * (size_t)n);
         PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
         if (!enc) return fail(GB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
         for (int i = 0; i < n; ++i) {
@@ -887,6 +922,9 @@ gb_status filter_batch_tc(gabor_bank *h, int n, const float *const *d_imgs, cons
             d.onesB = d.onesA + (int64_t)nu * W[i];
             d.corrA = reinterpret_cast<uint16_t *>(ws + off_corr[i]);
             d.corrB = d.corrA + (int64_t)nu * ((W[i] + 63) / 64) * kCorrBlockHalfs;
+            d.pimg = reinterpret_cast<uint16_t *>(ws + off_pimg[i]);
+            d.pq = tc_pimg_pitch(W[i]);
+            if (p_tma) GB_TRY(encode_pimg_map(&maps[n + i], d.pimg, H[i], W[i], d.pq, split, ty));
             // the intermediate's planes as in the single-image call: boxes of 256 elements (16
             // columns x both parts x 8 rows) x 4 column groups x 8 blocks
             d.Wq = tc_wq(W[i]);
@@ -932,7 +970,7 @@ gb_status filter_batch_tc(gabor_bank *h, int n, const float *const *d_imgs, cons
             h->tcb_cols_cap = cols.size();
         }
         GB_CU(cudaMemcpy(h->d_tcb_imgs, imgs.data(), n * sizeof(TcImgDev), cudaMemcpyHostToDevice));
-        GB_CU(cudaMemcpy(h->d_tcb_maps, maps.data(), n * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+        GB_CU(cudaMemcpy(h->d_tcb_maps, maps.data(), 2 * (size_t)n * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
         if (!rows.empty())
             GB_CU(cudaMemcpy(h->d_tcb_rows, rows.data(), rows.size() * sizeof(int4), cudaMemcpyHostToDevice));
         if (!cols.empty())
@@ -976,6 +1014,7 @@ gb_status filter_batch_tc(gabor_bank *h, int n, const float *const *d_imgs, cons
     a.n_col = h->tcb_ncol;
     a.nimg = n;
     a.split = split;
+    a.p_tma = p_tma ? 1 : 0;
     GB_CU(launch_gabor_tc_batch(a, h->sm_count, st));
     *done = true;
     return GB_OK;

@@ -193,16 +193,17 @@ struct TcImgView {
     const uint16_t *corrA, *corrB;
     const CUtensorMap *tm;
     int Wq;
+    const CUtensorMap *tmP;   // the row pass's operand image (p_tma)
 };
 __device__ __forceinline__ TcImgView tc_img(const TcBankArgs &a, int i)
 {
     if (a.imgs) {
         const TcImgDev d = a.imgs[i];
         return TcImgView{d.img, d.pitch, d.H, d.W, d.out, d.plane, d.sig, d.Hp, d.onesA, d.onesB, d.corrA, d.corrB,
-                         a.tmaps + i, d.Wq};
+                         a.tmaps + i, d.Wq, a.tmaps + a.nimg + i};
     }
     return TcImgView{a.img, a.pitch, a.H, a.W, a.out, a.plane, a.sig, a.Hp, a.onesA, a.onesB, a.corrA, a.corrB,
-                     &a.tmA[0], a.Wq};
+                     &a.tmA[0], a.Wq, &a.tmA[1]};
 }
 __device__ __forceinline__ int64_t tc_out_offset(const TcBankArgs &a, const TcImgView &im, int p, int y, int x)
 {
@@ -568,14 +569,15 @@ __global__ void __launch_bounds__(512, 1) k_gabor_tc_rows(const __grid_constant_
 // taps, no per-unit demodulated copy of the patch:
 //
 //   D[(x, re|im)][r] = sum_k Am[(x, re|im)][k] P[r][k],
-//   Am[(x, re)][k] = S(d) cos(w^c d),  Am[(x, im)][k] = -S(d) sin(w^c d),  d = k - x - R,
-//   P[r][k] = (f(y0 + r, x0 - R + k) - c) 2^-e
+//   Am[(x, re)][k] = S(d) cos(w^c d),  Am[(x, im)][k] = -S(d) sin(w^c d),  d = k - x - R8,
+//   P[r][k] = (f(y0 + r, x0 - R8 + k) - c) 2^-e          (R8 = R rounded up to 8)
 //
 // -> Re J, Im J of 64 columns x TY rows of one unit (operand row n = 2 x + re|im).  Per item
-// (frequency, tile): producers (warps 8-15) stage the patch once and convert it to the FP16
-// operand P; the MMA thread (256) brings each unit's Am (built once per plan) by one bulk copy
-// into one of two buffers and issues the MMA; 8 epilogue warps (two per lane quarter) store J
-// itself, two signals per unit, for the modulated-tap column pass.
+// (frequency, tile): P once, either as TMA boxes of the operand image that k_ones wrote (zero
+// rule; the window starts at x0 - R8, a multiple of 8 elements, as a tiled copy needs) or built
+// by producer warps 8-14 from the image; the MMA thread brings each unit's Am (built once per
+// plan) by one bulk copy into one of three buffers and issues the MMAs; 8 epilogue warps (two
+// per lane quarter) store J itself, two signals per unit, for the modulated-tap column pass.
 constexpr int kMtTileX = 64;     // output columns per item (MMA M = 2 x 64)
 constexpr int kMtEpiWarps = 8;
 
@@ -645,6 +647,8 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 4);
     volatile int *issued_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 8);   // Am copies issued
     volatile int *landed_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 12);  // Am copies waited for
+    volatile int *p_issued_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 16);  // P loads issued (TMA)
+    volatile int *p_landed_s = reinterpret_cast<volatile int *>(sm + L.misc_off + 20);  // P loads waited for
     const TcDesc D = load_desc(a, sm + L.desc_off);
     constexpr uint32_t np = SPLIT ? 2u : 1u;
     const uint32_t abuf = np * tstrip_bytes(a.row_kmax, 128);   // an A buffer (hi, lo strips)
@@ -664,6 +668,8 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
         mbar_init(drain, 1);
         *issued_s = 0;
         *landed_s = 0;
+        *p_issued_s = 0;
+        *p_landed_s = 0;
         *abort_s = 0;
         mbar_fence_init();
     }
@@ -699,7 +705,7 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
         // for its P (p_full) and release it (p_empty).
         if (lane == 0) {
             const int nu = a.nu_f;
-            int landed = 0;
+            int landed = 0, p_landed = 0;
             bool ok = true;
             for (int jq = 0; jq < kAmBufs && jq < njobs_row; ++jq) issue_am(jq);
             for (int nitem = 0; nitem < my_items && ok; ++nitem) {
@@ -707,6 +713,7 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
                 const int K = D.freqs[w.s].Kmt;
                 const int pb = nitem & 1;
                 if (ok) ok = mbar_wait(&p_full[pb], (nitem >> 1) & 1, abort_s);   // this item's P
+                if (ok) p_landed = nitem + 1;
                 for (int q = 0; q < nu && ok; ++q) {
                     const int jq = nitem * nu + q, b = jq & 1, ab = jq % kAmBufs;
                     ok = mbar_wait(&a_full[ab], (jq / kAmBufs) & 1, abort_s);
@@ -738,11 +745,38 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
                 mbar_wait(drain, 0, &dummy);
             }
             *landed_s = landed;
+            *p_landed_s = p_landed;
+        }
+    } else if (warp >= kMtEpiWarps && a.p_tma) {
+        // -------------------------------------------------------------- P by TMA (warp 8, lane 0)
+        // The K / 64 boxes of 64 columns x TY rows (hi, then lo under split) of the operand image
+        // at (x0 - R8 + 64 kb, y0) into buffer it & 1, once the MMAs of item it - 2 are done;
+        // zeros outside the image, as the zero rule wants.
+        if (warp == kMtEpiWarps && lane == 0) {
+            int nitem = 0;
+            for (int it = blockIdx.x; it < nitems && !*abort_s; it += gridDim.x, ++nitem) {
+                const RowItem w = row_item_mt(a, D, it);
+                const TcImgView im = tc_img(a, w.img);
+                const TcFreqDev f = D.freqs[w.s];
+                const int pb = nitem & 1, nkb = f.Kmt / 64;
+                if (nitem < 2) prefetch_tmap(im.tmP);
+                if (nitem >= 2 && !mbar_wait(&p_empty[pb], ((nitem - 2) >> 1) & 1, abort_s)) {
+                    fail_status(a.status, abort_s, 26);
+                    break;
+                }
+                mbar_arrive_expect_tx(&p_full[pb], np * (uint32_t)nkb * TY * 128u);
+                const uint32_t dP = smem_u32(sP + pb * pbuf);
+                for (uint32_t z = 0; z < np; ++z)
+                    for (int kb = 0; kb < nkb; ++kb)
+                        tma_load_3d(dP + z * plo + (uint32_t)kb * TY * 128u, im.tmP, w.x0 - f.R8 + 64 * kb, w.y0,
+                                    (int)z, &p_full[pb]);
+                *p_issued_s = nitem + 1;
+            }
         }
     } else if (warp >= kMtEpiWarps) {
         // -------------------------------------------------------------- producers (warps 8-14)
         // P of item it into buffer it's parity, straight from the image: P[r][k] =
-        // (f(x0 - R + k, y0 + r) - c) 2^-e in FP16 (zero beyond the window, and outside the image
+        // (f(x0 - R8 + k, y0 + r) - c) 2^-e in FP16 (zero beyond the window, and outside the image
         // under the zero rule), 8 k per 16-byte chunk of the swizzled K-major layout; a thread
         // takes chunks k8 = idx % (K / 8) of row r = idx / (K / 8), so a warp reads consecutive
         // 32-byte runs of image rows.  The buffer is free once the MMAs of item it - 2 are done.
@@ -759,8 +793,8 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
             tc_centre(a, w.img, cen, e);
             const float sc = ldexpf(1.f, -e);
             const TcFreqDev f = D.freqs[w.s];
-            const int R = f.R, K = f.Kmt, nk8 = K / 8;
-            const int ncols = kMtTileX + 2 * R;
+            const int R = f.R, R8 = f.R8, K = f.Kmt, nk8 = K / 8;
+            const int ncols = kMtTileX + R8 + R;
             const int pb = nitem & 1;
             bool failed = nitem >= 2 && !mbar_wait(&p_empty[pb], ((nitem - 2) >> 1) & 1, abort_s);
             if (named_barrier_or(1, NP, failed)) {
@@ -778,7 +812,7 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
                 for (int uu = 0; uu < kU; ++uu) {
                     const int idx = base + uu * NP;
                     const int r = idx / nk8, k0 = 8 * (idx - r * nk8);
-                    const int y = y0 + r, gx0 = x0 - R + k0;
+                    const int y = y0 + r, gx0 = x0 - R8 + k0;
                     const int yy = zero ? y : ext_coord(y, im.H, a.bmode);
                     const bool yok = idx < nchunks && (!zero || (y >= 0 && y < im.H));
                     const float *src = im.img + (int64_t)(yok ? yy : 0) * im.pitch;
@@ -910,13 +944,20 @@ __global__ void __launch_bounds__(512, 2) k_gabor_tc_rows_mt(const __grid_consta
             mbar_wait(&a_full[i % kAmBufs], (i / kAmBufs) & 1, &dummy);
         }
     }
+    if (a.p_tma && warp == kMtEpiWarps && lane == 0) {
+        // the same for the P loads: item i's went to buffer i & 1 as its (i / 2)-th use
+        for (int i = *p_landed_s; i < *p_issued_s; ++i) {
+            volatile int dummy = 0;
+            mbar_wait(&p_full[i & 1], (i >> 1) & 1, &dummy);
+        }
+    }
     if (warp == 0) tmem_dealloc(tmem, 128);
 }
 
 // Strip of a modulated Toeplitz operand (see tstrip_cores): core j, row r, element c holds
 // S(d) (cos, -sin)(w d) 2^sB for row part r & 1, d = 4 j + c + r / 2 - off, zero outside
-// |d| <= R; FP64, rounded to FP16.  Row pass (Am): off = 63 + R, w = w^c (rows x of the 64-
-// column tile backwards, k the input column from x0 - R on).  Column pass (Gm): off =
+// |d| <= R; FP64, rounded to FP16.  Row pass (Am): off = 63 + R8, w = w^c (rows x of the 64-
+// column tile backwards, k the input column from x0 - R8 on).  Column pass (Gm): off =
 // TYC - 1 + R8, w = w^s (rows y of the job backwards, l the window row from y0 - R8 on).
 // split = 1: BF16 instead, hi = bf16(v) in Q[0 .. n) and lo = bf16(v - hi) in Q[n .. 2 n).
 __global__ void k_build_tstrip(uint16_t *__restrict__ Q, int ncores, int off, int R, double sigma, double w, int sB,
@@ -1680,6 +1721,45 @@ __device__ void corr_rows(const TcBankArgs &a, const TcUnitDev *__restrict__ uni
     }
 }
 
+// The row pass's operand image (p_tma): P(x, y) = (f(x, y) - c) 2^-e as FP16, or as BF16 hi
+// rows followed by H lo rows (split), pq elements per row; 8 columns per thread of the
+// grid-stride loop (columns from W to the next multiple of 8 hold zeros).  The same arithmetic
+// as the row kernel's producers, so both ways of building P give the same operand.
+__device__ void operand_image(const float *__restrict__ img, int64_t pitch, int H, int W, float c, int e,
+                              uint16_t *__restrict__ P, int64_t pq, int split, int64_t gtid, int64_t gstride)
+{
+    const float sc = ldexpf(1.f, -e);
+    const int nx8 = (W + 7) / 8;
+    const int64_t n = (int64_t)H * nx8;
+    for (int64_t i = gtid; i < n; i += gstride) {
+        const int y = (int)(i / nx8), x0 = 8 * (int)(i - (int64_t)y * nx8);
+        const float *src = img + (int64_t)y * pitch + x0;
+        float v[8];
+        if (x0 + 8 <= W && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+            const float4 p = __ldg(reinterpret_cast<const float4 *>(src));
+            const float4 q = __ldg(reinterpret_cast<const float4 *>(src + 4));
+            v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w;
+            v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
+        } else {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = x0 + t < W ? __ldg(src + t) : c;   // c: 0 after - c
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = (v[t] - c) * sc;
+        uint16_t *d = P + (int64_t)y * pq + x0;
+        if (split) {
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) b2split(v[2 * t], v[2 * t + 1], hw[t], lw[t]);
+            *reinterpret_cast<uint4 *>(d) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4 *>(d + (int64_t)H * pq) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        } else {
+            *reinterpret_cast<uint4 *>(d) = make_uint4(h2pack(v[0], v[1]), h2pack(v[2], v[3]), h2pack(v[4], v[5]),
+                                                       h2pack(v[6], v[7]));
+        }
+    }
+}
+
 __global__ void k_ones(const TcBankArgs a, const TcUnitDev *__restrict__ units, const TcFreqDev *__restrict__ freqs,
                        int nunits, float2 *__restrict__ A, float2 *__restrict__ B)
 {
@@ -1705,6 +1785,7 @@ __global__ void k_ones(const TcBankArgs a, const TcUnitDev *__restrict__ units, 
         int e;
         image_centre(a, c, e);
         corr_rows(a, units, freqs, nunits, a.W, a.H, c, a.corrA, a.corrB, gtid, gstride);
+        if (a.p_tma) operand_image(a.img, a.pitch, a.H, a.W, c, e, a.pimg, a.pq, a.split, gtid, gstride);
     }
 }
 
@@ -1730,6 +1811,7 @@ __global__ void k_ones_batch(const TcBankArgs a, const TcUnitDev *__restrict__ u
     pdl_wait();
     // every block reduces the image's partial keys into its centre; block 0 records it
     __shared__ float cen_s;
+    __shared__ int e_s;
     if (threadIdx.x < 32) {
         const unsigned *p = a.mm_part + (int64_t)blockIdx.y * kMmParts * 2;
         unsigned nlo = 0u, hik = 0u;
@@ -1747,11 +1829,13 @@ __global__ void k_ones_batch(const TcBankArgs a, const TcUnitDev *__restrict__ u
             int e;
             centre_of(nlo, hik, c, e);
             cen_s = c;
+            e_s = e;
             if (blockIdx.x == 0) a.img_ce[blockIdx.y] = make_float2(c, (float)e);
         }
     }
     __syncthreads();
     corr_rows(a, units, freqs, nunits, im.W, im.H, cen_s, im.corrA, im.corrB, gtid, gstride);
+    if (a.p_tma) operand_image(im.img, im.pitch, im.H, im.W, cen_s, e_s, im.pimg, im.pq, a.split, gtid, gstride);
 }
 
 __global__ void k_build_toeplitz(uint16_t *__restrict__ B, int rows, int K, int off, int R, double sigma, int sB)
@@ -1849,7 +1933,8 @@ cudaError_t build_gabor_tc_am(uint16_t *Am, int R, double sigma, double wc, int 
     int e = 0;
     frexp(1.0 / (2.5066282746310002 * sigma), &e);
     const int nc = tstrip_cores(gabor_tc_mt_k(R), 128);
-    k_build_tstrip<<<(64 * nc + 255) / 256, 256, 0, st>>>(Am, nc, kMtTileX - 1 + R, R, sigma, wc, -e, split);
+    k_build_tstrip<<<(64 * nc + 255) / 256, 256, 0, st>>>(Am, nc, kMtTileX - 1 + round_up(R, 8), R, sigma, wc, -e,
+                                                            split);
     return cudaGetLastError();
 }
 
@@ -1915,7 +2000,8 @@ cudaError_t launch_gabor_tc(const TcBankArgs &a0, int sm_count, cudaStream_t st)
     if (e0 != cudaSuccess) return e0;
     {
         const int nu = a.nf * a.nu_f;
-        const int64_t n = (int64_t)nu * (a.W + a.H);
+        // threads for the tables, or for the operand image (8 columns each)
+        const int64_t n = std::max<int64_t>((int64_t)nu * (a.W + a.H), a.p_tma ? (int64_t)a.H * ((a.W + 7) / 8) : 0);
         const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4 * sm_count));
         e0 = launch_pdl(k_ones, dim3(blocks), dim3(256), 0, st, a, a.units, a.freqs, nu,
                         const_cast<float2 *>(a.onesA), const_cast<float2 *>(a.onesB));

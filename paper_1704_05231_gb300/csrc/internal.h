@@ -147,6 +147,8 @@ struct TcImgDev {
     const float2 *onesB;   // [unit][H]
     uint16_t *corrA;       // [unit][(W + 63) / 64] and [unit][(H + TYC - 1) / TYC] blocks of
     uint16_t *corrB;       // kCorrBlockHalfs: the correction operands (TcBankArgs)
+    uint16_t *pimg;        // the row pass's operand image (TcBankArgs), pq elements per row
+    int64_t pq;
 };
 constexpr int kMmParts = 64;   // partial min / max words per image of a batch (k_minmax)
 constexpr int kCorrBlockHalfs = 2048;   // one correction operand block: 128 rows x 16 K, 4 KB
@@ -210,7 +212,14 @@ struct TcBankArgs {
     int n_row, n_col, nimg;
     int split;             // 1: BF16 operands as hi + lo pairs (modulated-tap kernels)
     int col_mt_nst;        // operand stages of the modulated-tap column kernel (1 or 2)
-    int pad3_;
+    // p_tma = 1 (modulated taps, zero rule): k_ones writes the row pass's operand image
+    // P = (f - c) 2^-e as FP16 (BF16 hi rows, then lo rows: H rows of pq elements each) and the
+    // row kernel loads its tiles by TMA (map tmA[1], or tmaps[nimg + i] for image i of a batch,
+    // 128-byte swizzle, zeros outside the image); p_tma = 0: the row kernel's producer warps
+    // build P from the image.
+    int p_tma;
+    uint16_t *pimg;
+    int64_t pq;
 };
 struct TcGeometry {
     int R, R8, Krow, Kcol, PW;
