@@ -306,6 +306,8 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
             const bool yin = ext || (y >= 0 && y < im.H);
 #pragma unroll 1
             for (int v = 0; v < (twin ? 2 : 1); ++v) {   // the unit, then its twin
+                // the row's phase, loaded before the convolution so that its latency is hidden
+                const float2 cy = yin ? (v ? u2.phy : u.phy)[y] : make_float2(0.f, 0.f);
                 float2 acc[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
@@ -321,7 +323,6 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
                     acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, 16);
                     acc[j].y += __shfl_xor_sync(0xffffffffu, acc[j].y, 16);
                 }
-                const float2 cy = yin ? (v ? u2.phy : u.phy)[y] : make_float2(0.f, 0.f);
                 float2 *ring = sm.ring2 + (size_t)v * RS * stride + base;
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj) {
@@ -365,21 +366,24 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
         const int oplane = sub ? (twin ? u2.plane_a : u.plane_b) : u.plane_a;
         for (int yb = ybase; yb < nout; yb += ystep) {
             const int slot0 = (c - ys + yb) % RS;
+            // the 8 rows' phases, loaded before the convolution so that their latency is hidden
+            const int jn = nout - yb;
+            const float2 *py = phy + (c + yb);
+            float2 cyv[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) cyv[j] = j < jn ? py[j] : make_float2(0.f, 0.f);
             float2 acc[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
             conv8_ring<float2, kStripW + 1>(sm.ring2 + (size_t)sub * RS * stride + xl, RS, slot0, taps4, nchunks, acc,
                                             tail1);
             if (x < im.W) {
-                // output row c + yb + j: one pointer stepped by the row stride, phases at
-                // immediate offsets
+                // output row c + yb + j: one pointer stepped by the row stride
                 float2 *o = im.out + out_offset(a, oplane, plane, x) + (int64_t)(c + yb) * ystride;
-                const float2 *py = phy + (c + yb);
-                const int jn = nout - yb;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     if (j < jn) {
-                        const float2 cy = py[j];
+                        const float2 cy = cyv[j];
                         const float P = acc[j].x, Q = acc[j].y;
                         // Eq. 7-8 (theta_a) or Eq. 15-16 (pi - theta_a)
                         __stcs(o, make_float2(fmaf(cy.x, P, cy.y * Q), fmaf(cy.y, P, -cy.x * Q)));
