@@ -1079,6 +1079,45 @@ gb_status filter_device_iir(gabor_bank *h, const float *d_img, int H, int W, int
     return GB_OK;
 }
 
+// TMA maps for the FP32 kernel's modulated-tap row loads of one image under the zero rule: per
+// frequency a 2-D map of the image (W x H floats) with boxes of RW x TH (its raw buffer
+// exactly).  Frequencies whose box exceeds the copy unit's 256 x 256 limit, images whose base
+// or row pitch is not 16-byte aligned, and the other schedules keep the async copies.
+gb_status encode_raw_maps(gabor_bank *h, BankArgs &a, const float *d_img, int H, int W, int64_t pitch)
+{
+    a.raw_mask = 0;
+    const int nf = (int)h->freqs.size();
+    if (!a.mtaps || a.pipelined || a.bmode != kBoundaryZero || nf > kMaxRawMaps) return GB_OK;
+    if ((reinterpret_cast<uintptr_t>(d_img) & 15) != 0 || (pitch * 4) % 16 != 0) return GB_OK;
+    std::vector<int64_t> key = {(int64_t)reinterpret_cast<uintptr_t>(d_img), H, W, pitch};
+    for (int s = 0; s < nf; ++s) {
+        key.push_back(h->freqdev[s].RW);
+        key.push_back(h->freqdev[s].TH);
+        key.push_back(h->freqdev[s].mtaps);
+    }
+    if (key != h->raw_key) {
+        PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+        if (!enc) return GB_OK;
+        h->raw_mask = 0;
+        for (int s = 0; s < nf; ++s) {
+            const FreqDev &f = h->freqdev[s];
+            if (!f.mtaps || f.RW > 256 || f.TH > 256) continue;
+            const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+            const cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
+            const cuuint32_t box[2] = {(cuuint32_t)f.RW, (cuuint32_t)f.TH}, elem[2] = {1, 1};
+            const CUresult r = enc(&h->raw_maps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(d_img),
+                                   dims, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r == CUDA_SUCCESS) h->raw_mask |= 1u << s;
+        }
+        h->raw_key = key;
+    }
+    a.raw_mask = h->raw_mask;
+    for (int s = 0; s < nf; ++s)
+        if ((a.raw_mask >> s) & 1u) a.raw_map[s] = h->raw_maps[s];
+    return GB_OK;
+}
+
 // The bank on one device image; only_s >= 0 (FP32 FIR path, plane-major layout, a plan with
 // few enough groups) limits the launch to frequency only_s, whose planes it writes in place.
 gb_status filter_device(gabor_bank *h, const float *d_img, int H, int W, int64_t pitch,
@@ -1106,6 +1145,7 @@ gb_status filter_device(gabor_bank *h, const float *d_img, int H, int W, int64_t
     a.pipelined = h->fp32_pipelined ? 1 : 0;
     a.mtaps = h->fp32_row_form != 1 ? 1 : 0;
     a.ctas = h->fp32_ctas;
+    GB_TRY(encode_raw_maps(h, a, d_img, H, W, pitch));
     GB_CU(launch_gabor_fp32(a, n, h->max_smem, h->sm_count, st));
     return GB_OK;
 }

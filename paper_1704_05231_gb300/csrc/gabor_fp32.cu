@@ -42,16 +42,20 @@ struct Smem {
     float2 *ctaps;   // modulated taps: 2 x (Tpad + 8) complex taps S(t - R) exp(-i omega^c (t - R))
     float2 *phx;     // demodulation form: SW + 1 row phases
     float *taps;     // Tpad + 8 real taps (column pass)
-    uint64_t *bars;  // pipelined schedule: full[2], empty[2]; then the abort flag
+    uint64_t *bars;  // pipelined schedule: full[2], empty[2]; TMA row loads: full[2]; then the
+                     // abort flag
 };
 
 // modulated taps: one set per unit of a (twin) item
 __host__ __device__ __forceinline__ int ctap_count(const FreqDev &f) { return f.mtaps ? 2 * (f.Tpr + 8) : 0; }
 __host__ __device__ __forceinline__ int phx_count(const FreqDev &f) { return f.mtaps ? 0 : f.SW + 1; }
 
-// Every region starts on a 16-byte boundary (RS, TH multiples of 8; SW odd; Tpad + 8 even).
-__device__ __forceinline__ Smem carve(unsigned char *base, const FreqDev &f)
+// Every region starts on a 16-byte boundary (RS, TH multiples of 8; SW odd; Tpad + 8 even); the
+// base on a 128-byte one, and so do the raw buffers under modulated taps (SW = 0, ring rows of
+// 33 float2 pairs, RS and TH multiples of 8, RW a multiple of 4), as TMA writes want.
+__device__ __forceinline__ Smem carve(unsigned char *base0, const FreqDev &f)
 {
+    unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)base0 + 127) & ~(uintptr_t)127);
     Smem s;
     s.ring2 = reinterpret_cast<float2 *>(base);
     s.stage = s.ring2 + (size_t)2 * f.RS * (kStripW + 1);
@@ -69,7 +73,7 @@ size_t gabor_fp32_smem_bytes(const FreqDev &f)
 {
     return (size_t)f.RS * (kStripW + 1) * sizeof(float4) + (size_t)f.TH * f.SW * sizeof(float2) +
            (size_t)2 * f.TH * f.RW * sizeof(float) + (size_t)(ctap_count(f) + phx_count(f)) * sizeof(float2) +
-           (size_t)(f.Tpad + 8) * sizeof(float) + 8 + 4 * sizeof(uint64_t) + 16;
+           (size_t)(f.Tpad + 8) * sizeof(float) + 8 + 4 * sizeof(uint64_t) + 16 + 128;
 }
 
 // Dynamic shared memory one CTA may take when `ctas` CTAs share an SM (228 KB per SM, 1 KB
@@ -171,6 +175,18 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
 
     uint64_t *full = sm.bars, *empty = sm.bars + 2;   // pipelined hand-over, per ring half
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm.bars + 4);
+    // row blocks by TMA: boxes of RW columns from x0 - Rw (a multiple of 4 floats, 16 bytes, as a
+    // tiled copy needs) x TH rows, zeros outside the image; completion on sm.bars[b & 1]
+    const bool rtma = !PIPE && MT && a.imgs == nullptr && ((a.raw_mask >> u.s) & 1u);
+    if (rtma) {
+        if (tid == 0) {
+            mbar_init(&sm.bars[0], 1);
+            mbar_init(&sm.bars[1], 1);
+            *abort_s = 0;
+            mbar_fence_init();
+        }
+        __syncthreads();
+    }
     if (PIPE && tid == 0) {
         mbar_init(&full[0], kRowWarps * 32);
         mbar_init(&full[1], kRowWarps * 32);
@@ -191,9 +207,11 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
             const float g = in ? f.taps[t] : 0.f;
             sm.ctaps[i] = make_float2(g * ph.x, -(g * ph.y));
         }
-        // raw columns past the halo are read (by zero taps) and never copied: zero them
+        // raw columns past the halo are read (by zero taps) and never copied: zero them (the
+        // TMA boxes cover them)
         const int tail = RW - ncols;
-        for (int i = tid; i < 2 * TH * tail; i += kThreadsCta) sm.raw[(size_t)(i / tail) * RW + ncols + i % tail] = 0.f;
+        if (!rtma)
+            for (int i = tid; i < 2 * TH * tail; i += kThreadsCta) sm.raw[(size_t)(i / tail) * RW + ncols + i % tail] = 0.f;
     } else {
         // Demodulation phases at the staged positions (beyond the image only for non-zero
         // rules, whose extended samples are demodulated at their own positions).
@@ -226,6 +244,14 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
         int start, n;
         block_rows(b, start, n);
         float *dst = sm.raw + (size_t)(b & 1) * TH * RW;
+        if (rtma) {
+            if (tid == 0) {
+                fence_proxy_async_smem();   // the generic reads of this buffer's last block precede the copy
+                mbar_arrive_expect_tx(&sm.bars[b & 1], (uint32_t)TH * RW * 4u);
+                tma_load_2d(smem_u32(dst), &a.raw_map[u.s], x0 - Rw, start, &sm.bars[b & 1]);
+            }
+            return;
+        }
         if (!ext) {
             // strips whose window lies inside the image: 16-byte copies for rows that start on
             // a 16-byte boundary (raw rows do: RW and x0 - Rw are multiples of 4 under
@@ -398,8 +424,21 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
     // The demodulation form reads the raw buffer before its own barrier, so block b + 1 can
     // be issued before it; the modulated-tap form reads raw rows until the end of its pass, so
     // block b + 1 (which refills the buffer of block b - 1) is issued after the barrier.
-    auto advance = [&](int b) {
-        if (MT) {
+    // Returns false when a TMA wait gave up (every thread of the CTA alike).
+    auto advance = [&](int b) -> bool {
+        if (rtma) {
+            const bool ok = mbar_wait(&sm.bars[b & 1], (b >> 1) & 1, abort_s);
+            if (__syncthreads_or(!ok)) {   // raw block b landed everywhere, or a wait gave up
+                if (tid == 0) {
+                    // the copy of block b lands before the CTA moves on; report the stop
+                    volatile int dummy = 0;
+                    mbar_wait(&sm.bars[b & 1], (b >> 1) & 1, &dummy);
+                    if (a.status) atomicExch(a.status, 33);
+                }
+                return false;
+            }
+            if (b + 1 < nblocks) issue(b + 1);
+        } else if (MT) {
             cp_async_wait<0>();
             sync_rows();   // raw block b visible; the row pass of block b - 1 is done
             if (b + 1 < nblocks) issue(b + 1);
@@ -413,6 +452,7 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
             sync_rows();   // raw block b visible; previous stage / ring readers done
         }
         row_pass(b);
+        return true;
     };
 
     if (!PIPE) {
@@ -420,7 +460,8 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
         int b = 0;
         for (int k = 0; k < nch; ++k) {
             const int last = (k == 0) ? npro : npro + k;   // blocks [b, last) feed chunk k
-            for (; b < last; ++b) advance(b);
+            for (; b < last; ++b)
+                if (!advance(b)) return false;
             __syncthreads();       // ring rows of chunk k complete
             const int c = ys + k * TH;
             col_pass(c, min(TH, ye - c));
@@ -441,7 +482,7 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
                 break;
             }
             const int last = (k == 0) ? npro : npro + k;
-            for (; b < last; ++b) advance(b);
+            for (; b < last; ++b) advance(b);   // async copies: never gives up
             mbar_arrive(&full[k & 1]);   // this thread's ring rows of chunk k are written
         }
         cp_async_wait<0>();
@@ -492,10 +533,10 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_gabor_fp32(const __grid_co
         const bool ok = gabor_fp32_item<PIPE, MT, NW>(a, it, smem_raw);
         // shared memory is reused by the next item
         const bool failed = __syncthreads_or(!ok);
-        if (PIPE && threadIdx.x == 0) {
-            const FreqDev &f = a.freqs[a.units[it.unit].s];
-            uint64_t *bars = carve(smem_raw, f).bars;
-            for (int i = 0; i < 4; ++i) mbar_inval(bars + i);
+        const int s = a.units[it.unit].s;
+        if ((PIPE || (MT && a.imgs == nullptr && ((a.raw_mask >> s) & 1u))) && threadIdx.x == 0) {
+            uint64_t *bars = carve(smem_raw, a.freqs[s]).bars;
+            for (int i = 0; i < (PIPE ? 4 : 2); ++i) mbar_inval(bars + i);
         }
         if (failed) break;
     }

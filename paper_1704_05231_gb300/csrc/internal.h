@@ -93,6 +93,7 @@ struct ItemGroup {
     int ustride;        // units between consecutive items' units (2: twin items)
 };
 constexpr int kMaxGroups = 64;
+constexpr int kMaxRawMaps = 8;   // frequencies whose FP32 row loads can go by TMA
 
 // Arguments of the fused FP32 bank kernel (one launch covers every frequency).  Work items
 // come from a device list (`items`, batches) or, for one image, are decoded from `groups`
@@ -113,7 +114,12 @@ struct BankArgs {
     int pipelined;            // 1: warp-specialised row / column pipeline (host-side choice)
     int mtaps;                // 1: row pass with modulated taps (host-side choice)
     int ctas;                 // CTAs per SM: 1 (16 warps each) or 2 (8 warps each)
+    // Modulated-tap row loads by TMA (one image, zero rule, schedule without warp specialisation):
+    // bit s of raw_mask set = frequency s loads its row blocks as boxes of RW columns x TH rows
+    // of the FP32 image through raw_map[s] (zeros outside the image); clear = async copies.
+    unsigned raw_mask;
     ItemGroup groups[kMaxGroups];
+    CUtensorMap raw_map[kMaxRawMaps];
 };
 
 // ---- tensor-core bank (gabor_tc.cu) ----
@@ -423,6 +429,11 @@ struct gabor_bank {
     gb::UnitDev *d_unitdev = nullptr;
     gb::FreqDev *d_freqdev = nullptr;
     std::vector<gb::FreqDev> freqdev;       // host copy (taps pointers into d_taps)
+    // TMA maps of the FP32 row loads, encoded for the image and geometry in raw_key (the
+    // encoding costs host time every call would pay otherwise)
+    std::vector<int64_t> raw_key;
+    unsigned raw_mask = 0;
+    CUtensorMap raw_maps[gb::kMaxRawMaps];
     // work lists of the FP32 bank kernel, keyed by the image shapes of a launch
     std::map<std::vector<int64_t>, std::pair<gb::WorkItem *, int>> worklists;
     size_t max_smem = 0;
