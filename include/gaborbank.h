@@ -334,8 +334,9 @@ gb_status gabor_sdft_noalloc(const float *d_img, int H, int W, int64_t pitch, do
  * pass, the operands that add it back in the column pass's matrix products (4 KB per 64
  * image columns and per 32 image rows of every horizontal pass), and the row pass's operand
  * image (f - c) 2^-e (2 bytes per pixel, 4 under GB_BF16_TC, rows padded to 8 pixels), which
- * the zero rule's row pass loads by TMA.  Sized for the larger of the two forms.  0 for FP32 handles (their intermediates stay on chip) and for invalid
- * arguments.  Host-only; no device work.
+ * the zero rule's row pass loads by TMA.  Sized for the larger of the two forms.  0 for FP32
+ * handles (their intermediates stay on chip) and for invalid arguments.  Host-only; no device
+ * work.
  */
 int64_t gabor_bank_workspace_bytes(gabor_bank_t h, int H, int W);
 

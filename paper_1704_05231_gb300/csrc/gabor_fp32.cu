@@ -50,12 +50,15 @@ struct Smem {
 __host__ __device__ __forceinline__ int ctap_count(const FreqDev &f) { return f.mtaps ? 2 * (f.Tpr + 8) : 0; }
 __host__ __device__ __forceinline__ int phx_count(const FreqDev &f) { return f.mtaps ? 0 : f.SW + 1; }
 
-// Every region starts on a 16-byte boundary (RS, TH multiples of 8; SW odd; Tpad + 8 even); the
-// base on a 128-byte one, and so do the raw buffers under modulated taps (SW = 0, ring rows of
-// 33 float2 pairs, RS and TH multiples of 8, RW a multiple of 4), as TMA writes want.
+// Every region starts on a 16-byte boundary (RS, TH multiples of 8; SW odd; Tpad + 8 even).
+// ALIGN (kernels with TMA row loads): the base on a 128-byte boundary, and so the raw buffers
+// under modulated taps (SW = 0, ring rows of 33 float2 pairs, RS and TH multiples of 8, RW a
+// multiple of 4), as TMA writes want.
+template <bool ALIGN>
 __device__ __forceinline__ Smem carve(unsigned char *base0, const FreqDev &f)
 {
-    unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)base0 + 127) & ~(uintptr_t)127);
+    unsigned char *base =
+        ALIGN ? reinterpret_cast<unsigned char *>(((uintptr_t)base0 + 127) & ~(uintptr_t)127) : base0;
     Smem s;
     s.ring2 = reinterpret_cast<float2 *>(base);
     s.stage = s.ring2 + (size_t)2 * f.RS * (kStripW + 1);
@@ -132,7 +135,9 @@ __device__ __forceinline__ int64_t out_offset(const BankArgs &a, int p, int64_t 
 // with modulated taps; an item
 // of this form may also carry two unpaired units of one frequency ("twins"): two row passes
 // into the two ring planes, whose column passes then fill both halves of the CTA.
-template <bool PIPE, bool MT, int NW>
+// RT: the instance with TMA row loads (one-image launches under the zero rule); the others
+// carry none of its code.
+template <bool PIPE, bool MT, int NW, bool RT>
 __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkItem it, unsigned char *smem_raw)
 {
     const UnitDev u = a.units[it.unit];
@@ -159,7 +164,7 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
     const int nchunks_r = tail1r ? f.Tr / 8 : f.Tpr / 8;
     const int64_t plane = (int64_t)im.H * im.W;
     const int64_t ystride = a.layout ? (int64_t)im.W * a.nplanes : (int64_t)im.W;   // between output rows
-    const Smem sm = carve(smem_raw, f);
+    const Smem sm = carve<RT>(smem_raw, f);
     const float4 *taps4 = reinterpret_cast<const float4 *>(sm.taps);
     const float4 *ctaps4 = reinterpret_cast<const float4 *>(sm.ctaps);
     static_assert(NW == 16 || (NW == 8 && !PIPE), "16 warps, or 8 without the pipelined schedule");
@@ -177,7 +182,7 @@ __device__ __forceinline__ bool gabor_fp32_item(const BankArgs &a, const WorkIte
     volatile int *abort_s = reinterpret_cast<volatile int *>(sm.bars + 4);
     // row blocks by TMA: boxes of RW columns from x0 - Rw (a multiple of 4 floats, 16 bytes, as a
     // tiled copy needs) x TH rows, zeros outside the image; completion on sm.bars[b & 1]
-    const bool rtma = !PIPE && MT && a.imgs == nullptr && ((a.raw_mask >> u.s) & 1u);
+    const bool rtma = RT && !PIPE && MT && a.imgs == nullptr && ((a.raw_mask >> u.s) & 1u);
     if (rtma) {
         if (tid == 0) {
             mbar_init(&sm.bars[0], 1);
@@ -519,7 +524,7 @@ __device__ __forceinline__ WorkItem decode_item(const BankArgs &a, int item)
 // Persistent CTAs pull work items (cost-sorted, largest first) from a device counter that the
 // launcher zeroes before the launch.
 // A CTA stops taking items after a bounded wait gave up (pipelined schedule).
-template <bool PIPE, bool MT, int NW>
+template <bool PIPE, bool MT, int NW, bool RT>
 __global__ void __launch_bounds__(32 * NW, 16 / NW) k_gabor_fp32(const __grid_constant__ BankArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -530,23 +535,30 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_gabor_fp32(const __grid_co
         const int item = next_item;
         if (item >= a.nitems) break;
         const WorkItem it = a.items ? a.items[item] : decode_item(a, item);
-        const bool ok = gabor_fp32_item<PIPE, MT, NW>(a, it, smem_raw);
+        const bool ok = gabor_fp32_item<PIPE, MT, NW, RT>(a, it, smem_raw);
         // shared memory is reused by the next item
         const bool failed = __syncthreads_or(!ok);
-        const int s = a.units[it.unit].s;
-        if ((PIPE || (MT && a.imgs == nullptr && ((a.raw_mask >> s) & 1u))) && threadIdx.x == 0) {
-            uint64_t *bars = carve(smem_raw, a.freqs[s]).bars;
-            for (int i = 0; i < (PIPE ? 4 : 2); ++i) mbar_inval(bars + i);
+        if (PIPE && threadIdx.x == 0) {
+            const FreqDev &f = a.freqs[a.units[it.unit].s];
+            uint64_t *bars = carve<RT>(smem_raw, f).bars;
+            for (int i = 0; i < 4; ++i) mbar_inval(bars + i);
+        }
+        if (RT && !PIPE && MT && threadIdx.x == 0) {
+            const int s = a.units[it.unit].s;
+            if ((a.raw_mask >> s) & 1u) {
+                uint64_t *bars = carve<RT>(smem_raw, a.freqs[s]).bars;
+                for (int i = 0; i < 2; ++i) mbar_inval(bars + i);
+            }
         }
         if (failed) break;
     }
 }
 
-template <bool PIPE, bool MT, int NW>
+template <bool PIPE, bool MT, int NW, bool RT = false>
 cudaError_t prepare_one()
 {
     // the kernel's own static shared memory (the work-queue word) counts against the limit
-    return cudaFuncSetAttribute(k_gabor_fp32<PIPE, MT, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_gabor_fp32<PIPE, MT, NW, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kSmemLimit - kStaticSmemReserve);
 }
 
@@ -558,17 +570,19 @@ cudaError_t gabor_fp32_prepare()
     if (e == cudaSuccess) e = prepare_one<true, true, 16>();
     if (e == cudaSuccess) e = prepare_one<false, false, 8>();
     if (e == cudaSuccess) e = prepare_one<false, true, 8>();
+    if (e == cudaSuccess) e = prepare_one<false, true, 16, true>();
+    if (e == cudaSuccess) e = prepare_one<false, true, 8, true>();
     return e;
 }
 
-template <bool PIPE, bool MT, int NW>
+template <bool PIPE, bool MT, int NW, bool RT = false>
 cudaError_t launch_one(const BankArgs &a, int nitems, size_t smem, int sm_count, cudaStream_t st)
 {
     int cps = 1;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k_gabor_fp32<PIPE, MT, NW>, 32 * NW, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k_gabor_fp32<PIPE, MT, NW, RT>, 32 * NW, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(nitems, std::max(1, cps) * sm_count);
-    k_gabor_fp32<PIPE, MT, NW><<<grid, 32 * NW, smem, st>>>(a);
+    k_gabor_fp32<PIPE, MT, NW, RT><<<grid, 32 * NW, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -582,9 +596,13 @@ cudaError_t launch_gabor_fp32(const BankArgs &a0, int nitems, size_t smem, int s
     if (a.pipelined)
         return a.mtaps ? launch_one<true, true, 16>(a, nitems, smem, sm_count, st)
                        : launch_one<true, false, 16>(a, nitems, smem, sm_count, st);
-    if (a.ctas == 2)
+    const bool rt = a.mtaps && a.raw_mask != 0 && a.imgs == nullptr;   // TMA row loads somewhere
+    if (a.ctas == 2) {
+        if (rt) return launch_one<false, true, 8, true>(a, nitems, smem, sm_count, st);
         return a.mtaps ? launch_one<false, true, 8>(a, nitems, smem, sm_count, st)
                        : launch_one<false, false, 8>(a, nitems, smem, sm_count, st);
+    }
+    if (rt) return launch_one<false, true, 16, true>(a, nitems, smem, sm_count, st);
     return a.mtaps ? launch_one<false, true, 16>(a, nitems, smem, sm_count, st)
                    : launch_one<false, false, 16>(a, nitems, smem, sm_count, st);
 }
