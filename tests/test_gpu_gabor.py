@@ -66,6 +66,39 @@ def test_pitch_and_strided_view(torch_cuda):
     assert rel_err(got, ref) <= FP32_TOL
 
 
+def test_row_loads_by_tma_follow_the_image(torch_cuda):
+    # A one-image launch under the zero rule loads its row blocks as TMA boxes through maps that
+    # the handle encodes once per image and tile geometry and keeps.  Calls on other buffers
+    # must re-encode (each result equal to a fresh handle's), and views whose row pitch is not a
+    # multiple of 16 bytes take the per-thread async copies instead, with the same arithmetic:
+    # the same pixels give the same bits either way.
+    from paper_1704_05231_gb300 import GaborBank
+    torch = torch_cuda
+    H, W = 150, 203
+    th, om, sg = c2_bank()   # R up to 48: several row blocks per item, ragged last strip
+    ta = torch.from_numpy(synth.paper_like(0, H, W)).cuda()
+    tb = torch.from_numpy(synth.pink_noise([5, H, W], H, W)).cuda()
+    wide = torch.zeros((H, W + 2), dtype=torch.float32, device="cuda")   # pitch 820 bytes
+    wide[:, :W] = ta
+    tc = wide[:, :W]
+    wide2 = torch.zeros((H, W + 5), dtype=torch.float32, device="cuda")  # base 4 bytes past
+    wide2[:, 1:W + 1] = ta
+    td = wide2[:, 1:W + 1]
+    with GaborBank(th, om, sg) as g:
+        outs = [g.filter(t).cpu().numpy() for t in (ta, tb, ta, tc, td, tb)]
+    fresh = {}
+    for name, t in (("a", ta), ("b", tb)):
+        with GaborBank(th, om, sg) as g:
+            fresh[name] = g.filter(t).cpu().numpy()
+    for got, name in zip(outs, ("a", "b", "a", "a", "a", "b")):
+        assert np.array_equal(got, fresh[name])
+    # and the first image against the FP64 oracle at sampled pixels
+    xs, ys = sample_points(np.random.default_rng(3), H, W, 200)
+    ref = oracle.gabor_bank(ta.cpu().numpy(), th, om, sg, points=(xs, ys))
+    got = outs[0][:, :, ys, xs]
+    assert rel_err(got, ref) <= FP32_TOL
+
+
 def test_c2_bank_reduced_size_full_parity(torch_cuda):
     # The paper-size bank (sigma up to 16, R = 48) on a 160 x 200 image: halos wider than
     # a quarter of the image, several tiles and ragged edges.
